@@ -1,0 +1,302 @@
+/*
+ * Oracle: the adaptive FSAI smoother S = I - omega G^T G A (Sec. 3.1), the
+ * aFSAI factor aFSAI(A, G_s, k, rho, eps) (adaptive Factorized Sparse
+ * Approximate Inverse, reference [JanFerSarGam15] of the paper), the Lanczos
+ * estimate of lambda_1(G A G^T) and the set-up loop of Algorithm 3.
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * aFSAI, as computed here.  G is lower triangular with G^T G ~ A^{-1}.  Row i
+ * of G is g_i = gt_i / sqrt(psi_i) where gt_i has a unit entry at i and its
+ * other entries gh on the pattern Q_i (indices < i) solve
+ *     A[Q,Q] gh = -A[Q,i],          psi_i = a_ii + A[i,Q] gh,
+ * which minimises gt^T A gt = psi_i (the row's Kaporin functional) over the
+ * pattern and gives (G A G^T)_ii = 1.  The pattern grows in k steps: the
+ * gradient of gt^T A gt with respect to an entry j outside the pattern is
+ * 2 (A gt)_j; the rho entries with the largest gradient are added, the row is
+ * re-solved, and the row stops early when psi decreased by no more than eps
+ * relative to its previous value.
+ *
+ * Block form (b = 3).  The pattern is kept per node: node row I holds a set of
+ * nodes J < I, and each dof row c of node I uses all dofs of those nodes plus
+ * the dofs of I below c (so the diagonal block is lower triangular).  A
+ * candidate node J is scored by the sum of squares of the gradient entries of
+ * its b dofs over the b rows of I; rho counts nodes; the early stop needs
+ * every one of the b rows to have stalled.  At b = 1 all three rules are the
+ * scalar rules above.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+static double a_entry(const obsr *A, int r, int c) {
+  const int b = A->b;
+  const double *blk = or_bsr_find(A, r / b, c / b);
+  return blk ? blk[(r % b) * b + (c % b)] : 0.0;
+}
+
+/* Solve the b dof rows of node I for the node pattern pat[0..np-1]. gh[c] has
+ * room for b*np + b entries. */
+static int solve_rows(const obsr *A, int I, const int *pat, int np,
+                      double **gh, double *psi, double *M, double *L,
+                      double *rhs, int *Q) {
+  const int b = A->b;
+  for (int c = 0; c < b; ++c) {
+    const int i = b * I + c;
+    int m = 0;
+    for (int j = 0; j < np; ++j)
+      for (int e = 0; e < b; ++e) Q[m++] = b * pat[j] + e;
+    for (int e = 0; e < c; ++e) Q[m++] = b * I + e;
+    for (int a = 0; a < m; ++a) {
+      for (int a2 = 0; a2 < m; ++a2) M[a * m + a2] = a_entry(A, Q[a], Q[a2]);
+      rhs[a] = -a_entry(A, Q[a], i);
+    }
+    if (m > 0) {
+      int rc = or_chol(m, M, L);
+      if (rc) return rc;
+      or_chol_solve(m, L, rhs, gh[c]);
+    }
+    double s = a_entry(A, i, i);
+    for (int a = 0; a < m; ++a) s = s + a_entry(A, i, Q[a]) * gh[c][a];
+    if (!(s > 0.0)) return OR_ERR_NOT_SPD;
+    psi[c] = s;
+  }
+  return OR_OK;
+}
+
+static int cmp_int(const void *a, const void *b) {
+  const int x = *(const int *)a, y = *(const int *)b;
+  return (x > y) - (x < y);
+}
+
+int or_afsai(const obsr *A, const obsr *Gs, int ksteps, int rho, double eps,
+             int max_nodes, obsr *G) {
+  const int b = A->b, n = A->nr;
+  const int mmax = b * max_nodes + b;
+  int rc = OR_OK;
+  int *pat = (int *)malloc((size_t)(max_nodes + 1) * sizeof(int));
+  double *ghbuf = (double *)calloc((size_t)b * mmax, sizeof(double));
+  double *gh[3];
+  for (int c = 0; c < b; ++c) gh[c] = ghbuf + (size_t)c * mmax;
+  double psi[3], psi_old[3];
+  double *M = (double *)malloc((size_t)mmax * mmax * sizeof(double));
+  double *L = (double *)malloc((size_t)mmax * mmax * sizeof(double));
+  double *rhs = (double *)malloc((size_t)mmax * sizeof(double));
+  int *Q = (int *)malloc((size_t)mmax * sizeof(int));
+  int *mark = (int *)malloc((size_t)n * sizeof(int));
+  int *cand = (int *)malloc((size_t)n * sizeof(int));
+  double *score = (double *)malloc((size_t)n * sizeof(double));
+  for (int i = 0; i < n; ++i) mark[i] = -1;
+  /* output rows, grown as needed */
+  size_t cap = (size_t)n * 4 + 16, used = 0;
+  int *gcol = (int *)malloc(cap * sizeof(int));
+  double *gval = (double *)malloc(cap * b * b * sizeof(double));
+  int *growptr = (int *)malloc(((size_t)n + 1) * sizeof(int));
+  growptr[0] = 0;
+
+  for (int I = 0; I < n && rc == OR_OK; ++I) {
+    int np = 0;
+    if (Gs)
+      for (int k = Gs->rowptr[I]; k < Gs->rowptr[I + 1]; ++k)
+        if (Gs->col[k] != I && np < max_nodes) pat[np++] = Gs->col[k];
+    rc = solve_rows(A, I, pat, np, gh, psi, M, L, rhs, Q);
+    for (int step = 0; step < ksteps && rc == OR_OK; ++step) {
+      if (np >= max_nodes) break;
+      /* candidates: nodes J < I, outside the pattern, adjacent in A to the
+       * pattern or to I */
+      int nc = 0;
+      for (int j = 0; j < np; ++j) mark[pat[j]] = I;
+      for (int j = 0; j <= np; ++j) {
+        const int K = (j < np) ? pat[j] : I;
+        for (int k = A->rowptr[K]; k < A->rowptr[K + 1]; ++k) {
+          const int J = A->col[k];
+          if (J < I && mark[J] != I) {
+            mark[J] = I;
+            cand[nc++] = J;
+          }
+        }
+      }
+      qsort(cand, nc, sizeof(int), cmp_int);
+      for (int t = 0; t < nc; ++t) {
+        const int J = cand[t];
+        double s = 0.0;
+        for (int c = 0; c < b; ++c)
+          for (int d = 0; d < b; ++d) {
+            double g = 0.0;
+            for (int j = 0; j < np; ++j) {
+              const double *blk = or_bsr_find(A, J, pat[j]);
+              if (blk)
+                for (int e = 0; e < b; ++e) g = g + blk[d * b + e] * gh[c][b * j + e];
+            }
+            const double *blk = or_bsr_find(A, J, I);
+            if (blk) {
+              for (int e = 0; e < c; ++e) g = g + blk[d * b + e] * gh[c][b * np + e];
+              g = g + blk[d * b + c] * 1.0;
+            }
+            s = s + g * g;
+          }
+        score[t] = s;
+      }
+      /* take up to rho best (score > 0, ties to the smaller node) */
+      int want = rho < max_nodes - np ? rho : max_nodes - np, got = 0;
+      for (int p = 0; p < want; ++p) {
+        int best = -1;
+        for (int t = 0; t < nc; ++t)
+          if (score[t] > 0.0 && (best < 0 || score[t] > score[best])) best = t;
+        if (best < 0) break;
+        pat[np + got++] = cand[best];
+        score[best] = -1.0;
+      }
+      if (got == 0) break;
+      np += got;
+      qsort(pat, np, sizeof(int), cmp_int);
+      for (int c = 0; c < b; ++c) psi_old[c] = psi[c];
+      rc = solve_rows(A, I, pat, np, gh, psi, M, L, rhs, Q);
+      if (rc) break;
+      int stalled = 1;
+      for (int c = 0; c < b; ++c)
+        if (psi_old[c] - psi[c] > eps * psi_old[c]) stalled = 0;
+      if (stalled) break;
+    }
+    if (rc) break;
+    /* write row I: pattern blocks then the diagonal block */
+    if (used + np + 1 > cap) {
+      while (used + np + 1 > cap) cap *= 2;
+      gcol = (int *)realloc(gcol, cap * sizeof(int));
+      gval = (double *)realloc(gval, cap * b * b * sizeof(double));
+    }
+    for (int j = 0; j <= np; ++j) {
+      double *blk = gval + (used + j) * b * b;
+      gcol[used + j] = (j < np) ? pat[j] : I;
+      for (int c = 0; c < b; ++c) {
+        const double sq = sqrt(psi[c]);
+        for (int d = 0; d < b; ++d) {
+          double g;
+          if (j < np) g = gh[c][b * j + d];
+          else g = (d < c) ? gh[c][b * np + d] : (d == c ? 1.0 : 0.0);
+          blk[c * b + d] = (j < np || d <= c) ? g / sq : 0.0;
+        }
+      }
+    }
+    used += np + 1;
+    growptr[I + 1] = (int)used;
+  }
+  if (rc == OR_OK) {
+    or_bsr_alloc(G, n, n, b, (int)used);
+    memcpy(G->rowptr, growptr, ((size_t)n + 1) * sizeof(int));
+    memcpy(G->col, gcol, used * sizeof(int));
+    memcpy(G->val, gval, used * b * b * sizeof(double));
+  }
+  free(pat); free(ghbuf); free(M); free(L); free(rhs); free(Q);
+  free(mark); free(cand); free(score); free(gcol); free(gval); free(growptr);
+  return rc;
+}
+
+/* Sturm count: number of eigenvalues of the symmetric tridiagonal matrix
+ * (alpha, beta) that are smaller than x. */
+static int sturm_count(int m, const double *al, const double *be, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; ++i) {
+    d = (i == 0) ? (al[0] - x) : (al[i] - x) - (be[i - 1] * be[i - 1]) / d;
+    if (d == 0.0) d = 1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+/* Largest eigenvalue of G A G^T estimated by m Lanczos steps with full
+ * re-orthogonalisation (one Gram-Schmidt pass against all previous vectors),
+ * from the start vector of level `level` of the counter generator; the
+ * largest Ritz value is found by bisection on Sturm counts. */
+double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
+                       uint64_t seed, int level) {
+  const int n = A->nr * A->b;
+  if (m > n) m = n;
+  if (m > 64) m = 64;
+  double *Vs = (double *)malloc((size_t)m * n * sizeof(double));
+  double *w = (double *)malloc((size_t)n * sizeof(double));
+  double *t1 = (double *)malloc((size_t)n * sizeof(double));
+  double *t2 = (double *)malloc((size_t)n * sizeof(double));
+  double al[64], be[64];
+  for (int i = 0; i < n; ++i)
+    Vs[i] = or_uniform_pm1(seed, (1ull << 62) | ((uint64_t)level << 40) | (uint64_t)i);
+  double nr = sqrt(or_dot(n, Vs, Vs));
+  for (int i = 0; i < n; ++i) Vs[i] = Vs[i] / nr;
+  int mm = m;
+  for (int j = 0; j < m; ++j) {
+    double *v = Vs + (size_t)j * n;
+    or_spmv(GT, v, t1);
+    or_spmv(A, t1, t2);
+    or_spmv(G, t2, w);
+    al[j] = or_dot(n, w, v);
+    for (int i = 0; i < n; ++i) w[i] = w[i] - al[j] * v[i];
+    if (j > 0) {
+      const double *vp = Vs + (size_t)(j - 1) * n;
+      for (int i = 0; i < n; ++i) w[i] = w[i] - be[j - 1] * vp[i];
+    }
+    for (int k = 0; k <= j; ++k) {
+      const double *vk = Vs + (size_t)k * n;
+      const double h = or_dot(n, w, vk);
+      for (int i = 0; i < n; ++i) w[i] = w[i] - h * vk[i];
+    }
+    be[j] = sqrt(or_dot(n, w, w));
+    if (j == m - 1) break;
+    if (!(be[j] > 1e-12 * fabs(al[j]))) {
+      mm = j + 1;
+      break;
+    }
+    double *vn = Vs + (size_t)(j + 1) * n;
+    for (int i = 0; i < n; ++i) vn[i] = w[i] / be[j];
+  }
+  double lo = al[0], hi = al[0];
+  for (int i = 0; i < mm; ++i) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < mm - 1 ? fabs(be[i]) : 0.0);
+    if (al[i] - r < lo) lo = al[i] - r;
+    if (al[i] + r > hi) hi = al[i] + r;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (sturm_count(mm, al, be, mid) >= mm) hi = mid; else lo = mid;
+  }
+  free(Vs); free(w); free(t1); free(t2);
+  return hi;
+}
+
+/* Algorithm 3 (Smoother_SetUp): G from scratch with (k_g, rho_g, eps_g), then
+ * refined with (k_i, rho_i, eps_i) while 2/lambda_1 < omega_bar and the
+ * average number of blocks per block row of G is below rho_bar (at most
+ * max_refine passes).  The smoother's omega obeys omega < min(1, 2/lambda_1)
+ * (Sec. 3.1): it is min(1, omega_safety * 2/lambda_1), the safety factor
+ * covering the Lanczos under-estimate of lambda_1. */
+int or_smoother_setup(const obsr *A, const or_params *p, int level, obsr *G,
+                      obsr *GT, double *omega, double *lmax, int *npasses) {
+  int rc = or_afsai(A, NULL, p->k_g, p->rho_g, p->eps_g, p->max_g_nodes, G);
+  if (rc) return rc;
+  or_transpose(G, GT);
+  double lam = or_lanczos_lmax(A, G, GT, p->lanczos_m, p->seed, level);
+  double w = 2.0 / lam;
+  int passes = 0;
+  while (w < p->omega_bar &&
+         (double)G->rowptr[G->nr] / (double)G->nr < p->rho_bar &&
+         passes < p->max_refine) {
+    obsr G2;
+    rc = or_afsai(A, G, p->k_i, p->rho_i, p->eps_i, p->max_g_nodes, &G2);
+    if (rc) return rc;
+    or_bsr_free(G);
+    or_bsr_free(GT);
+    *G = G2;
+    or_transpose(G, GT);
+    lam = or_lanczos_lmax(A, G, GT, p->lanczos_m, p->seed, level);
+    w = 2.0 / lam;
+    ++passes;
+  }
+  double om = p->omega_safety * w;
+  if (om > 1.0) om = 1.0;
+  *omega = om;
+  *lmax = lam;
+  *npasses = passes;
+  return OR_OK;
+}

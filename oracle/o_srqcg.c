@@ -1,0 +1,250 @@
+/*
+ * Oracle: test-space generation by Simultaneous Rayleigh Quotient Minimisation
+ * by Conjugate Gradients, SRQCG (Sec. 3.2, Algorithm 4), on S = G A G^T.
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * For each column z of Z the Rayleigh quotient rq(z) = z^T S z / z^T z is
+ * lowered along a search direction p.  With a = p^T S z, b = p^T S p,
+ * c = p^T z, d = p^T p, e = z^T S z, f = z^T z, rq(z + alpha p) is
+ * (e + 2 alpha a + alpha^2 b) / (f + 2 alpha c + alpha^2 d), whose stationary
+ * points solve (bc - ad) alpha^2 + (bf - de) alpha + (af - ce) = 0; the root
+ * printed in Algorithm 4 is (de - bf + sqrt(Delta)) / (2 (bc - ad)).  Here both
+ * roots are formed and the one giving the smaller quotient is kept (the
+ * printed one whenever it is the minimiser).  The new gradient is
+ * 2 (S z - rq z) / f with rq the Rayleigh quotient z^T S z / f, the direction
+ * is made S-conjugate to the previous one (beta = -g^T S p / b), and every
+ * k_ritz iterations the block Z is rotated by the Ritz vectors of the pencil
+ * (Z^T S Z, Z^T Z).  At the end V = G^T Z with orthonormalised columns.
+ *
+ * All inner products use the fixed-order or_dot, all sparse products the
+ * fixed-order or_spmv; vector updates are single rounded operations per
+ * entry.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+static void apply_s(const obsr *A, const obsr *G, const obsr *GT,
+                    const double *x, double *y, double *t1, double *t2) {
+  or_spmv(GT, x, t1);
+  or_spmv(A, t1, t2);
+  or_spmv(G, t2, y);
+}
+
+/* Modified Gram-Schmidt on the columns of the n x t column-major V, in column
+ * order; each column is divided by its norm. */
+void or_mgs(int n, int t, double *V) {
+  for (int j = 0; j < t; ++j) {
+    double *vj = V + (size_t)j * n;
+    for (int i = 0; i < j; ++i) {
+      const double *vi = V + (size_t)i * n;
+      const double r = or_dot(n, vi, vj);
+      for (int k = 0; k < n; ++k) vj[k] = vj[k] - r * vi[k];
+    }
+    const double nr = sqrt(or_dot(n, vj, vj));
+    if (nr > 0.0)
+      for (int k = 0; k < n; ++k) vj[k] = vj[k] / nr;
+  }
+}
+
+/* Generalised symmetric eigenproblem H U = M U diag(lam), M SPD, t x t
+ * row-major.  M = L L^T; C = L^{-1} (L^{-1} H)^T, symmetrised as
+ * (C + C^T) * 0.5; cyclic Jacobi rotations (row by row over p < q) until the
+ * off-diagonal mass is negligible; eigenvalues sorted ascending (ties keep
+ * index order); U = L^{-T} W; each column of U signed so that its entry of
+ * largest magnitude (first on ties) is positive. */
+int or_gen_eig(int t, const double *H, const double *M, double *U,
+               double *lam) {
+  double L[64 * 64], W1[64 * 64], C[64 * 64], Wv[64 * 64], tmp[64];
+  if (t > 64) return OR_ERR_ARG;
+  int rc = or_chol(t, M, L);
+  if (rc) return rc;
+  for (int j = 0; j < t; ++j)
+    for (int i = 0; i < t; ++i) {
+      double s = H[i * t + j];
+      for (int k = 0; k < i; ++k) s = s - L[i * t + k] * W1[k * t + j];
+      W1[i * t + j] = s / L[i * t + i];
+    }
+  for (int j = 0; j < t; ++j)
+    for (int i = 0; i < t; ++i) {
+      double s = W1[j * t + i];
+      for (int k = 0; k < i; ++k) s = s - L[i * t + k] * C[k * t + j];
+      C[i * t + j] = s / L[i * t + i];
+    }
+  for (int i = 0; i < t; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double v = (C[i * t + j] + C[j * t + i]) * 0.5;
+      C[i * t + j] = v;
+      C[j * t + i] = v;
+    }
+  for (int i = 0; i < t; ++i)
+    for (int j = 0; j < t; ++j) Wv[i * t + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, dg = 0.0;
+    for (int p = 0; p < t; ++p) {
+      dg = dg + C[p * t + p] * C[p * t + p];
+      for (int q = p + 1; q < t; ++q) off = off + C[p * t + q] * C[p * t + q];
+    }
+    if (!(off > 1e-32 * dg)) break;
+    for (int p = 0; p < t - 1; ++p)
+      for (int q = p + 1; q < t; ++q) {
+        const double apq = C[p * t + q];
+        if (apq == 0.0) continue;
+        const double th = (C[q * t + q] - C[p * t + p]) / (2.0 * apq);
+        const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(tt * tt + 1.0);
+        const double s = tt * c;
+        for (int k = 0; k < t; ++k) {
+          const double xp = C[k * t + p], xq = C[k * t + q];
+          C[k * t + p] = c * xp - s * xq;
+          C[k * t + q] = s * xp + c * xq;
+        }
+        for (int k = 0; k < t; ++k) {
+          const double xp = C[p * t + k], xq = C[q * t + k];
+          C[p * t + k] = c * xp - s * xq;
+          C[q * t + k] = s * xp + c * xq;
+        }
+        for (int k = 0; k < t; ++k) {
+          const double xp = Wv[k * t + p], xq = Wv[k * t + q];
+          Wv[k * t + p] = c * xp - s * xq;
+          Wv[k * t + q] = s * xp + c * xq;
+        }
+        C[p * t + q] = 0.0;
+        C[q * t + p] = 0.0;
+      }
+  }
+  int order[64];
+  for (int i = 0; i < t; ++i) order[i] = i;
+  for (int i = 0; i < t; ++i) {
+    int best = i;
+    for (int j = i + 1; j < t; ++j)
+      if (C[order[j] * t + order[j]] < C[order[best] * t + order[best]]) best = j;
+    const int tmpi = order[best];
+    for (int j = best; j > i; --j) order[j] = order[j - 1];
+    order[i] = tmpi;
+  }
+  for (int jj = 0; jj < t; ++jj) {
+    const int j = order[jj];
+    lam[jj] = C[j * t + j];
+    for (int i = t - 1; i >= 0; --i) {
+      double s = Wv[i * t + j];
+      for (int k = t - 1; k > i; --k) s = s - L[k * t + i] * tmp[k];
+      tmp[i] = s / L[i * t + i];
+    }
+    int im = 0;
+    for (int i = 1; i < t; ++i)
+      if (fabs(tmp[i]) > fabs(tmp[im])) im = i;
+    const double sg = tmp[im] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < t; ++i) U[i * t + jj] = sg * tmp[i];
+  }
+  return OR_OK;
+}
+
+/* Step length of Algorithm 4: the root of
+ * (bc - ad) alpha^2 + (bf - de) alpha + (af - ce) = 0 that minimises
+ * rq(alpha) = (e + 2 alpha a + alpha^2 b) / (f + 2 alpha c + alpha^2 d);
+ * with p1 = de - bf, q1 = bc - ad, r1 = af - ce the roots are
+ * (p1 +- sqrt(p1^2 - 4 q1 r1)) / (2 q1) (the + root is the one printed), and
+ * q1 = 0 leaves the linear root r1 / p1. */
+double or_rq_line_min(double a, double b, double c, double d, double e,
+                      double f) {
+  const double p1 = d * e - b * f;
+  const double q1 = b * c - a * d;
+  const double r1 = a * f - c * e;
+  const double delta = p1 * p1 - (4.0 * q1) * r1;
+  if (q1 != 0.0 && delta >= 0.0) {
+    const double sq = sqrt(delta);
+    const double a1 = (p1 + sq) / (2.0 * q1), a2 = (p1 - sq) / (2.0 * q1);
+    const double n1 = (e + (2.0 * a1) * a) + (a1 * a1) * b, d1 = (f + (2.0 * a1) * c) + (a1 * a1) * d;
+    const double n2 = (e + (2.0 * a2) * a) + (a2 * a2) * b, d2 = (f + (2.0 * a2) * c) + (a2 * a2) * d;
+    return (n1 / d1 <= n2 / d2) ? a1 : a2;
+  }
+  if (q1 == 0.0 && p1 != 0.0) return r1 / p1;
+  return 0.0;
+}
+
+int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
+             int k_ritz, int t, const double *V0, double *V) {
+  const int n = A->nr * A->b;
+  const size_t nt = (size_t)n * t;
+  double *Z = (double *)malloc(nt * sizeof(double));
+  double *P = (double *)malloc(nt * sizeof(double));
+  double *SZall = (double *)malloc(nt * sizeof(double));
+  double *SZ = (double *)malloc((size_t)n * sizeof(double));
+  double *SP = (double *)malloc((size_t)n * sizeof(double));
+  double *Gv = (double *)malloc((size_t)n * sizeof(double));
+  double *t1 = (double *)malloc((size_t)n * sizeof(double));
+  double *t2 = (double *)malloc((size_t)n * sizeof(double));
+  double f[64], H[64 * 64], M[64 * 64], U[64 * 64], lam[64];
+  int rc = OR_OK;
+  if (t > 64) return OR_ERR_ARG;
+
+  /* Z0 = (I - S) V0, orthonormalised */
+  for (int i = 0; i < t; ++i) {
+    const double *v = V0 + (size_t)i * n;
+    double *z = Z + (size_t)i * n;
+    apply_s(A, G, GT, v, SZ, t1, t2);
+    for (int k = 0; k < n; ++k) z[k] = v[k] - SZ[k];
+  }
+  or_mgs(n, t, Z);
+  /* first residuals and directions: q = z^T S z (z has unit norm), P = 2R */
+  for (int i = 0; i < t; ++i) {
+    double *z = Z + (size_t)i * n, *p = P + (size_t)i * n;
+    apply_s(A, G, GT, z, SZ, t1, t2);
+    const double q = or_dot(n, z, SZ);
+    for (int k = 0; k < n; ++k) p[k] = 2.0 * (SZ[k] - q * z[k]);
+    f[i] = 1.0;
+  }
+  for (int it = 1; it <= kmax && rc == OR_OK; ++it) {
+    if (k_ritz > 0 && it % k_ritz == 0) {
+      for (int j = 0; j < t; ++j) apply_s(A, G, GT, Z + (size_t)j * n, SZall + (size_t)j * n, t1, t2);
+      for (int i = 0; i < t; ++i)
+        for (int j = i; j < t; ++j) {
+          const double h = or_dot(n, Z + (size_t)i * n, SZall + (size_t)j * n);
+          const double m = or_dot(n, Z + (size_t)i * n, Z + (size_t)j * n);
+          H[i * t + j] = h;
+          H[j * t + i] = h;
+          M[i * t + j] = m;
+          M[j * t + i] = m;
+        }
+      rc = or_gen_eig(t, H, M, U, lam);
+      if (rc) break;
+      /* Z <- Z U, column j = sum_i Z_i U[i][j], i ascending from 0 */
+      for (int k = 0; k < n; ++k) {
+        double row[64];
+        for (int j = 0; j < t; ++j) {
+          double s = 0.0;
+          for (int i = 0; i < t; ++i) s = s + Z[(size_t)i * n + k] * U[i * t + j];
+          row[j] = s;
+        }
+        for (int j = 0; j < t; ++j) Z[(size_t)j * n + k] = row[j];
+      }
+      for (int i = 0; i < t; ++i) f[i] = 1.0;
+    }
+    for (int i = 0; i < t; ++i) {
+      double *z = Z + (size_t)i * n, *p = P + (size_t)i * n;
+      apply_s(A, G, GT, z, SZ, t1, t2);
+      apply_s(A, G, GT, p, SP, t1, t2);
+      const double a = or_dot(n, p, SZ), b = or_dot(n, p, SP), c = or_dot(n, p, z);
+      const double d = or_dot(n, p, p), e = or_dot(n, z, SZ), fi = f[i];
+      if (!(b > 0.0)) continue;
+      const double alpha = or_rq_line_min(a, b, c, d, e, fi);
+      for (int k = 0; k < n; ++k) z[k] = z[k] + alpha * p[k];
+      apply_s(A, G, GT, z, SZ, t1, t2);
+      const double fn = or_dot(n, z, z);
+      const double q = or_dot(n, z, SZ) / fn;
+      for (int k = 0; k < n; ++k) Gv[k] = (2.0 * (SZ[k] - q * z[k])) / fn;
+      const double beta = -(or_dot(n, Gv, SP) / b);
+      for (int k = 0; k < n; ++k) p[k] = Gv[k] + beta * p[k];
+      f[i] = fn;
+    }
+  }
+  if (rc == OR_OK) {
+    for (int i = 0; i < t; ++i) or_spmv(GT, Z + (size_t)i * n, V + (size_t)i * n);
+    or_mgs(n, t, V);
+  }
+  free(Z); free(P); free(SZall); free(SZ); free(SP); free(Gv); free(t1); free(t2);
+  return rc;
+}

@@ -1,0 +1,143 @@
+"""Pins of the oracle's finite-element assembly (the problem class of Sec. 1:
+K is the integral of B^T D B with an SPD, isotropic D).  Each pin follows from
+linear elasticity, not from the oracle's own formulas."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def lame(nu, E=1.0):
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    return lam, mu
+
+
+def elem_coords(hx, hy, hz):
+    return np.array([[(a & 1) * hx, ((a >> 1) & 1) * hy, ((a >> 2) & 1) * hz] for a in range(8)])
+
+
+@pytest.mark.parametrize("nu,h", [(0.3, (1.0, 1.0, 1.0)), (0.45, (1.0, 1.0, 0.05)),
+                                  (0.2, (0.5, 2.0, 1.5))])
+def test_ke0_rigid_modes_and_definiteness(orc, nu, h):
+    Ke = orc.ke0(nu, *h)
+    assert np.array_equal(Ke, Ke.T)
+    ev = np.linalg.eigvalsh(Ke)
+    scale = ev.max()
+    assert np.sum(np.abs(ev) < 1e-12 * scale) == 6   # three translations, three rotations
+    assert np.all(ev[6:] > 1e-9 * scale)
+
+
+@pytest.mark.parametrize("nu,h", [(0.3, (1.0, 1.0, 1.0)), (0.45, (1.0, 1.0, 0.05)),
+                                  (0.2, (0.5, 2.0, 1.5))])
+def test_ke0_constant_strain_energy(orc, nu, h):
+    """u = eps x has energy V_e (lambda tr(eps)^2 + 2 mu eps:eps): the trilinear
+    element reproduces linear fields and 2x2x2 Gauss integrates the constant
+    integrand exactly; this checks D, B, the Voigt shear convention and the
+    Jacobian together."""
+    rng = np.random.default_rng(1)
+    Ke = orc.ke0(nu, *h)
+    X = elem_coords(*h)
+    lam, mu = lame(nu)
+    vol = h[0] * h[1] * h[2]
+    for _ in range(5):
+        A = rng.normal(size=(3, 3))
+        eps = 0.5 * (A + A.T)
+        W_ = 0.5 * (A - A.T)
+        u = (X @ eps.T).reshape(-1)
+        energy = u @ Ke @ u
+        expect = vol * (lam * np.trace(eps) ** 2 + 2 * mu * np.sum(eps * eps))
+        assert abs(energy - expect) <= 1e-12 * abs(expect)
+        # adding an infinitesimal rotation changes nothing
+        u2 = (X @ (eps + W_).T).reshape(-1)
+        assert abs(u2 @ Ke @ u2 - expect) <= 1e-11 * abs(expect)
+
+
+def _mesh(orc, nx, ny, nz, E=None, clamp=-1, h=(1.0, 1.0, 1.0), nu=0.3):
+    E = np.ones(nx * ny * nz) if E is None else E
+    return orc.assemble(nx, ny, nz, *h, nu, E, clamp)
+
+
+def test_K_bitwise_symmetric(orc):
+    E = np.exp(np.random.default_rng(2).normal(size=4 * 3 * 2))
+    K, _ = _mesh(orc, 4, 3, 2, E, clamp=2)
+    D = K.todense()
+    assert np.array_equal(D, D.T)
+
+
+def test_rigid_body_modes_in_nullspace(orc):
+    nx, ny, nz = 3, 4, 2
+    h = (0.7, 1.0, 0.4)
+    E = np.exp(np.random.default_rng(3).normal(size=nx * ny * nz))
+    K, nm = _mesh(orc, nx, ny, nz, E, clamp=-1, h=h)
+    V = orc.rbm(nx, ny, nz, *h, nm)
+    D = K.todense()
+    R = D @ V
+    assert np.abs(R).max() <= 1e-12 * np.abs(D).max() * np.abs(V).max()
+    # and they are the whole null space
+    ev = np.linalg.eigvalsh(D)
+    assert np.sum(np.abs(ev) < 1e-10 * ev.max()) == 6
+
+
+def test_patch_test(orc):
+    """A linear displacement field leaves zero force at interior nodes, and
+    prescribing it on the boundary reproduces it inside."""
+    nx, ny, nz = 4, 3, 3
+    h = (1.0, 0.5, 2.0)
+    K, nm = _mesh(orc, nx, ny, nz, np.full(nx * ny * nz, 3.0), clamp=-1, h=h, nu=0.35)
+    D = K.todense()
+    rng = np.random.default_rng(4)
+    a, B = rng.normal(size=3), rng.normal(size=(3, 3))
+    coords, interior = [], []
+    for iz in range(nz + 1):
+        for iy in range(ny + 1):
+            for ix in range(nx + 1):
+                coords.append((ix * h[0], iy * h[1], iz * h[2]))
+                interior.append(0 < ix < nx and 0 < iy < ny and 0 < iz < nz)
+    X = np.array(coords)
+    u = (a + X @ B.T).reshape(-1)
+    f = D @ u
+    idof = np.repeat(np.array(interior), 3)
+    assert np.abs(f[idof]).max() <= 1e-12 * np.abs(D).max() * np.abs(u).max()
+    # Dirichlet problem with the linear field on the boundary
+    bdof = ~idof
+    ui = np.linalg.solve(D[np.ix_(idof, idof)], -D[np.ix_(idof, bdof)] @ u[bdof])
+    assert np.abs(ui - u[idof]).max() <= 1e-11 * np.abs(u).max()
+
+
+def test_clamping_and_numbering(orc):
+    p = W.cube16(3)
+    K, nm = orc.assemble(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.nu, p.E, p.clamp_axis)
+    assert K.nr == p.free_nodes() == 4 * 4 * 3
+    free = nm[nm >= 0]
+    assert np.array_equal(free, np.arange(K.nr))
+    assert np.all(nm[:16] == -1)  # the z = 0 layer
+    pb = W.beam(4, 2, 2)
+    K2, nm2 = orc.assemble(pb.nx, pb.ny, pb.nz, 1.0, 1.0, 1.0, pb.nu, pb.E, pb.clamp_axis)
+    assert K2.nr == pb.free_nodes()
+    assert np.all(nm2.reshape(3, 3, 5)[:, :, 0] == -1)  # the x = 0 face
+
+
+def test_load_resultants(orc):
+    nx, ny, nz, h = 3, 2, 4, (0.5, 1.0, 0.25)
+    _, nm = _mesh(orc, nx, ny, nz, clamp=-1, h=h)
+    g = np.array([0.3, -1.0, 2.0])
+    f = orc.load_body(nx, ny, nz, *h, g, nm)
+    vol = nx * ny * nz * h[0] * h[1] * h[2]
+    assert np.allclose(f.reshape(-1, 3).sum(0), g * vol, rtol=1e-13, atol=0)
+    p = np.random.default_rng(5).uniform(size=nx * ny)
+    f = orc.load_top_pressure(nx, ny, nz, *h, p, nm)
+    assert np.isclose(f.reshape(-1, 3)[:, 2].sum(), -(p.sum() * h[0] * h[1]), rtol=1e-13)
+    assert np.all(f.reshape(-1, 3)[:, :2] == 0)
+    f = orc.load_end_shear(nx, ny, nz, *h, -1.0, nm)
+    assert np.isclose(f.reshape(-1, 3)[:, 2].sum(), -1.0, rtol=1e-13)
+
+
+def test_workload_recipes_shapes():
+    p = W.slab(8, 6, 4)
+    assert p.E.size == 8 * 6 * 4 and set(np.unique(p.E)) == {1.0, 1e4}
+    assert np.all(p.E[: 8 * 6] == 1.0)  # bottom layer soft
+    q = W.cube_simp(6)
+    assert np.allclose(q.E, q.rho ** 3) and q.rho.min() >= 0.1
+    c = W.cube_batched(5, 3)
+    assert c.nodal.shape == (3, 36, 3)
