@@ -1,0 +1,188 @@
+/*
+ * aspamg.h -- C ABI of the GB300 library for the adaptive AMG solver aSP-AMG
+ * (Franceschini, Paludetto Magri, Mazzucco, Spiezia, Janna, "A robust adaptive
+ * algebraic multigrid linear solver for structural mechanics", arXiv
+ * 1902.01715), with 3x3 nodal blocks.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are block CSR with 3x3 blocks ("BSR3"): rowptr[nnodes+1],
+ *    colind[nnzb] (ascending inside a row), vals[nnzb*9] with each block
+ *    row-major.  Vectors have 3*nnodes entries, dof 3*I+c = component c of
+ *    node I.  Several right-hand sides are stored column-major (n x k).
+ *  - Pointers are device pointers unless the argument says "host" or a
+ *    `mem` argument selects AMG_MEM_HOST.  Device pointers must be usable on
+ *    the handle's stream; the library never frees caller memory.
+ *  - Every function returns 0 (AMG_OK) or a negative AMG_ERR_* code and never
+ *    aborts or throws.  amg_last_error() gives a one-line description of the
+ *    last failure on the calling thread.
+ *  - The handle owns all hierarchy storage (device) and frees it in amg_free.
+ *    Calls on one handle must not run concurrently.
+ */
+#ifndef ASPAMG_H
+#define ASPAMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMG_OK 0
+#define AMG_ERR_ARG (-1)           /* invalid argument or unsupported size */
+#define AMG_ERR_NOT_SPD (-2)       /* non-positive pivot (FSAI row, Cholesky) */
+#define AMG_ERR_BREAKDOWN (-3)     /* p^T A p <= 0 or a NaN/Inf in PCG */
+#define AMG_ERR_NOT_CONVERGED (-4) /* maxit reached; X holds the last iterate */
+#define AMG_ERR_CUDA (-5)          /* a CUDA runtime call failed */
+#define AMG_ERR_COARSENING (-6)    /* coarsening stalled on a large level */
+#define AMG_ERR_MEM (-7)           /* allocation failed */
+
+#define AMG_MEM_DEVICE 0
+#define AMG_MEM_HOST 1
+
+/* precision of the V-cycle (smoother, transfers, level matrices).  The outer
+ * CG recurrence, its dot products, the true residual and the coarse Cholesky
+ * are FP64 in every mode. */
+#define AMG_FP64 0
+#define AMG_FP32 1        /* all V-cycle data and arithmetic FP32 */
+#define AMG_FP32_BF16GP 2 /* FP32, with G, G^T, P, R stored as bf16 */
+
+typedef struct amg_handle_s *amg_handle;
+
+/* Parameters.  amg_default_params fills the defaults of the paper's Table
+ * "TestParam" (Sec. 4.1): k_g = 4, eps_g = 1e-3, n_tv = 10, n_rq = 10,
+ * theta = 5, n_max = 5, kappa_p = 50, with rho_g counted in nodes (2 per
+ * step) for the nodal-block form; the other defaults are the library's
+ * readings of values the paper leaves open. */
+typedef struct {
+  int k_g, rho_g;         /* aFSAI adaptive steps, nodes added per step (Sec. 3.1) */
+  double eps_g;           /* aFSAI exit tolerance */
+  int k_i, rho_i;         /* refinement calls of Algorithm 3 */
+  double eps_i;
+  double omega_bar;       /* Algorithm 3: refine while omega < omega_bar ... */
+  double rho_bar;         /* ... and blocks per block row of G < rho_bar */
+  int max_refine;         /* at most this many refinement calls */
+  int max_g_nodes;        /* cap on off-diagonal nodes of a G row (<= 32) */
+  int lanczos_m;          /* Lanczos steps for lambda_1(G A G^T) (<= 64) */
+  double omega_safety;    /* omega = min(1, omega_safety * 2 / lambda_1) */
+  int n_tv, n_rq, k_ritz; /* test space size, SRQCG iterations, Ritz period (Alg. 4) */
+  int theta;              /* SoC connections kept per node (Sec. 3.3) */
+  int n_max, d_p;         /* DPLS: interpolation nodes, path length (Alg. 5) */
+  double kappa_p;         /* DPLS conditioning bound */
+  int n_coarse;           /* dense Cholesky once a level has <= n_coarse dofs */
+  int max_levels;
+  double max_coarse_ratio;/* stop coarsening when n_{k+1}/n_k exceeds this */
+  int vcycle_prec;        /* AMG_FP64 | AMG_FP32 | AMG_FP32_BF16GP */
+  int maxit;              /* PCG iteration limit (1000, as in Sec. 4.2) */
+  unsigned long long seed;/* counter generator: test-space padding, Lanczos start */
+} amg_params;
+
+typedef struct {
+  int nlev;
+  int n_it;               /* PCG iterations of the last solve (max over columns) */
+  double C_gd, C_op, C_fs;/* grid, operator and FSAI complexity (Sec. 4.1) */
+  double T_sm, T_ts, T_cs, T_pl, T_rap, T_p; /* set-up phase times, seconds */
+  double T_s;             /* last solve, seconds */
+  int level_nodes[32];
+  int level_nnzb[32];
+  int level_g_nnzb[32];
+  double level_omega[32];
+} amg_stats;
+
+/* Fill *p with the defaults.  Returns AMG_ERR_ARG for p == NULL. */
+int amg_default_params(amg_params *p);
+
+/* Build the hierarchy of Algorithm 1 (Sec. 2) for the SPD matrix K:
+ * per level the aFSAI smoother of Algorithm 3, the SRQCG test space of
+ * Algorithm 4 started from the near-null space V0 (padded to n_tv columns by
+ * the counter generator, Sec. 3.2), the affinity C/F split of Sec. 3.3, the
+ * DPLS prolongation of Algorithm 5 and A_{k+1} = P^T A P; a dense Cholesky
+ * factor on the last level.
+ *   K: rowptr, colind, vals as described above, in `mem` memory; copied.
+ *   V0: 3*nnodes x ntv0 column-major near-null space (e.g. the 6 rigid-body
+ *       modes), ntv0 <= n_tv, in `mem` memory; copied.
+ *   stream: cudaStream_t to run on (NULL: the legacy default stream).
+ * Errors: AMG_ERR_ARG (bad sizes/params), AMG_ERR_NOT_SPD, AMG_ERR_COARSENING,
+ * AMG_ERR_CUDA, AMG_ERR_MEM.  On error *out is NULL. */
+int amg_setup(const amg_params *p, int nnodes, int nnzb, const int *rowptr,
+              const int *colind, const double *vals, int ntv0,
+              const double *V0, int mem, void *stream, amg_handle *out);
+
+/* K changed values on the same pattern: rebuild the whole hierarchy (the
+ * adaptive set-up depends on the values).  vals in `mem` memory. */
+int amg_update_values(amg_handle h, const double *vals, int mem);
+
+/* Solve K X = B by PCG with one V(1,1)-cycle per iteration, x0 = 0, stopping
+ * column j when ||r_j||_2 <= rtol ||b_j||_2 on the recurrence residual
+ * (Sec. 4).  B and X are 3*nnodes x k column-major in `mem` memory (host
+ * buffers are staged through the device inside the call).  iters[k] and
+ * relres[k] (host) receive each column's iteration count and final
+ * ||r||/||b||.  k > 1 runs the batched (block SpMM) path with per-column
+ * convergence masks.  Returns AMG_ERR_NOT_CONVERGED if a column hit maxit
+ * (X still holds its last iterate) or AMG_ERR_BREAKDOWN. */
+int amg_solve(amg_handle h, int k, const double *B, double *X, double rtol,
+              int *iters, double *relres, int mem);
+
+/* Adjoint solve K Lambda = G reusing the hierarchy (K is symmetric), i.e.
+ * dL/df = K^{-1} dL/du.  Same arguments and errors as amg_solve. */
+int amg_adjoint(amg_handle h, int k, const double *G, double *Lambda,
+                double rtol, int *iters, double *relres, int mem);
+
+/* Element sensitivities on a structured Q1-hex mesh (device pointers):
+ *   grad[e] = -dEdp[e] * lam_e^T Ke0 u_e,
+ * the derivative of a functional L with adjoint Lam (K Lam = dL/du) with
+ * respect to an element parameter p_e when K_e = E_e(p_e) Ke0.
+ * conn: ne x 8 free-node indices (-1 for a clamped node), local node
+ * a = dx + 2 dy + 4 dz; Ke0: 24 x 24 row-major element matrix for E = 1;
+ * U, Lam: 3*nnodes vectors.  No handle needed. */
+int amg_elem_grad(int ne, const int *conn, const double *Ke0,
+                  const double *dEdp, const double *U, const double *Lam,
+                  double *grad, void *stream);
+
+int amg_get_stats(amg_handle h, amg_stats *s);
+void amg_free(amg_handle h);
+const char *amg_strerror(int code);
+const char *amg_last_error(void);
+
+/* ---- inspection (used by the parity tests) ---- */
+/* info[0..5] = nodes, nnzb(A), nnzb(G), nnzb(P), coarse nodes, refinement
+ * passes of level `lev`; dbl[0..1] = omega, lambda_1 estimate. */
+int amg_level_info(amg_handle h, int lev, int *info, double *dbl);
+/* Host copies of level matrices: which = 0 A, 1 G, 2 G^T, 3 P, 4 R; arrays
+ * sized from amg_level_info (rowptr nodes+1 / coarse nodes+1 for R). */
+int amg_level_matrix(amg_handle h, int lev, int which, int *rowptr, int *col,
+                     double *val);
+int amg_level_cf(amg_handle h, int lev, int *cf);          /* host, 1 = C */
+int amg_level_testspace(amg_handle h, int lev, double *V); /* host, n x n_tv */
+/* One V-cycle z = B(y) in the handle's precision (device vectors). */
+int amg_vcycle(amg_handle h, const double *y, double *z);
+
+/* ---- structured Q1-hex elasticity problems (problem generation) ----
+ * Mesh: nodes (ix,iy,iz) with global id ix + (nx+1)(iy + (ny+1) iz) at
+ * (ix hx, iy hy, iz hz); element (ex,ey,ez) id ex + nx (ey + ny ez); clamp
+ * 0: nodes with ix = 0, 2: nodes with iz = 0, -1: none; free nodes keep
+ * increasing global id.  K = sum_e E_e Ke0 (Sec. 1: K integrates B^T D B;
+ * D is linear in E), Ke0 by 2x2x2 Gauss quadrature. */
+int amg_fe_size(int nx, int ny, int nz, int clamp, int *nfree, int *nnzb);
+/* node_map (host, (nx+1)(ny+1)(nz+1)) = free index or -1; rowptr/colind
+ * (device) receive the 27-point block pattern; vals (device) the values for
+ * the element moduli E (device, ne).  Ke0 (device, 576) receives the
+ * element matrix for E = 1. */
+int amg_fe_assemble(int nx, int ny, int nz, double hx, double hy, double hz,
+                    double nu, const double *E, int clamp, int *node_map,
+                    int *rowptr, int *colind, double *vals, double *Ke0,
+                    void *stream);
+/* Load vectors (device, 3*nfree, accumulated into f):
+ * kind 0 body force g[3] per unit volume; kind 1 pressure p[nx*ny] on the top
+ * face pushing -z; kind 2 end shear of resultant g[0] in z on the x = nx*hx
+ * face; kind 3 nodal forces p[(nx+1)(ny+1)*3] on the top-face nodes. */
+int amg_fe_load(int nx, int ny, int nz, double hx, double hy, double hz,
+                int clamp, int kind, const double *g, const double *p,
+                double *f, void *stream);
+/* Rigid-body modes (device, 3*nfree x 6 column-major) about the mesh centre. */
+int amg_fe_rbm(int nx, int ny, int nz, double hx, double hy, double hz,
+               int clamp, double *V, void *stream);
+/* Element connectivity in free-node numbering (device, ne x 8). */
+int amg_fe_conn(int nx, int ny, int nz, int clamp, int *conn, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

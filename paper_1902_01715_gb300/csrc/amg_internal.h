@@ -1,0 +1,200 @@
+// Internal declarations of the aSP-AMG GB300 library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/aspamg.h"
+
+namespace amg {
+
+void set_error(const char *fmt, ...);
+
+#define AMG_CU(x)                                                                    \
+  do {                                                                               \
+    cudaError_t e_ = (x);                                                            \
+    if (e_ != cudaSuccess) {                                                         \
+      ::amg::set_error("%s:%d %s: %s", __FILE__, __LINE__, #x, cudaGetErrorString(e_)); \
+      return AMG_ERR_CUDA;                                                           \
+    }                                                                                \
+  } while (0)
+
+#define AMG_TRY(x)            \
+  do {                        \
+    int rc_ = (x);            \
+    if (rc_) return rc_;      \
+  } while (0)
+
+#define AMG_LAUNCH_CHECK() AMG_CU(cudaGetLastError())
+
+// Owning device buffer (cudaMalloc / cudaFree).
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf &operator=(DBuf &&o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  int alloc(size_t count) {
+    release();
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return AMG_ERR_MEM;
+    }
+    n = count;
+    return AMG_OK;
+  }
+  int zero(cudaStream_t s) {
+    if (!p) return AMG_OK;
+    AMG_CU(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    return AMG_OK;
+  }
+};
+
+// Block CSR matrix with 3x3 blocks, values row-major per block ("AoS"); the
+// pattern is mirrored on the host for the integer graph work of the set-up.
+struct DevBsr {
+  int nr = 0, nc = 0, nnzb = 0;
+  DBuf<int> rowptr, col;
+  DBuf<double> val;
+  std::vector<int> h_rowptr, h_col;
+  int alloc(int nr_, int nc_, int nnzb_) {
+    nr = nr_; nc = nc_; nnzb = nnzb_;
+    AMG_TRY(rowptr.alloc(nr + 1));
+    AMG_TRY(col.alloc(nnzb));
+    AMG_TRY(val.alloc((size_t)nnzb * 9));
+    return AMG_OK;
+  }
+  int upload_pattern(cudaStream_t s) {
+    AMG_CU(cudaMemcpyAsync(rowptr.p, h_rowptr.data(), (nr + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (nnzb) AMG_CU(cudaMemcpyAsync(col.p, h_col.data(), nnzb * sizeof(int), cudaMemcpyHostToDevice, s));
+    return AMG_OK;
+  }
+  int download_pattern(cudaStream_t s) {
+    h_rowptr.resize(nr + 1);
+    h_col.resize(nnzb);
+    AMG_CU(cudaMemcpyAsync(h_rowptr.data(), rowptr.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (nnzb) AMG_CU(cudaMemcpyAsync(h_col.data(), col.p, nnzb * sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CU(cudaStreamSynchronize(s));
+    return AMG_OK;
+  }
+};
+
+// Solve-phase copy of a level matrix: the 9 entries of every block stored as
+// 9 contiguous arrays ("entry-major"), so that the lanes of a warp reading
+// consecutive blocks of a row issue coalesced loads.
+struct SolveMat {
+  int nr = 0, nc = 0, nnzb = 0;
+  const int *rowptr = nullptr, *col = nullptr;
+  DBuf<double> v64;
+  DBuf<float> v32;
+  DBuf<__nv_bfloat16> v16;
+  int lpr = 8;  // lanes per block row (set by the autotuner)
+};
+
+struct Level {
+  int n = 0;  // nodes
+  DevBsr A, G, GT, P, R;
+  SolveMat sA, sG, sGT, sP, sR;
+  double omega = 0.0, lmax = 0.0;
+  int npasses = 0;
+  int nc = 0;
+  std::vector<int> cf;  // host, 1 = coarse
+  DBuf<double> V;       // test space, 3n x n_tv column-major
+  // V-cycle work vectors (3n x kcap, node-major with the k columns interleaved)
+  DBuf<double> y64, s64, r64, t64, z64;
+  DBuf<float> y32, s32, r32, t32, z32;
+};
+
+struct Handle {
+  amg_params prm{};
+  cudaStream_t stream = nullptr;
+  int n = 0;  // fine nodes
+  int nlev = 0;
+  std::vector<std::unique_ptr<Level>> lev;
+  // last level: explicit inverse Cholesky factor (lower) and its transpose
+  int nL = 0;
+  DBuf<double> Linv, LinvT;
+  // PCG state (FP64), sized for kcap columns
+  int kcap = 0;
+  DBuf<double> x, r, z, p, q, zold, bvec, scal;
+  DBuf<int> flags;
+  DBuf<double> red;  // reduction partials
+  amg_stats stats{};
+  DBuf<double> V0keep;  // starting near-null space given to amg_setup
+  int ntv0 = 0;
+  // CUDA graph of one PCG iteration per (k) configuration
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_k = -1;
+  int graph_prec = -1;
+  bool own_stream = false;  // created because the caller passed the legacy stream
+  ~Handle();
+};
+
+// ---- set-up (setup.cu) ----
+int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *vals, int mem,
+                    int ntv0, const double *V0, int memV);
+void free_hierarchy(Handle *h);
+
+// ---- solve (solve.cu) ----
+int prepare_solve(Handle *h);
+int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres);
+int vcycle_apply(Handle *h, const double *y, double *z);
+
+// ---- deterministic set-up kernels (det.cu) ----
+namespace det {
+int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s);
+// dots[d] = canonical dot of (xs[d], ys[d]) for d < nd; pointer arrays on the device
+int multidot(int n, int nd, const double *const *xs, const double *const *ys, double *out,
+             double *partials, cudaStream_t s);
+int dot(int n, const double *x, const double *y, double *out, double *partials, cudaStream_t s);
+struct FsaiOut {
+  int *np;        // [n] pattern nodes per row
+  int *pat;       // [n*maxg]
+  double *val;    // [n*(maxg+1)*9]
+};
+int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int maxg, int maxdeg,
+         FsaiOut out, int *status, cudaStream_t s);
+int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t seed, int level,
+            double safety, double *d_out /*[lmax, omega_loop, omega]*/, cudaStream_t s);
+int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ritz, int t,
+          const double *V0, double *V, int *status, cudaStream_t s);
+int mgs(int n, int t, double *V, cudaStream_t s);
+int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char *strong,
+               cudaStream_t s);
+int dpls(const DevBsr &A, const unsigned char *strong, const int *cf, const int *cidx,
+         const int *fnodes, int nf, const int *cand_ptr, const int *cand, int t, const double *V,
+         int n_max, double kappa_p, int *out_cnt, int *out_col, double *out_val, int *status,
+         cudaStream_t s);
+int spgemm_numeric(const DevBsr &X, const DevBsr &Y, DevBsr &Z, cudaStream_t s);
+int gather_rows(const int *src_idx, int nrows_out, int n_in, int t, const double *Vin, double *Vout,
+                cudaStream_t s);
+int uniform_fill(double *v, int n, int col0, int ncols, uint64_t seed, cudaStream_t s);
+}  // namespace det
+
+// helpers (setup.cu)
+int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s);
+int compact_rows(int n, int maxper, const int *h_cnt, const int *d_col_fixed, const double *d_val_fixed,
+                 DevBsr &out, int nc, cudaStream_t s);
+
+}  // namespace amg

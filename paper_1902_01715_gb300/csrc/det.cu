@@ -1,0 +1,1202 @@
+// Set-up kernels whose floating-point results decide the hierarchy's
+// structure: FSAI rows, the Lanczos estimate of lambda_1(G A G^T), SRQCG,
+// affinity SoC and its filter, DPLS least-squares fits and the Galerkin
+// product.  This file is compiled with -fmad=false: every sum is taken in the
+// fixed order stated at each kernel, with separately rounded multiplies and
+// adds, so that the hierarchy (C/F split, patterns of G, P and A_c) is
+// reproducible bit for bit by any implementation that follows the same order.
+// Fixed orders used throughout:
+//  * sparse row sums: blocks in ascending column order, then the block's
+//    columns, starting from 0;
+//  * global dot products: chunks of 8192 entries; inside a chunk, lane l of a
+//    warp sums entries l, l+32, ... ascending, the 32 lane sums are combined
+//    by xor-exchange steps 16, 8, 4, 2, 1; chunk sums are added ascending.
+#include <cfloat>
+
+#include "amg_internal.h"
+
+namespace amg {
+namespace det {
+
+constexpr int CHUNK = 8192;
+constexpr int TMAXD = 16;  // largest test space handled by the DPLS kernel
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+  // SplitMix64 (Steele, Lea, Flood 2014): state seed + (counter+1)*gamma,
+  // then the published 30/27/31 xor-shift-multiply finaliser.
+  uint64_t z = seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t counter) {
+  const uint64_t m = splitmix64(seed, counter) >> 11;
+  return ((double)m * 0x1.0p-53) * 2.0 - 1.0;
+}
+
+static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- SpMV
+__global__ void k_spmv(int nr, const int *__restrict__ rowptr, const int *__restrict__ col,
+                       const double *__restrict__ val, const double *__restrict__ x,
+                       double *__restrict__ y) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3L * nr) return;
+  const int I = (int)(t / 3), r = (int)(t - 3L * I);
+  double s = 0.0;
+  for (int k = rowptr[I]; k < rowptr[I + 1]; ++k) {
+    const double *blk = val + (size_t)k * 9;
+    const long J = col[k];
+    for (int c = 0; c < 3; ++c) s = s + blk[r * 3 + c] * x[J * 3 + c];
+  }
+  y[t] = s;
+}
+
+int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
+  if (A.nr == 0) return AMG_OK;
+  k_spmv<<<nblk(3L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- dots
+constexpr int MAXD = 8;
+struct DotArgs {
+  const double *x[MAXD];
+  const double *y[MAXD];
+};
+
+__device__ __forceinline__ double chunk_sum(const double *__restrict__ x, const double *__restrict__ y,
+                                            int base, int end, int lane) {
+  double s = 0.0;
+  for (int i = base + lane; i < end; i += 32) s = s + x[i] * y[i];
+  for (int off = 16; off >= 1; off >>= 1) s = s + __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+__global__ void k_dot_partials(int n, int nd, DotArgs a, double *__restrict__ part, int nchunks) {
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long)nchunks * nd) return;
+  const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
+  const int base = c * CHUNK, end = min(base + CHUNK, n);
+  const double s = chunk_sum(a.x[d], a.y[d], base, end, lane);
+  if (lane == 0) part[(size_t)d * nchunks + c] = s;
+}
+
+__global__ void k_dot_final(int nd, int nchunks, const double *__restrict__ part, double *__restrict__ out) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nd) return;
+  double t = 0.0;
+  for (int c = 0; c < nchunks; ++c) t = t + part[(size_t)d * nchunks + c];
+  out[d] = t;
+}
+
+static int dots(int n, int nd, const DotArgs &a, double *out, double *part, cudaStream_t s) {
+  const int nchunks = (n + CHUNK - 1) / CHUNK;
+  if (nchunks > 0) {
+    k_dot_partials<<<nblk((long)nchunks * nd * 32, 256), 256, 0, s>>>(n, nd, a, part, nchunks);
+    AMG_LAUNCH_CHECK();
+  }
+  k_dot_final<<<1, 32, 0, s>>>(nd, nchunks, part, out);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+int dot(int n, const double *x, const double *y, double *out, double *part, cudaStream_t s) {
+  DotArgs a{};
+  a.x[0] = x;
+  a.y[0] = y;
+  return dots(n, 1, a, out, part, s);
+}
+
+// Gram sums of the Ritz step: H[i][j] = Z_i . SZ_j and M[i][j] = Z_i . Z_j for
+// i <= j, each in the fixed dot order, mirrored to j < i.
+__global__ void k_gram_partials(int n, int t, const double *__restrict__ Z, const double *__restrict__ SZ,
+                                double *__restrict__ part, int nchunks) {
+  const int npair = t * (t + 1) / 2;
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long)nchunks * npair * 2) return;
+  const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
+  const int which = d / npair;
+  int pr = d - which * npair, i = 0;
+  while (pr >= t - i) { pr -= t - i; ++i; }
+  const int j = i + pr;
+  const double *x = Z + (size_t)i * n;
+  const double *y = which == 0 ? SZ + (size_t)j * n : Z + (size_t)j * n;
+  const int base = c * CHUNK, end = min(base + CHUNK, n);
+  const double s = chunk_sum(x, y, base, end, lane);
+  if (lane == 0) part[(size_t)d * nchunks + c] = s;
+}
+
+__global__ void k_gram_final(int t, int nchunks, const double *__restrict__ part, double *__restrict__ H,
+                             double *__restrict__ M) {
+  const int npair = t * (t + 1) / 2;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= 2 * npair) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s = s + part[(size_t)d * nchunks + c];
+  const int which = d / npair;
+  int pr = d - which * npair, i = 0;
+  while (pr >= t - i) { pr -= t - i; ++i; }
+  const int j = i + pr;
+  double *O = which == 0 ? H : M;
+  O[i * t + j] = s;
+  O[j * t + i] = s;
+}
+
+// ---------------------------------------------------------------- vector ops
+// y = y - (*a) * x
+__global__ void k_axmy(long n, double *__restrict__ y, const double *__restrict__ a,
+                       const double *__restrict__ x, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = y[i] - (*a) * x[i];
+}
+
+// v = v / sqrt(*nn) when *nn > 0 (normalisation by a squared norm)
+__global__ void k_div_sqrt(long n, double *__restrict__ v, const double *__restrict__ nn) {
+  const double nr = sqrt(*nn);
+  if (!(nr > 0.0)) return;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = v[i] / nr;
+}
+
+// out = in / (*d)
+__global__ void k_div(long n, double *__restrict__ out, const double *__restrict__ in, const double *__restrict__ d) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i] / (*d);
+}
+
+__global__ void k_uniform(long n, int col0, int ncols, uint64_t seed, double *__restrict__ V, int ld) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ncols) return;
+  const int j = col0 + (int)(t / n);
+  const long i = t - (long)(j - col0) * n;
+  V[(size_t)j * ld + i] = uniform_pm1(seed, ((uint64_t)j << 40) | (uint64_t)i);
+}
+
+int uniform_fill(double *v, int n, int col0, int ncols, uint64_t seed, cudaStream_t s) {
+  if (ncols <= 0 || n <= 0) return AMG_OK;
+  k_uniform<<<nblk((long)n * ncols, 256), 256, 0, s>>>(n, col0, ncols, seed, v, n);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+__global__ void k_gather_rows(const int *__restrict__ src, int nout, int nin, int t, const double *__restrict__ Vin,
+                              double *__restrict__ Vout) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long)nout * t) return;
+  const int j = (int)(q / nout);
+  const long i = q - (long)j * nout;
+  Vout[(size_t)j * nout + i] = Vin[(size_t)j * nin + src[i]];
+}
+
+int gather_rows(const int *src_idx, int nout, int nin, int t, const double *Vin, double *Vout, cudaStream_t s) {
+  if (nout <= 0) return AMG_OK;
+  k_gather_rows<<<nblk((long)nout * t, 256), 256, 0, s>>>(src_idx, nout, nin, t, Vin, Vout);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+// Modified Gram-Schmidt on the columns of V (n x t), column order; each column
+// divided by its norm when that is positive.
+int mgs(int n, int t, double *V, cudaStream_t s) {
+  DBuf<double> sc, part;
+  AMG_TRY(sc.alloc(4));
+  AMG_TRY(part.alloc((size_t)((n + CHUNK - 1) / CHUNK) + 1));
+  for (int j = 0; j < t; ++j) {
+    double *vj = V + (size_t)j * n;
+    for (int i = 0; i < j; ++i) {
+      const double *vi = V + (size_t)i * n;
+      AMG_TRY(dot(n, vi, vj, sc.p, part.p, s));
+      k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p, vi, nullptr);
+      AMG_LAUNCH_CHECK();
+    }
+    AMG_TRY(dot(n, vj, vj, sc.p, part.p, s));
+    k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p);
+    AMG_LAUNCH_CHECK();
+  }
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- FSAI
+// Warp-cooperative aFSAI rows (one warp per node row).  The arithmetic of each
+// scalar follows the plain sequential definition:
+//  * Cholesky of A[Q,Q] entry (i,j): A_ij - sum_{k<j} L_ik L_jk (k ascending),
+//    then sqrt / division (the right-looking update subtracts the same
+//    products in the same order);
+//  * forward substitution sums k ascending, backward substitution k
+//    descending (the column-oriented forms subtract in the same orders);
+//  * psi = a_ii + sum_a A[i,Q_a] gh_a, a ascending;
+//  * candidate gradient (A gt)_j over the row pattern in ascending dof order;
+//    node score = sum over rows c, dofs d of gradient^2, c outer.
+struct FsaiK {
+  int n;
+  const int *Arp, *Acol;
+  const double *Aval;
+  const int *Gsrp, *Gscol;
+  int ksteps, rho, maxg;
+  double eps;
+  int *out_np, *out_pat;
+  double *out_val;
+  int *status;
+  double *dscr;
+  int *iscr;
+  long dper, iper;
+  int candcap, mmax;
+};
+
+__device__ __forceinline__ const double *find_blk(const int *rp, const int *col, const double *val, int i, int j) {
+  int lo = rp[i], hi = rp[i + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1, c = col[mid];
+    if (c == j) return val + (size_t)mid * 9;
+    if (c < j) lo = mid + 1; else hi = mid - 1;
+  }
+  return nullptr;
+}
+
+__device__ __forceinline__ double a_entry(const FsaiK &K, int r, int c) {
+  const double *b = find_blk(K.Arp, K.Acol, K.Aval, r / 3, c / 3);
+  return b ? b[(r % 3) * 3 + (c % 3)] : 0.0;
+}
+
+// Solve the 3 dof rows of node I on pattern pat[0..np-1]; returns 0 or an error.
+__device__ int fsai_solve_rows(const FsaiK &K, int I, const int *pat, int np, double *M, double *gh,
+                               double *rhs, double *prod, int *Q, double *psi, int lane) {
+  for (int c = 0; c < 3; ++c) {
+    const int i = 3 * I + c;
+    const int m = 3 * np + c;
+    for (int a = lane; a < m; a += 32) Q[a] = (a < 3 * np) ? 3 * pat[a / 3] + (a % 3) : 3 * I + (a - 3 * np);
+    __syncwarp();
+    for (int idx = lane; idx < m * m; idx += 32) {
+      const int a = idx / m, a2 = idx - a * m;
+      M[idx] = a_entry(K, Q[a], Q[a2]);
+    }
+    for (int a = lane; a < m; a += 32) rhs[a] = -a_entry(K, Q[a], i);
+    __syncwarp();
+    int bad = 0;
+    for (int j = 0; j < m; ++j) {
+      const double sjj = M[j * m + j];
+      if (!(sjj > 0.0)) { bad = 1; break; }
+      const double d = sqrt(sjj);
+      __syncwarp();
+      for (int r = j + 1 + lane; r < m; r += 32) M[r * m + j] = M[r * m + j] / d;
+      if (lane == 0) M[j * m + j] = d;
+      __syncwarp();
+      const int w = m - j - 1;  // trailing size
+      for (int idx = lane; idx < w * w; idx += 32) {
+        const int r = j + 1 + idx / w, k = j + 1 + idx % w;
+        if (k <= r) M[r * m + k] = M[r * m + k] - M[r * m + j] * M[k * m + j];
+      }
+      __syncwarp();
+    }
+    if (bad) return AMG_ERR_NOT_SPD;
+    // forward: rhs <- L^{-1} rhs
+    for (int k = 0; k < m; ++k) {
+      const double yk = rhs[k] / M[k * m + k];
+      __syncwarp();
+      if (lane == 0) rhs[k] = yk;
+      for (int r = k + 1 + lane; r < m; r += 32) rhs[r] = rhs[r] - M[r * m + k] * yk;
+      __syncwarp();
+    }
+    // backward: gh <- L^{-T} rhs
+    double *x = gh + c * K.mmax;
+    for (int k = m - 1; k >= 0; --k) {
+      const double xk = rhs[k] / M[k * m + k];
+      __syncwarp();
+      if (lane == 0) x[k] = xk;
+      for (int r = lane; r < k; r += 32) rhs[r] = rhs[r] - M[k * m + r] * xk;
+      __syncwarp();
+    }
+    for (int a = lane; a < m; a += 32) prod[a] = a_entry(K, i, Q[a]) * x[a];
+    __syncwarp();
+    double s = 0.0;
+    if (lane == 0) {
+      s = a_entry(K, i, i);
+      for (int a = 0; a < m; ++a) s = s + prod[a];
+    }
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (!(s > 0.0)) return AMG_ERR_NOT_SPD;
+    psi[c] = s;
+    __syncwarp();
+  }
+  return AMG_OK;
+}
+
+__device__ __forceinline__ int in_sorted(const int *a, int n, int v) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] == v) return 1;
+    if (a[mid] < v) lo = mid + 1; else hi = mid - 1;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ int in_row(const int *rp, const int *col, int K, int v) {
+  int lo = rp[K], hi = rp[K + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    if (col[mid] == v) return 1;
+    if (col[mid] < v) lo = mid + 1; else hi = mid - 1;
+  }
+  return 0;
+}
+
+__global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
+  const int lane = threadIdx.x & 31;
+  const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long nw = ((long)gridDim.x * blockDim.x) >> 5;
+  double *M = K.dscr + gw * K.dper;
+  double *gh = M + (size_t)K.mmax * K.mmax;
+  double *rhs = gh + 3 * K.mmax;
+  double *prod = rhs + K.mmax;
+  double *score = prod + K.mmax;
+  int *Q = K.iscr + gw * K.iper;
+  int *pat = Q + K.mmax;
+  int *cand = pat + K.maxg + 1;
+  for (long Il = gw; Il < K.n; Il += nw) {
+    const int I = (int)Il;
+    int np = 0;
+    if (lane == 0 && K.Gsrp) {
+      for (int k = K.Gsrp[I]; k < K.Gsrp[I + 1]; ++k)
+        if (K.Gscol[k] != I && np < K.maxg) pat[np++] = K.Gscol[k];
+    }
+    np = __shfl_sync(0xffffffffu, np, 0);
+    __syncwarp();
+    double psi[3], psi_old[3];
+    int rc = fsai_solve_rows(K, I, pat, np, M, gh, rhs, prod, Q, psi, lane);
+    for (int step = 0; step < K.ksteps && rc == 0; ++step) {
+      if (np >= K.maxg) break;
+      // candidates: A-neighbours J < I of the pattern nodes and of I, outside
+      // the pattern, each listed once (first run that contains it)
+      int nc = 0;
+      for (int run = 0; run <= np; ++run) {
+        const int Kn = run < np ? pat[run] : I;
+        const int b0 = K.Arp[Kn], len = K.Arp[Kn + 1] - b0;
+        for (int base = 0; base < len; base += 32) {
+          int keep = 0, J = -1;
+          if (base + lane < len) {
+            J = K.Acol[b0 + base + lane];
+            keep = (J < I) && !in_sorted(pat, np, J);
+            for (int r2 = 0; keep && r2 < run; ++r2)
+              if (in_row(K.Arp, K.Acol, pat[r2], J)) keep = 0;
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, keep);
+          if (keep) cand[nc + __popc(bal & ((1u << lane) - 1u))] = J;
+          nc += __popc(bal);
+        }
+      }
+      __syncwarp();
+      for (int t = lane; t < nc; t += 32) {
+        const int J = cand[t];
+        double s = 0.0;
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) {
+            double g = 0.0;
+            for (int j = 0; j < np; ++j) {
+              const double *blk = find_blk(K.Arp, K.Acol, K.Aval, J, pat[j]);
+              if (blk)
+                for (int e = 0; e < 3; ++e) g = g + blk[d * 3 + e] * gh[c * K.mmax + 3 * j + e];
+            }
+            const double *blk = find_blk(K.Arp, K.Acol, K.Aval, J, I);
+            if (blk) {
+              for (int e = 0; e < c; ++e) g = g + blk[d * 3 + e] * gh[c * K.mmax + 3 * np + e];
+              g = g + blk[d * 3 + c] * 1.0;
+            }
+            s = s + g * g;
+          }
+        score[t] = s;
+      }
+      __syncwarp();
+      const int want = K.rho < K.maxg - np ? K.rho : K.maxg - np;
+      int got = 0;
+      for (int p = 0; p < want; ++p) {
+        double bs = -1.0;
+        int bj = 0x7fffffff, bt = -1;
+        for (int t = lane; t < nc; t += 32) {
+          const double sc = score[t];
+          if (sc > 0.0 && (sc > bs || (sc == bs && cand[t] < bj))) { bs = sc; bj = cand[t]; bt = t; }
+        }
+        for (int off = 16; off >= 1; off >>= 1) {
+          const double os = __shfl_xor_sync(0xffffffffu, bs, off);
+          const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
+          const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
+          if (os > bs || (os == bs && oj < bj)) { bs = os; bj = oj; bt = ot; }
+        }
+        if (bt < 0) break;
+        if (lane == 0) {
+          pat[np + got] = bj;
+          score[bt] = -1.0;
+        }
+        ++got;
+        __syncwarp();
+      }
+      if (got == 0) break;
+      if (lane == 0) {
+        const int tot = np + got;
+        for (int u = 1; u < tot; ++u) {
+          const int v = pat[u];
+          int w = u - 1;
+          while (w >= 0 && pat[w] > v) { pat[w + 1] = pat[w]; --w; }
+          pat[w + 1] = v;
+        }
+      }
+      np += got;
+      __syncwarp();
+      for (int c = 0; c < 3; ++c) psi_old[c] = psi[c];
+      rc = fsai_solve_rows(K, I, pat, np, M, gh, rhs, prod, Q, psi, lane);
+      if (rc) break;
+      int stalled = 1;
+      for (int c = 0; c < 3; ++c)
+        if (psi_old[c] - psi[c] > K.eps * psi_old[c]) stalled = 0;
+      if (stalled) break;
+    }
+    if (rc) {
+      if (lane == 0) atomicMin(K.status, rc);
+      continue;
+    }
+    if (lane == 0) K.out_np[I] = np;
+    for (int j = lane; j < np; j += 32) K.out_pat[(size_t)I * K.maxg + j] = pat[j];
+    double *ov = K.out_val + (size_t)I * (K.maxg + 1) * 9;
+    for (int idx = lane; idx < (np + 1) * 9; idx += 32) {
+      const int j = idx / 9, c = (idx % 9) / 3, d = idx % 3;
+      const double sq = sqrt(psi[c]);
+      double g;
+      if (j < np) g = gh[c * K.mmax + 3 * j + d];
+      else g = (d < c) ? gh[c * K.mmax + 3 * np + d] : (d == c ? 1.0 : 0.0);
+      ov[idx] = (j < np || d <= c) ? g / sq : 0.0;
+    }
+    __syncwarp();
+  }
+}
+
+int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int maxg, int maxdeg,
+         FsaiOut out, int *status, cudaStream_t s) {
+  FsaiK K{};
+  K.n = A.nr;
+  K.Arp = A.rowptr.p;
+  K.Acol = A.col.p;
+  K.Aval = A.val.p;
+  K.Gsrp = Gs ? Gs->rowptr.p : nullptr;
+  K.Gscol = Gs ? Gs->col.p : nullptr;
+  K.ksteps = ksteps;
+  K.rho = rho;
+  K.maxg = maxg;
+  K.eps = eps;
+  K.out_np = out.np;
+  K.out_pat = out.pat;
+  K.out_val = out.val;
+  K.status = status;
+  K.mmax = 3 * maxg + 3;
+  K.candcap = (maxg + 1) * maxdeg;
+  K.dper = (long)K.mmax * K.mmax + 5L * K.mmax + K.candcap;
+  K.iper = K.mmax + (maxg + 1) + K.candcap;
+  int dev = 0, nsm = 0;
+  AMG_CU(cudaGetDevice(&dev));
+  AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 128;
+  long nblocks = (long)nsm * 8;
+  const long need = ((long)A.nr + 3) / 4;
+  if (nblocks > need) nblocks = need > 0 ? need : 1;
+  const long nw = nblocks * (threads / 32);
+  DBuf<double> ds;
+  DBuf<int> is;
+  AMG_TRY(ds.alloc((size_t)nw * K.dper));
+  AMG_TRY(is.alloc((size_t)nw * K.iper));
+  K.dscr = ds.p;
+  K.iscr = is.p;
+  k_fsai<<<(int)nblocks, threads, 0, s>>>(K);
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- Lanczos
+__global__ void k_lanczos_beta(int j, int m, double *__restrict__ sc) {
+  // sc layout: [0..63] alpha, [64..127] beta, [128] mm (as double), [129] tmp
+  const double b = sqrt(sc[129]);
+  sc[64 + j] = b;
+  if (sc[128] < 0.0 && j < m - 1 && !(b > 1e-12 * fabs(sc[j]))) sc[128] = (double)(j + 1);
+}
+
+// largest eigenvalue of the tridiagonal (alpha, beta) by bisection on Sturm
+// counts; out = [lambda, 2/lambda, min(1, safety * 2/lambda)]
+__global__ void k_lanczos_bisect(int m, const double *__restrict__ sc, double safety, double *__restrict__ out) {
+  const double *al = sc, *be = sc + 64;
+  const int mm = sc[128] < 0.0 ? m : (int)sc[128];
+  double lo = al[0], hi = al[0];
+  for (int i = 0; i < mm; ++i) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < mm - 1 ? fabs(be[i]) : 0.0);
+    if (al[i] - r < lo) lo = al[i] - r;
+    if (al[i] + r > hi) hi = al[i] + r;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < mm; ++i) {
+      d = (i == 0) ? (al[0] - mid) : (al[i] - mid) - (be[i - 1] * be[i - 1]) / d;
+      if (d == 0.0) d = 1e-300;
+      if (d < 0.0) ++cnt;
+    }
+    if (cnt >= mm) hi = mid; else lo = mid;
+  }
+  const double w = 2.0 / hi;
+  double om = safety * w;
+  if (om > 1.0) om = 1.0;
+  out[0] = hi;
+  out[1] = w;
+  out[2] = om;
+}
+
+__global__ void k_set_neg(double *p) { *p = -1.0; }
+
+__global__ void k_lanczos_start(long n, uint64_t seed, uint64_t base, double *__restrict__ v) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = uniform_pm1(seed, base | (uint64_t)i);
+}
+
+int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t seed, int level,
+            double safety, double *d_out, cudaStream_t s) {
+  const int n = 3 * A.nr;
+  if (m > n) m = n;
+  if (m > 64) m = 64;
+  DBuf<double> Vs, w, t1, t2, sc, part;
+  AMG_TRY(Vs.alloc((size_t)m * n));
+  AMG_TRY(w.alloc(n));
+  AMG_TRY(t1.alloc(n));
+  AMG_TRY(t2.alloc(n));
+  AMG_TRY(sc.alloc(160));
+  AMG_TRY(part.alloc((size_t)(n + CHUNK - 1) / CHUNK + 1));
+  AMG_TRY(sc.zero(s));
+  k_set_neg<<<1, 1, 0, s>>>(sc.p + 128);
+  // start vector: counters (1<<62) | level<<40 | i of the generator
+  k_lanczos_start<<<nblk(n, 256), 256, 0, s>>>(n, seed, (1ull << 62) | ((uint64_t)level << 40), Vs.p);
+  AMG_LAUNCH_CHECK();
+  AMG_TRY(dot(n, Vs.p, Vs.p, sc.p + 129, part.p, s));
+  k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, Vs.p, sc.p + 129);
+  for (int j = 0; j < m; ++j) {
+    double *v = Vs.p + (size_t)j * n;
+    AMG_TRY(spmv(GT, v, t1.p, s));
+    AMG_TRY(spmv(A, t1.p, t2.p, s));
+    AMG_TRY(spmv(G, t2.p, w.p, s));
+    AMG_TRY(dot(n, w.p, v, sc.p + j, part.p, s));
+    k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + j, v, nullptr);
+    if (j > 0) k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 64 + j - 1, v - n, nullptr);
+    for (int k = 0; k <= j; ++k) {
+      const double *vk = Vs.p + (size_t)k * n;
+      AMG_TRY(dot(n, w.p, vk, sc.p + 130, part.p, s));
+      k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 130, vk, nullptr);
+    }
+    AMG_TRY(dot(n, w.p, w.p, sc.p + 129, part.p, s));
+    k_lanczos_beta<<<1, 1, 0, s>>>(j, m, sc.p);
+    if (j < m - 1) k_div<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 64 + j);
+    AMG_LAUNCH_CHECK();
+  }
+  k_lanczos_bisect<<<1, 1, 0, s>>>(m, sc.p, safety, d_out);
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+
+// ---------------------------------------------------------------- SRQCG
+// Scalar slots of the SRQCG state (device doubles).
+enum { S_A = 0, S_B, S_C, S_D, S_E, S_ALPHA, S_FN, S_ZSZ, S_Q, S_GSP, S_BETA, S_TMP, S_F0 = 16 };
+
+// Step length along p (Algorithm 4): root of
+// (bc - ad) alpha^2 + (bf - de) alpha + (af - ce) = 0 giving the smaller
+// Rayleigh quotient; same expression order as the reference definition.
+__device__ double line_min(double a, double b, double c, double d, double e, double f) {
+  const double p1 = d * e - b * f;
+  const double q1 = b * c - a * d;
+  const double r1 = a * f - c * e;
+  const double delta = p1 * p1 - (4.0 * q1) * r1;
+  if (q1 != 0.0 && delta >= 0.0) {
+    const double sq = sqrt(delta);
+    const double a1 = (p1 + sq) / (2.0 * q1), a2 = (p1 - sq) / (2.0 * q1);
+    const double n1 = (e + (2.0 * a1) * a) + (a1 * a1) * b, d1 = (f + (2.0 * a1) * c) + (a1 * a1) * d;
+    const double n2 = (e + (2.0 * a2) * a) + (a2 * a2) * b, d2 = (f + (2.0 * a2) * c) + (a2 * a2) * d;
+    return (n1 / d1 <= n2 / d2) ? a1 : a2;
+  }
+  if (q1 == 0.0 && p1 != 0.0) return r1 / p1;
+  return 0.0;
+}
+
+__global__ void k_srq_z0(long n, double *__restrict__ z, const double *__restrict__ v, const double *__restrict__ sv) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = v[i] - sv[i];
+}
+
+__global__ void k_srq_p0(long n, double *__restrict__ p, const double *__restrict__ z, const double *__restrict__ sz,
+                         const double *__restrict__ q) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 2.0 * (sz[i] - (*q) * z[i]);
+}
+
+__global__ void k_srq_alpha(double *__restrict__ sc, int i, int *__restrict__ skip) {
+  const double b = sc[S_B];
+  if (!(b > 0.0)) {
+    *skip = 1;
+    return;
+  }
+  *skip = 0;
+  sc[S_ALPHA] = line_min(sc[S_A], b, sc[S_C], sc[S_D], sc[S_E], sc[S_F0 + i]);
+}
+
+__global__ void k_srq_zupd(long n, double *__restrict__ z, const double *__restrict__ p, const double *__restrict__ sc,
+                           const int *__restrict__ skip) {
+  if (*skip) return;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = z[i] + sc[S_ALPHA] * p[i];
+}
+
+__global__ void k_srq_q(double *__restrict__ sc) { sc[S_Q] = sc[S_ZSZ] / sc[S_FN]; }
+
+__global__ void k_srq_grad(long n, double *__restrict__ g, const double *__restrict__ sz, const double *__restrict__ z,
+                           const double *__restrict__ sc, const int *__restrict__ skip) {
+  if (*skip) return;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) g[i] = (2.0 * (sz[i] - sc[S_Q] * z[i])) / sc[S_FN];
+}
+
+__global__ void k_srq_beta(double *__restrict__ sc) { sc[S_BETA] = -(sc[S_GSP] / sc[S_B]); }
+
+__global__ void k_srq_pupd(long n, double *__restrict__ p, const double *__restrict__ g, double *__restrict__ sc, int i0,
+                           const int *__restrict__ skip) {
+  if (*skip) return;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = g[i] + sc[S_BETA] * p[i];
+  if (i == 0) sc[S_F0 + i0] = sc[S_FN];
+}
+
+__global__ void k_fill(double *__restrict__ p, int n, double v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// Z <- Z U: row k of the new block is sum_i Z[i][k] U[i][j], i ascending.
+__global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__restrict__ U) {
+  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double row[TMAXD];
+  for (int j = 0; j < t; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < t; ++i) s = s + Z[(size_t)i * n + k] * U[i * t + j];
+    row[j] = s;
+  }
+  for (int j = 0; j < t; ++j) Z[(size_t)j * n + k] = row[j];
+}
+
+// Generalised eigenproblem H U = M U diag(lam) of the Ritz step, one thread:
+// M = L L^T, C = L^{-1} (L^{-1} H)^T symmetrised, cyclic Jacobi, ascending
+// sort, U = L^{-T} W, columns signed so the largest-magnitude entry is
+// positive.  Scratch w holds 4 t*t + t doubles.
+__global__ void k_gen_eig(int t, const double *__restrict__ H, const double *__restrict__ M, double *__restrict__ U,
+                          double *__restrict__ lam, double *__restrict__ w, int *__restrict__ status) {
+  double *L = w, *W1 = w + t * t, *C = w + 2 * t * t, *Wv = w + 3 * t * t, *tmp = w + 4 * t * t;
+  for (int i = 0; i < t * t; ++i) L[i] = 0.0;
+  for (int j = 0; j < t; ++j) {
+    double s = M[j * t + j];
+    for (int k = 0; k < j; ++k) s = s - L[j * t + k] * L[j * t + k];
+    if (!(s > 0.0)) {
+      atomicMin(status, AMG_ERR_NOT_SPD);
+      return;
+    }
+    const double d = sqrt(s);
+    L[j * t + j] = d;
+    for (int i = j + 1; i < t; ++i) {
+      double u = M[i * t + j];
+      for (int k = 0; k < j; ++k) u = u - L[i * t + k] * L[j * t + k];
+      L[i * t + j] = u / d;
+    }
+  }
+  for (int j = 0; j < t; ++j)
+    for (int i = 0; i < t; ++i) {
+      double s = H[i * t + j];
+      for (int k = 0; k < i; ++k) s = s - L[i * t + k] * W1[k * t + j];
+      W1[i * t + j] = s / L[i * t + i];
+    }
+  for (int j = 0; j < t; ++j)
+    for (int i = 0; i < t; ++i) {
+      double s = W1[j * t + i];
+      for (int k = 0; k < i; ++k) s = s - L[i * t + k] * C[k * t + j];
+      C[i * t + j] = s / L[i * t + i];
+    }
+  for (int i = 0; i < t; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double v = (C[i * t + j] + C[j * t + i]) * 0.5;
+      C[i * t + j] = v;
+      C[j * t + i] = v;
+    }
+  for (int i = 0; i < t; ++i)
+    for (int j = 0; j < t; ++j) Wv[i * t + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, dg = 0.0;
+    for (int p = 0; p < t; ++p) {
+      dg = dg + C[p * t + p] * C[p * t + p];
+      for (int q = p + 1; q < t; ++q) off = off + C[p * t + q] * C[p * t + q];
+    }
+    if (!(off > 1e-32 * dg)) break;
+    for (int p = 0; p < t - 1; ++p)
+      for (int q = p + 1; q < t; ++q) {
+        const double apq = C[p * t + q];
+        if (apq == 0.0) continue;
+        const double th = (C[q * t + q] - C[p * t + p]) / (2.0 * apq);
+        const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(tt * tt + 1.0);
+        const double s = tt * c;
+        for (int k = 0; k < t; ++k) {
+          const double xp = C[k * t + p], xq = C[k * t + q];
+          C[k * t + p] = c * xp - s * xq;
+          C[k * t + q] = s * xp + c * xq;
+        }
+        for (int k = 0; k < t; ++k) {
+          const double xp = C[p * t + k], xq = C[q * t + k];
+          C[p * t + k] = c * xp - s * xq;
+          C[q * t + k] = s * xp + c * xq;
+        }
+        for (int k = 0; k < t; ++k) {
+          const double xp = Wv[k * t + p], xq = Wv[k * t + q];
+          Wv[k * t + p] = c * xp - s * xq;
+          Wv[k * t + q] = s * xp + c * xq;
+        }
+        C[p * t + q] = 0.0;
+        C[q * t + p] = 0.0;
+      }
+  }
+  int order[TMAXD];
+  for (int i = 0; i < t; ++i) order[i] = i;
+  for (int i = 0; i < t; ++i) {
+    int best = i;
+    for (int j = i + 1; j < t; ++j)
+      if (C[order[j] * t + order[j]] < C[order[best] * t + order[best]]) best = j;
+    const int ti = order[best];
+    for (int j = best; j > i; --j) order[j] = order[j - 1];
+    order[i] = ti;
+  }
+  for (int jj = 0; jj < t; ++jj) {
+    const int j = order[jj];
+    lam[jj] = C[j * t + j];
+    for (int i = t - 1; i >= 0; --i) {
+      double s = Wv[i * t + j];
+      for (int k = t - 1; k > i; --k) s = s - L[k * t + i] * tmp[k];
+      tmp[i] = s / L[i * t + i];
+    }
+    int im = 0;
+    for (int i = 1; i < t; ++i)
+      if (fabs(tmp[i]) > fabs(tmp[im])) im = i;
+    const double sg = tmp[im] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < t; ++i) U[i * t + jj] = sg * tmp[i];
+  }
+}
+
+static int apply_s(const DevBsr &A, const DevBsr &G, const DevBsr &GT, const double *x, double *y, double *t1,
+                   double *t2, cudaStream_t s) {
+  AMG_TRY(spmv(GT, x, t1, s));
+  AMG_TRY(spmv(A, t1, t2, s));
+  AMG_TRY(spmv(G, t2, y, s));
+  return AMG_OK;
+}
+
+int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ritz, int t, const double *V0, double *V,
+          int *status, cudaStream_t s) {
+  const int n = 3 * A.nr;
+  if (t > TMAXD) {
+    set_error("n_tv = %d exceeds the supported maximum %d", t, TMAXD);
+    return AMG_ERR_ARG;
+  }
+  const size_t nt = (size_t)n * t;
+  DBuf<double> Z, P, SZall, SZ, SP, Gv, t1, t2, sc, part, H, Mg, U, lam, wk;
+  DBuf<int> skip;
+  AMG_TRY(Z.alloc(nt));
+  AMG_TRY(P.alloc(nt));
+  AMG_TRY(SZall.alloc(nt));
+  AMG_TRY(SZ.alloc(n));
+  AMG_TRY(SP.alloc(n));
+  AMG_TRY(Gv.alloc(n));
+  AMG_TRY(t1.alloc(n));
+  AMG_TRY(t2.alloc(n));
+  AMG_TRY(sc.alloc(S_F0 + 64));
+  const int nchunks = (n + CHUNK - 1) / CHUNK;
+  AMG_TRY(part.alloc((size_t)(nchunks + 1) * (t * (t + 1) + 8)));
+  AMG_TRY(H.alloc(t * t));
+  AMG_TRY(Mg.alloc(t * t));
+  AMG_TRY(U.alloc(t * t));
+  AMG_TRY(lam.alloc(t));
+  AMG_TRY(wk.alloc(4 * t * t + t));
+  AMG_TRY(skip.alloc(1));
+  AMG_TRY(sc.zero(s));
+  AMG_TRY(skip.zero(s));
+  const int nb = nblk(n, 256);
+  // Z0 = (I - S) V0, orthonormalised
+  for (int i = 0; i < t; ++i) {
+    const double *v = V0 + (size_t)i * n;
+    AMG_TRY(apply_s(A, G, GT, v, SZ.p, t1.p, t2.p, s));
+    k_srq_z0<<<nb, 256, 0, s>>>(n, Z.p + (size_t)i * n, v, SZ.p);
+    AMG_LAUNCH_CHECK();
+  }
+  AMG_TRY(mgs(n, t, Z.p, s));
+  for (int i = 0; i < t; ++i) {
+    double *z = Z.p + (size_t)i * n, *p = P.p + (size_t)i * n;
+    AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
+    AMG_TRY(dot(n, z, SZ.p, sc.p + S_TMP, part.p, s));
+    k_srq_p0<<<nb, 256, 0, s>>>(n, p, z, SZ.p, sc.p + S_TMP);
+    AMG_LAUNCH_CHECK();
+  }
+  k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
+  for (int it = 1; it <= kmax; ++it) {
+    if (k_ritz > 0 && it % k_ritz == 0) {
+      for (int j = 0; j < t; ++j)
+        AMG_TRY(apply_s(A, G, GT, Z.p + (size_t)j * n, SZall.p + (size_t)j * n, t1.p, t2.p, s));
+      const int npair = t * (t + 1) / 2;
+      if (nchunks > 0) {
+        k_gram_partials<<<nblk((long)nchunks * npair * 2 * 32, 256), 256, 0, s>>>(n, t, Z.p, SZall.p, part.p, nchunks);
+        AMG_LAUNCH_CHECK();
+      }
+      k_gram_final<<<nblk(2 * npair, 64), 64, 0, s>>>(t, nchunks, part.p, H.p, Mg.p);
+      k_gen_eig<<<1, 1, 0, s>>>(t, H.p, Mg.p, U.p, lam.p, wk.p, status);
+      k_rotate<<<nb, 256, 0, s>>>(n, t, Z.p, U.p);
+      k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
+      AMG_LAUNCH_CHECK();
+    }
+    for (int i = 0; i < t; ++i) {
+      double *z = Z.p + (size_t)i * n, *p = P.p + (size_t)i * n;
+      AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
+      AMG_TRY(apply_s(A, G, GT, p, SP.p, t1.p, t2.p, s));
+      DotArgs a5{};
+      a5.x[0] = p; a5.y[0] = SZ.p;
+      a5.x[1] = p; a5.y[1] = SP.p;
+      a5.x[2] = p; a5.y[2] = z;
+      a5.x[3] = p; a5.y[3] = p;
+      a5.x[4] = z; a5.y[4] = SZ.p;
+      AMG_TRY(dots(n, 5, a5, sc.p + S_A, part.p, s));
+      k_srq_alpha<<<1, 1, 0, s>>>(sc.p, i, skip.p);
+      k_srq_zupd<<<nb, 256, 0, s>>>(n, z, p, sc.p, skip.p);
+      AMG_LAUNCH_CHECK();
+      AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
+      DotArgs a2{};
+      a2.x[0] = z; a2.y[0] = z;
+      a2.x[1] = z; a2.y[1] = SZ.p;
+      AMG_TRY(dots(n, 2, a2, sc.p + S_FN, part.p, s));
+      k_srq_q<<<1, 1, 0, s>>>(sc.p);
+      k_srq_grad<<<nb, 256, 0, s>>>(n, Gv.p, SZ.p, z, sc.p, skip.p);
+      AMG_LAUNCH_CHECK();
+      AMG_TRY(dot(n, Gv.p, SP.p, sc.p + S_GSP, part.p, s));
+      k_srq_beta<<<1, 1, 0, s>>>(sc.p);
+      k_srq_pupd<<<nb, 256, 0, s>>>(n, p, Gv.p, sc.p, i, skip.p);
+      AMG_LAUNCH_CHECK();
+    }
+  }
+  for (int i = 0; i < t; ++i) AMG_TRY(spmv(GT, Z.p + (size_t)i * n, V + (size_t)i * n, s));
+  AMG_TRY(mgs(n, t, V, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- SoC + filter
+// Node gram of the test space: M[r][c] = sum_k V[k][3I+r] V[k][3J+c], k ascending.
+__device__ __forceinline__ void node_gram(long n, int t, const double *__restrict__ V, int I, int J, double *M) {
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < t; ++k) s = s + V[(size_t)k * n + 3L * I + r] * V[(size_t)k * n + 3L * J + c];
+      M[r * 3 + c] = s;
+    }
+}
+
+__device__ __forceinline__ double fro2(const double *M) {
+  double s = 0.0;
+  for (int i = 0; i < 9; ++i) s = s + M[i] * M[i];
+  return s;
+}
+
+__global__ void k_soc_nrm(int nn, int t, const double *__restrict__ V, double *__restrict__ nrm) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  double M[9];
+  node_gram(3L * nn, t, V, I, I, M);
+  nrm[I] = sqrt(fro2(M));
+}
+
+// SoC of every block of row I (smaller node first), then the theta largest
+// positive ones are kept (ties to the smaller column).
+__global__ void k_soc_filter(int nn, int t, const int *__restrict__ rp, const int *__restrict__ col,
+                             const double *__restrict__ V, const double *__restrict__ nrm, int theta,
+                             double *__restrict__ soc, unsigned char *__restrict__ kept) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  double M[9];
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int J = col[k];
+    kept[k] = 0;
+    if (J == I) {
+      soc[k] = 0.0;
+      continue;
+    }
+    const int lo = I < J ? I : J, hi = I < J ? J : I;
+    node_gram(3L * nn, t, V, lo, hi, M);
+    const double num = fro2(M), den = nrm[lo] * nrm[hi];
+    soc[k] = den > 0.0 ? num / den : 0.0;
+  }
+  for (int p = 0; p < theta; ++p) {
+    int best = -1;
+    for (int k = rp[I]; k < rp[I + 1]; ++k)
+      if (!kept[k] && col[k] != I && soc[k] > 0.0 && (best < 0 || soc[k] > soc[best])) best = k;
+    if (best < 0) break;
+    kept[best] = 1;
+  }
+}
+
+__global__ void k_strong(int nn, const int *__restrict__ rp, const int *__restrict__ col,
+                         const unsigned char *__restrict__ kept, unsigned char *__restrict__ strong) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int J = col[k];
+    int lo = rp[J], hi = rp[J + 1] - 1, kt = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      if (col[mid] == I) { kt = mid; break; }
+      if (col[mid] < I) lo = mid + 1; else hi = mid - 1;
+    }
+    strong[k] = (unsigned char)(kept[k] || (kt >= 0 && kept[kt]));
+  }
+}
+
+int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char *strong, cudaStream_t s) {
+  DBuf<double> nrm, soc;
+  DBuf<unsigned char> kept;
+  AMG_TRY(nrm.alloc(A.nr));
+  AMG_TRY(soc.alloc(A.nnzb));
+  AMG_TRY(kept.alloc(A.nnzb));
+  const int nb = nblk(A.nr, 128);
+  k_soc_nrm<<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
+  k_soc_filter<<<nb, 128, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, theta, soc.p, kept.p);
+  k_strong<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, kept.p, strong);
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- DPLS
+// One thread per fine node (Algorithm 5 in nodal-block form).  Householder
+// step on column x (rows p..t-1): sigma = sqrt(sum x^2), alpha = -sigma if
+// x_p >= 0 else sigma, v = x with v_p = x_p - alpha, vv = sum v^2; a column y
+// becomes y - ((2 v.y)/vv) v.  Affinity of residual X and candidate Y over
+// the trailing rows: ||X^T Y||_F^2 / (||X^T X||_F ||Y^T Y||_F).
+__device__ __forceinline__ void reflect(int t, int p, const double *v, double vv, double *y, int stride) {
+  double s = 0.0;
+  for (int k = p; k < t; ++k) s = s + v[k] * y[k * stride];
+  const double f = (2.0 * s) / vv;
+  for (int k = p; k < t; ++k) y[k * stride] = y[k * stride] - f * v[k];
+}
+
+__device__ __forceinline__ double affinity(int t, int p, const double *X, const double *Y) {
+  double xy = 0.0, xx = 0.0, yy = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      double sxy = 0.0, sxx = 0.0, syy = 0.0;
+      for (int k = p; k < t; ++k) {
+        sxy = sxy + X[k * 3 + a] * Y[k * 3 + c];
+        sxx = sxx + X[k * 3 + a] * X[k * 3 + c];
+        syy = syy + Y[k * 3 + a] * Y[k * 3 + c];
+      }
+      xy = xy + sxy * sxy;
+      xx = xx + sxx * sxx;
+      yy = yy + syy * syy;
+    }
+  const double den = sqrt(xx) * sqrt(yy);
+  return den > 0.0 ? xy / den : -1.0;
+}
+
+__global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, const double *__restrict__ V,
+                       const int *__restrict__ cptr, const int *__restrict__ cand, const int *__restrict__ cidx,
+                       double *__restrict__ Vt, unsigned char *__restrict__ taken, int n_max, double kappa_p,
+                       int nsel_cap, int *__restrict__ out_cnt, int *__restrict__ out_col,
+                       double *__restrict__ out_val) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int I = fnodes[f];
+  const int c0 = cptr[f], ncand = cptr[f + 1] - c0;
+  double *vt = Vt + (size_t)c0 * t * 3;
+  unsigned char *tk = taken + c0;
+  double r[TMAXD * 3], R[TMAXD * TMAXD], Y[TMAXD * 3], hv[3][TMAXD], hvv[3], w[TMAXD * 3];
+  int sel[TMAXD];
+  for (int i = 0; i < TMAXD * TMAXD; ++i) R[i] = 0.0;
+  for (int k = 0; k < t; ++k)
+    for (int c = 0; c < 3; ++c) r[k * 3 + c] = V[(size_t)k * n + 3L * I + c];
+  for (int j = 0; j < ncand; ++j) {
+    tk[j] = 0;
+    for (int k = 0; k < t; ++k)
+      for (int c = 0; c < 3; ++c) vt[((size_t)j * t + k) * 3 + c] = V[(size_t)k * n + 3L * cand[c0 + j] + c];
+  }
+  int nsel = 0, p = 0;
+  double rdmax = 0.0, rdmin = 0.0;
+  for (;;) {
+    if (nsel >= n_max || p + 3 > t) break;
+    double rr = 0.0;
+    for (int k = p; k < t; ++k)
+      for (int c = 0; c < 3; ++c) rr = rr + r[k * 3 + c] * r[k * 3 + c];
+    if (rr == 0.0) break;
+    int best = -1;
+    double baff = 0.0;
+    for (int j = 0; j < ncand; ++j) {
+      if (tk[j]) continue;
+      const double a = affinity(t, p, r, vt + (size_t)j * t * 3);
+      if (a < 0.0) continue;
+      if (best < 0 || a > baff) {
+        best = j;
+        baff = a;
+      }
+    }
+    if (best < 0) break;
+    for (int i = 0; i < t * 3; ++i) Y[i] = vt[(size_t)best * t * 3 + i];
+    int ok = 1;
+    double dmax = rdmax, dmin = rdmin;
+    for (int c = 0; c < 3 && ok; ++c) {
+      const int pc = p + c;
+      double sg = 0.0;
+      for (int k = pc; k < t; ++k) sg = sg + Y[k * 3 + c] * Y[k * 3 + c];
+      sg = sqrt(sg);
+      if (!(sg > 0.0)) {
+        ok = 0;
+        break;
+      }
+      const double alpha = Y[pc * 3 + c] >= 0.0 ? -sg : sg;
+      for (int k = 0; k < t; ++k) hv[c][k] = (k >= pc) ? Y[k * 3 + c] : 0.0;
+      hv[c][pc] = Y[pc * 3 + c] - alpha;
+      double vv = 0.0;
+      for (int k = pc; k < t; ++k) vv = vv + hv[c][k] * hv[c][k];
+      hvv[c] = vv;
+      for (int c2 = c + 1; c2 < 3; ++c2) reflect(t, pc, hv[c], vv, Y + c2, 3);
+      Y[pc * 3 + c] = alpha;
+      for (int k = pc + 1; k < t; ++k) Y[k * 3 + c] = 0.0;
+      const double ad = fabs(alpha);
+      if (pc == 0) {
+        dmax = ad;
+        dmin = ad;
+      } else {
+        if (ad > dmax) dmax = ad;
+        if (ad < dmin) dmin = ad;
+      }
+    }
+    if (!ok || !(dmin > 0.0) || dmax / dmin > kappa_p) break;
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k <= p + c; ++k) R[k * TMAXD + p + c] = Y[k * 3 + c];
+    for (int c = 0; c < 3; ++c) {
+      for (int c2 = 0; c2 < 3; ++c2) reflect(t, p + c, hv[c], hvv[c], r + c2, 3);
+      for (int j = 0; j < ncand; ++j) {
+        if (tk[j] || j == best) continue;
+        for (int c2 = 0; c2 < 3; ++c2) reflect(t, p + c, hv[c], hvv[c], vt + (size_t)j * t * 3 + c2, 3);
+      }
+    }
+    tk[best] = 1;
+    sel[nsel++] = cand[c0 + best];
+    p += 3;
+    rdmax = dmax;
+    rdmin = dmin;
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int i = p - 1; i >= 0; --i) {
+      double s = r[i * 3 + c];
+      for (int k = p - 1; k > i; --k) s = s - R[i * TMAXD + k] * w[k * 3 + c];
+      w[i * 3 + c] = s / R[i * TMAXD + i];
+    }
+  // entries sorted by coarse index
+  int ord[TMAXD];
+  for (int m = 0; m < nsel; ++m) ord[m] = m;
+  for (int u = 1; u < nsel; ++u) {
+    const int v = ord[u];
+    int q = u - 1;
+    while (q >= 0 && cidx[sel[ord[q]]] > cidx[sel[v]]) { ord[q + 1] = ord[q]; --q; }
+    ord[q + 1] = v;
+  }
+  out_cnt[f] = nsel;
+  for (int u = 0; u < nsel; ++u) {
+    const int m = ord[u];
+    out_col[(size_t)f * nsel_cap + u] = cidx[sel[m]];
+    double *o = out_val + ((size_t)f * nsel_cap + u) * 9;
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) o[c * 3 + d] = w[(3 * m + d) * 3 + c];
+  }
+}
+
+int dpls(const DevBsr &A, const unsigned char *strong, const int *cf, const int *cidx, const int *fnodes, int nf,
+         const int *cand_ptr, const int *cand, int t, const double *V, int n_max, double kappa_p, int *out_cnt,
+         int *out_col, double *out_val, int *status, cudaStream_t s) {
+  (void)strong; (void)cf; (void)status;
+  if (t > TMAXD) {
+    set_error("n_tv = %d exceeds the supported maximum %d", t, TMAXD);
+    return AMG_ERR_ARG;
+  }
+  if (nf == 0) return AMG_OK;
+  int total = 0;
+  AMG_CU(cudaMemcpyAsync(&total, cand_ptr + nf, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  DBuf<double> Vt;
+  DBuf<unsigned char> taken;
+  AMG_TRY(Vt.alloc((size_t)total * t * 3));
+  AMG_TRY(taken.alloc(total));
+  const int cap = n_max < t / 3 ? n_max : t / 3;
+  k_dpls<<<nblk(nf, 64), 64, 0, s>>>(nf, fnodes, 3L * A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p, n_max,
+                                     kappa_p, cap > 0 ? cap : 1, out_cnt, out_col, out_val);
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- SpGEMM
+// Z = X Y on Z's given pattern; each output block adds the block products
+// X_ik Y_kc over k ascending (entry (r,q) of a product: sum_d X(r,d) Y(d,q),
+// d ascending from 0), accumulating from 0.
+__global__ void k_spgemm(int nr, const int *__restrict__ xr, const int *__restrict__ xc, const double *__restrict__ xv,
+                         const int *__restrict__ yr, const int *__restrict__ yc, const double *__restrict__ yv,
+                         const int *__restrict__ zr, const int *__restrict__ zc, double *__restrict__ zv, int nnz) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nnz) return;
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {  // row of entry q: last row with zr[row] <= q
+    const int mid = (lo + hi + 1) >> 1;
+    if (zr[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  const int i = lo, c = zc[q];
+  double acc[9];
+  for (int e = 0; e < 9; ++e) acc[e] = 0.0;
+  for (int kx = xr[i]; kx < xr[i + 1]; ++kx) {
+    const int k = xc[kx];
+    int a = yr[k], b = yr[k + 1] - 1, ky = -1;
+    while (a <= b) {
+      const int mid = (a + b) >> 1;
+      if (yc[mid] == c) { ky = mid; break; }
+      if (yc[mid] < c) a = mid + 1; else b = mid - 1;
+    }
+    if (ky < 0) continue;
+    const double *x = xv + (size_t)kx * 9, *y = yv + (size_t)ky * 9;
+    for (int r = 0; r < 3; ++r)
+      for (int qq = 0; qq < 3; ++qq) {
+        double s = 0.0;
+        for (int d = 0; d < 3; ++d) s = s + x[r * 3 + d] * y[d * 3 + qq];
+        acc[r * 3 + qq] = acc[r * 3 + qq] + s;
+      }
+  }
+  for (int e = 0; e < 9; ++e) zv[(size_t)q * 9 + e] = acc[e];
+}
+
+int spgemm_numeric(const DevBsr &X, const DevBsr &Y, DevBsr &Z, cudaStream_t s) {
+  if (Z.nnzb == 0) return AMG_OK;
+  k_spgemm<<<nblk(Z.nnzb, 128), 128, 0, s>>>(Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
+                                            Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+}  // namespace det
+}  // namespace amg

@@ -1,0 +1,589 @@
+// Hierarchy set-up (Algorithm 1 of the paper): per level the aFSAI smoother
+// (Algorithm 3), the SRQCG test space (Algorithm 4), the affinity C/F split
+// (Sec. 3.3), DPLS prolongation (Algorithm 5) and the Galerkin product.
+// Floating-point work runs in the kernels of det.cu; this file does the
+// control flow and the integer graph work (pattern compaction and
+// transposition, the maximal independent set, DPLS candidate sets and the
+// symbolic Galerkin pattern) on the host.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstring>
+
+#include "amg_internal.h"
+
+namespace amg {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+const char *last_error() { return g_err; }
+
+static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------- kernels
+// Copy rows stored with a fixed capacity into a compact BSR (values only).
+__global__ void k_compact_vals(int n, int cap, const int *__restrict__ rowptr, const double *__restrict__ src,
+                               double *__restrict__ dst) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = (int)(t / (cap * 9));
+  if (I >= n) return;
+  const int rem = (int)(t - (long)I * cap * 9);
+  const int j = rem / 9, e = rem % 9;
+  const int len = rowptr[I + 1] - rowptr[I];
+  if (j >= len) return;
+  dst[((size_t)rowptr[I] + j) * 9 + e] = src[((size_t)I * cap + j) * 9 + e];
+}
+
+// T.val[dst] = transpose(A.val[perm[dst]])
+__global__ void k_transpose_vals(int nnzb, const int *__restrict__ perm, const double *__restrict__ src,
+                                 double *__restrict__ dst) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 9L * nnzb) return;
+  const int q = (int)(t / 9), e = (int)(t % 9), r = e / 3, c = e % 3;
+  dst[(size_t)q * 9 + c * 3 + r] = src[(size_t)perm[q] * 9 + e];
+}
+
+// P values: identity for coarse rows, DPLS blocks for fine rows.
+__global__ void k_p_vals(int n, const int *__restrict__ rowptr, const int *__restrict__ fidx, int cap,
+                         const double *__restrict__ fval, double *__restrict__ pv) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = (int)(t / (cap * 9));
+  if (I >= n) return;
+  const int rem = (int)(t - (long)I * cap * 9);
+  const int j = rem / 9, e = rem % 9;
+  const int len = rowptr[I + 1] - rowptr[I];
+  if (j >= len) return;
+  const int f = fidx[I];
+  const double v = (f < 0) ? ((e % 4 == 0) ? 1.0 : 0.0) : fval[((size_t)f * cap + j) * 9 + e];
+  pv[((size_t)rowptr[I] + j) * 9 + e] = v;
+}
+
+// dense copy of a BSR matrix (row-major m x m, m = 3 nr)
+__global__ void k_to_dense(int nr, const int *__restrict__ rp, const int *__restrict__ col,
+                           const double *__restrict__ val, double *__restrict__ D) {
+  const int I = blockIdx.x;
+  const int m = 3 * nr;
+  for (int k = rp[I] + threadIdx.x / 9; k < rp[I + 1]; k += blockDim.x / 9) {
+    if ((int)threadIdx.x >= (blockDim.x / 9) * 9) break;
+    const int e = threadIdx.x % 9, r = e / 3, c = e % 3;
+    D[(size_t)(3 * I + r) * m + 3 * col[k] + c] = val[(size_t)k * 9 + e];
+  }
+}
+
+// Right-looking dense Cholesky in place (lower triangle) by one block.
+__global__ void __launch_bounds__(1024) k_dense_chol(int m, double *__restrict__ D, int *__restrict__ status) {
+  __shared__ double dj;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (threadIdx.x == 0) {
+      const double s = D[(size_t)j * m + j];
+      if (!(s > 0.0)) bad = 1;
+      dj = sqrt(s);
+      D[(size_t)j * m + j] = dj;
+    }
+    __syncthreads();
+    if (bad) break;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) D[(size_t)i * m + j] /= dj;
+    __syncthreads();
+    const int w = m - j - 1;
+    const long tot = (long)w * w;
+    for (long idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      const int i = j + 1 + (int)(idx / w), k = j + 1 + (int)(idx % w);
+      if (k <= i) D[(size_t)i * m + k] -= D[(size_t)i * m + j] * D[(size_t)k * m + j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) atomicMin(status, AMG_ERR_NOT_SPD);
+}
+
+// Linv = L^{-1} column by column (one thread per column), Linv zeroed first.
+__global__ void k_tri_inv(int m, const double *__restrict__ L, double *__restrict__ Linv) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  for (int i = j; i < m; ++i) {
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int k = j; k < i; ++k) s -= L[(size_t)i * m + k] * Linv[(size_t)k * m + j];
+    Linv[(size_t)i * m + j] = s / L[(size_t)i * m + i];
+  }
+}
+
+__global__ void k_dense_transpose(int m, const double *__restrict__ A, double *__restrict__ T) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)m * m) return;
+  const int i = (int)(t / m), j = (int)(t % m);
+  T[(size_t)j * m + i] = A[t];
+}
+
+// ---------------------------------------------------------------- host graph work
+int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s) {
+  const int nnzb = A.nnzb;
+  AMG_TRY(T.alloc(A.nc, A.nr, nnzb));
+  T.h_rowptr.assign(A.nc + 1, 0);
+  T.h_col.resize(nnzb);
+  std::vector<int> perm(nnzb > 0 ? nnzb : 1);
+  for (int k = 0; k < nnzb; ++k) T.h_rowptr[A.h_col[k] + 1]++;
+  for (int i = 0; i < A.nc; ++i) T.h_rowptr[i + 1] += T.h_rowptr[i];
+  std::vector<int> next(T.h_rowptr.begin(), T.h_rowptr.end() - 1);
+  for (int I = 0; I < A.nr; ++I)
+    for (int k = A.h_rowptr[I]; k < A.h_rowptr[I + 1]; ++k) {
+      const int dst = next[A.h_col[k]]++;
+      T.h_col[dst] = I;
+      perm[dst] = k;
+    }
+  AMG_TRY(T.upload_pattern(s));
+  if (nnzb) {
+    DBuf<int> dperm;
+    AMG_TRY(dperm.alloc(nnzb));
+    AMG_CU(cudaMemcpyAsync(dperm.p, perm.data(), nnzb * sizeof(int), cudaMemcpyHostToDevice, s));
+    k_transpose_vals<<<nblk(9L * nnzb, 256), 256, 0, s>>>(nnzb, dperm.p, A.val.p, T.val.p);
+    AMG_LAUNCH_CHECK();
+    AMG_CU(cudaStreamSynchronize(s));
+  }
+  return AMG_OK;
+}
+
+// Greedy maximal independent set of the strong graph: nodes by degree
+// descending, index ascending; a visited undecided node becomes coarse and
+// its strong neighbours fine.
+static void mis_host(const DevBsr &A, const std::vector<unsigned char> &strong, std::vector<int> &cf) {
+  const int n = A.nr;
+  std::vector<int> deg(n, 0);
+  int maxdeg = 0;
+  for (int I = 0; I < n; ++I) {
+    for (int k = A.h_rowptr[I]; k < A.h_rowptr[I + 1]; ++k)
+      if (strong[k] && A.h_col[k] != I) deg[I]++;
+    maxdeg = std::max(maxdeg, deg[I]);
+  }
+  std::vector<int> cnt(maxdeg + 2, 0), order(n);
+  for (int I = 0; I < n; ++I) cnt[maxdeg - deg[I] + 1]++;
+  for (int d = 0; d <= maxdeg; ++d) cnt[d + 1] += cnt[d];
+  for (int I = 0; I < n; ++I) order[cnt[maxdeg - deg[I]]++] = I;
+  cf.assign(n, -1);
+  for (int q = 0; q < n; ++q) {
+    const int I = order[q];
+    if (cf[I] != -1) continue;
+    cf[I] = 1;
+    for (int k = A.h_rowptr[I]; k < A.h_rowptr[I + 1]; ++k) {
+      const int J = A.h_col[k];
+      if (strong[k] && J != I && cf[J] == -1) cf[J] = 0;
+    }
+  }
+}
+
+// Coarse nodes within d_p strong edges of every fine node, ascending.
+static void dpls_candidates(const DevBsr &A, const std::vector<unsigned char> &strong, const std::vector<int> &cf,
+                            int d_p, std::vector<int> &fnodes, std::vector<int> &cptr, std::vector<int> &cand) {
+  const int n = A.nr;
+  std::vector<int> dist(n, -1), front;
+  fnodes.clear();
+  cptr.assign(1, 0);
+  cand.clear();
+  for (int I = 0; I < n; ++I) {
+    if (cf[I] == 1) continue;
+    fnodes.push_back(I);
+    front.assign(1, I);
+    dist[I] = 0;
+    const size_t c0 = cand.size();
+    for (size_t q = 0; q < front.size(); ++q) {
+      const int K = front[q];
+      if (dist[K] >= d_p) continue;
+      for (int k = A.h_rowptr[K]; k < A.h_rowptr[K + 1]; ++k) {
+        const int J = A.h_col[k];
+        if (!strong[k] || J == K || dist[J] >= 0) continue;
+        dist[J] = dist[K] + 1;
+        front.push_back(J);
+        if (cf[J] == 1) cand.push_back(J);
+      }
+    }
+    for (int K : front) dist[K] = -1;
+    std::sort(cand.begin() + c0, cand.end());
+    cptr.push_back((int)cand.size());
+  }
+}
+
+// Pattern of Z = X Y (columns ascending).
+static void symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z) {
+  const int nr = X.nr, nc = Y.nc;
+  std::vector<int> mark(nc, -1), cols;
+  Z.h_rowptr.assign(nr + 1, 0);
+  Z.h_col.clear();
+  for (int i = 0; i < nr; ++i) {
+    cols.clear();
+    for (int kx = X.h_rowptr[i]; kx < X.h_rowptr[i + 1]; ++kx) {
+      const int k = X.h_col[kx];
+      for (int ky = Y.h_rowptr[k]; ky < Y.h_rowptr[k + 1]; ++ky) {
+        const int c = Y.h_col[ky];
+        if (mark[c] != i) {
+          mark[c] = i;
+          cols.push_back(c);
+        }
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    Z.h_col.insert(Z.h_col.end(), cols.begin(), cols.end());
+    Z.h_rowptr[i + 1] = (int)Z.h_col.size();
+  }
+  Z.nr = nr;
+  Z.nc = nc;
+  Z.nnzb = (int)Z.h_col.size();
+}
+
+static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &Ac, cudaStream_t s) {
+  DevBsr AP;
+  symbolic_product(A, P, AP);
+  {
+    std::vector<int> rp = AP.h_rowptr, cl = AP.h_col;
+    AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb));
+    AP.h_rowptr = rp;
+    AP.h_col = cl;
+  }
+  AMG_TRY(AP.upload_pattern(s));
+  AMG_TRY(det::spgemm_numeric(A, P, AP, s));
+  symbolic_product(R, AP, Ac);
+  {
+    std::vector<int> rp = Ac.h_rowptr, cl = Ac.h_col;
+    AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb));
+    Ac.h_rowptr = rp;
+    Ac.h_col = cl;
+  }
+  AMG_TRY(Ac.upload_pattern(s));
+  AMG_TRY(det::spgemm_numeric(R, AP, Ac, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// aFSAI(A, G_s, k, rho, eps) into a compact G.
+static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double eps, int maxg, DevBsr &G,
+                    cudaStream_t s) {
+  const int n = A.nr;
+  int maxdeg = 0;
+  for (int I = 0; I < n; ++I) maxdeg = std::max(maxdeg, A.h_rowptr[I + 1] - A.h_rowptr[I]);
+  DBuf<int> np, pat, status;
+  DBuf<double> val;
+  AMG_TRY(np.alloc(n));
+  AMG_TRY(pat.alloc((size_t)n * maxg));
+  AMG_TRY(val.alloc((size_t)n * (maxg + 1) * 9));
+  AMG_TRY(status.alloc(1));
+  AMG_TRY(status.zero(s));
+  det::FsaiOut out{np.p, pat.p, val.p};
+  AMG_TRY(det::fsai(A, Gs, k, rho, eps, maxg, maxdeg, out, status.p, s));
+  int st = 0;
+  AMG_CU(cudaMemcpy(&st, status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    set_error("aFSAI: non-positive pivot in a row system (matrix not SPD)");
+    return st;
+  }
+  std::vector<int> hnp(n), hpat((size_t)n * maxg);
+  AMG_CU(cudaMemcpy(hnp.data(), np.p, n * sizeof(int), cudaMemcpyDeviceToHost));
+  AMG_CU(cudaMemcpy(hpat.data(), pat.p, (size_t)n * maxg * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<int> rp(n + 1, 0), cl;
+  cl.reserve((size_t)n * 8);
+  for (int I = 0; I < n; ++I) {
+    for (int j = 0; j < hnp[I]; ++j) cl.push_back(hpat[(size_t)I * maxg + j]);
+    cl.push_back(I);
+    rp[I + 1] = (int)cl.size();
+  }
+  AMG_TRY(G.alloc(n, n, (int)cl.size()));
+  G.h_rowptr = std::move(rp);
+  G.h_col = std::move(cl);
+  AMG_TRY(G.upload_pattern(s));
+  k_compact_vals<<<nblk((long)n * (maxg + 1) * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// Algorithm 3.
+static int smoother_setup(Handle *h, Level &L, int level) {
+  const amg_params &p = h->prm;
+  cudaStream_t s = h->stream;
+  AMG_TRY(run_fsai(L.A, nullptr, p.k_g, p.rho_g, p.eps_g, p.max_g_nodes, L.G, s));
+  AMG_TRY(transpose_bsr(L.G, L.GT, s));
+  DBuf<double> out;
+  AMG_TRY(out.alloc(3));
+  double ho[3];
+  AMG_TRY(det::lanczos(L.A, L.G, L.GT, p.lanczos_m, p.seed, level, p.omega_safety, out.p, s));
+  AMG_CU(cudaMemcpy(ho, out.p, sizeof ho, cudaMemcpyDeviceToHost));
+  int passes = 0;
+  while (ho[1] < p.omega_bar && (double)L.G.nnzb / (double)L.G.nr < p.rho_bar && passes < p.max_refine) {
+    DevBsr G2;
+    AMG_TRY(run_fsai(L.A, &L.G, p.k_i, p.rho_i, p.eps_i, p.max_g_nodes, G2, s));
+    L.G = std::move(G2);
+    L.GT = DevBsr();
+    AMG_TRY(transpose_bsr(L.G, L.GT, s));
+    AMG_TRY(det::lanczos(L.A, L.G, L.GT, p.lanczos_m, p.seed, level, p.omega_safety, out.p, s));
+    AMG_CU(cudaMemcpy(ho, out.p, sizeof ho, cudaMemcpyDeviceToHost));
+    ++passes;
+  }
+  L.lmax = ho[0];
+  L.omega = ho[2];
+  L.npasses = passes;
+  return AMG_OK;
+}
+
+static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong) {
+  const amg_params &p = h->prm;
+  cudaStream_t s = h->stream;
+  const int n = L.n, t = p.n_tv;
+  std::vector<int> cidx(n, -1);
+  int nc = 0;
+  for (int I = 0; I < n; ++I)
+    if (L.cf[I] == 1) cidx[I] = nc++;
+  L.nc = nc;
+  std::vector<int> fnodes, cptr, cand;
+  dpls_candidates(L.A, strong, L.cf, p.d_p, fnodes, cptr, cand);
+  const int nf = (int)fnodes.size();
+  const int cap = std::max(1, std::min(p.n_max, t / 3));
+  DBuf<int> d_cidx, d_f, d_cptr, d_cand, d_cnt, d_col;
+  DBuf<double> d_val;
+  AMG_TRY(d_cidx.alloc(n));
+  AMG_TRY(d_f.alloc(nf));
+  AMG_TRY(d_cptr.alloc(nf + 1));
+  AMG_TRY(d_cand.alloc(cand.size()));
+  AMG_TRY(d_cnt.alloc(nf));
+  AMG_TRY(d_col.alloc((size_t)nf * cap));
+  AMG_TRY(d_val.alloc((size_t)nf * cap * 9));
+  AMG_CU(cudaMemcpyAsync(d_cidx.p, cidx.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (nf) {
+    AMG_CU(cudaMemcpyAsync(d_f.p, fnodes.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s));
+    AMG_CU(cudaMemcpyAsync(d_cptr.p, cptr.data(), (nf + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (!cand.empty())
+      AMG_CU(cudaMemcpyAsync(d_cand.p, cand.data(), cand.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    AMG_TRY(det::dpls(L.A, nullptr, nullptr, d_cidx.p, d_f.p, nf, d_cptr.p, d_cand.p, t, L.V.p, p.n_max,
+                      p.kappa_p, d_cnt.p, d_col.p, d_val.p, nullptr, s));
+  }
+  std::vector<int> hcnt(nf), hcol((size_t)nf * cap), fidx(n, -1);
+  if (nf) {
+    AMG_CU(cudaMemcpy(hcnt.data(), d_cnt.p, nf * sizeof(int), cudaMemcpyDeviceToHost));
+    AMG_CU(cudaMemcpy(hcol.data(), d_col.p, (size_t)nf * cap * sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  for (int f = 0; f < nf; ++f) fidx[fnodes[f]] = f;
+  std::vector<int> rp(n + 1, 0), cl;
+  for (int I = 0; I < n; ++I) {
+    if (L.cf[I] == 1) cl.push_back(cidx[I]);
+    else {
+      const int f = fidx[I];
+      for (int u = 0; u < hcnt[f]; ++u) cl.push_back(hcol[(size_t)f * cap + u]);
+    }
+    rp[I + 1] = (int)cl.size();
+  }
+  AMG_TRY(L.P.alloc(n, nc, (int)cl.size()));
+  L.P.h_rowptr = std::move(rp);
+  L.P.h_col = std::move(cl);
+  AMG_TRY(L.P.upload_pattern(s));
+  DBuf<int> d_fidx;
+  AMG_TRY(d_fidx.alloc(n));
+  AMG_CU(cudaMemcpyAsync(d_fidx.p, fidx.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  k_p_vals<<<nblk((long)n * cap * 9, 256), 256, 0, s>>>(n, L.P.rowptr.p, d_fidx.p, cap, d_val.p, L.P.val.p);
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+static int coarse_factor(Handle *h, Level &L) {
+  cudaStream_t s = h->stream;
+  const int m = 3 * L.n;
+  if (m > 6000) {
+    set_error("last level has %d dofs; the dense coarse solve supports at most 6000", m);
+    return AMG_ERR_COARSENING;
+  }
+  h->nL = m;
+  DBuf<double> D;
+  DBuf<int> st;
+  AMG_TRY(D.alloc((size_t)m * m));
+  AMG_TRY(D.zero(s));
+  AMG_TRY(st.alloc(1));
+  AMG_TRY(st.zero(s));
+  AMG_TRY(h->Linv.alloc((size_t)m * m));
+  AMG_TRY(h->LinvT.alloc((size_t)m * m));
+  AMG_TRY(h->Linv.zero(s));
+  if (L.n > 0) {
+    k_to_dense<<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D.p);
+    k_dense_chol<<<1, 1024, 0, s>>>(m, D.p, st.p);
+    k_tri_inv<<<nblk(m, 128), 128, 0, s>>>(m, D.p, h->Linv.p);
+    k_dense_transpose<<<nblk((long)m * m, 256), 256, 0, s>>>(m, h->Linv.p, h->LinvT.p);
+    AMG_LAUNCH_CHECK();
+  }
+  int hs = 0;
+  AMG_CU(cudaMemcpyAsync(&hs, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  if (hs) {
+    set_error("coarse-level Cholesky: non-positive pivot");
+    return hs;
+  }
+  return AMG_OK;
+}
+
+void free_hierarchy(Handle *h) {
+  h->lev.clear();
+  h->nlev = 0;
+  h->Linv.release();
+  h->LinvT.release();
+  h->nL = 0;
+}
+
+int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *vals, int mem, int ntv0,
+                    const double *V0, int memV) {
+  const amg_params &p = h->prm;
+  cudaStream_t s = h->stream;
+  const int t = p.n_tv;
+  free_hierarchy(h);
+  const double t_start = now_s();
+  double T_sm = 0, T_ts = 0, T_cs = 0, T_pl = 0, T_rap = 0;
+  const cudaMemcpyKind kind = mem == AMG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  auto L0 = std::make_unique<Level>();
+  {
+    const int n = h->n;
+    std::vector<int> hrp(n + 1);
+    if (mem == AMG_MEM_HOST) memcpy(hrp.data(), rowptr, (n + 1) * sizeof(int));
+    else AMG_CU(cudaMemcpy(hrp.data(), rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    const int nnzb = hrp[n];
+    AMG_TRY(L0->A.alloc(n, n, nnzb));
+    L0->A.h_rowptr = std::move(hrp);
+    L0->A.h_col.resize(nnzb);
+    if (mem == AMG_MEM_HOST) memcpy(L0->A.h_col.data(), col, nnzb * sizeof(int));
+    else AMG_CU(cudaMemcpy(L0->A.h_col.data(), col, nnzb * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int I = 0; I < n; ++I) {
+      for (int k = L0->A.h_rowptr[I]; k < L0->A.h_rowptr[I + 1]; ++k) {
+        const int J = L0->A.h_col[k];
+        if (J < 0 || J >= n || (k > L0->A.h_rowptr[I] && L0->A.h_col[k - 1] >= J)) {
+          set_error("K pattern: row %d has an invalid or unsorted column index %d", I, J);
+          return AMG_ERR_ARG;
+        }
+      }
+    }
+    AMG_TRY(L0->A.upload_pattern(s));
+    AMG_CU(cudaMemcpyAsync(L0->A.val.p, vals, (size_t)nnzb * 9 * sizeof(double), kind, s));
+    L0->n = n;
+  }
+  // starting test space: V0 padded with counter-generator columns
+  DBuf<double> Vin;
+  {
+    const int n3 = 3 * h->n;
+    AMG_TRY(Vin.alloc((size_t)n3 * t));
+    if (ntv0 > 0)
+      AMG_CU(cudaMemcpyAsync(Vin.p, V0, (size_t)n3 * ntv0 * sizeof(double),
+                             memV == AMG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (ntv0 > 0 && V0 != h->V0keep.p) {
+      AMG_TRY(h->V0keep.alloc((size_t)n3 * ntv0));
+      AMG_CU(cudaMemcpyAsync(h->V0keep.p, Vin.p, (size_t)n3 * ntv0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    h->ntv0 = ntv0;
+    AMG_TRY(det::uniform_fill(Vin.p, n3, ntv0, t - ntv0, p.seed, s));
+  }
+  h->lev.push_back(std::move(L0));
+  DBuf<unsigned char> d_strong;
+  for (int k = 0;; ++k) {
+    Level &L = *h->lev[k];
+    const int n3 = 3 * L.n;
+    if (n3 <= p.n_coarse || k == p.max_levels - 1 || k == 31) break;
+    double t0 = now_s();
+    AMG_TRY(smoother_setup(h, L, k));
+    double t1 = now_s();
+    T_sm += t1 - t0;
+    AMG_TRY(L.V.alloc((size_t)n3 * t));
+    DBuf<int> st;
+    AMG_TRY(st.alloc(1));
+    AMG_TRY(st.zero(s));
+    AMG_TRY(det::srqcg(L.A, L.G, L.GT, p.n_rq, p.k_ritz, t, Vin.p, L.V.p, st.p, s));
+    int hs = 0;
+    AMG_CU(cudaMemcpy(&hs, st.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hs) {
+      set_error("SRQCG: Ritz step lost rank");
+      return hs;
+    }
+    double t2 = now_s();
+    T_ts += t2 - t1;
+    AMG_TRY(d_strong.alloc(L.A.nnzb));
+    AMG_TRY(det::soc_filter(L.A, t, L.V.p, p.theta, d_strong.p, s));
+    std::vector<unsigned char> strong(L.A.nnzb);
+    if (L.A.nnzb)
+      AMG_CU(cudaMemcpy(strong.data(), d_strong.p, L.A.nnzb, cudaMemcpyDeviceToHost));
+    mis_host(L.A, strong, L.cf);
+    int nc = 0;
+    for (int I = 0; I < L.n; ++I) nc += (L.cf[I] == 1);
+    double t3 = now_s();
+    T_cs += t3 - t2;
+    if (nc == 0 || (double)nc > p.max_coarse_ratio * (double)L.n) {
+      L.G = DevBsr();
+      L.GT = DevBsr();
+      L.V.release();
+      L.cf.clear();
+      break;
+    }
+    AMG_TRY(build_P(h, L, strong));
+    AMG_TRY(transpose_bsr(L.P, L.R, s));
+    double t4 = now_s();
+    T_pl += t4 - t3;
+    auto Ln = std::make_unique<Level>();
+    AMG_TRY(galerkin(L.A, L.P, L.R, Ln->A, s));
+    Ln->n = Ln->A.nr;
+    double t5 = now_s();
+    T_rap += t5 - t4;
+    // next level's starting test space: rows of the coarse nodes
+    {
+      std::vector<int> src(3 * nc);
+      int q = 0;
+      for (int I = 0; I < L.n; ++I)
+        if (L.cf[I] == 1) {
+          for (int c = 0; c < 3; ++c) src[3 * q + c] = 3 * I + c;
+          ++q;
+        }
+      DBuf<int> dsrc;
+      AMG_TRY(dsrc.alloc(3 * nc));
+      AMG_CU(cudaMemcpyAsync(dsrc.p, src.data(), 3 * nc * sizeof(int), cudaMemcpyHostToDevice, s));
+      DBuf<double> Vn;
+      AMG_TRY(Vn.alloc((size_t)3 * nc * t));
+      AMG_TRY(det::gather_rows(dsrc.p, 3 * nc, n3, t, L.V.p, Vn.p, s));
+      AMG_CU(cudaStreamSynchronize(s));
+      Vin = std::move(Vn);
+    }
+    h->lev.push_back(std::move(Ln));
+    T_ts += now_s() - t5;
+  }
+  h->nlev = (int)h->lev.size();
+  const double t6 = now_s();
+  AMG_TRY(coarse_factor(h, *h->lev[h->nlev - 1]));
+  AMG_TRY(prepare_solve(h));
+  AMG_CU(cudaStreamSynchronize(s));
+  const double t_end = now_s();
+  amg_stats &st = h->stats;
+  st.nlev = h->nlev;
+  st.T_sm = T_sm;
+  st.T_ts = T_ts;
+  st.T_cs = T_cs;
+  st.T_pl = T_pl;
+  st.T_rap = T_rap + (t_end - t6);
+  st.T_p = t_end - t_start;
+  double rows = 0, nnz = 0, gnnz = 0;
+  for (int k = 0; k < h->nlev && k < 32; ++k) {
+    const Level &L = *h->lev[k];
+    rows += L.n;
+    nnz += L.A.nnzb;
+    gnnz += L.G.nnzb;
+    st.level_nodes[k] = L.n;
+    st.level_nnzb[k] = L.A.nnzb;
+    st.level_g_nnzb[k] = L.G.nnzb;
+    st.level_omega[k] = L.omega;
+  }
+  const Level &L0r = *h->lev[0];
+  st.C_gd = rows / (double)L0r.n;
+  st.C_op = nnz / (double)L0r.A.nnzb;
+  st.C_fs = gnnz / (double)L0r.A.nnzb;
+  return AMG_OK;
+}
+
+}  // namespace amg

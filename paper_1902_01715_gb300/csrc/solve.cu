@@ -1,0 +1,649 @@
+// Solve phase: PCG preconditioned by one V(1,1)-cycle per iteration
+// (Algorithm 2 with nu1 = nu2 = 1; post-smoothing with M^{-T} = M^{-1} since
+// M^{-1} = omega G^T G is symmetric, Sec. 2), with the FP64 CG recurrence of
+// Sec. 4 (x0 = 0, stop at ||r||_2 <= rtol ||b||_2).
+//
+// Every level matrix is stored "entry-major": entry e (0..8) of block k at
+// v[e*nnzb + k], so the LPR lanes that share a block row read consecutive
+// blocks with coalesced loads.  One sparse kernel computes y = A x with a
+// fused epilogue (plain, scaled, residual, scaled-add, accumulate), which
+// covers the two smoother products, the residual, restriction and
+// prolongation.  The V-cycle runs in FP64, FP32, or FP32 with bf16-stored
+// G, G^T, P, R; the CG recurrence, its reductions and the coarse solve are
+// FP64 in every mode.  One PCG iteration is captured in a CUDA graph; each
+// kernel returns at once when the device-side `done` flag is set, so the
+// host replays the graph and polls the flag.
+#include <cmath>
+
+#include "amg_internal.h"
+
+namespace amg {
+
+static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { typedef double type; };
+template <> struct Acc<float> { typedef float type; };
+
+__device__ __forceinline__ double cvt(double v, double) { return v; }
+__device__ __forceinline__ float cvt(float v, float) { return v; }
+__device__ __forceinline__ float cvt(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+__device__ __forceinline__ double cvt(float v, double) { return (double)v; }
+
+enum { EP_SET = 0, EP_SCALE = 1, EP_RESID = 2, EP_SADD = 3, EP_ACC = 4 };
+
+// y = epilogue(A x): EP_SET y = Ax; EP_SCALE y = w Ax; EP_RESID y = aux - Ax;
+// EP_SADD y = aux + w Ax; EP_ACC y += Ax.
+template <int LPR, typename TM, typename TX, int EP>
+__global__ void __launch_bounds__(256) k_bsrmv(int nr, const int *__restrict__ rp, const int *__restrict__ col,
+                                               const TM *__restrict__ v, long nnzb, const TX *__restrict__ x,
+                                               TX *__restrict__ y, const TX *__restrict__ aux, TX w,
+                                               const int *__restrict__ done) {
+  if (done && *done) return;
+  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = (int)(gt / LPR);
+  const int lane = (int)(gt & (LPR - 1));
+  const bool valid = row < nr;
+  TX a0 = 0, a1 = 0, a2 = 0;
+  if (valid) {
+    const int ke = rp[row + 1];
+    for (int k = rp[row] + lane; k < ke; k += LPR) {
+      const long j = col[k];
+      const TX x0 = x[3 * j], x1 = x[3 * j + 1], x2 = x[3 * j + 2];
+      a0 += cvt(v[k], TX(0)) * x0 + cvt(v[nnzb + k], TX(0)) * x1 + cvt(v[2 * nnzb + k], TX(0)) * x2;
+      a1 += cvt(v[3 * nnzb + k], TX(0)) * x0 + cvt(v[4 * nnzb + k], TX(0)) * x1 + cvt(v[5 * nnzb + k], TX(0)) * x2;
+      a2 += cvt(v[6 * nnzb + k], TX(0)) * x0 + cvt(v[7 * nnzb + k], TX(0)) * x1 + cvt(v[8 * nnzb + k], TX(0)) * x2;
+    }
+  }
+#pragma unroll
+  for (int off = LPR / 2; off > 0; off >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, off, LPR);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, off, LPR);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off, LPR);
+  }
+  if (valid && lane == 0) {
+    const long o = 3L * row;
+    if (EP == EP_SET) { y[o] = a0; y[o + 1] = a1; y[o + 2] = a2; }
+    if (EP == EP_SCALE) { y[o] = w * a0; y[o + 1] = w * a1; y[o + 2] = w * a2; }
+    if (EP == EP_RESID) { y[o] = aux[o] - a0; y[o + 1] = aux[o + 1] - a1; y[o + 2] = aux[o + 2] - a2; }
+    if (EP == EP_SADD) { y[o] = aux[o] + w * a0; y[o + 1] = aux[o + 1] + w * a1; y[o + 2] = aux[o + 2] + w * a2; }
+    if (EP == EP_ACC) { y[o] += a0; y[o + 1] += a1; y[o + 2] += a2; }
+  }
+}
+
+template <int LPR, typename TM, typename TX>
+static void launch_lpr(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
+                       const int *done, cudaStream_t s) {
+  const int nb = nblk((long)M.nr * LPR, 256);
+  if (nb == 0) return;
+  switch (ep) {
+    case EP_SET: k_bsrmv<LPR, TM, TX, EP_SET><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    case EP_SCALE: k_bsrmv<LPR, TM, TX, EP_SCALE><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    case EP_RESID: k_bsrmv<LPR, TM, TX, EP_RESID><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    case EP_SADD: k_bsrmv<LPR, TM, TX, EP_SADD><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    default: k_bsrmv<LPR, TM, TX, EP_ACC><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+  }
+}
+
+template <typename TM, typename TX>
+static void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
+                  cudaStream_t s) {
+  switch (M.lpr) {
+    case 4: launch_lpr<4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 8: launch_lpr<8>(ep, M, v, x, y, aux, w, done, s); break;
+    case 16: launch_lpr<16>(ep, M, v, x, y, aux, w, done, s); break;
+    default: launch_lpr<32>(ep, M, v, x, y, aux, w, done, s); break;
+  }
+}
+
+// ---------------------------------------------------------------- layout
+template <typename T>
+__global__ void k_entry_major(long nnzb, const double *__restrict__ src, T *__restrict__ dst) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 9 * nnzb) return;
+  const long k = t / 9;
+  const int e = (int)(t % 9);
+  dst[e * nnzb + k] = (T)src[t];
+}
+
+template <>
+__global__ void k_entry_major<__nv_bfloat16>(long nnzb, const double *__restrict__ src, __nv_bfloat16 *__restrict__ dst) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 9 * nnzb) return;
+  const long k = t / 9;
+  const int e = (int)(t % 9);
+  dst[e * nnzb + k] = __float2bfloat16_rn((float)src[t]);
+}
+
+static int pick_lpr(const DevBsr &A) {
+  const double avg = A.nr ? (double)A.nnzb / A.nr : 1.0;
+  if (avg <= 5.0) return 4;
+  if (avg <= 10.0) return 8;
+  if (avg <= 20.0) return 16;
+  return 32;
+}
+
+static int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s) {
+  M.nr = A.nr;
+  M.nc = A.nc;
+  M.nnzb = A.nnzb;
+  M.rowptr = A.rowptr.p;
+  M.col = A.col.p;
+  M.lpr = pick_lpr(A);
+  const long n9 = 9L * A.nnzb;
+  const int nb = nblk(n9, 256);
+  if (f64) {
+    AMG_TRY(M.v64.alloc(n9));
+    if (nb) k_entry_major<double><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v64.p);
+  }
+  if (f32) {
+    AMG_TRY(M.v32.alloc(n9));
+    if (nb) k_entry_major<float><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v32.p);
+  }
+  if (b16) {
+    AMG_TRY(M.v16.alloc(n9));
+    if (nb) k_entry_major<__nv_bfloat16><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v16.p);
+  }
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+int prepare_solve(Handle *h) {
+  cudaStream_t s = h->stream;
+  const int prec = h->prm.vcycle_prec;
+  const bool f64 = prec == AMG_FP64, f32 = prec != AMG_FP64, b16 = prec == AMG_FP32_BF16GP;
+  for (int k = 0; k < h->nlev; ++k) {
+    Level &L = *h->lev[k];
+    // level 0 A is always kept in FP64 for the outer CG operator
+    AMG_TRY(make_solvemat(L.A, L.sA, f64 || k == 0, f32, false, s));
+    if (k < h->nlev - 1) {
+      AMG_TRY(make_solvemat(L.G, L.sG, f64, f32 && !b16, b16, s));
+      AMG_TRY(make_solvemat(L.GT, L.sGT, f64, f32 && !b16, b16, s));
+      AMG_TRY(make_solvemat(L.P, L.sP, f64, f32 && !b16, b16, s));
+      AMG_TRY(make_solvemat(L.R, L.sR, f64, f32 && !b16, b16, s));
+    }
+    const size_t n3 = 3 * (size_t)L.n;
+    if (f64) {
+      AMG_TRY(L.y64.alloc(n3)); AMG_TRY(L.z64.alloc(n3));
+      AMG_TRY(L.s64.alloc(n3)); AMG_TRY(L.r64.alloc(n3)); AMG_TRY(L.t64.alloc(n3));
+    } else {
+      AMG_TRY(L.y32.alloc(n3)); AMG_TRY(L.z32.alloc(n3));
+      AMG_TRY(L.s32.alloc(n3)); AMG_TRY(L.r32.alloc(n3)); AMG_TRY(L.t32.alloc(n3));
+    }
+  }
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+    h->graph_k = -1;
+  }
+  h->kcap = 0;  // PCG work buffers are sized by the coarse level: reallocate
+  h->x.release();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- coarse solve
+// t = Linv y (lower triangular rows), z = LinvT t (upper triangular rows);
+// one warp per row, FP64.
+template <typename TX>
+__global__ void k_trmv_lower(int m, const double *__restrict__ Li, const TX *__restrict__ y, double *__restrict__ t,
+                             const int *__restrict__ done) {
+  if (done && *done) return;
+  const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  double s = 0.0;
+  const double *Lr = Li + (size_t)row * m;
+  for (int k = lane; k <= row; k += 32) s += Lr[k] * (double)y[k];
+  for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) t[row] = s;
+}
+
+template <typename TX>
+__global__ void k_trmv_upper(int m, const double *__restrict__ LiT, const double *__restrict__ t, TX *__restrict__ z,
+                             const int *__restrict__ done) {
+  if (done && *done) return;
+  const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  double s = 0.0;
+  const double *Lr = LiT + (size_t)row * m;
+  for (int k = row + lane; k < m; k += 32) s += Lr[k] * t[k];
+  for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) z[row] = (TX)s;
+}
+
+// ---------------------------------------------------------------- V-cycle
+template <typename TX> struct Vec;
+template <> struct Vec<double> {
+  static double *y(Level &L) { return L.y64.p; }
+  static double *z(Level &L) { return L.z64.p; }
+  static double *s(Level &L) { return L.s64.p; }
+  static double *r(Level &L) { return L.r64.p; }
+  static double *t(Level &L) { return L.t64.p; }
+};
+template <> struct Vec<float> {
+  static float *y(Level &L) { return L.y32.p; }
+  static float *z(Level &L) { return L.z32.p; }
+  static float *s(Level &L) { return L.s32.p; }
+  static float *r(Level &L) { return L.r32.p; }
+  static float *t(Level &L) { return L.t32.p; }
+};
+
+template <typename TX>
+static const TX *vals(const SolveMat &M, bool lowp);
+template <>
+const double *vals<double>(const SolveMat &M, bool) { return M.v64.p; }
+template <>
+const float *vals<float>(const SolveMat &M, bool) { return M.v32.p; }
+
+template <typename TX>
+static void mv(int ep, const SolveMat &M, bool b16, const TX *x, TX *y, const TX *aux, TX w, const int *done,
+               cudaStream_t s) {
+  if (b16) bsrmv<__nv_bfloat16, TX>(ep, M, M.v16.p, x, y, aux, w, done, s);
+  else bsrmv<TX, TX>(ep, M, vals<TX>(M, false), x, y, aux, w, done, s);
+}
+
+template <>
+void mv<double>(int ep, const SolveMat &M, bool, const double *x, double *y, const double *aux, double w,
+                const int *done, cudaStream_t s) {
+  bsrmv<double, double>(ep, M, M.v64.p, x, y, aux, w, done, s);
+}
+
+// z = B(y) on level k; y and z are the level's vectors (or the caller's at k=0)
+template <typename TX>
+static void vcycle_level(Handle *h, int k, const TX *y, TX *z, const int *done, double *ctmp) {
+  cudaStream_t st = h->stream;
+  Level &L = *h->lev[k];
+  const bool b16 = h->prm.vcycle_prec == AMG_FP32_BF16GP;
+  if (k == h->nlev - 1) {
+    const int m = h->nL;
+    if (m == 0) return;
+    k_trmv_lower<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->Linv.p, y, ctmp, done);
+    k_trmv_upper<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->LinvT.p, ctmp, z, done);
+    return;
+  }
+  Level &C = *h->lev[k + 1];
+  TX *s = Vec<TX>::s(L), *r = Vec<TX>::r(L), *t = Vec<TX>::t(L);
+  const TX w = (TX)L.omega;
+  mv<TX>(EP_SET, L.sG, b16, y, t, (const TX *)nullptr, w, done, st);       // t = G y
+  mv<TX>(EP_SCALE, L.sGT, b16, t, s, (const TX *)nullptr, w, done, st);    // s = w G^T t
+  mv<TX>(EP_RESID, L.sA, false, s, r, y, w, done, st);                    // r = y - A s
+  mv<TX>(EP_SET, L.sR, b16, r, Vec<TX>::y(C), (const TX *)nullptr, w, done, st);  // y_c = P^T r
+  vcycle_level<TX>(h, k + 1, Vec<TX>::y(C), Vec<TX>::z(C), done, ctmp);
+  mv<TX>(EP_ACC, L.sP, b16, Vec<TX>::z(C), s, (const TX *)nullptr, w, done, st);  // s += P z_c
+  mv<TX>(EP_RESID, L.sA, false, s, r, y, w, done, st);                    // r = y - A s
+  mv<TX>(EP_SET, L.sG, b16, r, t, (const TX *)nullptr, w, done, st);       // t = G r
+  mv<TX>(EP_SADD, L.sGT, b16, t, z, s, w, done, st);                       // z = s + w G^T t
+}
+
+// ---------------------------------------------------------------- PCG
+// scalar slots (doubles) and flags (ints) on the device
+enum { P_BN2 = 0, P_RZ, P_PQ, P_ALPHA, P_RR, P_RZN, P_RZO, P_BETA, P_TOL2, P_NSC };
+enum { F_DONE = 0, F_ITERS, F_STATUS, F_MAXIT, F_TICKET, F_NFL };
+
+constexpr int RED_BLOCKS = 296;
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  }
+  return t;  // valid in thread 0
+}
+
+// Deterministic two-level reduction: block partials, then the last block to
+// finish sums them in block order and runs `fin` on thread 0.
+template <class Fin>
+__device__ __forceinline__ void finish_reduce(double v, double *part, int *flags, double *sh, Fin fin) {
+  const double bs = block_sum(v, sh);
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(&flags[F_TICKET], 1) == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += ((volatile double *)part)[b];
+  const double tot = block_sum(t, sh);
+  if (threadIdx.x == 0) {
+    flags[F_TICKET] = 0;
+    fin(tot);
+  }
+}
+
+// pq = p.q ; alpha = rz / pq
+__global__ void __launch_bounds__(RED_THREADS) k_pcg_pq(long n, const double *__restrict__ p, const double *__restrict__ q,
+                                                        double *sc, int *flags, double *part) {
+  if (flags[F_DONE]) return;
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) v += p[i] * q[i];
+  finish_reduce(v, part, flags, sh, [&](double tot) {
+    sc[P_PQ] = tot;
+    if (!(tot > 0.0) || !isfinite(tot)) {
+      flags[F_STATUS] = AMG_ERR_BREAKDOWN;
+      flags[F_DONE] = 1;
+    } else {
+      sc[P_ALPHA] = sc[P_RZ] / tot;
+    }
+  });
+}
+
+// x += alpha p ; r -= alpha q ; rr = r.r ; convergence ; rlow = (TX) r
+template <typename TX>
+__global__ void __launch_bounds__(RED_THREADS) k_pcg_xr(long n, double *__restrict__ x, double *__restrict__ r,
+                                                        const double *__restrict__ p, const double *__restrict__ q,
+                                                        TX *__restrict__ rlow, double *sc, int *flags, double *part) {
+  if (flags[F_DONE]) return;
+  __shared__ double sh[32];
+  const double a = sc[P_ALPHA];
+  double v = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    const double ri = r[i] - a * q[i];
+    r[i] = ri;
+    if (rlow) rlow[i] = (TX)ri;
+    v += ri * ri;
+  }
+  finish_reduce(v, part, flags, sh, [&](double tot) {
+    sc[P_RR] = tot;
+    const int it = flags[F_ITERS] + 1;
+    flags[F_ITERS] = it;
+    if (!isfinite(tot)) {
+      flags[F_STATUS] = AMG_ERR_BREAKDOWN;
+      flags[F_DONE] = 1;
+    } else if (tot <= sc[P_TOL2]) {
+      flags[F_DONE] = 1;
+    } else if (it >= flags[F_MAXIT]) {
+      flags[F_STATUS] = AMG_ERR_NOT_CONVERGED;
+      flags[F_DONE] = 1;
+    }
+  });
+}
+
+// z = (double) zlow (mixed modes); rz = r.z and, for flexible CG, r.z_old;
+// beta = (rz - r.z_old) / rz_prev (flexible) or rz / rz_prev.
+template <typename TX>
+__global__ void __launch_bounds__(RED_THREADS) k_pcg_rz(long n, const double *__restrict__ r, double *__restrict__ z,
+                                                        const TX *__restrict__ zlow, const double *__restrict__ zold,
+                                                        int flexible, double *sc, int *flags, double *part,
+                                                        double *part2) {
+  if (flags[F_DONE]) return;
+  __shared__ double sh[32];
+  double v = 0.0, v2 = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double zi;
+    if (zlow) {
+      zi = (double)zlow[i];
+      z[i] = zi;
+    } else {
+      zi = z[i];
+    }
+    v += r[i] * zi;
+    if (flexible) v2 += r[i] * zold[i];
+  }
+  const double b2 = flexible ? block_sum(v2, sh) : 0.0;
+  if (flexible && threadIdx.x == 0) part2[blockIdx.x] = b2;
+  __syncthreads();
+  finish_reduce(v, part, flags, sh, [&](double tot) {
+    double rzo = 0.0;
+    if (flexible)
+      for (int b = 0; b < (int)gridDim.x; ++b) rzo += ((volatile double *)part2)[b];
+    const double prev = sc[P_RZ];
+    sc[P_BETA] = flexible ? (tot - rzo) / prev : tot / prev;
+    sc[P_RZ] = tot;
+    if (!isfinite(sc[P_BETA])) {
+      flags[F_STATUS] = AMG_ERR_BREAKDOWN;
+      flags[F_DONE] = 1;
+    }
+  });
+}
+
+__global__ void k_pcg_p(long n, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold,
+                        int flexible, const double *sc, const int *flags) {
+  if (flags[F_DONE]) return;
+  const double b = sc[P_BETA];
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    p[i] = z[i] + b * p[i];
+    if (flexible) zold[i] = z[i];
+  }
+}
+
+// start: x = 0, r = b, rlow = (TX) b, bn2 = b.b, tol2 = rtol^2 bn2
+template <typename TX>
+__global__ void __launch_bounds__(RED_THREADS) k_pcg_start(long n, const double *__restrict__ b, double *__restrict__ x,
+                                                           double *__restrict__ r, TX *__restrict__ rlow, double rtol,
+                                                           double *sc, int *flags, double *part) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    x[i] = 0.0;
+    r[i] = b[i];
+    if (rlow) rlow[i] = (TX)b[i];
+    v += b[i] * b[i];
+  }
+  finish_reduce(v, part, flags, sh, [&](double tot) {
+    sc[P_BN2] = tot;
+    sc[P_TOL2] = (rtol * rtol) * tot;
+    sc[P_RR] = tot;
+    sc[P_RZ] = 1.0;
+    if (!isfinite(tot)) {
+      flags[F_STATUS] = AMG_ERR_BREAKDOWN;
+      flags[F_DONE] = 1;
+    } else if (tot == 0.0) {
+      flags[F_DONE] = 1;
+    }
+  });
+}
+
+// first direction: p = z, z_old = z, rz = r.z
+__global__ void k_pcg_first_p(long n, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold,
+                              const int *flags) {
+  if (flags[F_DONE]) return;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    p[i] = z[i];
+    zold[i] = z[i];
+  }
+}
+
+__global__ void k_set_flags(int *flags, int maxit) {
+  flags[F_DONE] = 0;
+  flags[F_ITERS] = 0;
+  flags[F_STATUS] = 0;
+  flags[F_MAXIT] = maxit;
+  flags[F_TICKET] = 0;
+}
+
+static int ensure_pcg(Handle *h) {
+  if (h->kcap >= 1 && h->x.p) return AMG_OK;
+  const size_t n3 = 3 * (size_t)h->n;
+  AMG_TRY(h->x.alloc(n3));
+  AMG_TRY(h->r.alloc(n3));
+  AMG_TRY(h->z.alloc(n3));
+  AMG_TRY(h->p.alloc(n3));
+  AMG_TRY(h->q.alloc(n3));
+  AMG_TRY(h->zold.alloc(n3));
+  AMG_TRY(h->bvec.alloc(n3));
+  AMG_TRY(h->scal.alloc(P_NSC + 8));
+  AMG_TRY(h->flags.alloc(F_NFL + 4));
+  AMG_TRY(h->red.alloc(4 * RED_BLOCKS + 16 + 3 * (size_t)(h->nL > 0 ? h->nL : 1)));
+  h->kcap = 1;
+  return AMG_OK;
+}
+
+template <typename TX>
+static TX *low_r(Handle *h) { return Vec<TX>::y(*h->lev[0]); }
+template <typename TX>
+static TX *low_z(Handle *h) { return Vec<TX>::z(*h->lev[0]); }
+
+// one PCG iteration (graph body)
+template <typename TX>
+static void pcg_iteration(Handle *h, bool mixed) {
+  cudaStream_t s = h->stream;
+  Level &L0 = *h->lev[0];
+  const long n = 3L * h->n;
+  double *part = h->red.p, *part2 = h->red.p + 2 * RED_BLOCKS, *ctmp = h->red.p + 4 * RED_BLOCKS + 16;
+  int *fl = h->flags.p;
+  double *sc = h->scal.p;
+  const int *done = fl + F_DONE;
+  bsrmv<double, double>(EP_SET, L0.sA, L0.sA.v64.p, h->p.p, h->q.p, nullptr, 0.0, done, s);
+  k_pcg_pq<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->q.p, sc, fl, part);
+  if (mixed) {
+    k_pcg_xr<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, low_r<TX>(h), sc, fl, part);
+    vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), done, ctmp);
+    k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, low_z<TX>(h), h->zold.p, 1, sc, fl, part,
+                                                     part2);
+    k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 1, sc, fl);
+  } else {
+    k_pcg_xr<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, (double *)nullptr, sc, fl,
+                                                         part);
+    vcycle_level<double>(h, 0, h->r.p, h->z.p, done, ctmp);
+    k_pcg_rz<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, (const double *)nullptr, h->zold.p, 0, sc,
+                                                         fl, part, part2);
+    k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 0, sc, fl);
+  }
+}
+
+template <typename TX>
+static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int *iters, double *relres, bool mixed) {
+  cudaStream_t s = h->stream;
+  const long n = 3L * h->n;
+  double *part = h->red.p, *ctmp = h->red.p + 4 * RED_BLOCKS + 16;
+  int *fl = h->flags.p;
+  double *sc = h->scal.p;
+  k_set_flags<<<1, 1, 0, s>>>(fl, h->prm.maxit);
+  k_pcg_start<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, b, h->x.p, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr, rtol,
+                                                      sc, fl, part);
+  if (mixed) {
+    vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), fl + F_DONE, ctmp);
+  } else {
+    vcycle_level<double>(h, 0, h->r.p, h->z.p, fl + F_DONE, ctmp);
+  }
+  // rz = r.z (beta unused)
+  k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
+                                                   h->zold.p, 0, sc, fl, part, part + 2 * RED_BLOCKS);
+  k_pcg_first_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, fl);
+  AMG_LAUNCH_CHECK();
+  const int key = mixed ? 1 : 0;
+  if (!h->graph_exec || h->graph_k != 1 || h->graph_prec != key) {
+    if (h->graph_exec) {
+      cudaGraphExecDestroy(h->graph_exec);
+      h->graph_exec = nullptr;
+    }
+    cudaGraph_t g;
+    AMG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    pcg_iteration<TX>(h, mixed);
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (ce != cudaSuccess) {
+      set_error("graph capture failed: %s", cudaGetErrorString(ce));
+      return AMG_ERR_CUDA;
+    }
+    AMG_CU(cudaGraphInstantiate(&h->graph_exec, g, 0));
+    cudaGraphDestroy(g);
+    h->graph_k = 1;
+    h->graph_prec = key;
+  }
+  int hflags[F_NFL];
+  int *pinned = nullptr;
+  AMG_CU(cudaMallocHost((void **)&pinned, 4 * sizeof(int)));
+  int rc = AMG_OK;
+  // replay; the device flag makes finished iterations no-ops, the host checks
+  // it every `chunk` launches
+  const int chunk = 4;
+  for (int it = 0; it < h->prm.maxit + chunk; it += chunk) {
+    for (int c = 0; c < chunk; ++c) {
+      cudaError_t e = cudaGraphLaunch(h->graph_exec, s);
+      if (e != cudaSuccess) {
+        set_error("cudaGraphLaunch: %s", cudaGetErrorString(e));
+        rc = AMG_ERR_CUDA;
+        break;
+      }
+    }
+    if (rc) break;
+    cudaMemcpyAsync(pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("PCG: %s", cudaGetErrorString(e));
+      rc = AMG_ERR_CUDA;
+      break;
+    }
+    if (pinned[0]) break;
+  }
+  cudaFreeHost(pinned);
+  if (rc) return rc;
+  double hsc[P_NSC];
+  AMG_CU(cudaMemcpy(hflags, fl, sizeof hflags, cudaMemcpyDeviceToHost));
+  AMG_CU(cudaMemcpy(hsc, sc, sizeof hsc, cudaMemcpyDeviceToHost));
+  AMG_CU(cudaMemcpyAsync(x, h->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  *iters = hflags[F_ITERS];
+  *relres = hsc[P_BN2] > 0.0 ? std::sqrt(hsc[P_RR] / hsc[P_BN2]) : 0.0;
+  return hflags[F_STATUS];
+}
+
+int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres) {
+  AMG_TRY(ensure_pcg(h));
+  const long n = 3L * h->n;
+  const bool mixed = h->prm.vcycle_prec != AMG_FP64;
+  int worst = AMG_OK, maxit = 0;
+  for (int j = 0; j < k; ++j) {
+    int it = 0;
+    double rr = 0.0;
+    const int rc = mixed ? pcg_solve_one<float>(h, B + (size_t)j * n, X + (size_t)j * n, rtol, &it, &rr, true)
+                         : pcg_solve_one<double>(h, B + (size_t)j * n, X + (size_t)j * n, rtol, &it, &rr, false);
+    if (rc == AMG_ERR_CUDA) return rc;
+    if (rc && !worst) worst = rc;
+    iters[j] = it;
+    relres[j] = rr;
+    maxit = it > maxit ? it : maxit;
+  }
+  h->stats.n_it = maxit;
+  return worst;
+}
+
+__global__ void k_d2f(long n, const double *__restrict__ a, float *__restrict__ b) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_f2d(long n, const float *__restrict__ a, double *__restrict__ b) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+int vcycle_apply(Handle *h, const double *y, double *z) {
+  AMG_TRY(ensure_pcg(h));
+  cudaStream_t s = h->stream;
+  const long n = 3L * h->n;
+  double *ctmp = h->red.p + 4 * RED_BLOCKS + 16;
+  k_set_flags<<<1, 1, 0, s>>>(h->flags.p, 1);
+  if (h->prm.vcycle_prec == AMG_FP64) {
+    vcycle_level<double>(h, 0, y, z, h->flags.p + F_DONE, ctmp);
+  } else {
+    k_d2f<<<nblk(n, 256), 256, 0, s>>>(n, y, low_r<float>(h));
+    vcycle_level<float>(h, 0, low_r<float>(h), low_z<float>(h), h->flags.p + F_DONE, ctmp);
+    k_f2d<<<nblk(n, 256), 256, 0, s>>>(n, low_z<float>(h), z);
+  }
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+Handle::~Handle() {
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  lev.clear();
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+}  // namespace amg

@@ -1,0 +1,167 @@
+"""GPU library against the oracle, through the C ABI.
+
+Structure (C/F split, patterns of A_k, G_k, P_k) must be bit-identical; level
+values within 1e-13 relative; FP64 solutions within 1e-10 relative at
+rtol = 1e-12; mixed modes reach the 1e-8 relative true residual."""
+import numpy as np
+import pytest
+
+import workloads as W
+from _problems import SMALL, gpu_problem, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1902_01715_gb300 as lib_
+    lib_.build()
+    lib_.lib()
+    return lib_
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a - b).max())
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_fe_bitwise(A, orc, name):
+    p = SMALL[name]()
+    K, V0, f, nm = oracle_problem(orc, p)
+    d = gpu_problem(A, p)
+    assert np.array_equal(d["node_map"], nm)
+    assert np.array_equal(d["rowptr"].cpu().numpy(), K.rowptr)
+    assert np.array_equal(d["col"].cpu().numpy(), K.col[:K.nnzb])
+    assert np.array_equal(d["Ke0"].cpu().numpy(), orc.ke0(p.nu, p.hx, p.hy, p.hz))
+    assert np.array_equal(d["vals"].cpu().numpy(), K.val[:K.nnzb])
+    assert np.array_equal(d["f"].cpu().numpy(), f)
+    assert np.array_equal(d["V0"].cpu().numpy(), V0)
+
+
+def _both(A, orc, p, **over):
+    K, V0, f, nm = oracle_problem(orc, p)
+    H = orc.Hierarchy(K, V0, orc.default_params(3, **{k: v for k, v in over.items() if k != "vcycle_prec"}))
+    d = gpu_problem(A, p)
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], **over)
+    return H, S, K, f, d
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_hierarchy_bit_exact_structure(A, orc, name):
+    H, S, K, f, d = _both(A, orc, SMALL[name]())
+    assert S.nlev == H.nlev
+    for k in range(H.nlev):
+        go, oo = S.level_info(k), H.info(k)
+        assert go["nr"] == oo["nr"] and go["nnzb_A"] == oo["nnzb_A"], k
+        Ao = H.matrix(k, "A")
+        rp, col, val = S.level_matrix(k, "A")
+        assert np.array_equal(rp, Ao.rowptr) and np.array_equal(col, Ao.col[:Ao.nnzb]), k
+        assert rel(val, Ao.val[:Ao.nnzb]) <= 1e-13, k
+        if k == H.nlev - 1:
+            continue
+        assert go["npasses"] == oo["npasses"], k
+        assert go["omega"] == oo["omega"] and go["lmax"] == oo["lmax"], k
+        assert np.array_equal(S.level_cf(k), H.cf(k)), k
+        for which in ("G", "P", "R"):
+            Mo = H.matrix(k, which)
+            rp, col, val = S.level_matrix(k, which)
+            assert np.array_equal(rp, Mo.rowptr) and np.array_equal(col, Mo.col[:Mo.nnzb]), (k, which)
+            assert rel(val, Mo.val[:Mo.nnzb]) <= 1e-13, (k, which)
+        assert rel(S.level_testspace(k), H.V(k)) <= 1e-12, k
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_vcycle_matches_oracle(A, orc, name):
+    import torch
+    H, S, K, f, d = _both(A, orc, SMALL[name]())
+    y = np.random.default_rng(41).normal(size=3 * K.nr)
+    zo = H.vcycle(y)
+    zg = S.vcycle(torch.tensor(y, device="cuda")).cpu().numpy()
+    assert rel(zg, zo) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_fp64_solution_matches_oracle(A, orc, name):
+    import torch
+    H, S, K, f, d = _both(A, orc, SMALL[name]())
+    xo, ito, rro, rco = H.pcg(f, 1e-8)
+    xg, itg, rrg, rcg = S.solve(d["f"], 1e-8)
+    assert rco == 0 and rcg == 0
+    assert abs(itg[0] - ito) <= 1
+    assert rrg[0] <= 1e-8
+    # at a tight tolerance both approach K^{-1} f
+    xo12, _, _, _ = H.pcg(f, 1e-12)
+    xg12, it12, rr12, _ = S.solve(d["f"], 1e-12)
+    x = xg12.cpu().numpy()
+    assert np.linalg.norm(x - xo12) <= 1e-10 * np.linalg.norm(xo12)
+    # true residual with the oracle's matrix
+    r = f - K.matvec(x)
+    assert np.linalg.norm(r) <= 1.1e-12 * np.linalg.norm(f)
+    # host-buffer entry point gives the same iterate
+    xh, ith, rrh, _ = S.solve_host(f, 1e-12)
+    assert ith == it12 and np.array_equal(xh, x)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16gp"])
+def test_mixed_precision_reaches_tolerance(A, orc, prec):
+    p = SMALL["beam"]()
+    H, S64, K, f, d = _both(A, orc, p)
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec=prec)
+    x, it, rr, rc = S.solve(d["f"], 1e-8)
+    assert rc == 0
+    xn = x.cpu().numpy()
+    true_rel = np.linalg.norm(f - K.matvec(xn)) / np.linalg.norm(f)
+    assert true_rel <= 1.5e-8
+    xo, ito, _, _ = H.pcg(f, 1e-12)
+    err = np.linalg.norm(xn - xo) / np.linalg.norm(xo)
+    assert err <= 1e-5
+    assert it[0] <= 2 * ito + 10
+
+
+def test_zero_rhs_and_not_converged(A, orc):
+    import torch
+    p = SMALL["cube"]()
+    d = gpu_problem(A, p)
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
+    x, it, rr, rc = S.solve(torch.zeros_like(d["f"]), 1e-8)
+    assert rc == 0 and it[0] == 0 and float(x.abs().max()) == 0.0
+    S2 = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], maxit=3)
+    x, it, rr, rc = S2.solve(d["f"], 1e-8)
+    assert rc == A.AMG_ERR_NOT_CONVERGED and it[0] == 3 and rr[0] > 1e-8
+
+
+def test_nan_rhs_is_breakdown(A):
+    import torch
+    d = gpu_problem(A, SMALL["cube"]())
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
+    b = d["f"].clone()
+    b[5] = float("nan")
+    with pytest.raises(A.AmgError) as e:
+        S.solve(b, 1e-8)
+    assert e.value.code == A.AMG_ERR_BREAKDOWN
+
+
+def test_not_spd_is_reported(A):
+    p = W.cube16(6)
+    p.E = -p.E
+    d = gpu_problem(A, p)
+    with pytest.raises(A.AmgError) as e:
+        A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
+    assert e.value.code == A.AMG_ERR_NOT_SPD
+
+
+def test_invalid_arguments(A):
+    import ctypes as C
+    L = A.lib()
+    h = C.c_void_p()
+    p = A.default_params()
+    assert L.amg_setup(C.byref(p), 0, 0, None, None, None, 0, None, 0, None, C.byref(h)) == A.AMG_ERR_ARG
+    bad = A.default_params(n_tv=40)
+    d = gpu_problem(A, W.cube16(4))
+    with pytest.raises(A.AmgError) as e:
+        A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], params=bad)
+    assert e.value.code == A.AMG_ERR_ARG
