@@ -84,10 +84,11 @@ int or_afsai(const obsr *A, const obsr *Gs, int ksteps, int rho, double eps,
   double *L = (double *)malloc((size_t)mmax * mmax * sizeof(double));
   double *rhs = (double *)malloc((size_t)mmax * sizeof(double));
   int *Q = (int *)malloc((size_t)mmax * sizeof(int));
-  int *mark = (int *)malloc((size_t)n * sizeof(int));
+  long *mark = (long *)malloc((size_t)n * sizeof(long));
   int *cand = (int *)malloc((size_t)n * sizeof(int));
   double *score = (double *)malloc((size_t)n * sizeof(double));
   for (int i = 0; i < n; ++i) mark[i] = -1;
+  long stamp = -1;
   /* output rows, grown as needed */
   size_t cap = (size_t)n * 4 + 16, used = 0;
   int *gcol = (int *)malloc(cap * sizeof(int));
@@ -106,13 +107,14 @@ int or_afsai(const obsr *A, const obsr *Gs, int ksteps, int rho, double eps,
       /* candidates: nodes J < I, outside the pattern, adjacent in A to the
        * pattern or to I */
       int nc = 0;
-      for (int j = 0; j < np; ++j) mark[pat[j]] = I;
+      ++stamp; /* fresh mark for this row and step */
+      for (int j = 0; j < np; ++j) mark[pat[j]] = stamp;
       for (int j = 0; j <= np; ++j) {
         const int K = (j < np) ? pat[j] : I;
         for (int k = A->rowptr[K]; k < A->rowptr[K + 1]; ++k) {
           const int J = A->col[k];
-          if (J < I && mark[J] != I) {
-            mark[J] = I;
+          if (J < I && mark[J] != stamp) {
+            mark[J] = stamp;
             cand[nc++] = J;
           }
         }

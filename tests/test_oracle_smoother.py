@@ -200,3 +200,64 @@ def test_smoother_setup_loop_and_convergence(orc):
     G2, _, om2, lm2, np2 = orc.smoother_setup(A, orc.default_params(3, omega_bar=10.0), 0)
     assert np2 >= 1 and G2.nnzb > G.nnzb
     assert np.abs(np.diag(G2.todense() @ Ad @ G2.todense().T) - 1).max() < 1e-13
+
+
+def _afsai_dense(Ad, b, k, rho, eps, maxg, start=None):
+    """aFSAI straight from its definition on a dense matrix: per node row, k
+    steps; candidates are lower nodes outside the pattern adjacent to the
+    pattern or to the row's node; the rho nodes with the largest summed squared
+    gradient 2 (A gt)_j are added; stop when every row's psi decreased by at
+    most eps of its previous value."""
+    n = Ad.shape[0] // b
+    adj = [set(J for J in range(n) if np.any(Ad[b * I:b * I + b, b * J:b * J + b] != 0)) for I in range(n)]
+    pats = []
+    for I in range(n):
+        pat = sorted(start[I]) if start is not None else []
+
+        def rows(pat):
+            gts, psis = [], []
+            for c in range(b):
+                i = b * I + c
+                Q = [b * J + e for J in pat for e in range(b)] + [b * I + e for e in range(c)]
+                gh, psi = _row_system(Ad, Q, i)
+                gt = np.zeros(Ad.shape[0])
+                gt[Q] = gh
+                gt[i] = 1.0
+                gts.append(gt)
+                psis.append(psi)
+            return gts, np.array(psis)
+
+        gts, psi = rows(pat)
+        for _ in range(k):
+            if len(pat) >= maxg:
+                break
+            cand = sorted(J for K in pat + [I] for J in adj[K] if J < I and J not in pat)
+            cand = sorted(set(cand))
+            sc = {J: sum(np.sum((Ad @ gt)[b * J:b * J + b] ** 2) for gt in gts) for J in cand}
+            order = sorted((J for J in cand if sc[J] > 0), key=lambda J: (-sc[J], J))
+            pick = order[:min(rho, maxg - len(pat))]
+            if not pick:
+                break
+            pat = sorted(pat + pick)
+            old = psi
+            gts, psi = rows(pat)
+            if np.all(old - psi <= eps * old):
+                break
+        pats.append(pat)
+    return pats
+
+
+@pytest.mark.parametrize("b,k,rho,eps", [(3, 3, 2, 0.0), (3, 4, 2, 1e-3), (1, 3, 4, 1e-3), (3, 2, 1, 0.0)])
+def test_multistep_patterns_brute_force(orc, b, k, rho, eps):
+    A = small_problem(orc, n=4, b=b)
+    Ad = A.todense()
+    G = orc.afsai(A, None, k, rho, eps, 24)
+    ref = _afsai_dense(Ad, b, k, rho, eps, 24)
+    for I in range(A.nr):
+        assert list(G.col[G.rowptr[I]:G.rowptr[I + 1] - 1]) == ref[I], I
+    # a continuation call grows from the given pattern
+    G2 = orc.afsai(A, G, 2, rho, eps, 24)
+    start = [list(G.col[G.rowptr[I]:G.rowptr[I + 1] - 1]) for I in range(A.nr)]
+    ref2 = _afsai_dense(Ad, b, 2, rho, eps, 24, start=start)
+    for I in range(A.nr):
+        assert list(G2.col[G2.rowptr[I]:G2.rowptr[I + 1] - 1]) == ref2[I], I
