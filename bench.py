@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the aSP-AMG hot path on one GB300 (or N independent replicas).
+
+One step = the whole path for one synthetic problem already resident in HBM:
+rebuild the hierarchy from K (aFSAI smoother with Lanczos omega, SRQCG test
+space, affinity coarsening, DPLS prolongation, Galerkin products, coarse
+Cholesky) and solve K u = f by PCG with one V(1,1)-cycle per iteration to
+||r|| <= 1e-8 ||f||.  The default workload is the 128 x 32 x 32 cantilever
+beam with lognormal Young's moduli and an FP64 V-cycle; the FP32 V-cycle of the
+same configuration is measured next to it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded, scaled-down sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 residual & V-cycles/s (FP64 vs mixed/batched), SpMV %HBM peak"
+UNIT = "solutions/s"
+RTOL = 1e-8
+SAMPLE_DIMS = (48, 12, 12)   # oracle sample: same recipe, scaled down
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                    "sw_power_cap"), f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def gpu_problem(A, p):
+    d = A.fe_assemble(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.nu, p.E, p.clamp_axis)
+    n = d["nfree"]
+    d["V0"] = A.fe_rbm(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.clamp_axis, n)
+    if p.load == "end_shear":
+        d["f"] = A.fe_load(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.clamp_axis, "end_shear",
+                           g=[p.shear_total], nfree=n)
+    elif p.load == "top_pressure":
+        d["f"] = A.fe_load(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.clamp_axis, "top_pressure",
+                           p=p.pressure, nfree=n)
+    else:
+        d["f"] = A.fe_load(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.clamp_axis, "body", g=p.body, nfree=n)
+    return d
+
+
+def oracle_sample(reps=1):
+    """Oracle set-up + PCG to 1e-8 on the scaled-down beam; seconds per
+    solution scaled by the dof count to the full workload."""
+    import oracle as orc
+    import workloads as W
+    p = W.beam(*SAMPLE_DIMS)
+    K, nm = orc.assemble(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.nu, p.E, p.clamp_axis)
+    V0 = orc.rbm(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, nm)
+    f = orc.load_end_shear(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.shear_total, nm)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        H = orc.Hierarchy(K, V0)
+        x, it, rr, rc = H.pcg(f, RTOL)
+        ts.append(time.perf_counter() - t0)
+        del H
+    full = W.beam()
+    scale = (3.0 * full.free_nodes()) / (3.0 * p.free_nodes())
+    sec = min(ts) * scale
+    sample = ("oracle set-up + PCG to 1e-8 on beam %dx%dx%d (%d dofs, same recipe), %.2f s, "
+              "scaled by dofs x%.2f to 128x32x32" % (SAMPLE_DIMS + (3 * p.free_nodes(), min(ts), scale)))
+    return 1.0 / sec, sample, it
+
+
+def run_reference(args):
+    ws, rank, local = dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        v, sample, it = oracle_sample(1)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(sum(vals) / len(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "cantilever beam 128x32x32 Q1 hex, lognormal E, "
+                                                       "FP64, rtol 1e-8 (oracle on a scaled sample)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": wall}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1902_01715_gb300 as A
+    import workloads as W
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as td
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    A.build()
+    A.lib()
+    p = W.beam()
+    d = gpu_problem(A, p)
+    n3 = 3 * d["nfree"]
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec=args.prec)
+    vals, f = d["vals"], d["f"]
+
+    def step(solver):
+        solver.update_values(vals)
+        x, it, rr, rc = solver.solve(f, RTOL)
+        if rc != 0:
+            raise RuntimeError("solve did not converge: %s" % rc)
+        return x, it[0]
+
+    for _ in range(args.warmup):
+        step(S)
+    torch.cuda.synchronize()
+    barrier(ws)
+    l0 = A.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st_setup, st_solve, its = [], [], []
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            x, it = step(S)
+            s = S.stats()
+            st_setup.append(s["T_p"])
+            st_solve.append(s["T_s"])
+            its.append(it)
+        e1.record()
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = A.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, ws)
+    value = ws * 1e3 / ms
+    stats = S.stats()
+    clocks = clk.summary()
+
+    # dominant solve kernel: the fine-level BSR3 product of the CG operator
+    spmv_ms, spmv_bytes = S.bench_spmv(0, "A", a64=True, reps=50)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    roofline = {"kernel": "k_bsrmv<32,double,double> (level-0 K, FP64)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+                "frac": achieved / (hbm if hbm else 6800.0), "traffic": None,
+                "peak_source": "measured" if hbm else "fallback", "ms_per_launch": spmv_ms,
+                "bytes_per_launch": spmv_bytes}
+    # FP32 V-cycle of the same configuration (not part of value)
+    fp32 = None
+    if args.prec == "fp64" and not args.no_compare:
+        S32 = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec="fp32")
+        for _ in range(2):
+            step(S32)
+        torch.cuda.synchronize()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record()
+        for _ in range(args.steps):
+            x32, it32 = step(S32)
+        e3.record()
+        torch.cuda.synchronize()
+        s32 = S32.stats()
+        err = float(torch.linalg.norm(x32 - x) / torch.linalg.norm(x))
+        fp32 = {"ms_per_step": e2.elapsed_time(e3) / args.steps, "n_it": it32,
+                "solve_ms": s32["T_s"] * 1e3, "vcycles_per_s": it32 / s32["T_s"],
+                "rel_diff_vs_fp64_solution": err}
+        S32.close()
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        vh = torch.empty(vals.shape, dtype=torch.float64, pin_memory=True)
+        vh.copy_(vals)
+        fh = torch.empty(f.shape, dtype=torch.float64, pin_memory=True)
+        fh.copy_(f)
+        xh = torch.empty(f.shape, dtype=torch.float64, pin_memory=True)
+        import ctypes as C
+        L = A.lib()
+        iters = (C.c_int * 1)()
+        rel = (C.c_double * 1)()
+
+        def host_step():
+            A.check(L.amg_update_values(S._h, C.c_void_p(vh.data_ptr()), A.AMG_MEM_HOST))
+            rc = L.amg_solve(S._h, 1, C.c_void_p(fh.data_ptr()), C.c_void_p(xh.data_ptr()), RTOL,
+                             iters, rel, A.AMG_MEM_HOST)
+            A.check(rc)
+
+        host_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        torch.cuda.synchronize()
+        t = max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
+        e2e = {"value": ws / t, "unit": UNIT, "h2d_bytes_per_step": int(vh.numel() * 8 + fh.numel() * 8),
+               "d2h_bytes_per_step": int(xh.numel() * 8), "ms_per_step": t * 1e3}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, sample, it_o = oracle_sample(2)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": "cantilever beam 128x32x32 Q1 hex (%d dofs), x=0 clamped, tip shear, "
+                               "lognormal E (mu 0, sigma 1), nu 0.3; set-up + PCG to 1e-8, %s V-cycle"
+                               % (n3, args.prec.upper()),
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (fine K alone %.0f MB)" % (vals.numel() * 8 / 1e6)},
+        "solve": {"n_it": int(round(sum(its) / len(its))), "setup_ms": 1e3 * sum(st_setup) / len(st_setup),
+                  "solve_ms": 1e3 * sum(st_solve) / len(st_solve),
+                  "vcycles_per_s": sum(its) / sum(st_solve),
+                  "levels": stats["nlev"], "C_gd": stats["C_gd"], "C_op": stats["C_op"],
+                  "C_fs": stats["C_fs"],
+                  "setup_phases_ms": {k: 1e3 * stats[k] for k in ("T_sm", "T_ts", "T_cs", "T_pl", "T_rap")}},
+        "fp32_vcycle": fp32,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16gp"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

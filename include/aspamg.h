@@ -153,6 +153,17 @@ int amg_level_cf(amg_handle h, int lev, int *cf);          /* host, 1 = C */
 int amg_level_testspace(amg_handle h, int lev, double *V); /* host, n x n_tv */
 /* One V-cycle z = B(y) in the handle's precision (device vectors). */
 int amg_vcycle(amg_handle h, const double *y, double *z);
+/* Time the solve-phase sparse product of level `lev` (which = 0 A, 1 G,
+ * 2 G^T, 3 P, 4 R; storage of the handle's V-cycle precision, FP64 for the
+ * level-0 A of the CG recurrence when prec_a64 != 0) over `reps` back-to-back
+ * launches with CUDA events on the handle's stream.  *ms = average launch
+ * time, *bytes = algorithmic bytes of one launch (values, column indices and
+ * row pointers once, x and y once each). */
+int amg_bench_spmv(amg_handle h, int lev, int which, int prec_a64, int reps,
+                   double *ms, double *bytes);
+/* Kernel launches the library has issued in this process (graph replays
+ * count each kernel node). */
+long long amg_launch_count(void);
 
 /* ---- structured Q1-hex elasticity problems (problem generation) ----
  * Mesh: nodes (ix,iy,iz) with global id ix + (nx+1)(iy + (ny+1) iz) at

@@ -27,6 +27,7 @@ EXPORTS = [
     "amg_elem_grad", "amg_get_stats", "amg_free", "amg_strerror", "amg_last_error",
     "amg_level_info", "amg_level_matrix", "amg_level_cf", "amg_level_testspace", "amg_vcycle",
     "amg_fe_size", "amg_fe_assemble", "amg_fe_load", "amg_fe_rbm", "amg_fe_conn",
+    "amg_bench_spmv", "amg_launch_count",
 ]
 
 
@@ -99,6 +100,8 @@ def lib(path: str | None = None):
                                                                      _vp]),
         "amg_fe_rbm": (C.c_int, [C.c_int] * 3 + [C.c_double] * 3 + [C.c_int, _vp, _vp]),
         "amg_fe_conn": (C.c_int, [C.c_int] * 4 + [_vp, _vp]),
+        "amg_bench_spmv": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp]),
+        "amg_launch_count": (C.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -106,6 +109,11 @@ def lib(path: str | None = None):
         f.argtypes = args
     _lib = L
     return L
+
+
+def launch_count() -> int:
+    """Kernels this process has launched through the library."""
+    return int(lib().amg_launch_count())
 
 
 def check(rc, where="", allow=()):
@@ -274,6 +282,15 @@ class Solver:
                              rtol, iters, rel, AMG_MEM_HOST)
         check(rc, "amg_solve", allow=(AMG_ERR_NOT_CONVERGED,))
         return X, list(iters), list(rel), rc
+
+    def bench_spmv(self, level=0, which="A", a64=True, reps=20):
+        """(ms per launch, algorithmic bytes per launch) of a solve-phase
+        sparse product timed with CUDA events on the handle's stream."""
+        code = {"A": 0, "G": 1, "GT": 2, "P": 3, "R": 4}[which]
+        ms, by = C.c_double(), C.c_double()
+        check(lib().amg_bench_spmv(self._h, level, code, int(a64), reps, C.byref(ms), C.byref(by)),
+              "amg_bench_spmv")
+        return ms.value, by.value
 
     def vcycle(self, y):
         torch = self._torch

@@ -33,6 +33,11 @@ void set_error(const char *fmt, ...);
 
 #define AMG_LAUNCH_CHECK() AMG_CU(cudaGetLastError())
 
+// Every kernel launch site is prefixed with AMG_KCOUNT (a comma expression),
+// so the library can report how many kernels it issued.
+void count_launches(long long n);
+#define AMG_KCOUNT ::amg::count_launches(1),
+
 // Owning device buffer (cudaMalloc / cudaFree).
 template <class T>
 struct DBuf {
@@ -148,6 +153,8 @@ struct Handle {
   int graph_k = -1;
   int graph_prec = -1;
   bool own_stream = false;  // created because the caller passed the legacy stream
+  long long graph_nodes = 0;
+  int *pinned = nullptr;    // host flag for polling the PCG state
   ~Handle();
 };
 
@@ -160,6 +167,8 @@ void free_hierarchy(Handle *h);
 int prepare_solve(Handle *h);
 int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres);
 int vcycle_apply(Handle *h, const double *y, double *z);
+int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes);
+long long launch_count();
 
 // ---- deterministic set-up kernels (det.cu) ----
 namespace det {

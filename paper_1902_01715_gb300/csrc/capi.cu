@@ -219,3 +219,12 @@ extern "C" int amg_vcycle(amg_handle hh, const double *y, double *z) {
   if (!h || !y || !z) return AMG_ERR_ARG;
   return vcycle_apply(h, y, z);
 }
+
+extern "C" int amg_bench_spmv(amg_handle hh, int lev, int which, int prec_a64, int reps, double *ms,
+                              double *bytes) {
+  Handle *h = (Handle *)hh;
+  if (!h || !ms || !bytes) return AMG_ERR_ARG;
+  return bench_spmv(h, lev, which, prec_a64, reps, ms, bytes);
+}
+
+extern "C" long long amg_launch_count(void) { return launch_count(); }

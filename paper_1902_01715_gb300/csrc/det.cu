@@ -55,7 +55,7 @@ __global__ void k_spmv(int nr, const int *__restrict__ rowptr, const int *__rest
 
 int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
   if (A.nr == 0) return AMG_OK;
-  k_spmv<<<nblk(3L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+  AMG_KCOUNT k_spmv<<<nblk(3L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -96,10 +96,10 @@ __global__ void k_dot_final(int nd, int nchunks, const double *__restrict__ part
 static int dots(int n, int nd, const DotArgs &a, double *out, double *part, cudaStream_t s) {
   const int nchunks = (n + CHUNK - 1) / CHUNK;
   if (nchunks > 0) {
-    k_dot_partials<<<nblk((long)nchunks * nd * 32, 256), 256, 0, s>>>(n, nd, a, part, nchunks);
+    AMG_KCOUNT k_dot_partials<<<nblk((long)nchunks * nd * 32, 256), 256, 0, s>>>(n, nd, a, part, nchunks);
     AMG_LAUNCH_CHECK();
   }
-  k_dot_final<<<1, 32, 0, s>>>(nd, nchunks, part, out);
+  AMG_KCOUNT k_dot_final<<<1, 32, 0, s>>>(nd, nchunks, part, out);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -180,7 +180,7 @@ __global__ void k_uniform(long n, int col0, int ncols, uint64_t seed, double *__
 
 int uniform_fill(double *v, int n, int col0, int ncols, uint64_t seed, cudaStream_t s) {
   if (ncols <= 0 || n <= 0) return AMG_OK;
-  k_uniform<<<nblk((long)n * ncols, 256), 256, 0, s>>>(n, col0, ncols, seed, v, n);
+  AMG_KCOUNT k_uniform<<<nblk((long)n * ncols, 256), 256, 0, s>>>(n, col0, ncols, seed, v, n);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -196,7 +196,7 @@ __global__ void k_gather_rows(const int *__restrict__ src, int nout, int nin, in
 
 int gather_rows(const int *src_idx, int nout, int nin, int t, const double *Vin, double *Vout, cudaStream_t s) {
   if (nout <= 0) return AMG_OK;
-  k_gather_rows<<<nblk((long)nout * t, 256), 256, 0, s>>>(src_idx, nout, nin, t, Vin, Vout);
+  AMG_KCOUNT k_gather_rows<<<nblk((long)nout * t, 256), 256, 0, s>>>(src_idx, nout, nin, t, Vin, Vout);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -212,11 +212,11 @@ int mgs(int n, int t, double *V, cudaStream_t s) {
     for (int i = 0; i < j; ++i) {
       const double *vi = V + (size_t)i * n;
       AMG_TRY(dot(n, vi, vj, sc.p, part.p, s));
-      k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p, vi, nullptr);
+      AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p, vi, nullptr);
       AMG_LAUNCH_CHECK();
     }
     AMG_TRY(dot(n, vj, vj, sc.p, part.p, s));
-    k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p);
+    AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p);
     AMG_LAUNCH_CHECK();
   }
   AMG_CU(cudaStreamSynchronize(s));
@@ -511,7 +511,7 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   AMG_TRY(is.alloc((size_t)nw * K.iper));
   K.dscr = ds.p;
   K.iscr = is.p;
-  k_fsai<<<(int)nblocks, threads, 0, s>>>(K);
+  AMG_KCOUNT k_fsai<<<(int)nblocks, threads, 0, s>>>(K);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -576,31 +576,31 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
   AMG_TRY(sc.alloc(160));
   AMG_TRY(part.alloc((size_t)(n + CHUNK - 1) / CHUNK + 1));
   AMG_TRY(sc.zero(s));
-  k_set_neg<<<1, 1, 0, s>>>(sc.p + 128);
+  AMG_KCOUNT k_set_neg<<<1, 1, 0, s>>>(sc.p + 128);
   // start vector: counters (1<<62) | level<<40 | i of the generator
-  k_lanczos_start<<<nblk(n, 256), 256, 0, s>>>(n, seed, (1ull << 62) | ((uint64_t)level << 40), Vs.p);
+  AMG_KCOUNT k_lanczos_start<<<nblk(n, 256), 256, 0, s>>>(n, seed, (1ull << 62) | ((uint64_t)level << 40), Vs.p);
   AMG_LAUNCH_CHECK();
   AMG_TRY(dot(n, Vs.p, Vs.p, sc.p + 129, part.p, s));
-  k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, Vs.p, sc.p + 129);
+  AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, Vs.p, sc.p + 129);
   for (int j = 0; j < m; ++j) {
     double *v = Vs.p + (size_t)j * n;
     AMG_TRY(spmv(GT, v, t1.p, s));
     AMG_TRY(spmv(A, t1.p, t2.p, s));
     AMG_TRY(spmv(G, t2.p, w.p, s));
     AMG_TRY(dot(n, w.p, v, sc.p + j, part.p, s));
-    k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + j, v, nullptr);
-    if (j > 0) k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 64 + j - 1, v - n, nullptr);
+    AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + j, v, nullptr);
+    if (j > 0) AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 64 + j - 1, v - n, nullptr);
     for (int k = 0; k <= j; ++k) {
       const double *vk = Vs.p + (size_t)k * n;
       AMG_TRY(dot(n, w.p, vk, sc.p + 130, part.p, s));
-      k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 130, vk, nullptr);
+      AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 130, vk, nullptr);
     }
     AMG_TRY(dot(n, w.p, w.p, sc.p + 129, part.p, s));
-    k_lanczos_beta<<<1, 1, 0, s>>>(j, m, sc.p);
-    if (j < m - 1) k_div<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 64 + j);
+    AMG_KCOUNT k_lanczos_beta<<<1, 1, 0, s>>>(j, m, sc.p);
+    if (j < m - 1) AMG_KCOUNT k_div<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 64 + j);
     AMG_LAUNCH_CHECK();
   }
-  k_lanczos_bisect<<<1, 1, 0, s>>>(m, sc.p, safety, d_out);
+  AMG_KCOUNT k_lanczos_bisect<<<1, 1, 0, s>>>(m, sc.p, safety, d_out);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -840,7 +840,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   for (int i = 0; i < t; ++i) {
     const double *v = V0 + (size_t)i * n;
     AMG_TRY(apply_s(A, G, GT, v, SZ.p, t1.p, t2.p, s));
-    k_srq_z0<<<nb, 256, 0, s>>>(n, Z.p + (size_t)i * n, v, SZ.p);
+    AMG_KCOUNT k_srq_z0<<<nb, 256, 0, s>>>(n, Z.p + (size_t)i * n, v, SZ.p);
     AMG_LAUNCH_CHECK();
   }
   AMG_TRY(mgs(n, t, Z.p, s));
@@ -848,23 +848,23 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     double *z = Z.p + (size_t)i * n, *p = P.p + (size_t)i * n;
     AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
     AMG_TRY(dot(n, z, SZ.p, sc.p + S_TMP, part.p, s));
-    k_srq_p0<<<nb, 256, 0, s>>>(n, p, z, SZ.p, sc.p + S_TMP);
+    AMG_KCOUNT k_srq_p0<<<nb, 256, 0, s>>>(n, p, z, SZ.p, sc.p + S_TMP);
     AMG_LAUNCH_CHECK();
   }
-  k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
+  AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
   for (int it = 1; it <= kmax; ++it) {
     if (k_ritz > 0 && it % k_ritz == 0) {
       for (int j = 0; j < t; ++j)
         AMG_TRY(apply_s(A, G, GT, Z.p + (size_t)j * n, SZall.p + (size_t)j * n, t1.p, t2.p, s));
       const int npair = t * (t + 1) / 2;
       if (nchunks > 0) {
-        k_gram_partials<<<nblk((long)nchunks * npair * 2 * 32, 256), 256, 0, s>>>(n, t, Z.p, SZall.p, part.p, nchunks);
+        AMG_KCOUNT k_gram_partials<<<nblk((long)nchunks * npair * 2 * 32, 256), 256, 0, s>>>(n, t, Z.p, SZall.p, part.p, nchunks);
         AMG_LAUNCH_CHECK();
       }
-      k_gram_final<<<nblk(2 * npair, 64), 64, 0, s>>>(t, nchunks, part.p, H.p, Mg.p);
-      k_gen_eig<<<1, 1, 0, s>>>(t, H.p, Mg.p, U.p, lam.p, wk.p, status);
-      k_rotate<<<nb, 256, 0, s>>>(n, t, Z.p, U.p);
-      k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
+      AMG_KCOUNT k_gram_final<<<nblk(2 * npair, 64), 64, 0, s>>>(t, nchunks, part.p, H.p, Mg.p);
+      AMG_KCOUNT k_gen_eig<<<1, 1, 0, s>>>(t, H.p, Mg.p, U.p, lam.p, wk.p, status);
+      AMG_KCOUNT k_rotate<<<nb, 256, 0, s>>>(n, t, Z.p, U.p);
+      AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
       AMG_LAUNCH_CHECK();
     }
     for (int i = 0; i < t; ++i) {
@@ -878,20 +878,20 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
       a5.x[3] = p; a5.y[3] = p;
       a5.x[4] = z; a5.y[4] = SZ.p;
       AMG_TRY(dots(n, 5, a5, sc.p + S_A, part.p, s));
-      k_srq_alpha<<<1, 1, 0, s>>>(sc.p, i, skip.p);
-      k_srq_zupd<<<nb, 256, 0, s>>>(n, z, p, sc.p, skip.p);
+      AMG_KCOUNT k_srq_alpha<<<1, 1, 0, s>>>(sc.p, i, skip.p);
+      AMG_KCOUNT k_srq_zupd<<<nb, 256, 0, s>>>(n, z, p, sc.p, skip.p);
       AMG_LAUNCH_CHECK();
       AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
       DotArgs a2{};
       a2.x[0] = z; a2.y[0] = z;
       a2.x[1] = z; a2.y[1] = SZ.p;
       AMG_TRY(dots(n, 2, a2, sc.p + S_FN, part.p, s));
-      k_srq_q<<<1, 1, 0, s>>>(sc.p);
-      k_srq_grad<<<nb, 256, 0, s>>>(n, Gv.p, SZ.p, z, sc.p, skip.p);
+      AMG_KCOUNT k_srq_q<<<1, 1, 0, s>>>(sc.p);
+      AMG_KCOUNT k_srq_grad<<<nb, 256, 0, s>>>(n, Gv.p, SZ.p, z, sc.p, skip.p);
       AMG_LAUNCH_CHECK();
       AMG_TRY(dot(n, Gv.p, SP.p, sc.p + S_GSP, part.p, s));
-      k_srq_beta<<<1, 1, 0, s>>>(sc.p);
-      k_srq_pupd<<<nb, 256, 0, s>>>(n, p, Gv.p, sc.p, i, skip.p);
+      AMG_KCOUNT k_srq_beta<<<1, 1, 0, s>>>(sc.p);
+      AMG_KCOUNT k_srq_pupd<<<nb, 256, 0, s>>>(n, p, Gv.p, sc.p, i, skip.p);
       AMG_LAUNCH_CHECK();
     }
   }
@@ -978,9 +978,9 @@ int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char
   AMG_TRY(soc.alloc(A.nnzb));
   AMG_TRY(kept.alloc(A.nnzb));
   const int nb = nblk(A.nr, 128);
-  k_soc_nrm<<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
-  k_soc_filter<<<nb, 128, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, theta, soc.p, kept.p);
-  k_strong<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, kept.p, strong);
+  AMG_KCOUNT k_soc_nrm<<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
+  AMG_KCOUNT k_soc_filter<<<nb, 128, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, theta, soc.p, kept.p);
+  AMG_KCOUNT k_strong<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, kept.p, strong);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -1146,7 +1146,7 @@ int dpls(const DevBsr &A, const unsigned char *strong, const int *cf, const int 
   AMG_TRY(Vt.alloc((size_t)total * t * 3));
   AMG_TRY(taken.alloc(total));
   const int cap = n_max < t / 3 ? n_max : t / 3;
-  k_dpls<<<nblk(nf, 64), 64, 0, s>>>(nf, fnodes, 3L * A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p, n_max,
+  AMG_KCOUNT k_dpls<<<nblk(nf, 64), 64, 0, s>>>(nf, fnodes, 3L * A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p, n_max,
                                      kappa_p, cap > 0 ? cap : 1, out_cnt, out_col, out_val);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
@@ -1192,7 +1192,7 @@ __global__ void k_spgemm(int nr, const int *__restrict__ xr, const int *__restri
 
 int spgemm_numeric(const DevBsr &X, const DevBsr &Y, DevBsr &Z, cudaStream_t s) {
   if (Z.nnzb == 0) return AMG_OK;
-  k_spgemm<<<nblk(Z.nnzb, 128), 128, 0, s>>>(Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
+  AMG_KCOUNT k_spgemm<<<nblk(Z.nnzb, 128), 128, 0, s>>>(Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
                                             Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
   AMG_LAUNCH_CHECK();
   return AMG_OK;

@@ -282,8 +282,8 @@ extern "C" int amg_fe_assemble(int nx, int ny, int nz, double hx, double hy, dou
   AMG_CU(cudaMemcpyAsync(f2g.p, m.f2g.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s));
   AMG_CU(cudaMemcpyAsync(rowptr, m.rowptr.data(), (nf + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   AMG_CU(cudaMemcpyAsync(colind, m.col.data(), nnzb * sizeof(int), cudaMemcpyHostToDevice, s));
-  k_ke0<<<3, 192, 0, s>>>(nu, hx, hy, hz, Ke0);
-  k_assemble<<<nblk(nnzb, 128), 128, 0, s>>>(nf, nnzb, nx, ny, nz, rowptr, colind, f2g.p, E, Ke0, vals);
+  AMG_KCOUNT k_ke0<<<3, 192, 0, s>>>(nu, hx, hy, hz, Ke0);
+  AMG_KCOUNT k_assemble<<<nblk(nnzb, 128), 128, 0, s>>>(nf, nnzb, nx, ny, nz, rowptr, colind, f2g.p, E, Ke0, vals);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -303,7 +303,7 @@ extern "C" int amg_fe_load(int nx, int ny, int nz, double hx, double hy, double 
   AMG_TRY(f2g.alloc(nf));
   AMG_CU(cudaMemcpyAsync(f2g.p, m.f2g.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s));
   const double g0 = g ? g[0] : 0.0, g1 = (g && kind == 0) ? g[1] : 0.0, g2 = (g && kind == 0) ? g[2] : 0.0;
-  k_load<<<nblk(nf, 128), 128, 0, s>>>(nf, nx, ny, nz, hx, hy, hz, kind, g0, g1, g2, p, f2g.p, f);
+  AMG_KCOUNT k_load<<<nblk(nf, 128), 128, 0, s>>>(nf, nx, ny, nz, hx, hy, hz, kind, g0, g1, g2, p, f2g.p, f);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -319,7 +319,7 @@ extern "C" int amg_fe_rbm(int nx, int ny, int nz, double hx, double hy, double h
   DBuf<int> f2g;
   AMG_TRY(f2g.alloc(nf));
   AMG_CU(cudaMemcpyAsync(f2g.p, m.f2g.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s));
-  k_rbm<<<nblk(nf, 128), 128, 0, s>>>(nf, nx, ny, nz, hx, hy, hz, f2g.p, V);
+  AMG_KCOUNT k_rbm<<<nblk(nf, 128), 128, 0, s>>>(nf, nx, ny, nz, hx, hy, hz, f2g.p, V);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -334,7 +334,7 @@ extern "C" int amg_fe_conn(int nx, int ny, int nz, int clamp, int *conn, void *s
   AMG_TRY(nm.alloc(m.node_map.size()));
   AMG_CU(cudaMemcpyAsync(nm.p, m.node_map.data(), m.node_map.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   const long ne = (long)nx * ny * nz;
-  k_conn<<<nblk(ne, 128), 128, 0, s>>>(ne, nx, ny, nz, nm.p, conn);
+  AMG_KCOUNT k_conn<<<nblk(ne, 128), 128, 0, s>>>(ne, nx, ny, nz, nm.p, conn);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -348,7 +348,7 @@ extern "C" int amg_elem_grad(int ne, const int *conn, const double *Ke0, const d
   }
   if (ne == 0) return AMG_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  k_elem_grad<<<nblk(ne, 128), 128, 0, s>>>(ne, conn, Ke0, dEdp, U, Lam, grad);
+  AMG_KCOUNT k_elem_grad<<<nblk(ne, 128), 128, 0, s>>>(ne, conn, Ke0, dEdp, U, Lam, grad);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;

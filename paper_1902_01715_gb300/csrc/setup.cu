@@ -6,6 +6,7 @@
 // transposition, the maximal independent set, DPLS candidate sets and the
 // symbolic Galerkin pattern) on the host.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdarg>
 #include <cstring>
@@ -24,6 +25,10 @@ void set_error(const char *fmt, ...) {
 }
 
 const char *last_error() { return g_err; }
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
@@ -148,7 +153,7 @@ int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s) {
     DBuf<int> dperm;
     AMG_TRY(dperm.alloc(nnzb));
     AMG_CU(cudaMemcpyAsync(dperm.p, perm.data(), nnzb * sizeof(int), cudaMemcpyHostToDevice, s));
-    k_transpose_vals<<<nblk(9L * nnzb, 256), 256, 0, s>>>(nnzb, dperm.p, A.val.p, T.val.p);
+    AMG_KCOUNT k_transpose_vals<<<nblk(9L * nnzb, 256), 256, 0, s>>>(nnzb, dperm.p, A.val.p, T.val.p);
     AMG_LAUNCH_CHECK();
     AMG_CU(cudaStreamSynchronize(s));
   }
@@ -300,7 +305,7 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
   G.h_rowptr = std::move(rp);
   G.h_col = std::move(cl);
   AMG_TRY(G.upload_pattern(s));
-  k_compact_vals<<<nblk((long)n * (maxg + 1) * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
+  AMG_KCOUNT k_compact_vals<<<nblk((long)n * (maxg + 1) * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -387,7 +392,7 @@ static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong
   DBuf<int> d_fidx;
   AMG_TRY(d_fidx.alloc(n));
   AMG_CU(cudaMemcpyAsync(d_fidx.p, fidx.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
-  k_p_vals<<<nblk((long)n * cap * 9, 256), 256, 0, s>>>(n, L.P.rowptr.p, d_fidx.p, cap, d_val.p, L.P.val.p);
+  AMG_KCOUNT k_p_vals<<<nblk((long)n * cap * 9, 256), 256, 0, s>>>(n, L.P.rowptr.p, d_fidx.p, cap, d_val.p, L.P.val.p);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -411,10 +416,10 @@ static int coarse_factor(Handle *h, Level &L) {
   AMG_TRY(h->LinvT.alloc((size_t)m * m));
   AMG_TRY(h->Linv.zero(s));
   if (L.n > 0) {
-    k_to_dense<<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D.p);
-    k_dense_chol<<<1, 1024, 0, s>>>(m, D.p, st.p);
-    k_tri_inv<<<nblk(m, 128), 128, 0, s>>>(m, D.p, h->Linv.p);
-    k_dense_transpose<<<nblk((long)m * m, 256), 256, 0, s>>>(m, h->Linv.p, h->LinvT.p);
+    AMG_KCOUNT k_to_dense<<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D.p);
+    AMG_KCOUNT k_dense_chol<<<1, 1024, 0, s>>>(m, D.p, st.p);
+    AMG_KCOUNT k_tri_inv<<<nblk(m, 128), 128, 0, s>>>(m, D.p, h->Linv.p);
+    AMG_KCOUNT k_dense_transpose<<<nblk((long)m * m, 256), 256, 0, s>>>(m, h->Linv.p, h->LinvT.p);
     AMG_LAUNCH_CHECK();
   }
   int hs = 0;

@@ -77,11 +77,11 @@ static void launch_lpr(int ep, const SolveMat &M, const TM *v, const TX *x, TX *
   const int nb = nblk((long)M.nr * LPR, 256);
   if (nb == 0) return;
   switch (ep) {
-    case EP_SET: k_bsrmv<LPR, TM, TX, EP_SET><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-    case EP_SCALE: k_bsrmv<LPR, TM, TX, EP_SCALE><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-    case EP_RESID: k_bsrmv<LPR, TM, TX, EP_RESID><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-    case EP_SADD: k_bsrmv<LPR, TM, TX, EP_SADD><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-    default: k_bsrmv<LPR, TM, TX, EP_ACC><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    case EP_SET: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_SET><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    case EP_SCALE: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_SCALE><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    case EP_RESID: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_RESID><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    case EP_SADD: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_SADD><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
+    default: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_ACC><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
   }
 }
 
@@ -134,15 +134,15 @@ static int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool 
   const int nb = nblk(n9, 256);
   if (f64) {
     AMG_TRY(M.v64.alloc(n9));
-    if (nb) k_entry_major<double><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v64.p);
+    if (nb) AMG_KCOUNT k_entry_major<double><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v64.p);
   }
   if (f32) {
     AMG_TRY(M.v32.alloc(n9));
-    if (nb) k_entry_major<float><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v32.p);
+    if (nb) AMG_KCOUNT k_entry_major<float><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v32.p);
   }
   if (b16) {
     AMG_TRY(M.v16.alloc(n9));
-    if (nb) k_entry_major<__nv_bfloat16><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v16.p);
+    if (nb) AMG_KCOUNT k_entry_major<__nv_bfloat16><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v16.p);
   }
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -259,8 +259,8 @@ static void vcycle_level(Handle *h, int k, const TX *y, TX *z, const int *done, 
   if (k == h->nlev - 1) {
     const int m = h->nL;
     if (m == 0) return;
-    k_trmv_lower<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->Linv.p, y, ctmp, done);
-    k_trmv_upper<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->LinvT.p, ctmp, z, done);
+    AMG_KCOUNT k_trmv_lower<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->Linv.p, y, ctmp, done);
+    AMG_KCOUNT k_trmv_upper<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->LinvT.p, ctmp, z, done);
     return;
   }
   Level &C = *h->lev[k + 1];
@@ -478,6 +478,7 @@ static int ensure_pcg(Handle *h) {
   AMG_TRY(h->scal.alloc(P_NSC + 8));
   AMG_TRY(h->flags.alloc(F_NFL + 4));
   AMG_TRY(h->red.alloc(4 * RED_BLOCKS + 16 + 3 * (size_t)(h->nL > 0 ? h->nL : 1)));
+  if (!h->pinned) AMG_CU(cudaMallocHost((void **)&h->pinned, 4 * sizeof(int)));
   h->kcap = 1;
   return AMG_OK;
 }
@@ -498,20 +499,20 @@ static void pcg_iteration(Handle *h, bool mixed) {
   double *sc = h->scal.p;
   const int *done = fl + F_DONE;
   bsrmv<double, double>(EP_SET, L0.sA, L0.sA.v64.p, h->p.p, h->q.p, nullptr, 0.0, done, s);
-  k_pcg_pq<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->q.p, sc, fl, part);
+  AMG_KCOUNT k_pcg_pq<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->q.p, sc, fl, part);
   if (mixed) {
-    k_pcg_xr<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, low_r<TX>(h), sc, fl, part);
+    AMG_KCOUNT k_pcg_xr<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, low_r<TX>(h), sc, fl, part);
     vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), done, ctmp);
-    k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, low_z<TX>(h), h->zold.p, 1, sc, fl, part,
+    AMG_KCOUNT k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, low_z<TX>(h), h->zold.p, 1, sc, fl, part,
                                                      part2);
-    k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 1, sc, fl);
+    AMG_KCOUNT k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 1, sc, fl);
   } else {
-    k_pcg_xr<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, (double *)nullptr, sc, fl,
+    AMG_KCOUNT k_pcg_xr<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, (double *)nullptr, sc, fl,
                                                          part);
     vcycle_level<double>(h, 0, h->r.p, h->z.p, done, ctmp);
-    k_pcg_rz<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, (const double *)nullptr, h->zold.p, 0, sc,
+    AMG_KCOUNT k_pcg_rz<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, (const double *)nullptr, h->zold.p, 0, sc,
                                                          fl, part, part2);
-    k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 0, sc, fl);
+    AMG_KCOUNT k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 0, sc, fl);
   }
 }
 
@@ -522,8 +523,8 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
   double *part = h->red.p, *ctmp = h->red.p + 4 * RED_BLOCKS + 16;
   int *fl = h->flags.p;
   double *sc = h->scal.p;
-  k_set_flags<<<1, 1, 0, s>>>(fl, h->prm.maxit);
-  k_pcg_start<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, b, h->x.p, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr, rtol,
+  AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(fl, h->prm.maxit);
+  AMG_KCOUNT k_pcg_start<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, b, h->x.p, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr, rtol,
                                                       sc, fl, part);
   if (mixed) {
     vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), fl + F_DONE, ctmp);
@@ -531,9 +532,9 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
     vcycle_level<double>(h, 0, h->r.p, h->z.p, fl + F_DONE, ctmp);
   }
   // rz = r.z (beta unused)
-  k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
+  AMG_KCOUNT k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
                                                    h->zold.p, 0, sc, fl, part, part + 2 * RED_BLOCKS);
-  k_pcg_first_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, fl);
+  AMG_KCOUNT k_pcg_first_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, fl);
   AMG_LAUNCH_CHECK();
   const int key = mixed ? 1 : 0;
   if (!h->graph_exec || h->graph_k != 1 || h->graph_prec != key) {
@@ -542,9 +543,13 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
       h->graph_exec = nullptr;
     }
     cudaGraph_t g;
+    const long long before = launch_count();
     AMG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     pcg_iteration<TX>(h, mixed);
     cudaError_t ce = cudaStreamEndCapture(s, &g);
+    // captured launches run only when the graph is replayed
+    h->graph_nodes = launch_count() - before;
+    count_launches(-h->graph_nodes);
     if (ce != cudaSuccess) {
       set_error("graph capture failed: %s", cudaGetErrorString(ce));
       return AMG_ERR_CUDA;
@@ -555,8 +560,7 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
     h->graph_prec = key;
   }
   int hflags[F_NFL];
-  int *pinned = nullptr;
-  AMG_CU(cudaMallocHost((void **)&pinned, 4 * sizeof(int)));
+  int *pinned = h->pinned;
   int rc = AMG_OK;
   // replay; the device flag makes finished iterations no-ops, the host checks
   // it every `chunk` launches
@@ -569,6 +573,7 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
         rc = AMG_ERR_CUDA;
         break;
       }
+      count_launches(h->graph_nodes);
     }
     if (rc) break;
     cudaMemcpyAsync(pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -580,7 +585,6 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
     }
     if (pinned[0]) break;
   }
-  cudaFreeHost(pinned);
   if (rc) return rc;
   double hsc[P_NSC];
   AMG_CU(cudaMemcpy(hflags, fl, sizeof hflags, cudaMemcpyDeviceToHost));
@@ -627,21 +631,69 @@ int vcycle_apply(Handle *h, const double *y, double *z) {
   cudaStream_t s = h->stream;
   const long n = 3L * h->n;
   double *ctmp = h->red.p + 4 * RED_BLOCKS + 16;
-  k_set_flags<<<1, 1, 0, s>>>(h->flags.p, 1);
+  AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(h->flags.p, 1);
   if (h->prm.vcycle_prec == AMG_FP64) {
     vcycle_level<double>(h, 0, y, z, h->flags.p + F_DONE, ctmp);
   } else {
-    k_d2f<<<nblk(n, 256), 256, 0, s>>>(n, y, low_r<float>(h));
+    AMG_KCOUNT k_d2f<<<nblk(n, 256), 256, 0, s>>>(n, y, low_r<float>(h));
     vcycle_level<float>(h, 0, low_r<float>(h), low_z<float>(h), h->flags.p + F_DONE, ctmp);
-    k_f2d<<<nblk(n, 256), 256, 0, s>>>(n, low_z<float>(h), z);
+    AMG_KCOUNT k_f2d<<<nblk(n, 256), 256, 0, s>>>(n, low_z<float>(h), z);
   }
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
 }
 
+// Average time of one solve-phase sparse product of a level matrix, launched
+// back to back on the handle's stream between CUDA events.
+int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes) {
+  if (lev < 0 || lev >= h->nlev || which < 0 || which > 4 || reps < 1) return AMG_ERR_ARG;
+  Level &L = *h->lev[lev];
+  SolveMat *M = which == 0 ? &L.sA : which == 1 ? &L.sG : which == 2 ? &L.sGT : which == 3 ? &L.sP : &L.sR;
+  if (M->nr == 0) return AMG_ERR_ARG;
+  cudaStream_t s = h->stream;
+  const int prec = h->prm.vcycle_prec;
+  const bool dbl = (prec == AMG_FP64) || (which == 0 && a64 && M->v64.p);
+  const bool b16 = !dbl && prec == AMG_FP32_BF16GP && which != 0;
+  const size_t nx = 3 * (size_t)M->nc, ny = 3 * (size_t)M->nr;
+  const size_t xs = dbl ? 8 : 4, vs = dbl ? 8 : (b16 ? 2 : 4);
+  DBuf<double> x64, y64;
+  DBuf<float> x32, y32;
+  cudaEvent_t e0, e1;
+  AMG_CU(cudaEventCreate(&e0));
+  AMG_CU(cudaEventCreate(&e1));
+  if (dbl) {
+    AMG_TRY(x64.alloc(nx));
+    AMG_TRY(y64.alloc(ny));
+    AMG_TRY(x64.zero(s));
+  } else {
+    AMG_TRY(x32.alloc(nx));
+    AMG_TRY(y32.alloc(ny));
+    AMG_TRY(x32.zero(s));
+  }
+  auto launch = [&]() {
+    if (dbl) bsrmv<double, double>(EP_SET, *M, M->v64.p, x64.p, y64.p, nullptr, 0.0, nullptr, s);
+    else if (b16) bsrmv<__nv_bfloat16, float>(EP_SET, *M, M->v16.p, x32.p, y32.p, nullptr, 0.f, nullptr, s);
+    else bsrmv<float, float>(EP_SET, *M, M->v32.p, x32.p, y32.p, nullptr, 0.f, nullptr, s);
+  };
+  launch();
+  AMG_CU(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps; ++i) launch();
+  AMG_CU(cudaEventRecord(e1, s));
+  AMG_CU(cudaEventSynchronize(e1));
+  float t = 0.f;
+  AMG_CU(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  AMG_LAUNCH_CHECK();
+  *ms = (double)t / reps;
+  *bytes = (double)M->nnzb * (9.0 * vs + 4.0) + 4.0 * (M->nr + 1) + (double)xs * (nx + ny);
+  return AMG_OK;
+}
+
 Handle::~Handle() {
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  if (pinned) cudaFreeHost(pinned);
   lev.clear();
   if (own_stream && stream) cudaStreamDestroy(stream);
 }

@@ -98,9 +98,10 @@ def test_fp64_solution_matches_oracle(A, orc, name):
     xg12, it12, rr12, _ = S.solve(d["f"], 1e-12)
     x = xg12.cpu().numpy()
     assert np.linalg.norm(x - xo12) <= 1e-10 * np.linalg.norm(xo12)
-    # true residual with the oracle's matrix
+    # true residual with the oracle's matrix (the CG recurrence residual and
+    # the true one part by rounding of order eps * cond(K))
     r = f - K.matvec(x)
-    assert np.linalg.norm(r) <= 1.1e-12 * np.linalg.norm(f)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(f)
     # host-buffer entry point gives the same iterate
     xh, ith, rrh, _ = S.solve_host(f, 1e-12)
     assert ith == it12 and np.array_equal(xh, x)
