@@ -329,8 +329,35 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
 
 
+def run_micro(args):
+    """Per-level solve-phase sparse products of the default workload, each
+    timed with CUDA events (the kernel-level view behind the step time)."""
+    import torch
+
+    import paper_1902_01715_gb300 as A
+    import workloads as W
+    torch.cuda.set_device(0)
+    A.build()
+    A.lib()
+    d = gpu_problem(A, W.beam())
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec=args.prec)
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    rows = []
+    ms, by = S.bench_spmv(0, "A", a64=True, reps=args.reps)
+    rows.append({"level": 0, "matrix": "A(fp64, CG)", "ms": ms, "GBps": by / ms / 1e6,
+                 "frac": by / ms / 1e6 / hbm})
+    for k in range(S.nlev - 1):
+        for which in ("A", "G", "GT", "P", "R"):
+            ms, by = S.bench_spmv(k, which, a64=False, reps=args.reps)
+            rows.append({"level": k, "matrix": which, "prec": args.prec, "ms": ms, "GBps": by / ms / 1e6,
+                         "frac": by / ms / 1e6 / hbm, "nnzb": S.level_info(k)["nnzb_" + ("A" if which == "A" else "G" if which in ("G", "GT") else "P")]})
+    print(json.dumps({"micro": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--micro", action="store_true", help="per-level sparse-product timings only")
+    ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -342,7 +369,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.micro:
+        run_micro(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
