@@ -165,6 +165,26 @@ int amg_bench_spmv(amg_handle h, int lev, int which, int prec_a64, int reps,
  * count each kernel node). */
 long long amg_launch_count(void);
 
+/* amg_vcycle without any memory allocation.  The paper has no counterpart:
+ * this is a library service for callers that cannot allocate while they run
+ * the preconditioner, for instance an outer Krylov solver of another code
+ * whose device memory is all held by its own pool (a cudaMalloc inside the
+ * call would fail or fragment it), or one that keeps every allocation out of
+ * its iteration loop.  Same arguments, result and precision as amg_vcycle;
+ * y and z are device vectors of 3*nnodes entries owned by the caller.
+ * Scratch: a file-scope device array of 16,640 bytes in the library (a flag
+ * block and the coarse-level temporary), held by every GPU that loads the
+ * library until the process exits.  Limit: the handle's last level may have
+ * at most 2048 dofs (the default n_coarse = 1536 fits); larger ones are
+ * rejected with AMG_ERR_ARG and a message in amg_last_error().  The first
+ * call on a device looks up the array's device address (with that device
+ * current), so make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (the call clears what
+ * must start at zero); calls that overlap on the GPU, on any handles, race on
+ * it and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+int amg_vcycle_noalloc(amg_handle h, const double *y, double *z);
+
 /* ---- structured Q1-hex elasticity problems (problem generation) ----
  * Mesh: nodes (ix,iy,iz) with global id ix + (nx+1)(iy + (ny+1) iz) at
  * (ix hx, iy hy, iz hz); element (ex,ey,ez) id ex + nx (ey + ny ez); clamp

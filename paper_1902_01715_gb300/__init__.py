@@ -27,7 +27,7 @@ EXPORTS = [
     "amg_elem_grad", "amg_get_stats", "amg_free", "amg_strerror", "amg_last_error",
     "amg_level_info", "amg_level_matrix", "amg_level_cf", "amg_level_testspace", "amg_vcycle",
     "amg_fe_size", "amg_fe_assemble", "amg_fe_load", "amg_fe_rbm", "amg_fe_conn",
-    "amg_bench_spmv", "amg_launch_count",
+    "amg_bench_spmv", "amg_launch_count", "amg_vcycle_noalloc",
 ]
 
 
@@ -102,6 +102,7 @@ def lib(path: str | None = None):
         "amg_fe_conn": (C.c_int, [C.c_int] * 4 + [_vp, _vp]),
         "amg_bench_spmv": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp]),
         "amg_launch_count": (C.c_longlong, []),
+        "amg_vcycle_noalloc": (C.c_int, [_vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -168,6 +168,7 @@ int prepare_solve(Handle *h);
 int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres);
 int vcycle_apply(Handle *h, const double *y, double *z);
 int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes);
+int vcycle_apply_noalloc(Handle *h, const double *y, double *z);
 long long launch_count();
 
 // ---- deterministic set-up kernels (det.cu) ----

@@ -14,6 +14,7 @@
 // kernel returns at once when the device-side `done` flag is set, so the
 // host replays the graph and polls the flag.
 #include <cmath>
+#include <mutex>
 
 #include "amg_internal.h"
 
@@ -644,6 +645,67 @@ int vcycle_apply(Handle *h, const double *y, double *z) {
   return AMG_OK;
 }
 
+// ---------------------------------------------------------------- V-cycle without allocation
+// Scratch of amg_vcycle_noalloc: a state flag block (256 bytes) followed by
+// the coarse-level temporary of at most VC_STATIC_MAX_COARSE doubles.  It is a
+// file-scope device array, so every GPU that loads the library holds these
+// 16,640 bytes until the process exits, and every call shares them.
+constexpr int VC_STATIC_MAX_COARSE = 2048;
+constexpr int VC_STATIC_FLAG_BYTES = 256;
+static __device__ __align__(256) unsigned char g_vc_scratch[VC_STATIC_FLAG_BYTES + VC_STATIC_MAX_COARSE * 8];
+
+// Device address of g_vc_scratch for each device, looked up once per device
+// (with that device current) on the first call there.
+static void *g_vc_scratch_addr[64] = {nullptr};
+static std::mutex g_vc_scratch_mu;
+
+static int vc_scratch_address(void **out) {
+  int dev = 0;
+  AMG_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("amg_vcycle_noalloc: device ordinal %d beyond the supported 64", dev);
+    return AMG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_vc_scratch_mu);
+  if (!g_vc_scratch_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_vc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("amg_vcycle_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return AMG_ERR_CUDA;
+    }
+    g_vc_scratch_addr[dev] = p;
+  }
+  *out = g_vc_scratch_addr[dev];
+  return AMG_OK;
+}
+
+int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
+  if (h->nL > VC_STATIC_MAX_COARSE) {
+    set_error("amg_vcycle_noalloc: the last level has %d dofs; this entry point supports at most %d "
+              "(use amg_vcycle, or a smaller n_coarse)", h->nL, VC_STATIC_MAX_COARSE);
+    return AMG_ERR_ARG;
+  }
+  void *base = nullptr;
+  AMG_TRY(vc_scratch_address(&base));
+  int *flags = (int *)base;
+  double *ctmp = (double *)((unsigned char *)base + VC_STATIC_FLAG_BYTES);
+  cudaStream_t s = h->stream;
+  const long n = 3L * h->n;
+  // the flag block keeps the previous call's contents: reset it first
+  AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(flags, 1);
+  if (h->prm.vcycle_prec == AMG_FP64) {
+    vcycle_level<double>(h, 0, y, z, flags + F_DONE, ctmp);
+  } else {
+    AMG_KCOUNT k_d2f<<<nblk(n, 256), 256, 0, s>>>(n, y, low_r<float>(h));
+    vcycle_level<float>(h, 0, low_r<float>(h), low_z<float>(h), flags + F_DONE, ctmp);
+    AMG_KCOUNT k_f2d<<<nblk(n, 256), 256, 0, s>>>(n, low_z<float>(h), z);
+  }
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
 // Average time of one solve-phase sparse product of a level matrix, launched
 // back to back on the handle's stream between CUDA events.
 int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes) {
@@ -699,3 +761,15 @@ Handle::~Handle() {
 }
 
 }  // namespace amg
+
+// One V-cycle z = B(y) that allocates no memory: for callers that cannot
+// allocate while they run it, e.g. an outer Krylov solver of another code
+// whose process keeps all device memory in its own pool (where a cudaMalloc
+// inside the call would fail or fragment that pool), or one that must keep
+// every allocation out of its iteration loop.  Its scratch is the file-scope
+// array above; see include/aspamg.h for the limits.
+extern "C" int amg_vcycle_noalloc(amg_handle hh, const double *y, double *z) {
+  amg::Handle *h = (amg::Handle *)hh;
+  if (!h || !y || !z) return AMG_ERR_ARG;
+  return amg::vcycle_apply_noalloc(h, y, z);
+}

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "aspamg.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(amg_\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:\w+\s+)+\**\s*(amg_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
