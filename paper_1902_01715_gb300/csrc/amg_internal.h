@@ -174,10 +174,6 @@ long long launch_count();
 // ---- deterministic set-up kernels (det.cu) ----
 namespace det {
 int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s);
-// dots[d] = canonical dot of (xs[d], ys[d]) for d < nd; pointer arrays on the device
-int multidot(int n, int nd, const double *const *xs, const double *const *ys, double *out,
-             double *partials, cudaStream_t s);
-int dot(int n, const double *x, const double *y, double *out, double *partials, cudaStream_t s);
 struct FsaiOut {
   int *np;        // [n] pattern nodes per row
   int *pat;       // [n*maxg]
@@ -204,7 +200,5 @@ int uniform_fill(double *v, int n, int col0, int ncols, uint64_t seed, cudaStrea
 
 // helpers (setup.cu)
 int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s);
-int compact_rows(int n, int maxper, const int *h_cnt, const int *d_col_fixed, const double *d_val_fixed,
-                 DevBsr &out, int nc, cudaStream_t s);
 
 }  // namespace amg

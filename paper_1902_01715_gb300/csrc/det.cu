@@ -61,11 +61,26 @@ int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- dots
+// One launch per group of dot products: warp w sums chunk c of pair d in the
+// fixed order; the last warp to finish (ticket counter) adds the chunk sums of
+// every pair in ascending chunk order and then runs the scalar step that
+// consumes them (Fin), so no separate scalar kernel is needed.
 constexpr int MAXD = 8;
 struct DotArgs {
   const double *x[MAXD];
   const double *y[MAXD];
 };
+
+enum { FIN_NONE = 0, FIN_SRQ_ALPHA = 1, FIN_SRQ_Q = 2, FIN_SRQ_BETA = 3, FIN_LZ_BETA = 4 };
+struct Fin {
+  int op = FIN_NONE;
+  double *sc = nullptr;
+  int *skip = nullptr;
+  int i = 0, j = 0, m = 0;
+};
+
+__device__ double line_min(double a, double b, double c, double d, double e, double f);
+__device__ int gen_eig_dev(int t, const double *H, const double *M, double *U, double *lam, double *w);
 
 __device__ __forceinline__ double chunk_sum(const double *__restrict__ x, const double *__restrict__ y,
                                             int base, int end, int lane) {
@@ -75,76 +90,133 @@ __device__ __forceinline__ double chunk_sum(const double *__restrict__ x, const 
   return s;
 }
 
-__global__ void k_dot_partials(int n, int nd, DotArgs a, double *__restrict__ part, int nchunks) {
+// Ticket: returns true in every lane of the warp that finished last.
+__device__ __forceinline__ bool last_warp(unsigned *ticket, unsigned total, int lane) {
+  unsigned t = 0;
+  if (lane == 0) {
+    __threadfence();
+    t = atomicAdd(ticket, 1u);
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  return t == total - 1;
+}
+
+// scalar steps of Algorithm 4 and of the Lanczos recurrence
+__device__ void run_fin(const Fin &f, const double *v) {
+  double *sc = f.sc;
+  if (f.op == FIN_SRQ_ALPHA) {  // v = a, b, c, d, e (stored at sc[S_A..])
+    const double b = v[1];
+    if (!(b > 0.0)) {
+      *f.skip = 1;
+      return;
+    }
+    *f.skip = 0;
+    sc[5] = line_min(v[0], b, v[2], v[3], v[4], sc[16 + f.i]);
+  } else if (f.op == FIN_SRQ_Q) {  // v = f_new, z.Sz
+    sc[8] = v[1] / v[0];
+  } else if (f.op == FIN_SRQ_BETA) {  // v = g.Sp
+    sc[10] = -(v[0] / sc[1]);
+  } else if (f.op == FIN_LZ_BETA) {  // v = w.w ; beta_j and the breakdown test
+    const double b = sqrt(v[0]);
+    sc[64 + f.j] = b;
+    if (sc[128] < 0.0 && f.j < f.m - 1 && !(b > 1e-12 * fabs(sc[f.j]))) sc[128] = (double)(f.j + 1);
+  }
+}
+
+__global__ void k_dots(int n, int nd, DotArgs a, double *__restrict__ part, unsigned *ticket, int nchunks,
+                       double *__restrict__ out, Fin fin) {
   const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= (long)nchunks * nd) return;
-  const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
-  const int base = c * CHUNK, end = min(base + CHUNK, n);
-  const double s = chunk_sum(a.x[d], a.y[d], base, end, lane);
-  if (lane == 0) part[(size_t)d * nchunks + c] = s;
-}
-
-__global__ void k_dot_final(int nd, int nchunks, const double *__restrict__ part, double *__restrict__ out) {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= nd) return;
-  double t = 0.0;
-  for (int c = 0; c < nchunks; ++c) t = t + part[(size_t)d * nchunks + c];
-  out[d] = t;
-}
-
-static int dots(int n, int nd, const DotArgs &a, double *out, double *part, cudaStream_t s) {
-  const int nchunks = (n + CHUNK - 1) / CHUNK;
+  const long total = nchunks > 0 ? (long)nchunks * nd : 1;
+  if (w >= total) return;
   if (nchunks > 0) {
-    AMG_KCOUNT k_dot_partials<<<nblk((long)nchunks * nd * 32, 256), 256, 0, s>>>(n, nd, a, part, nchunks);
-    AMG_LAUNCH_CHECK();
+    const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
+    const int base = c * CHUNK, end = min(base + CHUNK, n);
+    const double s = chunk_sum(a.x[d], a.y[d], base, end, lane);
+    if (lane == 0) part[(size_t)d * nchunks + c] = s;
   }
-  AMG_KCOUNT k_dot_final<<<1, 32, 0, s>>>(nd, nchunks, part, out);
+  if (!last_warp(ticket, (unsigned)total, lane)) return;
+  double t = 0.0;
+  if (lane < nd)
+    for (int c = 0; c < nchunks; ++c) t = t + __ldcg(part + (size_t)lane * nchunks + c);
+  if (lane < nd) out[lane] = t;
+  double v[MAXD];
+  for (int d = 0; d < MAXD; ++d) v[d] = __shfl_sync(0xffffffffu, t, d);
+  if (lane == 0) {
+    run_fin(fin, v);
+    *ticket = 0u;
+  }
+}
+
+struct DotCtx {
+  double *part;
+  unsigned *ticket;
+};
+
+static int dots(int n, int nd, const DotArgs &a, double *out, DotCtx ctx, cudaStream_t s, Fin fin = Fin()) {
+  const int nchunks = (n + CHUNK - 1) / CHUNK;
+  const long warps = nchunks > 0 ? (long)nchunks * nd : 1;
+  AMG_KCOUNT k_dots<<<nblk(warps * 32, 256), 256, 0, s>>>(n, nd, a, ctx.part, ctx.ticket, nchunks, out, fin);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
 
-int dot(int n, const double *x, const double *y, double *out, double *part, cudaStream_t s) {
+static int dot1(int n, const double *x, const double *y, double *out, DotCtx ctx, cudaStream_t s,
+                Fin fin = Fin()) {
   DotArgs a{};
   a.x[0] = x;
   a.y[0] = y;
-  return dots(n, 1, a, out, part, s);
+  return dots(n, 1, a, out, ctx, s, fin);
 }
 
-// Gram sums of the Ritz step: H[i][j] = Z_i . SZ_j and M[i][j] = Z_i . Z_j for
-// i <= j, each in the fixed dot order, mirrored to j < i.
-__global__ void k_gram_partials(int n, int t, const double *__restrict__ Z, const double *__restrict__ SZ,
-                                double *__restrict__ part, int nchunks) {
+// Gram sums of the Ritz step, H[i][j] = Z_i . SZ_j and M[i][j] = Z_i . Z_j for
+// i <= j (each in the fixed dot order, mirrored to j < i); the last warp then
+// solves the pencil (H, M) for U and resets the quotient scalars f_i to 1.
+__device__ __forceinline__ void pair_of(int d, int t, int &which, int &i, int &j) {
   const int npair = t * (t + 1) / 2;
+  which = d / npair;
+  int pr = d - which * npair;
+  i = 0;
+  while (pr >= t - i) { pr -= t - i; ++i; }
+  j = i + pr;
+}
+
+__global__ void k_gram(int n, int t, const double *__restrict__ Z, const double *__restrict__ SZ,
+                       double *__restrict__ part, unsigned *ticket, int nchunks, double *__restrict__ H,
+                       double *__restrict__ M, double *__restrict__ U, double *__restrict__ lam,
+                       double *__restrict__ wk, double *__restrict__ f, int *__restrict__ status) {
+  const int nd = t * (t + 1);
   const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= (long)nchunks * npair * 2) return;
-  const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
-  const int which = d / npair;
-  int pr = d - which * npair, i = 0;
-  while (pr >= t - i) { pr -= t - i; ++i; }
-  const int j = i + pr;
-  const double *x = Z + (size_t)i * n;
-  const double *y = which == 0 ? SZ + (size_t)j * n : Z + (size_t)j * n;
-  const int base = c * CHUNK, end = min(base + CHUNK, n);
-  const double s = chunk_sum(x, y, base, end, lane);
-  if (lane == 0) part[(size_t)d * nchunks + c] = s;
-}
-
-__global__ void k_gram_final(int t, int nchunks, const double *__restrict__ part, double *__restrict__ H,
-                             double *__restrict__ M) {
-  const int npair = t * (t + 1) / 2;
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= 2 * npair) return;
-  double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s = s + part[(size_t)d * nchunks + c];
-  const int which = d / npair;
-  int pr = d - which * npair, i = 0;
-  while (pr >= t - i) { pr -= t - i; ++i; }
-  const int j = i + pr;
-  double *O = which == 0 ? H : M;
-  O[i * t + j] = s;
-  O[j * t + i] = s;
+  const long total = nchunks > 0 ? (long)nchunks * nd : 1;
+  if (w >= total) return;
+  if (nchunks > 0) {
+    const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
+    int which, i, j;
+    pair_of(d, t, which, i, j);
+    const double *x = Z + (size_t)i * n;
+    const double *y = which == 0 ? SZ + (size_t)j * n : Z + (size_t)j * n;
+    const int base = c * CHUNK, end = min(base + CHUNK, n);
+    const double s = chunk_sum(x, y, base, end, lane);
+    if (lane == 0) part[(size_t)d * nchunks + c] = s;
+  }
+  if (!last_warp(ticket, (unsigned)total, lane)) return;
+  for (int d = lane; d < nd; d += 32) {
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s = s + __ldcg(part + (size_t)d * nchunks + c);
+    int which, i, j;
+    pair_of(d, t, which, i, j);
+    double *O = which == 0 ? H : M;
+    O[i * t + j] = s;
+    O[j * t + i] = s;
+  }
+  __syncwarp();
+  __threadfence_block();
+  if (lane == 0) {
+    if (gen_eig_dev(t, H, M, U, lam, wk)) atomicMin(status, AMG_ERR_NOT_SPD);
+    for (int i = 0; i < t; ++i) f[i] = 1.0;
+    *ticket = 0u;
+  }
 }
 
 // ---------------------------------------------------------------- vector ops
@@ -205,17 +277,21 @@ int gather_rows(const int *src_idx, int nout, int nin, int t, const double *Vin,
 // divided by its norm when that is positive.
 int mgs(int n, int t, double *V, cudaStream_t s) {
   DBuf<double> sc, part;
+  DBuf<unsigned> tk;
   AMG_TRY(sc.alloc(4));
   AMG_TRY(part.alloc((size_t)((n + CHUNK - 1) / CHUNK) + 1));
+  AMG_TRY(tk.alloc(1));
+  AMG_TRY(tk.zero(s));
+  const DotCtx ctx{part.p, tk.p};
   for (int j = 0; j < t; ++j) {
     double *vj = V + (size_t)j * n;
     for (int i = 0; i < j; ++i) {
       const double *vi = V + (size_t)i * n;
-      AMG_TRY(dot(n, vi, vj, sc.p, part.p, s));
+      AMG_TRY(dot1(n, vi, vj, sc.p, ctx, s));
       AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p, vi, nullptr);
       AMG_LAUNCH_CHECK();
     }
-    AMG_TRY(dot(n, vj, vj, sc.p, part.p, s));
+    AMG_TRY(dot1(n, vj, vj, sc.p, ctx, s));
     AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p);
     AMG_LAUNCH_CHECK();
   }
@@ -518,13 +594,6 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
 }
 
 // ---------------------------------------------------------------- Lanczos
-__global__ void k_lanczos_beta(int j, int m, double *__restrict__ sc) {
-  // sc layout: [0..63] alpha, [64..127] beta, [128] mm (as double), [129] tmp
-  const double b = sqrt(sc[129]);
-  sc[64 + j] = b;
-  if (sc[128] < 0.0 && j < m - 1 && !(b > 1e-12 * fabs(sc[j]))) sc[128] = (double)(j + 1);
-}
-
 // largest eigenvalue of the tridiagonal (alpha, beta) by bisection on Sturm
 // counts; out = [lambda, 2/lambda, min(1, safety * 2/lambda)]
 __global__ void k_lanczos_bisect(int m, const double *__restrict__ sc, double safety, double *__restrict__ out) {
@@ -569,6 +638,9 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
   if (m > n) m = n;
   if (m > 64) m = 64;
   DBuf<double> Vs, w, t1, t2, sc, part;
+  DBuf<unsigned> tk;
+  AMG_TRY(tk.alloc(1));
+  AMG_TRY(tk.zero(s));
   AMG_TRY(Vs.alloc((size_t)m * n));
   AMG_TRY(w.alloc(n));
   AMG_TRY(t1.alloc(n));
@@ -580,23 +652,28 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
   // start vector: counters (1<<62) | level<<40 | i of the generator
   AMG_KCOUNT k_lanczos_start<<<nblk(n, 256), 256, 0, s>>>(n, seed, (1ull << 62) | ((uint64_t)level << 40), Vs.p);
   AMG_LAUNCH_CHECK();
-  AMG_TRY(dot(n, Vs.p, Vs.p, sc.p + 129, part.p, s));
+  const DotCtx ctx{part.p, tk.p};
+  AMG_TRY(dot1(n, Vs.p, Vs.p, sc.p + 129, ctx, s));
   AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, Vs.p, sc.p + 129);
   for (int j = 0; j < m; ++j) {
     double *v = Vs.p + (size_t)j * n;
     AMG_TRY(spmv(GT, v, t1.p, s));
     AMG_TRY(spmv(A, t1.p, t2.p, s));
     AMG_TRY(spmv(G, t2.p, w.p, s));
-    AMG_TRY(dot(n, w.p, v, sc.p + j, part.p, s));
+    AMG_TRY(dot1(n, w.p, v, sc.p + j, ctx, s));
     AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + j, v, nullptr);
     if (j > 0) AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 64 + j - 1, v - n, nullptr);
     for (int k = 0; k <= j; ++k) {
       const double *vk = Vs.p + (size_t)k * n;
-      AMG_TRY(dot(n, w.p, vk, sc.p + 130, part.p, s));
+      AMG_TRY(dot1(n, w.p, vk, sc.p + 130, ctx, s));
       AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 130, vk, nullptr);
     }
-    AMG_TRY(dot(n, w.p, w.p, sc.p + 129, part.p, s));
-    AMG_KCOUNT k_lanczos_beta<<<1, 1, 0, s>>>(j, m, sc.p);
+    Fin fb;
+    fb.op = FIN_LZ_BETA;
+    fb.sc = sc.p;
+    fb.j = j;
+    fb.m = m;
+    AMG_TRY(dot1(n, w.p, w.p, sc.p + 129, ctx, s, fb));
     if (j < m - 1) AMG_KCOUNT k_div<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 64 + j);
     AMG_LAUNCH_CHECK();
   }
@@ -641,15 +718,6 @@ __global__ void k_srq_p0(long n, double *__restrict__ p, const double *__restric
   if (i < n) p[i] = 2.0 * (sz[i] - (*q) * z[i]);
 }
 
-__global__ void k_srq_alpha(double *__restrict__ sc, int i, int *__restrict__ skip) {
-  const double b = sc[S_B];
-  if (!(b > 0.0)) {
-    *skip = 1;
-    return;
-  }
-  *skip = 0;
-  sc[S_ALPHA] = line_min(sc[S_A], b, sc[S_C], sc[S_D], sc[S_E], sc[S_F0 + i]);
-}
 
 __global__ void k_srq_zupd(long n, double *__restrict__ z, const double *__restrict__ p, const double *__restrict__ sc,
                            const int *__restrict__ skip) {
@@ -658,7 +726,6 @@ __global__ void k_srq_zupd(long n, double *__restrict__ z, const double *__restr
   if (i < n) z[i] = z[i] + sc[S_ALPHA] * p[i];
 }
 
-__global__ void k_srq_q(double *__restrict__ sc) { sc[S_Q] = sc[S_ZSZ] / sc[S_FN]; }
 
 __global__ void k_srq_grad(long n, double *__restrict__ g, const double *__restrict__ sz, const double *__restrict__ z,
                            const double *__restrict__ sc, const int *__restrict__ skip) {
@@ -667,7 +734,6 @@ __global__ void k_srq_grad(long n, double *__restrict__ g, const double *__restr
   if (i < n) g[i] = (2.0 * (sz[i] - sc[S_Q] * z[i])) / sc[S_FN];
 }
 
-__global__ void k_srq_beta(double *__restrict__ sc) { sc[S_BETA] = -(sc[S_GSP] / sc[S_B]); }
 
 __global__ void k_srq_pupd(long n, double *__restrict__ p, const double *__restrict__ g, double *__restrict__ sc, int i0,
                            const int *__restrict__ skip) {
@@ -699,17 +765,13 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__
 // M = L L^T, C = L^{-1} (L^{-1} H)^T symmetrised, cyclic Jacobi, ascending
 // sort, U = L^{-T} W, columns signed so the largest-magnitude entry is
 // positive.  Scratch w holds 4 t*t + t doubles.
-__global__ void k_gen_eig(int t, const double *__restrict__ H, const double *__restrict__ M, double *__restrict__ U,
-                          double *__restrict__ lam, double *__restrict__ w, int *__restrict__ status) {
+__device__ int gen_eig_dev(int t, const double *H, const double *M, double *U, double *lam, double *w) {
   double *L = w, *W1 = w + t * t, *C = w + 2 * t * t, *Wv = w + 3 * t * t, *tmp = w + 4 * t * t;
   for (int i = 0; i < t * t; ++i) L[i] = 0.0;
   for (int j = 0; j < t; ++j) {
     double s = M[j * t + j];
     for (int k = 0; k < j; ++k) s = s - L[j * t + k] * L[j * t + k];
-    if (!(s > 0.0)) {
-      atomicMin(status, AMG_ERR_NOT_SPD);
-      return;
-    }
+    if (!(s > 0.0)) return 1;
     const double d = sqrt(s);
     L[j * t + j] = d;
     for (int i = j + 1; i < t; ++i) {
@@ -796,6 +858,7 @@ __global__ void k_gen_eig(int t, const double *__restrict__ H, const double *__r
     const double sg = tmp[im] < 0.0 ? -1.0 : 1.0;
     for (int i = 0; i < t; ++i) U[i * t + jj] = sg * tmp[i];
   }
+  return 0;
 }
 
 static int apply_s(const DevBsr &A, const DevBsr &G, const DevBsr &GT, const double *x, double *y, double *t1,
@@ -816,6 +879,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   const size_t nt = (size_t)n * t;
   DBuf<double> Z, P, SZall, SZ, SP, Gv, t1, t2, sc, part, H, Mg, U, lam, wk;
   DBuf<int> skip;
+  DBuf<unsigned> tk;
   AMG_TRY(Z.alloc(nt));
   AMG_TRY(P.alloc(nt));
   AMG_TRY(SZall.alloc(nt));
@@ -833,8 +897,11 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   AMG_TRY(lam.alloc(t));
   AMG_TRY(wk.alloc(4 * t * t + t));
   AMG_TRY(skip.alloc(1));
+  AMG_TRY(tk.alloc(1));
   AMG_TRY(sc.zero(s));
   AMG_TRY(skip.zero(s));
+  AMG_TRY(tk.zero(s));
+  const DotCtx ctx{part.p, tk.p};
   const int nb = nblk(n, 256);
   // Z0 = (I - S) V0, orthonormalised
   for (int i = 0; i < t; ++i) {
@@ -847,24 +914,20 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   for (int i = 0; i < t; ++i) {
     double *z = Z.p + (size_t)i * n, *p = P.p + (size_t)i * n;
     AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
-    AMG_TRY(dot(n, z, SZ.p, sc.p + S_TMP, part.p, s));
+    AMG_TRY(dot1(n, z, SZ.p, sc.p + S_TMP, ctx, s));
     AMG_KCOUNT k_srq_p0<<<nb, 256, 0, s>>>(n, p, z, SZ.p, sc.p + S_TMP);
     AMG_LAUNCH_CHECK();
   }
   AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
-  for (int it = 1; it <= kmax; ++it) {
-    if (k_ritz > 0 && it % k_ritz == 0) {
+  // one iteration of the outer loop (optionally with the Ritz step)
+  auto iteration = [&](bool ritz) -> int {
+    if (ritz) {
       for (int j = 0; j < t; ++j)
         AMG_TRY(apply_s(A, G, GT, Z.p + (size_t)j * n, SZall.p + (size_t)j * n, t1.p, t2.p, s));
-      const int npair = t * (t + 1) / 2;
-      if (nchunks > 0) {
-        AMG_KCOUNT k_gram_partials<<<nblk((long)nchunks * npair * 2 * 32, 256), 256, 0, s>>>(n, t, Z.p, SZall.p, part.p, nchunks);
-        AMG_LAUNCH_CHECK();
-      }
-      AMG_KCOUNT k_gram_final<<<nblk(2 * npair, 64), 64, 0, s>>>(t, nchunks, part.p, H.p, Mg.p);
-      AMG_KCOUNT k_gen_eig<<<1, 1, 0, s>>>(t, H.p, Mg.p, U.p, lam.p, wk.p, status);
+      const long warps = nchunks > 0 ? (long)nchunks * t * (t + 1) : 1;
+      AMG_KCOUNT k_gram<<<nblk(warps * 32, 256), 256, 0, s>>>(n, t, Z.p, SZall.p, part.p, tk.p, nchunks, H.p,
+                                                             Mg.p, U.p, lam.p, wk.p, sc.p + S_F0, status);
       AMG_KCOUNT k_rotate<<<nb, 256, 0, s>>>(n, t, Z.p, U.p);
-      AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
       AMG_LAUNCH_CHECK();
     }
     for (int i = 0; i < t; ++i) {
@@ -877,24 +940,69 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
       a5.x[2] = p; a5.y[2] = z;
       a5.x[3] = p; a5.y[3] = p;
       a5.x[4] = z; a5.y[4] = SZ.p;
-      AMG_TRY(dots(n, 5, a5, sc.p + S_A, part.p, s));
-      AMG_KCOUNT k_srq_alpha<<<1, 1, 0, s>>>(sc.p, i, skip.p);
+      Fin fa;
+      fa.op = FIN_SRQ_ALPHA;
+      fa.sc = sc.p;
+      fa.skip = skip.p;
+      fa.i = i;
+      AMG_TRY(dots(n, 5, a5, sc.p + S_A, ctx, s, fa));
       AMG_KCOUNT k_srq_zupd<<<nb, 256, 0, s>>>(n, z, p, sc.p, skip.p);
       AMG_LAUNCH_CHECK();
       AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
       DotArgs a2{};
       a2.x[0] = z; a2.y[0] = z;
       a2.x[1] = z; a2.y[1] = SZ.p;
-      AMG_TRY(dots(n, 2, a2, sc.p + S_FN, part.p, s));
-      AMG_KCOUNT k_srq_q<<<1, 1, 0, s>>>(sc.p);
+      Fin fq;
+      fq.op = FIN_SRQ_Q;
+      fq.sc = sc.p;
+      AMG_TRY(dots(n, 2, a2, sc.p + S_FN, ctx, s, fq));
       AMG_KCOUNT k_srq_grad<<<nb, 256, 0, s>>>(n, Gv.p, SZ.p, z, sc.p, skip.p);
       AMG_LAUNCH_CHECK();
-      AMG_TRY(dot(n, Gv.p, SP.p, sc.p + S_GSP, part.p, s));
-      AMG_KCOUNT k_srq_beta<<<1, 1, 0, s>>>(sc.p);
+      Fin fbt;
+      fbt.op = FIN_SRQ_BETA;
+      fbt.sc = sc.p;
+      AMG_TRY(dot1(n, Gv.p, SP.p, sc.p + S_GSP, ctx, s, fbt));
       AMG_KCOUNT k_srq_pupd<<<nb, 256, 0, s>>>(n, p, Gv.p, sc.p, i, skip.p);
       AMG_LAUNCH_CHECK();
     }
+    return AMG_OK;
+  };
+  // every iteration issues the same kernels: record each kind once as a CUDA
+  // graph and replay it
+  cudaGraphExec_t ge[2] = {nullptr, nullptr};
+  long long nodes[2] = {0, 0};
+  int rc = AMG_OK;
+  for (int it = 1; it <= kmax && rc == AMG_OK; ++it) {
+    const int ritz = (k_ritz > 0 && it % k_ritz == 0) ? 1 : 0;
+    if (!ge[ritz]) {
+      cudaGraph_t g = nullptr;
+      const long long before = launch_count();
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = AMG_ERR_CUDA;
+        break;
+      }
+      const int rc_body = iteration(ritz != 0);
+      const cudaError_t ce = cudaStreamEndCapture(s, &g);
+      nodes[ritz] = launch_count() - before;
+      count_launches(-nodes[ritz]);
+      if (rc_body || ce != cudaSuccess || cudaGraphInstantiate(&ge[ritz], g, 0) != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        set_error("SRQCG: recording the iteration graph failed");
+        rc = rc_body ? rc_body : AMG_ERR_CUDA;
+        break;
+      }
+      cudaGraphDestroy(g);
+    }
+    if (cudaGraphLaunch(ge[ritz], s) != cudaSuccess) {
+      set_error("SRQCG: graph launch failed");
+      rc = AMG_ERR_CUDA;
+      break;
+    }
+    count_launches(nodes[ritz]);
   }
+  for (int k = 0; k < 2; ++k)
+    if (ge[k]) cudaGraphExecDestroy(ge[k]);
+  if (rc) return rc;
   for (int i = 0; i < t; ++i) AMG_TRY(spmv(GT, Z.p + (size_t)i * n, V + (size_t)i * n, s));
   AMG_TRY(mgs(n, t, V, s));
   AMG_CU(cudaStreamSynchronize(s));

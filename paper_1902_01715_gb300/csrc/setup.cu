@@ -9,6 +9,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 
 #include "amg_internal.h"
@@ -34,6 +35,17 @@ static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Set-up phase trace on stderr when the environment sets AMG_TRACE (phases
+// end with a stream synchronisation, so host time is device time).
+static bool trace_on() {
+  static const bool on = getenv("AMG_TRACE") != nullptr;
+  return on;
+}
+
+static void trace(const char *what, int level, double t0) {
+  if (trace_on()) fprintf(stderr, "[amg] level %d %-18s %9.3f ms\n", level, what, 1e3 * (now_s() - t0));
 }
 
 // ---------------------------------------------------------------- kernels
@@ -248,7 +260,9 @@ static void symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z) {
 
 static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &Ac, cudaStream_t s) {
   DevBsr AP;
+  double tt = now_s();
   symbolic_product(A, P, AP);
+  trace("AP symbolic", -1, tt);
   {
     std::vector<int> rp = AP.h_rowptr, cl = AP.h_col;
     AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb));
@@ -256,8 +270,13 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
     AP.h_col = cl;
   }
   AMG_TRY(AP.upload_pattern(s));
+  tt = now_s();
   AMG_TRY(det::spgemm_numeric(A, P, AP, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  trace("AP numeric", -1, tt);
+  tt = now_s();
   symbolic_product(R, AP, Ac);
+  trace("RAP symbolic", -1, tt);
   {
     std::vector<int> rp = Ac.h_rowptr, cl = Ac.h_col;
     AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb));
@@ -265,8 +284,10 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
     Ac.h_col = cl;
   }
   AMG_TRY(Ac.upload_pattern(s));
+  tt = now_s();
   AMG_TRY(det::spgemm_numeric(R, AP, Ac, s));
   AMG_CU(cudaStreamSynchronize(s));
+  trace("RAP numeric", -1, tt);
   return AMG_OK;
 }
 
@@ -315,12 +336,18 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
 static int smoother_setup(Handle *h, Level &L, int level) {
   const amg_params &p = h->prm;
   cudaStream_t s = h->stream;
+  double tt = now_s();
   AMG_TRY(run_fsai(L.A, nullptr, p.k_g, p.rho_g, p.eps_g, p.max_g_nodes, L.G, s));
+  trace("aFSAI", level, tt);
+  tt = now_s();
   AMG_TRY(transpose_bsr(L.G, L.GT, s));
+  trace("G transpose", level, tt);
   DBuf<double> out;
   AMG_TRY(out.alloc(3));
   double ho[3];
+  tt = now_s();
   AMG_TRY(det::lanczos(L.A, L.G, L.GT, p.lanczos_m, p.seed, level, p.omega_safety, out.p, s));
+  trace("Lanczos", level, tt);
   AMG_CU(cudaMemcpy(ho, out.p, sizeof ho, cudaMemcpyDeviceToHost));
   int passes = 0;
   while (ho[1] < p.omega_bar && (double)L.G.nnzb / (double)L.G.nr < p.rho_bar && passes < p.max_refine) {
@@ -349,7 +376,10 @@ static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong
     if (L.cf[I] == 1) cidx[I] = nc++;
   L.nc = nc;
   std::vector<int> fnodes, cptr, cand;
+  double tt = now_s();
   dpls_candidates(L.A, strong, L.cf, p.d_p, fnodes, cptr, cand);
+  trace("DPLS candidates", -1, tt);
+  tt = now_s();
   const int nf = (int)fnodes.size();
   const int cap = std::max(1, std::min(p.n_max, t / 3));
   DBuf<int> d_cidx, d_f, d_cptr, d_cand, d_cnt, d_col;
@@ -370,6 +400,7 @@ static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong
     AMG_TRY(det::dpls(L.A, nullptr, nullptr, d_cidx.p, d_f.p, nf, d_cptr.p, d_cand.p, t, L.V.p, p.n_max,
                       p.kappa_p, d_cnt.p, d_col.p, d_val.p, nullptr, s));
   }
+  trace("DPLS kernel", -1, tt);
   std::vector<int> hcnt(nf), hcol((size_t)nf * cap), fidx(n, -1);
   if (nf) {
     AMG_CU(cudaMemcpy(hcnt.data(), d_cnt.p, nf * sizeof(int), cudaMemcpyDeviceToHost));
@@ -504,6 +535,7 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     AMG_TRY(st.alloc(1));
     AMG_TRY(st.zero(s));
     AMG_TRY(det::srqcg(L.A, L.G, L.GT, p.n_rq, p.k_ritz, t, Vin.p, L.V.p, st.p, s));
+    trace("SRQCG", k, t1);
     int hs = 0;
     AMG_CU(cudaMemcpy(&hs, st.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (hs) {
@@ -562,8 +594,11 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
   h->nlev = (int)h->lev.size();
   const double t6 = now_s();
   AMG_TRY(coarse_factor(h, *h->lev[h->nlev - 1]));
+  trace("coarse Cholesky", h->nlev - 1, t6);
+  const double t7 = now_s();
   AMG_TRY(prepare_solve(h));
   AMG_CU(cudaStreamSynchronize(s));
+  trace("solve layout", -1, t7);
   const double t_end = now_s();
   amg_stats &st = h->stats;
   st.nlev = h->nlev;
