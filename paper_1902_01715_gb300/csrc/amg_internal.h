@@ -114,7 +114,8 @@ struct SolveMat {
   DBuf<double> v64;
   DBuf<float> v32;
   DBuf<__nv_bfloat16> v16;
-  int lpr = 8;  // lanes per block row (set by the autotuner)
+  int lpr = 8;    // lanes per block row, FP32/bf16 storage (set by the autotuner)
+  int lpr64 = 4;  // lanes per block row, FP64 storage
 };
 
 struct Level {

@@ -80,7 +80,7 @@ struct Fin {
 };
 
 __device__ double line_min(double a, double b, double c, double d, double e, double f);
-__device__ int gen_eig_dev(int t, const double *H, const double *M, double *U, double *lam, double *w);
+__device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, double *lam, double *w, int lane);
 
 __device__ __forceinline__ double chunk_sum(const double *__restrict__ x, const double *__restrict__ y,
                                             int base, int end, int lane) {
@@ -212,8 +212,9 @@ __global__ void k_gram(int n, int t, const double *__restrict__ Z, const double 
   }
   __syncwarp();
   __threadfence_block();
+  const int bad = gen_eig_warp(t, H, M, U, lam, wk, lane);
   if (lane == 0) {
-    if (gen_eig_dev(t, H, M, U, lam, wk)) atomicMin(status, AMG_ERR_NOT_SPD);
+    if (bad) atomicMin(status, AMG_ERR_NOT_SPD);
     for (int i = 0; i < t; ++i) f[i] = 1.0;
     *ticket = 0u;
   }
@@ -761,45 +762,56 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__
   for (int j = 0; j < t; ++j) Z[(size_t)j * n + k] = row[j];
 }
 
-// Generalised eigenproblem H U = M U diag(lam) of the Ritz step, one thread:
-// M = L L^T, C = L^{-1} (L^{-1} H)^T symmetrised, cyclic Jacobi, ascending
-// sort, U = L^{-T} W, columns signed so the largest-magnitude entry is
-// positive.  Scratch w holds 4 t*t + t doubles.
-__device__ int gen_eig_dev(int t, const double *H, const double *M, double *U, double *lam, double *w) {
-  double *L = w, *W1 = w + t * t, *C = w + 2 * t * t, *Wv = w + 3 * t * t, *tmp = w + 4 * t * t;
-  for (int i = 0; i < t * t; ++i) L[i] = 0.0;
+// Generalised eigenproblem H U = M U diag(lam) of the Ritz step, by one warp:
+// M = L L^T; C = L^{-1} (L^{-1} H)^T symmetrised as (C + C^T) * 0.5; cyclic
+// Jacobi rotations over p < q (row by row) until the off-diagonal mass is
+// negligible; eigenvalues sorted ascending (ties keep index order);
+// U = L^{-T} W with each column signed so that its entry of largest magnitude
+// (first on ties) is positive.  Lanes only split work between independent
+// entries (rows of a rotation, columns of a triangular solve); every entry is
+// computed by the same sequence of rounded operations as the sequential
+// definition.  Scratch w holds 4 t*t + t doubles; returns 1 if M is not SPD.
+__device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, double *lam, double *w, int lane) {
+  double *L = w, *W1 = w + t * t, *C = w + 2 * t * t, *Wv = w + 3 * t * t;
+  for (int i = lane; i < t * t; i += 32) L[i] = 0.0;
+  __syncwarp();
   for (int j = 0; j < t; ++j) {
-    double s = M[j * t + j];
-    for (int k = 0; k < j; ++k) s = s - L[j * t + k] * L[j * t + k];
-    if (!(s > 0.0)) return 1;
-    const double d = sqrt(s);
-    L[j * t + j] = d;
-    for (int i = j + 1; i < t; ++i) {
+    double sj = M[j * t + j];
+    for (int k = 0; k < j; ++k) sj = sj - L[j * t + k] * L[j * t + k];
+    if (!(sj > 0.0)) return 1;
+    const double d = sqrt(sj);
+    for (int i = j + 1 + lane; i < t; i += 32) {
       double u = M[i * t + j];
       for (int k = 0; k < j; ++k) u = u - L[i * t + k] * L[j * t + k];
       L[i * t + j] = u / d;
     }
+    if (lane == 0) L[j * t + j] = d;
+    __syncwarp();
   }
-  for (int j = 0; j < t; ++j)
+  for (int j = lane; j < t; j += 32)
     for (int i = 0; i < t; ++i) {
-      double s = H[i * t + j];
-      for (int k = 0; k < i; ++k) s = s - L[i * t + k] * W1[k * t + j];
-      W1[i * t + j] = s / L[i * t + i];
+      double sv = H[i * t + j];
+      for (int k = 0; k < i; ++k) sv = sv - L[i * t + k] * W1[k * t + j];
+      W1[i * t + j] = sv / L[i * t + i];
     }
-  for (int j = 0; j < t; ++j)
+  __syncwarp();
+  for (int j = lane; j < t; j += 32)
     for (int i = 0; i < t; ++i) {
-      double s = W1[j * t + i];
-      for (int k = 0; k < i; ++k) s = s - L[i * t + k] * C[k * t + j];
-      C[i * t + j] = s / L[i * t + i];
+      double sv = W1[j * t + i];
+      for (int k = 0; k < i; ++k) sv = sv - L[i * t + k] * C[k * t + j];
+      C[i * t + j] = sv / L[i * t + i];
     }
-  for (int i = 0; i < t; ++i)
-    for (int j = 0; j < i; ++j) {
+  __syncwarp();
+  for (int q = lane; q < t * t; q += 32) {
+    const int i = q / t, j = q % t;
+    if (j < i) {
       const double v = (C[i * t + j] + C[j * t + i]) * 0.5;
       C[i * t + j] = v;
       C[j * t + i] = v;
     }
-  for (int i = 0; i < t; ++i)
-    for (int j = 0; j < t; ++j) Wv[i * t + j] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int q = lane; q < t * t; q += 32) Wv[q] = (q / t == q % t) ? 1.0 : 0.0;
+  __syncwarp();
   for (int sweep = 0; sweep < 100; ++sweep) {
     double off = 0.0, dg = 0.0;
     for (int p = 0; p < t; ++p) {
@@ -814,24 +826,28 @@ __device__ int gen_eig_dev(int t, const double *H, const double *M, double *U, d
         const double th = (C[q * t + q] - C[p * t + p]) / (2.0 * apq);
         const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
         const double c = 1.0 / sqrt(tt * tt + 1.0);
-        const double s = tt * c;
-        for (int k = 0; k < t; ++k) {
-          const double xp = C[k * t + p], xq = C[k * t + q];
-          C[k * t + p] = c * xp - s * xq;
-          C[k * t + q] = s * xp + c * xq;
+        const double sn = tt * c;
+        __syncwarp();
+        if (lane < t) {
+          const double xp = C[lane * t + p], xq = C[lane * t + q];
+          C[lane * t + p] = c * xp - sn * xq;
+          C[lane * t + q] = sn * xp + c * xq;
         }
-        for (int k = 0; k < t; ++k) {
-          const double xp = C[p * t + k], xq = C[q * t + k];
-          C[p * t + k] = c * xp - s * xq;
-          C[q * t + k] = s * xp + c * xq;
+        __syncwarp();
+        if (lane < t) {
+          const double xp = C[p * t + lane], xq = C[q * t + lane];
+          C[p * t + lane] = c * xp - sn * xq;
+          C[q * t + lane] = sn * xp + c * xq;
+          const double wp = Wv[lane * t + p], wq = Wv[lane * t + q];
+          Wv[lane * t + p] = c * wp - sn * wq;
+          Wv[lane * t + q] = sn * wp + c * wq;
         }
-        for (int k = 0; k < t; ++k) {
-          const double xp = Wv[k * t + p], xq = Wv[k * t + q];
-          Wv[k * t + p] = c * xp - s * xq;
-          Wv[k * t + q] = s * xp + c * xq;
+        __syncwarp();
+        if (lane == 0) {
+          C[p * t + q] = 0.0;
+          C[q * t + p] = 0.0;
         }
-        C[p * t + q] = 0.0;
-        C[q * t + p] = 0.0;
+        __syncwarp();
       }
   }
   int order[TMAXD];
@@ -844,20 +860,22 @@ __device__ int gen_eig_dev(int t, const double *H, const double *M, double *U, d
     for (int j = best; j > i; --j) order[j] = order[j - 1];
     order[i] = ti;
   }
-  for (int jj = 0; jj < t; ++jj) {
+  for (int jj = lane; jj < t; jj += 32) {
     const int j = order[jj];
+    double col[TMAXD];
     lam[jj] = C[j * t + j];
     for (int i = t - 1; i >= 0; --i) {
-      double s = Wv[i * t + j];
-      for (int k = t - 1; k > i; --k) s = s - L[k * t + i] * tmp[k];
-      tmp[i] = s / L[i * t + i];
+      double sv = Wv[i * t + j];
+      for (int k = t - 1; k > i; --k) sv = sv - L[k * t + i] * col[k];
+      col[i] = sv / L[i * t + i];
     }
     int im = 0;
     for (int i = 1; i < t; ++i)
-      if (fabs(tmp[i]) > fabs(tmp[im])) im = i;
-    const double sg = tmp[im] < 0.0 ? -1.0 : 1.0;
-    for (int i = 0; i < t; ++i) U[i * t + jj] = sg * tmp[i];
+      if (fabs(col[i]) > fabs(col[im])) im = i;
+    const double sg = col[im] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < t; ++i) U[i * t + jj] = sg * col[i];
   }
+  __syncwarp();
   return 0;
 }
 

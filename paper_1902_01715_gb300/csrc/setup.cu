@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 
 #include "amg_internal.h"
 
@@ -98,43 +99,100 @@ __global__ void k_to_dense(int nr, const int *__restrict__ rp, const int *__rest
   }
 }
 
-// Right-looking dense Cholesky in place (lower triangle) by one block.
-__global__ void __launch_bounds__(1024) k_dense_chol(int m, double *__restrict__ D, int *__restrict__ status) {
-  __shared__ double dj;
+// Blocked right-looking dense Cholesky (lower triangle, in place) and the
+// explicit inverse factor L^{-1}, in panels of CB columns spread over all SMs.
+constexpr int CB = 32;
+
+// factor the diagonal block [j0, j0+nb) in shared memory (one CTA)
+__global__ void __launch_bounds__(CB *CB) k_potrf_diag(int m, int j0, int nb, double *__restrict__ D,
+                                                       int *__restrict__ status) {
+  __shared__ double a[CB][CB + 1];
   __shared__ int bad;
+  const int r = threadIdx.x / CB, c = threadIdx.x % CB;
   if (threadIdx.x == 0) bad = 0;
+  if (r < nb && c <= r) a[r][c] = D[(size_t)(j0 + r) * m + j0 + c];
   __syncthreads();
-  for (int j = 0; j < m; ++j) {
+  for (int j = 0; j < nb; ++j) {
     if (threadIdx.x == 0) {
-      const double s = D[(size_t)j * m + j];
-      if (!(s > 0.0)) bad = 1;
-      dj = sqrt(s);
-      D[(size_t)j * m + j] = dj;
+      const double sj = a[j][j];
+      if (!(sj > 0.0)) bad = 1;
+      a[j][j] = sqrt(sj);
     }
     __syncthreads();
     if (bad) break;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) D[(size_t)i * m + j] /= dj;
+    if (c == j && r > j && r < nb) a[r][j] /= a[j][j];
     __syncthreads();
-    const int w = m - j - 1;
-    const long tot = (long)w * w;
-    for (long idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      const int i = j + 1 + (int)(idx / w), k = j + 1 + (int)(idx % w);
-      if (k <= i) D[(size_t)i * m + k] -= D[(size_t)i * m + j] * D[(size_t)k * m + j];
-    }
+    if (r < nb && c > j && c <= r) a[r][c] -= a[r][j] * a[c][j];
     __syncthreads();
   }
-  if (threadIdx.x == 0 && bad) atomicMin(status, AMG_ERR_NOT_SPD);
+  if (bad) {
+    if (threadIdx.x == 0) atomicMin(status, AMG_ERR_NOT_SPD);
+    return;
+  }
+  if (r < nb && c <= r) D[(size_t)(j0 + r) * m + j0 + c] = a[r][c];
 }
 
-// Linv = L^{-1} column by column (one thread per column), Linv zeroed first.
-__global__ void k_tri_inv(int m, const double *__restrict__ L, double *__restrict__ Linv) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  for (int i = j; i < m; ++i) {
-    double s = (i == j) ? 1.0 : 0.0;
-    for (int k = j; k < i; ++k) s -= L[(size_t)i * m + k] * Linv[(size_t)k * m + j];
-    Linv[(size_t)i * m + j] = s / L[(size_t)i * m + i];
+// panel below the diagonal block: row i solves x L_jj^T = D[i][j0:j0+nb]
+__global__ void k_trsm_panel(int m, int j0, int nb, double *__restrict__ D) {
+  const int i = j0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double x[CB];
+  double *row = D + (size_t)i * m + j0;
+  for (int t = 0; t < nb; ++t) {
+    double v = row[t];
+    const double *Lt = D + (size_t)(j0 + t) * m + j0;
+    for (int q = 0; q < t; ++q) v -= x[q] * Lt[q];
+    x[t] = v / Lt[t];
   }
+  for (int t = 0; t < nb; ++t) row[t] = x[t];
+}
+
+// trailing update D[i][k] -= sum_t D[i][j0+t] D[k][j0+t], 16 x 16 tiles
+__global__ void __launch_bounds__(256) k_syrk_trail(int m, int j0, int nb, double *__restrict__ D) {
+  __shared__ double pi[16][CB + 1], pk[16][CB + 1];
+  const int t0 = j0 + nb;
+  const int bi = blockIdx.y, bk = blockIdx.x;
+  if (bk > bi) return;
+  const int ti = threadIdx.x / 16, tk = threadIdx.x % 16;
+  const int i0 = t0 + bi * 16, k0 = t0 + bk * 16;
+  for (int q = threadIdx.x; q < 16 * CB; q += 256) {
+    const int rr = q / CB, cc = q % CB;
+    pi[rr][cc] = (i0 + rr < m && cc < nb) ? D[(size_t)(i0 + rr) * m + j0 + cc] : 0.0;
+    pk[rr][cc] = (k0 + rr < m && cc < nb) ? D[(size_t)(k0 + rr) * m + j0 + cc] : 0.0;
+  }
+  __syncthreads();
+  const int i = i0 + ti, k = k0 + tk;
+  if (i >= m || k > i) return;
+  double s = 0.0;
+  for (int t = 0; t < nb; ++t) s += pi[ti][t] * pk[tk][t];
+  D[(size_t)i * m + k] -= s;
+}
+
+// X = L^{-1}, block row [r0, r0+nb): first X[i][j] = -sum_{r0 > k >= j} L[i][k] X[k][j]
+__global__ void k_trinv_gemm(int m, int r0, int nb, const double *__restrict__ L, double *__restrict__ X) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = r0 + blockIdx.y;
+  if (j >= r0 || blockIdx.y >= (unsigned)nb) return;
+  double s = 0.0;
+  const double *Li = L + (size_t)i * m;
+  for (int k = j; k < r0; ++k) s += Li[k] * X[(size_t)k * m + j];
+  X[(size_t)i * m + j] = -s;
+}
+
+// ... then each column j < r0+nb is finished by the diagonal block's forward
+// substitution (unit right-hand side on the block's own columns)
+__global__ void k_trinv_diag(int m, int r0, int nb, const double *__restrict__ L, double *__restrict__ X) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= r0 + nb) return;
+  double x[CB];
+  for (int t = 0; t < nb; ++t) {
+    const int i = r0 + t;
+    double v = (j < r0) ? X[(size_t)i * m + j] : (j == i ? 1.0 : 0.0);
+    const double *Li = L + (size_t)i * m + r0;
+    for (int q = 0; q < t; ++q) v -= Li[q] * x[q];
+    x[t] = v / Li[t];
+  }
+  for (int t = 0; t < nb; ++t) X[(size_t)(r0 + t) * m + j] = (j <= r0 + t) ? x[t] : 0.0;
 }
 
 __global__ void k_dense_transpose(int m, const double *__restrict__ A, double *__restrict__ T) {
@@ -200,58 +258,109 @@ static void mis_host(const DevBsr &A, const std::vector<unsigned char> &strong, 
   }
 }
 
+// Host worker pool for the row-parallel graph work: rows are cut into
+// contiguous ranges, each range produces its own output in row order, and the
+// ranges are concatenated in order, so the result does not depend on the
+// number of threads.
+static int host_threads() {
+  static const int n = [] {
+    const char *e = getenv("AMG_HOST_THREADS");
+    int v = e ? atoi(e) : (int)std::thread::hardware_concurrency();
+    return v < 1 ? 1 : (v > 64 ? 64 : v);
+  }();
+  return n;
+}
+
+template <class F>
+static void parallel_ranges(int n, F f) {
+  const int nt = std::min(host_threads(), std::max(1, n / 2048));
+  if (nt <= 1) {
+    f(0, 0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    const int lo = (int)((long)n * t / nt), hi = (int)((long)n * (t + 1) / nt);
+    th.emplace_back(f, t, lo, hi);
+  }
+  for (auto &x : th) x.join();
+}
+
 // Coarse nodes within d_p strong edges of every fine node, ascending.
 static void dpls_candidates(const DevBsr &A, const std::vector<unsigned char> &strong, const std::vector<int> &cf,
                             int d_p, std::vector<int> &fnodes, std::vector<int> &cptr, std::vector<int> &cand) {
   const int n = A.nr;
-  std::vector<int> dist(n, -1), front;
-  fnodes.clear();
-  cptr.assign(1, 0);
-  cand.clear();
-  for (int I = 0; I < n; ++I) {
-    if (cf[I] == 1) continue;
-    fnodes.push_back(I);
-    front.assign(1, I);
-    dist[I] = 0;
-    const size_t c0 = cand.size();
-    for (size_t q = 0; q < front.size(); ++q) {
-      const int K = front[q];
-      if (dist[K] >= d_p) continue;
-      for (int k = A.h_rowptr[K]; k < A.h_rowptr[K + 1]; ++k) {
-        const int J = A.h_col[k];
-        if (!strong[k] || J == K || dist[J] >= 0) continue;
-        dist[J] = dist[K] + 1;
-        front.push_back(J);
-        if (cf[J] == 1) cand.push_back(J);
+  const int nt = std::min(host_threads(), std::max(1, n / 2048));
+  std::vector<std::vector<int>> pf(nt), pl(nt), pc(nt);
+  parallel_ranges(n, [&](int t, int lo, int hi) {
+    std::vector<int> dist(n, -1), front;
+    std::vector<int> &fn = pf[t], &len = pl[t], &cd = pc[t];
+    for (int I = lo; I < hi; ++I) {
+      if (cf[I] == 1) continue;
+      fn.push_back(I);
+      front.assign(1, I);
+      dist[I] = 0;
+      const size_t c0 = cd.size();
+      for (size_t q = 0; q < front.size(); ++q) {
+        const int K = front[q];
+        if (dist[K] >= d_p) continue;
+        for (int k = A.h_rowptr[K]; k < A.h_rowptr[K + 1]; ++k) {
+          const int J = A.h_col[k];
+          if (!strong[k] || J == K || dist[J] >= 0) continue;
+          dist[J] = dist[K] + 1;
+          front.push_back(J);
+          if (cf[J] == 1) cd.push_back(J);
+        }
       }
+      for (int K : front) dist[K] = -1;
+      std::sort(cd.begin() + c0, cd.end());
+      len.push_back((int)(cd.size() - c0));
     }
-    for (int K : front) dist[K] = -1;
-    std::sort(cand.begin() + c0, cand.end());
-    cptr.push_back((int)cand.size());
+  });
+  fnodes.clear();
+  cand.clear();
+  cptr.assign(1, 0);
+  for (int t = 0; t < (int)pf.size(); ++t) {
+    fnodes.insert(fnodes.end(), pf[t].begin(), pf[t].end());
+    cand.insert(cand.end(), pc[t].begin(), pc[t].end());
+    for (int l : pl[t]) cptr.push_back(cptr.back() + l);
   }
 }
 
 // Pattern of Z = X Y (columns ascending).
 static void symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z) {
   const int nr = X.nr, nc = Y.nc;
-  std::vector<int> mark(nc, -1), cols;
-  Z.h_rowptr.assign(nr + 1, 0);
-  Z.h_col.clear();
-  for (int i = 0; i < nr; ++i) {
-    cols.clear();
-    for (int kx = X.h_rowptr[i]; kx < X.h_rowptr[i + 1]; ++kx) {
-      const int k = X.h_col[kx];
-      for (int ky = Y.h_rowptr[k]; ky < Y.h_rowptr[k + 1]; ++ky) {
-        const int c = Y.h_col[ky];
-        if (mark[c] != i) {
-          mark[c] = i;
-          cols.push_back(c);
+  const int nt = std::min(host_threads(), std::max(1, nr / 2048));
+  std::vector<std::vector<int>> pcols(nt), plen(nt);
+  parallel_ranges(nr, [&](int t, int lo, int hi) {
+    std::vector<int> mark(nc, -1), cols;
+    std::vector<int> &out = pcols[t], &len = plen[t];
+    for (int i = lo; i < hi; ++i) {
+      cols.clear();
+      for (int kx = X.h_rowptr[i]; kx < X.h_rowptr[i + 1]; ++kx) {
+        const int k = X.h_col[kx];
+        for (int ky = Y.h_rowptr[k]; ky < Y.h_rowptr[k + 1]; ++ky) {
+          const int c = Y.h_col[ky];
+          if (mark[c] != i) {
+            mark[c] = i;
+            cols.push_back(c);
+          }
         }
       }
+      std::sort(cols.begin(), cols.end());
+      out.insert(out.end(), cols.begin(), cols.end());
+      len.push_back((int)cols.size());
     }
-    std::sort(cols.begin(), cols.end());
-    Z.h_col.insert(Z.h_col.end(), cols.begin(), cols.end());
-    Z.h_rowptr[i + 1] = (int)Z.h_col.size();
+  });
+  Z.h_rowptr.assign(nr + 1, 0);
+  Z.h_col.clear();
+  int row = 0;
+  for (int t = 0; t < (int)pcols.size(); ++t) {
+    Z.h_col.insert(Z.h_col.end(), pcols[t].begin(), pcols[t].end());
+    for (int l : plen[t]) {
+      Z.h_rowptr[row + 1] = Z.h_rowptr[row] + l;
+      ++row;
+    }
   }
   Z.nr = nr;
   Z.nc = nc;
@@ -448,8 +557,21 @@ static int coarse_factor(Handle *h, Level &L) {
   AMG_TRY(h->Linv.zero(s));
   if (L.n > 0) {
     AMG_KCOUNT k_to_dense<<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D.p);
-    AMG_KCOUNT k_dense_chol<<<1, 1024, 0, s>>>(m, D.p, st.p);
-    AMG_KCOUNT k_tri_inv<<<nblk(m, 128), 128, 0, s>>>(m, D.p, h->Linv.p);
+    for (int j0 = 0; j0 < m; j0 += CB) {
+      const int nb = m - j0 < CB ? m - j0 : CB;
+      AMG_KCOUNT k_potrf_diag<<<1, CB * CB, 0, s>>>(m, j0, nb, D.p, st.p);
+      const int rest = m - j0 - nb;
+      if (rest > 0) {
+        AMG_KCOUNT k_trsm_panel<<<nblk(rest, 128), 128, 0, s>>>(m, j0, nb, D.p);
+        const int nt = (rest + 15) / 16;
+        AMG_KCOUNT k_syrk_trail<<<dim3(nt, nt), 256, 0, s>>>(m, j0, nb, D.p);
+      }
+    }
+    for (int r0 = 0; r0 < m; r0 += CB) {
+      const int nb = m - r0 < CB ? m - r0 : CB;
+      if (r0 > 0) AMG_KCOUNT k_trinv_gemm<<<dim3(nblk(r0, 128), nb), 128, 0, s>>>(m, r0, nb, D.p, h->Linv.p);
+      AMG_KCOUNT k_trinv_diag<<<nblk(r0 + nb, 128), 128, 0, s>>>(m, r0, nb, D.p, h->Linv.p);
+    }
     AMG_KCOUNT k_dense_transpose<<<nblk((long)m * m, 256), 256, 0, s>>>(m, h->Linv.p, h->LinvT.p);
     AMG_LAUNCH_CHECK();
   }

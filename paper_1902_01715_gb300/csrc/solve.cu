@@ -14,7 +14,9 @@
 // kernel returns at once when the device-side `done` flag is set, so the
 // host replays the graph and polls the flag.
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
+#include <type_traits>
 
 #include "amg_internal.h"
 
@@ -89,7 +91,7 @@ static void launch_lpr(int ep, const SolveMat &M, const TM *v, const TX *x, TX *
 template <typename TM, typename TX>
 static void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
                   cudaStream_t s) {
-  switch (M.lpr) {
+  switch (std::is_same<TM, double>::value ? M.lpr64 : M.lpr) {
     case 4: launch_lpr<4>(ep, M, v, x, y, aux, w, done, s); break;
     case 8: launch_lpr<8>(ep, M, v, x, y, aux, w, done, s); break;
     case 16: launch_lpr<16>(ep, M, v, x, y, aux, w, done, s); break;
@@ -116,12 +118,20 @@ __global__ void k_entry_major<__nv_bfloat16>(long nnzb, const double *__restrict
   dst[e * nnzb + k] = __float2bfloat16_rn((float)src[t]);
 }
 
+// Row-length rule for matrices too small to tune.  FP64 arithmetic is scarce
+// on this GPU, so FP64 storage prefers few lanes per row (fewer shuffle-add
+// reduction steps per row).
 static int pick_lpr(const DevBsr &A) {
   const double avg = A.nr ? (double)A.nnzb / A.nr : 1.0;
   if (avg <= 5.0) return 4;
   if (avg <= 10.0) return 8;
   if (avg <= 20.0) return 16;
   return 32;
+}
+
+static int pick_lpr64(const DevBsr &A) {
+  const double avg = A.nr ? (double)A.nnzb / A.nr : 1.0;
+  return avg <= 40.0 ? 4 : 8;
 }
 
 static int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s) {
@@ -131,6 +141,7 @@ static int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool 
   M.rowptr = A.rowptr.p;
   M.col = A.col.p;
   M.lpr = pick_lpr(A);
+  M.lpr64 = pick_lpr64(A);
   const long n9 = 9L * A.nnzb;
   const int nb = nblk(n9, 256);
   if (f64) {
@@ -149,19 +160,88 @@ static int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool 
   return AMG_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Lanes per block row of the sparse kernel, chosen by timing LPR = 4, 8, 16,
+// 32 on the matrix itself (CUDA events, one warm-up and three timed launches
+// each).  The winner is cached per (storage type, average row length) so that
+// every matrix of that kind in the process uses the same mapping; small
+// matrices (latency-bound) keep the row-length rule.
+static std::mutex g_tune_mu;
+static std::vector<std::pair<long, int>> g_tune_cache;
+
+template <typename TM, typename TX>
+static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
+  const double avg = M.nr ? (double)M.nnzb / M.nr : 1.0;
+  const long key = (long)kind * 100000 + (long)(avg * 4.0 + 0.5);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto &e : g_tune_cache)
+      if (e.first == key) {
+        (std::is_same<TM, double>::value ? M.lpr64 : M.lpr) = e.second;
+        return AMG_OK;
+      }
+  }
+  DBuf<TX> x, y;
+  AMG_TRY(x.alloc(3 * (size_t)M.nc));
+  AMG_TRY(y.alloc(3 * (size_t)M.nr));
+  AMG_TRY(x.zero(s));
+  cudaEvent_t e0, e1;
+  AMG_CU(cudaEventCreate(&e0));
+  AMG_CU(cudaEventCreate(&e1));
+  const int cand[4] = {4, 8, 16, 32};
+  int &lpr = std::is_same<TM, double>::value ? M.lpr64 : M.lpr;
+  float best = 1e30f;
+  int bl = lpr;
+  for (int c = 0; c < 4; ++c) {
+    lpr = cand[c];
+    bsrmv<TM, TX>(EP_SET, M, v, x.p, y.p, (const TX *)nullptr, TX(0), nullptr, s);
+    AMG_CU(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) bsrmv<TM, TX>(EP_SET, M, v, x.p, y.p, (const TX *)nullptr, TX(0), nullptr, s);
+    AMG_CU(cudaEventRecord(e1, s));
+    AMG_CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      bl = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  AMG_LAUNCH_CHECK();
+  lpr = bl;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.push_back({key, bl});
+  return AMG_OK;
+}
+
+static int tune(SolveMat &M, int kind, cudaStream_t s) {
+  if (M.nnzb < 100000 || getenv("AMG_NO_TUNE")) return AMG_OK;
+  if (kind == 0) return tune_one<double, double>(M, M.v64.p, s, 0);
+  if (kind == 1) return tune_one<float, float>(M, M.v32.p, s, 1);
+  return tune_one<__nv_bfloat16, float>(M, M.v16.p, s, 2);
+}
+
 int prepare_solve(Handle *h) {
   cudaStream_t s = h->stream;
   const int prec = h->prm.vcycle_prec;
   const bool f64 = prec == AMG_FP64, f32 = prec != AMG_FP64, b16 = prec == AMG_FP32_BF16GP;
+  const int kv = f64 ? 0 : 1, kg = f64 ? 0 : (b16 ? 2 : 1);
   for (int k = 0; k < h->nlev; ++k) {
     Level &L = *h->lev[k];
     // level 0 A is always kept in FP64 for the outer CG operator
     AMG_TRY(make_solvemat(L.A, L.sA, f64 || k == 0, f32, false, s));
+    AMG_TRY(tune(L.sA, kv, s));
+    if (k == 0 && !f64) AMG_TRY(tune(L.sA, 0, s));  // FP64 copy of the CG operator
     if (k < h->nlev - 1) {
       AMG_TRY(make_solvemat(L.G, L.sG, f64, f32 && !b16, b16, s));
       AMG_TRY(make_solvemat(L.GT, L.sGT, f64, f32 && !b16, b16, s));
       AMG_TRY(make_solvemat(L.P, L.sP, f64, f32 && !b16, b16, s));
       AMG_TRY(make_solvemat(L.R, L.sR, f64, f32 && !b16, b16, s));
+      AMG_TRY(tune(L.sG, kg, s));
+      AMG_TRY(tune(L.sGT, kg, s));
+      AMG_TRY(tune(L.sP, kg, s));
+      AMG_TRY(tune(L.sR, kg, s));
     }
     const size_t n3 = 3 * (size_t)L.n;
     if (f64) {
