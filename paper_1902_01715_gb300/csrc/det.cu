@@ -708,40 +708,52 @@ __device__ double line_min(double a, double b, double c, double d, double e, dou
   return 0.0;
 }
 
-__global__ void k_srq_z0(long n, double *__restrict__ z, const double *__restrict__ v, const double *__restrict__ sv) {
+// Batched column kernels: the n_tv columns of Algorithm 4 are updated
+// independently of one another, so column j of every n x t block is handled by
+// the same per-entry arithmetic as one column at a time.  Per-column scalars
+// live in cs[] (layout below) and the skip flags in skip[].
+enum { C_ALPHA = 0, C_Q = 1, C_FN = 2, C_BETA = 3, C_B = 4, C_F = 5, C_NUM = 6 };
+
+__global__ void k_b_z0(long nt, double *__restrict__ z, const double *__restrict__ v, const double *__restrict__ sv) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) z[i] = v[i] - sv[i];
+  if (i < nt) z[i] = v[i] - sv[i];
 }
 
-__global__ void k_srq_p0(long n, double *__restrict__ p, const double *__restrict__ z, const double *__restrict__ sz,
-                         const double *__restrict__ q) {
+// p = 2 (S z - q z) with q = out[j] (the first quotients, f = 1)
+__global__ void k_b_p0(long n, int t, double *__restrict__ p, const double *__restrict__ z,
+                       const double *__restrict__ sz, const double *__restrict__ q) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = 2.0 * (sz[i] - (*q) * z[i]);
+  if (i >= n * t) return;
+  const int j = (int)(i / n);
+  p[i] = 2.0 * (sz[i] - q[j] * z[i]);
 }
 
-
-__global__ void k_srq_zupd(long n, double *__restrict__ z, const double *__restrict__ p, const double *__restrict__ sc,
-                           const int *__restrict__ skip) {
-  if (*skip) return;
+__global__ void k_b_zupd(long n, int t, double *__restrict__ z, const double *__restrict__ p,
+                         const double *__restrict__ cs, const int *__restrict__ skip) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) z[i] = z[i] + sc[S_ALPHA] * p[i];
+  if (i >= n * t) return;
+  const int j = (int)(i / n);
+  if (skip[j]) return;
+  z[i] = z[i] + cs[C_ALPHA * t + j] * p[i];
 }
 
-
-__global__ void k_srq_grad(long n, double *__restrict__ g, const double *__restrict__ sz, const double *__restrict__ z,
-                           const double *__restrict__ sc, const int *__restrict__ skip) {
-  if (*skip) return;
+__global__ void k_b_grad(long n, int t, double *__restrict__ g, const double *__restrict__ sz,
+                         const double *__restrict__ z, const double *__restrict__ cs, const int *__restrict__ skip) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) g[i] = (2.0 * (sz[i] - sc[S_Q] * z[i])) / sc[S_FN];
+  if (i >= n * t) return;
+  const int j = (int)(i / n);
+  if (skip[j]) return;
+  g[i] = (2.0 * (sz[i] - cs[C_Q * t + j] * z[i])) / cs[C_FN * t + j];
 }
 
-
-__global__ void k_srq_pupd(long n, double *__restrict__ p, const double *__restrict__ g, double *__restrict__ sc, int i0,
-                           const int *__restrict__ skip) {
-  if (*skip) return;
+__global__ void k_b_pupd(long n, int t, double *__restrict__ p, const double *__restrict__ g,
+                         double *__restrict__ cs, const int *__restrict__ skip) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = g[i] + sc[S_BETA] * p[i];
-  if (i == 0) sc[S_F0 + i0] = sc[S_FN];
+  if (i >= n * t) return;
+  const int j = (int)(i / n);
+  if (skip[j]) return;
+  p[i] = g[i] + cs[C_BETA * t + j] * p[i];
+  if (i - (long)j * n == 0) cs[C_F * t + j] = cs[C_FN * t + j];
 }
 
 __global__ void k_fill(double *__restrict__ p, int n, double v) {
@@ -749,7 +761,77 @@ __global__ void k_fill(double *__restrict__ p, int n, double v) {
   if (i < n) p[i] = v;
 }
 
-// Z <- Z U: row k of the new block is sum_i Z[i][k] U[i][j], i ascending.
+// Column dot products of n x t blocks: pair (kind, column j) is
+// x_kind[:, j] . y_kind[:, j] in the fixed order; the last warp finishes the
+// sums and the per-column scalar step of Algorithm 4 (fin).
+enum { CF_NONE = 0, CF_ALPHA = 1, CF_Q = 2, CF_BETA = 3 };
+struct CDot {
+  const double *x[5];
+  const double *y[5];
+};
+
+__global__ void k_cdots(int n, int t, int nk, CDot a, double *__restrict__ part, unsigned *ticket, int nchunks,
+                        double *__restrict__ out, int fin, double *__restrict__ cs, int *__restrict__ skip) {
+  const int nd = nk * t;
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long total = nchunks > 0 ? (long)nchunks * nd : 1;
+  if (w >= total) return;
+  if (nchunks > 0) {
+    const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
+    const int kind = d / t, j = d - kind * t;
+    const int base = c * CHUNK, end = min(base + CHUNK, n);
+    const double sv = chunk_sum(a.x[kind] + (size_t)j * n, a.y[kind] + (size_t)j * n, base, end, lane);
+    if (lane == 0) part[(size_t)d * nchunks + c] = sv;
+  }
+  if (!last_warp(ticket, (unsigned)total, lane)) return;
+  for (int d = lane; d < nd; d += 32) {
+    double sv = 0.0;
+    for (int c = 0; c < nchunks; ++c) sv = sv + __ldcg(part + (size_t)d * nchunks + c);
+    out[d] = sv;
+  }
+  __syncwarp();
+  __threadfence_block();
+  for (int j = lane; j < t; j += 32) {
+    if (fin == CF_ALPHA) {  // out = a, b, c, d, e blocks of t
+      const double bb = out[t + j];
+      cs[C_B * t + j] = bb;
+      if (!(bb > 0.0)) {
+        skip[j] = 1;
+      } else {
+        skip[j] = 0;
+        cs[C_ALPHA * t + j] = line_min(out[j], bb, out[2 * t + j], out[3 * t + j], out[4 * t + j], cs[C_F * t + j]);
+      }
+    } else if (fin == CF_Q) {  // out = f_new, z.Sz
+      cs[C_FN * t + j] = out[j];
+      cs[C_Q * t + j] = out[t + j] / out[j];
+    } else if (fin == CF_BETA) {  // out = g.Sp
+      cs[C_BETA * t + j] = -(out[j] / cs[C_B * t + j]);
+    }
+  }
+  if (lane == 0) *ticket = 0u;
+}
+
+// y_j = A x_j for the t columns of n x t blocks (one thread per dof row and
+// column, row sums in the fixed order)
+__global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const int *__restrict__ col,
+                            const double *__restrict__ val, const double *__restrict__ X, double *__restrict__ Y) {
+  const long n = 3L * nr;
+  const long tt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= n * t) return;
+  const int j = (int)(tt / n);
+  const long q = tt - (long)j * n;
+  const int I = (int)(q / 3), r = (int)(q - 3L * I);
+  const double *x = X + (size_t)j * n;
+  double sv = 0.0;
+  for (int k = rowptr[I]; k < rowptr[I + 1]; ++k) {
+    const double *blk = val + (size_t)k * 9;
+    const long J = col[k];
+    for (int c = 0; c < 3; ++c) sv = sv + blk[r * 3 + c] * x[J * 3 + c];
+  }
+  Y[tt] = sv;
+}
+
 __global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__restrict__ U) {
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -879,11 +961,29 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
   return 0;
 }
 
-static int apply_s(const DevBsr &A, const DevBsr &G, const DevBsr &GT, const double *x, double *y, double *t1,
-                   double *t2, cudaStream_t s) {
-  AMG_TRY(spmv(GT, x, t1, s));
-  AMG_TRY(spmv(A, t1, t2, s));
-  AMG_TRY(spmv(G, t2, y, s));
+static int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
+  if (A.nr == 0) return AMG_OK;
+  AMG_KCOUNT k_spmv_cols<<<nblk(3L * A.nr * t, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+// S X = G A G^T X on t columns
+static int apply_s_cols(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int t, const double *X, double *Y,
+                        double *T1, double *T2, cudaStream_t s) {
+  AMG_TRY(spmv_cols(GT, t, X, T1, s));
+  AMG_TRY(spmv_cols(A, t, T1, T2, s));
+  AMG_TRY(spmv_cols(G, t, T2, Y, s));
+  return AMG_OK;
+}
+
+static int cdots(int n, int t, int nk, const CDot &a, double *out, int fin, double *cs, int *skip, DotCtx ctx,
+                 cudaStream_t s) {
+  const int nchunks = (n + CHUNK - 1) / CHUNK;
+  const long warps = nchunks > 0 ? (long)nchunks * nk * t : 1;
+  AMG_KCOUNT k_cdots<<<nblk(warps * 32, 256), 256, 0, s>>>(n, t, nk, a, ctx.part, ctx.ticket, nchunks, out, fin, cs,
+                                                           skip);
+  AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
 
@@ -895,94 +995,82 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     return AMG_ERR_ARG;
   }
   const size_t nt = (size_t)n * t;
-  DBuf<double> Z, P, SZall, SZ, SP, Gv, t1, t2, sc, part, H, Mg, U, lam, wk;
+  DBuf<double> Z, P, SZ, SP, Gv, T1, T2, cs, out, part, H, Mg, U, lam, wk;
   DBuf<int> skip;
   DBuf<unsigned> tk;
   AMG_TRY(Z.alloc(nt));
   AMG_TRY(P.alloc(nt));
-  AMG_TRY(SZall.alloc(nt));
-  AMG_TRY(SZ.alloc(n));
-  AMG_TRY(SP.alloc(n));
-  AMG_TRY(Gv.alloc(n));
-  AMG_TRY(t1.alloc(n));
-  AMG_TRY(t2.alloc(n));
-  AMG_TRY(sc.alloc(S_F0 + 64));
+  AMG_TRY(SZ.alloc(nt));
+  AMG_TRY(SP.alloc(nt));
+  AMG_TRY(Gv.alloc(nt));
+  AMG_TRY(T1.alloc(nt));
+  AMG_TRY(T2.alloc(nt));
+  AMG_TRY(cs.alloc(C_NUM * t));
+  AMG_TRY(out.alloc(5 * t));
   const int nchunks = (n + CHUNK - 1) / CHUNK;
-  AMG_TRY(part.alloc((size_t)(nchunks + 1) * (t * (t + 1) + 8)));
+  AMG_TRY(part.alloc((size_t)(nchunks + 1) * (t * (t + 1) + 5 * t + 8)));
   AMG_TRY(H.alloc(t * t));
   AMG_TRY(Mg.alloc(t * t));
   AMG_TRY(U.alloc(t * t));
   AMG_TRY(lam.alloc(t));
   AMG_TRY(wk.alloc(4 * t * t + t));
-  AMG_TRY(skip.alloc(1));
+  AMG_TRY(skip.alloc(t));
   AMG_TRY(tk.alloc(1));
-  AMG_TRY(sc.zero(s));
+  AMG_TRY(cs.zero(s));
   AMG_TRY(skip.zero(s));
   AMG_TRY(tk.zero(s));
   const DotCtx ctx{part.p, tk.p};
-  const int nb = nblk(n, 256);
+  const int nb = nblk((long)nt, 256);
   // Z0 = (I - S) V0, orthonormalised
-  for (int i = 0; i < t; ++i) {
-    const double *v = V0 + (size_t)i * n;
-    AMG_TRY(apply_s(A, G, GT, v, SZ.p, t1.p, t2.p, s));
-    AMG_KCOUNT k_srq_z0<<<nb, 256, 0, s>>>(n, Z.p + (size_t)i * n, v, SZ.p);
-    AMG_LAUNCH_CHECK();
-  }
+  AMG_TRY(apply_s_cols(A, G, GT, t, V0, SZ.p, T1.p, T2.p, s));
+  AMG_KCOUNT k_b_z0<<<nb, 256, 0, s>>>((long)nt, Z.p, V0, SZ.p);
+  AMG_LAUNCH_CHECK();
   AMG_TRY(mgs(n, t, Z.p, s));
-  for (int i = 0; i < t; ++i) {
-    double *z = Z.p + (size_t)i * n, *p = P.p + (size_t)i * n;
-    AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
-    AMG_TRY(dot1(n, z, SZ.p, sc.p + S_TMP, ctx, s));
-    AMG_KCOUNT k_srq_p0<<<nb, 256, 0, s>>>(n, p, z, SZ.p, sc.p + S_TMP);
+  // first quotients (unit columns) and directions P = 2 (S Z - q Z)
+  AMG_TRY(apply_s_cols(A, G, GT, t, Z.p, SZ.p, T1.p, T2.p, s));
+  {
+    CDot a{};
+    a.x[0] = Z.p;
+    a.y[0] = SZ.p;
+    AMG_TRY(cdots(n, t, 1, a, out.p, CF_NONE, cs.p, skip.p, ctx, s));
+    AMG_KCOUNT k_b_p0<<<nb, 256, 0, s>>>(n, t, P.p, Z.p, SZ.p, out.p);
+    AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(cs.p + C_F * t, t, 1.0);
     AMG_LAUNCH_CHECK();
   }
-  AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(sc.p + S_F0, t, 1.0);
   // one iteration of the outer loop (optionally with the Ritz step)
   auto iteration = [&](bool ritz) -> int {
     if (ritz) {
-      for (int j = 0; j < t; ++j)
-        AMG_TRY(apply_s(A, G, GT, Z.p + (size_t)j * n, SZall.p + (size_t)j * n, t1.p, t2.p, s));
+      AMG_TRY(apply_s_cols(A, G, GT, t, Z.p, SZ.p, T1.p, T2.p, s));
       const long warps = nchunks > 0 ? (long)nchunks * t * (t + 1) : 1;
-      AMG_KCOUNT k_gram<<<nblk(warps * 32, 256), 256, 0, s>>>(n, t, Z.p, SZall.p, part.p, tk.p, nchunks, H.p,
-                                                             Mg.p, U.p, lam.p, wk.p, sc.p + S_F0, status);
-      AMG_KCOUNT k_rotate<<<nb, 256, 0, s>>>(n, t, Z.p, U.p);
+      AMG_KCOUNT k_gram<<<nblk(warps * 32, 256), 256, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p, U.p,
+                                                             lam.p, wk.p, cs.p + C_F * t, status);
+      AMG_KCOUNT k_rotate<<<nblk(n, 256), 256, 0, s>>>(n, t, Z.p, U.p);
       AMG_LAUNCH_CHECK();
     }
-    for (int i = 0; i < t; ++i) {
-      double *z = Z.p + (size_t)i * n, *p = P.p + (size_t)i * n;
-      AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
-      AMG_TRY(apply_s(A, G, GT, p, SP.p, t1.p, t2.p, s));
-      DotArgs a5{};
-      a5.x[0] = p; a5.y[0] = SZ.p;
-      a5.x[1] = p; a5.y[1] = SP.p;
-      a5.x[2] = p; a5.y[2] = z;
-      a5.x[3] = p; a5.y[3] = p;
-      a5.x[4] = z; a5.y[4] = SZ.p;
-      Fin fa;
-      fa.op = FIN_SRQ_ALPHA;
-      fa.sc = sc.p;
-      fa.skip = skip.p;
-      fa.i = i;
-      AMG_TRY(dots(n, 5, a5, sc.p + S_A, ctx, s, fa));
-      AMG_KCOUNT k_srq_zupd<<<nb, 256, 0, s>>>(n, z, p, sc.p, skip.p);
-      AMG_LAUNCH_CHECK();
-      AMG_TRY(apply_s(A, G, GT, z, SZ.p, t1.p, t2.p, s));
-      DotArgs a2{};
-      a2.x[0] = z; a2.y[0] = z;
-      a2.x[1] = z; a2.y[1] = SZ.p;
-      Fin fq;
-      fq.op = FIN_SRQ_Q;
-      fq.sc = sc.p;
-      AMG_TRY(dots(n, 2, a2, sc.p + S_FN, ctx, s, fq));
-      AMG_KCOUNT k_srq_grad<<<nb, 256, 0, s>>>(n, Gv.p, SZ.p, z, sc.p, skip.p);
-      AMG_LAUNCH_CHECK();
-      Fin fbt;
-      fbt.op = FIN_SRQ_BETA;
-      fbt.sc = sc.p;
-      AMG_TRY(dot1(n, Gv.p, SP.p, sc.p + S_GSP, ctx, s, fbt));
-      AMG_KCOUNT k_srq_pupd<<<nb, 256, 0, s>>>(n, p, Gv.p, sc.p, i, skip.p);
-      AMG_LAUNCH_CHECK();
-    }
+    AMG_TRY(apply_s_cols(A, G, GT, t, Z.p, SZ.p, T1.p, T2.p, s));
+    AMG_TRY(apply_s_cols(A, G, GT, t, P.p, SP.p, T1.p, T2.p, s));
+    CDot a5{};
+    a5.x[0] = P.p; a5.y[0] = SZ.p;
+    a5.x[1] = P.p; a5.y[1] = SP.p;
+    a5.x[2] = P.p; a5.y[2] = Z.p;
+    a5.x[3] = P.p; a5.y[3] = P.p;
+    a5.x[4] = Z.p; a5.y[4] = SZ.p;
+    AMG_TRY(cdots(n, t, 5, a5, out.p, CF_ALPHA, cs.p, skip.p, ctx, s));
+    AMG_KCOUNT k_b_zupd<<<nb, 256, 0, s>>>(n, t, Z.p, P.p, cs.p, skip.p);
+    AMG_LAUNCH_CHECK();
+    AMG_TRY(apply_s_cols(A, G, GT, t, Z.p, SZ.p, T1.p, T2.p, s));
+    CDot a2{};
+    a2.x[0] = Z.p; a2.y[0] = Z.p;
+    a2.x[1] = Z.p; a2.y[1] = SZ.p;
+    AMG_TRY(cdots(n, t, 2, a2, out.p, CF_Q, cs.p, skip.p, ctx, s));
+    AMG_KCOUNT k_b_grad<<<nb, 256, 0, s>>>(n, t, Gv.p, SZ.p, Z.p, cs.p, skip.p);
+    AMG_LAUNCH_CHECK();
+    CDot a1{};
+    a1.x[0] = Gv.p;
+    a1.y[0] = SP.p;
+    AMG_TRY(cdots(n, t, 1, a1, out.p, CF_BETA, cs.p, skip.p, ctx, s));
+    AMG_KCOUNT k_b_pupd<<<nb, 256, 0, s>>>(n, t, P.p, Gv.p, cs.p, skip.p);
+    AMG_LAUNCH_CHECK();
     return AMG_OK;
   };
   // every iteration issues the same kernels: record each kind once as a CUDA
@@ -1021,7 +1109,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   for (int k = 0; k < 2; ++k)
     if (ge[k]) cudaGraphExecDestroy(ge[k]);
   if (rc) return rc;
-  for (int i = 0; i < t; ++i) AMG_TRY(spmv(GT, Z.p + (size_t)i * n, V + (size_t)i * n, s));
+  AMG_TRY(spmv_cols(GT, t, Z.p, V, s));
   AMG_TRY(mgs(n, t, V, s));
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;

@@ -81,7 +81,12 @@ def test_vcycle_matches_oracle(A, orc, name):
     y = np.random.default_rng(41).normal(size=3 * K.nr)
     zo = H.vcycle(y)
     zg = S.vcycle(torch.tensor(y, device="cuda")).cpu().numpy()
-    assert rel(zg, zo) <= 1e-12
+    # same hierarchy bit for bit, but the solve-phase products sum in the
+    # kernels' order (autotuned lanes per row) and the coarse level uses the
+    # explicit inverse factor: each product has relative error ~ k eps
+    # |A||x|/|Ax| (k ~ 81 terms, cancellation up to ~1e4 on the layered slab),
+    # compounded over ~8 products per level, hence the FP64 solution bound
+    assert rel(zg, zo) <= 1e-10
 
 
 @pytest.mark.parametrize("name", list(SMALL))
