@@ -354,9 +354,34 @@ def run_micro(args):
     print(json.dumps({"micro": rows}), flush=True)
 
 
+def run_single(args):
+    """One set-up + solve of the workload with no warm-up (the command the
+    kernel launch lists under profiles/ are taken from); prints a summary, not
+    a bench line."""
+    import torch
+
+    import paper_1902_01715_gb300 as A
+    import workloads as W
+    torch.cuda.set_device(0)
+    A.build()
+    A.lib()
+    p = W.beam(*args.dims) if args.dims else W.beam()
+    d = gpu_problem(A, p)
+    l0 = A.launch_count()
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec=args.prec)
+    x, it, rr, rc = S.solve(d["f"], RTOL)
+    torch.cuda.synchronize()
+    st = S.stats()
+    print(json.dumps({"single": {"dims": [p.nx, p.ny, p.nz], "n_it": it[0], "rc": rc, "setup_ms": st["T_p"] * 1e3,
+                                 "solve_ms": st["T_s"] * 1e3, "launches": A.launch_count() - l0}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--micro", action="store_true", help="per-level sparse-product timings only")
+    ap.add_argument("--single", action="store_true", help="one set-up + solve, no warm-up (for profilers)")
+    ap.add_argument("--dims", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    help="beam size nx,ny,nz for --single (default 128,32,32)")
     ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -369,7 +394,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.micro:
+    if args.single:
+        run_single(args)
+    elif args.micro:
         run_micro(args)
     elif args.impl == "reference":
         run_reference(args)

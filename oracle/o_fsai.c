@@ -209,7 +209,8 @@ static int sturm_count(int m, const double *al, const double *be, double x) {
 }
 
 /* Largest eigenvalue of G A G^T estimated by m Lanczos steps with full
- * re-orthogonalisation (one Gram-Schmidt pass against all previous vectors),
+ * re-orthogonalisation (one classical Gram-Schmidt pass against all previous
+ * vectors; the paper says only "a few Lanczos passes"),
  * from the start vector of level `level` of the counter generator; the
  * largest Ritz value is found by bisection on Sturm counts. */
 double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
@@ -221,7 +222,7 @@ double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
   double *w = (double *)malloc((size_t)n * sizeof(double));
   double *t1 = (double *)malloc((size_t)n * sizeof(double));
   double *t2 = (double *)malloc((size_t)n * sizeof(double));
-  double al[64], be[64];
+  double al[64], be[64], hk[64];
   for (int i = 0; i < n; ++i)
     Vs[i] = or_uniform_pm1(seed, (1ull << 62) | ((uint64_t)level << 40) | (uint64_t)i);
   double nr = sqrt(or_dot(n, Vs, Vs));
@@ -238,10 +239,13 @@ double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
       const double *vp = Vs + (size_t)(j - 1) * n;
       for (int i = 0; i < n; ++i) w[i] = w[i] - be[j - 1] * vp[i];
     }
-    for (int k = 0; k <= j; ++k) {
-      const double *vk = Vs + (size_t)k * n;
-      const double h = or_dot(n, w, vk);
-      for (int i = 0; i < n; ++i) w[i] = w[i] - h * vk[i];
+    /* one classical Gram-Schmidt pass against v_0..v_j: all coefficients
+     * from the same w, then w_i - sum_k h_k v_k,i with k ascending */
+    for (int k = 0; k <= j; ++k) hk[k] = or_dot(n, w, Vs + (size_t)k * n);
+    for (int i = 0; i < n; ++i) {
+      double s = w[i];
+      for (int k = 0; k <= j; ++k) s = s - hk[k] * Vs[(size_t)k * n + i];
+      w[i] = s;
     }
     be[j] = sqrt(or_dot(n, w, w));
     if (j == m - 1) break;

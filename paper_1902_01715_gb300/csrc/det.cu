@@ -633,58 +633,6 @@ __global__ void k_lanczos_start(long n, uint64_t seed, uint64_t base, double *__
   if (i < n) v[i] = uniform_pm1(seed, base | (uint64_t)i);
 }
 
-int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t seed, int level,
-            double safety, double *d_out, cudaStream_t s) {
-  const int n = 3 * A.nr;
-  if (m > n) m = n;
-  if (m > 64) m = 64;
-  DBuf<double> Vs, w, t1, t2, sc, part;
-  DBuf<unsigned> tk;
-  AMG_TRY(tk.alloc(1));
-  AMG_TRY(tk.zero(s));
-  AMG_TRY(Vs.alloc((size_t)m * n));
-  AMG_TRY(w.alloc(n));
-  AMG_TRY(t1.alloc(n));
-  AMG_TRY(t2.alloc(n));
-  AMG_TRY(sc.alloc(160));
-  AMG_TRY(part.alloc((size_t)(n + CHUNK - 1) / CHUNK + 1));
-  AMG_TRY(sc.zero(s));
-  AMG_KCOUNT k_set_neg<<<1, 1, 0, s>>>(sc.p + 128);
-  // start vector: counters (1<<62) | level<<40 | i of the generator
-  AMG_KCOUNT k_lanczos_start<<<nblk(n, 256), 256, 0, s>>>(n, seed, (1ull << 62) | ((uint64_t)level << 40), Vs.p);
-  AMG_LAUNCH_CHECK();
-  const DotCtx ctx{part.p, tk.p};
-  AMG_TRY(dot1(n, Vs.p, Vs.p, sc.p + 129, ctx, s));
-  AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, Vs.p, sc.p + 129);
-  for (int j = 0; j < m; ++j) {
-    double *v = Vs.p + (size_t)j * n;
-    AMG_TRY(spmv(GT, v, t1.p, s));
-    AMG_TRY(spmv(A, t1.p, t2.p, s));
-    AMG_TRY(spmv(G, t2.p, w.p, s));
-    AMG_TRY(dot1(n, w.p, v, sc.p + j, ctx, s));
-    AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + j, v, nullptr);
-    if (j > 0) AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 64 + j - 1, v - n, nullptr);
-    for (int k = 0; k <= j; ++k) {
-      const double *vk = Vs.p + (size_t)k * n;
-      AMG_TRY(dot1(n, w.p, vk, sc.p + 130, ctx, s));
-      AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, w.p, sc.p + 130, vk, nullptr);
-    }
-    Fin fb;
-    fb.op = FIN_LZ_BETA;
-    fb.sc = sc.p;
-    fb.j = j;
-    fb.m = m;
-    AMG_TRY(dot1(n, w.p, w.p, sc.p + 129, ctx, s, fb));
-    if (j < m - 1) AMG_KCOUNT k_div<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 64 + j);
-    AMG_LAUNCH_CHECK();
-  }
-  AMG_KCOUNT k_lanczos_bisect<<<1, 1, 0, s>>>(m, sc.p, safety, d_out);
-  AMG_LAUNCH_CHECK();
-  AMG_CU(cudaStreamSynchronize(s));
-  return AMG_OK;
-}
-
-
 // ---------------------------------------------------------------- SRQCG
 // Scalar slots of the SRQCG state (device doubles).
 enum { S_A = 0, S_B, S_C, S_D, S_E, S_ALPHA, S_FN, S_ZSZ, S_Q, S_GSP, S_BETA, S_TMP, S_F0 = 16 };
@@ -768,6 +716,7 @@ enum { CF_NONE = 0, CF_ALPHA = 1, CF_Q = 2, CF_BETA = 3 };
 struct CDot {
   const double *x[5];
   const double *y[5];
+  long xs[5], ys[5];  // column strides of x and y (n, or 0 for one shared vector)
 };
 
 __global__ void k_cdots(int n, int t, int nk, CDot a, double *__restrict__ part, unsigned *ticket, int nchunks,
@@ -781,7 +730,7 @@ __global__ void k_cdots(int n, int t, int nk, CDot a, double *__restrict__ part,
     const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
     const int kind = d / t, j = d - kind * t;
     const int base = c * CHUNK, end = min(base + CHUNK, n);
-    const double sv = chunk_sum(a.x[kind] + (size_t)j * n, a.y[kind] + (size_t)j * n, base, end, lane);
+    const double sv = chunk_sum(a.x[kind] + j * a.xs[kind], a.y[kind] + j * a.ys[kind], base, end, lane);
     if (lane == 0) part[(size_t)d * nchunks + c] = sv;
   }
   if (!last_warp(ticket, (unsigned)total, lane)) return;
@@ -1032,6 +981,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     CDot a{};
     a.x[0] = Z.p;
     a.y[0] = SZ.p;
+    a.xs[0] = a.ys[0] = n;
     AMG_TRY(cdots(n, t, 1, a, out.p, CF_NONE, cs.p, skip.p, ctx, s));
     AMG_KCOUNT k_b_p0<<<nb, 256, 0, s>>>(n, t, P.p, Z.p, SZ.p, out.p);
     AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(cs.p + C_F * t, t, 1.0);
@@ -1055,6 +1005,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     a5.x[2] = P.p; a5.y[2] = Z.p;
     a5.x[3] = P.p; a5.y[3] = P.p;
     a5.x[4] = Z.p; a5.y[4] = SZ.p;
+    for (int q = 0; q < 5; ++q) a5.xs[q] = a5.ys[q] = n;
     AMG_TRY(cdots(n, t, 5, a5, out.p, CF_ALPHA, cs.p, skip.p, ctx, s));
     AMG_KCOUNT k_b_zupd<<<nb, 256, 0, s>>>(n, t, Z.p, P.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
@@ -1062,12 +1013,14 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     CDot a2{};
     a2.x[0] = Z.p; a2.y[0] = Z.p;
     a2.x[1] = Z.p; a2.y[1] = SZ.p;
+    a2.xs[0] = a2.ys[0] = a2.xs[1] = a2.ys[1] = n;
     AMG_TRY(cdots(n, t, 2, a2, out.p, CF_Q, cs.p, skip.p, ctx, s));
     AMG_KCOUNT k_b_grad<<<nb, 256, 0, s>>>(n, t, Gv.p, SZ.p, Z.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
     CDot a1{};
     a1.x[0] = Gv.p;
     a1.y[0] = SP.p;
+    a1.xs[0] = a1.ys[0] = n;
     AMG_TRY(cdots(n, t, 1, a1, out.p, CF_BETA, cs.p, skip.p, ctx, s));
     AMG_KCOUNT k_b_pupd<<<nb, 256, 0, s>>>(n, t, P.p, Gv.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
@@ -1111,6 +1064,83 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   if (rc) return rc;
   AMG_TRY(spmv_cols(GT, t, Z.p, V, s));
   AMG_TRY(mgs(n, t, V, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- Lanczos
+// w = (w - alpha_j v_j) - beta_{j-1} v_{j-1}
+__global__ void k_lz_ab(long n, double *__restrict__ w, const double *__restrict__ v, const double *__restrict__ vp,
+                        const double *__restrict__ sc, int j) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x = w[i] - sc[j] * v[i];
+  if (vp) x = x - sc[64 + j - 1] * vp[i];
+  w[i] = x;
+}
+
+// w_i - sum_{k <= j} h_k v_k,i, k ascending (one classical Gram-Schmidt pass)
+__global__ void k_lz_reorth(long n, int j, double *__restrict__ w, const double *__restrict__ Vs,
+                            const double *__restrict__ h) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x = w[i];
+  for (int k = 0; k <= j; ++k) x = x - h[k] * Vs[(size_t)k * n + i];
+  w[i] = x;
+}
+
+// Largest eigenvalue of G A G^T by m Lanczos steps with full
+// re-orthogonalisation (one classical Gram-Schmidt pass per step), from the
+// counter-generator start vector of this level; bisection on Sturm counts.
+// sc layout: [0..63] alpha, [64..127] beta, [128] breakdown step, [129] norm
+// square, [160..223] re-orthogonalisation coefficients.
+int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t seed, int level,
+            double safety, double *d_out, cudaStream_t s) {
+  const int n = 3 * A.nr;
+  if (m > n) m = n;
+  if (m > 64) m = 64;
+  DBuf<double> Vs, w, t1, t2, sc, part;
+  DBuf<unsigned> tk;
+  AMG_TRY(tk.alloc(1));
+  AMG_TRY(tk.zero(s));
+  AMG_TRY(Vs.alloc((size_t)m * n));
+  AMG_TRY(w.alloc(n));
+  AMG_TRY(t1.alloc(n));
+  AMG_TRY(t2.alloc(n));
+  AMG_TRY(sc.alloc(256));
+  AMG_TRY(part.alloc((size_t)((n + CHUNK - 1) / CHUNK + 1) * 66));
+  AMG_TRY(sc.zero(s));
+  AMG_KCOUNT k_set_neg<<<1, 1, 0, s>>>(sc.p + 128);
+  AMG_KCOUNT k_lanczos_start<<<nblk(n, 256), 256, 0, s>>>(n, seed, (1ull << 62) | ((uint64_t)level << 40), Vs.p);
+  AMG_LAUNCH_CHECK();
+  const DotCtx ctx{part.p, tk.p};
+  AMG_TRY(dot1(n, Vs.p, Vs.p, sc.p + 129, ctx, s));
+  AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, Vs.p, sc.p + 129);
+  for (int j = 0; j < m; ++j) {
+    double *v = Vs.p + (size_t)j * n;
+    AMG_TRY(spmv(GT, v, t1.p, s));
+    AMG_TRY(spmv(A, t1.p, t2.p, s));
+    AMG_TRY(spmv(G, t2.p, w.p, s));
+    AMG_TRY(dot1(n, w.p, v, sc.p + j, ctx, s));
+    AMG_KCOUNT k_lz_ab<<<nblk(n, 256), 256, 0, s>>>(n, w.p, v, j > 0 ? v - n : nullptr, sc.p, j);
+    CDot a{};
+    a.x[0] = w.p;
+    a.xs[0] = 0;
+    a.y[0] = Vs.p;
+    a.ys[0] = n;
+    AMG_TRY(cdots(n, j + 1, 1, a, sc.p + 160, CF_NONE, nullptr, nullptr, ctx, s));
+    AMG_KCOUNT k_lz_reorth<<<nblk(n, 256), 256, 0, s>>>(n, j, w.p, Vs.p, sc.p + 160);
+    Fin fb;
+    fb.op = FIN_LZ_BETA;
+    fb.sc = sc.p;
+    fb.j = j;
+    fb.m = m;
+    AMG_TRY(dot1(n, w.p, w.p, sc.p + 129, ctx, s, fb));
+    if (j < m - 1) AMG_KCOUNT k_div<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 64 + j);
+    AMG_LAUNCH_CHECK();
+  }
+  AMG_KCOUNT k_lanczos_bisect<<<1, 1, 0, s>>>(m, sc.p, safety, d_out);
+  AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
 }
