@@ -24,6 +24,7 @@ UNITS = {
     "setup.cu": [],
     "solve.cu": [],
     "capi.cu": [],
+    "batch.cu": [],
 }
 
 

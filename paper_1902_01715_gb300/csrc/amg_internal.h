@@ -132,6 +132,8 @@ struct Level {
   DBuf<float> y32, s32, r32, t32, z32;
 };
 
+struct Batch;  // batched-solve state (batch.cu)
+
 struct Handle {
   amg_params prm{};
   cudaStream_t stream = nullptr;
@@ -156,6 +158,7 @@ struct Handle {
   bool own_stream = false;  // created because the caller passed the legacy stream
   long long graph_nodes = 0;
   int *pinned = nullptr;    // host flag for polling the PCG state
+  Batch *batch = nullptr;   // k > 1 right-hand sides
   ~Handle();
 };
 
@@ -170,6 +173,9 @@ int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters,
 int vcycle_apply(Handle *h, const double *y, double *z);
 int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes);
 int vcycle_apply_noalloc(Handle *h, const double *y, double *z);
+// ---- batched solve (batch.cu) ----
+int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres);
+void free_batch(Handle *h);
 long long launch_count();
 
 // ---- deterministic set-up kernels (det.cu) ----

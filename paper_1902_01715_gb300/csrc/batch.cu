@@ -1,0 +1,582 @@
+// Batched solve: k right-hand sides at once (block PCG with one V-cycle per
+// iteration and per-column convergence masks).  Vectors are stored
+// "interleaved" — entry (dof d, column c) at d*k + c — so one warp walks a
+// block row once and applies each 3x3 block (read once, broadcast to the
+// lanes) to all k columns with coalesced loads of the neighbour's 3 x k
+// values.  Each column runs its own CG recurrence (alpha, beta, residual,
+// convergence) in FP64; a converged column is frozen (its x, r, p no longer
+// change) while the V-cycle keeps processing the whole block.  Reductions
+// are deterministic (per-column partials per block, summed in block order by
+// the last block).
+#include <cmath>
+
+#include "amg_internal.h"
+
+namespace amg {
+
+static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
+
+__device__ __forceinline__ double cvb(double v, double) { return v; }
+__device__ __forceinline__ float cvb(float v, float) { return v; }
+__device__ __forceinline__ float cvb(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+
+enum { BE_SET = 0, BE_SCALE = 1, BE_RESID = 2, BE_SADD = 3, BE_ACC = 4 };
+
+// Y = epilogue(A X) on interleaved n x k blocks; one warp per block row.
+template <typename TM, typename TX, int EP>
+__global__ void __launch_bounds__(256) k_bsrmm(int nr, int k, const int *__restrict__ rp, const int *__restrict__ col,
+                                               const TM *__restrict__ v, long nnzb, const TX *__restrict__ X,
+                                               TX *__restrict__ Y, const TX *__restrict__ AUX, TX w,
+                                               const int *__restrict__ done) {
+  if (done && *done) return;
+  const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= nr) return;
+  const int kb = rp[row], ke = rp[row + 1];
+  for (int c0 = 0; c0 < k; c0 += 64) {
+    const int ca = c0 + lane, cb = c0 + 32 + lane;
+    const bool va = ca < k, vb = cb < k;
+    TX a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
+    for (int q = kb; q < ke; ++q) {
+      const long j = col[q];
+      const TX m0 = cvb(v[q], TX(0)), m1 = cvb(v[nnzb + q], TX(0)), m2 = cvb(v[2 * nnzb + q], TX(0));
+      const TX m3 = cvb(v[3 * nnzb + q], TX(0)), m4 = cvb(v[4 * nnzb + q], TX(0)), m5 = cvb(v[5 * nnzb + q], TX(0));
+      const TX m6 = cvb(v[6 * nnzb + q], TX(0)), m7 = cvb(v[7 * nnzb + q], TX(0)), m8 = cvb(v[8 * nnzb + q], TX(0));
+      const TX *xj = X + 3 * j * k;
+      if (va) {
+        const TX x0 = xj[ca], x1 = xj[k + ca], x2 = xj[2 * k + ca];
+        a0 += m0 * x0 + m1 * x1 + m2 * x2;
+        a1 += m3 * x0 + m4 * x1 + m5 * x2;
+        a2 += m6 * x0 + m7 * x1 + m8 * x2;
+      }
+      if (vb) {
+        const TX x0 = xj[cb], x1 = xj[k + cb], x2 = xj[2 * k + cb];
+        b0 += m0 * x0 + m1 * x1 + m2 * x2;
+        b1 += m3 * x0 + m4 * x1 + m5 * x2;
+        b2 += m6 * x0 + m7 * x1 + m8 * x2;
+      }
+    }
+    const long o = 3L * row * k;
+    auto put = [&](int c, TX s0, TX s1, TX s2) {
+      TX *y = Y + o + c;
+      const TX *ax = AUX ? AUX + o + c : nullptr;
+      if (EP == BE_SET) { y[0] = s0; y[k] = s1; y[2 * k] = s2; }
+      if (EP == BE_SCALE) { y[0] = w * s0; y[k] = w * s1; y[2 * k] = w * s2; }
+      if (EP == BE_RESID) { y[0] = ax[0] - s0; y[k] = ax[k] - s1; y[2 * k] = ax[2 * k] - s2; }
+      if (EP == BE_SADD) { y[0] = ax[0] + w * s0; y[k] = ax[k] + w * s1; y[2 * k] = ax[2 * k] + w * s2; }
+      if (EP == BE_ACC) { y[0] += s0; y[k] += s1; y[2 * k] += s2; }
+    };
+    if (va) put(ca, a0, a1, a2);
+    if (vb) put(cb, b0, b1, b2);
+  }
+}
+
+template <typename TM, typename TX>
+static void bmm(int ep, const SolveMat &M, const TM *v, int k, const TX *X, TX *Y, const TX *AUX, TX w, const int *done,
+                cudaStream_t s) {
+  const int nb = nblk(32L * M.nr, 256);
+  if (!nb) return;
+  switch (ep) {
+    case BE_SET: AMG_KCOUNT k_bsrmm<TM, TX, BE_SET><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
+    case BE_SCALE: AMG_KCOUNT k_bsrmm<TM, TX, BE_SCALE><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
+    case BE_RESID: AMG_KCOUNT k_bsrmm<TM, TX, BE_RESID><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
+    case BE_SADD: AMG_KCOUNT k_bsrmm<TM, TX, BE_SADD><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
+    default: AMG_KCOUNT k_bsrmm<TM, TX, BE_ACC><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
+  }
+}
+
+template <typename TX>
+static void bmv(int ep, const SolveMat &M, bool b16, int k, const TX *X, TX *Y, const TX *AUX, TX w, const int *done,
+                cudaStream_t s);
+template <>
+void bmv<double>(int ep, const SolveMat &M, bool, int k, const double *X, double *Y, const double *AUX, double w,
+                 const int *done, cudaStream_t s) {
+  bmm<double, double>(ep, M, M.v64.p, k, X, Y, AUX, w, done, s);
+}
+template <>
+void bmv<float>(int ep, const SolveMat &M, bool b16, int k, const float *X, float *Y, const float *AUX, float w,
+                const int *done, cudaStream_t s) {
+  if (b16) bmm<__nv_bfloat16, float>(ep, M, M.v16.p, k, X, Y, AUX, w, done, s);
+  else bmm<float, float>(ep, M, M.v32.p, k, X, Y, AUX, w, done, s);
+}
+
+// coarse level: T = Linv Y, Z = LinvT T (interleaved n x k, FP64 arithmetic)
+template <typename TX>
+__global__ void k_btrmm_lower(int m, int k, const double *__restrict__ Li, const TX *__restrict__ Y,
+                              double *__restrict__ T, const int *__restrict__ done) {
+  if (done && *done) return;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)m * k) return;
+  const int i = (int)(t / k), c = (int)(t % k);
+  double s = 0.0;
+  const double *Lr = Li + (size_t)i * m;
+  for (int q = 0; q <= i; ++q) s += Lr[q] * (double)Y[(size_t)q * k + c];
+  T[t] = s;
+}
+
+template <typename TX>
+__global__ void k_btrmm_upper(int m, int k, const double *__restrict__ LiT, const double *__restrict__ T,
+                              TX *__restrict__ Z, const int *__restrict__ done) {
+  if (done && *done) return;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)m * k) return;
+  const int i = (int)(t / k), c = (int)(t % k);
+  double s = 0.0;
+  const double *Lr = LiT + (size_t)i * m;
+  for (int q = i; q < m; ++q) s += Lr[q] * T[(size_t)q * k + c];
+  Z[t] = (TX)s;
+}
+
+// ---------------------------------------------------------------- block state
+struct BatchLevel {
+  DBuf<double> y64, z64, s64, r64, t64;
+  DBuf<float> y32, z32, s32, r32, t32;
+};
+
+struct Batch {
+  int k = 0, prec = -1;
+  std::vector<BatchLevel> lev;
+  DBuf<double> x, r, z, p, q, zold, ctmp, sc, part;
+  DBuf<int> flags;
+  DBuf<float> rlow, zlow;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_nodes = 0;
+  int *pinned = nullptr;
+  ~Batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (pinned) cudaFreeHost(pinned);
+  }
+};
+
+// per-column scalar slots: sc[slot * k + c]
+enum { BS_BN2 = 0, BS_RZ, BS_PQ, BS_ALPHA, BS_RR, BS_BETA, BS_TOL2, BS_NUM };
+// flags: [0] all done, [1] ticket, [2] status, [3] maxit, [4] iteration, then per column:
+// [8 + c] converged, [8 + k + c] iterations of column c
+enum { BF_DONE = 0, BF_TICKET = 1, BF_STATUS = 2, BF_MAXIT = 3, BF_ITER = 4, BF_COL = 8 };
+
+constexpr int BRED_BLOCKS = 148;
+
+// Per-column partial sums of one block into part[blockIdx][c]; the last
+// block adds the partials in block order and runs fin(c, total) per column.
+template <class Fin>
+__device__ void bfinish(double v, int k, double *part, int *flags, Fin fin) {
+  extern __shared__ double sh[];
+  const int c = threadIdx.x % k;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  const int per = blockDim.x / k;
+  if (threadIdx.x < k) {
+    double s = 0.0;
+    for (int q = 0; q < per; ++q) s += sh[c + q * k];
+    part[(size_t)blockIdx.x * k + c] = s;
+  }
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&flags[BF_TICKET], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < k) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double *)part)[(size_t)b * k + c];
+    fin(c, s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) flags[BF_TICKET] = 0;
+}
+
+__device__ __forceinline__ bool col_active(const int *flags, int c) { return flags[BF_COL + c] == 0; }
+
+// x = 0, r = b (from column-major B), rlow = (TX) r, bn2_c, tol2_c
+template <typename TX>
+__global__ void k_bstart(long n, int k, const double *__restrict__ B, double *__restrict__ x, double *__restrict__ r,
+                         TX *__restrict__ rlow, double rtol, double *sc, int *flags, double *part) {
+  double v = 0.0;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) {
+    const long d = t / k;
+    const int c = (int)(t - d * k);
+    const double b = B[(size_t)c * n + d];
+    x[t] = 0.0;
+    r[t] = b;
+    if (rlow) rlow[t] = (TX)b;
+    v += b * b;
+  }
+  bfinish(v, k, part, flags, [&](int c, double tot) {
+    sc[BS_BN2 * k + c] = tot;
+    sc[BS_TOL2 * k + c] = (rtol * rtol) * tot;
+    sc[BS_RZ * k + c] = 1.0;
+    flags[BF_COL + c] = (tot == 0.0) ? 1 : 0;
+    flags[BF_COL + k + c] = 0;
+  });
+}
+
+__global__ void k_bflags(int k, int maxit, int *flags) {
+  flags[BF_DONE] = 0;
+  flags[BF_TICKET] = 0;
+  flags[BF_STATUS] = 0;
+  flags[BF_MAXIT] = maxit;
+  flags[BF_ITER] = 0;
+}
+
+// pq_c = p.q ; alpha_c = rz_c / pq_c
+__global__ void k_bpq(long n, int k, const double *__restrict__ p, const double *__restrict__ q, double *sc,
+                      int *flags, double *part) {
+  if (flags[BF_DONE]) return;
+  double v = 0.0;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) v += p[t] * q[t];
+  bfinish(v, k, part, flags, [&](int c, double tot) {
+    sc[BS_PQ * k + c] = tot;
+    if (col_active(flags, c)) {
+      if (!(tot > 0.0) || !isfinite(tot)) {
+        flags[BF_STATUS] = AMG_ERR_BREAKDOWN;
+        flags[BF_COL + c] = 2;
+      } else {
+        sc[BS_ALPHA * k + c] = sc[BS_RZ * k + c] / tot;
+      }
+    }
+  });
+}
+
+// active columns: x += alpha p, r -= alpha q ; rr_c ; convergence ; rlow
+template <typename TX>
+__global__ void k_bxr(long n, int k, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                      const double *__restrict__ q, TX *__restrict__ rlow, double *sc, int *flags, double *part) {
+  if (flags[BF_DONE]) return;
+  double v = 0.0;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) {
+    const int c = (int)(t % k);
+    double ri = r[t];
+    if (col_active(flags, c)) {
+      const double a = sc[BS_ALPHA * k + c];
+      x[t] += a * p[t];
+      ri = ri - a * q[t];
+      r[t] = ri;
+    }
+    if (rlow) rlow[t] = (TX)ri;
+    v += ri * ri;
+  }
+  bfinish(v, k, part, flags, [&](int c, double tot) {
+    if (!col_active(flags, c)) return;
+    sc[BS_RR * k + c] = tot;
+    const int it = flags[BF_COL + k + c] + 1;
+    flags[BF_COL + k + c] = it;
+    if (!isfinite(tot)) {
+      flags[BF_STATUS] = AMG_ERR_BREAKDOWN;
+      flags[BF_COL + c] = 2;
+    } else if (tot <= sc[BS_TOL2 * k + c]) {
+      flags[BF_COL + c] = 1;
+    } else if (it >= flags[BF_MAXIT]) {
+      flags[BF_COL + c] = 3;
+    }
+  });
+}
+
+// z = (double) zlow ; rz_c (flexible: minus r.z_old) ; beta_c ; all-done test
+template <typename TX>
+__global__ void k_brz(long n, int k, const double *__restrict__ r, double *__restrict__ z, const TX *__restrict__ zlow,
+                      const double *__restrict__ zold, int flexible, double *sc, int *flags, double *part) {
+  if (flags[BF_DONE]) return;
+  double v = 0.0;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) {
+    double zi;
+    if (zlow) {
+      zi = (double)zlow[t];
+      z[t] = zi;
+    } else {
+      zi = z[t];
+    }
+    v += r[t] * (flexible ? zi - zold[t] : zi);
+  }
+  // for the flexible variant the sum above is r.(z - z_old); r.z itself is
+  // needed as the next rz: accumulate it in a second pass over the block
+  bfinish(v, k, part, flags, [&](int c, double tot) { sc[BS_BETA * k + c] = tot; });
+}
+
+// second reduction of the flexible variant: rz_c = r.z, then beta_c =
+// (r.(z - z_old)) / rz_prev (flexible) or rz_c / rz_prev
+__global__ void k_brz2(long n, int k, const double *__restrict__ r, const double *__restrict__ z, int flexible,
+                       double *sc, int *flags, double *part) {
+  if (flags[BF_DONE]) return;
+  double v = 0.0;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) v += r[t] * z[t];
+  bfinish(v, k, part, flags, [&](int c, double tot) {
+    const double prev = sc[BS_RZ * k + c];
+    const double num = flexible ? sc[BS_BETA * k + c] : tot;
+    if (col_active(flags, c)) {
+      sc[BS_BETA * k + c] = num / prev;
+      sc[BS_RZ * k + c] = tot;
+    }
+  });
+}
+
+// active columns: p = z + beta p (z_old = z); the last thread checks whether
+// every column has stopped
+__global__ void k_bp(long n, int k, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold,
+                     int flexible, const double *sc, int *flags) {
+  if (flags[BF_DONE]) return;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) {
+    const int c = (int)(t % k);
+    if (!col_active(flags, c)) continue;
+    p[t] = z[t] + sc[BS_BETA * k + c] * p[t];
+    if (flexible) zold[t] = z[t];
+  }
+}
+
+__global__ void k_bcheck(int k, int *flags) {
+  int all = 1;
+  for (int c = 0; c < k; ++c)
+    if (flags[BF_COL + c] == 0) all = 0;
+  if (all) flags[BF_DONE] = 1;
+}
+
+// first direction: p = z, z_old = z
+__global__ void k_bfirst(long n, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold) {
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    p[t] = z[t];
+    zold[t] = z[t];
+  }
+}
+
+// interleaved -> column-major
+__global__ void k_bout(long n, int k, const double *__restrict__ x, double *__restrict__ X) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const long d = t / k;
+  const int c = (int)(t - d * k);
+  X[(size_t)c * n + d] = x[t];
+}
+
+template <typename TX> struct BVec;
+template <> struct BVec<double> {
+  static double *y(BatchLevel &L) { return L.y64.p; }
+  static double *z(BatchLevel &L) { return L.z64.p; }
+  static double *s(BatchLevel &L) { return L.s64.p; }
+  static double *r(BatchLevel &L) { return L.r64.p; }
+  static double *t(BatchLevel &L) { return L.t64.p; }
+};
+template <> struct BVec<float> {
+  static float *y(BatchLevel &L) { return L.y32.p; }
+  static float *z(BatchLevel &L) { return L.z32.p; }
+  static float *s(BatchLevel &L) { return L.s32.p; }
+  static float *r(BatchLevel &L) { return L.r32.p; }
+  static float *t(BatchLevel &L) { return L.t32.p; }
+};
+
+template <typename TX>
+static void bvcycle(Handle *h, Batch &B, int lv, const TX *y, TX *z, const int *done) {
+  cudaStream_t st = h->stream;
+  const int k = B.k;
+  const bool b16 = h->prm.vcycle_prec == AMG_FP32_BF16GP;
+  if (lv == h->nlev - 1) {
+    const int m = h->nL;
+    if (!m) return;
+    AMG_KCOUNT k_btrmm_lower<TX><<<nblk((long)m * k, 256), 256, 0, st>>>(m, k, h->Linv.p, y, B.ctmp.p, done);
+    AMG_KCOUNT k_btrmm_upper<TX><<<nblk((long)m * k, 256), 256, 0, st>>>(m, k, h->LinvT.p, B.ctmp.p, z, done);
+    return;
+  }
+  Level &L = *h->lev[lv];
+  BatchLevel &BL = B.lev[lv], &BC = B.lev[lv + 1];
+  TX *s = BVec<TX>::s(BL), *r = BVec<TX>::r(BL), *t = BVec<TX>::t(BL);
+  const TX w = (TX)L.omega;
+  bmv<TX>(BE_SET, L.sG, b16, k, y, t, (const TX *)nullptr, w, done, st);
+  bmv<TX>(BE_SCALE, L.sGT, b16, k, t, s, (const TX *)nullptr, w, done, st);
+  bmv<TX>(BE_RESID, L.sA, false, k, s, r, y, w, done, st);
+  bmv<TX>(BE_SET, L.sR, b16, k, r, BVec<TX>::y(BC), (const TX *)nullptr, w, done, st);
+  bvcycle<TX>(h, B, lv + 1, BVec<TX>::y(BC), BVec<TX>::z(BC), done);
+  bmv<TX>(BE_ACC, L.sP, b16, k, BVec<TX>::z(BC), s, (const TX *)nullptr, w, done, st);
+  bmv<TX>(BE_RESID, L.sA, false, k, s, r, y, w, done, st);
+  bmv<TX>(BE_SET, L.sG, b16, k, r, t, (const TX *)nullptr, w, done, st);
+  bmv<TX>(BE_SADD, L.sGT, b16, k, t, z, s, w, done, st);
+}
+
+static int block_threads(int k) { return (256 / k) * k; }
+
+template <typename TX>
+static void biteration(Handle *h, Batch &B, bool mixed) {
+  cudaStream_t s = h->stream;
+  const int k = B.k;
+  const long n = 3L * h->n;
+  Level &L0 = *h->lev[0];
+  const int bt = block_threads(k);
+  const size_t shm = bt * sizeof(double);
+  int *fl = B.flags.p;
+  const int *done = fl + BF_DONE;
+  bmm<double, double>(BE_SET, L0.sA, L0.sA.v64.p, k, B.p.p, B.q.p, nullptr, 0.0, done, s);
+  AMG_KCOUNT k_bpq<<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.p.p, B.q.p, B.sc.p, fl, B.part.p);
+  if (mixed) {
+    AMG_KCOUNT k_bxr<float><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.x.p, B.r.p, B.p.p, B.q.p, B.rlow.p, B.sc.p, fl, B.part.p);
+    bvcycle<float>(h, B, 0, B.rlow.p, B.zlow.p, done);
+    AMG_KCOUNT k_brz<float><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.r.p, B.z.p, B.zlow.p, B.zold.p, 1, B.sc.p, fl, B.part.p);
+    AMG_KCOUNT k_brz2<<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.r.p, B.z.p, 1, B.sc.p, fl, B.part.p);
+    AMG_KCOUNT k_bp<<<BRED_BLOCKS, 256, 0, s>>>(n, k, B.p.p, B.z.p, B.zold.p, 1, B.sc.p, fl);
+  } else {
+    AMG_KCOUNT k_bxr<double><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.x.p, B.r.p, B.p.p, B.q.p, (double *)nullptr, B.sc.p, fl,
+                                                          B.part.p);
+    bvcycle<double>(h, B, 0, B.r.p, B.z.p, done);
+    AMG_KCOUNT k_brz2<<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.r.p, B.z.p, 0, B.sc.p, fl, B.part.p);
+    AMG_KCOUNT k_bp<<<BRED_BLOCKS, 256, 0, s>>>(n, k, B.p.p, B.z.p, B.zold.p, 0, B.sc.p, fl);
+  }
+  AMG_KCOUNT k_bcheck<<<1, 1, 0, s>>>(k, fl);
+}
+
+static int ensure_batch(Handle *h, Batch &B, int k) {
+  const int prec = h->prm.vcycle_prec;
+  if (B.k == k && B.prec == prec && B.x.p) return AMG_OK;
+  if (B.graph) {
+    cudaGraphExecDestroy(B.graph);
+    B.graph = nullptr;
+  }
+  B.k = k;
+  B.prec = prec;
+  const size_t nk = 3 * (size_t)h->n * k;
+  AMG_TRY(B.x.alloc(nk));
+  AMG_TRY(B.r.alloc(nk));
+  AMG_TRY(B.z.alloc(nk));
+  AMG_TRY(B.p.alloc(nk));
+  AMG_TRY(B.q.alloc(nk));
+  AMG_TRY(B.zold.alloc(nk));
+  AMG_TRY(B.sc.alloc((size_t)BS_NUM * k));
+  AMG_TRY(B.part.alloc((size_t)BRED_BLOCKS * k + 16));
+  AMG_TRY(B.flags.alloc(BF_COL + 2 * k + 8));
+  AMG_TRY(B.ctmp.alloc((size_t)(h->nL > 0 ? h->nL : 1) * k));
+  if (!B.pinned) AMG_CU(cudaMallocHost((void **)&B.pinned, 4 * sizeof(int)));
+  B.lev.clear();
+  B.lev.resize(h->nlev);
+  const bool mixed = prec != AMG_FP64;
+  if (mixed) {
+    AMG_TRY(B.rlow.alloc(nk));
+    AMG_TRY(B.zlow.alloc(nk));
+  }
+  for (int l = 0; l < h->nlev; ++l) {
+    const size_t m = 3 * (size_t)h->lev[l]->n * k;
+    BatchLevel &BL = B.lev[l];
+    if (mixed) {
+      if (l > 0) {
+        AMG_TRY(BL.y32.alloc(m));
+        AMG_TRY(BL.z32.alloc(m));
+      }
+      AMG_TRY(BL.s32.alloc(m));
+      AMG_TRY(BL.r32.alloc(m));
+      AMG_TRY(BL.t32.alloc(m));
+    } else {
+      if (l > 0) {
+        AMG_TRY(BL.y64.alloc(m));
+        AMG_TRY(BL.z64.alloc(m));
+      }
+      AMG_TRY(BL.s64.alloc(m));
+      AMG_TRY(BL.r64.alloc(m));
+      AMG_TRY(BL.t64.alloc(m));
+    }
+  }
+  return AMG_OK;
+}
+
+int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres) {
+  if (k > 256) {
+    // independent groups of at most 256 columns
+    int worst = AMG_OK;
+    const size_t n = 3 * (size_t)h->n;
+    for (int c0 = 0; c0 < k; c0 += 256) {
+      const int kk = k - c0 < 256 ? k - c0 : 256;
+      const int rc = solve_batched(h, kk, B + c0 * n, X + c0 * n, rtol, iters + c0, relres + c0);
+      if (rc == AMG_ERR_CUDA) return rc;
+      if (rc && !worst) worst = rc;
+    }
+    return worst;
+  }
+  if (!h->batch) h->batch = new Batch();
+  Batch &Bt = *h->batch;
+  AMG_TRY(ensure_batch(h, Bt, k));
+  cudaStream_t s = h->stream;
+  const long n = 3L * h->n;
+  const bool mixed = h->prm.vcycle_prec != AMG_FP64;
+  const int bt = block_threads(k);
+  const size_t shm = bt * sizeof(double);
+  int *fl = Bt.flags.p;
+  AMG_KCOUNT k_bflags<<<1, 1, 0, s>>>(k, h->prm.maxit, fl);
+  if (mixed) {
+    AMG_KCOUNT k_bstart<float><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B, Bt.x.p, Bt.r.p, Bt.rlow.p, rtol, Bt.sc.p, fl,
+                                                            Bt.part.p);
+    AMG_KCOUNT k_bcheck<<<1, 1, 0, s>>>(k, fl);
+    bvcycle<float>(h, Bt, 0, Bt.rlow.p, Bt.zlow.p, fl + BF_DONE);
+    AMG_KCOUNT k_brz<float><<<BRED_BLOCKS, bt, shm, s>>>(n, k, Bt.r.p, Bt.z.p, Bt.zlow.p, Bt.zold.p, 0, Bt.sc.p, fl,
+                                                         Bt.part.p);
+  } else {
+    AMG_KCOUNT k_bstart<double><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B, Bt.x.p, Bt.r.p, (double *)nullptr, rtol, Bt.sc.p,
+                                                             fl, Bt.part.p);
+    AMG_KCOUNT k_bcheck<<<1, 1, 0, s>>>(k, fl);
+    bvcycle<double>(h, Bt, 0, Bt.r.p, Bt.z.p, fl + BF_DONE);
+  }
+  AMG_KCOUNT k_brz2<<<BRED_BLOCKS, bt, shm, s>>>(n, k, Bt.r.p, Bt.z.p, 0, Bt.sc.p, fl, Bt.part.p);
+  AMG_KCOUNT k_bfirst<<<BRED_BLOCKS, 256, 0, s>>>(n * k, Bt.p.p, Bt.z.p, Bt.zold.p);
+  AMG_LAUNCH_CHECK();
+  if (!Bt.graph) {
+    cudaGraph_t g;
+    const long long before = launch_count();
+    AMG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    if (mixed) biteration<float>(h, Bt, true);
+    else biteration<double>(h, Bt, false);
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    Bt.graph_nodes = launch_count() - before;
+    count_launches(-Bt.graph_nodes);
+    if (ce != cudaSuccess) {
+      set_error("batched solve: graph capture failed: %s", cudaGetErrorString(ce));
+      return AMG_ERR_CUDA;
+    }
+    AMG_CU(cudaGraphInstantiate(&Bt.graph, g, 0));
+    cudaGraphDestroy(g);
+  }
+  const int chunk = 4;
+  int rc = AMG_OK;
+  for (int it = 0; it < h->prm.maxit + chunk; it += chunk) {
+    for (int c = 0; c < chunk; ++c) {
+      if (cudaGraphLaunch(Bt.graph, s) != cudaSuccess) {
+        set_error("batched solve: graph launch failed");
+        return AMG_ERR_CUDA;
+      }
+      count_launches(Bt.graph_nodes);
+    }
+    cudaMemcpyAsync(Bt.pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("batched solve: %s", cudaGetErrorString(e));
+      return AMG_ERR_CUDA;
+    }
+    if (Bt.pinned[0]) break;
+  }
+  AMG_KCOUNT k_bout<<<nblk(n * k, 256), 256, 0, s>>>(n, k, Bt.x.p, X);
+  AMG_LAUNCH_CHECK();
+  std::vector<int> hf(BF_COL + 2 * k);
+  std::vector<double> hs((size_t)BS_NUM * k);
+  AMG_CU(cudaMemcpyAsync(hf.data(), fl, hf.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CU(cudaMemcpyAsync(hs.data(), Bt.sc.p, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  int maxit = 0;
+  for (int c = 0; c < k; ++c) {
+    iters[c] = hf[BF_COL + k + c];
+    const double bn2 = hs[BS_BN2 * k + c];
+    relres[c] = bn2 > 0.0 ? std::sqrt(hs[BS_RR * k + c] / bn2) : 0.0;
+    if (bn2 == 0.0) relres[c] = 0.0;
+    const int st = hf[BF_COL + c];
+    if (st == 2) rc = AMG_ERR_BREAKDOWN;
+    else if ((st == 3 || st == 0) && rc == AMG_OK) rc = AMG_ERR_NOT_CONVERGED;
+    if (iters[c] > maxit) maxit = iters[c];
+  }
+  h->stats.n_it = maxit;
+  return rc;
+}
+
+void free_batch(Handle *h) {
+  delete h->batch;
+  h->batch = nullptr;
+}
+
+}  // namespace amg

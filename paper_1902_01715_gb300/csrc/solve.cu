@@ -259,6 +259,7 @@ int prepare_solve(Handle *h) {
   }
   h->kcap = 0;  // PCG work buffers are sized by the coarse level: reallocate
   h->x.release();
+  free_batch(h);
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
 }
@@ -678,6 +679,7 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
 }
 
 int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres) {
+  if (k > 1) return solve_batched(h, k, B, X, rtol, iters, relres);
   AMG_TRY(ensure_pcg(h));
   const long n = 3L * h->n;
   const bool mixed = h->prm.vcycle_prec != AMG_FP64;
@@ -834,6 +836,7 @@ int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, dou
 }
 
 Handle::~Handle() {
+  free_batch(this);
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   if (pinned) cudaFreeHost(pinned);
   lev.clear();
