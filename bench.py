@@ -343,7 +343,9 @@ def run_micro(args):
     S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec=args.prec)
     hbm = peaks().get("hbm_gbs", 6800.0)
     rows = []
+    torch.cuda.nvtx.range_push("spmv_A0_fp64")
     ms, by = S.bench_spmv(0, "A", a64=True, reps=args.reps)
+    torch.cuda.nvtx.range_pop()
     rows.append({"level": 0, "matrix": "A(fp64, CG)", "ms": ms, "GBps": by / ms / 1e6,
                  "frac": by / ms / 1e6 / hbm})
     for k in range(S.nlev - 1):

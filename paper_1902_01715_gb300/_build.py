@@ -25,6 +25,7 @@ UNITS = {
     "solve.cu": [],
     "capi.cu": [],
     "batch.cu": [],
+    "spmv.cu": [],
 }
 
 

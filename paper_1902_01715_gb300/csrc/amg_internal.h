@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <memory>
@@ -105,18 +106,74 @@ struct DevBsr {
   }
 };
 
-// Solve-phase copy of a level matrix: the 9 entries of every block stored as
-// 9 contiguous arrays ("entry-major"), so that the lanes of a warp reading
-// consecutive blocks of a row issue coalesced loads.
+// Solve-phase copy of a level matrix in the sliced layout of spmv.cu: block
+// rows in slices of 32, slice s owning slots [slp[s], slp[s+1]); slot
+// slp[s] + 32 j + l holds block j of row 32 s + l (column scol[slot], entry e
+// at 9 (slp[s] + 32 j) + 32 e + l of a value array).
 struct SolveMat {
   int nr = 0, nc = 0, nnzb = 0;
+  int ns = 0;      // slices
+  long nslot = 0;  // slots, including padding
   const int *rowptr = nullptr, *col = nullptr;
+  DBuf<int> slp, scol;
   DBuf<double> v64;
   DBuf<float> v32;
   DBuf<__nv_bfloat16> v16;
-  int lpr = 8;    // lanes per block row, FP32/bf16 storage (set by the autotuner)
-  int lpr64 = 4;  // lanes per block row, FP64 storage
+  int map = 0;    // warp mapping, FP32/bf16 storage (set by the autotuner)
+  int map64 = 0;  // warp mapping, FP64 storage
 };
+
+// Row accumulator of the solve-phase block products.  FP64: every product is one FMA into the running sum.
+// FP32: the 3 products of a block are fused into a block partial, which is
+// added to the running sum with an error-free two-sum (Knuth), the rounding
+// errors being collected in a second word.  Stiffness rows cancel strongly
+// (K applied to a smooth vector), and an FP32 V-cycle whose residual
+// y - A s carries the rounding of a plain 81-term FP32 sum preconditions
+// visibly worse; the compensated sum costs a few FP32 additions, which this
+// HBM-bound product has to spare.
+template <typename TX> struct RowAcc;
+template <> struct RowAcc<double> {
+  double s[3] = {0.0, 0.0, 0.0};
+  __device__ __forceinline__ void add(int r, double m0, double m1, double m2, double x0, double x1, double x2) {
+    s[r] = fma(m0, x0, s[r]);
+    s[r] = fma(m1, x1, s[r]);
+    s[r] = fma(m2, x2, s[r]);
+  }
+  __device__ __forceinline__ void merge(int r, double hi, double) { s[r] += hi; }
+  __device__ __forceinline__ double hi(int r) const { return s[r]; }
+  __device__ __forceinline__ double lo(int) const { return 0.0; }
+  __device__ __forceinline__ double get(int r) const { return s[r]; }
+};
+template <> struct RowAcc<float> {
+  float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void two_sum(int r, float t) {
+    const float a = s[r], u = __fadd_rn(a, t);
+    const float bp = __fsub_rn(u, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(u, bp)), __fsub_rn(t, bp));
+    s[r] = u;
+    c[r] = __fadd_rn(c[r], err);
+  }
+  __device__ __forceinline__ void add(int r, float m0, float m1, float m2, float x0, float x1, float x2) {
+    two_sum(r, fmaf(m2, x2, fmaf(m1, x1, __fmul_rn(m0, x0))));
+  }
+  __device__ __forceinline__ void merge(int r, float hi, float lo) {
+    two_sum(r, hi);
+    c[r] = __fadd_rn(c[r], lo);
+  }
+  __device__ __forceinline__ float hi(int r) const { return s[r]; }
+  __device__ __forceinline__ float lo(int r) const { return c[r]; }
+  __device__ __forceinline__ float get(int r) const { return __fadd_rn(s[r], c[r]); }
+};
+
+// y = epilogue(A x): EP_SET y = Ax; EP_SCALE y = w Ax; EP_RESID y = aux - Ax;
+// EP_SADD y = aux + w Ax; EP_ACC y += Ax.
+enum { EP_SET = 0, EP_SCALE = 1, EP_RESID = 2, EP_SADD = 3, EP_ACC = 4 };
+template <typename TM, typename TX>
+void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
+           cudaStream_t s);
+int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s);
+int tune_solvemat(SolveMat &M, int kind, cudaStream_t s);  // kind 0 FP64, 1 FP32, 2 bf16
+const char *mapping_name(const SolveMat &M, bool f64);
 
 struct Level {
   int n = 0;  // nodes

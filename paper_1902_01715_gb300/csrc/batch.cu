@@ -22,38 +22,42 @@ __device__ __forceinline__ float cvb(__nv_bfloat16 v, float) { return __bfloat16
 
 enum { BE_SET = 0, BE_SCALE = 1, BE_RESID = 2, BE_SADD = 3, BE_ACC = 4 };
 
-// Y = epilogue(A X) on interleaved n x k blocks; one warp per block row.
+// Y = epilogue(A X) on interleaved n x k blocks; one warp per block row of
+// the sliced layout (every lane reads the same block: a broadcast).
 template <typename TM, typename TX, int EP>
-__global__ void __launch_bounds__(256) k_bsrmm(int nr, int k, const int *__restrict__ rp, const int *__restrict__ col,
-                                               const TM *__restrict__ v, long nnzb, const TX *__restrict__ X,
-                                               TX *__restrict__ Y, const TX *__restrict__ AUX, TX w,
-                                               const int *__restrict__ done) {
+__global__ void __launch_bounds__(256) k_bsrmm(int nr, int k, const int *__restrict__ rp, const int *__restrict__ slp,
+                                               const int *__restrict__ scol, const TM *__restrict__ v,
+                                               const TX *__restrict__ X, TX *__restrict__ Y,
+                                               const TX *__restrict__ AUX, TX w, const int *__restrict__ done) {
   if (done && *done) return;
   const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= nr) return;
-  const int kb = rp[row], ke = rp[row + 1];
+  const int len = rp[row + 1] - rp[row];
+  const long base = (long)slp[row >> 5] + (row & 31);
   for (int c0 = 0; c0 < k; c0 += 64) {
     const int ca = c0 + lane, cb = c0 + 32 + lane;
     const bool va = ca < k, vb = cb < k;
-    TX a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
-    for (int q = kb; q < ke; ++q) {
-      const long j = col[q];
-      const TX m0 = cvb(v[q], TX(0)), m1 = cvb(v[nnzb + q], TX(0)), m2 = cvb(v[2 * nnzb + q], TX(0));
-      const TX m3 = cvb(v[3 * nnzb + q], TX(0)), m4 = cvb(v[4 * nnzb + q], TX(0)), m5 = cvb(v[5 * nnzb + q], TX(0));
-      const TX m6 = cvb(v[6 * nnzb + q], TX(0)), m7 = cvb(v[7 * nnzb + q], TX(0)), m8 = cvb(v[8 * nnzb + q], TX(0));
+    RowAcc<TX> a, b;
+    for (int q = 0; q < len; ++q) {
+      const long slot = base + 32L * q;
+      const long j = scol[slot];
+      const TM *mp = v + 9 * (slot - (row & 31)) + (row & 31);
+      const TX m0 = cvb(mp[0], TX(0)), m1 = cvb(mp[32], TX(0)), m2 = cvb(mp[64], TX(0));
+      const TX m3 = cvb(mp[96], TX(0)), m4 = cvb(mp[128], TX(0)), m5 = cvb(mp[160], TX(0));
+      const TX m6 = cvb(mp[192], TX(0)), m7 = cvb(mp[224], TX(0)), m8 = cvb(mp[256], TX(0));
       const TX *xj = X + 3 * j * k;
       if (va) {
         const TX x0 = xj[ca], x1 = xj[k + ca], x2 = xj[2 * k + ca];
-        a0 += m0 * x0 + m1 * x1 + m2 * x2;
-        a1 += m3 * x0 + m4 * x1 + m5 * x2;
-        a2 += m6 * x0 + m7 * x1 + m8 * x2;
+        a.add(0, m0, m1, m2, x0, x1, x2);
+        a.add(1, m3, m4, m5, x0, x1, x2);
+        a.add(2, m6, m7, m8, x0, x1, x2);
       }
       if (vb) {
         const TX x0 = xj[cb], x1 = xj[k + cb], x2 = xj[2 * k + cb];
-        b0 += m0 * x0 + m1 * x1 + m2 * x2;
-        b1 += m3 * x0 + m4 * x1 + m5 * x2;
-        b2 += m6 * x0 + m7 * x1 + m8 * x2;
+        b.add(0, m0, m1, m2, x0, x1, x2);
+        b.add(1, m3, m4, m5, x0, x1, x2);
+        b.add(2, m6, m7, m8, x0, x1, x2);
       }
     }
     const long o = 3L * row * k;
@@ -66,8 +70,8 @@ __global__ void __launch_bounds__(256) k_bsrmm(int nr, int k, const int *__restr
       if (EP == BE_SADD) { y[0] = ax[0] + w * s0; y[k] = ax[k] + w * s1; y[2 * k] = ax[2 * k] + w * s2; }
       if (EP == BE_ACC) { y[0] += s0; y[k] += s1; y[2 * k] += s2; }
     };
-    if (va) put(ca, a0, a1, a2);
-    if (vb) put(cb, b0, b1, b2);
+    if (va) put(ca, a.get(0), a.get(1), a.get(2));
+    if (vb) put(cb, b.get(0), b.get(1), b.get(2));
   }
 }
 
@@ -77,11 +81,11 @@ static void bmm(int ep, const SolveMat &M, const TM *v, int k, const TX *X, TX *
   const int nb = nblk(32L * M.nr, 256);
   if (!nb) return;
   switch (ep) {
-    case BE_SET: AMG_KCOUNT k_bsrmm<TM, TX, BE_SET><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
-    case BE_SCALE: AMG_KCOUNT k_bsrmm<TM, TX, BE_SCALE><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
-    case BE_RESID: AMG_KCOUNT k_bsrmm<TM, TX, BE_RESID><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
-    case BE_SADD: AMG_KCOUNT k_bsrmm<TM, TX, BE_SADD><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
-    default: AMG_KCOUNT k_bsrmm<TM, TX, BE_ACC><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.col, v, M.nnzb, X, Y, AUX, w, done); break;
+    case BE_SET: AMG_KCOUNT k_bsrmm<TM, TX, BE_SET><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
+    case BE_SCALE: AMG_KCOUNT k_bsrmm<TM, TX, BE_SCALE><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
+    case BE_RESID: AMG_KCOUNT k_bsrmm<TM, TX, BE_RESID><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
+    case BE_SADD: AMG_KCOUNT k_bsrmm<TM, TX, BE_SADD><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
+    default: AMG_KCOUNT k_bsrmm<TM, TX, BE_ACC><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
   }
 }
 

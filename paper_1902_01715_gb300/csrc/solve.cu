@@ -3,12 +3,11 @@
 // M^{-1} = omega G^T G is symmetric, Sec. 2), with the FP64 CG recurrence of
 // Sec. 4 (x0 = 0, stop at ||r||_2 <= rtol ||b||_2).
 //
-// Every level matrix is stored "entry-major": entry e (0..8) of block k at
-// v[e*nnzb + k], so the LPR lanes that share a block row read consecutive
-// blocks with coalesced loads.  One sparse kernel computes y = A x with a
-// fused epilogue (plain, scaled, residual, scaled-add, accumulate), which
-// covers the two smoother products, the residual, restriction and
-// prolongation.  The V-cycle runs in FP64, FP32, or FP32 with bf16-stored
+// Every level matrix is stored in the sliced layout of spmv.cu (32 block
+// rows per slice, one lane per row, coalesced entry loads).  One sparse
+// kernel computes y = A x with a fused epilogue (plain, scaled, residual,
+// scaled-add, accumulate), which covers the two smoother products, the
+// residual, restriction and prolongation.  The V-cycle runs in FP64, FP32, or FP32 with bf16-stored
 // G, G^T, P, R; the CG recurrence, its reductions and the coarse solve are
 // FP64 in every mode.  One PCG iteration is captured in a CUDA graph; each
 // kernel returns at once when the device-side `done` flag is set, so the
@@ -24,204 +23,6 @@ namespace amg {
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
-template <typename T> struct Acc;
-template <> struct Acc<double> { typedef double type; };
-template <> struct Acc<float> { typedef float type; };
-
-__device__ __forceinline__ double cvt(double v, double) { return v; }
-__device__ __forceinline__ float cvt(float v, float) { return v; }
-__device__ __forceinline__ float cvt(__nv_bfloat16 v, float) { return __bfloat162float(v); }
-__device__ __forceinline__ double cvt(float v, double) { return (double)v; }
-
-enum { EP_SET = 0, EP_SCALE = 1, EP_RESID = 2, EP_SADD = 3, EP_ACC = 4 };
-
-// y = epilogue(A x): EP_SET y = Ax; EP_SCALE y = w Ax; EP_RESID y = aux - Ax;
-// EP_SADD y = aux + w Ax; EP_ACC y += Ax.
-template <int LPR, typename TM, typename TX, int EP>
-__global__ void __launch_bounds__(256) k_bsrmv(int nr, const int *__restrict__ rp, const int *__restrict__ col,
-                                               const TM *__restrict__ v, long nnzb, const TX *__restrict__ x,
-                                               TX *__restrict__ y, const TX *__restrict__ aux, TX w,
-                                               const int *__restrict__ done) {
-  if (done && *done) return;
-  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int row = (int)(gt / LPR);
-  const int lane = (int)(gt & (LPR - 1));
-  const bool valid = row < nr;
-  TX a0 = 0, a1 = 0, a2 = 0;
-  if (valid) {
-    const int ke = rp[row + 1];
-    for (int k = rp[row] + lane; k < ke; k += LPR) {
-      const long j = col[k];
-      const TX x0 = x[3 * j], x1 = x[3 * j + 1], x2 = x[3 * j + 2];
-      a0 += cvt(v[k], TX(0)) * x0 + cvt(v[nnzb + k], TX(0)) * x1 + cvt(v[2 * nnzb + k], TX(0)) * x2;
-      a1 += cvt(v[3 * nnzb + k], TX(0)) * x0 + cvt(v[4 * nnzb + k], TX(0)) * x1 + cvt(v[5 * nnzb + k], TX(0)) * x2;
-      a2 += cvt(v[6 * nnzb + k], TX(0)) * x0 + cvt(v[7 * nnzb + k], TX(0)) * x1 + cvt(v[8 * nnzb + k], TX(0)) * x2;
-    }
-  }
-#pragma unroll
-  for (int off = LPR / 2; off > 0; off >>= 1) {
-    a0 += __shfl_xor_sync(0xffffffffu, a0, off, LPR);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, off, LPR);
-    a2 += __shfl_xor_sync(0xffffffffu, a2, off, LPR);
-  }
-  if (valid && lane == 0) {
-    const long o = 3L * row;
-    if (EP == EP_SET) { y[o] = a0; y[o + 1] = a1; y[o + 2] = a2; }
-    if (EP == EP_SCALE) { y[o] = w * a0; y[o + 1] = w * a1; y[o + 2] = w * a2; }
-    if (EP == EP_RESID) { y[o] = aux[o] - a0; y[o + 1] = aux[o + 1] - a1; y[o + 2] = aux[o + 2] - a2; }
-    if (EP == EP_SADD) { y[o] = aux[o] + w * a0; y[o + 1] = aux[o + 1] + w * a1; y[o + 2] = aux[o + 2] + w * a2; }
-    if (EP == EP_ACC) { y[o] += a0; y[o + 1] += a1; y[o + 2] += a2; }
-  }
-}
-
-template <int LPR, typename TM, typename TX>
-static void launch_lpr(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
-                       const int *done, cudaStream_t s) {
-  const int nb = nblk((long)M.nr * LPR, 256);
-  if (nb == 0) return;
-  switch (ep) {
-    case EP_SET: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_SET><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-    case EP_SCALE: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_SCALE><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-    case EP_RESID: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_RESID><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-    case EP_SADD: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_SADD><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-    default: AMG_KCOUNT k_bsrmv<LPR, TM, TX, EP_ACC><<<nb, 256, 0, s>>>(M.nr, M.rowptr, M.col, v, M.nnzb, x, y, aux, w, done); break;
-  }
-}
-
-template <typename TM, typename TX>
-static void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
-                  cudaStream_t s) {
-  switch (std::is_same<TM, double>::value ? M.lpr64 : M.lpr) {
-    case 4: launch_lpr<4>(ep, M, v, x, y, aux, w, done, s); break;
-    case 8: launch_lpr<8>(ep, M, v, x, y, aux, w, done, s); break;
-    case 16: launch_lpr<16>(ep, M, v, x, y, aux, w, done, s); break;
-    default: launch_lpr<32>(ep, M, v, x, y, aux, w, done, s); break;
-  }
-}
-
-// ---------------------------------------------------------------- layout
-template <typename T>
-__global__ void k_entry_major(long nnzb, const double *__restrict__ src, T *__restrict__ dst) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 9 * nnzb) return;
-  const long k = t / 9;
-  const int e = (int)(t % 9);
-  dst[e * nnzb + k] = (T)src[t];
-}
-
-template <>
-__global__ void k_entry_major<__nv_bfloat16>(long nnzb, const double *__restrict__ src, __nv_bfloat16 *__restrict__ dst) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 9 * nnzb) return;
-  const long k = t / 9;
-  const int e = (int)(t % 9);
-  dst[e * nnzb + k] = __float2bfloat16_rn((float)src[t]);
-}
-
-// Row-length rule for matrices too small to tune.  FP64 arithmetic is scarce
-// on this GPU, so FP64 storage prefers few lanes per row (fewer shuffle-add
-// reduction steps per row).
-static int pick_lpr(const DevBsr &A) {
-  const double avg = A.nr ? (double)A.nnzb / A.nr : 1.0;
-  if (avg <= 5.0) return 4;
-  if (avg <= 10.0) return 8;
-  if (avg <= 20.0) return 16;
-  return 32;
-}
-
-static int pick_lpr64(const DevBsr &A) {
-  const double avg = A.nr ? (double)A.nnzb / A.nr : 1.0;
-  return avg <= 40.0 ? 4 : 8;
-}
-
-static int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s) {
-  M.nr = A.nr;
-  M.nc = A.nc;
-  M.nnzb = A.nnzb;
-  M.rowptr = A.rowptr.p;
-  M.col = A.col.p;
-  M.lpr = pick_lpr(A);
-  M.lpr64 = pick_lpr64(A);
-  const long n9 = 9L * A.nnzb;
-  const int nb = nblk(n9, 256);
-  if (f64) {
-    AMG_TRY(M.v64.alloc(n9));
-    if (nb) AMG_KCOUNT k_entry_major<double><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v64.p);
-  }
-  if (f32) {
-    AMG_TRY(M.v32.alloc(n9));
-    if (nb) AMG_KCOUNT k_entry_major<float><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v32.p);
-  }
-  if (b16) {
-    AMG_TRY(M.v16.alloc(n9));
-    if (nb) AMG_KCOUNT k_entry_major<__nv_bfloat16><<<nb, 256, 0, s>>>(A.nnzb, A.val.p, M.v16.p);
-  }
-  AMG_LAUNCH_CHECK();
-  return AMG_OK;
-}
-
-// ---------------------------------------------------------------- autotuner
-// Lanes per block row of the sparse kernel, chosen by timing LPR = 4, 8, 16,
-// 32 on the matrix itself (CUDA events, one warm-up and three timed launches
-// each).  The winner is cached per (storage type, average row length) so that
-// every matrix of that kind in the process uses the same mapping; small
-// matrices (latency-bound) keep the row-length rule.
-static std::mutex g_tune_mu;
-static std::vector<std::pair<long, int>> g_tune_cache;
-
-template <typename TM, typename TX>
-static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
-  const double avg = M.nr ? (double)M.nnzb / M.nr : 1.0;
-  const long key = (long)kind * 100000 + (long)(avg * 4.0 + 0.5);
-  {
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    for (auto &e : g_tune_cache)
-      if (e.first == key) {
-        (std::is_same<TM, double>::value ? M.lpr64 : M.lpr) = e.second;
-        return AMG_OK;
-      }
-  }
-  DBuf<TX> x, y;
-  AMG_TRY(x.alloc(3 * (size_t)M.nc));
-  AMG_TRY(y.alloc(3 * (size_t)M.nr));
-  AMG_TRY(x.zero(s));
-  cudaEvent_t e0, e1;
-  AMG_CU(cudaEventCreate(&e0));
-  AMG_CU(cudaEventCreate(&e1));
-  const int cand[4] = {4, 8, 16, 32};
-  int &lpr = std::is_same<TM, double>::value ? M.lpr64 : M.lpr;
-  float best = 1e30f;
-  int bl = lpr;
-  for (int c = 0; c < 4; ++c) {
-    lpr = cand[c];
-    bsrmv<TM, TX>(EP_SET, M, v, x.p, y.p, (const TX *)nullptr, TX(0), nullptr, s);
-    AMG_CU(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) bsrmv<TM, TX>(EP_SET, M, v, x.p, y.p, (const TX *)nullptr, TX(0), nullptr, s);
-    AMG_CU(cudaEventRecord(e1, s));
-    AMG_CU(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    AMG_CU(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
-      bl = cand[c];
-    }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  AMG_LAUNCH_CHECK();
-  lpr = bl;
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_cache.push_back({key, bl});
-  return AMG_OK;
-}
-
-static int tune(SolveMat &M, int kind, cudaStream_t s) {
-  if (M.nnzb < 100000 || getenv("AMG_NO_TUNE")) return AMG_OK;
-  if (kind == 0) return tune_one<double, double>(M, M.v64.p, s, 0);
-  if (kind == 1) return tune_one<float, float>(M, M.v32.p, s, 1);
-  return tune_one<__nv_bfloat16, float>(M, M.v16.p, s, 2);
-}
-
 int prepare_solve(Handle *h) {
   cudaStream_t s = h->stream;
   const int prec = h->prm.vcycle_prec;
@@ -231,17 +32,17 @@ int prepare_solve(Handle *h) {
     Level &L = *h->lev[k];
     // level 0 A is always kept in FP64 for the outer CG operator
     AMG_TRY(make_solvemat(L.A, L.sA, f64 || k == 0, f32, false, s));
-    AMG_TRY(tune(L.sA, kv, s));
-    if (k == 0 && !f64) AMG_TRY(tune(L.sA, 0, s));  // FP64 copy of the CG operator
+    AMG_TRY(tune_solvemat(L.sA, kv, s));
+    if (k == 0 && !f64) AMG_TRY(tune_solvemat(L.sA, 0, s));  // FP64 copy of the CG operator
     if (k < h->nlev - 1) {
       AMG_TRY(make_solvemat(L.G, L.sG, f64, f32 && !b16, b16, s));
       AMG_TRY(make_solvemat(L.GT, L.sGT, f64, f32 && !b16, b16, s));
       AMG_TRY(make_solvemat(L.P, L.sP, f64, f32 && !b16, b16, s));
       AMG_TRY(make_solvemat(L.R, L.sR, f64, f32 && !b16, b16, s));
-      AMG_TRY(tune(L.sG, kg, s));
-      AMG_TRY(tune(L.sGT, kg, s));
-      AMG_TRY(tune(L.sP, kg, s));
-      AMG_TRY(tune(L.sR, kg, s));
+      AMG_TRY(tune_solvemat(L.sG, kg, s));
+      AMG_TRY(tune_solvemat(L.sGT, kg, s));
+      AMG_TRY(tune_solvemat(L.sP, kg, s));
+      AMG_TRY(tune_solvemat(L.sR, kg, s));
     }
     const size_t n3 = 3 * (size_t)L.n;
     if (f64) {

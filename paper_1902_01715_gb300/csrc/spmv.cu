@@ -1,0 +1,304 @@
+// Solve-phase sparse products y = epilogue(A x) over 3x3-block matrices
+// (the level matrices A_k, the smoother factors G_k and G_k^T, P_k and
+// R_k = P_k^T of the V-cycle, Algorithm 2), in a sliced layout built for
+// coalesced streaming from HBM.
+//
+// Layout ("SELL-32" over block rows).  Block rows are grouped in slices of 32
+// consecutive rows.  Slice s owns the slot range [slp[s], slp[s+1]), whose
+// length is 32 x (longest row of the slice).  Slot slp[s] + 32 j + l holds
+// block j of row 32 s + l: its column in scol[slot] and its 9 entries
+// (row-major within the block) at v[9 (slp[s] + 32 j) + 32 e + l], e = 0..8.
+// So the 32 lanes of a warp, one block row each, read every entry of their
+// j-th blocks with one fully used 32-element load per entry, and a slice is
+// one contiguous run of memory.  Padding slots (rows shorter than the
+// slice's longest) are never read: each lane stops at its own row length.
+//
+// Mapping.  A CTA of 128 threads holds 4 warps; WPS warps share one slice
+// (warp p of the slice takes blocks j = p, p + WPS, ...) and their partial
+// sums are added in warp order through shared memory, so small coarse
+// levels still spread over the SMs.  In FP64 every product is one fused
+// multiply-add into the row's accumulator (9 per block): FP64 arithmetic is
+// the scarce resource of this GPU (about 0.63e12 FP64 FMA/s against
+// 6.7 TB/s of HBM, i.e. 10.6 bytes per FMA, while an FP64 block brings 8.4
+// bytes per FMA), so the FP64 product is bounded by the FP64 pipe and must
+// spend nothing else there; FP32 and bf16 storage are HBM-bound.  Each
+// warp issues the loads of U blocks before it uses any of them.  (WPS, U)
+// is picked per matrix by timing the candidates on the matrix itself.
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "amg_internal.h"
+
+namespace amg {
+
+static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
+
+__device__ __forceinline__ double cvs(double v, double) { return v; }
+__device__ __forceinline__ float cvs(float v, float) { return v; }
+__device__ __forceinline__ float cvs(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+
+struct Mapping {
+  int wps, u;
+};
+static const Mapping kMaps[] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}, {4, 4}};
+constexpr int kNumMaps = (int)(sizeof(kMaps) / sizeof(kMaps[0]));
+
+template <typename TM, typename TX, int EP, int WPS, int U>
+__global__ void __launch_bounds__(128) k_sellmv(int nr, const int *__restrict__ rp, const int *__restrict__ slp,
+                                                const int *__restrict__ scol, const TM *__restrict__ v,
+                                                const TX *__restrict__ x, TX *__restrict__ y,
+                                                const TX *__restrict__ aux, TX w, const int *__restrict__ done) {
+  if (done && *done) return;
+  constexpr int SPB = 4 / WPS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sl = blockIdx.x * SPB + warp / WPS;
+  const int part = warp % WPS;
+  const int row = sl * 32 + lane;
+  const bool valid = row < nr;
+  const int len = valid ? rp[row + 1] - rp[row] : 0;
+  const long base = valid ? (long)slp[sl] : 0L;
+  RowAcc<TX> acc;
+  for (int j0 = part; j0 < len; j0 += WPS * U) {
+    int c[U];
+    TM m[U][9];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u * WPS;
+      if (j < len) {
+        const long slot = base + 32L * j;
+        c[u] = scol[slot + lane];
+        const TM *vp = v + 9 * slot + lane;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) m[u][e] = vp[32 * e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u * WPS;
+      if (j < len) {
+        const TX *xp = x + 3L * c[u];
+        const TX x0 = xp[0], x1 = xp[1], x2 = xp[2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          acc.add(r, cvs(m[u][3 * r], TX(0)), cvs(m[u][3 * r + 1], TX(0)), cvs(m[u][3 * r + 2], TX(0)), x0, x1, x2);
+      }
+    }
+  }
+  if (WPS > 1) {
+    __shared__ TX red[4][6][32];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      red[warp][r][lane] = acc.hi(r);
+      red[warp][3 + r][lane] = acc.lo(r);
+    }
+    __syncthreads();
+    if (part != 0) return;
+#pragma unroll
+    for (int p = 1; p < WPS; ++p)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) acc.merge(r, red[warp + p][r][lane], red[warp + p][3 + r][lane]);
+  }
+  const TX a0 = acc.get(0), a1 = acc.get(1), a2 = acc.get(2);
+  if (!valid) return;
+  const long o = 3L * row;
+  if (EP == EP_SET) { y[o] = a0; y[o + 1] = a1; y[o + 2] = a2; }
+  if (EP == EP_SCALE) { y[o] = w * a0; y[o + 1] = w * a1; y[o + 2] = w * a2; }
+  if (EP == EP_RESID) { y[o] = aux[o] - a0; y[o + 1] = aux[o + 1] - a1; y[o + 2] = aux[o + 2] - a2; }
+  if (EP == EP_SADD) { y[o] = aux[o] + w * a0; y[o + 1] = aux[o + 1] + w * a1; y[o + 2] = aux[o + 2] + w * a2; }
+  if (EP == EP_ACC) { y[o] += a0; y[o + 1] += a1; y[o + 2] += a2; }
+}
+
+template <typename TM, typename TX, int WPS, int U>
+static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
+                       const int *done, cudaStream_t s) {
+  const int nb = nblk(M.ns, 4 / WPS);
+  if (nb == 0) return;
+#define AMG_SELL_ARGS M.nr, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
+  switch (ep) {
+    case EP_SET: AMG_KCOUNT k_sellmv<TM, TX, EP_SET, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SCALE: AMG_KCOUNT k_sellmv<TM, TX, EP_SCALE, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_RESID: AMG_KCOUNT k_sellmv<TM, TX, EP_RESID, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SADD: AMG_KCOUNT k_sellmv<TM, TX, EP_SADD, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
+    default: AMG_KCOUNT k_sellmv<TM, TX, EP_ACC, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
+  }
+#undef AMG_SELL_ARGS
+}
+
+template <typename TM, typename TX>
+void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
+           cudaStream_t s) {
+  switch (std::is_same<TM, double>::value ? M.map64 : M.map) {
+    case 0: launch_map<TM, TX, 1, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 1: launch_map<TM, TX, 1, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 2: launch_map<TM, TX, 2, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 3: launch_map<TM, TX, 2, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 4: launch_map<TM, TX, 4, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    default: launch_map<TM, TX, 4, 4>(ep, M, v, x, y, aux, w, done, s); break;
+  }
+}
+
+template void bsrmv<double, double>(int, const SolveMat &, const double *, const double *, double *, const double *,
+                                    double, const int *, cudaStream_t);
+template void bsrmv<float, float>(int, const SolveMat &, const float *, const float *, float *, const float *, float,
+                                  const int *, cudaStream_t);
+template void bsrmv<__nv_bfloat16, float>(int, const SolveMat &, const __nv_bfloat16 *, const float *, float *,
+                                          const float *, float, const int *, cudaStream_t);
+
+// ---------------------------------------------------------------- layout
+// One thread per block row copies its blocks into the slice layout (and, for
+// the first value array, the column indices); lanes of a warp write
+// consecutive slots.
+template <typename T>
+__device__ __forceinline__ T from_f64(double a);
+template <> __device__ __forceinline__ double from_f64<double>(double a) { return a; }
+template <> __device__ __forceinline__ float from_f64<float>(double a) { return (float)a; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double a) {
+  return __float2bfloat16_rn((float)a);
+}
+
+template <typename T>
+__global__ void k_to_sell(int nr, const int *__restrict__ rp, const int *__restrict__ col,
+                          const double *__restrict__ src, const int *__restrict__ slp, int *__restrict__ scol,
+                          T *__restrict__ dst) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nr) return;
+  const int sl = row >> 5, lane = row & 31;
+  const int kb = rp[row], len = rp[row + 1] - kb;
+  const long base = slp[sl];
+  for (int j = 0; j < len; ++j) {
+    const long slot = base + 32L * j;
+    if (scol) scol[slot + lane] = col[kb + j];
+    const double *b = src + 9L * (kb + j);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) dst[9 * slot + 32 * e + lane] = from_f64<T>(b[e]);
+  }
+}
+
+// Mapping rule for matrices too small to time: short rows or few slices
+// leave SMs idle unless several warps share a slice.
+static int rule_map(const SolveMat &M) {
+  if (M.ns < 1024) return 4;  // WPS 4, U 2
+  if (M.ns < 4096) return 2;  // WPS 2, U 2
+  return 0;                   // WPS 1, U 2
+}
+
+int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s) {
+  M.nr = A.nr;
+  M.nc = A.nc;
+  M.nnzb = A.nnzb;
+  M.rowptr = A.rowptr.p;
+  M.col = A.col.p;
+  M.ns = (A.nr + 31) / 32;
+  std::vector<int> hs(M.ns + 1, 0);
+  long tot = 0;
+  for (int sl = 0; sl < M.ns; ++sl) {
+    int mx = 0;
+    const int r1 = std::min(A.nr, 32 * sl + 32);
+    for (int r = 32 * sl; r < r1; ++r) mx = std::max(mx, A.h_rowptr[r + 1] - A.h_rowptr[r]);
+    hs[sl] = (int)tot;
+    tot += 32L * mx;
+  }
+  if (tot > 0x7fffffffL) {
+    set_error("matrix too large for 32-bit slot offsets (%ld slots)", tot);
+    return AMG_ERR_ARG;
+  }
+  hs[M.ns] = (int)tot;
+  M.nslot = tot;
+  AMG_TRY(M.slp.alloc(M.ns + 1));
+  AMG_CU(cudaMemcpyAsync(M.slp.p, hs.data(), (M.ns + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMG_TRY(M.scol.alloc(tot));
+  M.map = M.map64 = rule_map(M);
+  const long n9 = 9L * tot;
+  const int nb = nblk(A.nr, 128);
+  int *cols = M.scol.p;
+  if (f64) {
+    AMG_TRY(M.v64.alloc(n9));
+    if (nb) AMG_KCOUNT k_to_sell<double><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, M.v64.p);
+    cols = nullptr;
+  }
+  if (f32) {
+    AMG_TRY(M.v32.alloc(n9));
+    if (nb) AMG_KCOUNT k_to_sell<float><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, M.v32.p);
+    cols = nullptr;
+  }
+  if (b16) {
+    AMG_TRY(M.v16.alloc(n9));
+    if (nb)
+      AMG_KCOUNT k_to_sell<__nv_bfloat16><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols,
+                                                               M.v16.p);
+  }
+  AMG_LAUNCH_CHECK();
+  // the host slice offsets must outlive the asynchronous copy
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// The (WPS, U) mapping is chosen by timing every candidate on the matrix
+// itself (CUDA events, one warm-up and three timed launches each).  The
+// winner is cached per (storage type, slice count, average row length) so
+// that later hierarchies of the same shape reuse it; matrices too small to
+// time keep the rule.
+static std::mutex g_tune_mu;
+static std::vector<std::pair<long long, int>> g_tune_cache;
+
+template <typename TM, typename TX>
+static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
+  const double avg = M.nr ? (double)M.nnzb / M.nr : 1.0;
+  const long long key = ((long long)kind << 56) | ((long long)M.ns << 20) | (long long)(avg * 16.0 + 0.5);
+  int &map = std::is_same<TM, double>::value ? M.map64 : M.map;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto &e : g_tune_cache)
+      if (e.first == key) {
+        map = e.second;
+        return AMG_OK;
+      }
+  }
+  DBuf<TX> x, y;
+  AMG_TRY(x.alloc(3 * (size_t)M.nc));
+  AMG_TRY(y.alloc(3 * (size_t)M.nr));
+  AMG_TRY(x.zero(s));
+  cudaEvent_t e0, e1;
+  AMG_CU(cudaEventCreate(&e0));
+  AMG_CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bm = map;
+  for (int c = 0; c < kNumMaps; ++c) {
+    map = c;
+    bsrmv<TM, TX>(EP_SET, M, v, x.p, y.p, (const TX *)nullptr, TX(0), nullptr, s);
+    AMG_CU(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) bsrmv<TM, TX>(EP_SET, M, v, x.p, y.p, (const TX *)nullptr, TX(0), nullptr, s);
+    AMG_CU(cudaEventRecord(e1, s));
+    AMG_CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      bm = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  AMG_LAUNCH_CHECK();
+  map = bm;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.push_back({key, bm});
+  return AMG_OK;
+}
+
+int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
+  if (M.nnzb < 100000 || getenv("AMG_NO_TUNE")) return AMG_OK;
+  if (kind == 0) return tune_one<double, double>(M, M.v64.p, s, 0);
+  if (kind == 1) return tune_one<float, float>(M, M.v32.p, s, 1);
+  return tune_one<__nv_bfloat16, float>(M, M.v16.p, s, 2);
+}
+
+const char *mapping_name(const SolveMat &M, bool f64) {
+  static const char *names[kNumMaps] = {"wps1_u2", "wps1_u4", "wps2_u2", "wps2_u4", "wps4_u2", "wps4_u4"};
+  const int m = f64 ? M.map64 : M.map;
+  return (m >= 0 && m < kNumMaps) ? names[m] : "?";
+}
+
+}  // namespace amg
