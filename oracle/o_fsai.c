@@ -58,7 +58,7 @@ static int solve_rows(const obsr *A, int I, const int *pat, int np,
       or_chol_solve(m, L, rhs, gh[c]);
     }
     double s = a_entry(A, i, i);
-    for (int a = 0; a < m; ++a) s = s + a_entry(A, i, Q[a]) * gh[c][a];
+    for (int a = 0; a < m; ++a) s = fma(a_entry(A, i, Q[a]), gh[c][a], s);
     if (!(s > 0.0)) return OR_ERR_NOT_SPD;
     psi[c] = s;
   }
@@ -129,14 +129,14 @@ int or_afsai(const obsr *A, const obsr *Gs, int ksteps, int rho, double eps,
             for (int j = 0; j < np; ++j) {
               const double *blk = or_bsr_find(A, J, pat[j]);
               if (blk)
-                for (int e = 0; e < b; ++e) g = g + blk[d * b + e] * gh[c][b * j + e];
+                for (int e = 0; e < b; ++e) g = fma(blk[d * b + e], gh[c][b * j + e], g);
             }
             const double *blk = or_bsr_find(A, J, I);
             if (blk) {
-              for (int e = 0; e < c; ++e) g = g + blk[d * b + e] * gh[c][b * np + e];
+              for (int e = 0; e < c; ++e) g = fma(blk[d * b + e], gh[c][b * np + e], g);
               g = g + blk[d * b + c] * 1.0;
             }
-            s = s + g * g;
+            s = fma(g, g, s);
           }
         score[t] = s;
       }

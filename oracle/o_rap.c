@@ -10,6 +10,7 @@
  * accumulator, which starts at 0.  The pattern is the structural one (no
  * dropping); columns ascend.
  */
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -43,7 +44,7 @@ static int spgemm(const obsr *X, const obsr *Y, obsr *Z) {
         for (int r = 0; r < b; ++r)
           for (int q = 0; q < b; ++q) {
             double s = 0.0;
-            for (int d = 0; d < b; ++d) s = s + x[r * b + d] * y[d * b + q];
+            for (int d = 0; d < b; ++d) s = fma(x[r * b + d], y[d * b + q], s);
             a[r * b + q] = a[r * b + q] + s;
           }
       }

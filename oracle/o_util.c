@@ -39,7 +39,7 @@ double or_dot(int n, const double *x, const double *y) {
     for (int l = 0; l < 32; ++l) {
       double s = 0.0;
       for (int i = base + l; i < base + 8192 && i < n; i += 32)
-        s = s + x[i] * y[i];
+        s = fma(x[i], y[i], s);
       lane[l] = s;
     }
     for (int off = 16; off >= 1; off >>= 1) {
@@ -62,7 +62,7 @@ void or_spmv(const obsr *A, const double *x, double *y) {
       for (int k = A->rowptr[I]; k < A->rowptr[I + 1]; ++k) {
         const double *blk = A->val + (size_t)k * b * b;
         const int J = A->col[k];
-        for (int c = 0; c < b; ++c) s = s + blk[r * b + c] * x[(size_t)J * b + c];
+        for (int c = 0; c < b; ++c) s = fma(blk[r * b + c], x[(size_t)J * b + c], s);
       }
       y[(size_t)I * b + r] = s;
     }
@@ -128,13 +128,13 @@ int or_chol(int m, const double *M, double *L) {
   memset(L, 0, (size_t)m * m * sizeof(double));
   for (int j = 0; j < m; ++j) {
     double s = M[j * m + j];
-    for (int k = 0; k < j; ++k) s = s - L[j * m + k] * L[j * m + k];
+    for (int k = 0; k < j; ++k) s = fma(-L[j * m + k], L[j * m + k], s);
     if (!(s > 0.0)) return OR_ERR_NOT_SPD;
     const double d = sqrt(s);
     L[j * m + j] = d;
     for (int i = j + 1; i < m; ++i) {
       double t = M[i * m + j];
-      for (int k = 0; k < j; ++k) t = t - L[i * m + k] * L[j * m + k];
+      for (int k = 0; k < j; ++k) t = fma(-L[i * m + k], L[j * m + k], t);
       L[i * m + j] = t / d;
     }
   }
@@ -147,12 +147,12 @@ void or_chol_solve(int m, const double *L, const double *rhs, double *x) {
   double *y = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
   for (int i = 0; i < m; ++i) {
     double s = rhs[i];
-    for (int k = 0; k < i; ++k) s = s - L[i * m + k] * y[k];
+    for (int k = 0; k < i; ++k) s = fma(-L[i * m + k], y[k], s);
     y[i] = s / L[i * m + i];
   }
   for (int i = m - 1; i >= 0; --i) {
     double s = y[i];
-    for (int k = m - 1; k > i; --k) s = s - L[k * m + i] * x[k];
+    for (int k = m - 1; k > i; --k) s = fma(-L[k * m + i], x[k], s);
     x[i] = s / L[i * m + i];
   }
   free(y);

@@ -14,11 +14,18 @@
  * extension the paper names as future work (Sec. 5).  Every b = 3 rule below
  * reduces to the paper's rule at b = 1.
  *
- * Floating point: the oracle is compiled with -ffp-contract=off (no fused
- * multiply-add) and without -ffast-math.  Every sum that decides structure
- * (FSAI candidate ranking, Lanczos omega, SRQCG, SoC, DPLS selection) is taken
- * in a fixed, documented order, so that an independent implementation that
- * follows the same order reproduces it bit for bit.
+ * Floating point: the oracle is compiled with -ffp-contract=off (the
+ * compiler fuses nothing) and without -ffast-math.  Every sum that decides
+ * structure (FSAI candidate ranking, Lanczos omega, SRQCG, SoC, DPLS
+ * selection) is taken in a fixed, documented order, so that an independent
+ * implementation that follows the same order reproduces it bit for bit.  The
+ * accumulations of the inner product (or_dot), the block sparse product
+ * (or_spmv), the dense Cholesky factor and its triangular solves
+ * (or_chol, or_chol_solve), the aFSAI row functional and candidate gradients
+ * and the Galerkin block product are written as explicit C99 fma() calls,
+ * s <- fma(a, b, s): one rounding per term, as IEEE 754 fusedMultiplyAdd
+ * defines it on every conforming machine.  All other arithmetic rounds each
+ * product and each sum separately.
  */
 #ifndef ASPAMG_ORACLE_H
 #define ASPAMG_ORACLE_H

@@ -2,9 +2,14 @@
 // structure: FSAI rows, the Lanczos estimate of lambda_1(G A G^T), SRQCG,
 // affinity SoC and its filter, DPLS least-squares fits and the Galerkin
 // product.  This file is compiled with -fmad=false: every sum is taken in the
-// fixed order stated at each kernel, with separately rounded multiplies and
-// adds, so that the hierarchy (C/F split, patterns of G, P and A_c) is
-// reproducible bit for bit by any implementation that follows the same order.
+// fixed order stated at each kernel, so that the hierarchy (C/F split,
+// patterns of G, P and A_c) is reproducible bit for bit by any implementation
+// that follows the same order.  The accumulations of dot products, sparse
+// row sums, Cholesky updates, triangular-solve updates, the aFSAI functional
+// and gradients and the Galerkin block product are explicit fused
+// multiply-adds, s <- fma(a, b, s) (one IEEE rounding per term; FP64 issue
+// slots are the scarce resource of this GPU); everything else rounds each
+// multiply and each add separately (the compiler fuses nothing).
 // Fixed orders used throughout:
 //  * sparse row sums: blocks in ascending column order, then the block's
 //    columns, starting from 0;
@@ -48,7 +53,7 @@ __global__ void k_spmv(int nr, const int *__restrict__ rowptr, const int *__rest
   for (int k = rowptr[I]; k < rowptr[I + 1]; ++k) {
     const double *blk = val + (size_t)k * 9;
     const long J = col[k];
-    for (int c = 0; c < 3; ++c) s = s + blk[r * 3 + c] * x[J * 3 + c];
+    for (int c = 0; c < 3; ++c) s = fma(blk[r * 3 + c], x[J * 3 + c], s);
   }
   y[t] = s;
 }
@@ -85,7 +90,7 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
 __device__ __forceinline__ double chunk_sum(const double *__restrict__ x, const double *__restrict__ y,
                                             int base, int end, int lane) {
   double s = 0.0;
-  for (int i = base + lane; i < end; i += 32) s = s + x[i] * y[i];
+  for (int i = base + lane; i < end; i += 32) s = fma(x[i], y[i], s);
   for (int off = 16; off >= 1; off >>= 1) s = s + __shfl_xor_sync(0xffffffffu, s, off);
   return s;
 }
@@ -343,64 +348,99 @@ __device__ __forceinline__ double a_entry(const FsaiK &K, int r, int c) {
 }
 
 // Solve the 3 dof rows of node I on pattern pat[0..np-1]; returns 0 or an error.
+// The system of dof row c is A[Q_c, Q_c] with Q_c = (pattern dofs, 3I, ...,
+// 3I+c-1), so the systems of rows 0 and 1 are leading principal blocks of
+// the system of row 2: one Cholesky factor of the largest serves all three
+// (entry (r,k) of a Cholesky factor depends only on the leading (r+1)x(r+1)
+// block, so each row's factor is exactly what factoring it alone gives).
+// A is read one 3x3 block per node pair: the lower triangle of the largest
+// system, rhs_c = -A[Q_c, 3I+c] and ent_c = A[3I+c, Q_c].
 __device__ int fsai_solve_rows(const FsaiK &K, int I, const int *pat, int np, double *M, double *gh,
-                               double *rhs, double *prod, int *Q, double *psi, int lane) {
-  for (int c = 0; c < 3; ++c) {
-    const int i = 3 * I + c;
-    const int m = 3 * np + c;
-    for (int a = lane; a < m; a += 32) Q[a] = (a < 3 * np) ? 3 * pat[a / 3] + (a % 3) : 3 * I + (a - 3 * np);
-    __syncwarp();
-    for (int idx = lane; idx < m * m; idx += 32) {
-      const int a = idx / m, a2 = idx - a * m;
-      M[idx] = a_entry(K, Q[a], Q[a2]);
-    }
-    for (int a = lane; a < m; a += 32) rhs[a] = -a_entry(K, Q[a], i);
-    __syncwarp();
-    int bad = 0;
-    for (int j = 0; j < m; ++j) {
-      const double sjj = M[j * m + j];
-      if (!(sjj > 0.0)) { bad = 1; break; }
-      const double d = sqrt(sjj);
-      __syncwarp();
-      for (int r = j + 1 + lane; r < m; r += 32) M[r * m + j] = M[r * m + j] / d;
-      if (lane == 0) M[j * m + j] = d;
-      __syncwarp();
-      const int w = m - j - 1;  // trailing size
-      for (int idx = lane; idx < w * w; idx += 32) {
-        const int r = j + 1 + idx / w, k = j + 1 + idx % w;
-        if (k <= r) M[r * m + k] = M[r * m + k] - M[r * m + j] * M[k * m + j];
+                               double *rhs, double *ent, double *psi, int lane) {
+  const int m2 = 3 * np + 2, mm = K.mmax, nn = np + 1;
+  const int npairs = nn * (nn + 1) / 2;
+  for (int idx = lane; idx < npairs; idx += 32) {
+    int p = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+    while ((p + 1) * (p + 2) / 2 <= idx) ++p;
+    while (p * (p + 1) / 2 > idx) --p;
+    const int q = idx - p * (p + 1) / 2;
+    const double *b = find_blk(K.Arp, K.Acol, K.Aval, p < np ? pat[p] : I, q < np ? pat[q] : I);
+    for (int a = 0; a < 3; ++a) {
+      const int r = 3 * p + a;
+      if (r >= m2) break;
+      for (int e = 0; e < 3; ++e) {
+        const int cc = 3 * q + e;
+        if (cc <= r) M[r * m2 + cc] = b ? b[a * 3 + e] : 0.0;
       }
-      __syncwarp();
     }
-    if (bad) return AMG_ERR_NOT_SPD;
-    // forward: rhs <- L^{-1} rhs
-    for (int k = 0; k < m; ++k) {
-      const double yk = rhs[k] / M[k * m + k];
-      __syncwarp();
-      if (lane == 0) rhs[k] = yk;
-      for (int r = k + 1 + lane; r < m; r += 32) rhs[r] = rhs[r] - M[r * m + k] * yk;
-      __syncwarp();
+  }
+  for (int idx = lane; idx < nn; idx += 32) {
+    const int Np = idx < np ? pat[idx] : I;
+    const double *bc = find_blk(K.Arp, K.Acol, K.Aval, Np, I);
+    const double *br = find_blk(K.Arp, K.Acol, K.Aval, I, Np);
+    for (int a = 0; a < 3; ++a) {
+      const int qa = 3 * idx + a;
+      for (int c = 0; c < 3; ++c)
+        if (qa < 3 * np + c) {
+          rhs[c * mm + qa] = -(bc ? bc[a * 3 + c] : 0.0);
+          ent[c * mm + qa] = br ? br[c * 3 + a] : 0.0;
+        }
     }
-    // backward: gh <- L^{-T} rhs
-    double *x = gh + c * K.mmax;
-    for (int k = m - 1; k >= 0; --k) {
-      const double xk = rhs[k] / M[k * m + k];
-      __syncwarp();
-      if (lane == 0) x[k] = xk;
-      for (int r = lane; r < k; r += 32) rhs[r] = rhs[r] - M[k * m + r] * xk;
-      __syncwarp();
-    }
-    for (int a = lane; a < m; a += 32) prod[a] = a_entry(K, i, Q[a]) * x[a];
+  }
+  __syncwarp();
+  // right-looking Cholesky of the lower triangle (each entry receives its
+  // updates k = 0, 1, ... in ascending order, then the division)
+  int bad = 0;
+  for (int j = 0; j < m2; ++j) {
+    const double sjj = M[j * m2 + j];
+    if (!(sjj > 0.0)) { bad = 1; break; }
+    const double d = sqrt(sjj);
     __syncwarp();
-    double s = 0.0;
-    if (lane == 0) {
-      s = a_entry(K, i, i);
-      for (int a = 0; a < m; ++a) s = s + prod[a];
-    }
-    s = __shfl_sync(0xffffffffu, s, 0);
-    if (!(s > 0.0)) return AMG_ERR_NOT_SPD;
-    psi[c] = s;
+    for (int r = j + 1 + lane; r < m2; r += 32) M[r * m2 + j] = M[r * m2 + j] / d;
+    if (lane == 0) M[j * m2 + j] = d;
     __syncwarp();
+    const int w = m2 - j - 1;
+    for (int idx = lane; idx < w * w; idx += 32) {
+      const int r = j + 1 + idx / w, k = j + 1 + idx % w;
+      if (k <= r) M[r * m2 + k] = fma(-M[r * m2 + j], M[k * m2 + j], M[r * m2 + k]);
+    }
+    __syncwarp();
+  }
+  if (bad) return AMG_ERR_NOT_SPD;
+  // forward substitution for the three right-hand sides together (row c
+  // uses the leading 3np + c rows): y_k = rhs_k / L_kk, then rhs_r -= L_rk y_k
+  for (int k = 0; k < m2; ++k) {
+    if (lane < 3 && k < 3 * np + lane) rhs[lane * mm + k] = rhs[lane * mm + k] / M[k * m2 + k];
+    __syncwarp();
+    for (int idx = lane; idx < 3 * m2; idx += 32) {
+      const int c = idx / m2, r = idx - c * m2;
+      if (r > k && r < 3 * np + c) rhs[c * mm + r] = fma(-M[r * m2 + k], rhs[c * mm + k], rhs[c * mm + r]);
+    }
+    __syncwarp();
+  }
+  // backward substitution: x_k = rhs_k / L_kk for k descending, then
+  // rhs_r -= L_kr x_k for r < k
+  for (int k = m2 - 1; k >= 0; --k) {
+    if (lane < 3 && k < 3 * np + lane) gh[lane * mm + k] = rhs[lane * mm + k] / M[k * m2 + k];
+    __syncwarp();
+    for (int idx = lane; idx < 3 * k; idx += 32) {
+      const int c = idx / k, r = idx - c * k;
+      if (k < 3 * np + c) rhs[c * mm + r] = fma(-M[k * m2 + r], gh[c * mm + k], rhs[c * mm + r]);
+    }
+    __syncwarp();
+  }
+  // psi_c = a_ii + sum_a A[i, Q_a] gh_a (a ascending), i = 3I + c
+  if (lane < 3) {
+    const int c = lane;
+    const double *bii = find_blk(K.Arp, K.Acol, K.Aval, I, I);
+    double sv = bii ? bii[c * 3 + c] : 0.0;
+    for (int a = 0; a < 3 * np + c; ++a) sv = fma(ent[c * mm + a], gh[c * mm + a], sv);
+    psi[c] = sv;
+  }
+  __syncwarp();
+  for (int c = 0; c < 3; ++c) {
+    psi[c] = __shfl_sync(0xffffffffu, psi[c], c);
+    if (!(psi[c] > 0.0)) return AMG_ERR_NOT_SPD;
   }
   return AMG_OK;
 }
@@ -432,8 +472,8 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
   double *M = K.dscr + gw * K.dper;
   double *gh = M + (size_t)K.mmax * K.mmax;
   double *rhs = gh + 3 * K.mmax;
-  double *prod = rhs + K.mmax;
-  double *score = prod + K.mmax;
+  double *ent = rhs + 3 * K.mmax;
+  double *score = ent + 3 * K.mmax;
   int *Q = K.iscr + gw * K.iper;
   int *pat = Q + K.mmax;
   int *cand = pat + K.maxg + 1;
@@ -447,7 +487,7 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
     np = __shfl_sync(0xffffffffu, np, 0);
     __syncwarp();
     double psi[3], psi_old[3];
-    int rc = fsai_solve_rows(K, I, pat, np, M, gh, rhs, prod, Q, psi, lane);
+    int rc = fsai_solve_rows(K, I, pat, np, M, gh, rhs, ent, psi, lane);
     for (int step = 0; step < K.ksteps && rc == 0; ++step) {
       if (np >= K.maxg) break;
       // candidates: A-neighbours J < I of the pattern nodes and of I, outside
@@ -472,21 +512,28 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
       __syncwarp();
       for (int t = lane; t < nc; t += 32) {
         const int J = cand[t];
+        // gradient entries g[c][d] = (A gt_c)_{3J+d}: pattern dofs in
+        // ascending order, then the dofs 3I+e < 3I+c, then the unit entry
+        double g[3][3];
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) g[c][d] = 0.0;
+        for (int j = 0; j < np; ++j) {
+          const double *blk = find_blk(K.Arp, K.Acol, K.Aval, J, pat[j]);
+          if (blk)
+            for (int c = 0; c < 3; ++c)
+              for (int d = 0; d < 3; ++d)
+                for (int e = 0; e < 3; ++e) g[c][d] = fma(blk[d * 3 + e], gh[c * K.mmax + 3 * j + e], g[c][d]);
+        }
+        const double *bI = find_blk(K.Arp, K.Acol, K.Aval, J, I);
         double s = 0.0;
         for (int c = 0; c < 3; ++c)
           for (int d = 0; d < 3; ++d) {
-            double g = 0.0;
-            for (int j = 0; j < np; ++j) {
-              const double *blk = find_blk(K.Arp, K.Acol, K.Aval, J, pat[j]);
-              if (blk)
-                for (int e = 0; e < 3; ++e) g = g + blk[d * 3 + e] * gh[c * K.mmax + 3 * j + e];
+            double gv = g[c][d];
+            if (bI) {
+              for (int e = 0; e < c; ++e) gv = fma(bI[d * 3 + e], gh[c * K.mmax + 3 * np + e], gv);
+              gv = gv + bI[d * 3 + c] * 1.0;
             }
-            const double *blk = find_blk(K.Arp, K.Acol, K.Aval, J, I);
-            if (blk) {
-              for (int e = 0; e < c; ++e) g = g + blk[d * 3 + e] * gh[c * K.mmax + 3 * np + e];
-              g = g + blk[d * 3 + c] * 1.0;
-            }
-            s = s + g * g;
+            s = fma(gv, gv, s);
           }
         score[t] = s;
       }
@@ -527,7 +574,7 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
       np += got;
       __syncwarp();
       for (int c = 0; c < 3; ++c) psi_old[c] = psi[c];
-      rc = fsai_solve_rows(K, I, pat, np, M, gh, rhs, prod, Q, psi, lane);
+      rc = fsai_solve_rows(K, I, pat, np, M, gh, rhs, ent, psi, lane);
       if (rc) break;
       int stalled = 1;
       for (int c = 0; c < 3; ++c)
@@ -572,7 +619,7 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   K.status = status;
   K.mmax = 3 * maxg + 3;
   K.candcap = (maxg + 1) * maxdeg;
-  K.dper = (long)K.mmax * K.mmax + 5L * K.mmax + K.candcap;
+  K.dper = (long)K.mmax * K.mmax + 9L * K.mmax + K.candcap;
   K.iper = K.mmax + (maxg + 1) + K.candcap;
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
@@ -776,7 +823,7 @@ __global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const
   for (int k = rowptr[I]; k < rowptr[I + 1]; ++k) {
     const double *blk = val + (size_t)k * 9;
     const long J = col[k];
-    for (int c = 0; c < 3; ++c) sv = sv + blk[r * 3 + c] * x[J * 3 + c];
+    for (int c = 0; c < 3; ++c) sv = fma(blk[r * 3 + c], x[J * 3 + c], sv);
   }
   Y[tt] = sv;
 }
@@ -808,12 +855,12 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
   __syncwarp();
   for (int j = 0; j < t; ++j) {
     double sj = M[j * t + j];
-    for (int k = 0; k < j; ++k) sj = sj - L[j * t + k] * L[j * t + k];
+    for (int k = 0; k < j; ++k) sj = fma(-L[j * t + k], L[j * t + k], sj);
     if (!(sj > 0.0)) return 1;
     const double d = sqrt(sj);
     for (int i = j + 1 + lane; i < t; i += 32) {
       double u = M[i * t + j];
-      for (int k = 0; k < j; ++k) u = u - L[i * t + k] * L[j * t + k];
+      for (int k = 0; k < j; ++k) u = fma(-L[i * t + k], L[j * t + k], u);
       L[i * t + j] = u / d;
     }
     if (lane == 0) L[j * t + j] = d;
@@ -1427,7 +1474,7 @@ __global__ void k_spgemm(int nr, const int *__restrict__ xr, const int *__restri
     for (int r = 0; r < 3; ++r)
       for (int qq = 0; qq < 3; ++qq) {
         double s = 0.0;
-        for (int d = 0; d < 3; ++d) s = s + x[r * 3 + d] * y[d * 3 + qq];
+        for (int d = 0; d < 3; ++d) s = fma(x[r * 3 + d], y[d * 3 + qq], s);
         acc[r * 3 + qq] = acc[r * 3 + qq] + s;
       }
   }
