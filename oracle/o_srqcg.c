@@ -51,10 +51,22 @@ void or_mgs(int n, int t, double *V) {
 
 /* Generalised symmetric eigenproblem H U = M U diag(lam), M SPD, t x t
  * row-major.  M = L L^T; C = L^{-1} (L^{-1} H)^T, symmetrised as
- * (C + C^T) * 0.5; cyclic Jacobi rotations (row by row over p < q) until the
- * off-diagonal mass is negligible; eigenvalues sorted ascending (ties keep
- * index order); U = L^{-T} W; each column of U signed so that its entry of
- * largest magnitude (first on ties) is positive. */
+ * (C + C^T) * 0.5; Jacobi sweeps until the off-diagonal mass is negligible;
+ * eigenvalues sorted ascending (ties keep index order); U = L^{-T} W; each
+ * column of U signed so that its entry of largest magnitude (first on ties)
+ * is positive.
+ *
+ * A sweep visits every pair p < q once, in round-robin order (the circle
+ * method of tournament scheduling): the indices, padded with one dummy index
+ * when t is odd to T = t + (t mod 2), form T/2 disjoint pairs per round and
+ * T - 1 rounds per sweep; in round r position 0 holds index 0 and position
+ * i >= 1 holds index 1 + (i - 1 + r) mod (T - 1), and positions i and
+ * T - 1 - i are paired (pairs with the dummy index are skipped).  In a round
+ * the rotation of every pair with C[p][q] != 0 is computed from the current
+ * C; then all column rotations are applied, then all row rotations, then the
+ * rotations of W, and every rotated pivot C[p][q] = C[q][p] is set to 0.
+ * Disjoint pairs touch disjoint rows and columns, so each phase could run in
+ * any pair order with the same result. */
 int or_gen_eig(int t, const double *H, const double *M, double *U,
                double *lam) {
   double L[64 * 64], W1[64 * 64], C[64 * 64], Wv[64 * 64], tmp[64];
@@ -88,32 +100,59 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
       for (int q = p + 1; q < t; ++q) off = off + C[p * t + q] * C[p * t + q];
     }
     if (!(off > 1e-32 * dg)) break;
-    for (int p = 0; p < t - 1; ++p)
-      for (int q = p + 1; q < t; ++q) {
+    const int T = t + (t & 1);
+    for (int r = 0; r < T - 1; ++r) {
+      int rp[32], rq[32], np = 0;
+      double rc_[32], rs_[32];
+      for (int i = 0; i < T / 2; ++i) {
+        const int a = (i == 0) ? 0 : 1 + (i - 1 + r) % (T - 1);
+        const int j2 = T - 1 - i;
+        const int b2 = (j2 == 0) ? 0 : 1 + (j2 - 1 + r) % (T - 1);
+        const int p = a < b2 ? a : b2, q = a < b2 ? b2 : a;
+        if (q >= t) continue;
         const double apq = C[p * t + q];
         if (apq == 0.0) continue;
         const double th = (C[q * t + q] - C[p * t + p]) / (2.0 * apq);
         const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
         const double c = 1.0 / sqrt(tt * tt + 1.0);
-        const double s = tt * c;
+        rp[np] = p;
+        rq[np] = q;
+        rc_[np] = c;
+        rs_[np] = tt * c;
+        ++np;
+      }
+      for (int u = 0; u < np; ++u) {
+        const int p = rp[u], q = rq[u];
+        const double c = rc_[u], s = rs_[u];
         for (int k = 0; k < t; ++k) {
           const double xp = C[k * t + p], xq = C[k * t + q];
           C[k * t + p] = c * xp - s * xq;
           C[k * t + q] = s * xp + c * xq;
         }
+      }
+      for (int u = 0; u < np; ++u) {
+        const int p = rp[u], q = rq[u];
+        const double c = rc_[u], s = rs_[u];
         for (int k = 0; k < t; ++k) {
           const double xp = C[p * t + k], xq = C[q * t + k];
           C[p * t + k] = c * xp - s * xq;
           C[q * t + k] = s * xp + c * xq;
         }
+      }
+      for (int u = 0; u < np; ++u) {
+        const int p = rp[u], q = rq[u];
+        const double c = rc_[u], s = rs_[u];
         for (int k = 0; k < t; ++k) {
           const double xp = Wv[k * t + p], xq = Wv[k * t + q];
           Wv[k * t + p] = c * xp - s * xq;
           Wv[k * t + q] = s * xp + c * xq;
         }
-        C[p * t + q] = 0.0;
-        C[q * t + p] = 0.0;
       }
+      for (int u = 0; u < np; ++u) {
+        C[rp[u] * t + rq[u]] = 0.0;
+        C[rq[u] * t + rp[u]] = 0.0;
+      }
+    }
   }
   int order[64];
   for (int i = 0; i < t; ++i) order[i] = i;

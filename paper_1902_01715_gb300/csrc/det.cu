@@ -69,7 +69,10 @@ int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
 // One launch per group of dot products: warp w sums chunk c of pair d in the
 // fixed order; the last warp to finish (ticket counter) adds the chunk sums of
 // every pair in ascending chunk order and then runs the scalar step that
-// consumes them (Fin), so no separate scalar kernel is needed.
+// consumes them (Fin), so no separate scalar kernel is needed.  The dot
+// kernels run as one-warp blocks: a dot product has few chunk warps, and
+// each warp's 256-term FMA chains are bound by its SM's FP64 pipe, so the
+// warps must land on different SMs.
 constexpr int MAXD = 8;
 struct DotArgs {
   const double *x[MAXD];
@@ -93,6 +96,22 @@ __device__ __forceinline__ double chunk_sum(const double *__restrict__ x, const 
   for (int i = base + lane; i < end; i += 32) s = fma(x[i], y[i], s);
   for (int off = 16; off >= 1; off >>= 1) s = s + __shfl_xor_sync(0xffffffffu, s, off);
   return s;
+}
+
+// Chunk sums of one dot product added in ascending chunk order; the loads
+// are issued 16 at a time ahead of the additions (independent addresses),
+// so the chain waits on memory once per 16 chunks.
+__device__ __forceinline__ double sum_chunks(const double *p, int nchunks) {
+  double t = 0.0;
+  for (int c0 = 0; c0 < nchunks; c0 += 16) {
+    double v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = (c0 + u < nchunks) ? __ldcg(p + c0 + u) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (c0 + u < nchunks) t = t + v[u];
+  }
+  return t;
 }
 
 // Ticket: returns true in every lane of the warp that finished last.
@@ -143,7 +162,7 @@ __global__ void k_dots(int n, int nd, DotArgs a, double *__restrict__ part, unsi
   if (!last_warp(ticket, (unsigned)total, lane)) return;
   double t = 0.0;
   if (lane < nd)
-    for (int c = 0; c < nchunks; ++c) t = t + __ldcg(part + (size_t)lane * nchunks + c);
+    t = sum_chunks(part + (size_t)lane * nchunks, nchunks);
   if (lane < nd) out[lane] = t;
   double v[MAXD];
   for (int d = 0; d < MAXD; ++d) v[d] = __shfl_sync(0xffffffffu, t, d);
@@ -161,7 +180,7 @@ struct DotCtx {
 static int dots(int n, int nd, const DotArgs &a, double *out, DotCtx ctx, cudaStream_t s, Fin fin = Fin()) {
   const int nchunks = (n + CHUNK - 1) / CHUNK;
   const long warps = nchunks > 0 ? (long)nchunks * nd : 1;
-  AMG_KCOUNT k_dots<<<nblk(warps * 32, 256), 256, 0, s>>>(n, nd, a, ctx.part, ctx.ticket, nchunks, out, fin);
+  AMG_KCOUNT k_dots<<<nblk(warps * 32, 32), 32, 0, s>>>(n, nd, a, ctx.part, ctx.ticket, nchunks, out, fin);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -208,7 +227,7 @@ __global__ void k_gram(int n, int t, const double *__restrict__ Z, const double 
   if (!last_warp(ticket, (unsigned)total, lane)) return;
   for (int d = lane; d < nd; d += 32) {
     double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s = s + __ldcg(part + (size_t)d * nchunks + c);
+    s = sum_chunks(part + (size_t)d * nchunks, nchunks);
     int which, i, j;
     pair_of(d, t, which, i, j);
     double *O = which == 0 ? H : M;
@@ -783,7 +802,7 @@ __global__ void k_cdots(int n, int t, int nk, CDot a, double *__restrict__ part,
   if (!last_warp(ticket, (unsigned)total, lane)) return;
   for (int d = lane; d < nd; d += 32) {
     double sv = 0.0;
-    for (int c = 0; c < nchunks; ++c) sv = sv + __ldcg(part + (size_t)d * nchunks + c);
+    sv = sum_chunks(part + (size_t)d * nchunks, nchunks);
     out[d] = sv;
   }
   __syncwarp();
@@ -808,24 +827,28 @@ __global__ void k_cdots(int n, int t, int nk, CDot a, double *__restrict__ part,
   if (lane == 0) *ticket = 0u;
 }
 
-// y_j = A x_j for the t columns of n x t blocks (one thread per dof row and
-// column, row sums in the fixed order)
+// y_j = A x_j for the t columns of n x t blocks, row sums in the fixed
+// order.  One warp per block row: lane (j, r) computes dof row r of column j,
+// so every lane walks the same blocks (the row's values are read once per
+// warp and no FP64 instruction runs on a partly idle warp for lack of work).
 __global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const int *__restrict__ col,
                             const double *__restrict__ val, const double *__restrict__ X, double *__restrict__ Y) {
   const long n = 3L * nr;
-  const long tt = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tt >= n * t) return;
-  const int j = (int)(tt / n);
-  const long q = tt - (long)j * n;
-  const int I = (int)(q / 3), r = (int)(q - 3L * I);
-  const double *x = X + (size_t)j * n;
-  double sv = 0.0;
-  for (int k = rowptr[I]; k < rowptr[I + 1]; ++k) {
-    const double *blk = val + (size_t)k * 9;
-    const long J = col[k];
-    for (int c = 0; c < 3; ++c) sv = fma(blk[r * 3 + c], x[J * 3 + c], sv);
+  const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (I >= nr) return;
+  const int kb = rowptr[I], ke = rowptr[I + 1];
+  for (int pr = lane; pr < 3 * t; pr += 32) {
+    const int j = pr / 3, r = pr - 3 * j;
+    const double *x = X + (size_t)j * n;
+    double sv = 0.0;
+    for (int k = kb; k < ke; ++k) {
+      const double *blk = val + (size_t)k * 9;
+      const long J = col[k];
+      for (int c = 0; c < 3; ++c) sv = fma(blk[r * 3 + c], x[J * 3 + c], sv);
+    }
+    Y[(size_t)j * n + 3L * I + r] = sv;
   }
-  Y[tt] = sv;
 }
 
 __global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__restrict__ U) {
@@ -841,9 +864,11 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__
 }
 
 // Generalised eigenproblem H U = M U diag(lam) of the Ritz step, by one warp:
-// M = L L^T; C = L^{-1} (L^{-1} H)^T symmetrised as (C + C^T) * 0.5; cyclic
-// Jacobi rotations over p < q (row by row) until the off-diagonal mass is
-// negligible; eigenvalues sorted ascending (ties keep index order);
+// M = L L^T; C = L^{-1} (L^{-1} H)^T symmetrised as (C + C^T) * 0.5; Jacobi
+// sweeps in round-robin order (per round T/2 disjoint pairs from the circle
+// method, rotations computed from the current C, then all column, all row
+// and all W rotations applied) until the off-diagonal mass is negligible;
+// eigenvalues sorted ascending (ties keep index order);
 // U = L^{-T} W with each column signed so that its entry of largest magnitude
 // (first on ties) is positive.  Lanes only split work between independent
 // entries (rows of a rotation, columns of a triangular solve); every entry is
@@ -897,36 +922,56 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
       for (int q = p + 1; q < t; ++q) off = off + C[p * t + q] * C[p * t + q];
     }
     if (!(off > 1e-32 * dg)) break;
-    for (int p = 0; p < t - 1; ++p)
-      for (int q = p + 1; q < t; ++q) {
-        const double apq = C[p * t + q];
-        if (apq == 0.0) continue;
-        const double th = (C[q * t + q] - C[p * t + p]) / (2.0 * apq);
-        const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = 1.0 / sqrt(tt * tt + 1.0);
-        const double sn = tt * c;
-        __syncwarp();
-        if (lane < t) {
-          const double xp = C[lane * t + p], xq = C[lane * t + q];
-          C[lane * t + p] = c * xp - sn * xq;
-          C[lane * t + q] = sn * xp + c * xq;
+    // one sweep in round-robin order: lane i < T/2 owns pair i of the round
+    // (its rotation computed from the current C), then the column, row and
+    // W rotations of all pairs, then the pivots are zeroed
+    const int T = t + (t & 1), hp = T / 2;
+    for (int r = 0; r < T - 1; ++r) {
+      int p = 0, q = 0, act = 0;
+      double c = 1.0, sn = 0.0;
+      if (lane < hp) {
+        const int a = (lane == 0) ? 0 : 1 + (lane - 1 + r) % (T - 1);
+        const int j2 = T - 1 - lane;
+        const int b2 = (j2 == 0) ? 0 : 1 + (j2 - 1 + r) % (T - 1);
+        p = a < b2 ? a : b2;
+        q = a < b2 ? b2 : a;
+        if (q < t) {
+          const double apq = C[p * t + q];
+          if (apq != 0.0) {
+            const double th = (C[q * t + q] - C[p * t + p]) / (2.0 * apq);
+            const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(tt * tt + 1.0);
+            sn = tt * c;
+            act = 1;
+          }
         }
-        __syncwarp();
-        if (lane < t) {
-          const double xp = C[p * t + lane], xq = C[q * t + lane];
-          C[p * t + lane] = c * xp - sn * xq;
-          C[q * t + lane] = sn * xp + c * xq;
-          const double wp = Wv[lane * t + p], wq = Wv[lane * t + q];
-          Wv[lane * t + p] = c * wp - sn * wq;
-          Wv[lane * t + q] = sn * wp + c * wq;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          C[p * t + q] = 0.0;
-          C[q * t + p] = 0.0;
+      }
+      __syncwarp();
+      for (int phase = 0; phase < 3; ++phase) {
+        double *X = phase == 2 ? Wv : C;
+        for (int base = 0; base < hp * t; base += 32) {
+          const int idx = base + lane;
+          const int i = idx < hp * t ? idx / t : 0, k = idx - i * t;
+          const int pi = __shfl_sync(0xffffffffu, p, i), qi = __shfl_sync(0xffffffffu, q, i);
+          const int ai = __shfl_sync(0xffffffffu, act, i);
+          const double ci = __shfl_sync(0xffffffffu, c, i), si = __shfl_sync(0xffffffffu, sn, i);
+          if (idx < hp * t && ai) {
+            // columns p, q (phases 0 and 2) or rows p, q (phase 1), entry k
+            const int ip = phase == 1 ? pi * t + k : k * t + pi;
+            const int iq = phase == 1 ? qi * t + k : k * t + qi;
+            const double xp = X[ip], xq = X[iq];
+            X[ip] = ci * xp - si * xq;
+            X[iq] = si * xp + ci * xq;
+          }
         }
         __syncwarp();
       }
+      if (act) {
+        C[p * t + q] = 0.0;
+        C[q * t + p] = 0.0;
+      }
+      __syncwarp();
+    }
   }
   int order[TMAXD];
   for (int i = 0; i < t; ++i) order[i] = i;
@@ -959,7 +1004,7 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
 
 static int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
   if (A.nr == 0) return AMG_OK;
-  AMG_KCOUNT k_spmv_cols<<<nblk(3L * A.nr * t, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+  AMG_KCOUNT k_spmv_cols<<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -977,7 +1022,7 @@ static int cdots(int n, int t, int nk, const CDot &a, double *out, int fin, doub
                  cudaStream_t s) {
   const int nchunks = (n + CHUNK - 1) / CHUNK;
   const long warps = nchunks > 0 ? (long)nchunks * nk * t : 1;
-  AMG_KCOUNT k_cdots<<<nblk(warps * 32, 256), 256, 0, s>>>(n, t, nk, a, ctx.part, ctx.ticket, nchunks, out, fin, cs,
+  AMG_KCOUNT k_cdots<<<nblk(warps * 32, 32), 32, 0, s>>>(n, t, nk, a, ctx.part, ctx.ticket, nchunks, out, fin, cs,
                                                            skip);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -1037,9 +1082,11 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   // one iteration of the outer loop (optionally with the Ritz step)
   auto iteration = [&](bool ritz) -> int {
     if (ritz) {
-      AMG_TRY(apply_s_cols(A, G, GT, t, Z.p, SZ.p, T1.p, T2.p, s));
+      // SZ already holds S Z for the current Z (computed at the end of the
+      // previous iteration, or for the first quotients, and Z has not
+      // changed since): the Ritz step reuses it
       const long warps = nchunks > 0 ? (long)nchunks * t * (t + 1) : 1;
-      AMG_KCOUNT k_gram<<<nblk(warps * 32, 256), 256, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p, U.p,
+      AMG_KCOUNT k_gram<<<nblk(warps * 32, 32), 32, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p, U.p,
                                                              lam.p, wk.p, cs.p + C_F * t, status);
       AMG_KCOUNT k_rotate<<<nblk(n, 256), 256, 0, s>>>(n, t, Z.p, U.p);
       AMG_LAUNCH_CHECK();
@@ -1447,20 +1494,25 @@ int dpls(const DevBsr &A, const unsigned char *strong, const int *cf, const int 
 // ---------------------------------------------------------------- SpGEMM
 // Z = X Y on Z's given pattern; each output block adds the block products
 // X_ik Y_kc over k ascending (entry (r,q) of a product: sum_d X(r,d) Y(d,q),
-// d ascending from 0), accumulating from 0.
+// d ascending from 0), accumulating from 0.  Nine lanes per output block,
+// one per entry (3 blocks per warp): the nine walk the same k and take the
+// same branches, so the FP64 work runs on full lane groups.
 __global__ void k_spgemm(int nr, const int *__restrict__ xr, const int *__restrict__ xc, const double *__restrict__ xv,
                          const int *__restrict__ yr, const int *__restrict__ yc, const double *__restrict__ yv,
                          const int *__restrict__ zr, const int *__restrict__ zc, double *__restrict__ zv, int nnz) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nnz) return;
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (lane >= 27) return;
+  const long ql = 3 * w + lane / 9;
+  if (ql >= nnz) return;
+  const int q = (int)ql, e = lane % 9, r = e / 3, qq = e - 3 * r;
   int lo = 0, hi = nr - 1;
   while (lo < hi) {  // row of entry q: last row with zr[row] <= q
     const int mid = (lo + hi + 1) >> 1;
     if (zr[mid] <= q) lo = mid; else hi = mid - 1;
   }
   const int i = lo, c = zc[q];
-  double acc[9];
-  for (int e = 0; e < 9; ++e) acc[e] = 0.0;
+  double acc = 0.0;
   for (int kx = xr[i]; kx < xr[i + 1]; ++kx) {
     const int k = xc[kx];
     int a = yr[k], b = yr[k + 1] - 1, ky = -1;
@@ -1471,19 +1523,16 @@ __global__ void k_spgemm(int nr, const int *__restrict__ xr, const int *__restri
     }
     if (ky < 0) continue;
     const double *x = xv + (size_t)kx * 9, *y = yv + (size_t)ky * 9;
-    for (int r = 0; r < 3; ++r)
-      for (int qq = 0; qq < 3; ++qq) {
-        double s = 0.0;
-        for (int d = 0; d < 3; ++d) s = fma(x[r * 3 + d], y[d * 3 + qq], s);
-        acc[r * 3 + qq] = acc[r * 3 + qq] + s;
-      }
+    double sv = 0.0;
+    for (int d = 0; d < 3; ++d) sv = fma(x[r * 3 + d], y[d * 3 + qq], sv);
+    acc = acc + sv;
   }
-  for (int e = 0; e < 9; ++e) zv[(size_t)q * 9 + e] = acc[e];
+  zv[(size_t)q * 9 + e] = acc;
 }
 
 int spgemm_numeric(const DevBsr &X, const DevBsr &Y, DevBsr &Z, cudaStream_t s) {
   if (Z.nnzb == 0) return AMG_OK;
-  AMG_KCOUNT k_spgemm<<<nblk(Z.nnzb, 128), 128, 0, s>>>(Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
+  AMG_KCOUNT k_spgemm<<<nblk(32L * ((Z.nnzb + 2) / 3), 128), 128, 0, s>>>(Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
                                             Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
