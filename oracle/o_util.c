@@ -27,28 +27,36 @@ double or_uniform_pm1(uint64_t seed, uint64_t counter) {
 }
 
 /* Dot product in the fixed order used for every quantity that decides
- * structure: the vector is cut into chunks of 8192 entries; inside a chunk,
- * lane l (0..31) sums entries l, l+32, l+64, ... in increasing order; the 32
- * lane sums are combined by five exchange steps (lane l adds lane l^16, then
- * l^8, l^4, l^2, l^1), leaving the chunk sum in every lane; the chunk sums are
- * added in increasing chunk order. */
+ * structure.  The vector is cut into chunks of 1024 entries.  Inside a chunk,
+ * lane l (0..31) accumulates entries l, l+32, l+64, ... in increasing order
+ * (s <- fma(x_i, y_i, s) from 0), and the 32 lane sums are combined by five
+ * exchange steps (lane l adds lane l^16, then l^8, l^4, l^2, l^1), leaving the
+ * chunk sum in every lane.  The chunk sums are combined the same way one level
+ * up: lane l adds chunk sums l, l+32, l+64, ... in increasing order (from 0),
+ * and five exchange steps give the total. */
+static void exchange32(double *v) {
+  double tmp[32];
+  for (int off = 16; off >= 1; off >>= 1) {
+    for (int l = 0; l < 32; ++l) tmp[l] = v[l] + v[l ^ off];
+    memcpy(v, tmp, sizeof tmp);
+  }
+}
+
 double or_dot(int n, const double *x, const double *y) {
-  double total = 0.0;
-  for (int base = 0; base < n; base += 8192) {
-    double lane[32], tmp[32];
+  double top[32];
+  for (int l = 0; l < 32; ++l) top[l] = 0.0;
+  for (int c = 0, base = 0; base < n; ++c, base += 1024) {
+    double lane[32];
     for (int l = 0; l < 32; ++l) {
       double s = 0.0;
-      for (int i = base + l; i < base + 8192 && i < n; i += 32)
-        s = fma(x[i], y[i], s);
+      for (int i = base + l; i < base + 1024 && i < n; i += 32) s = fma(x[i], y[i], s);
       lane[l] = s;
     }
-    for (int off = 16; off >= 1; off >>= 1) {
-      for (int l = 0; l < 32; ++l) tmp[l] = lane[l] + lane[l ^ off];
-      memcpy(lane, tmp, sizeof lane);
-    }
-    total = total + lane[0];
+    exchange32(lane);
+    top[c % 32] = top[c % 32] + lane[0];
   }
-  return total;
+  exchange32(top);
+  return top[0];
 }
 
 /* y = A x.  Row r of block row I: sum over the blocks of row I in stored

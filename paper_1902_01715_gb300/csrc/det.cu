@@ -13,9 +13,10 @@
 // Fixed orders used throughout:
 //  * sparse row sums: blocks in ascending column order, then the block's
 //    columns, starting from 0;
-//  * global dot products: chunks of 8192 entries; inside a chunk, lane l of a
+//  * global dot products: chunks of 1024 entries; inside a chunk, lane l of a
 //    warp sums entries l, l+32, ... ascending, the 32 lane sums are combined
-//    by xor-exchange steps 16, 8, 4, 2, 1; chunk sums are added ascending.
+//    by xor-exchange steps 16, 8, 4, 2, 1; one level up, lane l sums chunk
+//    sums l, l+32, ... ascending and the same exchange steps give the total.
 #include <cfloat>
 
 #include "amg_internal.h"
@@ -23,7 +24,8 @@
 namespace amg {
 namespace det {
 
-constexpr int CHUNK = 8192;
+constexpr int CHUNK = 1024;
+constexpr int MAXTICKETS = 512;  // per-pair tickets of one dot launch, plus one
 constexpr int TMAXD = 16;  // largest test space handled by the DPLS kernel
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t counter) {
@@ -66,13 +68,13 @@ int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- dots
-// One launch per group of dot products: warp w sums chunk c of pair d in the
-// fixed order; the last warp to finish (ticket counter) adds the chunk sums of
-// every pair in ascending chunk order and then runs the scalar step that
-// consumes them (Fin), so no separate scalar kernel is needed.  The dot
-// kernels run as one-warp blocks: a dot product has few chunk warps, and
-// each warp's 256-term FMA chains are bound by its SM's FP64 pipe, so the
-// warps must land on different SMs.
+// One launch per group of dot products, one-warp blocks.  Warp w computes
+// chunk c of pair d (lane sums of stride 32, then the exchange steps); the
+// warp that completes the last chunk of a pair (per-pair ticket) combines
+// that pair's chunk sums in the fixed order; the warp that completes the
+// last pair (one more ticket) runs the scalar step that consumes the sums
+// (Fin), so no separate scalar kernel is needed.  Warps are spread over the
+// SMs because each SM's FP64 pipe is narrow.
 constexpr int MAXD = 8;
 struct DotArgs {
   const double *x[MAXD];
@@ -90,28 +92,46 @@ struct Fin {
 __device__ double line_min(double a, double b, double c, double d, double e, double f);
 __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, double *lam, double *w, int lane);
 
-__device__ __forceinline__ double chunk_sum(const double *__restrict__ x, const double *__restrict__ y,
-                                            int base, int end, int lane) {
-  double s = 0.0;
-  for (int i = base + lane; i < end; i += 32) s = fma(x[i], y[i], s);
+__device__ __forceinline__ double exchange32(double s) {
   for (int off = 16; off >= 1; off >>= 1) s = s + __shfl_xor_sync(0xffffffffu, s, off);
   return s;
 }
 
-// Chunk sums of one dot product added in ascending chunk order; the loads
-// are issued 16 at a time ahead of the additions (independent addresses),
-// so the chain waits on memory once per 16 chunks.
-__device__ __forceinline__ double sum_chunks(const double *p, int nchunks) {
-  double t = 0.0;
-  for (int c0 = 0; c0 < nchunks; c0 += 16) {
-    double v[16];
+// Chunk [base, end) of x . y: lane l accumulates entries base+l, base+l+32,
+// ... (at most 32 of them, loads issued 16 at a time ahead of the chain),
+// then the exchange steps.
+__device__ __forceinline__ double chunk_sum(const double *__restrict__ x, const double *__restrict__ y,
+                                            int base, int end, int lane) {
+  double s = 0.0;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) v[u] = (c0 + u < nchunks) ? __ldcg(p + c0 + u) : 0.0;
+  for (int h = 0; h < 2; ++h) {
+    double xv[16], yv[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int i = base + lane + 32 * (16 * h + u);
+      xv[u] = i < end ? x[i] : 0.0;
+      yv[u] = i < end ? y[i] : 0.0;
+    }
 #pragma unroll
     for (int u = 0; u < 16; ++u)
-      if (c0 + u < nchunks) t = t + v[u];
+      if (base + lane + 32 * (16 * h + u) < end) s = fma(xv[u], yv[u], s);
   }
-  return t;
+  return exchange32(s);
+}
+
+// Chunk sums p[0..nchunks) of one pair: lane l adds sums l, l+32, ... in
+// increasing order (loads 8 at a time ahead), then the exchange steps.
+__device__ __forceinline__ double sum_chunks(const double *p, int nchunks, int lane) {
+  double t = 0.0;
+  for (int c0 = lane; c0 < nchunks; c0 += 32 * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (c0 + 32 * u < nchunks) ? __ldcg(p + c0 + 32 * u) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (c0 + 32 * u < nchunks) t = t + v[u];
+  }
+  return exchange32(t);
 }
 
 // Ticket: returns true in every lane of the warp that finished last.
@@ -123,6 +143,36 @@ __device__ __forceinline__ bool last_warp(unsigned *ticket, unsigned total, int 
   }
   t = __shfl_sync(0xffffffffu, t, 0);
   return t == total - 1;
+}
+
+// The work of warp w in a dot launch over nd pairs (x_d, y_d given by xy);
+// the finished sum of pair d goes to put(d, value) from lane 0.  Returns true
+// in the one warp that completed the last pair (every put is then visible
+// through __ldcg).  With empty vectors a single warp puts zeros.
+template <class XY, class Put>
+__device__ __forceinline__ bool dot_warp(long w, int n, int nd, int nchunks, double *part, unsigned *ticket, int lane,
+                                         XY xy, Put put) {
+  if (nchunks == 0) {
+    if (lane == 0)
+      for (int d = 0; d < nd; ++d) put(d, 0.0);
+    __threadfence();
+    return true;
+  }
+  const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
+  const double *x, *y;
+  xy(d, x, y);
+  const int base = c * CHUNK, end = min(base + CHUNK, n);
+  const double sc = chunk_sum(x, y, base, end, lane);
+  if (lane == 0) part[(size_t)d * nchunks + c] = sc;
+  if (!last_warp(ticket + d, (unsigned)nchunks, lane)) return false;
+  const double tot = sum_chunks(part + (size_t)d * nchunks, nchunks, lane);
+  if (lane == 0) {
+    put(d, tot);
+    ticket[d] = 0u;
+  }
+  if (!last_warp(ticket + nd, (unsigned)nd, lane)) return false;
+  if (lane == 0) ticket[nd] = 0u;
+  return true;
 }
 
 // scalar steps of Algorithm 4 and of the Lanczos recurrence
@@ -147,29 +197,23 @@ __device__ void run_fin(const Fin &f, const double *v) {
   }
 }
 
-__global__ void k_dots(int n, int nd, DotArgs a, double *__restrict__ part, unsigned *ticket, int nchunks,
-                       double *__restrict__ out, Fin fin) {
-  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(32) k_dots(int n, int nd, DotArgs a, double *__restrict__ part, unsigned *ticket,
+                                             int nchunks, double *__restrict__ out, Fin fin) {
+  const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
   const long total = nchunks > 0 ? (long)nchunks * nd : 1;
   if (w >= total) return;
-  if (nchunks > 0) {
-    const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
-    const int base = c * CHUNK, end = min(base + CHUNK, n);
-    const double s = chunk_sum(a.x[d], a.y[d], base, end, lane);
-    if (lane == 0) part[(size_t)d * nchunks + c] = s;
-  }
-  if (!last_warp(ticket, (unsigned)total, lane)) return;
-  double t = 0.0;
-  if (lane < nd)
-    t = sum_chunks(part + (size_t)lane * nchunks, nchunks);
-  if (lane < nd) out[lane] = t;
+  const bool last = dot_warp(
+      w, n, nd, nchunks, part, ticket, lane,
+      [&](int d, const double *&x, const double *&y) {
+        x = a.x[d];
+        y = a.y[d];
+      },
+      [&](int d, double v) { out[d] = v; });
+  if (!last || lane != 0) return;
   double v[MAXD];
-  for (int d = 0; d < MAXD; ++d) v[d] = __shfl_sync(0xffffffffu, t, d);
-  if (lane == 0) {
-    run_fin(fin, v);
-    *ticket = 0u;
-  }
+  for (int d = 0; d < MAXD; ++d) v[d] = d < nd ? __ldcg(out + d) : 0.0;
+  run_fin(fin, v);
 }
 
 struct DotCtx {
@@ -180,7 +224,7 @@ struct DotCtx {
 static int dots(int n, int nd, const DotArgs &a, double *out, DotCtx ctx, cudaStream_t s, Fin fin = Fin()) {
   const int nchunks = (n + CHUNK - 1) / CHUNK;
   const long warps = nchunks > 0 ? (long)nchunks * nd : 1;
-  AMG_KCOUNT k_dots<<<nblk(warps * 32, 32), 32, 0, s>>>(n, nd, a, ctx.part, ctx.ticket, nchunks, out, fin);
+  AMG_KCOUNT k_dots<<<(int)warps, 32, 0, s>>>(n, nd, a, ctx.part, ctx.ticket, nchunks, out, fin);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -205,42 +249,43 @@ __device__ __forceinline__ void pair_of(int d, int t, int &which, int &i, int &j
   j = i + pr;
 }
 
-__global__ void k_gram(int n, int t, const double *__restrict__ Z, const double *__restrict__ SZ,
-                       double *__restrict__ part, unsigned *ticket, int nchunks, double *__restrict__ H,
-                       double *__restrict__ M, double *__restrict__ U, double *__restrict__ lam,
-                       double *__restrict__ wk, double *__restrict__ f, int *__restrict__ status) {
+__global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restrict__ Z, const double *__restrict__ SZ,
+                                             double *__restrict__ part, unsigned *ticket, int nchunks,
+                                             double *__restrict__ H, double *__restrict__ M, double *__restrict__ U,
+                                             double *__restrict__ lam, double *__restrict__ wk, double *__restrict__ f,
+                                             int *__restrict__ status) {
   const int nd = t * (t + 1);
-  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
   const long total = nchunks > 0 ? (long)nchunks * nd : 1;
   if (w >= total) return;
-  if (nchunks > 0) {
-    const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
-    int which, i, j;
-    pair_of(d, t, which, i, j);
-    const double *x = Z + (size_t)i * n;
-    const double *y = which == 0 ? SZ + (size_t)j * n : Z + (size_t)j * n;
-    const int base = c * CHUNK, end = min(base + CHUNK, n);
-    const double s = chunk_sum(x, y, base, end, lane);
-    if (lane == 0) part[(size_t)d * nchunks + c] = s;
-  }
-  if (!last_warp(ticket, (unsigned)total, lane)) return;
-  for (int d = lane; d < nd; d += 32) {
-    double s = 0.0;
-    s = sum_chunks(part + (size_t)d * nchunks, nchunks);
-    int which, i, j;
-    pair_of(d, t, which, i, j);
-    double *O = which == 0 ? H : M;
-    O[i * t + j] = s;
-    O[j * t + i] = s;
+  const bool last = dot_warp(
+      w, n, nd, nchunks, part, ticket, lane,
+      [&](int d, const double *&x, const double *&y) {
+        int which, i, j;
+        pair_of(d, t, which, i, j);
+        x = Z + (size_t)i * n;
+        y = which == 0 ? SZ + (size_t)j * n : Z + (size_t)j * n;
+      },
+      [&](int d, double v) {
+        int which, i, j;
+        pair_of(d, t, which, i, j);
+        double *O = which == 0 ? H : M;
+        O[i * t + j] = v;
+        O[j * t + i] = v;
+      });
+  if (!last) return;
+  // the pencil was written by other warps: read it through L2 into scratch
+  double *Hs = wk + 4 * t * t + t, *Ms = Hs + t * t;
+  for (int q = lane; q < t * t; q += 32) {
+    Hs[q] = __ldcg(H + q);
+    Ms[q] = __ldcg(M + q);
   }
   __syncwarp();
-  __threadfence_block();
-  const int bad = gen_eig_warp(t, H, M, U, lam, wk, lane);
+  const int bad = gen_eig_warp(t, Hs, Ms, U, lam, wk, lane);
   if (lane == 0) {
     if (bad) atomicMin(status, AMG_ERR_NOT_SPD);
     for (int i = 0; i < t; ++i) f[i] = 1.0;
-    *ticket = 0u;
   }
 }
 
@@ -305,7 +350,7 @@ int mgs(int n, int t, double *V, cudaStream_t s) {
   DBuf<unsigned> tk;
   AMG_TRY(sc.alloc(4));
   AMG_TRY(part.alloc((size_t)((n + CHUNK - 1) / CHUNK) + 1));
-  AMG_TRY(tk.alloc(1));
+  AMG_TRY(tk.alloc(MAXTICKETS));
   AMG_TRY(tk.zero(s));
   const DotCtx ctx{part.p, tk.p};
   for (int j = 0; j < t; ++j) {
@@ -785,46 +830,42 @@ struct CDot {
   long xs[5], ys[5];  // column strides of x and y (n, or 0 for one shared vector)
 };
 
-__global__ void k_cdots(int n, int t, int nk, CDot a, double *__restrict__ part, unsigned *ticket, int nchunks,
-                        double *__restrict__ out, int fin, double *__restrict__ cs, int *__restrict__ skip) {
+__global__ void __launch_bounds__(32) k_cdots(int n, int t, int nk, CDot a, double *__restrict__ part, unsigned *ticket,
+                                              int nchunks, double *__restrict__ out, int fin, double *__restrict__ cs,
+                                              int *__restrict__ skip) {
   const int nd = nk * t;
-  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
   const long total = nchunks > 0 ? (long)nchunks * nd : 1;
   if (w >= total) return;
-  if (nchunks > 0) {
-    const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
-    const int kind = d / t, j = d - kind * t;
-    const int base = c * CHUNK, end = min(base + CHUNK, n);
-    const double sv = chunk_sum(a.x[kind] + j * a.xs[kind], a.y[kind] + j * a.ys[kind], base, end, lane);
-    if (lane == 0) part[(size_t)d * nchunks + c] = sv;
-  }
-  if (!last_warp(ticket, (unsigned)total, lane)) return;
-  for (int d = lane; d < nd; d += 32) {
-    double sv = 0.0;
-    sv = sum_chunks(part + (size_t)d * nchunks, nchunks);
-    out[d] = sv;
-  }
-  __syncwarp();
-  __threadfence_block();
+  const bool last = dot_warp(
+      w, n, nd, nchunks, part, ticket, lane,
+      [&](int d, const double *&x, const double *&y) {
+        const int kind = d / t, j = d - kind * t;
+        x = a.x[kind] + j * a.xs[kind];
+        y = a.y[kind] + j * a.ys[kind];
+      },
+      [&](int d, double v) { out[d] = v; });
+  if (!last) return;
+  // the sums were written by other warps: read them through L2
+  auto o = [&](int k) { return __ldcg(out + k); };
   for (int j = lane; j < t; j += 32) {
     if (fin == CF_ALPHA) {  // out = a, b, c, d, e blocks of t
-      const double bb = out[t + j];
+      const double bb = o(t + j);
       cs[C_B * t + j] = bb;
       if (!(bb > 0.0)) {
         skip[j] = 1;
       } else {
         skip[j] = 0;
-        cs[C_ALPHA * t + j] = line_min(out[j], bb, out[2 * t + j], out[3 * t + j], out[4 * t + j], cs[C_F * t + j]);
+        cs[C_ALPHA * t + j] = line_min(o(j), bb, o(2 * t + j), o(3 * t + j), o(4 * t + j), cs[C_F * t + j]);
       }
     } else if (fin == CF_Q) {  // out = f_new, z.Sz
-      cs[C_FN * t + j] = out[j];
-      cs[C_Q * t + j] = out[t + j] / out[j];
+      cs[C_FN * t + j] = o(j);
+      cs[C_Q * t + j] = o(t + j) / o(j);
     } else if (fin == CF_BETA) {  // out = g.Sp
-      cs[C_BETA * t + j] = -(out[j] / cs[C_B * t + j]);
+      cs[C_BETA * t + j] = -(o(j) / cs[C_B * t + j]);
     }
   }
-  if (lane == 0) *ticket = 0u;
 }
 
 // y_j = A x_j for the t columns of n x t blocks, row sums in the fixed
@@ -1022,7 +1063,7 @@ static int cdots(int n, int t, int nk, const CDot &a, double *out, int fin, doub
                  cudaStream_t s) {
   const int nchunks = (n + CHUNK - 1) / CHUNK;
   const long warps = nchunks > 0 ? (long)nchunks * nk * t : 1;
-  AMG_KCOUNT k_cdots<<<nblk(warps * 32, 32), 32, 0, s>>>(n, t, nk, a, ctx.part, ctx.ticket, nchunks, out, fin, cs,
+  AMG_KCOUNT k_cdots<<<(int)warps, 32, 0, s>>>(n, t, nk, a, ctx.part, ctx.ticket, nchunks, out, fin, cs,
                                                            skip);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -1054,9 +1095,9 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   AMG_TRY(Mg.alloc(t * t));
   AMG_TRY(U.alloc(t * t));
   AMG_TRY(lam.alloc(t));
-  AMG_TRY(wk.alloc(4 * t * t + t));
+  AMG_TRY(wk.alloc(6 * t * t + t));
   AMG_TRY(skip.alloc(t));
-  AMG_TRY(tk.alloc(1));
+  AMG_TRY(tk.alloc(MAXTICKETS));
   AMG_TRY(cs.zero(s));
   AMG_TRY(skip.zero(s));
   AMG_TRY(tk.zero(s));
@@ -1086,7 +1127,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
       // previous iteration, or for the first quotients, and Z has not
       // changed since): the Ritz step reuses it
       const long warps = nchunks > 0 ? (long)nchunks * t * (t + 1) : 1;
-      AMG_KCOUNT k_gram<<<nblk(warps * 32, 32), 32, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p, U.p,
+      AMG_KCOUNT k_gram<<<(int)warps, 32, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p, U.p,
                                                              lam.p, wk.p, cs.p + C_F * t, status);
       AMG_KCOUNT k_rotate<<<nblk(n, 256), 256, 0, s>>>(n, t, Z.p, U.p);
       AMG_LAUNCH_CHECK();
@@ -1195,7 +1236,7 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
   if (m > 64) m = 64;
   DBuf<double> Vs, w, t1, t2, sc, part;
   DBuf<unsigned> tk;
-  AMG_TRY(tk.alloc(1));
+  AMG_TRY(tk.alloc(MAXTICKETS));
   AMG_TRY(tk.zero(s));
   AMG_TRY(Vs.alloc((size_t)m * n));
   AMG_TRY(w.alloc(n));
