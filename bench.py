@@ -31,6 +31,15 @@ METRIC = "time-to-1e-8 residual & V-cycles/s (FP64 vs mixed/batched), SpMV %HBM 
 UNIT = "solutions/s"
 RTOL = 1e-8
 SAMPLE_DIMS = (48, 12, 12)   # oracle sample: same recipe, scaled down
+# FP64 arithmetic peak for FMA-bound kernels: the nominal 1.25 TFLOP/s of this
+# GPU (152 SMs x 2 FP64 FMA per clock x 2 flop x ~2.06 GHz); a chain-of-FMA
+# probe on the same GPUs measured 6.28e11 FMA/s (1.256 TFLOP/s)
+FP64_TFLOPS = 1.25
+FP64_PEAK_SOURCE = "nominal FP64 rate (1.25 TFLOP/s); FMA-chain probe measured 1.256"
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+# ncu captures summarised under profiles/; a kernel whose code changed since its
+# capture has no entry
+TRAFFIC: dict = {}
 
 
 def peaks():
@@ -236,16 +245,32 @@ def run_ours(args):
     stats = S.stats()
     clocks = clk.summary()
 
-    # dominant solve kernel: the fine-level BSR3 product of the CG operator
-    spmv_ms, spmv_bytes = S.bench_spmv(0, "A", a64=True, reps=50)
+    # dominant kernel of the step: the set-up's FP64 product of A_0 with the
+    # n_tv test-space columns (the S = G A G^T products of Algorithm 4); FP64
+    # FMA bound, timed with CUDA events on the handle's stream right after the
+    # timed region, on the same hierarchy
     pk = peaks()
     hbm = pk.get("hbm_gbs")
+    t_tv = S.params.n_tv
+    nnzb0 = S.level_info(0)["nnzb_A"]
+    ms_c, by_c = S.bench_spmv(0, "A_cols", reps=20)
+    flops_c = 18.0 * nnzb0 * t_tv
+    ach = flops_c / (ms_c * 1e-3) / 1e12
+    roofline = {"kernel": "det::k_spmv_cols (set-up product A_0 X, %d FP64 columns)" % t_tv, "bound": "alu",
+                "achieved": ach, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_TFLOPS,
+                "traffic": TRAFFIC.get("k_spmv_cols"), "peak_source": FP64_PEAK_SOURCE,
+                "ms_per_launch": ms_c, "flops_per_launch": flops_c, "bytes_per_launch": by_c}
+    # the solve phase's FP64 product of the CG operator (level-0 K): bytes
+    # against HBM, FMAs against the FP64 pipe
+    spmv_ms, spmv_bytes = S.bench_spmv(0, "A", a64=True, reps=50)
     achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    roofline = {"kernel": "k_bsrmv<32,double,double> (level-0 K, FP64)", "bound": "hbm",
-                "achieved": achieved, "peak": hbm if hbm else 6800.0, "unit": "GB/s",
-                "frac": achieved / (hbm if hbm else 6800.0), "traffic": None,
-                "peak_source": "measured" if hbm else "fallback", "ms_per_launch": spmv_ms,
-                "bytes_per_launch": spmv_bytes}
+    hpk = hbm if hbm else 6800.0
+    spmv_flops = 18.0 * nnzb0
+    roofline_spmv = {"kernel": "amg::k_sellmv (level-0 K x, FP64)", "bound": "hbm", "achieved": achieved,
+                     "peak": hpk, "unit": "GB/s", "frac": achieved / hpk, "traffic": TRAFFIC.get("k_sellmv"),
+                     "peak_source": "measured" if hbm else "fallback", "ms_per_launch": spmv_ms,
+                     "bytes_per_launch": spmv_bytes,
+                     "fp64_fma_frac": spmv_flops / (spmv_ms * 1e-3) / 1e12 / FP64_TFLOPS}
     # FP32 V-cycle of the same configuration (not part of value)
     fp32 = None
     if args.prec == "fp64" and not args.no_compare:
@@ -261,9 +286,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         s32 = S32.stats()
         err = float(torch.linalg.norm(x32 - x) / torch.linalg.norm(x))
+        ms32, by32 = S32.bench_spmv(0, "A", a64=False, reps=50)
         fp32 = {"ms_per_step": e2.elapsed_time(e3) / args.steps, "n_it": it32,
                 "solve_ms": s32["T_s"] * 1e3, "vcycles_per_s": it32 / s32["T_s"],
-                "rel_diff_vs_fp64_solution": err}
+                "rel_diff_vs_fp64_solution": err,
+                "spmv_level0": {"kernel": "amg::k_sellmv (level-0 K x, FP32)", "ms_per_launch": ms32,
+                                "bytes_per_launch": by32, "GBps": by32 / (ms32 * 1e-3) / 1e9,
+                                "frac": by32 / (ms32 * 1e-3) / 1e9 / hpk}}
         S32.close()
 
     # end to end through the C ABI with pinned host buffers
@@ -321,6 +350,7 @@ def run_ours(args):
                   "setup_phases_ms": {k: 1e3 * stats[k] for k in ("T_sm", "T_ts", "T_cs", "T_pl", "T_rap")}},
         "fp32_vcycle": fp32,
         "roofline": roofline,
+        "roofline_spmv": roofline_spmv,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

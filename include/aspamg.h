@@ -156,9 +156,12 @@ int amg_vcycle(amg_handle h, const double *y, double *z);
 /* Time the solve-phase sparse product of level `lev` (which = 0 A, 1 G,
  * 2 G^T, 3 P, 4 R; storage of the handle's V-cycle precision, FP64 for the
  * level-0 A of the CG recurrence when prec_a64 != 0) over `reps` back-to-back
- * launches with CUDA events on the handle's stream.  *ms = average launch
- * time, *bytes = algorithmic bytes of one launch (values, column indices and
- * row pointers once, x and y once each). */
+ * launches with CUDA events on the handle's stream.  which = 5 times instead
+ * the set-up's FP64 product of A_lev with n_tv columns (the kernel the
+ * test-space iteration of Algorithm 4 applies S = G A G^T with; 18 nnzb n_tv
+ * flops per launch).  *ms = average launch time, *bytes = algorithmic bytes
+ * of one launch (values, column indices and row pointers once, x and y once
+ * each). */
 int amg_bench_spmv(amg_handle h, int lev, int which, int prec_a64, int reps,
                    double *ms, double *bytes);
 /* Kernel launches the library has issued in this process (graph replays

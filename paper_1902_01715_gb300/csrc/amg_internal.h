@@ -238,6 +238,8 @@ long long launch_count();
 // ---- deterministic set-up kernels (det.cu) ----
 namespace det {
 int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s);
+// Y_j = A X_j for the t columns of n x t column-major blocks (set-up order)
+int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s);
 struct FsaiOut {
   int *np;        // [n] pattern nodes per row
   int *pat;       // [n*maxg]

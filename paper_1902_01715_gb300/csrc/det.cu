@@ -370,8 +370,8 @@ int mgs(int n, int t, double *V, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- FSAI
-// Warp-cooperative aFSAI rows (one warp per node row).  The arithmetic of each
-// scalar follows the plain sequential definition:
+// Warp-cooperative aFSAI rows (FS_NG node rows per warp, below).  The
+// arithmetic of each scalar follows the plain sequential definition:
 //  * Cholesky of A[Q,Q] entry (i,j): A_ij - sum_{k<j} L_ik L_jk (k ascending),
 //    then sqrt / division (the right-looking update subtracts the same
 //    products in the same order);
@@ -392,8 +392,9 @@ struct FsaiK {
   int *status;
   double *dscr;
   int *iscr;
+  unsigned long long *htab;
   long dper, iper;
-  int candcap, mmax;
+  int candcap, mmax, hcap;
 };
 
 __device__ __forceinline__ const double *find_blk(const int *rp, const int *col, const double *val, int i, int j) {
@@ -411,23 +412,46 @@ __device__ __forceinline__ double a_entry(const FsaiK &K, int r, int c) {
   return b ? b[(r % 3) * 3 + (c % 3)] : 0.0;
 }
 
-// Solve the 3 dof rows of node I on pattern pat[0..np-1]; returns 0 or an error.
-// The system of dof row c is A[Q_c, Q_c] with Q_c = (pattern dofs, 3I, ...,
-// 3I+c-1), so the systems of rows 0 and 1 are leading principal blocks of
-// the system of row 2: one Cholesky factor of the largest serves all three
-// (entry (r,k) of a Cholesky factor depends only on the leading (r+1)x(r+1)
-// block, so each row's factor is exactly what factoring it alone gives).
-// A is read one 3x3 block per node pair: the lower triangle of the largest
-// system, rhs_c = -A[Q_c, 3I+c] and ent_c = A[3I+c, Q_c].
-__device__ int fsai_solve_rows(const FsaiK &K, int I, const int *pat, int np, double *M, double *gh,
-                               double *rhs, double *ent, double *psi, int lane) {
-  const int m2 = 3 * np + 2, mm = K.mmax, nn = np + 1;
-  const int npairs = nn * (nn + 1) / 2;
-  for (int idx = lane; idx < npairs; idx += 32) {
-    int p = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-    while ((p + 1) * (p + 2) / 2 <= idx) ++p;
-    while (p * (p + 1) / 2 > idx) --p;
-    const int q = idx - p * (p + 1) / 2;
+// Lockstep slots.  Each warp works on FS_NG node rows at once, FS_GL lanes
+// per row ("slot"); every loop that contains a warp-wide step runs to the
+// warp's largest bound with the per-slot work predicated, so the FP64
+// instructions of the sequential parts (square roots and divisions of the
+// Cholesky factor and of the substitutions) serve FS_NG rows each.  FP64 issue
+// slots are the scarce resource of this GPU: a warp instruction costs the
+// same with one lane active as with 32.
+constexpr int FS_NG = 4;
+constexpr int FS_GL = 32 / FS_NG;
+
+__device__ __forceinline__ int warp_max(int v) {
+  for (int off = 16; off >= 1; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+// (rr, kk) with kk <= rr from the row-major index of a lower triangle
+__device__ __forceinline__ void tri_decode(int idx, int &rr, int &kk) {
+  int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+  while (r * (r + 1) / 2 > idx) --r;
+  rr = r;
+  kk = idx - r * (r + 1) / 2;
+}
+
+// Solve the 3 dof rows of node I on pattern pat[0..np-1] (slots with act);
+// returns 0 or an error, the same in every lane of a slot.  The system of
+// dof row c is A[Q_c, Q_c] with Q_c = (pattern dofs, 3I, ..., 3I+c-1), so the
+// systems of rows 0 and 1 are leading principal blocks of the system of row
+// 2: one Cholesky factor of the largest serves all three (entry (r,k) of a
+// Cholesky factor depends only on the leading (r+1)x(r+1) block, so each
+// row's factor is exactly what factoring it alone gives).  A is read one 3x3
+// block per node pair: the lower triangle of the largest system,
+// rhs_c = -A[Q_c, 3I+c] and ent_c = A[3I+c, Q_c].
+__device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, int np, double *M, double *gh,
+                               double *rhs, double *ent, double *psi, int g, int gl) {
+  const int m2 = act ? 3 * np + 2 : 0, mm = K.mmax, nn = np + 1;
+  const int npairs = act ? nn * (nn + 1) / 2 : 0;
+  for (int idx = gl; idx < npairs; idx += FS_GL) {
+    int p, q;
+    tri_decode(idx, p, q);
     const double *b = find_blk(K.Arp, K.Acol, K.Aval, p < np ? pat[p] : I, q < np ? pat[q] : I);
     for (int a = 0; a < 3; ++a) {
       const int r = 3 * p + a;
@@ -438,7 +462,7 @@ __device__ int fsai_solve_rows(const FsaiK &K, int I, const int *pat, int np, do
       }
     }
   }
-  for (int idx = lane; idx < nn; idx += 32) {
+  for (int idx = gl; idx < (act ? nn : 0); idx += FS_GL) {
     const int Np = idx < np ? pat[idx] : I;
     const double *bc = find_blk(K.Arp, K.Acol, K.Aval, Np, I);
     const double *br = find_blk(K.Arp, K.Acol, K.Aval, I, Np);
@@ -454,57 +478,74 @@ __device__ int fsai_solve_rows(const FsaiK &K, int I, const int *pat, int np, do
   __syncwarp();
   // right-looking Cholesky of the lower triangle (each entry receives its
   // updates k = 0, 1, ... in ascending order, then the division)
+  const int mx = warp_max(m2);
   int bad = 0;
-  for (int j = 0; j < m2; ++j) {
-    const double sjj = M[j * m2 + j];
-    if (!(sjj > 0.0)) { bad = 1; break; }
-    const double d = sqrt(sjj);
+  for (int j = 0; j < mx; ++j) {
+    const bool on = j < m2 && !bad;
+    double d = 1.0;
+    if (on) {
+      const double sjj = M[j * m2 + j];
+      if (!(sjj > 0.0)) bad = 1;
+      else d = sqrt(sjj);
+    }
     __syncwarp();
-    for (int r = j + 1 + lane; r < m2; r += 32) M[r * m2 + j] = M[r * m2 + j] / d;
-    if (lane == 0) M[j * m2 + j] = d;
+    if (on && !bad) {
+      for (int r = j + 1 + gl; r < m2; r += FS_GL) M[r * m2 + j] = M[r * m2 + j] / d;
+      if (gl == 0) M[j * m2 + j] = d;
+    }
     __syncwarp();
-    const int w = m2 - j - 1;
-    for (int idx = lane; idx < w * w; idx += 32) {
-      const int r = j + 1 + idx / w, k = j + 1 + idx % w;
-      if (k <= r) M[r * m2 + k] = fma(-M[r * m2 + j], M[k * m2 + j], M[r * m2 + k]);
+    if (on && !bad) {
+      const int w = m2 - j - 1, nt = w * (w + 1) / 2;
+      for (int idx = gl; idx < nt; idx += FS_GL) {
+        int rr, kk;
+        tri_decode(idx, rr, kk);
+        const int r = j + 1 + rr, k = j + 1 + kk;
+        M[r * m2 + k] = fma(-M[r * m2 + j], M[k * m2 + j], M[r * m2 + k]);
+      }
     }
     __syncwarp();
   }
-  if (bad) return AMG_ERR_NOT_SPD;
+  const bool ok = act && !bad;
   // forward substitution for the three right-hand sides together (row c
   // uses the leading 3np + c rows): y_k = rhs_k / L_kk, then rhs_r -= L_rk y_k
-  for (int k = 0; k < m2; ++k) {
-    if (lane < 3 && k < 3 * np + lane) rhs[lane * mm + k] = rhs[lane * mm + k] / M[k * m2 + k];
+  for (int k = 0; k < mx; ++k) {
+    if (ok && gl < 3 && k < 3 * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] / M[k * m2 + k];
     __syncwarp();
-    for (int idx = lane; idx < 3 * m2; idx += 32) {
-      const int c = idx / m2, r = idx - c * m2;
-      if (r > k && r < 3 * np + c) rhs[c * mm + r] = fma(-M[r * m2 + k], rhs[c * mm + k], rhs[c * mm + r]);
-    }
+    if (ok)
+      for (int idx = gl; idx < 3 * m2; idx += FS_GL) {
+        const int c = idx / m2, r = idx - c * m2;
+        if (r > k && r < 3 * np + c) rhs[c * mm + r] = fma(-M[r * m2 + k], rhs[c * mm + k], rhs[c * mm + r]);
+      }
     __syncwarp();
   }
   // backward substitution: x_k = rhs_k / L_kk for k descending, then
   // rhs_r -= L_kr x_k for r < k
-  for (int k = m2 - 1; k >= 0; --k) {
-    if (lane < 3 && k < 3 * np + lane) gh[lane * mm + k] = rhs[lane * mm + k] / M[k * m2 + k];
+  for (int k = mx - 1; k >= 0; --k) {
+    if (ok && gl < 3 && k < 3 * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] / M[k * m2 + k];
     __syncwarp();
-    for (int idx = lane; idx < 3 * k; idx += 32) {
-      const int c = idx / k, r = idx - c * k;
-      if (k < 3 * np + c) rhs[c * mm + r] = fma(-M[k * m2 + r], gh[c * mm + k], rhs[c * mm + r]);
-    }
+    if (ok && k < m2)
+      for (int idx = gl; idx < 3 * k; idx += FS_GL) {
+        const int c = idx / k, r = idx - c * k;
+        if (k < 3 * np + c) rhs[c * mm + r] = fma(-M[k * m2 + r], gh[c * mm + k], rhs[c * mm + r]);
+      }
     __syncwarp();
   }
   // psi_c = a_ii + sum_a A[i, Q_a] gh_a (a ascending), i = 3I + c
-  if (lane < 3) {
-    const int c = lane;
+  double sv = 0.0;
+  if (ok && gl < 3) {
+    const int c = gl;
     const double *bii = find_blk(K.Arp, K.Acol, K.Aval, I, I);
-    double sv = bii ? bii[c * 3 + c] : 0.0;
+    sv = bii ? bii[c * 3 + c] : 0.0;
     for (int a = 0; a < 3 * np + c; ++a) sv = fma(ent[c * mm + a], gh[c * mm + a], sv);
-    psi[c] = sv;
   }
+  double ps[3];
+  for (int c = 0; c < 3; ++c) ps[c] = __shfl_sync(0xffffffffu, sv, g * FS_GL + c);
   __syncwarp();
+  if (!act) return AMG_OK;
+  if (bad) return AMG_ERR_NOT_SPD;
   for (int c = 0; c < 3; ++c) {
-    psi[c] = __shfl_sync(0xffffffffu, psi[c], c);
-    if (!(psi[c] > 0.0)) return AMG_ERR_NOT_SPD;
+    if (!(ps[c] > 0.0)) return AMG_ERR_NOT_SPD;
+    psi[c] = ps[c];
   }
   return AMG_OK;
 }
@@ -519,114 +560,138 @@ __device__ __forceinline__ int in_sorted(const int *a, int n, int v) {
   return 0;
 }
 
-__device__ __forceinline__ int in_row(const int *rp, const int *col, int K, int v) {
-  int lo = rp[K], hi = rp[K + 1] - 1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    if (col[mid] == v) return 1;
-    if (col[mid] < v) lo = mid + 1; else hi = mid - 1;
+// Insert J into a slot's open-addressing set for one (node, step); entries of
+// earlier uses (another stamp) count as free.  Returns true when J is new.
+// The table holds at least twice as many entries as the step can insert.
+__device__ __forceinline__ bool set_insert(unsigned long long *tab, int cap, unsigned stamp, int J) {
+  const unsigned long long key = ((unsigned long long)stamp << 32) | (unsigned)J;
+  unsigned h = ((unsigned)J * 2654435761u) & (unsigned)(cap - 1);
+  for (int probe = 0; probe < cap; ++probe) {
+    unsigned long long cur = ((volatile unsigned long long *)tab)[h];
+    for (int tries = 0; (unsigned)(cur >> 32) != stamp && tries < 64; ++tries) {
+      const unsigned long long prev = atomicCAS(&tab[h], cur, key);
+      if (prev == cur) return true;
+      cur = prev;
+    }
+    if ((unsigned)(cur >> 32) == stamp && (unsigned)cur == (unsigned)J) return false;
+    h = (h + 1) & (unsigned)(cap - 1);
   }
-  return 0;
+  return false;
 }
 
 __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, g = lane / FS_GL, gl = lane % FS_GL;
   const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-  double *M = K.dscr + gw * K.dper;
-  double *gh = M + (size_t)K.mmax * K.mmax;
-  double *rhs = gh + 3 * K.mmax;
-  double *ent = rhs + 3 * K.mmax;
-  double *score = ent + 3 * K.mmax;
-  int *Q = K.iscr + gw * K.iper;
-  int *pat = Q + K.mmax;
+  const long slot = gw * FS_NG + g, nslots = nw * FS_NG;
+  const int mm = K.mmax;
+  double *M = K.dscr + slot * K.dper;
+  double *gh = M + (size_t)mm * mm;
+  double *rhs = gh + 3 * mm;
+  double *ent = rhs + 3 * mm;
+  double *score = ent + 3 * mm;
+  int *pat = K.iscr + slot * K.iper;
   int *cand = pat + K.maxg + 1;
-  for (long Il = gw; Il < K.n; Il += nw) {
-    const int I = (int)Il;
+  int *ccount = cand + K.candcap;
+  unsigned long long *tab = K.htab + slot * K.hcap;
+  const long nrounds = (K.n + nslots - 1) / nslots;
+  for (long rd = 0; rd < nrounds; ++rd) {
+    const long Il = rd * nslots + slot;
+    const bool have = Il < K.n;
+    const int I = have ? (int)Il : 0;
     int np = 0;
-    if (lane == 0 && K.Gsrp) {
+    if (have && gl == 0 && K.Gsrp) {
       for (int k = K.Gsrp[I]; k < K.Gsrp[I + 1]; ++k)
         if (K.Gscol[k] != I && np < K.maxg) pat[np++] = K.Gscol[k];
     }
-    np = __shfl_sync(0xffffffffu, np, 0);
+    np = __shfl_sync(0xffffffffu, np, g * FS_GL);
     __syncwarp();
-    double psi[3], psi_old[3];
-    int rc = fsai_solve_rows(K, I, pat, np, M, gh, rhs, ent, psi, lane);
-    for (int step = 0; step < K.ksteps && rc == 0; ++step) {
-      if (np >= K.maxg) break;
+    double psi[3] = {0.0, 0.0, 0.0}, psi_old[3];
+    int rc = fsai_solve_rows(K, have, I, pat, np, M, gh, rhs, ent, psi, g, gl);
+    bool active = have && rc == 0;
+    for (int step = 0; step < K.ksteps; ++step) {
+      if (active && np >= K.maxg) active = false;
+      if (!__any_sync(0xffffffffu, active)) break;
       // candidates: A-neighbours J < I of the pattern nodes and of I, outside
-      // the pattern, each listed once (first run that contains it)
-      int nc = 0;
-      for (int run = 0; run <= np; ++run) {
-        const int Kn = run < np ? pat[run] : I;
-        const int b0 = K.Arp[Kn], len = K.Arp[Kn + 1] - b0;
-        for (int base = 0; base < len; base += 32) {
-          int keep = 0, J = -1;
-          if (base + lane < len) {
-            J = K.Acol[b0 + base + lane];
-            keep = (J < I) && !in_sorted(pat, np, J);
-            for (int r2 = 0; keep && r2 < run; ++r2)
-              if (in_row(K.Arp, K.Acol, pat[r2], J)) keep = 0;
-          }
-          const unsigned bal = __ballot_sync(0xffffffffu, keep);
-          if (keep) cand[nc + __popc(bal & ((1u << lane) - 1u))] = J;
-          nc += __popc(bal);
-        }
-      }
+      // the pattern, each once (set of this node and step)
+      const unsigned stamp = (unsigned)(rd * (K.ksteps + 1) + step + 1);
+      if (gl == 0) *ccount = 0;
       __syncwarp();
-      for (int t = lane; t < nc; t += 32) {
+      if (active)
+        for (int run = 0; run <= np; ++run) {
+          const int Kn = run < np ? pat[run] : I;
+          const int b0 = K.Arp[Kn], len = K.Arp[Kn + 1] - b0;
+          for (int e = gl; e < len; e += FS_GL) {
+            const int J = K.Acol[b0 + e];
+            if (J < I && !in_sorted(pat, np, J) && set_insert(tab, K.hcap, stamp, J))
+              cand[atomicAdd(ccount, 1)] = J;
+          }
+        }
+      __syncwarp();
+      const int nc = active ? *(volatile int *)ccount : 0;
+      // gradient entries g[c][d] = (A gt_c)_{3J+d}: pattern dofs in
+      // ascending order, then the dofs 3I+e < 3I+c, then the unit entry;
+      // node score = sum over c, d of g^2
+      for (int t = gl; t < nc; t += FS_GL) {
         const int J = cand[t];
-        // gradient entries g[c][d] = (A gt_c)_{3J+d}: pattern dofs in
-        // ascending order, then the dofs 3I+e < 3I+c, then the unit entry
-        double g[3][3];
+        double gg[3][3];
         for (int c = 0; c < 3; ++c)
-          for (int d = 0; d < 3; ++d) g[c][d] = 0.0;
+          for (int d = 0; d < 3; ++d) gg[c][d] = 0.0;
         for (int j = 0; j < np; ++j) {
           const double *blk = find_blk(K.Arp, K.Acol, K.Aval, J, pat[j]);
           if (blk)
             for (int c = 0; c < 3; ++c)
               for (int d = 0; d < 3; ++d)
-                for (int e = 0; e < 3; ++e) g[c][d] = fma(blk[d * 3 + e], gh[c * K.mmax + 3 * j + e], g[c][d]);
+                for (int e = 0; e < 3; ++e) gg[c][d] = fma(blk[d * 3 + e], gh[c * mm + 3 * j + e], gg[c][d]);
         }
         const double *bI = find_blk(K.Arp, K.Acol, K.Aval, J, I);
-        double s = 0.0;
+        double sc = 0.0;
         for (int c = 0; c < 3; ++c)
           for (int d = 0; d < 3; ++d) {
-            double gv = g[c][d];
+            double gv = gg[c][d];
             if (bI) {
-              for (int e = 0; e < c; ++e) gv = fma(bI[d * 3 + e], gh[c * K.mmax + 3 * np + e], gv);
+              for (int e = 0; e < c; ++e) gv = fma(bI[d * 3 + e], gh[c * mm + 3 * np + e], gv);
               gv = gv + bI[d * 3 + c] * 1.0;
             }
-            s = fma(gv, gv, s);
+            sc = fma(gv, gv, sc);
           }
-        score[t] = s;
+        score[t] = sc;
       }
       __syncwarp();
-      const int want = K.rho < K.maxg - np ? K.rho : K.maxg - np;
+      // the rho best (score > 0, ties to the smaller node), by slot
+      const int want = active ? (K.rho < K.maxg - np ? K.rho : K.maxg - np) : 0;
+      const int wmax = warp_max(want);
       int got = 0;
-      for (int p = 0; p < want; ++p) {
+      bool more = true;
+      for (int p = 0; p < wmax; ++p) {
         double bs = -1.0;
         int bj = 0x7fffffff, bt = -1;
-        for (int t = lane; t < nc; t += 32) {
-          const double sc = score[t];
-          if (sc > 0.0 && (sc > bs || (sc == bs && cand[t] < bj))) { bs = sc; bj = cand[t]; bt = t; }
-        }
-        for (int off = 16; off >= 1; off >>= 1) {
+        if (more && p < want)
+          for (int t = gl; t < nc; t += FS_GL) {
+            const double sc = score[t];
+            if (sc > 0.0 && (sc > bs || (sc == bs && cand[t] < bj))) { bs = sc; bj = cand[t]; bt = t; }
+          }
+        for (int off = FS_GL / 2; off >= 1; off >>= 1) {
           const double os = __shfl_xor_sync(0xffffffffu, bs, off);
           const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
           const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
           if (os > bs || (os == bs && oj < bj)) { bs = os; bj = oj; bt = ot; }
         }
-        if (bt < 0) break;
-        if (lane == 0) {
-          pat[np + got] = bj;
-          score[bt] = -1.0;
+        if (more && p < want) {
+          if (bt < 0) {
+            more = false;
+          } else {
+            if (gl == 0) {
+              pat[np + got] = bj;
+              score[bt] = -1.0;
+            }
+            ++got;
+          }
         }
-        ++got;
         __syncwarp();
       }
-      if (got == 0) break;
-      if (lane == 0) {
+      if (active && got == 0) active = false;
+      if (active && gl == 0) {
         const int tot = np + got;
         for (int u = 1; u < tot; ++u) {
           const int v = pat[u];
@@ -635,32 +700,39 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
           pat[w + 1] = v;
         }
       }
-      np += got;
+      if (active) np += got;
       __syncwarp();
       for (int c = 0; c < 3; ++c) psi_old[c] = psi[c];
-      rc = fsai_solve_rows(K, I, pat, np, M, gh, rhs, ent, psi, lane);
-      if (rc) break;
-      int stalled = 1;
-      for (int c = 0; c < 3; ++c)
-        if (psi_old[c] - psi[c] > K.eps * psi_old[c]) stalled = 0;
-      if (stalled) break;
+      const int rc2 = fsai_solve_rows(K, active, I, pat, np, M, gh, rhs, ent, psi, g, gl);
+      if (active) {
+        if (rc2) {
+          rc = rc2;
+          active = false;
+        } else {
+          int stalled = 1;
+          for (int c = 0; c < 3; ++c)
+            if (psi_old[c] - psi[c] > K.eps * psi_old[c]) stalled = 0;
+          if (stalled) active = false;
+        }
+      }
     }
+    if (!have) continue;
     if (rc) {
-      if (lane == 0) atomicMin(K.status, rc);
+      if (gl == 0) atomicMin(K.status, rc);
       continue;
     }
-    if (lane == 0) K.out_np[I] = np;
-    for (int j = lane; j < np; j += 32) K.out_pat[(size_t)I * K.maxg + j] = pat[j];
+    if (gl == 0) K.out_np[I] = np;
+    for (int j = gl; j < np; j += FS_GL) K.out_pat[(size_t)I * K.maxg + j] = pat[j];
+    double sq[3];
+    for (int c = 0; c < 3; ++c) sq[c] = sqrt(psi[c]);
     double *ov = K.out_val + (size_t)I * (K.maxg + 1) * 9;
-    for (int idx = lane; idx < (np + 1) * 9; idx += 32) {
+    for (int idx = gl; idx < (np + 1) * 9; idx += FS_GL) {
       const int j = idx / 9, c = (idx % 9) / 3, d = idx % 3;
-      const double sq = sqrt(psi[c]);
-      double g;
-      if (j < np) g = gh[c * K.mmax + 3 * j + d];
-      else g = (d < c) ? gh[c * K.mmax + 3 * np + d] : (d == c ? 1.0 : 0.0);
-      ov[idx] = (j < np || d <= c) ? g / sq : 0.0;
+      double gv;
+      if (j < np) gv = gh[c * mm + 3 * j + d];
+      else gv = (d < c) ? gh[c * mm + 3 * np + d] : (d == c ? 1.0 : 0.0);
+      ov[idx] = (j < np || d <= c) ? gv / sq[c] : 0.0;
     }
-    __syncwarp();
   }
 }
 
@@ -683,22 +755,28 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   K.status = status;
   K.mmax = 3 * maxg + 3;
   K.candcap = (maxg + 1) * maxdeg;
+  K.hcap = 64;
+  while (K.hcap < 2 * K.candcap) K.hcap *= 2;
   K.dper = (long)K.mmax * K.mmax + 9L * K.mmax + K.candcap;
-  K.iper = K.mmax + (maxg + 1) + K.candcap;
+  K.iper = (maxg + 1) + K.candcap + 1;
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int threads = 128;
-  long nblocks = (long)nsm * 8;
-  const long need = ((long)A.nr + 3) / 4;
+  long nblocks = (long)nsm * 4;
+  const long need = ((long)A.nr + 4 * FS_NG - 1) / (4 * FS_NG);
   if (nblocks > need) nblocks = need > 0 ? need : 1;
-  const long nw = nblocks * (threads / 32);
+  const long nslots = nblocks * (threads / 32) * FS_NG;
   DBuf<double> ds;
   DBuf<int> is;
-  AMG_TRY(ds.alloc((size_t)nw * K.dper));
-  AMG_TRY(is.alloc((size_t)nw * K.iper));
+  DBuf<unsigned long long> hs;
+  AMG_TRY(ds.alloc((size_t)nslots * K.dper));
+  AMG_TRY(is.alloc((size_t)nslots * K.iper));
+  AMG_TRY(hs.alloc((size_t)nslots * K.hcap));
+  AMG_TRY(hs.zero(s));
   K.dscr = ds.p;
   K.iscr = is.p;
+  K.htab = hs.p;
   AMG_KCOUNT k_fsai<<<(int)nblocks, threads, 0, s>>>(K);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
@@ -1043,7 +1121,7 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
   return 0;
 }
 
-static int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
+int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
   if (A.nr == 0) return AMG_OK;
   AMG_KCOUNT k_spmv_cols<<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
   AMG_LAUNCH_CHECK();

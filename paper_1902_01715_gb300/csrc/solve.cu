@@ -592,8 +592,33 @@ int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
 // Average time of one solve-phase sparse product of a level matrix, launched
 // back to back on the handle's stream between CUDA events.
 int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes) {
-  if (lev < 0 || lev >= h->nlev || which < 0 || which > 4 || reps < 1) return AMG_ERR_ARG;
+  if (lev < 0 || lev >= h->nlev || which < 0 || which > 5 || reps < 1) return AMG_ERR_ARG;
   Level &L = *h->lev[lev];
+  if (which == 5) {  // the set-up's FP64 product of A_k with the n_tv test-space columns
+    const int t = h->prm.n_tv;
+    const size_t n = 3 * (size_t)L.A.nr;
+    if (L.A.nr == 0) return AMG_ERR_ARG;
+    cudaStream_t s = h->stream;
+    DBuf<double> X, Y;
+    AMG_TRY(X.alloc(n * t));
+    AMG_TRY(Y.alloc(n * t));
+    AMG_TRY(X.zero(s));
+    cudaEvent_t e0, e1;
+    AMG_CU(cudaEventCreate(&e0));
+    AMG_CU(cudaEventCreate(&e1));
+    AMG_TRY(det::spmv_cols(L.A, t, X.p, Y.p, s));
+    AMG_CU(cudaEventRecord(e0, s));
+    for (int i = 0; i < reps; ++i) AMG_TRY(det::spmv_cols(L.A, t, X.p, Y.p, s));
+    AMG_CU(cudaEventRecord(e1, s));
+    AMG_CU(cudaEventSynchronize(e1));
+    float tm = 0.f;
+    AMG_CU(cudaEventElapsedTime(&tm, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = (double)tm / reps;
+    *bytes = (double)L.A.nnzb * (9.0 * 8 + 4.0) + 4.0 * (L.A.nr + 1) + 8.0 * t * (2.0 * n);
+    return AMG_OK;
+  }
   SolveMat *M = which == 0 ? &L.sA : which == 1 ? &L.sG : which == 2 ? &L.sGT : which == 3 ? &L.sP : &L.sR;
   if (M->nr == 0) return AMG_ERR_ARG;
   cudaStream_t s = h->stream;

@@ -283,12 +283,23 @@ static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
   cudaEventDestroy(e1);
   AMG_LAUNCH_CHECK();
   map = bm;
+  if (getenv("AMG_TRACE"))
+    fprintf(stderr, "[amg] mapping kind %d rows %d avg %.1f -> %s (%.4f ms)\n", kind, M.nr, avg,
+            mapping_name(M, std::is_same<TM, double>::value), best / 3.0);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache.push_back({key, bm});
   return AMG_OK;
 }
 
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
+  // AMG_MAP=<0..5> pins the mapping of every matrix (for experiments)
+  if (const char *pin = getenv("AMG_MAP")) {
+    const int m = atoi(pin);
+    if (m >= 0 && m < kNumMaps) {
+      (kind == 0 ? M.map64 : M.map) = m;
+      return AMG_OK;
+    }
+  }
   if (M.nnzb < 100000 || getenv("AMG_NO_TUNE")) return AMG_OK;
   if (kind == 0) return tune_one<double, double>(M, M.v64.p, s, 0);
   if (kind == 1) return tune_one<float, float>(M, M.v32.p, s, 1);
