@@ -39,7 +39,10 @@ FP64_PEAK_SOURCE = "nominal FP64 rate (1.25 TFLOP/s); FMA-chain probe measured 1
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu captures summarised under profiles/; a kernel whose code changed since its
 # capture has no entry
-TRAFFIC: dict = {}
+TRAFFIC: dict = {
+    # level-0 A of the 128x32x32 beam times 10 columns: 307.25 MB read + 27.51 MB written
+    "k_spmv_cols": 334.76e6,
+}
 
 
 def peaks():
@@ -380,7 +383,11 @@ def run_micro(args):
                  "frac": by / ms / 1e6 / hbm})
     for k in range(S.nlev - 1):
         for which in ("A", "G", "GT", "P", "R"):
+            if k == 0 and which == "A":
+                torch.cuda.nvtx.range_push("spmv_A0_vcycle")
             ms, by = S.bench_spmv(k, which, a64=False, reps=args.reps)
+            if k == 0 and which == "A":
+                torch.cuda.nvtx.range_pop()
             rows.append({"level": k, "matrix": which, "prec": args.prec, "ms": ms, "GBps": by / ms / 1e6,
                          "frac": by / ms / 1e6 / hbm, "nnzb": S.level_info(k)["nnzb_" + ("A" if which == "A" else "G" if which in ("G", "GT") else "P")]})
     print(json.dumps({"micro": rows}), flush=True)
