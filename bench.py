@@ -146,6 +146,100 @@ def gpu_problem(A, p):
     return d
 
 
+def _timed(fn, reps=1):
+    """(result, ms) of fn() timed with CUDA events on the current stream,
+    after one untimed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / reps
+
+
+def extra_slab(A, W):
+    """The 256x256x4 layered slab: FP64, FP32 and FP32 with bf16-stored G, P
+    V-cycles inside FP64 CG to 1e-8 (set-up + solve per step)."""
+    import torch
+    p = W.slab()
+    d = gpu_problem(A, p)
+    out = {"workload": "slab 256x256x4 (%d dofs), E 1/1e4 layers, nu 0.45, h_z 0.05" % (3 * d["nfree"])}
+    x64 = None
+    for prec in ("fp64", "fp32", "bf16gp"):
+        S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec=prec)
+
+        def step():
+            S.update_values(d["vals"])
+            return S.solve(d["f"], RTOL)
+        (x, its, rel, rc), ms = _timed(step)
+        st = S.stats()
+        r = {"ms_per_solution": ms, "n_it": its[0], "setup_ms": st["T_p"] * 1e3, "solve_ms": st["T_s"] * 1e3}
+        if x64 is None:
+            x64 = x
+        else:
+            r["rel_diff_vs_fp64_solution"] = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+        out[prec] = r
+        S.close()
+    return out
+
+
+def extra_batched(A, W):
+    """The 96^3 cube with 64 load cases: one block solve (FP32 V-cycle, FP64
+    CG, per-column masks) against solving the cases one at a time in FP64."""
+    import torch
+    p = W.cube_batched()
+    d = gpu_problem(A, p)
+    k = p.nodal.shape[0]
+    F = torch.empty((3 * d["nfree"], k), dtype=torch.float64, device="cuda")
+    for c in range(k):
+        F[:, c] = A.fe_load(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.clamp_axis, "top_nodal",
+                            p=p.nodal[c].reshape(-1), nfree=d["nfree"])
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec="fp32")
+    (X, its, rel, rc), ms_b = _timed(lambda: S.solve(F, RTOL))
+    S64 = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
+    (x1, it1, rel1, rc1), ms_1 = _timed(lambda: S64.solve(F[:, 0].contiguous(), RTOL))
+    out = {"workload": "cube 96^3 (%d dofs), 64 load cases N(0,1) on the top face" % (3 * d["nfree"]),
+           "k": k, "batched_fp32_ms": ms_b, "batched_solutions_per_s": k * 1e3 / ms_b,
+           "n_it_max": max(its), "n_it_min": min(its), "single_fp64_ms": ms_1, "single_fp64_n_it": it1[0],
+           "speedup_per_solution_vs_single_fp64": ms_1 * k / ms_b,
+           "setup_ms": S.stats()["T_p"] * 1e3,
+           "rel_diff_col0_vs_fp64": float(torch.linalg.norm(X[:, 0] - x1) / torch.linalg.norm(x1))}
+    S.close()
+    S64.close()
+    return out
+
+
+def extra_adjoint(A, W):
+    """The 128^3 SIMP cube: compliance, its gradient for every element by one
+    forward and one adjoint solve (FP32 V-cycle, FP64 CG) and the element
+    gather kernel."""
+    import torch
+    p = W.cube_simp()
+    d = gpu_problem(A, p)
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec="fp32")
+    conn = A.fe_conn(p.nx, p.ny, p.nz, p.clamp_axis)
+    rho = torch.tensor(p.rho, device="cuda")
+
+    def step():
+        r = rho.clone().requires_grad_(True)
+        u = A.LinearSolve.apply(S, d["f"], r ** 3, d["Ke0"], conn, RTOL)
+        L = torch.dot(d["f"], u)
+        L.backward()
+        return r.grad
+    g, ms = _timed(step)
+    st = S.stats()
+    out = {"workload": "SIMP cube 128^3 (%d dofs, %d elements), rho ~ U(0.1, 1), E = rho^3"
+                       % (3 * d["nfree"], p.ne),
+           "forward_adjoint_gradient_ms": ms, "setup_ms": st["T_p"] * 1e3, "n_it": st["n_it"],
+           "grad_abs_sum": float(g.abs().sum())}
+    S.close()
+    return out
+
+
 def oracle_sample(reps=1):
     """Oracle set-up + PCG to 1e-8 on the scaled-down beam; seconds per
     solution scaled by the dof count to the full workload."""
@@ -328,6 +422,11 @@ def run_ours(args):
         e2e = {"value": ws / t, "unit": UNIT, "h2d_bytes_per_step": int(vh.numel() * 8 + fh.numel() * 8),
                "d2h_bytes_per_step": int(xh.numel() * 8), "ms_per_step": t * 1e3}
 
+    extras = None
+    if not args.no_extras:
+        extras = {"mixed_precision": extra_slab(A, W), "batched": extra_batched(A, W),
+                  "adjoint": extra_adjoint(A, W)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, sample, it_o = oracle_sample(2)
@@ -354,6 +453,7 @@ def run_ours(args):
         "fp32_vcycle": fp32,
         "roofline": roofline,
         "roofline_spmv": roofline_spmv,
+        "configs": extras,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -430,6 +530,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the slab, batched and adjoint runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
