@@ -220,8 +220,10 @@ struct Handle {
 };
 
 // ---- set-up (setup.cu) ----
+// keep_pattern: take the level-0 pattern the handle already holds (rowptr and
+// col unused) and replace only the values
 int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *vals, int mem,
-                    int ntv0, const double *V0, int memV);
+                    int ntv0, const double *V0, int memV, bool keep_pattern = false);
 void free_hierarchy(Handle *h);
 
 // ---- solve (solve.cu) ----

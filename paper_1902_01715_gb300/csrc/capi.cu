@@ -96,10 +96,9 @@ extern "C" int amg_update_values(amg_handle hh, const double *vals, int mem) {
   Handle *h = (Handle *)hh;
   if (!h || !vals || (mem != AMG_MEM_HOST && mem != AMG_MEM_DEVICE)) return AMG_ERR_ARG;
   // same pattern and starting near-null space; the adaptive set-up depends on
-  // the values, so the whole hierarchy is rebuilt
-  std::vector<int> rp = h->lev[0]->A.h_rowptr, cl = h->lev[0]->A.h_col;
-  return build_hierarchy(h, rp.data(), cl.data(), vals, mem == AMG_MEM_HOST ? AMG_MEM_HOST : AMG_MEM_DEVICE,
-                         h->ntv0, h->V0keep.p, AMG_MEM_DEVICE);
+  // the values, so the whole hierarchy is rebuilt on the pattern it holds
+  return build_hierarchy(h, nullptr, nullptr, vals, mem == AMG_MEM_HOST ? AMG_MEM_HOST : AMG_MEM_DEVICE,
+                         h->ntv0, h->V0keep.p, AMG_MEM_DEVICE, true);
 }
 
 static int staged_solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres,

@@ -3,14 +3,17 @@
 // (Sec. 3.3), DPLS prolongation (Algorithm 5) and the Galerkin product.
 // Floating-point work runs in the kernels of det.cu; this file does the
 // control flow and the integer graph work (pattern compaction and
-// transposition, the maximal independent set, DPLS candidate sets and the
-// symbolic Galerkin pattern) on the host.
+// transposition, DPLS candidate sets and the symbolic Galerkin pattern) on
+// the host; the maximal independent set runs in rounds on the GPU.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdarg>
 #include <cstdlib>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <thread>
 
 #include "amg_internal.h"
@@ -230,32 +233,89 @@ int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s) {
   return AMG_OK;
 }
 
-// Greedy maximal independent set of the strong graph: nodes by degree
-// descending, index ascending; a visited undecided node becomes coarse and
-// its strong neighbours fine.
-static void mis_host(const DevBsr &A, const std::vector<unsigned char> &strong, std::vector<int> &cf) {
-  const int n = A.nr;
-  std::vector<int> deg(n, 0);
-  int maxdeg = 0;
-  for (int I = 0; I < n; ++I) {
-    for (int k = A.h_rowptr[I]; k < A.h_rowptr[I + 1]; ++k)
-      if (strong[k] && A.h_col[k] != I) deg[I]++;
-    maxdeg = std::max(maxdeg, deg[I]);
-  }
-  std::vector<int> cnt(maxdeg + 2, 0), order(n);
-  for (int I = 0; I < n; ++I) cnt[maxdeg - deg[I] + 1]++;
-  for (int d = 0; d <= maxdeg; ++d) cnt[d + 1] += cnt[d];
-  for (int I = 0; I < n; ++I) order[cnt[maxdeg - deg[I]]++] = I;
-  cf.assign(n, -1);
-  for (int q = 0; q < n; ++q) {
-    const int I = order[q];
-    if (cf[I] != -1) continue;
-    cf[I] = 1;
-    for (int k = A.h_rowptr[I]; k < A.h_rowptr[I + 1]; ++k) {
-      const int J = A.h_col[k];
-      if (strong[k] && J != I && cf[J] == -1) cf[J] = 0;
+// Maximal independent set of the strong graph, the one the greedy visit by
+// (degree descending, index ascending) gives: a visited undecided node
+// becomes coarse and its strong neighbours fine.  The same set comes out of
+// rounds in which every undecided node that outranks all its undecided strong
+// neighbours becomes coarse and the undecided neighbours of the new coarse
+// nodes become fine (the greedy order restricted to the undecided nodes puts
+// such a node first among its neighbours), so the GPU runs rounds.
+__device__ __forceinline__ bool mis_beats(int di, int i, int dj, int j) { return di > dj || (di == dj && i < j); }
+
+__global__ void k_mis_deg(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                          const unsigned char *__restrict__ strong, int *__restrict__ deg, int *__restrict__ state) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  int d = 0;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) d += (strong[k] && col[k] != I);
+  deg[I] = d;
+  state[I] = -1;
+}
+
+// flag = undecided nodes that outrank every undecided strong neighbour
+__global__ void k_mis_select(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                             const unsigned char *__restrict__ strong, const int *__restrict__ deg,
+                             const int *__restrict__ state, unsigned char *__restrict__ flag, int *__restrict__ left) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  unsigned char f = 0;
+  if (state[I] == -1) {
+    atomicAdd(left, 1);
+    f = 1;
+    const int di = deg[I];
+    for (int k = rp[I]; k < rp[I + 1] && f; ++k) {
+      const int J = col[k];
+      if (strong[k] && J != I && state[J] == -1 && !mis_beats(di, I, deg[J], J)) f = 0;
     }
   }
+  flag[I] = f;
+}
+
+__global__ void k_mis_apply(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                            const unsigned char *__restrict__ strong, const unsigned char *__restrict__ flag,
+                            int *__restrict__ state) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n || state[I] != -1) return;
+  if (flag[I]) {
+    state[I] = 1;
+    return;
+  }
+  for (int k = rp[I]; k < rp[I + 1]; ++k)
+    if (strong[k] && col[k] != I && flag[col[k]]) {
+      state[I] = 0;
+      return;
+    }
+}
+
+static int mis_gpu(const DevBsr &A, const unsigned char *d_strong, std::vector<int> &cf, cudaStream_t s) {
+  const int n = A.nr;
+  cf.assign(n, 0);
+  if (n == 0) return AMG_OK;
+  DBuf<int> deg, state, left;
+  DBuf<unsigned char> flag;
+  AMG_TRY(deg.alloc(n));
+  AMG_TRY(state.alloc(n));
+  AMG_TRY(flag.alloc(n));
+  AMG_TRY(left.alloc(1));
+  const int nb = nblk(n, 256);
+  AMG_KCOUNT k_mis_deg<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state.p);
+  AMG_LAUNCH_CHECK();
+  for (int round = 0;; ++round) {
+    AMG_TRY(left.zero(s));
+    AMG_KCOUNT k_mis_select<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state.p, flag.p, left.p);
+    AMG_KCOUNT k_mis_apply<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, flag.p, state.p);
+    AMG_LAUNCH_CHECK();
+    int hl = 0;
+    AMG_CU(cudaMemcpyAsync(&hl, left.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CU(cudaStreamSynchronize(s));
+    if (hl == 0) break;
+    if (round > n) {  // every round decides at least the top-ranked undecided node
+      set_error("MIS: no progress");
+      return AMG_ERR_CUDA;
+    }
+  }
+  AMG_CU(cudaMemcpy(cf.data(), state.p, n * sizeof(int), cudaMemcpyDeviceToHost));
+  return AMG_OK;
 }
 
 // Host worker pool for the row-parallel graph work: rows are cut into
@@ -271,6 +331,70 @@ static int host_threads() {
   return n;
 }
 
+// Persistent workers: parallel_ranges hands each worker one contiguous range
+// and waits for all of them (threads are created once per process).
+class HostPool {
+ public:
+  static HostPool &get() {
+    static HostPool pool(host_threads());
+    return pool;
+  }
+  void run(int nt, const std::function<void(int)> &job) {
+    std::lock_guard<std::mutex> one_at_a_time(run_mu_);  // callers from several host threads
+    std::unique_lock<std::mutex> lock(mu_);
+    job_ = &job;
+    njobs_ = nt;
+    next_ = 1;
+    done_ = 0;
+    ++epoch_;
+    cv_.notify_all();
+    lock.unlock();
+    job(0);  // the caller takes range 0
+    lock.lock();
+    ++done_;
+    done_cv_.wait(lock, [&] { return done_ == njobs_; });
+    job_ = nullptr;
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      stop_ = true;
+      ++epoch_;
+    }
+    cv_.notify_all();
+    for (auto &t : th_) t.join();
+  }
+
+ private:
+  explicit HostPool(int n) {
+    for (int i = 1; i < n; ++i) th_.emplace_back([this] { loop(); });
+  }
+  void loop() {
+    long seen = 0;
+    std::unique_lock<std::mutex> lock(mu_);
+    for (;;) {
+      cv_.wait(lock, [&] { return stop_ || (epoch_ != seen && job_ && next_ < njobs_); });
+      if (stop_) return;
+      seen = epoch_;
+      while (job_ && next_ < njobs_) {
+        const int id = next_++;
+        const std::function<void(int)> *job = job_;
+        lock.unlock();
+        (*job)(id);
+        lock.lock();
+        if (++done_ == njobs_) done_cv_.notify_all();
+      }
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)> *job_ = nullptr;
+  int njobs_ = 0, next_ = 0, done_ = 0;
+  long epoch_ = 0;
+  bool stop_ = false;
+};
+
 template <class F>
 static void parallel_ranges(int n, F f) {
   const int nt = std::min(host_threads(), std::max(1, n / 2048));
@@ -278,12 +402,35 @@ static void parallel_ranges(int n, F f) {
     f(0, 0, n);
     return;
   }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t) {
+  const std::function<void(int)> job = [&](int t) {
     const int lo = (int)((long)n * t / nt), hi = (int)((long)n * (t + 1) / nt);
-    th.emplace_back(f, t, lo, hi);
+    f(t, lo, hi);
+  };
+  HostPool::get().run(nt, job);
+}
+
+// Concatenates per-range outputs in range order: row lengths into a row
+// pointer starting at rp[0], entries into out (both filled in parallel).
+static void concat_ranges(const std::vector<std::vector<int>> &len, const std::vector<std::vector<int>> &ent,
+                          std::vector<int> &rp, std::vector<int> &out) {
+  const int nt = (int)len.size();
+  std::vector<long> row0(nt + 1, 0), e0(nt + 1, 0);
+  for (int t = 0; t < nt; ++t) {
+    row0[t + 1] = row0[t] + (long)len[t].size();
+    e0[t + 1] = e0[t] + (long)ent[t].size();
   }
-  for (auto &x : th) x.join();
+  rp.assign(row0[nt] + 1, 0);
+  out.resize(e0[nt]);
+  const std::function<void(int)> job = [&](int t) {
+    std::copy(ent[t].begin(), ent[t].end(), out.begin() + e0[t]);
+    long r = row0[t], acc = e0[t];
+    for (int l : len[t]) {
+      acc += l;
+      rp[++r] = (int)acc;
+    }
+  };
+  if (nt > 1) HostPool::get().run(nt, job);
+  else if (nt == 1) job(0);
 }
 
 // Coarse nodes within d_p strong edges of every fine node, ascending.
@@ -318,13 +465,8 @@ static void dpls_candidates(const DevBsr &A, const std::vector<unsigned char> &s
     }
   });
   fnodes.clear();
-  cand.clear();
-  cptr.assign(1, 0);
-  for (int t = 0; t < (int)pf.size(); ++t) {
-    fnodes.insert(fnodes.end(), pf[t].begin(), pf[t].end());
-    cand.insert(cand.end(), pc[t].begin(), pc[t].end());
-    for (int l : pl[t]) cptr.push_back(cptr.back() + l);
-  }
+  for (int t = 0; t < (int)pf.size(); ++t) fnodes.insert(fnodes.end(), pf[t].begin(), pf[t].end());
+  concat_ranges(pl, pc, cptr, cand);
 }
 
 // Pattern of Z = X Y (columns ascending).
@@ -352,16 +494,7 @@ static void symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z) {
       len.push_back((int)cols.size());
     }
   });
-  Z.h_rowptr.assign(nr + 1, 0);
-  Z.h_col.clear();
-  int row = 0;
-  for (int t = 0; t < (int)pcols.size(); ++t) {
-    Z.h_col.insert(Z.h_col.end(), pcols[t].begin(), pcols[t].end());
-    for (int l : plen[t]) {
-      Z.h_rowptr[row + 1] = Z.h_rowptr[row] + l;
-      ++row;
-    }
-  }
+  concat_ranges(plen, pcols, Z.h_rowptr, Z.h_col);
   Z.nr = nr;
   Z.nc = nc;
   Z.nnzb = (int)Z.h_col.size();
@@ -372,12 +505,7 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
   double tt = now_s();
   symbolic_product(A, P, AP);
   trace("AP symbolic", -1, tt);
-  {
-    std::vector<int> rp = AP.h_rowptr, cl = AP.h_col;
-    AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb));
-    AP.h_rowptr = rp;
-    AP.h_col = cl;
-  }
+  AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb));
   AMG_TRY(AP.upload_pattern(s));
   tt = now_s();
   AMG_TRY(det::spgemm_numeric(A, P, AP, s));
@@ -386,12 +514,7 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
   tt = now_s();
   symbolic_product(R, AP, Ac);
   trace("RAP symbolic", -1, tt);
-  {
-    std::vector<int> rp = Ac.h_rowptr, cl = Ac.h_col;
-    AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb));
-    Ac.h_rowptr = rp;
-    Ac.h_col = cl;
-  }
+  AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb));
   AMG_TRY(Ac.upload_pattern(s));
   tt = now_s();
   AMG_TRY(det::spgemm_numeric(R, AP, Ac, s));
@@ -424,13 +547,16 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
   std::vector<int> hnp(n), hpat((size_t)n * maxg);
   AMG_CU(cudaMemcpy(hnp.data(), np.p, n * sizeof(int), cudaMemcpyDeviceToHost));
   AMG_CU(cudaMemcpy(hpat.data(), pat.p, (size_t)n * maxg * sizeof(int), cudaMemcpyDeviceToHost));
-  std::vector<int> rp(n + 1, 0), cl;
-  cl.reserve((size_t)n * 8);
-  for (int I = 0; I < n; ++I) {
-    for (int j = 0; j < hnp[I]; ++j) cl.push_back(hpat[(size_t)I * maxg + j]);
-    cl.push_back(I);
-    rp[I + 1] = (int)cl.size();
-  }
+  std::vector<int> rp(n + 1, 0);
+  for (int I = 0; I < n; ++I) rp[I + 1] = rp[I] + hnp[I] + 1;
+  std::vector<int> cl(rp[n]);
+  parallel_ranges(n, [&](int, int lo, int hi) {
+    for (int I = lo; I < hi; ++I) {
+      int *o = cl.data() + rp[I];
+      for (int j = 0; j < hnp[I]; ++j) o[j] = hpat[(size_t)I * maxg + j];
+      o[hnp[I]] = I;
+    }
+  });
   AMG_TRY(G.alloc(n, n, (int)cl.size()));
   G.h_rowptr = std::move(rp);
   G.h_col = std::move(cl);
@@ -594,16 +720,26 @@ void free_hierarchy(Handle *h) {
 }
 
 int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *vals, int mem, int ntv0,
-                    const double *V0, int memV) {
+                    const double *V0, int memV, bool keep_pattern) {
   const amg_params &p = h->prm;
   cudaStream_t s = h->stream;
   const int t = p.n_tv;
-  free_hierarchy(h);
   const double t_start = now_s();
   double T_sm = 0, T_ts = 0, T_cs = 0, T_pl = 0, T_rap = 0;
   const cudaMemcpyKind kind = mem == AMG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   auto L0 = std::make_unique<Level>();
-  {
+  if (keep_pattern && !h->lev.empty() && h->lev[0]->A.nr == h->n) {
+    // new values on the pattern already held (checked when it was set up)
+    L0->A = std::move(h->lev[0]->A);
+    L0->n = L0->A.nr;
+    free_hierarchy(h);
+    AMG_CU(cudaMemcpyAsync(L0->A.val.p, vals, (size_t)L0->A.nnzb * 9 * sizeof(double), kind, s));
+  } else {
+    free_hierarchy(h);
+    if (!rowptr || !col) {
+      set_error("no level-0 pattern to reuse");
+      return AMG_ERR_ARG;
+    }
     const int n = h->n;
     std::vector<int> hrp(n + 1);
     if (mem == AMG_MEM_HOST) memcpy(hrp.data(), rowptr, (n + 1) * sizeof(int));
@@ -671,7 +807,10 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     std::vector<unsigned char> strong(L.A.nnzb);
     if (L.A.nnzb)
       AMG_CU(cudaMemcpy(strong.data(), d_strong.p, L.A.nnzb, cudaMemcpyDeviceToHost));
-    mis_host(L.A, strong, L.cf);
+    trace("SoC filter", k, t2);
+    double tm = now_s();
+    AMG_TRY(mis_gpu(L.A, d_strong.p, L.cf, s));
+    trace("MIS", k, tm);
     int nc = 0;
     for (int I = 0; I < L.n; ++I) nc += (L.cf[I] == 1);
     double t3 = now_s();

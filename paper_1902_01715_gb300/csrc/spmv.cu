@@ -13,10 +13,10 @@
 // one contiguous run of memory.  Padding slots (rows shorter than the
 // slice's longest) are never read: each lane stops at its own row length.
 //
-// Mapping.  A CTA of 128 threads holds 4 warps; WPS warps share one slice
-// (warp p of the slice takes blocks j = p, p + WPS, ...) and their partial
-// sums are added in warp order through shared memory, so small coarse
-// levels still spread over the SMs.  In FP64 every product is one fused
+// Mapping.  WPS warps share one slice (warp p of the slice takes blocks
+// j = p, p + WPS, ...) and their partial sums are added in warp order through
+// shared memory, so small coarse levels with long rows still spread over the
+// SMs; a CTA holds 4 warps (WPS <= 4) or one slice's WPS warps (8, 16).  In FP64 every product is one fused
 // multiply-add into the row's accumulator (9 per block): FP64 arithmetic is
 // the scarce resource of this GPU (about 0.63e12 FP64 FMA/s against
 // 6.7 TB/s of HBM, i.e. 10.6 bytes per FMA, while an FP64 block brings 8.4
@@ -41,16 +41,26 @@ __device__ __forceinline__ float cvs(__nv_bfloat16 v, float) { return __bfloat16
 struct Mapping {
   int wps, u;
 };
-static const Mapping kMaps[] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}, {4, 4}};
+static const Mapping kMaps[] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}, {4, 4}, {8, 2}, {16, 2}};
 constexpr int kNumMaps = (int)(sizeof(kMaps) / sizeof(kMaps[0]));
 
+// CTA size: 4 warps, or one slice of WPS warps when WPS > 4
+template <int WPS> struct SellCta {
+  static constexpr int warps = WPS > 4 ? WPS : 4;
+  static constexpr int threads = 32 * warps;
+  static constexpr int slices = warps / WPS;
+};
+
 template <typename TM, typename TX, int EP, int WPS, int U>
-__global__ void __launch_bounds__(128) k_sellmv(int nr, const int *__restrict__ rp, const int *__restrict__ slp,
-                                                const int *__restrict__ scol, const TM *__restrict__ v,
-                                                const TX *__restrict__ x, TX *__restrict__ y,
-                                                const TX *__restrict__ aux, TX w, const int *__restrict__ done) {
+__global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int nr, const int *__restrict__ rp,
+                                                                  const int *__restrict__ slp,
+                                                                  const int *__restrict__ scol,
+                                                                  const TM *__restrict__ v,
+                                                                  const TX *__restrict__ x, TX *__restrict__ y,
+                                                                  const TX *__restrict__ aux, TX w,
+                                                                  const int *__restrict__ done) {
   if (done && *done) return;
-  constexpr int SPB = 4 / WPS;
+  constexpr int SPB = SellCta<WPS>::slices;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sl = blockIdx.x * SPB + warp / WPS;
   const int part = warp % WPS;
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(128) k_sellmv(int nr, const int *__restrict__ 
     }
   }
   if (WPS > 1) {
-    __shared__ TX red[4][6][32];
+    __shared__ TX red[SellCta<WPS>::warps][6][32];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       red[warp][r][lane] = acc.hi(r);
@@ -112,15 +122,16 @@ __global__ void __launch_bounds__(128) k_sellmv(int nr, const int *__restrict__ 
 template <typename TM, typename TX, int WPS, int U>
 static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
                        const int *done, cudaStream_t s) {
-  const int nb = nblk(M.ns, 4 / WPS);
+  const int nb = nblk(M.ns, SellCta<WPS>::slices);
+  constexpr int T = SellCta<WPS>::threads;
   if (nb == 0) return;
 #define AMG_SELL_ARGS M.nr, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
   switch (ep) {
-    case EP_SET: AMG_KCOUNT k_sellmv<TM, TX, EP_SET, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SCALE: AMG_KCOUNT k_sellmv<TM, TX, EP_SCALE, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_RESID: AMG_KCOUNT k_sellmv<TM, TX, EP_RESID, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SADD: AMG_KCOUNT k_sellmv<TM, TX, EP_SADD, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
-    default: AMG_KCOUNT k_sellmv<TM, TX, EP_ACC, WPS, U><<<nb, 128, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SET: AMG_KCOUNT k_sellmv<TM, TX, EP_SET, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SCALE: AMG_KCOUNT k_sellmv<TM, TX, EP_SCALE, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_RESID: AMG_KCOUNT k_sellmv<TM, TX, EP_RESID, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SADD: AMG_KCOUNT k_sellmv<TM, TX, EP_SADD, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    default: AMG_KCOUNT k_sellmv<TM, TX, EP_ACC, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
   }
 #undef AMG_SELL_ARGS
 }
@@ -134,7 +145,9 @@ void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX 
     case 2: launch_map<TM, TX, 2, 2>(ep, M, v, x, y, aux, w, done, s); break;
     case 3: launch_map<TM, TX, 2, 4>(ep, M, v, x, y, aux, w, done, s); break;
     case 4: launch_map<TM, TX, 4, 2>(ep, M, v, x, y, aux, w, done, s); break;
-    default: launch_map<TM, TX, 4, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 5: launch_map<TM, TX, 4, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 6: launch_map<TM, TX, 8, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    default: launch_map<TM, TX, 16, 2>(ep, M, v, x, y, aux, w, done, s); break;
   }
 }
 
@@ -175,12 +188,21 @@ __global__ void k_to_sell(int nr, const int *__restrict__ rp, const int *__restr
   }
 }
 
-// Mapping rule for matrices too small to time: short rows or few slices
-// leave SMs idle unless several warps share a slice.
+// Mapping rule for matrices too small to time: few slices of long rows
+// leave SMs idle unless several warps share a slice, so the warps per slice
+// double while the launch has fewer than 16 warps per SM and each warp keeps
+// at least two blocks of an average row per chunk.
 static int rule_map(const SolveMat &M) {
-  if (M.ns < 1024) return 4;  // WPS 4, U 2
-  if (M.ns < 4096) return 2;  // WPS 2, U 2
-  return 0;                   // WPS 1, U 2
+  const double avg = M.nr ? (double)M.nnzb / M.nr : 1.0;
+  int wps = 1;
+  while (wps < 16 && (long)M.ns * wps < 16L * 152 && avg / (2.0 * wps * 2) >= 1.0) wps *= 2;
+  switch (wps) {
+    case 1: return 0;   // WPS 1, U 2
+    case 2: return 2;   // WPS 2, U 2
+    case 4: return 4;   // WPS 4, U 2
+    case 8: return 6;   // WPS 8, U 2
+    default: return 7;  // WPS 16, U 2
+  }
 }
 
 int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s) {
@@ -292,7 +314,7 @@ static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
 }
 
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
-  // AMG_MAP=<0..5> pins the mapping of every matrix (for experiments)
+  // AMG_MAP=<0..7> pins the mapping of every matrix (for experiments)
   if (const char *pin = getenv("AMG_MAP")) {
     const int m = atoi(pin);
     if (m >= 0 && m < kNumMaps) {
@@ -307,7 +329,8 @@ int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
 }
 
 const char *mapping_name(const SolveMat &M, bool f64) {
-  static const char *names[kNumMaps] = {"wps1_u2", "wps1_u4", "wps2_u2", "wps2_u4", "wps4_u2", "wps4_u4"};
+  static const char *names[kNumMaps] = {"wps1_u2", "wps1_u4", "wps2_u2", "wps2_u4",
+                                        "wps4_u2", "wps4_u4", "wps8_u2", "wps16_u2"};
   const int m = f64 ? M.map64 : M.map;
   return (m >= 0 && m < kNumMaps) ? names[m] : "?";
 }
