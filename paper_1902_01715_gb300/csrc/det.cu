@@ -1383,26 +1383,51 @@ __global__ void k_soc_nrm(int nn, int t, const double *__restrict__ V, double *_
   nrm[I] = sqrt(fro2(M));
 }
 
-// SoC of every block of row I (smaller node first), then the theta largest
-// positive ones are kept (ties to the smaller column).
-__global__ void k_soc_filter(int nn, int t, const int *__restrict__ rp, const int *__restrict__ col,
-                             const double *__restrict__ V, const double *__restrict__ nrm, int theta,
-                             double *__restrict__ soc, unsigned char *__restrict__ kept) {
+__device__ __forceinline__ int find_in_row(const int *rp, const int *col, int row, int v) {
+  int lo = rp[row], hi = rp[row + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    if (col[mid] == v) return mid;
+    if (col[mid] < v) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// SoC of the block pair {(I,J), (J,I)} with I < J, computed once from the
+// smaller node first and written to both positions (one thread per stored
+// block of the upper triangle); diagonal blocks get 0.
+__global__ void k_soc_pairs(int nn, int nnzb, int t, const int *__restrict__ rp, const int *__restrict__ col,
+                            const double *__restrict__ V, const double *__restrict__ nrm, double *__restrict__ soc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnzb) return;
+  int lo = 0, hi = nn - 1;
+  while (lo < hi) {  // row of block k: last row with rp[row] <= k
+    const int mid = (lo + hi + 1) >> 1;
+    if (rp[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  const int I = lo, J = col[k];
+  if (J == I) {
+    soc[k] = 0.0;
+    return;
+  }
+  const int kt = find_in_row(rp, col, J, I);
+  if (J < I && kt >= 0) return;  // the mirror's thread writes both
+  const int a = I < J ? I : J, b = I < J ? J : I;
+  double M[9];
+  node_gram(3L * nn, t, V, a, b, M);
+  const double num = fro2(M), den = nrm[a] * nrm[b];
+  const double v = den > 0.0 ? num / den : 0.0;
+  soc[k] = v;
+  if (kt >= 0) soc[kt] = v;
+}
+
+// The theta largest positive SoC of row I are kept (ties to the smaller
+// column).
+__global__ void k_soc_select(int nn, const int *__restrict__ rp, const int *__restrict__ col,
+                             const double *__restrict__ soc, int theta, unsigned char *__restrict__ kept) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nn) return;
-  double M[9];
-  for (int k = rp[I]; k < rp[I + 1]; ++k) {
-    const int J = col[k];
-    kept[k] = 0;
-    if (J == I) {
-      soc[k] = 0.0;
-      continue;
-    }
-    const int lo = I < J ? I : J, hi = I < J ? J : I;
-    node_gram(3L * nn, t, V, lo, hi, M);
-    const double num = fro2(M), den = nrm[lo] * nrm[hi];
-    soc[k] = den > 0.0 ? num / den : 0.0;
-  }
+  for (int k = rp[I]; k < rp[I + 1]; ++k) kept[k] = 0;
   for (int p = 0; p < theta; ++p) {
     int best = -1;
     for (int k = rp[I]; k < rp[I + 1]; ++k)
@@ -1435,8 +1460,10 @@ int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char
   AMG_TRY(soc.alloc(A.nnzb));
   AMG_TRY(kept.alloc(A.nnzb));
   const int nb = nblk(A.nr, 128);
+  AMG_TRY(soc.zero(s));
   AMG_KCOUNT k_soc_nrm<<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
-  AMG_KCOUNT k_soc_filter<<<nb, 128, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, theta, soc.p, kept.p);
+  AMG_KCOUNT k_soc_pairs<<<nblk(A.nnzb, 128), 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+  AMG_KCOUNT k_soc_select<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, soc.p, theta, kept.p);
   AMG_KCOUNT k_strong<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, kept.p, strong);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));

@@ -500,22 +500,125 @@ static void symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z) {
   Z.nnzb = (int)Z.h_col.size();
 }
 
+// Pattern of Z = X Y on the GPU: row i of Z is the union of the (sorted)
+// rows of Y named by row i of X.  One warp per row merges them: lane l holds
+// the heads of lists l, l+32, ...; each step takes the warp minimum, emits it
+// once and advances every list whose head equals it, so the output is
+// ascending and duplicate-free.  Pass 0 counts, pass 1 writes.
+__global__ void k_sym_merge(int nr, const int *__restrict__ xr, const int *__restrict__ xc,
+                            const int *__restrict__ yr, const int *__restrict__ yc, const int *__restrict__ zr,
+                            int *__restrict__ zc, int *__restrict__ cnt) {
+  const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= nr) return;
+  const int l0 = xr[i], nl = xr[i + 1] - l0;
+  constexpr int PER = 8;  // lists per lane held in registers
+  int pos[PER], end[PER];
+  for (int u = 0; u < PER; ++u) {
+    const int q = lane + 32 * u;
+    if (q < nl) {
+      const int k = xc[l0 + q];
+      pos[u] = yr[k];
+      end[u] = yr[k + 1];
+    } else {
+      pos[u] = end[u] = 0;
+    }
+  }
+  int out = zc ? zr[i] : 0, n = 0;
+  for (;;) {
+    int h = 0x7fffffff;
+    for (int u = 0; u < PER; ++u)
+      if (pos[u] < end[u]) h = min(h, yc[pos[u]]);
+    for (int off = 16; off >= 1; off >>= 1) h = min(h, __shfl_xor_sync(0xffffffffu, h, off));
+    if (h == 0x7fffffff) break;
+    if (lane == 0 && zc) zc[out + n] = h;
+    ++n;
+    for (int u = 0; u < PER; ++u)
+      if (pos[u] < end[u] && yc[pos[u]] == h) ++pos[u];
+  }
+  if (lane == 0 && !zc) cnt[i] = n;
+}
+
+// exclusive prefix sum of n ints into out[0..n] (one block; the host checks
+// that n is small enough, else the scan runs on the host)
+__global__ void __launch_bounds__(1024) k_scan1(int n, const int *__restrict__ in, int *__restrict__ out) {
+  __shared__ int part[1024];
+  const int per = (n + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(n, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += in[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int acc = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int i = lo; i < hi; ++i) {
+    out[i] = acc;
+    acc += in[i];
+  }
+  if (threadIdx.x == 1023) out[n] = part[1023];
+}
+
+// Z's pattern on the device (Z.rowptr, Z.col, Z.val allocated); the host
+// mirror only when want_host.
+static int symbolic_product_gpu(const DevBsr &X, const DevBsr &Y, DevBsr &Z, bool want_host, cudaStream_t s) {
+  const int nr = X.nr;
+  int maxlen = 0;
+  for (int i = 0; i < nr; ++i) maxlen = std::max(maxlen, X.h_rowptr[i + 1] - X.h_rowptr[i]);
+  if (maxlen > 32 * 8) return AMG_ERR_ARG;  // caller falls back to the host product
+  DBuf<int> cnt, rp;
+  AMG_TRY(cnt.alloc(nr));
+  AMG_TRY(rp.alloc(nr + 1));
+  const int nb = nblk(32L * nr, 256);
+  if (nr) AMG_KCOUNT k_sym_merge<<<nb, 256, 0, s>>>(nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, nullptr, nullptr, cnt.p);
+  AMG_KCOUNT k_scan1<<<1, 1024, 0, s>>>(nr, cnt.p, rp.p);
+  AMG_LAUNCH_CHECK();
+  int nnz = 0;
+  AMG_CU(cudaMemcpyAsync(&nnz, rp.p + nr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  AMG_TRY(Z.alloc(nr, Y.nc, nnz));
+  AMG_CU(cudaMemcpyAsync(Z.rowptr.p, rp.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (nr) AMG_KCOUNT k_sym_merge<<<nb, 256, 0, s>>>(nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, rp.p, Z.col.p, nullptr);
+  AMG_LAUNCH_CHECK();
+  if (want_host) AMG_TRY(Z.download_pattern(s));
+  return AMG_OK;
+}
+
 static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &Ac, cudaStream_t s) {
   DevBsr AP;
   double tt = now_s();
-  symbolic_product(A, P, AP);
+  // AP's pattern stays on the device (its host mirror is only needed when
+  // R's rows are too long for the GPU merge)
+  int rc = symbolic_product_gpu(A, P, AP, false, s);
+  bool ap_host = false;
+  if (rc == AMG_ERR_ARG) {
+    symbolic_product(A, P, AP);
+    AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb));
+    AMG_TRY(AP.upload_pattern(s));
+    ap_host = true;
+  } else if (rc) {
+    return rc;
+  }
   trace("AP symbolic", -1, tt);
-  AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb));
-  AMG_TRY(AP.upload_pattern(s));
   tt = now_s();
   AMG_TRY(det::spgemm_numeric(A, P, AP, s));
   AMG_CU(cudaStreamSynchronize(s));
   trace("AP numeric", -1, tt);
   tt = now_s();
-  symbolic_product(R, AP, Ac);
+  rc = symbolic_product_gpu(R, AP, Ac, true, s);
+  if (rc == AMG_ERR_ARG) {
+    if (!ap_host) AMG_TRY(AP.download_pattern(s));
+    symbolic_product(R, AP, Ac);
+    AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb));
+    AMG_TRY(Ac.upload_pattern(s));
+  } else if (rc) {
+    return rc;
+  }
   trace("RAP symbolic", -1, tt);
-  AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb));
-  AMG_TRY(Ac.upload_pattern(s));
   tt = now_s();
   AMG_TRY(det::spgemm_numeric(R, AP, Ac, s));
   AMG_CU(cudaStreamSynchronize(s));
