@@ -704,37 +704,122 @@ static int smoother_setup(Handle *h, Level &L, int level) {
   return AMG_OK;
 }
 
-static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong) {
+// Candidate sets of the fine nodes on the GPU (d_p <= 2): the coarse nodes
+// within d_p strong edges of node I are the union of the strong coarse
+// neighbours of I and, for d_p = 2, of each strong neighbour of I; one warp
+// per fine node merges these sorted lists (as in k_sym_merge), skipping
+// entries that are not strong, not coarse or the row's own node.  Pass 0
+// counts, pass 1 writes.
+__device__ __forceinline__ int cand_next(int pos, int end, int row, const int *__restrict__ col,
+                                         const unsigned char *__restrict__ strong, const int *__restrict__ cf) {
+  while (pos < end && !(strong[pos] && col[pos] != row && cf[col[pos]] == 1)) ++pos;
+  return pos;
+}
+
+__global__ void __launch_bounds__(128) k_dpls_cand(int nf, const int *__restrict__ fnodes, int d_p,
+                                                   const int *__restrict__ rp, const int *__restrict__ col,
+                                                   const unsigned char *__restrict__ strong,
+                                                   const int *__restrict__ cf, const int *__restrict__ cptr,
+                                                   int *__restrict__ cand, int *__restrict__ cnt) {
+  constexpr int PER = 8, MAXL = 32 * PER;
+  __shared__ int nbr[4][MAXL];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (f >= nf) return;
+  const int I = fnodes[f];
+  // lists: 0 = row I; 1 + q = row of the q-th strong neighbour of I
+  int nl = 1;
+  if (d_p >= 2) {
+    for (int b = rp[I]; b < rp[I + 1]; b += 32) {
+      const int k = b + lane;
+      const bool sn = k < rp[I + 1] && strong[k] && col[k] != I;
+      const unsigned bal = __ballot_sync(0xffffffffu, sn);
+      const int at = nl - 1 + __popc(bal & ((1u << lane) - 1u));
+      if (sn && at < MAXL) nbr[w][at] = col[k];
+      nl += __popc(bal);
+    }
+    __syncwarp();
+  }
+  if (d_p <= 0) nl = 0;
+  int row[PER], pos[PER], end[PER];
+  for (int u = 0; u < PER; ++u) {
+    const int q = lane + 32 * u;
+    row[u] = -1;
+    pos[u] = end[u] = 0;
+    if (q < nl && q <= MAXL) {
+      row[u] = q == 0 ? I : nbr[w][q - 1];
+      end[u] = rp[row[u] + 1];
+      pos[u] = cand_next(rp[row[u]], end[u], row[u], col, strong, cf);
+    }
+  }
+  int out = cand ? cptr[f] : 0, n = 0;
+  for (;;) {
+    int h = 0x7fffffff;
+    for (int u = 0; u < PER; ++u)
+      if (pos[u] < end[u]) h = min(h, col[pos[u]]);
+    for (int off = 16; off >= 1; off >>= 1) h = min(h, __shfl_xor_sync(0xffffffffu, h, off));
+    if (h == 0x7fffffff) break;
+    if (lane == 0 && cand) cand[out + n] = h;
+    ++n;
+    for (int u = 0; u < PER; ++u)
+      if (pos[u] < end[u] && col[pos[u]] == h) pos[u] = cand_next(pos[u] + 1, end[u], row[u], col, strong, cf);
+  }
+  if (lane == 0 && !cand) cnt[f] = n;
+}
+
+static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong, const unsigned char *d_strong) {
   const amg_params &p = h->prm;
   cudaStream_t s = h->stream;
   const int n = L.n, t = p.n_tv;
-  std::vector<int> cidx(n, -1);
+  std::vector<int> cidx(n, -1), fnodes;
   int nc = 0;
-  for (int I = 0; I < n; ++I)
+  for (int I = 0; I < n; ++I) {
     if (L.cf[I] == 1) cidx[I] = nc++;
+    else fnodes.push_back(I);
+  }
   L.nc = nc;
-  std::vector<int> fnodes, cptr, cand;
   double tt = now_s();
-  dpls_candidates(L.A, strong, L.cf, p.d_p, fnodes, cptr, cand);
-  trace("DPLS candidates", -1, tt);
-  tt = now_s();
   const int nf = (int)fnodes.size();
   const int cap = std::max(1, std::min(p.n_max, t / 3));
-  DBuf<int> d_cidx, d_f, d_cptr, d_cand, d_cnt, d_col;
+  DBuf<int> d_cidx, d_f, d_cptr, d_cand, d_cnt, d_col, d_cf;
   DBuf<double> d_val;
   AMG_TRY(d_cidx.alloc(n));
   AMG_TRY(d_f.alloc(nf));
   AMG_TRY(d_cptr.alloc(nf + 1));
-  AMG_TRY(d_cand.alloc(cand.size()));
   AMG_TRY(d_cnt.alloc(nf));
   AMG_TRY(d_col.alloc((size_t)nf * cap));
   AMG_TRY(d_val.alloc((size_t)nf * cap * 9));
   AMG_CU(cudaMemcpyAsync(d_cidx.p, cidx.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
-  if (nf) {
-    AMG_CU(cudaMemcpyAsync(d_f.p, fnodes.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (nf) AMG_CU(cudaMemcpyAsync(d_f.p, fnodes.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s));
+  int maxdeg = 0;
+  for (int I = 0; I < n; ++I) maxdeg = std::max(maxdeg, L.A.h_rowptr[I + 1] - L.A.h_rowptr[I]);
+  if (nf && p.d_p <= 2 && maxdeg < 256) {
+    AMG_TRY(d_cf.alloc(n));
+    AMG_CU(cudaMemcpyAsync(d_cf.p, L.cf.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    const int nb = nblk(32L * nf, 128);
+    AMG_KCOUNT k_dpls_cand<<<nb, 128, 0, s>>>(nf, d_f.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, d_cf.p,
+                                              nullptr, nullptr, d_cnt.p);
+    AMG_KCOUNT k_scan1<<<1, 1024, 0, s>>>(nf, d_cnt.p, d_cptr.p);
+    AMG_LAUNCH_CHECK();
+    int ncand = 0;
+    AMG_CU(cudaMemcpyAsync(&ncand, d_cptr.p + nf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CU(cudaStreamSynchronize(s));
+    AMG_TRY(d_cand.alloc(ncand));
+    AMG_KCOUNT k_dpls_cand<<<nb, 128, 0, s>>>(nf, d_f.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, d_cf.p,
+                                              d_cptr.p, d_cand.p, nullptr);
+    AMG_LAUNCH_CHECK();
+  } else if (nf) {
+    std::vector<int> fn2, cptr, cand;
+    dpls_candidates(L.A, strong, L.cf, p.d_p, fn2, cptr, cand);
+    AMG_TRY(d_cand.alloc(cand.size()));
     AMG_CU(cudaMemcpyAsync(d_cptr.p, cptr.data(), (nf + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
     if (!cand.empty())
       AMG_CU(cudaMemcpyAsync(d_cand.p, cand.data(), cand.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    AMG_CU(cudaStreamSynchronize(s));
+  }
+  trace("DPLS candidates", -1, tt);
+  tt = now_s();
+  if (nf) {
     AMG_TRY(det::dpls(L.A, nullptr, nullptr, d_cidx.p, d_f.p, nf, d_cptr.p, d_cand.p, t, L.V.p, p.n_max,
                       p.kappa_p, d_cnt.p, d_col.p, d_val.p, nullptr, s));
   }
@@ -925,7 +1010,7 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
       L.cf.clear();
       break;
     }
-    AMG_TRY(build_P(h, L, strong));
+    AMG_TRY(build_P(h, L, strong, d_strong.p));
     AMG_TRY(transpose_bsr(L.P, L.R, s));
     double t4 = now_s();
     T_pl += t4 - t3;
