@@ -122,13 +122,22 @@ def barrier(ws):
 
 
 def max_over_ranks(v, ws):
+    """Largest value over the ranks (the slowest replica's time)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as td
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if td.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     td.all_reduce(t, op=td.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(ms_local, ws):
+    """(ms per step of the slowest rank, whole-job solutions per second): every
+    rank solves its own replica of the workload in each step."""
+    ms = max_over_ranks(ms_local, ws)
+    return ms, ws * 1e3 / ms
 
 
 def gpu_problem(A, p):
@@ -336,9 +345,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     barrier(ws)
     launches = A.launch_count() - l0
-    ms = e0.elapsed_time(e1) / args.steps
-    ms = max_over_ranks(ms, ws)
-    value = ws * 1e3 / ms
+    ms, value = aggregate(e0.elapsed_time(e1) / args.steps, ws)
     stats = S.stats()
     clocks = clk.summary()
 
@@ -493,6 +500,38 @@ def run_micro(args):
     print(json.dumps({"micro": rows}), flush=True)
 
 
+def run_sweep(args):
+    """Parameter sensitivity on the default beam (GPU timings): one JSON line
+    per setting of the coarsening threshold theta, the prolongation limits
+    (n_max, kappa_p) and the smoother growth (k_g, rho_g), the other
+    parameters at their defaults; FP64 V-cycle, set-up + solve to 1e-8."""
+    import torch
+
+    import paper_1902_01715_gb300 as A
+    import workloads as W
+    torch.cuda.set_device(0)
+    A.build()
+    A.lib()
+    p = W.beam(*args.dims) if args.dims else W.beam()
+    d = gpu_problem(A, p)
+    grid = [("theta", {"theta": v}) for v in (2, 3, 4, 5, 6, 8, 10)]
+    grid += [("n_max", {"n_max": v}) for v in (1, 2, 3, 4, 5)]
+    grid += [("kappa_p", {"kappa_p": v}) for v in (10.0, 50.0, 100.0)]
+    grid += [("k_g x rho_g", {"k_g": k, "rho_g": r, "k_i": k, "rho_i": r}) for k, r in ((2, 1), (2, 2), (4, 2), (6, 2), (4, 3))]
+    for name, over in grid:
+        S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], **over)
+
+        def step():
+            S.update_values(d["vals"])
+            return S.solve(d["f"], RTOL)
+        (x, its, rel, rc), ms = _timed(step)
+        st = S.stats()
+        print(json.dumps({"sweep": name, "params": over, "ms_per_solution": ms, "n_it": its[0], "rc": rc,
+                          "setup_ms": st["T_p"] * 1e3, "solve_ms": st["T_s"] * 1e3, "levels": st["nlev"],
+                          "C_gd": st["C_gd"], "C_op": st["C_op"], "C_fs": st["C_fs"]}), flush=True)
+        S.close()
+
+
 def run_single(args):
     """One set-up + solve of the workload with no warm-up (the command the
     kernel launch lists under profiles/ are taken from); prints a summary, not
@@ -519,6 +558,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--micro", action="store_true", help="per-level sparse-product timings only")
     ap.add_argument("--single", action="store_true", help="one set-up + solve, no warm-up (for profilers)")
+    ap.add_argument("--sweep", action="store_true", help="parameter sensitivity on the beam (one line per setting)")
     ap.add_argument("--dims", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
                     help="beam size nx,ny,nz for --single (default 128,32,32)")
     ap.add_argument("--reps", type=int, default=50)
@@ -536,6 +576,8 @@ def main():
         args.warmup = 3
     if args.single:
         run_single(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.micro:
         run_micro(args)
     elif args.impl == "reference":
