@@ -476,31 +476,48 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
     }
   }
   __syncwarp();
-  // right-looking Cholesky of the lower triangle (each entry receives its
-  // updates k = 0, 1, ... in ascending order, then the division)
+  // right-looking Cholesky of the lower triangle in panels of FS_PB columns
+  // (each entry receives its updates k = 0, 1, ... in ascending order, then
+  // the division, exactly as column by column): inside a panel column by
+  // column; the trailing entries then receive the panel's FS_PB updates in
+  // one pass, reading each of their two panel rows once
+  constexpr int FS_PB = 8;
   const int mx = warp_max(m2);
   int bad = 0;
-  for (int j = 0; j < mx; ++j) {
-    const bool on = j < m2 && !bad;
-    double d = 1.0;
-    if (on) {
-      const double sjj = M[j * m2 + j];
-      if (!(sjj > 0.0)) bad = 1;
-      else d = sqrt(sjj);
+  for (int j0 = 0; j0 < mx; j0 += FS_PB) {
+    const int j1 = min(j0 + FS_PB, m2);  // this slot's panel end
+    for (int j = j0; j < j0 + FS_PB && j < mx; ++j) {
+      const bool on = j < m2 && !bad;
+      double d = 1.0;
+      if (on) {
+        const double sjj = M[j * m2 + j];
+        if (!(sjj > 0.0)) bad = 1;
+        else d = sqrt(sjj);
+      }
+      __syncwarp();
+      if (on && !bad) {
+        for (int r = j + 1 + gl; r < m2; r += FS_GL) M[r * m2 + j] = M[r * m2 + j] / d;
+        if (gl == 0) M[j * m2 + j] = d;
+      }
+      __syncwarp();
+      if (on && !bad) {  // the panel's later columns, rows k..m2-1
+        const int pk = j1 - j - 1;
+        for (int idx = gl; idx < pk * (m2 - j - 1); idx += FS_GL) {
+          const int k = j + 1 + idx % pk, r = j + 1 + idx / pk;
+          if (r >= k) M[r * m2 + k] = fma(-M[r * m2 + j], M[k * m2 + j], M[r * m2 + k]);
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    if (on && !bad) {
-      for (int r = j + 1 + gl; r < m2; r += FS_GL) M[r * m2 + j] = M[r * m2 + j] / d;
-      if (gl == 0) M[j * m2 + j] = d;
-    }
-    __syncwarp();
-    if (on && !bad) {
-      const int w = m2 - j - 1, nt = w * (w + 1) / 2;
+    if (!bad && j1 < m2 && j0 < m2) {  // trailing lower triangle from column j1
+      const int w = m2 - j1, nt = w * (w + 1) / 2;
       for (int idx = gl; idx < nt; idx += FS_GL) {
         int rr, kk;
         tri_decode(idx, rr, kk);
-        const int r = j + 1 + rr, k = j + 1 + kk;
-        M[r * m2 + k] = fma(-M[r * m2 + j], M[k * m2 + j], M[r * m2 + k]);
+        const int r = j1 + rr, k = j1 + kk;
+        double a = M[r * m2 + k];
+        for (int j = j0; j < j1; ++j) a = fma(-M[r * m2 + j], M[k * m2 + j], a);
+        M[r * m2 + k] = a;
       }
     }
     __syncwarp();
@@ -508,25 +525,53 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
   const bool ok = act && !bad;
   // forward substitution for the three right-hand sides together (row c
   // uses the leading 3np + c rows): y_k = rhs_k / L_kk, then rhs_r -= L_rk y_k
-  for (int k = 0; k < mx; ++k) {
-    if (ok && gl < 3 && k < 3 * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] / M[k * m2 + k];
-    __syncwarp();
-    if (ok)
-      for (int idx = gl; idx < 3 * m2; idx += FS_GL) {
-        const int c = idx / m2, r = idx - c * m2;
-        if (r > k && r < 3 * np + c) rhs[c * mm + r] = fma(-M[r * m2 + k], rhs[c * mm + k], rhs[c * mm + r]);
+  // (k ascending for every r), in blocks of FS_PB columns: inside a block
+  // column by column, then the rows below it take the block's updates in
+  // one pass
+  for (int k0 = 0; k0 < mx; k0 += FS_PB) {
+    const int k1 = min(k0 + FS_PB, mx);
+    for (int k = k0; k < k1; ++k) {
+      if (ok && gl < 3 && k < 3 * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] / M[k * m2 + k];
+      __syncwarp();
+      if (ok)
+        for (int idx = gl; idx < 3 * (k1 - k - 1); idx += FS_GL) {
+          const int c = idx / (k1 - k - 1), r = k + 1 + idx % (k1 - k - 1);
+          if (r < 3 * np + c) rhs[c * mm + r] = fma(-M[r * m2 + k], rhs[c * mm + k], rhs[c * mm + r]);
+        }
+      __syncwarp();
+    }
+    if (ok && k1 < m2)
+      for (int idx = gl; idx < 3 * (m2 - k1); idx += FS_GL) {
+        const int c = idx / (m2 - k1), r = k1 + idx % (m2 - k1);
+        if (r < 3 * np + c) {
+          double a = rhs[c * mm + r];
+          for (int k = k0; k < k1; ++k) a = fma(-M[r * m2 + k], rhs[c * mm + k], a);
+          rhs[c * mm + r] = a;
+        }
       }
     __syncwarp();
   }
   // backward substitution: x_k = rhs_k / L_kk for k descending, then
-  // rhs_r -= L_kr x_k for r < k
-  for (int k = mx - 1; k >= 0; --k) {
-    if (ok && gl < 3 && k < 3 * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] / M[k * m2 + k];
-    __syncwarp();
-    if (ok && k < m2)
-      for (int idx = gl; idx < 3 * k; idx += FS_GL) {
-        const int c = idx / k, r = idx - c * k;
-        if (k < 3 * np + c) rhs[c * mm + r] = fma(-M[k * m2 + r], gh[c * mm + k], rhs[c * mm + r]);
+  // rhs_r -= L_kr x_k for r < k (k descending for every r), in blocks of
+  // FS_PB columns from the top
+  for (int k1 = mx; k1 > 0; k1 -= FS_PB) {
+    const int k0 = max(k1 - FS_PB, 0);
+    for (int k = k1 - 1; k >= k0; --k) {
+      if (ok && gl < 3 && k < 3 * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] / M[k * m2 + k];
+      __syncwarp();
+      if (ok && k < m2)
+        for (int idx = gl; idx < 3 * (k - k0); idx += FS_GL) {
+          const int c = idx / (k - k0), r = k0 + idx % (k - k0);
+          if (k < 3 * np + c) rhs[c * mm + r] = fma(-M[k * m2 + r], gh[c * mm + k], rhs[c * mm + r]);
+        }
+      __syncwarp();
+    }
+    if (ok)
+      for (int idx = gl; idx < 3 * k0; idx += FS_GL) {
+        const int c = idx / k0, r = idx % k0;
+        double a = rhs[c * mm + r];
+        for (int k = min(k1, 3 * np + c) - 1; k >= k0; --k) a = fma(-M[k * m2 + r], gh[c * mm + k], a);
+        rhs[c * mm + r] = a;
       }
     __syncwarp();
   }
