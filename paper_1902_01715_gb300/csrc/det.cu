@@ -1200,16 +1200,19 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     return AMG_ERR_ARG;
   }
   const size_t nt = (size_t)n * t;
-  DBuf<double> Z, P, SZ, SP, Gv, T1, T2, cs, out, part, H, Mg, U, lam, wk;
+  // Z and P (and S Z, S P) are adjacent column blocks, so that S is applied
+  // to both in one pass of 2t columns
+  DBuf<double> ZP, SZP, Gv, T1, T2, cs, out, part, H, Mg, U, lam, wk;
   DBuf<int> skip;
   DBuf<unsigned> tk;
-  AMG_TRY(Z.alloc(nt));
-  AMG_TRY(P.alloc(nt));
-  AMG_TRY(SZ.alloc(nt));
-  AMG_TRY(SP.alloc(nt));
+  AMG_TRY(ZP.alloc(2 * nt));
+  AMG_TRY(SZP.alloc(2 * nt));
   AMG_TRY(Gv.alloc(nt));
-  AMG_TRY(T1.alloc(nt));
-  AMG_TRY(T2.alloc(nt));
+  AMG_TRY(T1.alloc(2 * nt));
+  AMG_TRY(T2.alloc(2 * nt));
+  struct Half {
+    double *p;
+  } Z{ZP.p}, P{ZP.p + nt}, SZ{SZP.p}, SP{SZP.p + nt};
   AMG_TRY(cs.alloc(C_NUM * t));
   AMG_TRY(out.alloc(5 * t));
   const int nchunks = (n + CHUNK - 1) / CHUNK;
@@ -1255,8 +1258,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
       AMG_KCOUNT k_rotate<<<nblk(n, 256), 256, 0, s>>>(n, t, Z.p, U.p);
       AMG_LAUNCH_CHECK();
     }
-    AMG_TRY(apply_s_cols(A, G, GT, t, Z.p, SZ.p, T1.p, T2.p, s));
-    AMG_TRY(apply_s_cols(A, G, GT, t, P.p, SP.p, T1.p, T2.p, s));
+    AMG_TRY(apply_s_cols(A, G, GT, 2 * t, ZP.p, SZP.p, T1.p, T2.p, s));  // S Z and S P
     CDot a5{};
     a5.x[0] = P.p; a5.y[0] = SZ.p;
     a5.x[1] = P.p; a5.y[1] = SP.p;
