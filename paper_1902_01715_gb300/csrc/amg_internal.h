@@ -174,6 +174,7 @@ void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX 
 int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s);
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s);  // kind 0 FP64, 1 FP32, 2 bf16
 const char *mapping_name(const SolveMat &M, bool f64);
+int bulk_copy_error();  // AMG_ERR_CUDA (and clears it) if a bulk-copy stage timed out
 
 struct Level {
   int n = 0;  // nodes

@@ -476,6 +476,7 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
   AMG_CU(cudaStreamSynchronize(s));
   *iters = hflags[F_ITERS];
   *relres = hsc[P_BN2] > 0.0 ? std::sqrt(hsc[P_RR] / hsc[P_BN2]) : 0.0;
+  if (mixed) AMG_TRY(bulk_copy_error());
   return hflags[F_STATUS];
 }
 

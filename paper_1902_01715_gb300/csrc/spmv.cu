@@ -41,7 +41,8 @@ __device__ __forceinline__ float cvs(__nv_bfloat16 v, float) { return __bfloat16
 struct Mapping {
   int wps, u;
 };
-static const Mapping kMaps[] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}, {4, 4}, {8, 2}, {16, 2}};
+// the last entry is the bulk-copy variant below (FP32 and bf16 storage)
+static const Mapping kMaps[] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}, {4, 4}, {8, 2}, {16, 2}, {0, 0}};
 constexpr int kNumMaps = (int)(sizeof(kMaps) / sizeof(kMaps[0]));
 
 // CTA size: 4 warps, or one slice of WPS warps when WPS > 4
@@ -136,6 +137,197 @@ static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *
 #undef AMG_SELL_ARGS
 }
 
+// ---------------------------------------------------------------- bulk-copy variant
+// For FP32 and bf16 storage (HBM-bound): each warp runs its own pipeline of
+// BK_ST shared-memory stages; lane 0 fills a stage with one chunk of a slice
+// (the values and column indices of BK_JC consecutive block columns, which
+// are contiguous in the slice layout) by two asynchronous bulk copies
+// completing on the stage's mbarrier, while the lanes compute on the stages
+// filled before.  Loads of the matrix then cost two instructions per chunk
+// and the bytes in flight no longer depend on registers.  Every wait is
+// bounded: a stage that does not complete within the limit sets the error
+// word and ends the warp's work.
+constexpr int BK_JC = 4;   // block columns per chunk
+constexpr int BK_ST = 2;   // stages per warp
+constexpr int BK_WARPS = 4;
+__device__ int g_bulk_err;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+// bounded wait: gives up after about two seconds of SM clock
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > (1LL << 32)) return false;
+  return true;
+}
+
+template <typename TM>
+struct BulkStage {
+  TM v[9 * 32 * BK_JC];
+  int c[32 * BK_JC];
+};
+
+template <typename TM, typename TX, int EP>
+__global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, const int *__restrict__ rp,
+                                                               const int *__restrict__ slp,
+                                                               const int *__restrict__ scol,
+                                                               const TM *__restrict__ v, const TX *__restrict__ x,
+                                                               TX *__restrict__ y, const TX *__restrict__ aux, TX w,
+                                                               const int *__restrict__ done) {
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char bk_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  BulkStage<TM> *st = reinterpret_cast<BulkStage<TM> *>(bk_smem) + warp * BK_ST;
+  __shared__ __align__(8) unsigned long long bars[BK_WARPS][BK_ST];
+  const int gw = blockIdx.x * BK_WARPS + warp, nw = gridDim.x * BK_WARPS;
+  if (lane == 0) {
+    for (int q = 0; q < BK_ST; ++q) mbar_init(smem_u32(&bars[warp][q]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // chunk stream of this warp: slices gw, gw + nw, ...; chunk c of a slice
+  // covers block columns [c BK_JC, (c+1) BK_JC)
+  int ps = gw, pc = 0;  // next chunk to fill (producer)
+  auto fill = [&](int q) {  // lane 0: start the next chunk into stage q
+    while (ps < ns) {
+      const int len = (slp[ps + 1] - slp[ps]) >> 5;
+      if (pc * BK_JC < len) break;
+      ps += nw;
+      pc = 0;
+    }
+    if (ps >= ns) return;
+    const int len = (slp[ps + 1] - slp[ps]) >> 5;
+    const int nb = min(BK_JC, len - pc * BK_JC);
+    const long slot = (long)slp[ps] + 32L * BK_JC * pc;
+    const unsigned vb = (unsigned)(9 * 32 * nb * sizeof(TM)), cb = (unsigned)(32 * nb * sizeof(int));
+    const unsigned bar = smem_u32(&bars[warp][q]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect(bar, vb + cb);
+    bulk_g2s(smem_u32(st[q].v), v + 9 * slot, vb, bar);
+    bulk_g2s(smem_u32(st[q].c), scol + slot, cb, bar);
+    ++pc;
+  };
+  if (lane == 0)
+    for (int q = 0; q < BK_ST; ++q) fill(q);
+  __syncwarp();
+  unsigned phase[BK_ST];
+  for (int q = 0; q < BK_ST; ++q) phase[q] = 0;
+  int q = 0;
+  bool failed = false;
+  for (int sl = gw; sl < ns && !failed; sl += nw) {
+    const int len_s = (slp[sl + 1] - slp[sl]) >> 5;
+    const int row = sl * 32 + lane;
+    const int len = row < nr ? rp[row + 1] - rp[row] : 0;
+    RowAcc<TX> acc;
+    for (int c = 0; c * BK_JC < len_s; ++c) {
+      const bool got = mbar_wait(smem_u32(&bars[warp][q]), phase[q]);
+      if (!__all_sync(0xffffffffu, got)) {  // the warp leaves together
+        if (lane == 0) atomicExch(&g_bulk_err, 1);
+        failed = true;
+        break;
+      }
+      phase[q] ^= 1u;
+      // the chunk's neighbour values are gathered before any is used
+      TX xv[BK_JC][3];
+#pragma unroll
+      for (int jj = 0; jj < BK_JC; ++jj)
+        if (c * BK_JC + jj < len) {
+          const TX *xp = x + 3L * st[q].c[jj * 32 + lane];
+          xv[jj][0] = xp[0];
+          xv[jj][1] = xp[1];
+          xv[jj][2] = xp[2];
+        }
+#pragma unroll
+      for (int jj = 0; jj < BK_JC; ++jj)
+        if (c * BK_JC + jj < len) {
+          const TM *m = st[q].v + jj * 9 * 32 + lane;
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+            acc.add(r, cvs(m[32 * (3 * r)], TX(0)), cvs(m[32 * (3 * r + 1)], TX(0)), cvs(m[32 * (3 * r + 2)], TX(0)),
+                    xv[jj][0], xv[jj][1], xv[jj][2]);
+        }
+      __syncwarp();
+      if (lane == 0) fill(q);
+      __syncwarp();
+      q = q + 1 == BK_ST ? 0 : q + 1;
+    }
+    if (failed || row >= nr) continue;
+    const TX a0 = acc.get(0), a1 = acc.get(1), a2 = acc.get(2);
+    const long o = 3L * row;
+    if (EP == EP_SET) { y[o] = a0; y[o + 1] = a1; y[o + 2] = a2; }
+    if (EP == EP_SCALE) { y[o] = w * a0; y[o + 1] = w * a1; y[o + 2] = w * a2; }
+    if (EP == EP_RESID) { y[o] = aux[o] - a0; y[o + 1] = aux[o + 1] - a1; y[o + 2] = aux[o + 2] - a2; }
+    if (EP == EP_SADD) { y[o] = aux[o] + w * a0; y[o + 1] = aux[o + 1] + w * a1; y[o + 2] = aux[o + 2] + w * a2; }
+    if (EP == EP_ACC) { y[o] += a0; y[o + 1] += a1; y[o + 2] += a2; }
+  }
+  if (failed && lane == 0)  // let the copies still in flight land (bounded) before the warp leaves
+    for (int k = 0; k < BK_ST; ++k) mbar_wait(smem_u32(&bars[warp][k]), phase[k]);
+}
+
+template <typename TM, typename TX>
+static void launch_bulk(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
+                        const int *done, cudaStream_t s) {
+  static int nsm = 0;
+  static bool attr = false;
+  const size_t shm = sizeof(BulkStage<TM>) * BK_ST * BK_WARPS;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (!attr) {
+    cudaFuncSetAttribute(k_sellmv_bulk<TM, TX, EP_SET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_sellmv_bulk<TM, TX, EP_SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_sellmv_bulk<TM, TX, EP_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_sellmv_bulk<TM, TX, EP_SADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_sellmv_bulk<TM, TX, EP_ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    attr = true;
+  }
+  int nb = (M.ns + BK_WARPS - 1) / BK_WARPS;
+  const int cap = nsm * 5;  // five CTAs per SM
+  if (nb > cap) nb = cap;
+  if (nb == 0) return;
+#define AMG_BULK_ARGS M.nr, M.ns, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
+  switch (ep) {
+    case EP_SET: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_SET><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
+    case EP_SCALE: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_SCALE><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
+    case EP_RESID: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_RESID><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
+    case EP_SADD: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_SADD><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
+    default: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_ACC><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
+  }
+#undef AMG_BULK_ARGS
+}
+
+int bulk_copy_error() {
+  int e = 0;
+  AMG_CU(cudaMemcpyFromSymbol(&e, g_bulk_err, sizeof(int)));
+  if (e) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_bulk_err, &z, sizeof(int));
+    set_error("a bulk-copy stage of the sparse product did not complete in time");
+    return AMG_ERR_CUDA;
+  }
+  return AMG_OK;
+}
+
 template <typename TM, typename TX>
 void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
            cudaStream_t s) {
@@ -147,7 +339,11 @@ void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX 
     case 4: launch_map<TM, TX, 4, 2>(ep, M, v, x, y, aux, w, done, s); break;
     case 5: launch_map<TM, TX, 4, 4>(ep, M, v, x, y, aux, w, done, s); break;
     case 6: launch_map<TM, TX, 8, 2>(ep, M, v, x, y, aux, w, done, s); break;
-    default: launch_map<TM, TX, 16, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 7: launch_map<TM, TX, 16, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    default:
+      if constexpr (std::is_same<TM, double>::value) launch_map<TM, TX, 1, 2>(ep, M, v, x, y, aux, w, done, s);
+      else launch_bulk<TM, TX>(ep, M, v, x, y, aux, w, done, s);
+      break;
   }
 }
 
@@ -314,7 +510,7 @@ static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
 }
 
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
-  // AMG_MAP=<0..7> pins the mapping of every matrix (for experiments)
+  // AMG_MAP=<0..8> pins the mapping of every matrix (for experiments)
   if (const char *pin = getenv("AMG_MAP")) {
     const int m = atoi(pin);
     if (m >= 0 && m < kNumMaps) {
@@ -329,8 +525,8 @@ int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
 }
 
 const char *mapping_name(const SolveMat &M, bool f64) {
-  static const char *names[kNumMaps] = {"wps1_u2", "wps1_u4", "wps2_u2", "wps2_u4",
-                                        "wps4_u2", "wps4_u4", "wps8_u2", "wps16_u2"};
+  static const char *names[kNumMaps] = {"wps1_u2", "wps1_u4", "wps2_u2", "wps2_u4", "wps4_u2",
+                                        "wps4_u4", "wps8_u2", "wps16_u2", "bulk_copy"};
   const int m = f64 ? M.map64 : M.map;
   return (m >= 0 && m < kNumMaps) ? names[m] : "?";
 }
