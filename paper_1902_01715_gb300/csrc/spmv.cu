@@ -151,6 +151,10 @@ constexpr int BK_JC = 4;   // block columns per chunk
 constexpr int BK_ST = 2;   // stages per warp
 constexpr int BK_WARPS = 4;
 __device__ int g_bulk_err;
+// Test knob: when set, the first warp that reads it skips filling one stage
+// (once), so its wait runs out and the timeout path is exercised without any
+// fault.  Set from the environment (AMG_BULK_STALL_ONCE) at the first launch.
+__device__ int g_bulk_stall;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -205,7 +209,8 @@ __global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, c
   __syncwarp();
   // chunk stream of this warp: slices gw, gw + nw, ...; chunk c of a slice
   // covers block columns [c BK_JC, (c+1) BK_JC)
-  int ps = gw, pc = 0;  // next chunk to fill (producer)
+  int ps = gw, pc = 0;      // next chunk to fill (producer)
+  unsigned pending = 0;     // lane 0: stages with copies in flight
   auto fill = [&](int q) {  // lane 0: start the next chunk into stage q
     while (ps < ns) {
       const int len = (slp[ps + 1] - slp[ps]) >> 5;
@@ -219,11 +224,13 @@ __global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, c
     const long slot = (long)slp[ps] + 32L * BK_JC * pc;
     const unsigned vb = (unsigned)(9 * 32 * nb * sizeof(TM)), cb = (unsigned)(32 * nb * sizeof(int));
     const unsigned bar = smem_u32(&bars[warp][q]);
+    ++pc;
+    if (g_bulk_stall && atomicExch(&g_bulk_stall, 0)) return;  // test knob: leave this stage empty
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect(bar, vb + cb);
     bulk_g2s(smem_u32(st[q].v), v + 9 * slot, vb, bar);
     bulk_g2s(smem_u32(st[q].c), scol + slot, cb, bar);
-    ++pc;
+    pending |= 1u << q;
   };
   if (lane == 0)
     for (int q = 0; q < BK_ST; ++q) fill(q);
@@ -245,6 +252,7 @@ __global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, c
         break;
       }
       phase[q] ^= 1u;
+      pending &= ~(1u << q);
       // the chunk's neighbour values are gathered before any is used
       TX xv[BK_JC][3];
 #pragma unroll
@@ -279,7 +287,8 @@ __global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, c
     if (EP == EP_ACC) { y[o] += a0; y[o + 1] += a1; y[o + 2] += a2; }
   }
   if (failed && lane == 0)  // let the copies still in flight land (bounded) before the warp leaves
-    for (int k = 0; k < BK_ST; ++k) mbar_wait(smem_u32(&bars[warp][k]), phase[k]);
+    for (int k = 0; k < BK_ST; ++k)
+      if (pending & (1u << k)) mbar_wait(smem_u32(&bars[warp][k]), phase[k]);
 }
 
 template <typename TM, typename TX>
@@ -294,6 +303,10 @@ static void launch_bulk(int ep, const SolveMat &M, const TM *v, const TX *x, TX 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   }
   if (!attr) {
+    if (getenv("AMG_BULK_STALL_ONCE")) {
+      const int one = 1;
+      cudaMemcpyToSymbol(g_bulk_stall, &one, sizeof(int));
+    }
     cudaFuncSetAttribute(k_sellmv_bulk<TM, TX, EP_SET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     cudaFuncSetAttribute(k_sellmv_bulk<TM, TX, EP_SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     cudaFuncSetAttribute(k_sellmv_bulk<TM, TX, EP_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
