@@ -29,7 +29,8 @@
  * Householder step on column x (rows p..t-1): sigma = sqrt(sum x_k^2),
  * alpha = -sigma if x_p >= 0 else sigma, v = x with v_p = x_p - alpha,
  * vv = sum v_k^2, R_pp = alpha; a column y becomes y - ((2 v^T y) / vv) v.
- * All sums ascend.
+ * All sums ascend; each multiply-add of a sum, of the update y - f v and of
+ * the back substitution is one fused multiply-add.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -43,9 +44,9 @@
 static void reflect(int t, int p, const double *v, double vv, double *y,
                     int stride) {
   double s = 0.0;
-  for (int k = p; k < t; ++k) s = s + v[k] * y[k * stride];
+  for (int k = p; k < t; ++k) s = fma(v[k], y[k * stride], s);
   const double f = (2.0 * s) / vv;
-  for (int k = p; k < t; ++k) y[k * stride] = y[k * stride] - f * v[k];
+  for (int k = p; k < t; ++k) y[k * stride] = fma(-f, v[k], y[k * stride]);
 }
 
 static double affinity(int t, int p, int b, const double *X, const double *Y) {
@@ -54,13 +55,13 @@ static double affinity(int t, int p, int b, const double *X, const double *Y) {
     for (int c = 0; c < b; ++c) {
       double sxy = 0.0, sxx = 0.0, syy = 0.0;
       for (int k = p; k < t; ++k) {
-        sxy = sxy + X[k * b + a] * Y[k * b + c];
-        sxx = sxx + X[k * b + a] * X[k * b + c];
-        syy = syy + Y[k * b + a] * Y[k * b + c];
+        sxy = fma(X[k * b + a], Y[k * b + c], sxy);
+        sxx = fma(X[k * b + a], X[k * b + c], sxx);
+        syy = fma(Y[k * b + a], Y[k * b + c], syy);
       }
-      xy = xy + sxy * sxy;
-      xx = xx + sxx * sxx;
-      yy = yy + syy * syy;
+      xy = fma(sxy, sxy, xy);
+      xx = fma(sxx, sxx, xx);
+      yy = fma(syy, syy, yy);
     }
   const double den = sqrt(xx) * sqrt(yy);
   return den > 0.0 ? xy / den : -1.0;
@@ -149,7 +150,7 @@ int or_dpls(const obsr *A, const unsigned char *strong, const int *cf,
         if (nsel >= n_max || p + b > t) break;
         double rr = 0.0;
         for (int k = p; k < t; ++k)
-          for (int c = 0; c < b; ++c) rr = rr + r[k * b + c] * r[k * b + c];
+          for (int c = 0; c < b; ++c) rr = fma(r[k * b + c], r[k * b + c], rr);
         if (rr == 0.0) break;
         int best = -1;
         double baff = 0.0;
@@ -170,7 +171,7 @@ int or_dpls(const obsr *A, const unsigned char *strong, const int *cf,
         for (int c = 0; c < b && ok; ++c) {
           const int pc = p + c;
           double sg = 0.0;
-          for (int k = pc; k < t; ++k) sg = sg + Y[k * b + c] * Y[k * b + c];
+          for (int k = pc; k < t; ++k) sg = fma(Y[k * b + c], Y[k * b + c], sg);
           sg = sqrt(sg);
           if (!(sg > 0.0)) {
             ok = 0;
@@ -180,7 +181,7 @@ int or_dpls(const obsr *A, const unsigned char *strong, const int *cf,
           for (int k = 0; k < t; ++k) hv[c][k] = (k >= pc) ? Y[k * b + c] : 0.0;
           hv[c][pc] = Y[pc * b + c] - alpha;
           double vv = 0.0;
-          for (int k = pc; k < t; ++k) vv = vv + hv[c][k] * hv[c][k];
+          for (int k = pc; k < t; ++k) vv = fma(hv[c][k], hv[c][k], vv);
           hvv[c] = vv;
           for (int c2 = c + 1; c2 < b; ++c2) reflect(t, pc, hv[c], vv, Y + c2, b);
           Y[pc * b + c] = alpha;
@@ -217,7 +218,7 @@ int or_dpls(const obsr *A, const unsigned char *strong, const int *cf,
       for (int c = 0; c < b; ++c)
         for (int i = p - 1; i >= 0; --i) {
           double s = r[i * b + c];
-          for (int k = p - 1; k > i; --k) s = s - R[i * TMAX + k] * w[k * b + c];
+          for (int k = p - 1; k > i; --k) s = fma(-R[i * TMAX + k], w[k * b + c], s);
           w[i * b + c] = s / R[i * TMAX + i];
         }
       for (int m = 0; m < nsel; ++m) {

@@ -1525,25 +1525,47 @@ int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char
 // the trailing rows: ||X^T Y||_F^2 / (||X^T X||_F ||Y^T Y||_F).
 __device__ __forceinline__ void reflect(int t, int p, const double *v, double vv, double *y, int stride) {
   double s = 0.0;
-  for (int k = p; k < t; ++k) s = s + v[k] * y[k * stride];
+  for (int k = p; k < t; ++k) s = fma(v[k], y[k * stride], s);
   const double f = (2.0 * s) / vv;
-  for (int k = p; k < t; ++k) y[k * stride] = y[k * stride] - f * v[k];
+  for (int k = p; k < t; ++k) y[k * stride] = fma(-f, v[k], y[k * stride]);
 }
 
-__device__ __forceinline__ double affinity(int t, int p, const double *X, const double *Y) {
-  double xy = 0.0, xx = 0.0, yy = 0.0;
+// ||X^T X||_F^2 over rows p..t-1.  Entry (a, c) and entry (c, a) are the
+// same chain of fused multiply-adds with the factors swapped, hence equal
+// bit for bit: the six distinct entries are formed once and the nine squares
+// are added in row-major order.
+__device__ __forceinline__ double gram_fro2(int t, int p, const double *X) {
+  double g[3][3];
+#pragma unroll
   for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) {
-      double sxy = 0.0, sxx = 0.0, syy = 0.0;
-      for (int k = p; k < t; ++k) {
-        sxy = sxy + X[k * 3 + a] * Y[k * 3 + c];
-        sxx = sxx + X[k * 3 + a] * X[k * 3 + c];
-        syy = syy + Y[k * 3 + a] * Y[k * 3 + c];
-      }
-      xy = xy + sxy * sxy;
-      xx = xx + sxx * sxx;
-      yy = yy + syy * syy;
+#pragma unroll
+    for (int c = a; c < 3; ++c) {
+      double s = 0.0;
+      for (int k = p; k < t; ++k) s = fma(X[k * 3 + a], X[k * 3 + c], s);
+      g[a][c] = s;
+      g[c][a] = s;
     }
+  double f = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f = fma(g[a][c], g[a][c], f);
+  return f;
+}
+
+// affinity of residual X and candidate Y; xx = gram_fro2(X), the same for
+// every candidate of one step
+__device__ __forceinline__ double affinity(int t, int p, const double *X, double xx, const double *Y) {
+  double xy = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+      for (int k = p; k < t; ++k) s = fma(X[k * 3 + a], Y[k * 3 + c], s);
+      xy = fma(s, s, xy);
+    }
+  const double yy = gram_fro2(t, p, Y);
   const double den = sqrt(xx) * sqrt(yy);
   return den > 0.0 ? xy / den : -1.0;
 }
@@ -1575,13 +1597,14 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
     if (nsel >= n_max || p + 3 > t) break;
     double rr = 0.0;
     for (int k = p; k < t; ++k)
-      for (int c = 0; c < 3; ++c) rr = rr + r[k * 3 + c] * r[k * 3 + c];
+      for (int c = 0; c < 3; ++c) rr = fma(r[k * 3 + c], r[k * 3 + c], rr);
     if (rr == 0.0) break;
+    const double xx = gram_fro2(t, p, r);
     int best = -1;
     double baff = 0.0;
     for (int j = 0; j < ncand; ++j) {
       if (tk[j]) continue;
-      const double a = affinity(t, p, r, vt + (size_t)j * t * 3);
+      const double a = affinity(t, p, r, xx, vt + (size_t)j * t * 3);
       if (a < 0.0) continue;
       if (best < 0 || a > baff) {
         best = j;
@@ -1595,7 +1618,7 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
     for (int c = 0; c < 3 && ok; ++c) {
       const int pc = p + c;
       double sg = 0.0;
-      for (int k = pc; k < t; ++k) sg = sg + Y[k * 3 + c] * Y[k * 3 + c];
+      for (int k = pc; k < t; ++k) sg = fma(Y[k * 3 + c], Y[k * 3 + c], sg);
       sg = sqrt(sg);
       if (!(sg > 0.0)) {
         ok = 0;
@@ -1605,7 +1628,7 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
       for (int k = 0; k < t; ++k) hv[c][k] = (k >= pc) ? Y[k * 3 + c] : 0.0;
       hv[c][pc] = Y[pc * 3 + c] - alpha;
       double vv = 0.0;
-      for (int k = pc; k < t; ++k) vv = vv + hv[c][k] * hv[c][k];
+      for (int k = pc; k < t; ++k) vv = fma(hv[c][k], hv[c][k], vv);
       hvv[c] = vv;
       for (int c2 = c + 1; c2 < 3; ++c2) reflect(t, pc, hv[c], vv, Y + c2, 3);
       Y[pc * 3 + c] = alpha;
@@ -1638,7 +1661,7 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
   for (int c = 0; c < 3; ++c)
     for (int i = p - 1; i >= 0; --i) {
       double s = r[i * 3 + c];
-      for (int k = p - 1; k > i; --k) s = s - R[i * TMAXD + k] * w[k * 3 + c];
+      for (int k = p - 1; k > i; --k) s = fma(-R[i * TMAXD + k], w[k * 3 + c], s);
       w[i * 3 + c] = s / R[i * TMAXD + i];
     }
   // entries sorted by coarse index
