@@ -196,14 +196,38 @@ int or_afsai(const obsr *A, const obsr *Gs, int ksteps, int rho, double eps,
 }
 
 /* Sturm count: number of eigenvalues of the symmetric tridiagonal matrix
- * (alpha, beta) that are smaller than x. */
+ * (alpha, beta) that are smaller than x, as the number of sign changes in the
+ * sequence of leading principal minors of T - x I:
+ *   q_0 = 1, q_1 = a_0 - x, q_{i+1} = (a_i - x) q_i - b_{i-1}^2 q_{i-1}
+ * (each product and difference rounded once, in that order).  The recurrence
+ * needs no division (on the GPU a division costs about ten products).  A minor
+ * that is exactly zero is replaced by q_{i-1} 2^-200 (the sign of the one
+ * before it: the next minor then records the change); when a minor's binary
+ * exponent leaves [-512, 511] it and its predecessor are multiplied by 2^-512
+ * or 2^512, which is exact and keeps every sign. */
+static int bexp(double v) {
+  uint64_t u;
+  memcpy(&u, &v, sizeof u);
+  return (int)((u >> 52) & 0x7ff) - 1023;
+}
+
 static int sturm_count(int m, const double *al, const double *be, double x) {
   int cnt = 0;
-  double d = 1.0;
+  double qp = 1.0, q = 1.0;
   for (int i = 0; i < m; ++i) {
-    d = (i == 0) ? (al[0] - x) : (al[i] - x) - (be[i - 1] * be[i - 1]) / d;
-    if (d == 0.0) d = 1e-300;
-    if (d < 0.0) ++cnt;
+    double qn = (i == 0) ? (al[0] - x) : (al[i] - x) * q - (be[i - 1] * be[i - 1]) * qp;
+    if (qn == 0.0) qn = q * 0x1p-200;
+    if ((qn < 0.0) != (q < 0.0)) ++cnt;
+    qp = q;
+    q = qn;
+    const int e = bexp(q);
+    if (e > 511) {
+      q = q * 0x1p-512;
+      qp = qp * 0x1p-512;
+    } else if (e < -512) {
+      q = q * 0x1p512;
+      qp = qp * 0x1p512;
+    }
   }
   return cnt;
 }

@@ -16,6 +16,13 @@
  * k_ritz iterations the block Z is rotated by the Ritz vectors of the pencil
  * (Z^T S Z, Z^T Z).  At the end V = G^T Z with orthonormalised columns.
  *
+ * S Z and S P are formed once from the first Z and P and then carried by the
+ * same linear recurrences as Z and P (the usual SRQCG organisation; the
+ * algorithm only names the quantities): z <- z + alpha p brings
+ * S z <- S z + alpha S p, p <- g + beta p brings S p <- S g + beta S p, and
+ * the Ritz rotation Z <- Z U brings S Z <- (S Z) U.  The one product with S
+ * per column and iteration is S g.
+ *
  * All inner products use the fixed-order or_dot, all sparse products the
  * fixed-order or_spmv; vector updates are single rounded operations per
  * entry.
@@ -50,7 +57,8 @@ void or_mgs(int n, int t, double *V) {
 }
 
 /* Generalised symmetric eigenproblem H U = M U diag(lam), M SPD, t x t
- * row-major.  M = L L^T; C = L^{-1} (L^{-1} H)^T, symmetrised as
+ * row-major.  M = L L^T (or_chol); the triangular solves multiply by
+ * 1 / L[i][i] like or_chol_solve; C = L^{-1} (L^{-1} H)^T, symmetrised as
  * (C + C^T) * 0.5; Jacobi sweeps until the off-diagonal mass is negligible;
  * eigenvalues sorted ascending (ties keep index order); U = L^{-T} W; each
  * column of U signed so that its entry of largest magnitude (first on ties)
@@ -77,13 +85,13 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
     for (int i = 0; i < t; ++i) {
       double s = H[i * t + j];
       for (int k = 0; k < i; ++k) s = s - L[i * t + k] * W1[k * t + j];
-      W1[i * t + j] = s / L[i * t + i];
+      W1[i * t + j] = s * (1.0 / L[i * t + i]);
     }
   for (int j = 0; j < t; ++j)
     for (int i = 0; i < t; ++i) {
       double s = W1[j * t + i];
       for (int k = 0; k < i; ++k) s = s - L[i * t + k] * C[k * t + j];
-      C[i * t + j] = s / L[i * t + i];
+      C[i * t + j] = s * (1.0 / L[i * t + i]);
     }
   for (int i = 0; i < t; ++i)
     for (int j = 0; j < i; ++j) {
@@ -170,7 +178,7 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
     for (int i = t - 1; i >= 0; --i) {
       double s = Wv[i * t + j];
       for (int k = t - 1; k > i; --k) s = s - L[k * t + i] * tmp[k];
-      tmp[i] = s / L[i * t + i];
+      tmp[i] = s * (1.0 / L[i * t + i]);
     }
     int im = 0;
     for (int i = 1; i < t; ++i)
@@ -210,10 +218,10 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
   const size_t nt = (size_t)n * t;
   double *Z = (double *)malloc(nt * sizeof(double));
   double *P = (double *)malloc(nt * sizeof(double));
-  double *SZall = (double *)malloc(nt * sizeof(double));
-  double *SZ = (double *)malloc((size_t)n * sizeof(double));
-  double *SP = (double *)malloc((size_t)n * sizeof(double));
+  double *SZ = (double *)malloc(nt * sizeof(double));
+  double *SP = (double *)malloc(nt * sizeof(double));
   double *Gv = (double *)malloc((size_t)n * sizeof(double));
+  double *SG = (double *)malloc((size_t)n * sizeof(double));
   double *t1 = (double *)malloc((size_t)n * sizeof(double));
   double *t2 = (double *)malloc((size_t)n * sizeof(double));
   double f[64], H[64 * 64], M[64 * 64], U[64 * 64], lam[64];
@@ -224,24 +232,26 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
   for (int i = 0; i < t; ++i) {
     const double *v = V0 + (size_t)i * n;
     double *z = Z + (size_t)i * n;
-    apply_s(A, G, GT, v, SZ, t1, t2);
-    for (int k = 0; k < n; ++k) z[k] = v[k] - SZ[k];
+    apply_s(A, G, GT, v, Gv, t1, t2);
+    for (int k = 0; k < n; ++k) z[k] = v[k] - Gv[k];
   }
   or_mgs(n, t, Z);
-  /* first residuals and directions: q = z^T S z (z has unit norm), P = 2R */
+  /* first residuals and directions: q = z^T S z (z has unit norm), P = 2R;
+   * S Z and S P formed once here, then carried by the recurrences below */
   for (int i = 0; i < t; ++i) {
     double *z = Z + (size_t)i * n, *p = P + (size_t)i * n;
-    apply_s(A, G, GT, z, SZ, t1, t2);
-    const double q = or_dot(n, z, SZ);
-    for (int k = 0; k < n; ++k) p[k] = 2.0 * (SZ[k] - q * z[k]);
+    double *sz = SZ + (size_t)i * n, *sp = SP + (size_t)i * n;
+    apply_s(A, G, GT, z, sz, t1, t2);
+    const double q = or_dot(n, z, sz);
+    for (int k = 0; k < n; ++k) p[k] = 2.0 * (sz[k] - q * z[k]);
+    apply_s(A, G, GT, p, sp, t1, t2);
     f[i] = 1.0;
   }
   for (int it = 1; it <= kmax && rc == OR_OK; ++it) {
     if (k_ritz > 0 && it % k_ritz == 0) {
-      for (int j = 0; j < t; ++j) apply_s(A, G, GT, Z + (size_t)j * n, SZall + (size_t)j * n, t1, t2);
       for (int i = 0; i < t; ++i)
         for (int j = i; j < t; ++j) {
-          const double h = or_dot(n, Z + (size_t)i * n, SZall + (size_t)j * n);
+          const double h = or_dot(n, Z + (size_t)i * n, SZ + (size_t)j * n);
           const double m = or_dot(n, Z + (size_t)i * n, Z + (size_t)j * n);
           H[i * t + j] = h;
           H[j * t + i] = h;
@@ -250,33 +260,42 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
         }
       rc = or_gen_eig(t, H, M, U, lam);
       if (rc) break;
-      /* Z <- Z U, column j = sum_i Z_i U[i][j], i ascending from 0 */
-      for (int k = 0; k < n; ++k) {
-        double row[64];
-        for (int j = 0; j < t; ++j) {
-          double s = 0.0;
-          for (int i = 0; i < t; ++i) s = s + Z[(size_t)i * n + k] * U[i * t + j];
-          row[j] = s;
+      /* Z <- Z U and S Z <- (S Z) U, column j = sum_i X_i U[i][j], i
+       * ascending from 0 */
+      for (int w = 0; w < 2; ++w) {
+        double *X = w == 0 ? Z : SZ;
+        for (int k = 0; k < n; ++k) {
+          double row[64];
+          for (int j = 0; j < t; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < t; ++i) s = s + X[(size_t)i * n + k] * U[i * t + j];
+            row[j] = s;
+          }
+          for (int j = 0; j < t; ++j) X[(size_t)j * n + k] = row[j];
         }
-        for (int j = 0; j < t; ++j) Z[(size_t)j * n + k] = row[j];
       }
       for (int i = 0; i < t; ++i) f[i] = 1.0;
     }
     for (int i = 0; i < t; ++i) {
       double *z = Z + (size_t)i * n, *p = P + (size_t)i * n;
-      apply_s(A, G, GT, z, SZ, t1, t2);
-      apply_s(A, G, GT, p, SP, t1, t2);
-      const double a = or_dot(n, p, SZ), b = or_dot(n, p, SP), c = or_dot(n, p, z);
-      const double d = or_dot(n, p, p), e = or_dot(n, z, SZ), fi = f[i];
+      double *sz = SZ + (size_t)i * n, *sp = SP + (size_t)i * n;
+      const double a = or_dot(n, p, sz), b = or_dot(n, p, sp), c = or_dot(n, p, z);
+      const double d = or_dot(n, p, p), e = or_dot(n, z, sz), fi = f[i];
       if (!(b > 0.0)) continue;
       const double alpha = or_rq_line_min(a, b, c, d, e, fi);
-      for (int k = 0; k < n; ++k) z[k] = z[k] + alpha * p[k];
-      apply_s(A, G, GT, z, SZ, t1, t2);
+      for (int k = 0; k < n; ++k) {
+        z[k] = z[k] + alpha * p[k];
+        sz[k] = sz[k] + alpha * sp[k];
+      }
       const double fn = or_dot(n, z, z);
-      const double q = or_dot(n, z, SZ) / fn;
-      for (int k = 0; k < n; ++k) Gv[k] = (2.0 * (SZ[k] - q * z[k])) / fn;
-      const double beta = -(or_dot(n, Gv, SP) / b);
-      for (int k = 0; k < n; ++k) p[k] = Gv[k] + beta * p[k];
+      const double q = or_dot(n, z, sz) / fn;
+      for (int k = 0; k < n; ++k) Gv[k] = (2.0 * (sz[k] - q * z[k])) / fn;
+      apply_s(A, G, GT, Gv, SG, t1, t2);
+      const double beta = -(or_dot(n, Gv, sp) / b);
+      for (int k = 0; k < n; ++k) {
+        p[k] = Gv[k] + beta * p[k];
+        sp[k] = SG[k] + beta * sp[k];
+      }
       f[i] = fn;
     }
   }
@@ -284,6 +303,6 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
     for (int i = 0; i < t; ++i) or_spmv(GT, Z + (size_t)i * n, V + (size_t)i * n);
     or_mgs(n, t, V);
   }
-  free(Z); free(P); free(SZall); free(SZ); free(SP); free(Gv); free(t1); free(t2);
+  free(Z); free(P); free(SZ); free(SP); free(Gv); free(SG); free(t1); free(t2);
   return rc;
 }

@@ -131,37 +131,40 @@ const double *or_bsr_find(const obsr *A, int i, int j) {
 /* Dense Cholesky M = L L^T of an m x m row-major matrix (only the lower
  * triangle of M is read).  Entry (i,j), i >= j:
  *   s = M[i][j] - sum_{k<j} L[i][k] L[j][k]   (k ascending)
- *   L[j][j] = sqrt(s) for i = j, else L[i][j] = s / L[j][j].  */
+ *   L[j][j] = sqrt(s) for i = j, else L[i][j] = s * rho_j with the
+ * reciprocal rho_j = 1 / L[j][j] (one correctly rounded division per column,
+ * then products: a division costs many times a product on the GPU).  */
 int or_chol(int m, const double *M, double *L) {
   memset(L, 0, (size_t)m * m * sizeof(double));
   for (int j = 0; j < m; ++j) {
     double s = M[j * m + j];
     for (int k = 0; k < j; ++k) s = fma(-L[j * m + k], L[j * m + k], s);
     if (!(s > 0.0)) return OR_ERR_NOT_SPD;
-    const double d = sqrt(s);
+    const double d = sqrt(s), rho = 1.0 / d;
     L[j * m + j] = d;
     for (int i = j + 1; i < m; ++i) {
       double t = M[i * m + j];
       for (int k = 0; k < j; ++k) t = fma(-L[i * m + k], L[j * m + k], t);
-      L[i * m + j] = t / d;
+      L[i * m + j] = t * rho;
     }
   }
   return OR_OK;
 }
 
 /* Solve L L^T x = rhs: forward substitution with k ascending, then backward
- * substitution with k descending (from m-1 down to i+1). */
+ * substitution with k descending (from m-1 down to i+1); each unknown is its
+ * reduced right-hand side times 1 / L[i][i]. */
 void or_chol_solve(int m, const double *L, const double *rhs, double *x) {
   double *y = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
   for (int i = 0; i < m; ++i) {
     double s = rhs[i];
     for (int k = 0; k < i; ++k) s = fma(-L[i * m + k], y[k], s);
-    y[i] = s / L[i * m + i];
+    y[i] = s * (1.0 / L[i * m + i]);
   }
   for (int i = m - 1; i >= 0; --i) {
     double s = y[i];
     for (int k = m - 1; k > i; --k) s = fma(-L[k * m + i], x[k], s);
-    x[i] = s / L[i * m + i];
+    x[i] = s * (1.0 / L[i * m + i]);
   }
   free(y);
 }

@@ -45,24 +45,55 @@ __device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t counter) {
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------- SpMV
+// sum_k sum_c A_k[r][c] x[3 J_k + c] over the blocks kb..ke-1 of one block
+// row, one fused multiply-add per term in block and column order.  The
+// indices and operands of B blocks are loaded ahead of their chain, so a long
+// row waits on memory once per B blocks rather than once per block.
+template <int B>
+__device__ __forceinline__ double row_chain(int kb, int ke, int r, const int *__restrict__ col,
+                                            const double *__restrict__ val, const double *__restrict__ x, double s) {
+  for (int k0 = kb; k0 < ke; k0 += B) {
+    long J[B];
+    double a[B][3], xv[B][3];
+#pragma unroll
+    for (int u = 0; u < B; ++u) J[u] = k0 + u < ke ? col[k0 + u] : 0;
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a[u][c] = k0 + u < ke ? val[(size_t)(k0 + u) * 9 + r * 3 + c] : 0.0;
+        xv[u][c] = k0 + u < ke ? x[J[u] * 3 + c] : 0.0;
+      }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (k0 + u < ke)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s = fma(a[u][c], xv[u][c], s);
+  }
+  return s;
+}
+
+template <int B>
 __global__ void k_spmv(int nr, const int *__restrict__ rowptr, const int *__restrict__ col,
                        const double *__restrict__ val, const double *__restrict__ x,
                        double *__restrict__ y) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3L * nr) return;
   const int I = (int)(t / 3), r = (int)(t - 3L * I);
-  double s = 0.0;
-  for (int k = rowptr[I]; k < rowptr[I + 1]; ++k) {
-    const double *blk = val + (size_t)k * 9;
-    const long J = col[k];
-    for (int c = 0; c < 3; ++c) s = fma(blk[r * 3 + c], x[J * 3 + c], s);
-  }
-  y[t] = s;
+  y[t] = row_chain<B>(rowptr[I], rowptr[I + 1], r, col, val, x, 0.0);
 }
+
+// Below this many block rows a product has too few warps to hide memory
+// latency and the loads are batched (more registers per thread); above it the
+// plain loop keeps more warps resident.
+constexpr int SMALL_ROWS = 16384;
 
 int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
   if (A.nr == 0) return AMG_OK;
-  AMG_KCOUNT k_spmv<<<nblk(3L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+  if (A.nr < SMALL_ROWS)
+    AMG_KCOUNT k_spmv<8><<<nblk(3L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+  else
+    AMG_KCOUNT k_spmv<1><<<nblk(3L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -252,8 +283,10 @@ __device__ __forceinline__ void pair_of(int d, int t, int &which, int &i, int &j
 __global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restrict__ Z, const double *__restrict__ SZ,
                                              double *__restrict__ part, unsigned *ticket, int nchunks,
                                              double *__restrict__ H, double *__restrict__ M, double *__restrict__ U,
-                                             double *__restrict__ lam, double *__restrict__ wk, double *__restrict__ f,
+                                             double *__restrict__ lam, double *__restrict__ f,
                                              int *__restrict__ status) {
+  // the last warp's working arrays (6 t^2 + t doubles, dynamic shared memory)
+  extern __shared__ double wk[];
   const int nd = t * (t + 1);
   const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
@@ -275,7 +308,7 @@ __global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restr
         O[j * t + i] = v;
       });
   if (!last) return;
-  // the pencil was written by other warps: read it through L2 into scratch
+  // the pencil was written by other warps: read it through L2 into shared memory
   double *Hs = wk + 4 * t * t + t, *Ms = Hs + t * t;
   for (int q = lane; q < t * t; q += 32) {
     Hs[q] = __ldcg(H + q);
@@ -444,7 +477,9 @@ __device__ __forceinline__ void tri_decode(int idx, int &rr, int &kk) {
 // Cholesky factor depends only on the leading (r+1)x(r+1) block, so each
 // row's factor is exactly what factoring it alone gives).  A is read one 3x3
 // block per node pair: the lower triangle of the largest system,
-// rhs_c = -A[Q_c, 3I+c] and ent_c = A[3I+c, Q_c].
+// rhs_c = -A[Q_c, 3I+c] and ent_c = A[3I+c, Q_c].  Column j of the factor is
+// scaled by rho_j = 1 / L_jj, which the diagonal then holds for the
+// substitutions (a product per unknown instead of a division).
 __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, int np, double *M, double *gh,
                                double *rhs, double *ent, double *psi, int g, int gl) {
   const int m2 = act ? 3 * np + 2 : 0, mm = K.mmax, nn = np + 1;
@@ -488,16 +523,16 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
     const int j1 = min(j0 + FS_PB, m2);  // this slot's panel end
     for (int j = j0; j < j0 + FS_PB && j < mx; ++j) {
       const bool on = j < m2 && !bad;
-      double d = 1.0;
+      double rho = 1.0;
       if (on) {
         const double sjj = M[j * m2 + j];
         if (!(sjj > 0.0)) bad = 1;
-        else d = sqrt(sjj);
+        else rho = 1.0 / sqrt(sjj);
       }
       __syncwarp();
       if (on && !bad) {
-        for (int r = j + 1 + gl; r < m2; r += FS_GL) M[r * m2 + j] = M[r * m2 + j] / d;
-        if (gl == 0) M[j * m2 + j] = d;
+        for (int r = j + 1 + gl; r < m2; r += FS_GL) M[r * m2 + j] = M[r * m2 + j] * rho;
+        if (gl == 0) M[j * m2 + j] = rho;  // the diagonal holds 1 / L_jj
       }
       __syncwarp();
       if (on && !bad) {  // the panel's later columns, rows k..m2-1
@@ -524,14 +559,14 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
   }
   const bool ok = act && !bad;
   // forward substitution for the three right-hand sides together (row c
-  // uses the leading 3np + c rows): y_k = rhs_k / L_kk, then rhs_r -= L_rk y_k
+  // uses the leading 3np + c rows): y_k = rhs_k (1 / L_kk), then rhs_r -= L_rk y_k
   // (k ascending for every r), in blocks of FS_PB columns: inside a block
   // column by column, then the rows below it take the block's updates in
   // one pass
   for (int k0 = 0; k0 < mx; k0 += FS_PB) {
     const int k1 = min(k0 + FS_PB, mx);
     for (int k = k0; k < k1; ++k) {
-      if (ok && gl < 3 && k < 3 * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] / M[k * m2 + k];
+      if (ok && gl < 3 && k < 3 * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] * M[k * m2 + k];
       __syncwarp();
       if (ok)
         for (int idx = gl; idx < 3 * (k1 - k - 1); idx += FS_GL) {
@@ -551,13 +586,13 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       }
     __syncwarp();
   }
-  // backward substitution: x_k = rhs_k / L_kk for k descending, then
+  // backward substitution: x_k = rhs_k (1 / L_kk) for k descending, then
   // rhs_r -= L_kr x_k for r < k (k descending for every r), in blocks of
   // FS_PB columns from the top
   for (int k1 = mx; k1 > 0; k1 -= FS_PB) {
     const int k0 = max(k1 - FS_PB, 0);
     for (int k = k1 - 1; k >= k0; --k) {
-      if (ok && gl < 3 && k < 3 * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] / M[k * m2 + k];
+      if (ok && gl < 3 && k < 3 * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] * M[k * m2 + k];
       __syncwarp();
       if (ok && k < m2)
         for (int idx = gl; idx < 3 * (k - k0); idx += FS_GL) {
@@ -830,9 +865,54 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
 
 // ---------------------------------------------------------------- Lanczos
 // largest eigenvalue of the tridiagonal (alpha, beta) by bisection on Sturm
-// counts; out = [lambda, 2/lambda, min(1, safety * 2/lambda)]
-__global__ void k_lanczos_bisect(int m, const double *__restrict__ sc, double safety, double *__restrict__ out) {
-  const double *al = sc, *be = sc + 64;
+// counts; out = [lambda, 2/lambda, min(1, safety * 2/lambda)].
+//
+// One warp.  The bisection is a walk down a binary tree whose nodes are the
+// intervals it can visit; each round the 31 lanes take the 31 nodes of the
+// next five levels below the current interval (heap order: node q has
+// children 2q+1, holding the lower half, and 2q+2), replay the midpoints on
+// the path to their node, and form the Sturm count at its midpoint; the walk
+// then takes five steps using those counts.  Every midpoint and count is the
+// one the step-by-step bisection forms, so the result is the same number.
+//
+// The Sturm count is the number of sign changes among the leading principal
+// minors of T - x I, q_0 = 1, q_1 = a_0 - x,
+// q_{i+1} = (a_i - x) q_i - b_{i-1}^2 q_{i-1}: no division (a division costs
+// about ten FP64 issue slots).  A zero minor becomes q_{i-1} 2^-200 (it keeps
+// the previous sign and the next minor records the change); a minor whose
+// binary exponent leaves [-512, 511] is multiplied, with its predecessor, by
+// 2^-512 or 2^512 (exact, signs unchanged).
+__device__ __forceinline__ int sturm_count(int mm, const double *al, const double *bb, double x) {
+  int cnt = 0;
+  double qp = 1.0, q = 1.0;
+  for (int i = 0; i < mm; ++i) {
+    double qn = (i == 0) ? (al[0] - x) : (al[i] - x) * q - bb[i - 1] * qp;
+    if (qn == 0.0) qn = q * 0x1p-200;
+    if ((qn < 0.0) != (q < 0.0)) ++cnt;
+    qp = q;
+    q = qn;
+    const int e = (int)((__double_as_longlong(q) >> 52) & 0x7ff) - 1023;
+    if (e > 511) {
+      q = q * 0x1p-512;
+      qp = qp * 0x1p-512;
+    } else if (e < -512) {
+      q = q * 0x1p512;
+      qp = qp * 0x1p512;
+    }
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(32) k_lanczos_bisect(int m, const double *__restrict__ sc, double safety,
+                                                       double *__restrict__ out) {
+  __shared__ double al[64], be[64], bb[64];
+  const int lane = threadIdx.x;
+  for (int i = lane; i < 64; i += 32) {
+    al[i] = sc[i];
+    be[i] = sc[64 + i];
+    bb[i] = be[i] * be[i];
+  }
+  __syncwarp();
   const int mm = sc[128] < 0.0 ? m : (int)sc[128];
   double lo = al[0], hi = al[0];
   for (int i = 0; i < mm; ++i) {
@@ -840,24 +920,59 @@ __global__ void k_lanczos_bisect(int m, const double *__restrict__ sc, double sa
     if (al[i] - r < lo) lo = al[i] - r;
     if (al[i] + r > hi) hi = al[i] + r;
   }
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (!(mid > lo && mid < hi)) break;
-    int cnt = 0;
-    double d = 1.0;
-    for (int i = 0; i < mm; ++i) {
-      d = (i == 0) ? (al[0] - mid) : (al[i] - mid) - (be[i - 1] * be[i - 1]) / d;
-      if (d == 0.0) d = 1e-300;
-      if (d < 0.0) ++cnt;
+  int it = 0;
+  bool done = false;
+  while (!done && it < 200) {
+    int qok = 0, qcnt = 0;
+    double qmid = 0.0;
+    if (lane < 31) {
+      const int h = lane + 1, lev = 31 - __clz(h);
+      double ql = lo, qh = hi;
+      qok = 1;
+      for (int b = lev - 1; b >= 0; --b) {
+        const double md = 0.5 * (ql + qh);
+        if (!(md > ql && md < qh)) {
+          qok = 0;
+          break;
+        }
+        if ((h >> b) & 1)
+          ql = md;
+        else
+          qh = md;
+      }
+      if (qok) {
+        qmid = 0.5 * (ql + qh);
+        qok = qmid > ql && qmid < qh;
+        if (qok) qcnt = sturm_count(mm, al, bb, qmid);
+      }
     }
-    if (cnt >= mm) hi = mid; else lo = mid;
+    int node = 0;
+    for (int l = 0; l < 5 && it < 200; ++l) {
+      const int ok = __shfl_sync(0xffffffffu, qok, node);
+      const double md = __shfl_sync(0xffffffffu, qmid, node);
+      const int cnt = __shfl_sync(0xffffffffu, qcnt, node);
+      if (!ok) {
+        done = true;
+        break;
+      }
+      if (cnt >= mm) {
+        hi = md;
+        node = 2 * node + 1;
+      } else {
+        lo = md;
+        node = 2 * node + 2;
+      }
+      ++it;
+    }
   }
-  const double w = 2.0 / hi;
-  double om = safety * w;
-  if (om > 1.0) om = 1.0;
-  out[0] = hi;
-  out[1] = w;
-  out[2] = om;
+  if (lane == 0) {
+    const double w = 2.0 / hi;
+    double om = safety * w;
+    if (om > 1.0) om = 1.0;
+    out[0] = hi;
+    out[1] = w;
+    out[2] = om;
+  }
 }
 
 __global__ void k_set_neg(double *p) { *p = -1.0; }
@@ -910,13 +1025,17 @@ __global__ void k_b_p0(long n, int t, double *__restrict__ p, const double *__re
   p[i] = 2.0 * (sz[i] - q[j] * z[i]);
 }
 
+// z += alpha p and, by linearity, S z += alpha S p
 __global__ void k_b_zupd(long n, int t, double *__restrict__ z, const double *__restrict__ p,
-                         const double *__restrict__ cs, const int *__restrict__ skip) {
+                         double *__restrict__ sz, const double *__restrict__ sp, const double *__restrict__ cs,
+                         const int *__restrict__ skip) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * t) return;
   const int j = (int)(i / n);
   if (skip[j]) return;
-  z[i] = z[i] + cs[C_ALPHA * t + j] * p[i];
+  const double al = cs[C_ALPHA * t + j];
+  z[i] = z[i] + al * p[i];
+  sz[i] = sz[i] + al * sp[i];
 }
 
 __global__ void k_b_grad(long n, int t, double *__restrict__ g, const double *__restrict__ sz,
@@ -928,13 +1047,17 @@ __global__ void k_b_grad(long n, int t, double *__restrict__ g, const double *__
   g[i] = (2.0 * (sz[i] - cs[C_Q * t + j] * z[i])) / cs[C_FN * t + j];
 }
 
+// p = g + beta p and, by linearity, S p = S g + beta S p
 __global__ void k_b_pupd(long n, int t, double *__restrict__ p, const double *__restrict__ g,
-                         double *__restrict__ cs, const int *__restrict__ skip) {
+                         double *__restrict__ sp, const double *__restrict__ sg, double *__restrict__ cs,
+                         const int *__restrict__ skip) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * t) return;
   const int j = (int)(i / n);
   if (skip[j]) return;
-  p[i] = g[i] + cs[C_BETA * t + j] * p[i];
+  const double be = cs[C_BETA * t + j];
+  p[i] = g[i] + be * p[i];
+  sp[i] = sg[i] + be * sp[i];
   if (i - (long)j * n == 0) cs[C_F * t + j] = cs[C_FN * t + j];
 }
 
@@ -995,6 +1118,7 @@ __global__ void __launch_bounds__(32) k_cdots(int n, int t, int nk, CDot a, doub
 // order.  One warp per block row: lane (j, r) computes dof row r of column j,
 // so every lane walks the same blocks (the row's values are read once per
 // warp and no FP64 instruction runs on a partly idle warp for lack of work).
+template <int B>
 __global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const int *__restrict__ col,
                             const double *__restrict__ val, const double *__restrict__ X, double *__restrict__ Y) {
   const long n = 3L * nr;
@@ -1004,20 +1128,16 @@ __global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const
   const int kb = rowptr[I], ke = rowptr[I + 1];
   for (int pr = lane; pr < 3 * t; pr += 32) {
     const int j = pr / 3, r = pr - 3 * j;
-    const double *x = X + (size_t)j * n;
-    double sv = 0.0;
-    for (int k = kb; k < ke; ++k) {
-      const double *blk = val + (size_t)k * 9;
-      const long J = col[k];
-      for (int c = 0; c < 3; ++c) sv = fma(blk[r * 3 + c], x[J * 3 + c], sv);
-    }
-    Y[(size_t)j * n + 3L * I + r] = sv;
+    Y[(size_t)j * n + 3L * I + r] = row_chain<B>(kb, ke, r, col, val, X + (size_t)j * n, 0.0);
   }
 }
 
-__global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__restrict__ U) {
+// X = X U for X = Z (blockIdx.y 0) and X = S Z (blockIdx.y 1)
+__global__ void k_rotate(long n, int t, double *__restrict__ Z0, double *__restrict__ Z1,
+                         const double *__restrict__ U) {
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
+  double *__restrict__ Z = blockIdx.y ? Z1 : Z0;
   double row[TMAXD];
   for (int j = 0; j < t; ++j) {
     double s = 0.0;
@@ -1028,7 +1148,8 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__
 }
 
 // Generalised eigenproblem H U = M U diag(lam) of the Ritz step, by one warp:
-// M = L L^T; C = L^{-1} (L^{-1} H)^T symmetrised as (C + C^T) * 0.5; Jacobi
+// M = L L^T (sub-diagonal entries scaled by 1 / L_jj, the triangular solves
+// multiply by the reciprocals Ri); C = L^{-1} (L^{-1} H)^T symmetrised as (C + C^T) * 0.5; Jacobi
 // sweeps in round-robin order (per round T/2 disjoint pairs from the circle
 // method, rotations computed from the current C, then all column, all row
 // and all W rotations applied) until the off-diagonal mass is negligible;
@@ -1039,34 +1160,37 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z, const double *__
 // computed by the same sequence of rounded operations as the sequential
 // definition.  Scratch w holds 4 t*t + t doubles; returns 1 if M is not SPD.
 __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, double *lam, double *w, int lane) {
-  double *L = w, *W1 = w + t * t, *C = w + 2 * t * t, *Wv = w + 3 * t * t;
+  double *L = w, *W1 = w + t * t, *C = w + 2 * t * t, *Wv = w + 3 * t * t, *Ri = w + 4 * t * t;
   for (int i = lane; i < t * t; i += 32) L[i] = 0.0;
   __syncwarp();
   for (int j = 0; j < t; ++j) {
     double sj = M[j * t + j];
     for (int k = 0; k < j; ++k) sj = fma(-L[j * t + k], L[j * t + k], sj);
     if (!(sj > 0.0)) return 1;
-    const double d = sqrt(sj);
+    const double d = sqrt(sj), rho = 1.0 / d;
     for (int i = j + 1 + lane; i < t; i += 32) {
       double u = M[i * t + j];
       for (int k = 0; k < j; ++k) u = fma(-L[i * t + k], L[j * t + k], u);
-      L[i * t + j] = u / d;
+      L[i * t + j] = u * rho;
     }
-    if (lane == 0) L[j * t + j] = d;
+    if (lane == 0) {
+      L[j * t + j] = d;
+      Ri[j] = rho;
+    }
     __syncwarp();
   }
   for (int j = lane; j < t; j += 32)
     for (int i = 0; i < t; ++i) {
       double sv = H[i * t + j];
       for (int k = 0; k < i; ++k) sv = sv - L[i * t + k] * W1[k * t + j];
-      W1[i * t + j] = sv / L[i * t + i];
+      W1[i * t + j] = sv * Ri[i];
     }
   __syncwarp();
   for (int j = lane; j < t; j += 32)
     for (int i = 0; i < t; ++i) {
       double sv = W1[j * t + i];
       for (int k = 0; k < i; ++k) sv = sv - L[i * t + k] * C[k * t + j];
-      C[i * t + j] = sv / L[i * t + i];
+      C[i * t + j] = sv * Ri[i];
     }
   __syncwarp();
   for (int q = lane; q < t * t; q += 32) {
@@ -1154,7 +1278,7 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
     for (int i = t - 1; i >= 0; --i) {
       double sv = Wv[i * t + j];
       for (int k = t - 1; k > i; --k) sv = sv - L[k * t + i] * col[k];
-      col[i] = sv / L[i * t + i];
+      col[i] = sv * Ri[i];
     }
     int im = 0;
     for (int i = 1; i < t; ++i)
@@ -1168,7 +1292,10 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
 
 int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
   if (A.nr == 0) return AMG_OK;
-  AMG_KCOUNT k_spmv_cols<<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+  if (A.nr < SMALL_ROWS)
+    AMG_KCOUNT k_spmv_cols<4><<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+  else
+    AMG_KCOUNT k_spmv_cols<1><<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -1200,19 +1327,23 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     return AMG_ERR_ARG;
   }
   const size_t nt = (size_t)n * t;
-  // Z and P (and S Z, S P) are adjacent column blocks, so that S is applied
-  // to both in one pass of 2t columns
-  DBuf<double> ZP, SZP, Gv, T1, T2, cs, out, part, H, Mg, U, lam, wk;
+  // S Z and S P are formed once and then carried by the recurrences of Z
+  // and P (z += alpha p, p = g + beta p, Z = Z U are linear), so an
+  // iteration applies S once, to the gradients
+  DBuf<double> Zb, Pb, SZb, SPb, Gv, SG, T1, T2, cs, out, part, H, Mg, U, lam;
   DBuf<int> skip;
   DBuf<unsigned> tk;
-  AMG_TRY(ZP.alloc(2 * nt));
-  AMG_TRY(SZP.alloc(2 * nt));
+  AMG_TRY(Zb.alloc(nt));
+  AMG_TRY(Pb.alloc(nt));
+  AMG_TRY(SZb.alloc(nt));
+  AMG_TRY(SPb.alloc(nt));
   AMG_TRY(Gv.alloc(nt));
-  AMG_TRY(T1.alloc(2 * nt));
-  AMG_TRY(T2.alloc(2 * nt));
+  AMG_TRY(SG.alloc(nt));
+  AMG_TRY(T1.alloc(nt));
+  AMG_TRY(T2.alloc(nt));
   struct Half {
     double *p;
-  } Z{ZP.p}, P{ZP.p + nt}, SZ{SZP.p}, SP{SZP.p + nt};
+  } Z{Zb.p}, P{Pb.p}, SZ{SZb.p}, SP{SPb.p};
   AMG_TRY(cs.alloc(C_NUM * t));
   AMG_TRY(out.alloc(5 * t));
   const int nchunks = (n + CHUNK - 1) / CHUNK;
@@ -1221,7 +1352,6 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   AMG_TRY(Mg.alloc(t * t));
   AMG_TRY(U.alloc(t * t));
   AMG_TRY(lam.alloc(t));
-  AMG_TRY(wk.alloc(6 * t * t + t));
   AMG_TRY(skip.alloc(t));
   AMG_TRY(tk.alloc(MAXTICKETS));
   AMG_TRY(cs.zero(s));
@@ -1234,7 +1364,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   AMG_KCOUNT k_b_z0<<<nb, 256, 0, s>>>((long)nt, Z.p, V0, SZ.p);
   AMG_LAUNCH_CHECK();
   AMG_TRY(mgs(n, t, Z.p, s));
-  // first quotients (unit columns) and directions P = 2 (S Z - q Z)
+  // first quotients (unit columns), directions P = 2 (S Z - q Z), then S P
   AMG_TRY(apply_s_cols(A, G, GT, t, Z.p, SZ.p, T1.p, T2.p, s));
   {
     CDot a{};
@@ -1246,19 +1376,16 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(cs.p + C_F * t, t, 1.0);
     AMG_LAUNCH_CHECK();
   }
+  AMG_TRY(apply_s_cols(A, G, GT, t, P.p, SP.p, T1.p, T2.p, s));
   // one iteration of the outer loop (optionally with the Ritz step)
   auto iteration = [&](bool ritz) -> int {
     if (ritz) {
-      // SZ already holds S Z for the current Z (computed at the end of the
-      // previous iteration, or for the first quotients, and Z has not
-      // changed since): the Ritz step reuses it
       const long warps = nchunks > 0 ? (long)nchunks * t * (t + 1) : 1;
-      AMG_KCOUNT k_gram<<<(int)warps, 32, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p, U.p,
-                                                             lam.p, wk.p, cs.p + C_F * t, status);
-      AMG_KCOUNT k_rotate<<<nblk(n, 256), 256, 0, s>>>(n, t, Z.p, U.p);
+      AMG_KCOUNT k_gram<<<(int)warps, 32, (6 * t * t + t) * sizeof(double), s>>>(
+          n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p, U.p, lam.p, cs.p + C_F * t, status);
+      AMG_KCOUNT k_rotate<<<dim3(nblk(n, 256), 2), 256, 0, s>>>(n, t, Z.p, SZ.p, U.p);  // Z U, (S Z) U
       AMG_LAUNCH_CHECK();
     }
-    AMG_TRY(apply_s_cols(A, G, GT, 2 * t, ZP.p, SZP.p, T1.p, T2.p, s));  // S Z and S P
     CDot a5{};
     a5.x[0] = P.p; a5.y[0] = SZ.p;
     a5.x[1] = P.p; a5.y[1] = SP.p;
@@ -1267,9 +1394,8 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     a5.x[4] = Z.p; a5.y[4] = SZ.p;
     for (int q = 0; q < 5; ++q) a5.xs[q] = a5.ys[q] = n;
     AMG_TRY(cdots(n, t, 5, a5, out.p, CF_ALPHA, cs.p, skip.p, ctx, s));
-    AMG_KCOUNT k_b_zupd<<<nb, 256, 0, s>>>(n, t, Z.p, P.p, cs.p, skip.p);
+    AMG_KCOUNT k_b_zupd<<<nb, 256, 0, s>>>(n, t, Z.p, P.p, SZ.p, SP.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
-    AMG_TRY(apply_s_cols(A, G, GT, t, Z.p, SZ.p, T1.p, T2.p, s));
     CDot a2{};
     a2.x[0] = Z.p; a2.y[0] = Z.p;
     a2.x[1] = Z.p; a2.y[1] = SZ.p;
@@ -1277,12 +1403,13 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     AMG_TRY(cdots(n, t, 2, a2, out.p, CF_Q, cs.p, skip.p, ctx, s));
     AMG_KCOUNT k_b_grad<<<nb, 256, 0, s>>>(n, t, Gv.p, SZ.p, Z.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
+    AMG_TRY(apply_s_cols(A, G, GT, t, Gv.p, SG.p, T1.p, T2.p, s));  // the one product with S
     CDot a1{};
     a1.x[0] = Gv.p;
     a1.y[0] = SP.p;
     a1.xs[0] = a1.ys[0] = n;
     AMG_TRY(cdots(n, t, 1, a1, out.p, CF_BETA, cs.p, skip.p, ctx, s));
-    AMG_KCOUNT k_b_pupd<<<nb, 256, 0, s>>>(n, t, P.p, Gv.p, cs.p, skip.p);
+    AMG_KCOUNT k_b_pupd<<<nb, 256, 0, s>>>(n, t, P.p, Gv.p, SP.p, SG.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
     return AMG_OK;
   };
@@ -1399,7 +1526,7 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
     if (j < m - 1) AMG_KCOUNT k_div<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 64 + j);
     AMG_LAUNCH_CHECK();
   }
-  AMG_KCOUNT k_lanczos_bisect<<<1, 1, 0, s>>>(m, sc.p, safety, d_out);
+  AMG_KCOUNT k_lanczos_bisect<<<1, 32, 0, s>>>(m, sc.p, safety, d_out);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
