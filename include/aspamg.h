@@ -16,7 +16,11 @@
  *    aborts or throws.  amg_last_error() gives a one-line description of the
  *    last failure on the calling thread.
  *  - The handle owns all hierarchy storage (device) and frees it in amg_free.
- *    Calls on one handle must not run concurrently.
+ *    Calls on one handle must not run concurrently.  Device storage and
+ *    temporaries come from the device's default stream-ordered memory pool
+ *    (cudaMallocAsync on the handle's stream); the first allocation raises
+ *    that pool's release threshold so that freed memory stays in the pool
+ *    for the process instead of being returned at each synchronisation.
  */
 #ifndef ASPAMG_H
 #define ASPAMG_H
@@ -171,8 +175,8 @@ long long amg_launch_count(void);
 /* amg_vcycle without any memory allocation.  The paper has no counterpart:
  * this is a library service for callers that cannot allocate while they run
  * the preconditioner, for instance an outer Krylov solver of another code
- * whose device memory is all held by its own pool (a cudaMalloc inside the
- * call would fail or fragment it), or one that keeps every allocation out of
+ * whose device memory is all held by its own pool (a device allocation inside
+ * the call would fail or fragment it), or one that keeps every allocation out of
  * its iteration loop.  Same arguments, result and precision as amg_vcycle;
  * y and z are device vectors of 3*nnodes entries owned by the caller.
  * Scratch: a file-scope device array of 16,640 bytes in the library (a flag
@@ -184,8 +188,8 @@ long long amg_launch_count(void);
  * current), so make that first call before any stream capture.  All calls
  * share the array and it keeps the last call's contents (the call clears what
  * must start at zero); calls that overlap on the GPU, on any handles, race on
- * it and must be serialised by the caller.  No cudaMalloc, cudaFree or
- * allocating library routine is called. */
+ * it and must be serialised by the caller.  No device allocation or free
+ * (pool or otherwise) and no allocating library routine is called. */
 int amg_vcycle_noalloc(amg_handle h, const double *y, double *z);
 
 /* ---- structured Q1-hex elasticity problems (problem generation) ----

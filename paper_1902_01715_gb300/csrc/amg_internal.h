@@ -39,32 +39,49 @@ void set_error(const char *fmt, ...);
 void count_launches(long long n);
 #define AMG_KCOUNT ::amg::count_launches(1),
 
-// Owning device buffer (cudaMalloc / cudaFree).
+// Device memory comes from the device's stream-ordered pool: a buffer is
+// taken and given back in the order of the stream that is current for the
+// calling thread when it is allocated (the entry points make the handle's
+// stream current).  The set-up allocates and frees hundreds of temporaries;
+// cudaFree would synchronise the device each time, and the pool keeps freed
+// memory for reuse instead of returning it to the driver.
+cudaStream_t current_stream();
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s);
+  ~StreamScope();
+};
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+
+// Owning device buffer (pool allocation on the current stream; freed on the
+// same stream).
 template <class T>
 struct DBuf {
   T *p = nullptr;
   size_t n = 0;
+  cudaStream_t s = nullptr;
   DBuf() = default;
   DBuf(const DBuf &) = delete;
   DBuf &operator=(const DBuf &) = delete;
-  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
   DBuf &operator=(DBuf &&o) noexcept {
-    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
     return *this;
   }
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     n = 0;
   }
   int alloc(size_t count) {
     release();
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+    s = current_stream();
+    cudaError_t e = pool_alloc((void **)&p, count * sizeof(T), s);
     if (e != cudaSuccess) {
       p = nullptr;
-      set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
       return AMG_ERR_MEM;
     }
     n = count;

@@ -83,6 +83,7 @@ extern "C" int amg_setup(const amg_params *p, int nnodes, int nnzb, const int *r
     h->own_stream = true;
   }
   h->n = nnodes;
+  StreamScope scope(h->stream);
   int rc = build_hierarchy(h, rowptr, colind, vals, mem, ntv0, V0, mem);
   if (rc) {
     delete h;
@@ -97,6 +98,7 @@ extern "C" int amg_update_values(amg_handle hh, const double *vals, int mem) {
   if (!h || !vals || (mem != AMG_MEM_HOST && mem != AMG_MEM_DEVICE)) return AMG_ERR_ARG;
   // same pattern and starting near-null space; the adaptive set-up depends on
   // the values, so the whole hierarchy is rebuilt on the pattern it holds
+  StreamScope scope(h->stream);
   return build_hierarchy(h, nullptr, nullptr, vals, mem == AMG_MEM_HOST ? AMG_MEM_HOST : AMG_MEM_DEVICE,
                          h->ntv0, h->V0keep.p, AMG_MEM_DEVICE, true);
 }
@@ -108,6 +110,7 @@ static int staged_solve(Handle *h, int k, const double *B, double *X, double rto
     return AMG_ERR_ARG;
   }
   const size_t nk = (size_t)3 * h->n * k;
+  StreamScope scope(h->stream);
   const auto t0 = std::chrono::steady_clock::now();
   int rc;
   if (mem == AMG_MEM_HOST) {
@@ -216,6 +219,7 @@ extern "C" int amg_level_testspace(amg_handle hh, int lev, double *V) {
 extern "C" int amg_vcycle(amg_handle hh, const double *y, double *z) {
   Handle *h = (Handle *)hh;
   if (!h || !y || !z) return AMG_ERR_ARG;
+  StreamScope scope(h->stream);
   return vcycle_apply(h, y, z);
 }
 
@@ -223,6 +227,7 @@ extern "C" int amg_bench_spmv(amg_handle hh, int lev, int which, int prec_a64, i
                               double *bytes) {
   Handle *h = (Handle *)hh;
   if (!h || !ms || !bytes) return AMG_ERR_ARG;
+  StreamScope scope(h->stream);
   return bench_spmv(h, lev, which, prec_a64, reps, ms, bytes);
 }
 

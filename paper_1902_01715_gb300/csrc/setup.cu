@@ -33,6 +33,33 @@ const char *last_error() { return g_err; }
 
 static std::atomic<long long> g_launches{0};
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static thread_local cudaStream_t t_stream = nullptr;
+cudaStream_t current_stream() { return t_stream; }
+StreamScope::StreamScope(cudaStream_t s) : prev(t_stream) { t_stream = s; }
+StreamScope::~StreamScope() { t_stream = prev; }
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+  // once per device: keep freed pool memory (the default threshold returns
+  // it to the driver at every synchronisation)
+  static std::mutex mu;
+  static bool init[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!init[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      init[dev] = true;
+    }
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }

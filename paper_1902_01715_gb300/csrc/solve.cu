@@ -667,6 +667,9 @@ Handle::~Handle() {
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   if (pinned) cudaFreeHost(pinned);
   lev.clear();
+  // buffers are returned on the stream they were taken on: before it goes
+  for (DBuf<double> *b : {&Linv, &LinvT, &x, &r, &z, &p, &q, &zold, &bvec, &scal, &red, &V0keep}) b->release();
+  flags.release();
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
@@ -674,8 +677,8 @@ Handle::~Handle() {
 
 // One V-cycle z = B(y) that allocates no memory: for callers that cannot
 // allocate while they run it, e.g. an outer Krylov solver of another code
-// whose process keeps all device memory in its own pool (where a cudaMalloc
-// inside the call would fail or fragment that pool), or one that must keep
+// whose process keeps all device memory in its own pool (where a device
+// allocation inside the call would fail or fragment that pool), or one that must keep
 // every allocation out of its iteration loop.  Its scratch is the file-scope
 // array above; see include/aspamg.h for the limits.
 extern "C" int amg_vcycle_noalloc(amg_handle hh, const double *y, double *z) {
