@@ -234,6 +234,10 @@ struct Handle {
   long long graph_nodes = 0;
   int *pinned = nullptr;    // host flag for polling the PCG state
   Batch *batch = nullptr;   // k > 1 right-hand sides
+  // second stream of the set-up: the Lanczos estimate of a level runs there
+  // while the test space of the same level is generated
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_aux = nullptr;
   ~Handle();
 };
 
@@ -268,7 +272,7 @@ struct FsaiOut {
 int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int maxg, int maxdeg,
          FsaiOut out, int *status, cudaStream_t s);
 int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t seed, int level,
-            double safety, double *d_out /*[lmax, omega_loop, omega]*/, cudaStream_t s);
+            double safety, double *d_out /*[lmax, omega_loop, omega]*/, cudaStream_t s, bool sync = true);
 int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ritz, int t,
           const double *V0, double *V, int *status, cudaStream_t s);
 int mgs(int n, int t, double *V, cudaStream_t s);

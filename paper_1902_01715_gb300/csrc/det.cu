@@ -1482,7 +1482,7 @@ __global__ void k_lz_reorth(long n, int j, double *__restrict__ w, const double 
 // sc layout: [0..63] alpha, [64..127] beta, [128] breakdown step, [129] norm
 // square, [160..223] re-orthogonalisation coefficients.
 int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t seed, int level,
-            double safety, double *d_out, cudaStream_t s) {
+            double safety, double *d_out, cudaStream_t s, bool sync) {
   const int n = 3 * A.nr;
   if (m > n) m = n;
   if (m > 64) m = 64;
@@ -1528,7 +1528,8 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
   }
   AMG_KCOUNT k_lanczos_bisect<<<1, 32, 0, s>>>(m, sc.p, safety, d_out);
   AMG_LAUNCH_CHECK();
-  AMG_CU(cudaStreamSynchronize(s));
+  // the temporaries above are returned to the pool in the order of s
+  if (sync) AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
 }
 

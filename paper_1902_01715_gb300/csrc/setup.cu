@@ -54,6 +54,10 @@ cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
       if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = ~0ull;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        // memory freed on one stream is not handed to another by making the
+        // second wait for the first (the set-up runs two streams at once)
+        int no = 0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
       }
       init[dev] = true;
     }
@@ -697,8 +701,11 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
   return AMG_OK;
 }
 
-// Algorithm 3.
-static int smoother_setup(Handle *h, Level &L, int level) {
+// Algorithm 3, first part: the aFSAI factor G of the level, then the
+// Lanczos estimate of lambda_max(G A G^T) queued on the second stream into
+// `out` (3 doubles); smoother_finish waits for it.  The test space of the
+// level (S = G A G^T, no omega) is generated on the main stream meanwhile.
+static int smoother_start(Handle *h, Level &L, int level, DBuf<double> &out) {
   const amg_params &p = h->prm;
   cudaStream_t s = h->stream;
   double tt = now_s();
@@ -707,12 +714,33 @@ static int smoother_setup(Handle *h, Level &L, int level) {
   tt = now_s();
   AMG_TRY(transpose_bsr(L.G, L.GT, s));
   trace("G transpose", level, tt);
-  DBuf<double> out;
   AMG_TRY(out.alloc(3));
+  if (!h->aux) {
+    AMG_CU(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    AMG_CU(cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming));
+    AMG_CU(cudaEventCreateWithFlags(&h->ev_aux, cudaEventDisableTiming));
+  }
+  // A, G, G^T and out are ready in the order of s
+  AMG_CU(cudaEventRecord(h->ev_main, s));
+  AMG_CU(cudaStreamWaitEvent(h->aux, h->ev_main, 0));
+  {
+    StreamScope scope(h->aux);
+    AMG_TRY(det::lanczos(L.A, L.G, L.GT, p.lanczos_m, p.seed, level, p.omega_safety, out.p, h->aux, false));
+  }
+  AMG_CU(cudaEventRecord(h->ev_aux, h->aux));
+  return AMG_OK;
+}
+
+// Algorithm 3, second part: omega from the estimate; while the smoother is
+// too weak and G not yet too dense, refine G (each refinement re-estimates
+// on the main stream).  refined tells the caller that G changed.
+static int smoother_finish(Handle *h, Level &L, int level, DBuf<double> &out, bool &refined) {
+  const amg_params &p = h->prm;
+  cudaStream_t s = h->stream;
   double ho[3];
-  tt = now_s();
-  AMG_TRY(det::lanczos(L.A, L.G, L.GT, p.lanczos_m, p.seed, level, p.omega_safety, out.p, s));
-  trace("Lanczos", level, tt);
+  double tt = now_s();
+  AMG_CU(cudaEventSynchronize(h->ev_aux));
+  trace("Lanczos wait", level, tt);
   AMG_CU(cudaMemcpy(ho, out.p, sizeof ho, cudaMemcpyDeviceToHost));
   int passes = 0;
   while (ho[1] < p.omega_bar && (double)L.G.nnzb / (double)L.G.nr < p.rho_bar && passes < p.max_refine) {
@@ -728,6 +756,7 @@ static int smoother_setup(Handle *h, Level &L, int level) {
   L.lmax = ho[0];
   L.omega = ho[2];
   L.npasses = passes;
+  refined = passes > 0;
   return AMG_OK;
 }
 
@@ -1000,15 +1029,34 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     const int n3 = 3 * L.n;
     if (n3 <= p.n_coarse || k == p.max_levels - 1 || k == 31) break;
     double t0 = now_s();
-    AMG_TRY(smoother_setup(h, L, k));
+    DBuf<double> om;
+    // on every way out of this level (errors included) the second stream has
+    // finished writing om before om is freed
+    struct AuxDone {
+      Handle *h;
+      ~AuxDone() {
+        if (h->aux) cudaStreamSynchronize(h->aux);
+      }
+    } aux_done{h};
+    AMG_TRY(smoother_start(h, L, k, om));
     double t1 = now_s();
     T_sm += t1 - t0;
     AMG_TRY(L.V.alloc((size_t)n3 * t));
     DBuf<int> st;
     AMG_TRY(st.alloc(1));
-    AMG_TRY(st.zero(s));
-    AMG_TRY(det::srqcg(L.A, L.G, L.GT, p.n_rq, p.k_ritz, t, Vin.p, L.V.p, st.p, s));
-    trace("SRQCG", k, t1);
+    double tw = 0.0;
+    for (int attempt = 0;; ++attempt) {
+      AMG_TRY(st.zero(s));
+      AMG_TRY(det::srqcg(L.A, L.G, L.GT, p.n_rq, p.k_ritz, t, Vin.p, L.V.p, st.p, s));
+      trace("SRQCG", k, t1);
+      if (attempt > 0) break;
+      // the test space used G as first built; a refined G needs a new one
+      bool refined = false;
+      const double tf = now_s();
+      AMG_TRY(smoother_finish(h, L, k, om, refined));
+      tw = now_s() - tf;
+      if (!refined) break;
+    }
     int hs = 0;
     AMG_CU(cudaMemcpy(&hs, st.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (hs) {
@@ -1016,7 +1064,8 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
       return hs;
     }
     double t2 = now_s();
-    T_ts += t2 - t1;
+    T_sm += tw;
+    T_ts += t2 - t1 - tw;
     AMG_TRY(d_strong.alloc(L.A.nnzb));
     AMG_TRY(det::soc_filter(L.A, t, L.V.p, p.theta, d_strong.p, s));
     std::vector<unsigned char> strong(L.A.nnzb);

@@ -670,6 +670,9 @@ Handle::~Handle() {
   // buffers are returned on the stream they were taken on: before it goes
   for (DBuf<double> *b : {&Linv, &LinvT, &x, &r, &z, &p, &q, &zold, &bvec, &scal, &red, &V0keep}) b->release();
   flags.release();
+  if (aux) cudaStreamDestroy(aux);
+  if (ev_main) cudaEventDestroy(ev_main);
+  if (ev_aux) cudaEventDestroy(ev_aux);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 

@@ -74,6 +74,26 @@ def test_hierarchy_bit_exact_structure(A, orc, name):
         assert rel(S.level_testspace(k), H.V(k)) <= 1e-12, k
 
 
+def test_refinement_passes_bit_exact(A, orc):
+    """An unreachable omega_bar forces the aFSAI refinement passes of
+    Algorithm 3: the test space first generated with the unrefined G (while
+    the omega estimate ran beside it) is generated again with the refined G,
+    and the hierarchy still equals the oracle's."""
+    name = list(SMALL)[0]
+    H, S, K, f, d = _both(A, orc, SMALL[name](), omega_bar=10.0)
+    assert S.nlev == H.nlev
+    assert H.info(0)["npasses"] > 0
+    for k in range(H.nlev - 1):
+        go, oo = S.level_info(k), H.info(k)
+        assert go["npasses"] == oo["npasses"], k
+        assert go["omega"] == oo["omega"] and go["lmax"] == oo["lmax"], k
+        assert np.array_equal(S.level_cf(k), H.cf(k)), k
+        Go = H.matrix(k, "G")
+        rp, col, val = S.level_matrix(k, "G")
+        assert np.array_equal(rp, Go.rowptr) and np.array_equal(col, Go.col[:Go.nnzb]), k
+        assert rel(S.level_testspace(k), H.V(k)) <= 1e-12, k
+
+
 @pytest.mark.parametrize("name", list(SMALL))
 def test_vcycle_matches_oracle(A, orc, name):
     import torch
