@@ -179,13 +179,10 @@ long long amg_launch_count(void);
  * the call would fail or fragment it), or one that keeps every allocation out of
  * its iteration loop.  Same arguments, result and precision as amg_vcycle;
  * y and z are device vectors of 3*nnodes entries owned by the caller.
- * Scratch: a file-scope device array of 16,640 bytes in the library (a flag
- * block and the coarse-level temporary), held by every GPU that loads the
- * library until the process exits.  Limit: the handle's last level may have
- * at most 2048 dofs (the default n_coarse = 1536 fits); larger ones are
- * rejected with AMG_ERR_ARG and a message in amg_last_error().  The first
- * call on a device looks up the array's device address (with that device
- * current), so make that first call before any stream capture.  All calls
+ * Scratch: a file-scope device array of 256 bytes in the library (a flag
+ * block), held by every GPU that loads the library until the process exits.
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture.  All calls
  * share the array and it keeps the last call's contents (the call clears what
  * must start at zero); calls that overlap on the GPU, on any handles, race on
  * it and must be serialised by the caller.  No device allocation or free

@@ -4,7 +4,7 @@ The solver is the adaptive algebraic multigrid of Franceschini et al.,
 "A robust adaptive algebraic multigrid linear solver for structural
 mechanics" (arXiv 1902.01715), with 3x3 nodal blocks: PCG preconditioned by
 one V(1,1)-cycle with the adaptive FSAI smoother, least-squares (DPLS)
-prolongation and a dense coarse Cholesky.  Every step runs in the CUDA
+prolongation and a dense coarse solve (explicit inverse).  Every step runs in the CUDA
 library ``libaspamg.so``; this module only marshals arguments (PyTorch CUDA
 tensors supply device memory and the current stream).  Importing the module
 does not need a GPU; using it without the compiled library raises.

@@ -215,9 +215,9 @@ struct Handle {
   int n = 0;  // fine nodes
   int nlev = 0;
   std::vector<std::unique_ptr<Level>> lev;
-  // last level: explicit inverse Cholesky factor (lower) and its transpose
+  // last level: explicit inverse of its matrix (dense, row-major, symmetric)
   int nL = 0;
-  DBuf<double> Linv, LinvT;
+  DBuf<double> Cinv;
   // PCG state (FP64), sized for kcap columns
   int kcap = 0;
   DBuf<double> x, r, z, p, q, zold, bvec, scal;

@@ -104,30 +104,18 @@ void bmv<float>(int ep, const SolveMat &M, bool b16, int k, const float *X, floa
   else bmm<float, float>(ep, M, M.v32.p, k, X, Y, AUX, w, done, s);
 }
 
-// coarse level: T = Linv Y, Z = LinvT T (interleaved n x k, FP64 arithmetic)
+// coarse level: Z = Cinv Y with the explicit inverse (interleaved n x k, FP64
+// arithmetic)
 template <typename TX>
-__global__ void k_btrmm_lower(int m, int k, const double *__restrict__ Li, const TX *__restrict__ Y,
-                              double *__restrict__ T, const int *__restrict__ done) {
+__global__ void k_bcoarse_mm(int m, int k, const double *__restrict__ Ci, const TX *__restrict__ Y,
+                             TX *__restrict__ Z, const int *__restrict__ done) {
   if (done && *done) return;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long)m * k) return;
   const int i = (int)(t / k), c = (int)(t % k);
   double s = 0.0;
-  const double *Lr = Li + (size_t)i * m;
-  for (int q = 0; q <= i; ++q) s += Lr[q] * (double)Y[(size_t)q * k + c];
-  T[t] = s;
-}
-
-template <typename TX>
-__global__ void k_btrmm_upper(int m, int k, const double *__restrict__ LiT, const double *__restrict__ T,
-                              TX *__restrict__ Z, const int *__restrict__ done) {
-  if (done && *done) return;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long)m * k) return;
-  const int i = (int)(t / k), c = (int)(t % k);
-  double s = 0.0;
-  const double *Lr = LiT + (size_t)i * m;
-  for (int q = i; q < m; ++q) s += Lr[q] * T[(size_t)q * k + c];
+  const double *Cr = Ci + (size_t)i * m;
+  for (int q = 0; q < m; ++q) s = fma(Cr[q], (double)Y[(size_t)q * k + c], s);
   Z[t] = (TX)s;
 }
 
@@ -140,7 +128,7 @@ struct BatchLevel {
 struct Batch {
   int k = 0, prec = -1;
   std::vector<BatchLevel> lev;
-  DBuf<double> x, r, z, p, q, zold, ctmp, sc, part;
+  DBuf<double> x, r, z, p, q, zold, sc, part;
   DBuf<int> flags;
   DBuf<float> rlow, zlow;
   cudaGraphExec_t graph = nullptr;
@@ -382,8 +370,7 @@ static void bvcycle(Handle *h, Batch &B, int lv, const TX *y, TX *z, const int *
   if (lv == h->nlev - 1) {
     const int m = h->nL;
     if (!m) return;
-    AMG_KCOUNT k_btrmm_lower<TX><<<nblk((long)m * k, 256), 256, 0, st>>>(m, k, h->Linv.p, y, B.ctmp.p, done);
-    AMG_KCOUNT k_btrmm_upper<TX><<<nblk((long)m * k, 256), 256, 0, st>>>(m, k, h->LinvT.p, B.ctmp.p, z, done);
+    AMG_KCOUNT k_bcoarse_mm<TX><<<nblk((long)m * k, 256), 256, 0, st>>>(m, k, h->Cinv.p, y, z, done);
     return;
   }
   Level &L = *h->lev[lv];
@@ -450,7 +437,6 @@ static int ensure_batch(Handle *h, Batch &B, int k) {
   AMG_TRY(B.sc.alloc((size_t)BS_NUM * k));
   AMG_TRY(B.part.alloc((size_t)BRED_BLOCKS * k + 16));
   AMG_TRY(B.flags.alloc(BF_COL + 2 * k + 8));
-  AMG_TRY(B.ctmp.alloc((size_t)(h->nL > 0 ? h->nL : 1) * k));
   if (!B.pinned) AMG_CU(cudaMallocHost((void **)&B.pinned, 4 * sizeof(int)));
   B.lev.clear();
   B.lev.resize(h->nlev);

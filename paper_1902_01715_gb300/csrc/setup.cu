@@ -133,107 +133,98 @@ __global__ void k_to_dense(int nr, const int *__restrict__ rp, const int *__rest
   }
 }
 
-// Blocked right-looking dense Cholesky (lower triangle, in place) and the
-// explicit inverse factor L^{-1}, in panels of CB columns spread over all SMs.
+// Explicit inverse of the last level's matrix by blocked Gauss-Jordan
+// elimination, in place in a dense row-major m x m array, pivot blocks of CB
+// columns.  No pivoting is needed: every pivot block is a Schur complement of
+// an SPD matrix, hence SPD.  Step k (block rows/columns [k0, k0+nb)):
+// P = A_kk^{-1}; R = P A_kj and C = A_ik (copies of the pivot row and column
+// panels); then A_ij -= C_i R_j for i, j outside the block, A_ik = -C_i P,
+// A_kj = R_j and A_kk = P.  The coarse solve is then one dense product with
+// the (symmetric) inverse.  Each step's update is m^2 CB independent
+// multiply-adds spread over all SMs; only the CB x CB pivot inversion is
+// serial.
 constexpr int CB = 32;
 
-// factor the diagonal block [j0, j0+nb) in shared memory (one CTA)
-__global__ void __launch_bounds__(CB *CB) k_potrf_diag(int m, int j0, int nb, double *__restrict__ D,
-                                                       int *__restrict__ status) {
+// P = A_kk^{-1} by scalar Gauss-Jordan in shared memory (one CTA, one
+// thread per entry); a pivot that is not positive sets status
+__global__ void __launch_bounds__(CB *CB) k_gj_pivot(int m, int k0, int nb, const double *__restrict__ D,
+                                                     double *__restrict__ P, int *__restrict__ status) {
   __shared__ double a[CB][CB + 1];
+  __shared__ double rinv;
   __shared__ int bad;
   const int r = threadIdx.x / CB, c = threadIdx.x % CB;
   if (threadIdx.x == 0) bad = 0;
-  if (r < nb && c <= r) a[r][c] = D[(size_t)(j0 + r) * m + j0 + c];
-  __syncthreads();
+  if (r < nb && c < nb) a[r][c] = D[(size_t)(k0 + r) * m + k0 + c];
   for (int j = 0; j < nb; ++j) {
+    __syncthreads();
     if (threadIdx.x == 0) {
-      const double sj = a[j][j];
-      if (!(sj > 0.0)) bad = 1;
-      a[j][j] = sqrt(sj);
+      const double pv = a[j][j];
+      if (!(pv > 0.0)) bad = 1;
+      rinv = 1.0 / pv;
     }
     __syncthreads();
     if (bad) break;
-    if (c == j && r > j && r < nb) a[r][j] /= a[j][j];
+    if (r == j && c < nb) a[j][c] = (c == j) ? rinv : a[j][c] * rinv;
     __syncthreads();
-    if (r < nb && c > j && c <= r) a[r][c] -= a[r][j] * a[c][j];
+    double f = 0.0, rowj = 0.0;
+    if (r < nb && c < nb && r != j) {
+      f = a[r][j];
+      rowj = a[j][c];
+    }
     __syncthreads();
+    if (r < nb && c < nb && r != j) a[r][c] = (c == j) ? -f * rinv : fma(-f, rowj, a[r][c]);
   }
+  __syncthreads();
   if (bad) {
     if (threadIdx.x == 0) atomicMin(status, AMG_ERR_NOT_SPD);
     return;
   }
-  if (r < nb && c <= r) D[(size_t)(j0 + r) * m + j0 + c] = a[r][c];
+  if (r < nb && c < nb) P[r * CB + c] = a[r][c];
 }
 
-// panel below the diagonal block: row i solves x L_jj^T = D[i][j0:j0+nb]
-__global__ void k_trsm_panel(int m, int j0, int nb, double *__restrict__ D) {
-  const int i = j0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  double x[CB];
-  double *row = D + (size_t)i * m + j0;
-  for (int t = 0; t < nb; ++t) {
-    double v = row[t];
-    const double *Lt = D + (size_t)(j0 + t) * m + j0;
-    for (int q = 0; q < t; ++q) v -= x[q] * Lt[q];
-    x[t] = v / Lt[t];
-  }
-  for (int t = 0; t < nb; ++t) row[t] = x[t];
+// R[q][j] = sum_p P[q][p] A[k0+p][j] (pivot row panel times P) and
+// C[i][q] = A[i][k0+q] (pivot column panel), for every i, j of the matrix
+__global__ void k_gj_panels(int m, int k0, int nb, const double *__restrict__ D, const double *__restrict__ P,
+                            double *__restrict__ R, double *__restrict__ C) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)CB * m) return;
+  const int q = (int)(t / m), j = (int)(t % m);
+  if (q >= nb) return;
+  double s = 0.0;
+  for (int p = 0; p < nb; ++p) s = fma(P[q * CB + p], D[(size_t)(k0 + p) * m + j], s);
+  R[(size_t)q * m + j] = s;
+  C[(size_t)j * CB + q] = D[(size_t)j * m + k0 + q];
 }
 
-// trailing update D[i][k] -= sum_t D[i][j0+t] D[k][j0+t], 16 x 16 tiles
-__global__ void __launch_bounds__(256) k_syrk_trail(int m, int j0, int nb, double *__restrict__ D) {
-  __shared__ double pi[16][CB + 1], pk[16][CB + 1];
-  const int t0 = j0 + nb;
-  const int bi = blockIdx.y, bk = blockIdx.x;
-  if (bk > bi) return;
-  const int ti = threadIdx.x / 16, tk = threadIdx.x % 16;
-  const int i0 = t0 + bi * 16, k0 = t0 + bk * 16;
-  for (int q = threadIdx.x; q < 16 * CB; q += 256) {
-    const int rr = q / CB, cc = q % CB;
-    pi[rr][cc] = (i0 + rr < m && cc < nb) ? D[(size_t)(i0 + rr) * m + j0 + cc] : 0.0;
-    pk[rr][cc] = (k0 + rr < m && cc < nb) ? D[(size_t)(k0 + rr) * m + j0 + cc] : 0.0;
+// every entry of the matrix for step k, 32 x 32 tiles, 256 threads (4 rows each)
+__global__ void __launch_bounds__(256) k_gj_update(int m, int k0, int nb, double *__restrict__ D,
+                                                   const double *__restrict__ P, const double *__restrict__ R,
+                                                   const double *__restrict__ C) {
+  __shared__ double ct[CB][CB + 1], rt[CB][CB + 1];
+  const int i0 = blockIdx.y * CB, j0 = blockIdx.x * CB;
+  const bool kr = i0 == k0, kc = j0 == k0;
+  const int tx = threadIdx.x % CB, ty = threadIdx.x / CB;  // column, first row
+  for (int e = threadIdx.x; e < CB * CB; e += 256) {
+    const int a = e / CB, b = e % CB;
+    // C rows of this tile; R columns of this tile (P for the pivot column)
+    ct[a][b] = (i0 + a < m && b < nb) ? C[(size_t)(i0 + a) * CB + b] : 0.0;
+    rt[a][b] = (a < nb && j0 + b < m) ? (kc ? (b < nb ? P[a * CB + b] : 0.0) : R[(size_t)a * m + j0 + b]) : 0.0;
   }
   __syncthreads();
-  const int i = i0 + ti, k = k0 + tk;
-  if (i >= m || k > i) return;
-  double s = 0.0;
-  for (int t = 0; t < nb; ++t) s += pi[ti][t] * pk[tk][t];
-  D[(size_t)i * m + k] -= s;
-}
-
-// X = L^{-1}, block row [r0, r0+nb): first X[i][j] = -sum_{r0 > k >= j} L[i][k] X[k][j]
-__global__ void k_trinv_gemm(int m, int r0, int nb, const double *__restrict__ L, double *__restrict__ X) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = r0 + blockIdx.y;
-  if (j >= r0 || blockIdx.y >= (unsigned)nb) return;
-  double s = 0.0;
-  const double *Li = L + (size_t)i * m;
-  for (int k = j; k < r0; ++k) s += Li[k] * X[(size_t)k * m + j];
-  X[(size_t)i * m + j] = -s;
-}
-
-// ... then each column j < r0+nb is finished by the diagonal block's forward
-// substitution (unit right-hand side on the block's own columns)
-__global__ void k_trinv_diag(int m, int r0, int nb, const double *__restrict__ L, double *__restrict__ X) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= r0 + nb) return;
-  double x[CB];
-  for (int t = 0; t < nb; ++t) {
-    const int i = r0 + t;
-    double v = (j < r0) ? X[(size_t)i * m + j] : (j == i ? 1.0 : 0.0);
-    const double *Li = L + (size_t)i * m + r0;
-    for (int q = 0; q < t; ++q) v -= Li[q] * x[q];
-    x[t] = v / Li[t];
+  const int j = j0 + tx;
+  if (j >= m) return;
+  for (int rr = ty; rr < CB; rr += 8) {
+    const int i = i0 + rr;
+    if (i >= m) break;
+    double *dij = D + (size_t)i * m + j;
+    if (kr) {
+      if (tx < CB) *dij = kc ? (tx < nb && rr < nb ? P[rr * CB + tx] : *dij) : R[(size_t)rr * m + j];
+      continue;
+    }
+    double s = 0.0;
+    for (int q = 0; q < nb; ++q) s = fma(ct[rr][q], rt[q][tx], s);
+    *dij = kc ? -s : *dij - s;
   }
-  for (int t = 0; t < nb; ++t) X[(size_t)(r0 + t) * m + j] = (j <= r0 + t) ? x[t] : 0.0;
-}
-
-__global__ void k_dense_transpose(int m, const double *__restrict__ A, double *__restrict__ T) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long)m * m) return;
-  const int i = (int)(t / m), j = (int)(t % m);
-  T[(size_t)j * m + i] = A[t];
 }
 
 // ---------------------------------------------------------------- host graph work
@@ -916,40 +907,32 @@ static int coarse_factor(Handle *h, Level &L) {
     return AMG_ERR_COARSENING;
   }
   h->nL = m;
-  DBuf<double> D;
+  DBuf<double> Pk, R, C;
   DBuf<int> st;
-  AMG_TRY(D.alloc((size_t)m * m));
-  AMG_TRY(D.zero(s));
   AMG_TRY(st.alloc(1));
   AMG_TRY(st.zero(s));
-  AMG_TRY(h->Linv.alloc((size_t)m * m));
-  AMG_TRY(h->LinvT.alloc((size_t)m * m));
-  AMG_TRY(h->Linv.zero(s));
+  AMG_TRY(h->Cinv.alloc((size_t)m * m));
+  AMG_TRY(h->Cinv.zero(s));
   if (L.n > 0) {
-    AMG_KCOUNT k_to_dense<<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D.p);
-    for (int j0 = 0; j0 < m; j0 += CB) {
-      const int nb = m - j0 < CB ? m - j0 : CB;
-      AMG_KCOUNT k_potrf_diag<<<1, CB * CB, 0, s>>>(m, j0, nb, D.p, st.p);
-      const int rest = m - j0 - nb;
-      if (rest > 0) {
-        AMG_KCOUNT k_trsm_panel<<<nblk(rest, 128), 128, 0, s>>>(m, j0, nb, D.p);
-        const int nt = (rest + 15) / 16;
-        AMG_KCOUNT k_syrk_trail<<<dim3(nt, nt), 256, 0, s>>>(m, j0, nb, D.p);
-      }
+    AMG_TRY(Pk.alloc(CB * CB));
+    AMG_TRY(R.alloc((size_t)CB * m));
+    AMG_TRY(C.alloc((size_t)m * CB));
+    double *D = h->Cinv.p;
+    AMG_KCOUNT k_to_dense<<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
+    const int nt = (m + CB - 1) / CB;
+    for (int k0 = 0; k0 < m; k0 += CB) {
+      const int nb = m - k0 < CB ? m - k0 : CB;
+      AMG_KCOUNT k_gj_pivot<<<1, CB * CB, 0, s>>>(m, k0, nb, D, Pk.p, st.p);
+      AMG_KCOUNT k_gj_panels<<<nblk((long)CB * m, 256), 256, 0, s>>>(m, k0, nb, D, Pk.p, R.p, C.p);
+      AMG_KCOUNT k_gj_update<<<dim3(nt, nt), 256, 0, s>>>(m, k0, nb, D, Pk.p, R.p, C.p);
     }
-    for (int r0 = 0; r0 < m; r0 += CB) {
-      const int nb = m - r0 < CB ? m - r0 : CB;
-      if (r0 > 0) AMG_KCOUNT k_trinv_gemm<<<dim3(nblk(r0, 128), nb), 128, 0, s>>>(m, r0, nb, D.p, h->Linv.p);
-      AMG_KCOUNT k_trinv_diag<<<nblk(r0 + nb, 128), 128, 0, s>>>(m, r0, nb, D.p, h->Linv.p);
-    }
-    AMG_KCOUNT k_dense_transpose<<<nblk((long)m * m, 256), 256, 0, s>>>(m, h->Linv.p, h->LinvT.p);
     AMG_LAUNCH_CHECK();
   }
   int hs = 0;
   AMG_CU(cudaMemcpyAsync(&hs, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   AMG_CU(cudaStreamSynchronize(s));
   if (hs) {
-    set_error("coarse-level Cholesky: non-positive pivot");
+    set_error("coarse-level inverse: non-positive pivot");
     return hs;
   }
   return AMG_OK;
@@ -958,8 +941,7 @@ static int coarse_factor(Handle *h, Level &L) {
 void free_hierarchy(Handle *h) {
   h->lev.clear();
   h->nlev = 0;
-  h->Linv.release();
-  h->LinvT.release();
+  h->Cinv.release();
   h->nL = 0;
 }
 
@@ -1119,7 +1101,7 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
   h->nlev = (int)h->lev.size();
   const double t6 = now_s();
   AMG_TRY(coarse_factor(h, *h->lev[h->nlev - 1]));
-  trace("coarse Cholesky", h->nlev - 1, t6);
+  trace("coarse inverse", h->nlev - 1, t6);
   const double t7 = now_s();
   AMG_TRY(prepare_solve(h));
   AMG_CU(cudaStreamSynchronize(s));

@@ -66,32 +66,18 @@ int prepare_solve(Handle *h) {
 }
 
 // ---------------------------------------------------------------- coarse solve
-// t = Linv y (lower triangular rows), z = LinvT t (upper triangular rows);
-// one warp per row, FP64.
+// z = Cinv y with the explicit inverse of the last level (symmetric, so row i
+// is also column i); one warp per row, FP64.
 template <typename TX>
-__global__ void k_trmv_lower(int m, const double *__restrict__ Li, const TX *__restrict__ y, double *__restrict__ t,
-                             const int *__restrict__ done) {
+__global__ void k_coarse_mv(int m, const double *__restrict__ Ci, const TX *__restrict__ y, TX *__restrict__ z,
+                            const int *__restrict__ done) {
   if (done && *done) return;
   const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
   double s = 0.0;
-  const double *Lr = Li + (size_t)row * m;
-  for (int k = lane; k <= row; k += 32) s += Lr[k] * (double)y[k];
-  for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) t[row] = s;
-}
-
-template <typename TX>
-__global__ void k_trmv_upper(int m, const double *__restrict__ LiT, const double *__restrict__ t, TX *__restrict__ z,
-                             const int *__restrict__ done) {
-  if (done && *done) return;
-  const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= m) return;
-  double s = 0.0;
-  const double *Lr = LiT + (size_t)row * m;
-  for (int k = row + lane; k < m; k += 32) s += Lr[k] * t[k];
+  const double *Cr = Ci + (size_t)row * m;
+  for (int k = lane; k < m; k += 32) s = fma(Cr[k], (double)y[k], s);
   for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (lane == 0) z[row] = (TX)s;
 }
@@ -135,15 +121,14 @@ void mv<double>(int ep, const SolveMat &M, bool, const double *x, double *y, con
 
 // z = B(y) on level k; y and z are the level's vectors (or the caller's at k=0)
 template <typename TX>
-static void vcycle_level(Handle *h, int k, const TX *y, TX *z, const int *done, double *ctmp) {
+static void vcycle_level(Handle *h, int k, const TX *y, TX *z, const int *done) {
   cudaStream_t st = h->stream;
   Level &L = *h->lev[k];
   const bool b16 = h->prm.vcycle_prec == AMG_FP32_BF16GP;
   if (k == h->nlev - 1) {
     const int m = h->nL;
     if (m == 0) return;
-    AMG_KCOUNT k_trmv_lower<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->Linv.p, y, ctmp, done);
-    AMG_KCOUNT k_trmv_upper<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->LinvT.p, ctmp, z, done);
+    AMG_KCOUNT k_coarse_mv<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->Cinv.p, y, z, done);
     return;
   }
   Level &C = *h->lev[k + 1];
@@ -153,7 +138,7 @@ static void vcycle_level(Handle *h, int k, const TX *y, TX *z, const int *done, 
   mv<TX>(EP_SCALE, L.sGT, b16, t, s, (const TX *)nullptr, w, done, st);    // s = w G^T t
   mv<TX>(EP_RESID, L.sA, false, s, r, y, w, done, st);                    // r = y - A s
   mv<TX>(EP_SET, L.sR, b16, r, Vec<TX>::y(C), (const TX *)nullptr, w, done, st);  // y_c = P^T r
-  vcycle_level<TX>(h, k + 1, Vec<TX>::y(C), Vec<TX>::z(C), done, ctmp);
+  vcycle_level<TX>(h, k + 1, Vec<TX>::y(C), Vec<TX>::z(C), done);
   mv<TX>(EP_ACC, L.sP, b16, Vec<TX>::z(C), s, (const TX *)nullptr, w, done, st);  // s += P z_c
   mv<TX>(EP_RESID, L.sA, false, s, r, y, w, done, st);                    // r = y - A s
   mv<TX>(EP_SET, L.sG, b16, r, t, (const TX *)nullptr, w, done, st);       // t = G r
@@ -360,7 +345,7 @@ static int ensure_pcg(Handle *h) {
   AMG_TRY(h->bvec.alloc(n3));
   AMG_TRY(h->scal.alloc(P_NSC + 8));
   AMG_TRY(h->flags.alloc(F_NFL + 4));
-  AMG_TRY(h->red.alloc(4 * RED_BLOCKS + 16 + 3 * (size_t)(h->nL > 0 ? h->nL : 1)));
+  AMG_TRY(h->red.alloc(4 * RED_BLOCKS + 16));
   if (!h->pinned) AMG_CU(cudaMallocHost((void **)&h->pinned, 4 * sizeof(int)));
   h->kcap = 1;
   return AMG_OK;
@@ -377,7 +362,7 @@ static void pcg_iteration(Handle *h, bool mixed) {
   cudaStream_t s = h->stream;
   Level &L0 = *h->lev[0];
   const long n = 3L * h->n;
-  double *part = h->red.p, *part2 = h->red.p + 2 * RED_BLOCKS, *ctmp = h->red.p + 4 * RED_BLOCKS + 16;
+  double *part = h->red.p, *part2 = h->red.p + 2 * RED_BLOCKS;
   int *fl = h->flags.p;
   double *sc = h->scal.p;
   const int *done = fl + F_DONE;
@@ -385,14 +370,14 @@ static void pcg_iteration(Handle *h, bool mixed) {
   AMG_KCOUNT k_pcg_pq<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->q.p, sc, fl, part);
   if (mixed) {
     AMG_KCOUNT k_pcg_xr<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, low_r<TX>(h), sc, fl, part);
-    vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), done, ctmp);
+    vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), done);
     AMG_KCOUNT k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, low_z<TX>(h), h->zold.p, 1, sc, fl, part,
                                                      part2);
     AMG_KCOUNT k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 1, sc, fl);
   } else {
     AMG_KCOUNT k_pcg_xr<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, (double *)nullptr, sc, fl,
                                                          part);
-    vcycle_level<double>(h, 0, h->r.p, h->z.p, done, ctmp);
+    vcycle_level<double>(h, 0, h->r.p, h->z.p, done);
     AMG_KCOUNT k_pcg_rz<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, (const double *)nullptr, h->zold.p, 0, sc,
                                                          fl, part, part2);
     AMG_KCOUNT k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 0, sc, fl);
@@ -403,16 +388,16 @@ template <typename TX>
 static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int *iters, double *relres, bool mixed) {
   cudaStream_t s = h->stream;
   const long n = 3L * h->n;
-  double *part = h->red.p, *ctmp = h->red.p + 4 * RED_BLOCKS + 16;
+  double *part = h->red.p;
   int *fl = h->flags.p;
   double *sc = h->scal.p;
   AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(fl, h->prm.maxit);
   AMG_KCOUNT k_pcg_start<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, b, h->x.p, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr, rtol,
                                                       sc, fl, part);
   if (mixed) {
-    vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), fl + F_DONE, ctmp);
+    vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), fl + F_DONE);
   } else {
-    vcycle_level<double>(h, 0, h->r.p, h->z.p, fl + F_DONE, ctmp);
+    vcycle_level<double>(h, 0, h->r.p, h->z.p, fl + F_DONE);
   }
   // rz = r.z (beta unused)
   AMG_KCOUNT k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
@@ -515,13 +500,12 @@ int vcycle_apply(Handle *h, const double *y, double *z) {
   AMG_TRY(ensure_pcg(h));
   cudaStream_t s = h->stream;
   const long n = 3L * h->n;
-  double *ctmp = h->red.p + 4 * RED_BLOCKS + 16;
   AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(h->flags.p, 1);
   if (h->prm.vcycle_prec == AMG_FP64) {
-    vcycle_level<double>(h, 0, y, z, h->flags.p + F_DONE, ctmp);
+    vcycle_level<double>(h, 0, y, z, h->flags.p + F_DONE);
   } else {
     AMG_KCOUNT k_d2f<<<nblk(n, 256), 256, 0, s>>>(n, y, low_r<float>(h));
-    vcycle_level<float>(h, 0, low_r<float>(h), low_z<float>(h), h->flags.p + F_DONE, ctmp);
+    vcycle_level<float>(h, 0, low_r<float>(h), low_z<float>(h), h->flags.p + F_DONE);
     AMG_KCOUNT k_f2d<<<nblk(n, 256), 256, 0, s>>>(n, low_z<float>(h), z);
   }
   AMG_LAUNCH_CHECK();
@@ -530,13 +514,11 @@ int vcycle_apply(Handle *h, const double *y, double *z) {
 }
 
 // ---------------------------------------------------------------- V-cycle without allocation
-// Scratch of amg_vcycle_noalloc: a state flag block (256 bytes) followed by
-// the coarse-level temporary of at most VC_STATIC_MAX_COARSE doubles.  It is a
-// file-scope device array, so every GPU that loads the library holds these
-// 16,640 bytes until the process exits, and every call shares them.
-constexpr int VC_STATIC_MAX_COARSE = 2048;
+// Scratch of amg_vcycle_noalloc: a state flag block of 256 bytes.  It is a
+// file-scope device array, so every GPU that loads the library holds it
+// until the process exits, and every call shares it.
 constexpr int VC_STATIC_FLAG_BYTES = 256;
-static __device__ __align__(256) unsigned char g_vc_scratch[VC_STATIC_FLAG_BYTES + VC_STATIC_MAX_COARSE * 8];
+static __device__ __align__(256) unsigned char g_vc_scratch[VC_STATIC_FLAG_BYTES];
 
 // Device address of g_vc_scratch for each device, looked up once per device
 // (with that device current) on the first call there.
@@ -565,24 +547,18 @@ static int vc_scratch_address(void **out) {
 }
 
 int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
-  if (h->nL > VC_STATIC_MAX_COARSE) {
-    set_error("amg_vcycle_noalloc: the last level has %d dofs; this entry point supports at most %d "
-              "(use amg_vcycle, or a smaller n_coarse)", h->nL, VC_STATIC_MAX_COARSE);
-    return AMG_ERR_ARG;
-  }
   void *base = nullptr;
   AMG_TRY(vc_scratch_address(&base));
   int *flags = (int *)base;
-  double *ctmp = (double *)((unsigned char *)base + VC_STATIC_FLAG_BYTES);
   cudaStream_t s = h->stream;
   const long n = 3L * h->n;
   // the flag block keeps the previous call's contents: reset it first
   AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(flags, 1);
   if (h->prm.vcycle_prec == AMG_FP64) {
-    vcycle_level<double>(h, 0, y, z, flags + F_DONE, ctmp);
+    vcycle_level<double>(h, 0, y, z, flags + F_DONE);
   } else {
     AMG_KCOUNT k_d2f<<<nblk(n, 256), 256, 0, s>>>(n, y, low_r<float>(h));
-    vcycle_level<float>(h, 0, low_r<float>(h), low_z<float>(h), flags + F_DONE, ctmp);
+    vcycle_level<float>(h, 0, low_r<float>(h), low_z<float>(h), flags + F_DONE);
     AMG_KCOUNT k_f2d<<<nblk(n, 256), 256, 0, s>>>(n, low_z<float>(h), z);
   }
   AMG_LAUNCH_CHECK();
@@ -668,7 +644,7 @@ Handle::~Handle() {
   if (pinned) cudaFreeHost(pinned);
   lev.clear();
   // buffers are returned on the stream they were taken on: before it goes
-  for (DBuf<double> *b : {&Linv, &LinvT, &x, &r, &z, &p, &q, &zold, &bvec, &scal, &red, &V0keep}) b->release();
+  for (DBuf<double> *b : {&Cinv, &x, &r, &z, &p, &q, &zold, &bvec, &scal, &red, &V0keep}) b->release();
   flags.release();
   if (aux) cudaStreamDestroy(aux);
   if (ev_main) cudaEventDestroy(ev_main);

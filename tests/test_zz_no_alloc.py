@@ -47,11 +47,26 @@ def test_noalloc_vcycle_matches_vcycle_twice(A, prec):
         assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
 
 
-def test_noalloc_rejects_large_coarse_level(A):
+def test_noalloc_large_coarse_level(A):
+    """A last level of 3,630 dofs (a 10^3 cube kept whole): the coarse solve is
+    one product with the level's explicit inverse and needs no scratch."""
     import torch
-    S, nf = _solver(A, W.cube16(10), n_coarse=4000)  # one level of 3,630 dofs > 2,048
-    y = torch.ones(3 * nf, dtype=torch.float64, device="cuda")
-    z = torch.empty_like(y)
-    rc = A.lib().amg_vcycle_noalloc(S._h, C.c_void_p(y.data_ptr()), C.c_void_p(z.data_ptr()))
-    assert rc == A.AMG_ERR_ARG
-    assert b"at most 2048" in A.lib().amg_last_error()
+    S, nf = _solver(A, W.cube16(10), n_coarse=4000)
+    assert S.nlev == 1
+    L = A.lib()
+    y = torch.tensor(np.random.default_rng(52).normal(size=3 * nf), device="cuda")
+    z_ref = torch.empty_like(y)
+    A.check(L.amg_vcycle(S._h, C.c_void_p(y.data_ptr()), C.c_void_p(z_ref.data_ptr())), "amg_vcycle")
+    z = torch.full_like(y, float("nan"))
+    A.check(L.amg_vcycle_noalloc(S._h, C.c_void_p(y.data_ptr()), C.c_void_p(z.data_ptr())),
+            "amg_vcycle_noalloc")
+    assert torch.equal(z, z_ref)
+    # one level: the V-cycle is the exact solve K z = y
+    rp, col, val = S.level_matrix(0, "A")
+    K = np.zeros((3 * nf, 3 * nf))
+    for I in range(nf):
+        for k in range(rp[I], rp[I + 1]):
+            J = col[k]
+            K[3 * I:3 * I + 3, 3 * J:3 * J + 3] = val[k].reshape(3, 3)
+    zn, yn = z.cpu().numpy(), y.cpu().numpy()
+    assert np.linalg.norm(K @ zn - yn) <= 1e-9 * np.linalg.norm(yn)
