@@ -34,14 +34,14 @@ static void node_gram(int n, int b, int t, const double *V, int I, int J,
     for (int c = 0; c < b; ++c) {
       double s = 0.0;
       for (int k = 0; k < t; ++k)
-        s = s + V[(size_t)k * n + (size_t)b * I + r] * V[(size_t)k * n + (size_t)b * J + c];
+        s = fma(V[(size_t)k * n + (size_t)b * I + r], V[(size_t)k * n + (size_t)b * J + c], s);
       M[r * b + c] = s;
     }
 }
 
 static double fro2(int b, const double *M) {
   double s = 0.0;
-  for (int i = 0; i < b * b; ++i) s = s + M[i] * M[i];
+  for (int i = 0; i < b * b; ++i) s = fma(M[i], M[i], s);
   return s;
 }
 

@@ -234,7 +234,9 @@ static int sturm_count(int m, const double *al, const double *be, double x) {
 
 /* Largest eigenvalue of G A G^T estimated by m Lanczos steps with full
  * re-orthogonalisation (one classical Gram-Schmidt pass against all previous
- * vectors; the paper says only "a few Lanczos passes"),
+ * vectors; the paper says only "a few Lanczos passes"; every multiply-add of
+ * the vector updates is one fused multiply-add and the normalisations multiply
+ * by the reciprocal of the norm),
  * from the start vector of level `level` of the counter generator; the
  * largest Ritz value is found by bisection on Sturm counts. */
 double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
@@ -250,7 +252,10 @@ double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
   for (int i = 0; i < n; ++i)
     Vs[i] = or_uniform_pm1(seed, (1ull << 62) | ((uint64_t)level << 40) | (uint64_t)i);
   double nr = sqrt(or_dot(n, Vs, Vs));
-  for (int i = 0; i < n; ++i) Vs[i] = Vs[i] / nr;
+  {
+    const double rn = 1.0 / nr;
+    for (int i = 0; i < n; ++i) Vs[i] = Vs[i] * rn;
+  }
   int mm = m;
   for (int j = 0; j < m; ++j) {
     double *v = Vs + (size_t)j * n;
@@ -258,17 +263,17 @@ double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
     or_spmv(A, t1, t2);
     or_spmv(G, t2, w);
     al[j] = or_dot(n, w, v);
-    for (int i = 0; i < n; ++i) w[i] = w[i] - al[j] * v[i];
+    for (int i = 0; i < n; ++i) w[i] = fma(-al[j], v[i], w[i]);
     if (j > 0) {
       const double *vp = Vs + (size_t)(j - 1) * n;
-      for (int i = 0; i < n; ++i) w[i] = w[i] - be[j - 1] * vp[i];
+      for (int i = 0; i < n; ++i) w[i] = fma(-be[j - 1], vp[i], w[i]);
     }
     /* one classical Gram-Schmidt pass against v_0..v_j: all coefficients
      * from the same w, then w_i - sum_k h_k v_k,i with k ascending */
     for (int k = 0; k <= j; ++k) hk[k] = or_dot(n, w, Vs + (size_t)k * n);
     for (int i = 0; i < n; ++i) {
       double s = w[i];
-      for (int k = 0; k <= j; ++k) s = s - hk[k] * Vs[(size_t)k * n + i];
+      for (int k = 0; k <= j; ++k) s = fma(-hk[k], Vs[(size_t)k * n + i], s);
       w[i] = s;
     }
     be[j] = sqrt(or_dot(n, w, w));
@@ -278,7 +283,8 @@ double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
       break;
     }
     double *vn = Vs + (size_t)(j + 1) * n;
-    for (int i = 0; i < n; ++i) vn[i] = w[i] / be[j];
+    const double rb = 1.0 / be[j];
+    for (int i = 0; i < n; ++i) vn[i] = w[i] * rb;
   }
   double lo = al[0], hi = al[0];
   for (int i = 0; i < mm; ++i) {

@@ -24,8 +24,10 @@
  * per column and iteration is S g.
  *
  * All inner products use the fixed-order or_dot, all sparse products the
- * fixed-order or_spmv; vector updates are single rounded operations per
- * entry.
+ * fixed-order or_spmv; every multiply-add of a vector update (and of the
+ * dense triangular solves and rotations) is one fused multiply-add, and a
+ * vector divided by a shared scalar is multiplied by its reciprocal (one
+ * division per vector: on the GPU a division costs about ten products).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -41,18 +43,21 @@ static void apply_s(const obsr *A, const obsr *G, const obsr *GT,
 }
 
 /* Modified Gram-Schmidt on the columns of the n x t column-major V, in column
- * order; each column is divided by its norm. */
+ * order (v_j <- v_j - (v_i . v_j) v_i for i < j, one fused multiply-add per
+ * entry); each column is then multiplied by the reciprocal of its norm. */
 void or_mgs(int n, int t, double *V) {
   for (int j = 0; j < t; ++j) {
     double *vj = V + (size_t)j * n;
     for (int i = 0; i < j; ++i) {
       const double *vi = V + (size_t)i * n;
       const double r = or_dot(n, vi, vj);
-      for (int k = 0; k < n; ++k) vj[k] = vj[k] - r * vi[k];
+      for (int k = 0; k < n; ++k) vj[k] = fma(-r, vi[k], vj[k]);
     }
     const double nr = sqrt(or_dot(n, vj, vj));
-    if (nr > 0.0)
-      for (int k = 0; k < n; ++k) vj[k] = vj[k] / nr;
+    if (nr > 0.0) {
+      const double rn = 1.0 / nr;
+      for (int k = 0; k < n; ++k) vj[k] = vj[k] * rn;
+    }
   }
 }
 
@@ -84,13 +89,13 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
   for (int j = 0; j < t; ++j)
     for (int i = 0; i < t; ++i) {
       double s = H[i * t + j];
-      for (int k = 0; k < i; ++k) s = s - L[i * t + k] * W1[k * t + j];
+      for (int k = 0; k < i; ++k) s = fma(-L[i * t + k], W1[k * t + j], s);
       W1[i * t + j] = s * (1.0 / L[i * t + i]);
     }
   for (int j = 0; j < t; ++j)
     for (int i = 0; i < t; ++i) {
       double s = W1[j * t + i];
-      for (int k = 0; k < i; ++k) s = s - L[i * t + k] * C[k * t + j];
+      for (int k = 0; k < i; ++k) s = fma(-L[i * t + k], C[k * t + j], s);
       C[i * t + j] = s * (1.0 / L[i * t + i]);
     }
   for (int i = 0; i < t; ++i)
@@ -104,8 +109,8 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
   for (int sweep = 0; sweep < 100; ++sweep) {
     double off = 0.0, dg = 0.0;
     for (int p = 0; p < t; ++p) {
-      dg = dg + C[p * t + p] * C[p * t + p];
-      for (int q = p + 1; q < t; ++q) off = off + C[p * t + q] * C[p * t + q];
+      dg = fma(C[p * t + p], C[p * t + p], dg);
+      for (int q = p + 1; q < t; ++q) off = fma(C[p * t + q], C[p * t + q], off);
     }
     if (!(off > 1e-32 * dg)) break;
     const int T = t + (t & 1);
@@ -120,13 +125,18 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
         if (q >= t) continue;
         const double apq = C[p * t + q];
         if (apq == 0.0) continue;
-        const double th = (C[q * t + q] - C[p * t + p]) / (2.0 * apq);
-        const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = 1.0 / sqrt(tt * tt + 1.0);
+        /* tangent tt = sgn(d) a2 / (|d| + R), R = sqrt(d^2 + a2^2), the smaller
+         * root of tt^2 + 2 (d / a2) tt - 1 = 0; c = 1 / sqrt(1 + tt^2) =
+         * u / w and s = tt c = sgn(d) a2 / w with u = |d| + R and
+         * w = sqrt(u^2 + a2^2): two square roots and one division */
+        const double d = C[q * t + q] - C[p * t + p], a2 = 2.0 * apq;
+        const double R = sqrt(fma(a2, a2, d * d));
+        const double u = fabs(d) + R;
+        const double iw = 1.0 / sqrt(fma(a2, a2, u * u));
         rp[np] = p;
         rq[np] = q;
-        rc_[np] = c;
-        rs_[np] = tt * c;
+        rc_[np] = u * iw;
+        rs_[np] = (d >= 0.0 ? a2 : -a2) * iw;
         ++np;
       }
       for (int u = 0; u < np; ++u) {
@@ -134,8 +144,8 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
         const double c = rc_[u], s = rs_[u];
         for (int k = 0; k < t; ++k) {
           const double xp = C[k * t + p], xq = C[k * t + q];
-          C[k * t + p] = c * xp - s * xq;
-          C[k * t + q] = s * xp + c * xq;
+          C[k * t + p] = fma(c, xp, -(s * xq));
+          C[k * t + q] = fma(s, xp, c * xq);
         }
       }
       for (int u = 0; u < np; ++u) {
@@ -143,8 +153,8 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
         const double c = rc_[u], s = rs_[u];
         for (int k = 0; k < t; ++k) {
           const double xp = C[p * t + k], xq = C[q * t + k];
-          C[p * t + k] = c * xp - s * xq;
-          C[q * t + k] = s * xp + c * xq;
+          C[p * t + k] = fma(c, xp, -(s * xq));
+          C[q * t + k] = fma(s, xp, c * xq);
         }
       }
       for (int u = 0; u < np; ++u) {
@@ -152,8 +162,8 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
         const double c = rc_[u], s = rs_[u];
         for (int k = 0; k < t; ++k) {
           const double xp = Wv[k * t + p], xq = Wv[k * t + q];
-          Wv[k * t + p] = c * xp - s * xq;
-          Wv[k * t + q] = s * xp + c * xq;
+          Wv[k * t + p] = fma(c, xp, -(s * xq));
+          Wv[k * t + q] = fma(s, xp, c * xq);
         }
       }
       for (int u = 0; u < np; ++u) {
@@ -177,7 +187,7 @@ int or_gen_eig(int t, const double *H, const double *M, double *U,
     lam[jj] = C[j * t + j];
     for (int i = t - 1; i >= 0; --i) {
       double s = Wv[i * t + j];
-      for (int k = t - 1; k > i; --k) s = s - L[k * t + i] * tmp[k];
+      for (int k = t - 1; k > i; --k) s = fma(-L[k * t + i], tmp[k], s);
       tmp[i] = s * (1.0 / L[i * t + i]);
     }
     int im = 0;
@@ -243,7 +253,7 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
     double *sz = SZ + (size_t)i * n, *sp = SP + (size_t)i * n;
     apply_s(A, G, GT, z, sz, t1, t2);
     const double q = or_dot(n, z, sz);
-    for (int k = 0; k < n; ++k) p[k] = 2.0 * (sz[k] - q * z[k]);
+    for (int k = 0; k < n; ++k) p[k] = 2.0 * fma(-q, z[k], sz[k]);
     apply_s(A, G, GT, p, sp, t1, t2);
     f[i] = 1.0;
   }
@@ -268,7 +278,7 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
           double row[64];
           for (int j = 0; j < t; ++j) {
             double s = 0.0;
-            for (int i = 0; i < t; ++i) s = s + X[(size_t)i * n + k] * U[i * t + j];
+            for (int i = 0; i < t; ++i) s = fma(X[(size_t)i * n + k], U[i * t + j], s);
             row[j] = s;
           }
           for (int j = 0; j < t; ++j) X[(size_t)j * n + k] = row[j];
@@ -284,17 +294,18 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
       if (!(b > 0.0)) continue;
       const double alpha = or_rq_line_min(a, b, c, d, e, fi);
       for (int k = 0; k < n; ++k) {
-        z[k] = z[k] + alpha * p[k];
-        sz[k] = sz[k] + alpha * sp[k];
+        z[k] = fma(alpha, p[k], z[k]);
+        sz[k] = fma(alpha, sp[k], sz[k]);
       }
       const double fn = or_dot(n, z, z);
       const double q = or_dot(n, z, sz) / fn;
-      for (int k = 0; k < n; ++k) Gv[k] = (2.0 * (sz[k] - q * z[k])) / fn;
+      const double rf = 1.0 / fn;
+      for (int k = 0; k < n; ++k) Gv[k] = (2.0 * fma(-q, z[k], sz[k])) * rf;
       apply_s(A, G, GT, Gv, SG, t1, t2);
       const double beta = -(or_dot(n, Gv, sp) / b);
       for (int k = 0; k < n; ++k) {
-        p[k] = Gv[k] + beta * p[k];
-        sp[k] = SG[k] + beta * sp[k];
+        p[k] = fma(beta, p[k], Gv[k]);
+        sp[k] = fma(beta, sp[k], SG[k]);
       }
       f[i] = fn;
     }

@@ -176,6 +176,26 @@ __device__ __forceinline__ bool last_warp(unsigned *ticket, unsigned total, int 
   return t == total - 1;
 }
 
+// Second half of a dot launch for warp w (nchunks > 0): store this warp's
+// chunk sum sc, and in the warp completing pair d add the pair's chunk sums
+// in order and put the total; returns true in the warp completing the last
+// pair.
+template <class Put>
+__device__ __forceinline__ bool dot_finish(long w, int nd, int nchunks, double *part, unsigned *ticket, int lane,
+                                           double sc, Put put) {
+  const int d = (int)(w / nchunks), c = (int)(w - (long)d * nchunks);
+  if (lane == 0) part[(size_t)d * nchunks + c] = sc;
+  if (!last_warp(ticket + d, (unsigned)nchunks, lane)) return false;
+  const double tot = sum_chunks(part + (size_t)d * nchunks, nchunks, lane);
+  if (lane == 0) {
+    put(d, tot);
+    ticket[d] = 0u;
+  }
+  if (!last_warp(ticket + nd, (unsigned)nd, lane)) return false;
+  if (lane == 0) ticket[nd] = 0u;
+  return true;
+}
+
 // The work of warp w in a dot launch over nd pairs (x_d, y_d given by xy);
 // the finished sum of pair d goes to put(d, value) from lane 0.  Returns true
 // in the one warp that completed the last pair (every put is then visible
@@ -193,17 +213,7 @@ __device__ __forceinline__ bool dot_warp(long w, int n, int nd, int nchunks, dou
   const double *x, *y;
   xy(d, x, y);
   const int base = c * CHUNK, end = min(base + CHUNK, n);
-  const double sc = chunk_sum(x, y, base, end, lane);
-  if (lane == 0) part[(size_t)d * nchunks + c] = sc;
-  if (!last_warp(ticket + d, (unsigned)nchunks, lane)) return false;
-  const double tot = sum_chunks(part + (size_t)d * nchunks, nchunks, lane);
-  if (lane == 0) {
-    put(d, tot);
-    ticket[d] = 0u;
-  }
-  if (!last_warp(ticket + nd, (unsigned)nd, lane)) return false;
-  if (lane == 0) ticket[nd] = 0u;
-  return true;
+  return dot_finish(w, nd, nchunks, part, ticket, lane, chunk_sum(x, y, base, end, lane), put);
 }
 
 // scalar steps of Algorithm 4 and of the Lanczos recurrence
@@ -224,6 +234,7 @@ __device__ void run_fin(const Fin &f, const double *v) {
   } else if (f.op == FIN_LZ_BETA) {  // v = w.w ; beta_j and the breakdown test
     const double b = sqrt(v[0]);
     sc[64 + f.j] = b;
+    sc[256 + f.j] = 1.0 / b;
     if (sc[128] < 0.0 && f.j < f.m - 1 && !(b > 1e-12 * fabs(sc[f.j]))) sc[128] = (double)(f.j + 1);
   }
 }
@@ -323,26 +334,21 @@ __global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restr
 }
 
 // ---------------------------------------------------------------- vector ops
-// y = y - (*a) * x
-__global__ void k_axmy(long n, double *__restrict__ y, const double *__restrict__ a,
-                       const double *__restrict__ x, const int *__restrict__ skip) {
-  if (skip && *skip) return;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = y[i] - (*a) * x[i];
-}
 
-// v = v / sqrt(*nn) when *nn > 0 (normalisation by a squared norm)
+// v = v (1 / sqrt(*nn)) when *nn > 0 (normalisation by a squared norm)
 __global__ void k_div_sqrt(long n, double *__restrict__ v, const double *__restrict__ nn) {
   const double nr = sqrt(*nn);
   if (!(nr > 0.0)) return;
+  const double rn = 1.0 / nr;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = v[i] / nr;
+  if (i < n) v[i] = v[i] * rn;
 }
 
-// out = in / (*d)
-__global__ void k_div(long n, double *__restrict__ out, const double *__restrict__ in, const double *__restrict__ d) {
+// out = in * (*rd), rd a reciprocal formed once
+__global__ void k_mul_by(long n, double *__restrict__ out, const double *__restrict__ in,
+                         const double *__restrict__ rd) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = in[i] / (*d);
+  if (i < n) out[i] = in[i] * (*rd);
 }
 
 __global__ void k_uniform(long n, int col0, int ncols, uint64_t seed, double *__restrict__ V, int ld) {
@@ -378,26 +384,66 @@ int gather_rows(const int *src_idx, int nout, int nin, int t, const double *Vin,
 
 // Modified Gram-Schmidt on the columns of V (n x t), column order; each column
 // divided by its norm when that is positive.
+// Step (j, i) of modified Gram-Schmidt, fused with the vector work the
+// previous step left pending, chunk by chunk (warp c owns chunk c, lane l its
+// entries base+l, base+l+32, ..., the dot order): for i = 0 and j > 0 column
+// j-1 is divided by sqrt(sc[t]) (its norm square); for i > 0,
+// v_j -= sc[i-1] v_{i-1}; then the chunk's part of v_i . v_j (i < j, into
+// sc[i]) or v_j . v_j (i = j, into sc[t]), from the values this lane has
+// just formed, in the two-level dot order.  Each entry receives the same
+// rounded operations, in the same order, as the column-by-column definition.
+__global__ void __launch_bounds__(32) k_mgs_step(int n, int t, int nchunks, double *__restrict__ V, int j, int i,
+                                                 double *__restrict__ sc, double *__restrict__ part,
+                                                 unsigned *ticket) {
+  const long w = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  double *vj = V + (size_t)j * n;
+  if (nchunks == 0) {
+    if (lane == 0) sc[i < j ? i : t] = 0.0;
+    return;
+  }
+  const int base = (int)w * CHUNK, end = min(base + CHUNK, n);
+  const bool norm_prev = i == 0 && j > 0;
+  double *vp = V + (size_t)(j > 0 ? j - 1 : 0) * n;
+  const double nr = norm_prev ? sqrt(sc[t]) : 1.0, rn = 1.0 / nr;
+  const double r = i > 0 ? sc[i - 1] : 0.0;
+  const double *vu = V + (size_t)(i > 0 ? i - 1 : 0) * n;  // v_{i-1}
+  const double *vi = V + (size_t)i * n;
+  double s = 0.0;
+  for (int k = base + lane; k < end; k += 32) {
+    double xp = 0.0;
+    if (norm_prev) {
+      xp = vp[k];
+      if (nr > 0.0) {
+        xp = xp * rn;
+        vp[k] = xp;
+      }
+    }
+    double y = vj[k];
+    if (i > 0) {
+      y = fma(-r, vu[k], y);
+      vj[k] = y;
+    }
+    const double x = i == j ? y : (norm_prev && i == j - 1) ? xp : vi[k];
+    s = fma(x, y, s);
+  }
+  s = exchange32(s);
+  dot_finish(w, 1, nchunks, part, ticket, lane, s, [&](int, double v) { sc[i < j ? i : t] = v; });
+}
+
 int mgs(int n, int t, double *V, cudaStream_t s) {
   DBuf<double> sc, part;
   DBuf<unsigned> tk;
-  AMG_TRY(sc.alloc(4));
-  AMG_TRY(part.alloc((size_t)((n + CHUNK - 1) / CHUNK) + 1));
+  AMG_TRY(sc.alloc(t + 1));
+  const int nchunks = (n + CHUNK - 1) / CHUNK;
+  AMG_TRY(part.alloc((size_t)nchunks + 1));
   AMG_TRY(tk.alloc(MAXTICKETS));
   AMG_TRY(tk.zero(s));
-  const DotCtx ctx{part.p, tk.p};
-  for (int j = 0; j < t; ++j) {
-    double *vj = V + (size_t)j * n;
-    for (int i = 0; i < j; ++i) {
-      const double *vi = V + (size_t)i * n;
-      AMG_TRY(dot1(n, vi, vj, sc.p, ctx, s));
-      AMG_KCOUNT k_axmy<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p, vi, nullptr);
-      AMG_LAUNCH_CHECK();
-    }
-    AMG_TRY(dot1(n, vj, vj, sc.p, ctx, s));
-    AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, vj, sc.p);
-    AMG_LAUNCH_CHECK();
-  }
+  for (int j = 0; j < t; ++j)
+    for (int i = 0; i <= j; ++i)
+      AMG_KCOUNT k_mgs_step<<<nchunks > 0 ? nchunks : 1, 32, 0, s>>>(n, t, nchunks, V, j, i, sc.p, part.p, tk.p);
+  if (t > 0 && n > 0) AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, V + (size_t)(t - 1) * n, sc.p + t);
+  AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
 }
@@ -1009,7 +1055,7 @@ __device__ double line_min(double a, double b, double c, double d, double e, dou
 // independently of one another, so column j of every n x t block is handled by
 // the same per-entry arithmetic as one column at a time.  Per-column scalars
 // live in cs[] (layout below) and the skip flags in skip[].
-enum { C_ALPHA = 0, C_Q = 1, C_FN = 2, C_BETA = 3, C_B = 4, C_F = 5, C_NUM = 6 };
+enum { C_ALPHA = 0, C_Q = 1, C_FN = 2, C_BETA = 3, C_B = 4, C_F = 5, C_RF = 6, C_NUM = 7 };
 
 __global__ void k_b_z0(long nt, double *__restrict__ z, const double *__restrict__ v, const double *__restrict__ sv) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1022,7 +1068,7 @@ __global__ void k_b_p0(long n, int t, double *__restrict__ p, const double *__re
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * t) return;
   const int j = (int)(i / n);
-  p[i] = 2.0 * (sz[i] - q[j] * z[i]);
+  p[i] = 2.0 * fma(-q[j], z[i], sz[i]);
 }
 
 // z += alpha p and, by linearity, S z += alpha S p
@@ -1034,8 +1080,8 @@ __global__ void k_b_zupd(long n, int t, double *__restrict__ z, const double *__
   const int j = (int)(i / n);
   if (skip[j]) return;
   const double al = cs[C_ALPHA * t + j];
-  z[i] = z[i] + al * p[i];
-  sz[i] = sz[i] + al * sp[i];
+  z[i] = fma(al, p[i], z[i]);
+  sz[i] = fma(al, sp[i], sz[i]);
 }
 
 __global__ void k_b_grad(long n, int t, double *__restrict__ g, const double *__restrict__ sz,
@@ -1044,7 +1090,7 @@ __global__ void k_b_grad(long n, int t, double *__restrict__ g, const double *__
   if (i >= n * t) return;
   const int j = (int)(i / n);
   if (skip[j]) return;
-  g[i] = (2.0 * (sz[i] - cs[C_Q * t + j] * z[i])) / cs[C_FN * t + j];
+  g[i] = (2.0 * fma(-cs[C_Q * t + j], z[i], sz[i])) * cs[C_RF * t + j];
 }
 
 // p = g + beta p and, by linearity, S p = S g + beta S p
@@ -1056,8 +1102,8 @@ __global__ void k_b_pupd(long n, int t, double *__restrict__ p, const double *__
   const int j = (int)(i / n);
   if (skip[j]) return;
   const double be = cs[C_BETA * t + j];
-  p[i] = g[i] + be * p[i];
-  sp[i] = sg[i] + be * sp[i];
+  p[i] = fma(be, p[i], g[i]);
+  sp[i] = fma(be, sp[i], sg[i]);
   if (i - (long)j * n == 0) cs[C_F * t + j] = cs[C_FN * t + j];
 }
 
@@ -1108,6 +1154,7 @@ __global__ void __launch_bounds__(32) k_cdots(int n, int t, int nk, CDot a, doub
     } else if (fin == CF_Q) {  // out = f_new, z.Sz
       cs[C_FN * t + j] = o(j);
       cs[C_Q * t + j] = o(t + j) / o(j);
+      cs[C_RF * t + j] = 1.0 / o(j);
     } else if (fin == CF_BETA) {  // out = g.Sp
       cs[C_BETA * t + j] = -(o(j) / cs[C_B * t + j]);
     }
@@ -1141,7 +1188,7 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z0, double *__restr
   double row[TMAXD];
   for (int j = 0; j < t; ++j) {
     double s = 0.0;
-    for (int i = 0; i < t; ++i) s = s + Z[(size_t)i * n + k] * U[i * t + j];
+    for (int i = 0; i < t; ++i) s = fma(Z[(size_t)i * n + k], U[i * t + j], s);
     row[j] = s;
   }
   for (int j = 0; j < t; ++j) Z[(size_t)j * n + k] = row[j];
@@ -1182,14 +1229,14 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
   for (int j = lane; j < t; j += 32)
     for (int i = 0; i < t; ++i) {
       double sv = H[i * t + j];
-      for (int k = 0; k < i; ++k) sv = sv - L[i * t + k] * W1[k * t + j];
+      for (int k = 0; k < i; ++k) sv = fma(-L[i * t + k], W1[k * t + j], sv);
       W1[i * t + j] = sv * Ri[i];
     }
   __syncwarp();
   for (int j = lane; j < t; j += 32)
     for (int i = 0; i < t; ++i) {
       double sv = W1[j * t + i];
-      for (int k = 0; k < i; ++k) sv = sv - L[i * t + k] * C[k * t + j];
+      for (int k = 0; k < i; ++k) sv = fma(-L[i * t + k], C[k * t + j], sv);
       C[i * t + j] = sv * Ri[i];
     }
   __syncwarp();
@@ -1206,8 +1253,8 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
   for (int sweep = 0; sweep < 100; ++sweep) {
     double off = 0.0, dg = 0.0;
     for (int p = 0; p < t; ++p) {
-      dg = dg + C[p * t + p] * C[p * t + p];
-      for (int q = p + 1; q < t; ++q) off = off + C[p * t + q] * C[p * t + q];
+      dg = fma(C[p * t + p], C[p * t + p], dg);
+      for (int q = p + 1; q < t; ++q) off = fma(C[p * t + q], C[p * t + q], off);
     }
     if (!(off > 1e-32 * dg)) break;
     // one sweep in round-robin order: lane i < T/2 owns pair i of the round
@@ -1226,10 +1273,13 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
         if (q < t) {
           const double apq = C[p * t + q];
           if (apq != 0.0) {
-            const double th = (C[q * t + q] - C[p * t + p]) / (2.0 * apq);
-            const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            c = 1.0 / sqrt(tt * tt + 1.0);
-            sn = tt * c;
+            // tangent sgn(d) a2 / (|d| + R): c = u / w, s = sgn(d) a2 / w
+            const double d = C[q * t + q] - C[p * t + p], a2 = 2.0 * apq;
+            const double R = sqrt(fma(a2, a2, d * d));
+            const double u = fabs(d) + R;
+            const double iw = 1.0 / sqrt(fma(a2, a2, u * u));
+            c = u * iw;
+            sn = (d >= 0.0 ? a2 : -a2) * iw;
             act = 1;
           }
         }
@@ -1248,8 +1298,8 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
             const int ip = phase == 1 ? pi * t + k : k * t + pi;
             const int iq = phase == 1 ? qi * t + k : k * t + qi;
             const double xp = X[ip], xq = X[iq];
-            X[ip] = ci * xp - si * xq;
-            X[iq] = si * xp + ci * xq;
+            X[ip] = fma(ci, xp, -(si * xq));
+            X[iq] = fma(si, xp, ci * xq);
           }
         }
         __syncwarp();
@@ -1277,7 +1327,7 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
     lam[jj] = C[j * t + j];
     for (int i = t - 1; i >= 0; --i) {
       double sv = Wv[i * t + j];
-      for (int k = t - 1; k > i; --k) sv = sv - L[k * t + i] * col[k];
+      for (int k = t - 1; k > i; --k) sv = fma(-L[k * t + i], col[k], sv);
       col[i] = sv * Ri[i];
     }
     int im = 0;
@@ -1461,8 +1511,8 @@ __global__ void k_lz_ab(long n, double *__restrict__ w, const double *__restrict
                         const double *__restrict__ sc, int j) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double x = w[i] - sc[j] * v[i];
-  if (vp) x = x - sc[64 + j - 1] * vp[i];
+  double x = fma(-sc[j], v[i], w[i]);
+  if (vp) x = fma(-sc[64 + j - 1], vp[i], x);
   w[i] = x;
 }
 
@@ -1472,7 +1522,7 @@ __global__ void k_lz_reorth(long n, int j, double *__restrict__ w, const double 
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = w[i];
-  for (int k = 0; k <= j; ++k) x = x - h[k] * Vs[(size_t)k * n + i];
+  for (int k = 0; k <= j; ++k) x = fma(-h[k], Vs[(size_t)k * n + i], x);
   w[i] = x;
 }
 
@@ -1480,7 +1530,7 @@ __global__ void k_lz_reorth(long n, int j, double *__restrict__ w, const double 
 // re-orthogonalisation (one classical Gram-Schmidt pass per step), from the
 // counter-generator start vector of this level; bisection on Sturm counts.
 // sc layout: [0..63] alpha, [64..127] beta, [128] breakdown step, [129] norm
-// square, [160..223] re-orthogonalisation coefficients.
+// square, [160..223] re-orthogonalisation coefficients, [256..319] 1 / beta.
 int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t seed, int level,
             double safety, double *d_out, cudaStream_t s, bool sync) {
   const int n = 3 * A.nr;
@@ -1494,7 +1544,7 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
   AMG_TRY(w.alloc(n));
   AMG_TRY(t1.alloc(n));
   AMG_TRY(t2.alloc(n));
-  AMG_TRY(sc.alloc(256));
+  AMG_TRY(sc.alloc(320));
   AMG_TRY(part.alloc((size_t)((n + CHUNK - 1) / CHUNK + 1) * 66));
   AMG_TRY(sc.zero(s));
   AMG_KCOUNT k_set_neg<<<1, 1, 0, s>>>(sc.p + 128);
@@ -1523,7 +1573,7 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
     fb.j = j;
     fb.m = m;
     AMG_TRY(dot1(n, w.p, w.p, sc.p + 129, ctx, s, fb));
-    if (j < m - 1) AMG_KCOUNT k_div<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 64 + j);
+    if (j < m - 1) AMG_KCOUNT k_mul_by<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 256 + j);
     AMG_LAUNCH_CHECK();
   }
   AMG_KCOUNT k_lanczos_bisect<<<1, 32, 0, s>>>(m, sc.p, safety, d_out);
@@ -1539,14 +1589,14 @@ __device__ __forceinline__ void node_gram(long n, int t, const double *__restric
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) {
       double s = 0.0;
-      for (int k = 0; k < t; ++k) s = s + V[(size_t)k * n + 3L * I + r] * V[(size_t)k * n + 3L * J + c];
+      for (int k = 0; k < t; ++k) s = fma(V[(size_t)k * n + 3L * I + r], V[(size_t)k * n + 3L * J + c], s);
       M[r * 3 + c] = s;
     }
 }
 
 __device__ __forceinline__ double fro2(const double *M) {
   double s = 0.0;
-  for (int i = 0; i < 9; ++i) s = s + M[i] * M[i];
+  for (int i = 0; i < 9; ++i) s = fma(M[i], M[i], s);
   return s;
 }
 

@@ -54,6 +54,24 @@ def test_gen_eig_matches_scipy(orc):
             assert U[np.argmax(np.abs(U[:, j])), j] > 0
 
 
+def test_gen_eig_equal_diagonal_and_repeated_eigenvalues(orc):
+    """Pivots with C_pp = C_qq (the 45-degree rotation, d = 0 in the rotation
+    formula, with either sign of C_pq) and a pencil with a repeated eigenvalue."""
+    for off in (0.5, -0.5):
+        H = np.array([[1.0, off], [off, 1.0]])
+        lam, U = orc.gen_eig(H, np.eye(2))
+        assert np.allclose(lam, [0.5, 1.5], rtol=0, atol=1e-15)
+        assert np.allclose(H @ U, U @ np.diag(lam), atol=1e-15)
+    rng = np.random.default_rng(14)
+    Q, _ = np.linalg.qr(rng.normal(size=(6, 6)))
+    H = Q @ np.diag([1.0, 2.0, 2.0, 2.0, 3.0, -1.0]) @ Q.T
+    H = (H + H.T) / 2
+    lam, U = orc.gen_eig(H, np.eye(6))
+    assert np.allclose(lam, [-1.0, 1.0, 2.0, 2.0, 2.0, 3.0], rtol=0, atol=1e-13)
+    assert np.allclose(U.T @ U, np.eye(6), atol=1e-13)
+    assert np.allclose(H @ U, U @ np.diag(lam), atol=1e-13)
+
+
 def test_mgs_orthonormal(orc):
     V = np.random.default_rng(13).normal(size=(500, 7))
     Q = orc.mgs(V)
