@@ -28,7 +28,8 @@
  *
  * Householder step on column x (rows p..t-1): sigma = sqrt(sum x_k^2),
  * alpha = -sigma if x_p >= 0 else sigma, v = x with v_p = x_p - alpha,
- * vv = sum v_k^2, R_pp = alpha; a column y becomes y - ((2 v^T y) / vv) v.
+ * vv = sum v_k^2, R_pp = alpha; a column y becomes y - ((2 v^T y) (1 / vv)) v
+ * (the reciprocal of vv, not a division per column).
  * All sums ascend; each multiply-add of a sum, of the update y - f v and of
  * the back substitution is one fused multiply-add.
  */
@@ -40,12 +41,13 @@
 
 #define TMAX 64
 
-/* apply reflection (v from row p, vv) to column y (stride b) */
+/* apply reflection (v from row p, vv) to column y (stride b):
+ * y <- y - ((2 v.y) (1 / vv)) v */
 static void reflect(int t, int p, const double *v, double vv, double *y,
                     int stride) {
   double s = 0.0;
   for (int k = p; k < t; ++k) s = fma(v[k], y[k * stride], s);
-  const double f = (2.0 * s) / vv;
+  const double f = (2.0 * s) * (1.0 / vv);
   for (int k = p; k < t; ++k) y[k * stride] = fma(-f, v[k], y[k * stride]);
 }
 

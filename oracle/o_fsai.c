@@ -172,12 +172,12 @@ int or_afsai(const obsr *A, const obsr *Gs, int ksteps, int rho, double eps,
       double *blk = gval + (used + j) * b * b;
       gcol[used + j] = (j < np) ? pat[j] : I;
       for (int c = 0; c < b; ++c) {
-        const double sq = sqrt(psi[c]);
+        const double rs = 1.0 / sqrt(psi[c]); /* g / sqrt(psi) as g times 1 / sqrt(psi) */
         for (int d = 0; d < b; ++d) {
           double g;
           if (j < np) g = gh[c][b * j + d];
           else g = (d < c) ? gh[c][b * np + d] : (d == c ? 1.0 : 0.0);
-          blk[c * b + d] = (j < np || d <= c) ? g / sq : 0.0;
+          blk[c * b + d] = (j < np || d <= c) ? g * rs : 0.0;
         }
       }
     }

@@ -849,15 +849,15 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
     }
     if (gl == 0) K.out_np[I] = np;
     for (int j = gl; j < np; j += FS_GL) K.out_pat[(size_t)I * K.maxg + j] = pat[j];
-    double sq[3];
-    for (int c = 0; c < 3; ++c) sq[c] = sqrt(psi[c]);
+    double rs[3];  // 1 / sqrt(psi_c): one division per row, products per entry
+    for (int c = 0; c < 3; ++c) rs[c] = 1.0 / sqrt(psi[c]);
     double *ov = K.out_val + (size_t)I * (K.maxg + 1) * 9;
     for (int idx = gl; idx < (np + 1) * 9; idx += FS_GL) {
       const int j = idx / 9, c = (idx % 9) / 3, d = idx % 3;
       double gv;
       if (j < np) gv = gh[c * mm + 3 * j + d];
       else gv = (d < c) ? gh[c * mm + 3 * np + d] : (d == c ? 1.0 : 0.0);
-      ov[idx] = (j < np || d <= c) ? gv / sq[c] : 0.0;
+      ov[idx] = (j < np || d <= c) ? gv * rs[c] : 0.0;
     }
   }
 }
@@ -1699,12 +1699,12 @@ int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char
 // One thread per fine node (Algorithm 5 in nodal-block form).  Householder
 // step on column x (rows p..t-1): sigma = sqrt(sum x^2), alpha = -sigma if
 // x_p >= 0 else sigma, v = x with v_p = x_p - alpha, vv = sum v^2; a column y
-// becomes y - ((2 v.y)/vv) v.  Affinity of residual X and candidate Y over
+// becomes y - ((2 v.y)(1/vv)) v, the reciprocal rvv = 1/vv formed once per v.  Affinity of residual X and candidate Y over
 // the trailing rows: ||X^T Y||_F^2 / (||X^T X||_F ||Y^T Y||_F).
-__device__ __forceinline__ void reflect(int t, int p, const double *v, double vv, double *y, int stride) {
+__device__ __forceinline__ void reflect(int t, int p, const double *v, double rvv, double *y, int stride) {
   double s = 0.0;
   for (int k = p; k < t; ++k) s = fma(v[k], y[k * stride], s);
-  const double f = (2.0 * s) / vv;
+  const double f = (2.0 * s) * rvv;
   for (int k = p; k < t; ++k) y[k * stride] = fma(-f, v[k], y[k * stride]);
 }
 
@@ -1807,8 +1807,8 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
       hv[c][pc] = Y[pc * 3 + c] - alpha;
       double vv = 0.0;
       for (int k = pc; k < t; ++k) vv = fma(hv[c][k], hv[c][k], vv);
-      hvv[c] = vv;
-      for (int c2 = c + 1; c2 < 3; ++c2) reflect(t, pc, hv[c], vv, Y + c2, 3);
+      hvv[c] = 1.0 / vv;  // reciprocal
+      for (int c2 = c + 1; c2 < 3; ++c2) reflect(t, pc, hv[c], hvv[c], Y + c2, 3);
       Y[pc * 3 + c] = alpha;
       for (int k = pc + 1; k < t; ++k) Y[k * 3 + c] = 0.0;
       const double ad = fabs(alpha);

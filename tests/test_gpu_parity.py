@@ -22,6 +22,18 @@ def A():
     return lib_
 
 
+def _dense(M):
+    """Dense copy of an oracle block matrix (3x3 blocks)."""
+    n = M.nr
+    D = np.zeros((3 * n, 3 * n))
+    vals = np.asarray(M.val).reshape(-1, 3, 3)
+    for I in range(n):
+        for q in range(M.rowptr[I], M.rowptr[I + 1]):
+            J = M.col[q]
+            D[3 * I:3 * I + 3, 3 * J:3 * J + 3] = vals[q]
+    return D
+
+
 def rel(a, b):
     a, b = np.asarray(a), np.asarray(b)
     den = np.abs(b).max()
@@ -102,11 +114,14 @@ def test_vcycle_matches_oracle(A, orc, name):
     zo = H.vcycle(y)
     zg = S.vcycle(torch.tensor(y, device="cuda")).cpu().numpy()
     # same hierarchy bit for bit, but the solve-phase products sum in the
-    # kernels' order (autotuned lanes per row) and the coarse level uses the
-    # explicit inverse factor: each product has relative error ~ k eps
-    # |A||x|/|Ax| (k ~ 81 terms, cancellation up to ~1e4 on the layered slab),
-    # compounded over ~8 products per level, hence the FP64 solution bound
-    assert rel(zg, zo) <= 1e-10
+    # kernels' order (autotuned lanes per row): each product has relative
+    # error ~ k eps |A||x|/|Ax| (k ~ 81 terms, cancellation up to ~1e4 on the
+    # layered slab), compounded over ~8 products per level (1e-10); and the
+    # last level is solved with its explicit inverse where the oracle
+    # substitutes with its Cholesky factor, a difference of order
+    # eps cond(A_c) that the prolongation carries into z
+    kc = np.linalg.cond(_dense(H.matrix(H.nlev - 1, "A")))
+    assert rel(zg, zo) <= 1e-10 + 2 * np.finfo(float).eps * kc
 
 
 @pytest.mark.parametrize("name", list(SMALL))
