@@ -879,8 +879,22 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   K.out_pat = out.pat;
   K.out_val = out.val;
   K.status = status;
-  K.mmax = 3 * maxg + 3;
-  K.candcap = (maxg + 1) * maxdeg;
+  // the largest pattern a row can reach: its starting pattern (a row of Gs
+  // without the diagonal) plus rho nodes per step, at most maxg; the row
+  // systems, candidate lists and hash sets are sized by it (the hash sets
+  // are probed at random positions, so smaller ones stay in L2)
+  long npcap = (long)ksteps * rho;
+  if (Gs) {
+    int np0 = 0;
+    for (int I = 0; I < Gs->nr; ++I) {
+      const int len = Gs->h_rowptr[I + 1] - Gs->h_rowptr[I] - 1;
+      if (len > np0) np0 = len;
+    }
+    npcap += np0;
+  }
+  if (npcap > maxg) npcap = maxg;
+  K.mmax = 3 * (int)npcap + 3;
+  K.candcap = ((int)npcap + 1) * maxdeg;
   K.hcap = 64;
   while (K.hcap < 2 * K.candcap) K.hcap *= 2;
   K.dper = (long)K.mmax * K.mmax + 9L * K.mmax + K.candcap;
