@@ -31,7 +31,7 @@ extern "C" {
 
 #define AMG_OK 0
 #define AMG_ERR_ARG (-1)           /* invalid argument or unsupported size */
-#define AMG_ERR_NOT_SPD (-2)       /* non-positive pivot (FSAI row, Cholesky) */
+#define AMG_ERR_NOT_SPD (-2)       /* non-positive pivot (FSAI row, Ritz pencil, coarse inverse) */
 #define AMG_ERR_BREAKDOWN (-3)     /* p^T A p <= 0 or a NaN/Inf in PCG */
 #define AMG_ERR_NOT_CONVERGED (-4) /* maxit reached; X holds the last iterate */
 #define AMG_ERR_CUDA (-5)          /* a CUDA runtime call failed */
@@ -42,7 +42,7 @@ extern "C" {
 #define AMG_MEM_HOST 1
 
 /* precision of the V-cycle (smoother, transfers, level matrices).  The outer
- * CG recurrence, its dot products, the true residual and the coarse Cholesky
+ * CG recurrence, its dot products, the true residual and the coarse solve
  * are FP64 in every mode. */
 #define AMG_FP64 0
 #define AMG_FP32 1        /* all V-cycle data and arithmetic FP32 */
@@ -70,7 +70,7 @@ typedef struct {
   int theta;              /* SoC connections kept per node (Sec. 3.3) */
   int n_max, d_p;         /* DPLS: interpolation nodes, path length (Alg. 5) */
   double kappa_p;         /* DPLS conditioning bound */
-  int n_coarse;           /* dense Cholesky once a level has <= n_coarse dofs */
+  int n_coarse;           /* dense direct solve once a level has <= n_coarse dofs */
   int max_levels;
   double max_coarse_ratio;/* stop coarsening when n_{k+1}/n_k exceeds this */
   int vcycle_prec;        /* AMG_FP64 | AMG_FP32 | AMG_FP32_BF16GP */
@@ -97,8 +97,10 @@ int amg_default_params(amg_params *p);
  * per level the aFSAI smoother of Algorithm 3, the SRQCG test space of
  * Algorithm 4 started from the near-null space V0 (padded to n_tv columns by
  * the counter generator, Sec. 3.2), the affinity C/F split of Sec. 3.3, the
- * DPLS prolongation of Algorithm 5 and A_{k+1} = P^T A P; a dense Cholesky
- * factor on the last level.
+ * DPLS prolongation of Algorithm 5 and A_{k+1} = P^T A P; on the last level
+ * its dense explicit inverse (blocked Gauss-Jordan, pivot blocks of 32; the
+ * paper's Algorithm 1 uses a dense Cholesky factor, and both give the exact
+ * coarse solve up to rounding).
  *   K: rowptr, colind, vals as described above, in `mem` memory; copied.
  *   V0: 3*nnodes x ntv0 column-major near-null space (e.g. the 6 rigid-body
  *       modes), ntv0 <= n_tv, in `mem` memory; copied.
