@@ -903,7 +903,7 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int threads = 128;
-  long nblocks = (long)nsm * 4;  // 16 warps, 64 slots per SM: scratch stays in L2
+  long nblocks = (long)nsm * 5;  // 20 warps, 80 slots per SM (96 registers a thread allow 5 blocks)
   const long need = ((long)A.nr + 4 * FS_NG - 1) / (4 * FS_NG);
   if (nblocks > need) nblocks = need > 0 ? need : 1;
   const long nslots = nblocks * (threads / 32) * FS_NG;
