@@ -56,3 +56,27 @@ def test_dot_special_cases(orc):
     # one fused multiply-add per term: x*y + 0 is the correctly rounded product
     p, q = 1.0 + 2.0 ** -30, 1.0 - 2.0 ** -30
     assert orc.dot(np.array([p]), np.array([q])) == float(Fraction(p) * Fraction(q))
+
+
+@pytest.mark.parametrize("m", [1, 2, 7, 40])
+def test_chol_factor_and_solve(orc, m):
+    """The dense Cholesky factor reproduces M, its solve matches a direct
+    solve within the conditioning bound, and a matrix that is not positive
+    definite is refused."""
+    rng = np.random.default_rng(100 + m)
+    X = rng.normal(size=(m, m))
+    M = X @ X.T + m * np.eye(m)
+    rc, L = orc.chol(M)
+    assert rc == 0
+    assert np.allclose(np.triu(L, 1), 0.0)
+    assert np.all(np.diag(L) > 0)
+    assert np.abs(L @ L.T - M).max() <= 1e-13 * np.abs(M).max()
+    b = rng.normal(size=m)
+    x = orc.chol_solve(L, b)
+    xr = np.linalg.solve(M, b)
+    assert np.linalg.norm(x - xr) <= 1e-12 * np.linalg.cond(M) * np.linalg.norm(xr)
+    if m > 1:
+        Mbad = M.copy()
+        Mbad[m - 1, m - 1] = -1.0
+        rc2, _ = orc.chol(Mbad)
+        assert rc2 != 0
