@@ -272,6 +272,7 @@ extern "C" int amg_fe_assemble(int nx, int ny, int nz, double hx, double hy, dou
     return AMG_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  StreamScope scope(s);  // temporaries are taken and returned on s
   Mesh m;
   AMG_TRY(build_mesh(nx, ny, nz, clamp, m, true));
   const int nf = (int)m.f2g.size();
@@ -296,6 +297,7 @@ extern "C" int amg_fe_load(int nx, int ny, int nz, double hx, double hy, double 
     return AMG_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  StreamScope scope(s);  // temporaries are taken and returned on s
   Mesh m;
   AMG_TRY(build_mesh(nx, ny, nz, clamp, m, false));
   const int nf = (int)m.f2g.size();
@@ -313,6 +315,7 @@ extern "C" int amg_fe_rbm(int nx, int ny, int nz, double hx, double hy, double h
                           void *stream) {
   if (!V) return AMG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  StreamScope scope(s);  // temporaries are taken and returned on s
   Mesh m;
   AMG_TRY(build_mesh(nx, ny, nz, clamp, m, false));
   const int nf = (int)m.f2g.size();
@@ -328,6 +331,7 @@ extern "C" int amg_fe_rbm(int nx, int ny, int nz, double hx, double hy, double h
 extern "C" int amg_fe_conn(int nx, int ny, int nz, int clamp, int *conn, void *stream) {
   if (!conn) return AMG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  StreamScope scope(s);  // temporaries are taken and returned on s
   Mesh m;
   AMG_TRY(build_mesh(nx, ny, nz, clamp, m, false));
   DBuf<int> nm;
