@@ -88,6 +88,11 @@ typedef struct {
   int level_nnzb[32];
   int level_g_nnzb[32];
   double level_omega[32];
+  /* last solve, largest over its columns: the recurrence residual
+   * ||r||/||b|| the CG iteration stopped on, the FP64 true residual
+   * ||b - K x||/||b||, and the number of true-residual restarts */
+  double relres_rec, relres_true;
+  int restarts;
 } amg_stats;
 
 /* Fill *p with the defaults.  Returns AMG_ERR_ARG for p == NULL. */
@@ -117,12 +122,22 @@ int amg_update_values(amg_handle h, const double *vals, int mem);
 
 /* Solve K X = B by PCG with one V(1,1)-cycle per iteration, x0 = 0, stopping
  * column j when ||r_j||_2 <= rtol ||b_j||_2 on the recurrence residual
- * (Sec. 4).  B and X are 3*nnodes x k column-major in `mem` memory (host
- * buffers are staged through the device inside the call).  iters[k] and
- * relres[k] (host) receive each column's iteration count and final
- * ||r||/||b||.  k > 1 runs the batched (block SpMM) path with per-column
- * convergence masks.  Returns AMG_ERR_NOT_CONVERGED if a column hit maxit
- * (X still holds its last iterate) or AMG_ERR_BREAKDOWN. */
+ * (Sec. 4).  When the recurrence stops, the true residual b_j - K x_j is
+ * formed in FP64 with the level-0 K on the GPU; if ||b_j - K x_j||_2 >
+ * rtol ||b_j||_2 (rounding of an FP32 or bf16 V-cycle, or the recurrence and
+ * true residuals straddling rtol) the recurrence restarts from the true
+ * residual, keeping x_j and its iteration count: at most 8 restarts, within
+ * maxit, and only while each restart halves the true residual (a smaller
+ * rtol than FP64 attains on K, about eps cond(K), stops there).  B and X are
+ * 3*nnodes x k column-major in `mem` memory (host buffers are staged through
+ * the device inside the call).  iters[k] and relres[k] (host) receive each
+ * column's iteration count (restarts included) and final FP64 true residual
+ * ||b - K x||/||b||; amg_get_stats gives the largest recurrence residual too.
+ * k > 1 runs the batched (block SpMM) path with per-column convergence masks.
+ * The status follows the recurrence rule: AMG_ERR_NOT_CONVERGED if a column
+ * hit maxit (X holds its last iterate), AMG_ERR_BREAKDOWN on p^T K p <= 0 or
+ * a NaN/Inf, else AMG_OK (relres then is <= rtol unless rtol is below the
+ * attainable accuracy). */
 int amg_solve(amg_handle h, int k, const double *B, double *X, double rtol,
               int *iters, double *relres, int mem);
 

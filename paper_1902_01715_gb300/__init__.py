@@ -48,7 +48,8 @@ class AmgStats(C.Structure):
                 ("T_cs", C.c_double), ("T_pl", C.c_double), ("T_rap", C.c_double),
                 ("T_p", C.c_double), ("T_s", C.c_double), ("level_nodes", C.c_int * 32),
                 ("level_nnzb", C.c_int * 32), ("level_g_nnzb", C.c_int * 32),
-                ("level_omega", C.c_double * 32)]
+                ("level_omega", C.c_double * 32), ("relres_rec", C.c_double),
+                ("relres_true", C.c_double), ("restarts", C.c_int)]
 
 
 class AmgError(RuntimeError):
@@ -265,7 +266,8 @@ class Solver:
         return x, list(iters), list(rel), rc
 
     def solve(self, B, rtol=1e-8):
-        """PCG with one V-cycle per iteration; returns (x, iters, relres, rc)."""
+        """PCG with one V-cycle per iteration; returns (x, iters, relres, rc),
+        relres being each column's FP64 true residual ||b - K x|| / ||b||."""
         return self._solve(lib().amg_solve, B, rtol)
 
     def adjoint(self, G, rtol=1e-8):

@@ -212,6 +212,7 @@ struct Batch;  // batched-solve state (batch.cu)
 struct Handle {
   amg_params prm{};
   cudaStream_t stream = nullptr;
+  int dev = -1;  // device current at amg_setup
   int n = 0;  // fine nodes
   int nlev = 0;
   std::vector<std::unique_ptr<Level>> lev;

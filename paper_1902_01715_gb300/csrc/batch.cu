@@ -141,10 +141,14 @@ struct Batch {
 };
 
 // per-column scalar slots: sc[slot * k + c]
-enum { BS_BN2 = 0, BS_RZ, BS_PQ, BS_ALPHA, BS_RR, BS_BETA, BS_TOL2, BS_NUM };
-// flags: [0] all done, [1] ticket, [2] status, [3] maxit, [4] iteration, then per column:
-// [8 + c] converged, [8 + k + c] iterations of column c
-enum { BF_DONE = 0, BF_TICKET = 1, BF_STATUS = 2, BF_MAXIT = 3, BF_ITER = 4, BF_COL = 8 };
+enum { BS_BN2 = 0, BS_RZ, BS_PQ, BS_ALPHA, BS_RR, BS_BETA, BS_TOL2, BS_TRR, BS_TRRP, BS_NUM };
+// flags: [0] all done, [1] ticket, [2] status, [3] maxit, [4] iteration,
+// [5] a column restarts from its true residual, then per column:
+// [8 + c] state (0 active, 1 converged, 2 breakdown, 3 not converged),
+// [8 + k + c] iterations of column c
+enum { BF_DONE = 0, BF_TICKET = 1, BF_STATUS = 2, BF_MAXIT = 3, BF_ITER = 4, BF_RESTART = 5, BF_COL = 8 };
+// true-residual restarts of one batched solve
+constexpr int kMaxBatchRestarts = 8;
 
 constexpr int BRED_BLOCKS = 148;
 
@@ -329,12 +333,58 @@ __global__ void k_bcheck(int k, int *flags) {
 }
 
 // first direction: p = z, z_old = z
-__global__ void k_bfirst(long n, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold) {
+__global__ void k_bfirst(long n, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold,
+                         const int *flags) {
+  if (flags[BF_DONE]) return;
   const long stride = (long)gridDim.x * blockDim.x;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
     p[t] = z[t];
     zold[t] = z[t];
   }
+}
+
+// True residuals after every column stopped: q holds K x (FP64 level-0 K);
+// r = b - q (b read from the column-major right-hand sides), rlow = (TX) r,
+// trr_c = ||r_c||^2.  A column that stopped as converged but whose true
+// residual is above rtol ||b_c|| becomes active again (restart from its true
+// residual, iteration count kept), within the limits of the single
+// right-hand-side solve: at most max_phase restarts, below the iteration
+// limit, and only while the previous restart halved its true residual.
+template <typename TX>
+__global__ void k_btrue(long n, int k, const double *__restrict__ B, const double *__restrict__ q,
+                        double *__restrict__ r, TX *__restrict__ rlow, int phase, int max_phase, double *sc,
+                        int *flags, double *part) {
+  double v = 0.0;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) {
+    const long d = t / k;
+    const int c = (int)(t - d * k);
+    const double ri = B[(size_t)c * n + d] - q[t];
+    r[t] = ri;
+    if (rlow) rlow[t] = (TX)ri;
+    v += ri * ri;
+  }
+  bfinish(v, k, part, flags, [&](int c, double tot) {
+    const double prev = sc[BS_TRRP * k + c];
+    sc[BS_TRR * k + c] = tot;
+    sc[BS_TRRP * k + c] = tot;
+    if (flags[BF_COL + c] != 1) return;
+    if (!isfinite(tot)) {
+      flags[BF_STATUS] = AMG_ERR_BREAKDOWN;
+      flags[BF_COL + c] = 2;
+    } else if (tot > sc[BS_TOL2 * k + c] && phase < max_phase && flags[BF_COL + k + c] < flags[BF_MAXIT] &&
+               !(phase > 0 && tot > 0.25 * prev)) {
+      sc[BS_RR * k + c] = tot;
+      flags[BF_COL + c] = 0;
+      flags[BF_RESTART] = 1;
+    }
+  });
+}
+
+// done again unless a column restarts
+__global__ void k_brestart_done(int *flags) {
+  flags[BF_DONE] = flags[BF_RESTART] ? 0 : 1;
+  flags[BF_RESTART] = 0;
 }
 
 // interleaved -> column-major
@@ -472,14 +522,23 @@ static int ensure_batch(Handle *h, Batch &B, int k) {
 int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres) {
   if (k > 256) {
     // independent groups of at most 256 columns
-    int worst = AMG_OK;
+    int worst = AMG_OK, nit = 0, nrs = 0;
+    double rec = 0.0, tru = 0.0;
     const size_t n = 3 * (size_t)h->n;
     for (int c0 = 0; c0 < k; c0 += 256) {
       const int kk = k - c0 < 256 ? k - c0 : 256;
       const int rc = solve_batched(h, kk, B + c0 * n, X + c0 * n, rtol, iters + c0, relres + c0);
       if (rc == AMG_ERR_CUDA) return rc;
       if (rc && !worst) worst = rc;
+      nit = std::max(nit, h->stats.n_it);
+      rec = std::max(rec, h->stats.relres_rec);
+      tru = std::max(tru, h->stats.relres_true);
+      nrs += h->stats.restarts;
     }
+    h->stats.n_it = nit;
+    h->stats.relres_rec = rec;
+    h->stats.relres_true = tru;
+    h->stats.restarts = nrs;
     return worst;
   }
   if (!h->batch) h->batch = new Batch();
@@ -506,7 +565,7 @@ int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int
     bvcycle<double>(h, Bt, 0, Bt.r.p, Bt.z.p, fl + BF_DONE);
   }
   AMG_KCOUNT k_brz2<<<BRED_BLOCKS, bt, shm, s>>>(n, k, Bt.r.p, Bt.z.p, 0, Bt.sc.p, fl, Bt.part.p);
-  AMG_KCOUNT k_bfirst<<<BRED_BLOCKS, 256, 0, s>>>(n * k, Bt.p.p, Bt.z.p, Bt.zold.p);
+  AMG_KCOUNT k_bfirst<<<BRED_BLOCKS, 256, 0, s>>>(n * k, Bt.p.p, Bt.z.p, Bt.zold.p, fl);
   AMG_LAUNCH_CHECK();
   if (!Bt.graph) {
     cudaGraph_t g;
@@ -526,21 +585,50 @@ int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int
   }
   const int chunk = 4;
   int rc = AMG_OK;
-  for (int it = 0; it < h->prm.maxit + chunk; it += chunk) {
-    for (int c = 0; c < chunk; ++c) {
-      if (cudaGraphLaunch(Bt.graph, s) != cudaSuccess) {
-        set_error("batched solve: graph launch failed");
+  Level &L0 = *h->lev[0];
+  int restarts = 0;
+  // Phases: replay until every column stopped, then the FP64 true residuals;
+  // columns above rtol restart from theirs (one V-cycle of the block).
+  for (;;) {
+    for (int it = 0; it < h->prm.maxit + chunk; it += chunk) {
+      for (int c = 0; c < chunk; ++c) {
+        if (cudaGraphLaunch(Bt.graph, s) != cudaSuccess) {
+          set_error("batched solve: graph launch failed");
+          return AMG_ERR_CUDA;
+        }
+        count_launches(Bt.graph_nodes);
+      }
+      AMG_CU(cudaMemcpyAsync(Bt.pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s));
+      const cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_error("batched solve: %s", cudaGetErrorString(e));
         return AMG_ERR_CUDA;
       }
-      count_launches(Bt.graph_nodes);
+      if (Bt.pinned[0]) break;
     }
-    cudaMemcpyAsync(Bt.pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s);
-    const cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      set_error("batched solve: %s", cudaGetErrorString(e));
-      return AMG_ERR_CUDA;
+    bmm<double, double>(BE_SET, L0.sA, L0.sA.v64.p, k, Bt.x.p, Bt.q.p, nullptr, 0.0, nullptr, s);
+    if (mixed)
+      AMG_KCOUNT k_btrue<float><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B, Bt.q.p, Bt.r.p, Bt.rlow.p, restarts,
+                                                             kMaxBatchRestarts, Bt.sc.p, fl, Bt.part.p);
+    else
+      AMG_KCOUNT k_btrue<double><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B, Bt.q.p, Bt.r.p, (double *)nullptr, restarts,
+                                                              kMaxBatchRestarts, Bt.sc.p, fl, Bt.part.p);
+    AMG_KCOUNT k_brestart_done<<<1, 1, 0, s>>>(fl);
+    // restart of the reopened columns (done-gated, as the start sequence)
+    if (mixed) {
+      bvcycle<float>(h, Bt, 0, Bt.rlow.p, Bt.zlow.p, fl + BF_DONE);
+      AMG_KCOUNT k_brz<float><<<BRED_BLOCKS, bt, shm, s>>>(n, k, Bt.r.p, Bt.z.p, Bt.zlow.p, Bt.zold.p, 0, Bt.sc.p, fl,
+                                                           Bt.part.p);
+    } else {
+      bvcycle<double>(h, Bt, 0, Bt.r.p, Bt.z.p, fl + BF_DONE);
     }
+    AMG_KCOUNT k_brz2<<<BRED_BLOCKS, bt, shm, s>>>(n, k, Bt.r.p, Bt.z.p, 0, Bt.sc.p, fl, Bt.part.p);
+    AMG_KCOUNT k_bfirst<<<BRED_BLOCKS, 256, 0, s>>>(n * k, Bt.p.p, Bt.z.p, Bt.zold.p, fl);
+    AMG_LAUNCH_CHECK();
+    AMG_CU(cudaMemcpyAsync(Bt.pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CU(cudaStreamSynchronize(s));
     if (Bt.pinned[0]) break;
+    ++restarts;
   }
   AMG_KCOUNT k_bout<<<nblk(n * k, 256), 256, 0, s>>>(n, k, Bt.x.p, X);
   AMG_LAUNCH_CHECK();
@@ -550,17 +638,23 @@ int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int
   AMG_CU(cudaMemcpyAsync(hs.data(), Bt.sc.p, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   AMG_CU(cudaStreamSynchronize(s));
   int maxit = 0;
+  double rec_max = 0.0, true_max = 0.0;
   for (int c = 0; c < k; ++c) {
     iters[c] = hf[BF_COL + k + c];
     const double bn2 = hs[BS_BN2 * k + c];
-    relres[c] = bn2 > 0.0 ? std::sqrt(hs[BS_RR * k + c] / bn2) : 0.0;
-    if (bn2 == 0.0) relres[c] = 0.0;
+    relres[c] = bn2 > 0.0 ? std::sqrt(hs[BS_TRR * k + c] / bn2) : 0.0;
+    const double rec = bn2 > 0.0 ? std::sqrt(hs[BS_RR * k + c] / bn2) : 0.0;
+    rec_max = rec > rec_max ? rec : rec_max;
+    true_max = relres[c] > true_max ? relres[c] : true_max;
     const int st = hf[BF_COL + c];
     if (st == 2) rc = AMG_ERR_BREAKDOWN;
     else if ((st == 3 || st == 0) && rc == AMG_OK) rc = AMG_ERR_NOT_CONVERGED;
     if (iters[c] > maxit) maxit = iters[c];
   }
   h->stats.n_it = maxit;
+  h->stats.relres_rec = rec_max;
+  h->stats.relres_true = true_max;
+  h->stats.restarts = restarts;
   return rc;
 }
 

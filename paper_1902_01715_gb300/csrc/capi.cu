@@ -71,6 +71,11 @@ extern "C" int amg_setup(const amg_params *p, int nnodes, int nnzb, const int *r
   Handle *h = new (std::nothrow) Handle();
   if (!h) return AMG_ERR_MEM;
   h->prm = *p;
+  if (cudaGetDevice(&h->dev) != cudaSuccess) {
+    delete h;
+    set_error("amg_setup: cudaGetDevice failed");
+    return AMG_ERR_CUDA;
+  }
   h->stream = (cudaStream_t)stream;
   if (!h->stream) {
     // the legacy default stream cannot be captured into a CUDA graph; a

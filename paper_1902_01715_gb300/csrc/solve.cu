@@ -147,10 +147,12 @@ static void vcycle_level(Handle *h, int k, const TX *y, TX *z, const int *done) 
 
 // ---------------------------------------------------------------- PCG
 // scalar slots (doubles) and flags (ints) on the device
-enum { P_BN2 = 0, P_RZ, P_PQ, P_ALPHA, P_RR, P_RZN, P_RZO, P_BETA, P_TOL2, P_NSC };
+enum { P_BN2 = 0, P_RZ, P_PQ, P_ALPHA, P_RR, P_RZN, P_RZO, P_BETA, P_TOL2, P_TRR, P_TRRP, P_NSC };
 enum { F_DONE = 0, F_ITERS, F_STATUS, F_MAXIT, F_TICKET, F_NFL };
 
 constexpr int RED_BLOCKS = 296;
+// true-residual restarts of one solve (each one V-cycle and one FP64 product more)
+constexpr int kMaxRestarts = 8;
 constexpr int RED_THREADS = 256;
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -325,6 +327,40 @@ __global__ void k_pcg_first_p(long n, double *__restrict__ p, const double *__re
   }
 }
 
+// True residual after the recurrence stopped: r already holds b - K x (FP64
+// level-0 K); trr = r.r.  When the column stopped as converged but
+// ||b - K x||^2 > rtol^2 ||b||^2, the recurrence restarts from the true
+// residual (done is cleared, so the V-cycle and first-direction kernels that
+// follow run; rlow receives (TX) r for the V-cycle; the iteration count
+// carries on) -- unless this is restart number kMaxRestarts, the iteration
+// limit is reached, or the previous restart did not halve the true residual
+// (rtol is then below the accuracy FP64 attains on this system).  The status
+// stays that of the recurrence rule (Sec. 4); the true residual is reported.
+template <typename TX>
+__global__ void __launch_bounds__(RED_THREADS) k_pcg_true(long n, const double *__restrict__ r, TX *__restrict__ rlow,
+                                                          int phase, int max_phase, double *sc, int *flags,
+                                                          double *part) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    if (rlow) rlow[i] = (TX)ri;
+    v += ri * ri;
+  }
+  finish_reduce(v, part, flags, sh, [&](double tot) {
+    const double prev = sc[P_TRRP];
+    sc[P_TRR] = tot;
+    sc[P_TRRP] = tot;
+    if (!isfinite(tot)) {
+      if (flags[F_STATUS] == 0) flags[F_STATUS] = AMG_ERR_BREAKDOWN;
+    } else if (flags[F_STATUS] == 0 && tot > sc[P_TOL2] && phase < max_phase && flags[F_ITERS] < flags[F_MAXIT] &&
+               !(phase > 0 && tot > 0.25 * prev)) {
+      sc[P_RR] = tot;
+      flags[F_DONE] = 0;
+    }
+  });
+}
+
 __global__ void k_set_flags(int *flags, int maxit) {
   flags[F_DONE] = 0;
   flags[F_ITERS] = 0;
@@ -385,7 +421,8 @@ static void pcg_iteration(Handle *h, bool mixed) {
 }
 
 template <typename TX>
-static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int *iters, double *relres, bool mixed) {
+static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int *iters, double *relres,
+                         double *rec_relres, int *nrestart, bool mixed) {
   cudaStream_t s = h->stream;
   const long n = 3L * h->n;
   double *part = h->red.p;
@@ -429,38 +466,56 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
   }
   int hflags[F_NFL];
   int *pinned = h->pinned;
-  int rc = AMG_OK;
-  // replay; the device flag makes finished iterations no-ops, the host checks
-  // it every `chunk` launches
+  Level &L0 = *h->lev[0];
+  int restarts = 0;
+  // Phases: replay the iteration graph until the device flag says the
+  // recurrence stopped (the host checks it every `chunk` launches), then form
+  // the FP64 true residual b - K x; if it is above rtol ||b|| the recurrence
+  // restarts from it (see k_pcg_true for the limits).
   const int chunk = 4;
-  for (int it = 0; it < h->prm.maxit + chunk; it += chunk) {
-    for (int c = 0; c < chunk; ++c) {
-      cudaError_t e = cudaGraphLaunch(h->graph_exec, s);
-      if (e != cudaSuccess) {
-        set_error("cudaGraphLaunch: %s", cudaGetErrorString(e));
-        rc = AMG_ERR_CUDA;
-        break;
+  for (;;) {
+    for (int it = 0; it < h->prm.maxit + chunk; it += chunk) {
+      for (int c = 0; c < chunk; ++c) {
+        cudaError_t e = cudaGraphLaunch(h->graph_exec, s);
+        if (e != cudaSuccess) {
+          set_error("cudaGraphLaunch: %s", cudaGetErrorString(e));
+          return AMG_ERR_CUDA;
+        }
+        count_launches(h->graph_nodes);
       }
-      count_launches(h->graph_nodes);
+      AMG_CU(cudaMemcpyAsync(pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s));
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_error("PCG: %s", cudaGetErrorString(e));
+        return AMG_ERR_CUDA;
+      }
+      if (pinned[0]) break;
     }
-    if (rc) break;
-    cudaMemcpyAsync(pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      set_error("PCG: %s", cudaGetErrorString(e));
-      rc = AMG_ERR_CUDA;
-      break;
-    }
+    // r = b - K x with the FP64 level-0 K, its norm, and the restart decision
+    bsrmv<double, double>(EP_RESID, L0.sA, L0.sA.v64.p, h->x.p, h->r.p, b, 0.0, nullptr, s);
+    AMG_KCOUNT k_pcg_true<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr,
+                                                                restarts, kMaxRestarts, sc, fl, part);
+    // restart (all done-gated: nothing runs unless k_pcg_true cleared done)
+    if (mixed) vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), fl + F_DONE);
+    else vcycle_level<double>(h, 0, h->r.p, h->z.p, fl + F_DONE);
+    AMG_KCOUNT k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
+                                                     h->zold.p, 0, sc, fl, part, part + 2 * RED_BLOCKS);
+    AMG_KCOUNT k_pcg_first_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, fl);
+    AMG_LAUNCH_CHECK();
+    AMG_CU(cudaMemcpyAsync(pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CU(cudaStreamSynchronize(s));
     if (pinned[0]) break;
+    ++restarts;
   }
-  if (rc) return rc;
   double hsc[P_NSC];
   AMG_CU(cudaMemcpy(hflags, fl, sizeof hflags, cudaMemcpyDeviceToHost));
   AMG_CU(cudaMemcpy(hsc, sc, sizeof hsc, cudaMemcpyDeviceToHost));
   AMG_CU(cudaMemcpyAsync(x, h->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   AMG_CU(cudaStreamSynchronize(s));
   *iters = hflags[F_ITERS];
-  *relres = hsc[P_BN2] > 0.0 ? std::sqrt(hsc[P_RR] / hsc[P_BN2]) : 0.0;
+  *relres = hsc[P_BN2] > 0.0 ? std::sqrt(hsc[P_TRR] / hsc[P_BN2]) : 0.0;
+  *rec_relres = hsc[P_BN2] > 0.0 ? std::sqrt(hsc[P_RR] / hsc[P_BN2]) : 0.0;
+  *nrestart = restarts;
   if (mixed) AMG_TRY(bulk_copy_error());
   return hflags[F_STATUS];
 }
@@ -470,19 +525,26 @@ int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters,
   AMG_TRY(ensure_pcg(h));
   const long n = 3L * h->n;
   const bool mixed = h->prm.vcycle_prec != AMG_FP64;
-  int worst = AMG_OK, maxit = 0;
+  int worst = AMG_OK, maxit = 0, nrs = 0;
+  double rec_max = 0.0, true_max = 0.0;
   for (int j = 0; j < k; ++j) {
-    int it = 0;
-    double rr = 0.0;
-    const int rc = mixed ? pcg_solve_one<float>(h, B + (size_t)j * n, X + (size_t)j * n, rtol, &it, &rr, true)
-                         : pcg_solve_one<double>(h, B + (size_t)j * n, X + (size_t)j * n, rtol, &it, &rr, false);
+    int it = 0, rs = 0;
+    double rr = 0.0, rec = 0.0;
+    const int rc = mixed ? pcg_solve_one<float>(h, B + (size_t)j * n, X + (size_t)j * n, rtol, &it, &rr, &rec, &rs, true)
+                         : pcg_solve_one<double>(h, B + (size_t)j * n, X + (size_t)j * n, rtol, &it, &rr, &rec, &rs, false);
     if (rc == AMG_ERR_CUDA) return rc;
     if (rc && !worst) worst = rc;
     iters[j] = it;
     relres[j] = rr;
     maxit = it > maxit ? it : maxit;
+    rec_max = rec > rec_max ? rec : rec_max;
+    true_max = rr > true_max ? rr : true_max;
+    nrs += rs;
   }
   h->stats.n_it = maxit;
+  h->stats.relres_rec = rec_max;
+  h->stats.relres_true = true_max;
+  h->stats.restarts = nrs;
   return worst;
 }
 
@@ -510,6 +572,8 @@ int vcycle_apply(Handle *h, const double *y, double *z) {
   }
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
+  // a bulk-copy stage that timed out left rows of z unwritten
+  if (h->prm.vcycle_prec != AMG_FP64) AMG_TRY(bulk_copy_error());
   return AMG_OK;
 }
 
@@ -547,6 +611,13 @@ static int vc_scratch_address(void **out) {
 }
 
 int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
+  // the scratch address is per device: it must be the device of the handle
+  int cur = -1;
+  AMG_CU(cudaGetDevice(&cur));
+  if (cur != h->dev) {
+    set_error("amg_vcycle_noalloc: current device %d is not the handle's device %d", cur, h->dev);
+    return AMG_ERR_ARG;
+  }
   void *base = nullptr;
   AMG_TRY(vc_scratch_address(&base));
   int *flags = (int *)base;
@@ -563,6 +634,9 @@ int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
   }
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
+  // a bulk-copy stage that timed out left rows of z unwritten (the error word
+  // is read and cleared with plain symbol copies: no allocation)
+  if (h->prm.vcycle_prec != AMG_FP64) AMG_TRY(bulk_copy_error());
   return AMG_OK;
 }
 

@@ -466,8 +466,13 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
 }
 
 // ---------------------------------------------------------------- autotuner
-// The (WPS, U) mapping is chosen by timing every candidate on the matrix
-// itself (CUDA events, one warm-up and three timed launches each).  The
+// The mapping is chosen by timing candidates on the matrix itself (CUDA
+// events, one warm-up and three timed launches each).  Only WPS decides the
+// order in which a row's blocks are summed (warp p sums blocks p, p + WPS,
+// ... in order whatever U, and the bulk-copy variant sums them in order like
+// WPS = 1), so WPS is fixed by the size rule and the timing picks among the
+// candidates with that WPS: the products, and with them the iteration count
+// of a solve, do not depend on which candidate won on a given run.  The
 // winner is cached per (storage type, slice count, average row length) so
 // that later hierarchies of the same shape reuse it; matrices too small to
 // time keep the rule.
@@ -496,7 +501,11 @@ static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
   AMG_CU(cudaEventCreate(&e1));
   float best = 1e30f;
   int bm = map;
+  const int rule_wps = kMaps[rule_map(M)].wps;
   for (int c = 0; c < kNumMaps; ++c) {
+    const int wps = kMaps[c].wps == 0 ? 1 : kMaps[c].wps;  // bulk copy: one warp per slice
+    if (wps != rule_wps) continue;
+    if (kMaps[c].wps == 0 && std::is_same<TM, double>::value) continue;  // FP64 has no bulk variant
     map = c;
     bsrmv<TM, TX>(EP_SET, M, v, x.p, y.p, (const TX *)nullptr, TX(0), nullptr, s);
     AMG_CU(cudaEventRecord(e0, s));

@@ -54,9 +54,12 @@ def test_batched_mixed_reaches_tolerance(A, orc, prec):
     X, its, rel, rc = S.solve(Fg, 1e-8)
     assert rc == 0
     Xn = X.cpu().numpy()
+    # rel[c] is the library's FP64 true residual of column c (restarted from
+    # it when above rtol); the oracle's K gives the same value to rounding
     for c in range(F.shape[1]):
         true_rel = np.linalg.norm(F[:, c] - K.matvec(Xn[:, c])) / np.linalg.norm(F[:, c])
-        assert true_rel <= 1.5e-8, (c, true_rel)
+        assert rel[c] <= 1e-8, (c, rel[c])
+        assert abs(true_rel - rel[c]) <= 1e-10, (c, true_rel, rel[c])
 
 
 def test_batched_masks_freeze_finished_columns(A, orc):
@@ -119,8 +122,9 @@ def test_adjoint_gradient_against_oracle_and_fd(A, orc):
                 ue[3 * a:3 * a + 3] = uo[3 * I:3 * I + 3]
         go[e] = -3.0 * rho[e] ** 2 * (ue @ Ke0 @ ue)
     assert np.abs(g - go).max() <= 1e-8 * np.abs(go).max()
-    # central finite differences on a few elements
-    for e in W.fd_elements(p, 4):
+    # central finite differences on 32 seeded elements (the element count of
+    # the 128^3 compliance workload's check; here each perturbed solve is cheap)
+    for e in W.fd_elements(p, 32):
         h = 1e-4 * rho[e]
         vals = []
         for sgn in (1.0, -1.0):

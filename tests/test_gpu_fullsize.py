@@ -83,10 +83,11 @@ def test_beam_solution_true_residual(A, beam):
     p, K, f, d, S = beam
     x, its, rel, rc = S.solve(d["f"], 1e-8)
     assert rc == 0 and rel[0] <= 1e-8
-    assert _true_rel(K, x.cpu().numpy(), f) <= 1.05e-8
+    assert abs(_true_rel(K, x.cpu().numpy(), f) - rel[0]) <= 2e-10
     S32 = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec="fp32")
     x32, its32, rel32, rc32 = S32.solve(d["f"], 1e-8)
-    assert rc32 == 0 and _true_rel(K, x32.cpu().numpy(), f) <= 1.05e-8
+    assert rc32 == 0 and rel32[0] <= 1e-8
+    assert abs(_true_rel(K, x32.cpu().numpy(), f) - rel32[0]) <= 2e-10
     assert its32[0] <= 1.15 * its[0] + 2
 
 
@@ -152,12 +153,15 @@ def test_slab_mixed_precision(A, orc, prec):
     K, V0, f, nm = oracle_problem(orc, p)
     d = gpu_problem(A, p)
     S64 = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
-    x64, its64, _, rc64 = S64.solve(d["f"], 1e-8)
+    x64, its64, rel64, rc64 = S64.solve(d["f"], 1e-8)
     S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec=prec)
-    x, its, _, rc = S.solve(d["f"], 1e-8)
+    x, its, rel, rc = S.solve(d["f"], 1e-8)
     assert rc64 == 0 and rc == 0
-    assert _true_rel(K, x.cpu().numpy(), f) <= 1.05e-8
-    assert _true_rel(K, x64.cpu().numpy(), f) <= 1.05e-8
+    # library FP64 true residuals meet the rule; the oracle's K agrees with
+    # them to the rounding of b - K x on this ill-conditioned system
+    assert rel[0] <= 1e-8 and rel64[0] <= 1e-8
+    assert abs(_true_rel(K, x.cpu().numpy(), f) - rel[0]) <= 5e-10
+    assert abs(_true_rel(K, x64.cpu().numpy(), f) - rel64[0]) <= 5e-10
     assert its[0] <= 1.5 * its64[0] + 2
     # the two solutions differ by K^{-1}(r64 - r): compare them in the energy
     # norm, relative to the solution's
@@ -189,7 +193,7 @@ def test_cube96_batched_64_load_cases(A, orc):
     for c in cols:
         fc = nodal_to_free(p, nm, c)
         assert np.array_equal(Fg[:, c].cpu().numpy(), fc)
-        assert _true_rel(K, X[:, c].cpu().numpy(), fc) <= 1.05e-8, c
+        assert abs(_true_rel(K, X[:, c].cpu().numpy(), fc) - rel[c]) <= 2e-10, c
     for c in cols[:2]:
         x1, it1, _, rc1 = S.solve(Fg[:, c].contiguous(), 1e-8)
         assert rc1 == 0 and abs(it1[0] - its[c]) <= 1
