@@ -11,8 +11,9 @@ same configuration is measured next to it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
-bounded, scaled-down sample of the same workload.
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(plain C, OpenMP over its row loops on all host cores) on the same workload:
+each step one whole set-up + PCG solve of the 128 x 32 x 32 beam.
 """
 from __future__ import annotations
 
@@ -30,7 +31,6 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-1e-8 residual & V-cycles/s (FP64 vs mixed/batched), SpMV %HBM peak"
 UNIT = "solutions/s"
 RTOL = 1e-8
-SAMPLE_DIMS = (48, 12, 12)   # oracle sample: same recipe, scaled down
 # FP64 arithmetic peak for FMA-bound kernels: the nominal 1.25 TFLOP/s of this
 # GPU (152 SMs x 2 FP64 FMA per clock x 2 flop x ~2.06 GHz); a chain-of-FMA
 # probe on the same GPUs measured 6.28e11 FMA/s (1.256 TFLOP/s)
@@ -39,11 +39,20 @@ FP64_PEAK_SOURCE = "nominal FP64 rate (1.25 TFLOP/s); FMA-chain probe measured 1
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu captures summarised under profiles/; a kernel whose code changed since its
 # capture has no entry
-TRAFFIC: dict = {
-    # level-0 A of the 128x32x32 beam times 10 columns (k_spmv_cols<1>):
-    # 307.22 MB read + 27.28 MB written
-    "k_spmv_cols": 334.50e6,
-}
+TRAFFIC: dict = {}
+# aFSAI kernel: fraction of the FP64 FMA lane peak in its ncu capture
+# (profiles/k_fsai_beam96x24x24.md); None once the kernel changed
+FSAI_LANE_FRAC = None
+
+
+def workload_config(n3=None):
+    """The bench workload's config, the same for both arms."""
+    import workloads as W
+    if n3 is None:
+        n3 = 3 * W.beam().free_nodes()
+    return {"workload": "cantilever beam 128x32x32 Q1 hex (%d dofs), x=0 clamped, tip shear, lognormal E "
+                        "(mu 0, sigma 1), nu 0.3; set-up + PCG to 1e-8, FP64" % n3,
+            "l2": "inputs larger than L2 (fine K alone 259 MB)"}
 
 
 def peaks():
@@ -250,28 +259,49 @@ def extra_adjoint(A, W):
     return out
 
 
-def oracle_sample(reps=1):
-    """Oracle set-up + PCG to 1e-8 on the scaled-down beam; seconds per
-    solution scaled by the dof count to the full workload."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_full():
+    """One whole oracle solution of the bench workload: FE assembly, set-up
+    (Algorithm 1) and PCG to 1e-8; (seconds of set-up + solve, iterations).
+    The oracle's row loops run on all host cores (OpenMP)."""
     import oracle as orc
     import workloads as W
-    p = W.beam(*SAMPLE_DIMS)
+    p = W.beam()
     K, nm = orc.assemble(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.nu, p.E, p.clamp_axis)
     V0 = orc.rbm(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, nm)
     f = orc.load_end_shear(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.shear_total, nm)
-    ts = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        H = orc.Hierarchy(K, V0)
-        x, it, rr, rc = H.pcg(f, RTOL)
-        ts.append(time.perf_counter() - t0)
-        del H
-    full = W.beam()
-    scale = (3.0 * full.free_nodes()) / (3.0 * p.free_nodes())
-    sec = min(ts) * scale
-    sample = ("oracle set-up + PCG to 1e-8 on beam %dx%dx%d (%d dofs, same recipe), %.2f s, "
-              "scaled by dofs x%.2f to 128x32x32" % (SAMPLE_DIMS + (3 * p.free_nodes(), min(ts), scale)))
-    return 1.0 / sec, sample, it
+    t0 = time.perf_counter()
+    H = orc.Hierarchy(K, V0)
+    x, it, rr, rc = H.pcg(f, RTOL)
+    sec = time.perf_counter() - t0
+    del H
+    if rc != 0:
+        raise RuntimeError("oracle PCG did not converge: %s" % rc)
+    return sec, it
+
+
+def oracle_baseline():
+    """cpu_baseline of the GPU arm: the oracle on the whole workload, run in a
+    child process (its OpenMP threads stay out of the GPU process)."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-once"], capture_output=True,
+                       text=True, timeout=1800, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": 1.0 / d["sec"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
+            "sample": "the whole workload: oracle set-up + PCG to 1e-8 on the 128x32x32 beam (%d its), "
+                      "%.2f s, OpenMP on %d host cores" % (d["it"], d["sec"], d["cores"])}
+
+
+def run_oracle_once(args):
+    sec, it = oracle_full()
+    print(json.dumps({"sec": sec, "it": it, "cores": host_cores()}), flush=True)
 
 
 def run_reference(args):
@@ -279,23 +309,72 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(1)
+        oracle_full()
     t0 = time.perf_counter()
-    vals = []
+    secs, its = [], []
     for _ in range(args.steps):
-        v, sample, it = oracle_sample(1)
-        vals.append(v)
+        sec, it = oracle_full()
+        secs.append(sec)
+        its.append(it)
     wall = time.perf_counter() - t0
-    value = float(sum(vals) / len(vals))
+    ms = 1e3 * sum(secs) / len(secs)
+    value = 1e3 / ms
+    cores = host_cores()
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": "cantilever beam 128x32x32 Q1 hex, lognormal E, "
-                                                       "FP64, rtol 1e-8 (oracle on a scaled sample)"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "data": "synthetic", "config": workload_config(),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "each step the whole workload: oracle set-up + PCG to 1e-8 on the "
+                                      "128x32x32 beam (%d its), OpenMP on %d host cores" % (its[-1], cores)},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": wall}
     print(json.dumps(out), flush=True)
+
+
+def level_sizes(S):
+    """Per level: (block rows, nnzb A, nnzb G, nnzb P, coarse block rows)."""
+    out = []
+    for k in range(S.nlev):
+        i = S.level_info(k)
+        out.append((i["nr"], i["nnzb_A"], i["nnzb_G"], i["nnzb_P"], i["nc"]))
+    return out
+
+
+def vcycle_work(levels, prec):
+    """Algorithmic bytes and fused multiply-adds of one PCG iteration: the FP64
+    CG operator product and vector kernels, plus one V(1,1)-cycle (per level:
+    G, G^T, A twice each, R and P once, every matrix streamed once per product
+    with its column indices, row pointers and slice offsets, every vector read
+    or written once per product; the coarse level one dense product).  Values
+    8 B (FP64), 4 B (FP32) or 2 B (bf16 G, G^T, P, R); V-cycle vectors 8 or 4 B."""
+    sv_a = 8 if prec == "fp64" else 4
+    sv_g = {"fp64": 8, "fp32": 4, "bf16gp": 2}[prec]
+    w = 8 if prec == "fp64" else 4
+
+    def mat(nr, nnzb, sv):
+        return nnzb * (9 * sv + 4) + 4 * (nr + 1) + 4 * ((nr + 31) // 32 + 1)
+
+    nr0, nnzb0 = levels[0][0], levels[0][1]
+    n0 = 3 * nr0
+    by = mat(nr0, nnzb0, 8) + 16 * n0            # CG operator q = K p
+    fma = 9 * nnzb0
+    mixed = prec != "fp64"
+    by += 16 * n0                                 # p.q
+    by += (48 + (4 if mixed else 0)) * n0         # x, r updates, r.r (+ FP32 copy of r)
+    by += (28 if mixed else 16) * n0              # r.z (+ FP64 copy of z, r.z_old)
+    by += (32 if mixed else 24) * n0              # p = z + beta p (+ z_old)
+    for k, (nr, na, ng, npb, nc) in enumerate(levels):
+        n = 3 * nr
+        if k == len(levels) - 1:
+            by += 8 * n * n + 2 * w * n
+            fma += n * n
+            continue
+        by += 2 * mat(nr, ng, sv_g) + 2 * mat(nr, ng, sv_g) + 2 * mat(nr, na, sv_a)
+        by += mat(nr, npb, sv_g) + mat(nc, npb, sv_g)
+        by += w * (18 * n + 2 * 3 * nc)
+        fma += 9 * (4 * ng + 2 * na + 2 * npb)
+    return by, fma
 
 
 def run_ours(args):
@@ -350,36 +429,60 @@ def run_ours(args):
     stats = S.stats()
     clocks = clk.summary()
 
-    # dominant kernel of the step: the set-up's FP64 product of A_0 with the
-    # n_tv test-space columns (the S = G A G^T products of Algorithm 4); FP64
-    # FMA bound, timed with CUDA events on the handle's stream right after the
-    # timed region, on the same hierarchy
     pk = peaks()
     hbm = pk.get("hbm_gbs")
+    hpk = hbm if hbm else 6800.0
+    hsrc = "measured" if hbm else "fallback"
+    levels = level_sizes(S)
+    nnzb0 = levels[0][1]
+    # dominant kernel of the step: the solve phase's sparse product k_sellmv
+    # (all its launches together hold the largest share of the step's launch
+    # time), measured on its largest launch, the FP64 product with the level-0
+    # K.  A 3x3 FP64 block brings 76 B for 9 FMAs (8.4 B per FMA), less than
+    # the 10.7 B per FMA at which HBM and the FP64 pipe balance: its roof is
+    # the FP64 pipe ("alu"); the HBM fraction is reported beside it
+    spmv_ms, spmv_bytes = S.bench_spmv(0, "A", a64=True, reps=50)
+    gbps = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    spmv_flops = 18.0 * nnzb0
+    spmv_tf = spmv_flops / (spmv_ms * 1e-3) / 1e12
+    roofline = {"kernel": "amg::k_sellmv (solve-phase sparse product; level-0 K x, FP64)", "bound": "alu",
+                "achieved": spmv_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": spmv_tf / FP64_TFLOPS,
+                "traffic": TRAFFIC.get("k_sellmv_fp64_level0"), "peak_source": FP64_PEAK_SOURCE,
+                "ms_per_launch": spmv_ms, "flops_per_launch": spmv_flops, "bytes_per_launch": spmv_bytes,
+                "hbm": {"achieved": gbps, "peak": hpk, "unit": "GB/s", "frac": gbps / hpk, "peak_source": hsrc}}
+    # the set-up's FP64 product of A_0 with the n_tv test-space columns (the
+    # S = G A G^T products of Algorithm 4)
     t_tv = S.params.n_tv
-    nnzb0 = S.level_info(0)["nnzb_A"]
     ms_c, by_c = S.bench_spmv(0, "A_cols", reps=20)
     flops_c = 18.0 * nnzb0 * t_tv
     ach = flops_c / (ms_c * 1e-3) / 1e12
-    roofline = {"kernel": "det::k_spmv_cols (set-up product A_0 X, %d FP64 columns)" % t_tv, "bound": "alu",
-                "achieved": ach, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_TFLOPS,
-                "traffic": TRAFFIC.get("k_spmv_cols"), "peak_source": FP64_PEAK_SOURCE,
-                "ms_per_launch": ms_c, "flops_per_launch": flops_c, "bytes_per_launch": by_c}
-    # the solve phase's FP64 product of the CG operator (level-0 K): a 3x3
-    # FP64 block brings 76 B for 9 FMAs (8.4 B per FMA), less than the 10.7 B
-    # per FMA at which HBM and the FP64 pipe balance, so its roof is the FP64
-    # pipe; the HBM fraction is reported beside it
-    spmv_ms, spmv_bytes = S.bench_spmv(0, "A", a64=True, reps=50)
-    gbps = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    hpk = hbm if hbm else 6800.0
-    spmv_flops = 18.0 * nnzb0
-    spmv_tf = spmv_flops / (spmv_ms * 1e-3) / 1e12
-    roofline_spmv = {"kernel": "amg::k_sellmv (level-0 K x, FP64)", "bound": "alu", "achieved": spmv_tf,
-                     "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": spmv_tf / FP64_TFLOPS,
-                     "traffic": TRAFFIC.get("k_sellmv"), "peak_source": FP64_PEAK_SOURCE,
-                     "ms_per_launch": spmv_ms, "flops_per_launch": spmv_flops, "bytes_per_launch": spmv_bytes,
-                     "hbm": {"achieved": gbps, "peak": hpk, "unit": "GB/s", "frac": gbps / hpk,
-                             "peak_source": "measured" if hbm else "fallback"}}
+    roofline_cols = {"kernel": "det::k_spmv_cols (set-up product A_0 X, %d FP64 columns)" % t_tv, "bound": "alu",
+                     "achieved": ach, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_TFLOPS,
+                     "traffic": TRAFFIC.get("k_spmv_cols"), "peak_source": FP64_PEAK_SOURCE,
+                     "ms_per_launch": ms_c, "flops_per_launch": flops_c, "bytes_per_launch": by_c}
+    # the largest set-up kernel: the first aFSAI pass on A_0 (FP64 issue bound;
+    # dense row systems of varying size, so no byte or flop count per unit)
+    fsai_ms, _ = S.bench_spmv(0, "fsai", reps=3)
+    setup_ms = 1e3 * sum(st_setup) / len(st_setup)
+    roofline_fsai = {"kernel": "det::k_fsai (first aFSAI pass on A_0, Algorithm 3)", "bound": "alu",
+                     "ms_per_launch": fsai_ms, "share_of_setup": fsai_ms / setup_ms, "share_of_step": fsai_ms / ms,
+                     "fp64_lane_frac_ncu": FSAI_LANE_FRAC}
+    # the whole PCG iteration (CG operator, vector kernels and one V-cycle)
+    # against its algorithmic bytes and FMAs, from the per-level sizes
+    sol_ms = 1e3 * sum(st_solve) / len(st_solve)
+    it_avg = sum(its) / len(its)
+
+    def vc_line(prec, ms_it):
+        by, fm = vcycle_work(levels, prec)
+        d = {"bytes_per_it": by, "fma_per_it": fm, "ms_per_it": ms_it, "GBps": by / (ms_it * 1e-3) / 1e9}
+        d["hbm_frac"] = d["GBps"] / hpk
+        if prec == "fp64":
+            d["fp64_tflops"] = 2.0 * fm / (ms_it * 1e-3) / 1e12
+            d["fp64_frac"] = d["fp64_tflops"] / FP64_TFLOPS
+        return d
+
+    roofline_vcycle = {"note": "solve time / iterations (includes the first V-cycle and the true-residual check)",
+                       args.prec: vc_line(args.prec, sol_ms / it_avg)}
     # FP32 V-cycle of the same configuration (not part of value)
     fp32 = None
     if args.prec == "fp64" and not args.no_compare:
@@ -396,8 +499,15 @@ def run_ours(args):
         s32 = S32.stats()
         err = float(torch.linalg.norm(x32 - x) / torch.linalg.norm(x))
         ms32, by32 = S32.bench_spmv(0, "A", a64=False, reps=50)
+        levels32 = level_sizes(S32)
+        by32it, fm32it = vcycle_work(levels32, "fp32")
+        ms32it = s32["T_s"] * 1e3 / it32
+        roofline_vcycle["fp32"] = {"bytes_per_it": by32it, "fma_per_it": fm32it, "ms_per_it": ms32it,
+                                   "GBps": by32it / (ms32it * 1e-3) / 1e9,
+                                   "hbm_frac": by32it / (ms32it * 1e-3) / 1e9 / hpk}
         fp32 = {"ms_per_step": e2.elapsed_time(e3) / args.steps, "n_it": it32,
                 "solve_ms": s32["T_s"] * 1e3, "vcycles_per_s": it32 / s32["T_s"],
+                "restarts": s32["restarts"], "true_relres": s32["relres_true"],
                 "rel_diff_vs_fp64_solution": err,
                 "spmv_level0": {"kernel": "amg::k_sellmv (level-0 K x, FP32)", "ms_per_launch": ms32,
                                 "bytes_per_launch": by32, "GBps": by32 / (ms32 * 1e-3) / 1e9,
@@ -441,8 +551,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, sample, it_o = oracle_sample(2)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = oracle_baseline()
 
     if rank != 0:
         return
@@ -451,20 +560,22 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
         "data": "synthetic",
-        "config": {"workload": "cantilever beam 128x32x32 Q1 hex (%d dofs), x=0 clamped, tip shear, "
-                               "lognormal E (mu 0, sigma 1), nu 0.3; set-up + PCG to 1e-8, %s V-cycle"
-                               % (n3, args.prec.upper()),
-                   "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (fine K alone %.0f MB)" % (vals.numel() * 8 / 1e6)},
+        "config": workload_config(n3) if args.prec == "fp64" else
+                  dict(workload_config(n3), workload=workload_config(n3)["workload"] + " CG, %s V-cycle"
+                       % args.prec.upper()),
+        "parallelism": "%d independent replicas" % ws if ws > 1 else "single GPU",
         "solve": {"n_it": int(round(sum(its) / len(its))), "setup_ms": 1e3 * sum(st_setup) / len(st_setup),
-                  "solve_ms": 1e3 * sum(st_solve) / len(st_solve),
+                  "solve_ms": 1e3 * sum(st_solve) / len(st_solve), "true_relres": stats["relres_true"],
+                  "rec_relres": stats["relres_rec"], "restarts": stats["restarts"],
                   "vcycles_per_s": sum(its) / sum(st_solve),
                   "levels": stats["nlev"], "C_gd": stats["C_gd"], "C_op": stats["C_op"],
                   "C_fs": stats["C_fs"],
                   "setup_phases_ms": {k: 1e3 * stats[k] for k in ("T_sm", "T_ts", "T_cs", "T_pl", "T_rap")}},
         "fp32_vcycle": fp32,
         "roofline": roofline,
-        "roofline_spmv": roofline_spmv,
+        "roofline_vcycle": roofline_vcycle,
+        "roofline_setup_cols": roofline_cols,
+        "roofline_fsai": roofline_fsai,
         "configs": extras,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -576,10 +687,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the slab, batched and adjoint runs")
+    ap.add_argument("--oracle-once", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.single:
+    if args.oracle_once:
+        run_oracle_once(args)
+    elif args.single:
         run_single(args)
     elif args.sweep:
         run_sweep(args)

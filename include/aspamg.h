@@ -180,8 +180,10 @@ int amg_vcycle(amg_handle h, const double *y, double *z);
  * launches with CUDA events on the handle's stream.  which = 5 times instead
  * the set-up's FP64 product of A_lev with n_tv columns (the kernel the
  * test-space iteration of Algorithm 4 applies S = G A G^T with; 18 nnzb n_tv
- * flops per launch).  *ms = average launch time, *bytes = algorithmic bytes
- * of one launch (values, column indices and row pointers once, x and y once
+ * flops per launch).  which = 6 times the first aFSAI pass of Algorithm 3
+ * on A_lev (k_g steps from the identity pattern; *bytes = 0), lev below the
+ * last level.  *ms = average launch time, *bytes = algorithmic bytes of one
+ * launch (values, column indices and row pointers once, x and y once
  * each). */
 int amg_bench_spmv(amg_handle h, int lev, int which, int prec_a64, int reps,
                    double *ms, double *bytes);

@@ -31,14 +31,15 @@ OK, ERR_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_MEM, ERR_COARSEN
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, no contraction); returns the .so path."""
+    """Compile the oracle with gcc (FP64, no contraction, OpenMP row loops);
+    returns the .so path."""
     srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "oracle.h")]
     if not force and os.path.exists(_LIB):
         if os.path.getmtime(_LIB) >= max(os.path.getmtime(s) for s in srcs):
             return _LIB
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB + ".%d.tmp" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
            "-fPIC", "-shared", "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)

@@ -188,17 +188,22 @@ static void vcycle_level(const or_hier *h, int k, const double *y, double *z) {
   double *zc = (double *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(double));
   or_spmv(&L->G, y, t);
   or_spmv(&L->GT, t, s);
+  #pragma omp parallel for schedule(static) if (n > 65536)
   for (int i = 0; i < n; ++i) s[i] = L->omega * s[i];
   or_spmv(&L->A, s, r);
+  #pragma omp parallel for schedule(static) if (n > 65536)
   for (int i = 0; i < n; ++i) r[i] = y[i] - r[i];
   or_spmv(&L->R, r, yc);
   vcycle_level(h, k + 1, yc, zc);
   or_spmv(&L->P, zc, u);
+  #pragma omp parallel for schedule(static) if (n > 65536)
   for (int i = 0; i < n; ++i) s[i] = s[i] + u[i];
   or_spmv(&L->A, s, r);
+  #pragma omp parallel for schedule(static) if (n > 65536)
   for (int i = 0; i < n; ++i) r[i] = y[i] - r[i];
   or_spmv(&L->G, r, t);
   or_spmv(&L->GT, t, u);
+  #pragma omp parallel for schedule(static) if (n > 65536)
   for (int i = 0; i < n; ++i) z[i] = s[i] + L->omega * u[i];
   free(t); free(s); free(r); free(u); free(yc); free(zc);
 }
@@ -248,6 +253,7 @@ int or_pcg(const or_hier *h, const double *b, double *x, double rtol,
         break;
       }
       const double alpha = rz / pq;
+      #pragma omp parallel for schedule(static) if (n > 65536)
       for (int i = 0; i < n; ++i) {
         x[i] = x[i] + alpha * p[i];
         r[i] = r[i] - alpha * q[i];
@@ -258,6 +264,7 @@ int or_pcg(const or_hier *h, const double *b, double *x, double rtol,
       or_vcycle(h, r, z);
       const double rz2 = dot_seq(n, r, z);
       const double beta = rz2 / rz;
+      #pragma omp parallel for schedule(static) if (n > 65536)
       for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
       rz = rz2;
     }

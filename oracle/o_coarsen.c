@@ -48,13 +48,18 @@ static double fro2(int b, const double *M) {
 int or_soc(const obsr *A, int t, const double *V, double *soc) {
   const int b = A->b, nn = A->nr, n = nn * b;
   double *nrm = (double *)malloc((size_t)nn * sizeof(double));
-  double M[9];
+  /* rows are independent (OpenMP may split them; each value is formed by
+   * the same operations) */
+#pragma omp parallel for schedule(static) if (nn > 4096)
   for (int I = 0; I < nn; ++I) {
+    double M[9];
     node_gram(n, b, t, V, I, I, M);
     nrm[I] = sqrt(fro2(b, M));
   }
+#pragma omp parallel for schedule(static) if (nn > 4096)
   for (int I = 0; I < nn; ++I)
     for (int k = A->rowptr[I]; k < A->rowptr[I + 1]; ++k) {
+      double M[9];
       const int J = A->col[k];
       if (J == I) {
         soc[k] = 0.0;

@@ -27,6 +27,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include "oracle.h"
 
@@ -70,128 +73,190 @@ static int cmp_int(const void *a, const void *b) {
   return (x > y) - (x < y);
 }
 
+/* Per-thread work space of one aFSAI row. */
+typedef struct {
+  int *pat, *Q, *cand;
+  double *ghbuf, *M, *L, *rhs, *score;
+  long *mark; /* per node: the row-and-step stamp that last marked it */
+  long stamp;
+} afsai_ws;
+
+/* Row I of aFSAI: its pattern nodes (ascending, *np_out of them, into
+ * pat_out) and its np+1 blocks (pattern blocks, then the diagonal block) into
+ * val_out. */
+static int afsai_row(const obsr *A, const obsr *Gs, int I, int ksteps, int rho, double eps,
+                     int max_nodes, afsai_ws *w, int *np_out, int *pat_out, double *val_out) {
+  const int b = A->b;
+  const int mmax = b * max_nodes + b;
+  int *pat = w->pat, *cand = w->cand;
+  double *score = w->score;
+  double *gh[3];
+  for (int c = 0; c < b; ++c) gh[c] = w->ghbuf + (size_t)c * mmax;
+  double psi[3], psi_old[3];
+  int np = 0;
+  if (Gs)
+    for (int k = Gs->rowptr[I]; k < Gs->rowptr[I + 1]; ++k)
+      if (Gs->col[k] != I && np < max_nodes) pat[np++] = Gs->col[k];
+  int rc = solve_rows(A, I, pat, np, gh, psi, w->M, w->L, w->rhs, w->Q);
+  for (int step = 0; step < ksteps && rc == OR_OK; ++step) {
+    if (np >= max_nodes) break;
+    /* candidates: nodes J < I, outside the pattern, adjacent in A to the
+     * pattern or to I */
+    int nc = 0;
+    ++w->stamp; /* fresh mark for this row and step */
+    const long stamp = w->stamp;
+    for (int j = 0; j < np; ++j) w->mark[pat[j]] = stamp;
+    for (int j = 0; j <= np; ++j) {
+      const int K = (j < np) ? pat[j] : I;
+      for (int k = A->rowptr[K]; k < A->rowptr[K + 1]; ++k) {
+        const int J = A->col[k];
+        if (J < I && w->mark[J] != stamp) {
+          w->mark[J] = stamp;
+          cand[nc++] = J;
+        }
+      }
+    }
+    qsort(cand, nc, sizeof(int), cmp_int);
+    for (int t = 0; t < nc; ++t) {
+      const int J = cand[t];
+      double s = 0.0;
+      for (int c = 0; c < b; ++c)
+        for (int d = 0; d < b; ++d) {
+          double g = 0.0;
+          for (int j = 0; j < np; ++j) {
+            const double *blk = or_bsr_find(A, J, pat[j]);
+            if (blk)
+              for (int e = 0; e < b; ++e) g = fma(blk[d * b + e], gh[c][b * j + e], g);
+          }
+          const double *blk = or_bsr_find(A, J, I);
+          if (blk) {
+            for (int e = 0; e < c; ++e) g = fma(blk[d * b + e], gh[c][b * np + e], g);
+            g = g + blk[d * b + c] * 1.0;
+          }
+          s = fma(g, g, s);
+        }
+      score[t] = s;
+    }
+    /* take up to rho best (score > 0, ties to the smaller node) */
+    int want = rho < max_nodes - np ? rho : max_nodes - np, got = 0;
+    for (int p = 0; p < want; ++p) {
+      int best = -1;
+      for (int t = 0; t < nc; ++t)
+        if (score[t] > 0.0 && (best < 0 || score[t] > score[best])) best = t;
+      if (best < 0) break;
+      pat[np + got++] = cand[best];
+      score[best] = -1.0;
+    }
+    if (got == 0) break;
+    np += got;
+    qsort(pat, np, sizeof(int), cmp_int);
+    for (int c = 0; c < b; ++c) psi_old[c] = psi[c];
+    rc = solve_rows(A, I, pat, np, gh, psi, w->M, w->L, w->rhs, w->Q);
+    if (rc) break;
+    int stalled = 1;
+    for (int c = 0; c < b; ++c)
+      if (psi_old[c] - psi[c] > eps * psi_old[c]) stalled = 0;
+    if (stalled) break;
+  }
+  if (rc) return rc;
+  /* row I: pattern blocks then the diagonal block */
+  for (int j = 0; j <= np; ++j) {
+    double *blk = val_out + (size_t)j * b * b;
+    if (j < np) pat_out[j] = pat[j];
+    for (int c = 0; c < b; ++c) {
+      const double rs = 1.0 / sqrt(psi[c]); /* g / sqrt(psi) as g times 1 / sqrt(psi) */
+      for (int d = 0; d < b; ++d) {
+        double g;
+        if (j < np) g = gh[c][b * j + d];
+        else g = (d < c) ? gh[c][b * np + d] : (d == c ? 1.0 : 0.0);
+        blk[c * b + d] = (j < np || d <= c) ? g * rs : 0.0;
+      }
+    }
+  }
+  *np_out = np;
+  return OR_OK;
+}
+
+/* aFSAI of A continuing from the pattern of Gs (NULL: from the identity).
+ * Rows are independent: with OpenMP a batch of rows is computed by several
+ * threads (each row exactly as in a single thread, into its own slot), and
+ * the batch is appended to G in row order. */
 int or_afsai(const obsr *A, const obsr *Gs, int ksteps, int rho, double eps,
              int max_nodes, obsr *G) {
-  const int b = A->b, n = A->nr;
+  const int b = A->b, n = A->nr, bb = b * b;
   const int mmax = b * max_nodes + b;
+  const int batch = 8192;
   int rc = OR_OK;
-  int *pat = (int *)malloc((size_t)(max_nodes + 1) * sizeof(int));
-  double *ghbuf = (double *)calloc((size_t)b * mmax, sizeof(double));
-  double *gh[3];
-  for (int c = 0; c < b; ++c) gh[c] = ghbuf + (size_t)c * mmax;
-  double psi[3], psi_old[3];
-  double *M = (double *)malloc((size_t)mmax * mmax * sizeof(double));
-  double *L = (double *)malloc((size_t)mmax * mmax * sizeof(double));
-  double *rhs = (double *)malloc((size_t)mmax * sizeof(double));
-  int *Q = (int *)malloc((size_t)mmax * sizeof(int));
-  long *mark = (long *)malloc((size_t)n * sizeof(long));
-  int *cand = (int *)malloc((size_t)n * sizeof(int));
-  double *score = (double *)malloc((size_t)n * sizeof(double));
-  for (int i = 0; i < n; ++i) mark[i] = -1;
-  long stamp = -1;
+  int nthr = 1;
+#ifdef _OPENMP
+  nthr = omp_get_max_threads();
+#endif
+  afsai_ws *ws = (afsai_ws *)calloc((size_t)nthr, sizeof(afsai_ws));
+  for (int t = 0; t < nthr; ++t) {
+    ws[t].pat = (int *)malloc((size_t)(max_nodes + 1) * sizeof(int));
+    ws[t].ghbuf = (double *)calloc((size_t)b * mmax, sizeof(double));
+    ws[t].M = (double *)malloc((size_t)mmax * mmax * sizeof(double));
+    ws[t].L = (double *)malloc((size_t)mmax * mmax * sizeof(double));
+    ws[t].rhs = (double *)malloc((size_t)mmax * sizeof(double));
+    ws[t].Q = (int *)malloc((size_t)mmax * sizeof(int));
+    ws[t].mark = (long *)malloc((size_t)n * sizeof(long));
+    ws[t].cand = (int *)malloc((size_t)n * sizeof(int));
+    ws[t].score = (double *)malloc((size_t)n * sizeof(double));
+    for (int i = 0; i < n; ++i) ws[t].mark[i] = -1;
+    ws[t].stamp = -1;
+  }
+  int *bnp = (int *)malloc((size_t)batch * sizeof(int));
+  int *bpat = (int *)malloc((size_t)batch * max_nodes * sizeof(int));
+  double *bval = (double *)malloc((size_t)batch * (max_nodes + 1) * bb * sizeof(double));
+  int *brc = (int *)malloc((size_t)batch * sizeof(int));
   /* output rows, grown as needed */
   size_t cap = (size_t)n * 4 + 16, used = 0;
   int *gcol = (int *)malloc(cap * sizeof(int));
-  double *gval = (double *)malloc(cap * b * b * sizeof(double));
+  double *gval = (double *)malloc(cap * bb * sizeof(double));
   int *growptr = (int *)malloc(((size_t)n + 1) * sizeof(int));
   growptr[0] = 0;
 
-  for (int I = 0; I < n && rc == OR_OK; ++I) {
-    int np = 0;
-    if (Gs)
-      for (int k = Gs->rowptr[I]; k < Gs->rowptr[I + 1]; ++k)
-        if (Gs->col[k] != I && np < max_nodes) pat[np++] = Gs->col[k];
-    rc = solve_rows(A, I, pat, np, gh, psi, M, L, rhs, Q);
-    for (int step = 0; step < ksteps && rc == OR_OK; ++step) {
-      if (np >= max_nodes) break;
-      /* candidates: nodes J < I, outside the pattern, adjacent in A to the
-       * pattern or to I */
-      int nc = 0;
-      ++stamp; /* fresh mark for this row and step */
-      for (int j = 0; j < np; ++j) mark[pat[j]] = stamp;
-      for (int j = 0; j <= np; ++j) {
-        const int K = (j < np) ? pat[j] : I;
-        for (int k = A->rowptr[K]; k < A->rowptr[K + 1]; ++k) {
-          const int J = A->col[k];
-          if (J < I && mark[J] != stamp) {
-            mark[J] = stamp;
-            cand[nc++] = J;
-          }
-        }
-      }
-      qsort(cand, nc, sizeof(int), cmp_int);
-      for (int t = 0; t < nc; ++t) {
-        const int J = cand[t];
-        double s = 0.0;
-        for (int c = 0; c < b; ++c)
-          for (int d = 0; d < b; ++d) {
-            double g = 0.0;
-            for (int j = 0; j < np; ++j) {
-              const double *blk = or_bsr_find(A, J, pat[j]);
-              if (blk)
-                for (int e = 0; e < b; ++e) g = fma(blk[d * b + e], gh[c][b * j + e], g);
-            }
-            const double *blk = or_bsr_find(A, J, I);
-            if (blk) {
-              for (int e = 0; e < c; ++e) g = fma(blk[d * b + e], gh[c][b * np + e], g);
-              g = g + blk[d * b + c] * 1.0;
-            }
-            s = fma(g, g, s);
-          }
-        score[t] = s;
-      }
-      /* take up to rho best (score > 0, ties to the smaller node) */
-      int want = rho < max_nodes - np ? rho : max_nodes - np, got = 0;
-      for (int p = 0; p < want; ++p) {
-        int best = -1;
-        for (int t = 0; t < nc; ++t)
-          if (score[t] > 0.0 && (best < 0 || score[t] > score[best])) best = t;
-        if (best < 0) break;
-        pat[np + got++] = cand[best];
-        score[best] = -1.0;
-      }
-      if (got == 0) break;
-      np += got;
-      qsort(pat, np, sizeof(int), cmp_int);
-      for (int c = 0; c < b; ++c) psi_old[c] = psi[c];
-      rc = solve_rows(A, I, pat, np, gh, psi, M, L, rhs, Q);
-      if (rc) break;
-      int stalled = 1;
-      for (int c = 0; c < b; ++c)
-        if (psi_old[c] - psi[c] > eps * psi_old[c]) stalled = 0;
-      if (stalled) break;
+  for (int I0 = 0; I0 < n && rc == OR_OK; I0 += batch) {
+    const int nb = n - I0 < batch ? n - I0 : batch;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int q = 0; q < nb; ++q) {
+      int t = 0;
+#ifdef _OPENMP
+      t = omp_get_thread_num();
+#endif
+      brc[q] = afsai_row(A, Gs, I0 + q, ksteps, rho, eps, max_nodes, &ws[t], &bnp[q],
+                         bpat + (size_t)q * max_nodes, bval + (size_t)q * (max_nodes + 1) * bb);
     }
-    if (rc) break;
-    /* write row I: pattern blocks then the diagonal block */
-    if (used + np + 1 > cap) {
-      while (used + np + 1 > cap) cap *= 2;
-      gcol = (int *)realloc(gcol, cap * sizeof(int));
-      gval = (double *)realloc(gval, cap * b * b * sizeof(double));
-    }
-    for (int j = 0; j <= np; ++j) {
-      double *blk = gval + (used + j) * b * b;
-      gcol[used + j] = (j < np) ? pat[j] : I;
-      for (int c = 0; c < b; ++c) {
-        const double rs = 1.0 / sqrt(psi[c]); /* g / sqrt(psi) as g times 1 / sqrt(psi) */
-        for (int d = 0; d < b; ++d) {
-          double g;
-          if (j < np) g = gh[c][b * j + d];
-          else g = (d < c) ? gh[c][b * np + d] : (d == c ? 1.0 : 0.0);
-          blk[c * b + d] = (j < np || d <= c) ? g * rs : 0.0;
-        }
+    for (int q = 0; q < nb; ++q) {
+      if (brc[q]) {
+        rc = brc[q];
+        break;
       }
+      const int I = I0 + q, np = bnp[q];
+      if (used + np + 1 > cap) {
+        while (used + np + 1 > cap) cap *= 2;
+        gcol = (int *)realloc(gcol, cap * sizeof(int));
+        gval = (double *)realloc(gval, cap * bb * sizeof(double));
+      }
+      for (int j = 0; j < np; ++j) gcol[used + j] = bpat[(size_t)q * max_nodes + j];
+      gcol[used + np] = I;
+      memcpy(gval + used * bb, bval + (size_t)q * (max_nodes + 1) * bb, (size_t)(np + 1) * bb * sizeof(double));
+      used += np + 1;
+      growptr[I + 1] = (int)used;
     }
-    used += np + 1;
-    growptr[I + 1] = (int)used;
   }
   if (rc == OR_OK) {
     or_bsr_alloc(G, n, n, b, (int)used);
     memcpy(G->rowptr, growptr, ((size_t)n + 1) * sizeof(int));
     memcpy(G->col, gcol, used * sizeof(int));
-    memcpy(G->val, gval, used * b * b * sizeof(double));
+    memcpy(G->val, gval, used * bb * sizeof(double));
   }
-  free(pat); free(ghbuf); free(M); free(L); free(rhs); free(Q);
-  free(mark); free(cand); free(score); free(gcol); free(gval); free(growptr);
+  for (int t = 0; t < nthr; ++t) {
+    free(ws[t].pat); free(ws[t].ghbuf); free(ws[t].M); free(ws[t].L); free(ws[t].rhs);
+    free(ws[t].Q); free(ws[t].mark); free(ws[t].cand); free(ws[t].score);
+  }
+  free(ws); free(bnp); free(bpat); free(bval); free(brc);
+  free(gcol); free(gval); free(growptr);
   return rc;
 }
 
@@ -263,14 +328,17 @@ double or_lanczos_lmax(const obsr *A, const obsr *G, const obsr *GT, int m,
     or_spmv(A, t1, t2);
     or_spmv(G, t2, w);
     al[j] = or_dot(n, w, v);
+#pragma omp parallel for schedule(static) if (n > 65536)
     for (int i = 0; i < n; ++i) w[i] = fma(-al[j], v[i], w[i]);
     if (j > 0) {
       const double *vp = Vs + (size_t)(j - 1) * n;
+#pragma omp parallel for schedule(static) if (n > 65536)
       for (int i = 0; i < n; ++i) w[i] = fma(-be[j - 1], vp[i], w[i]);
     }
     /* one classical Gram-Schmidt pass against v_0..v_j: all coefficients
      * from the same w, then w_i - sum_k h_k v_k,i with k ascending */
     for (int k = 0; k <= j; ++k) hk[k] = or_dot(n, w, Vs + (size_t)k * n);
+#pragma omp parallel for schedule(static) if (n > 65536)
     for (int i = 0; i < n; ++i) {
       double s = w[i];
       for (int k = 0; k <= j; ++k) s = fma(-hk[k], Vs[(size_t)k * n + i], s);

@@ -23,6 +23,10 @@
  * the Ritz rotation Z <- Z U brings S Z <- (S Z) U.  The one product with S
  * per column and iteration is S g.
  *
+ * Loops over the entries of a vector may run on several OpenMP threads: each
+ * entry is still formed by the same operations, so the results do not depend
+ * on the number of threads.
+ *
  * All inner products use the fixed-order or_dot, all sparse products the
  * fixed-order or_spmv; every multiply-add of a vector update (and of the
  * dense triangular solves and rotations) is one fused multiply-add, and a
@@ -51,11 +55,13 @@ void or_mgs(int n, int t, double *V) {
     for (int i = 0; i < j; ++i) {
       const double *vi = V + (size_t)i * n;
       const double r = or_dot(n, vi, vj);
+      #pragma omp parallel for schedule(static) if (n > 65536)
       for (int k = 0; k < n; ++k) vj[k] = fma(-r, vi[k], vj[k]);
     }
     const double nr = sqrt(or_dot(n, vj, vj));
     if (nr > 0.0) {
       const double rn = 1.0 / nr;
+      #pragma omp parallel for schedule(static) if (n > 65536)
       for (int k = 0; k < n; ++k) vj[k] = vj[k] * rn;
     }
   }
@@ -243,6 +249,7 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
     const double *v = V0 + (size_t)i * n;
     double *z = Z + (size_t)i * n;
     apply_s(A, G, GT, v, Gv, t1, t2);
+    #pragma omp parallel for schedule(static) if (n > 65536)
     for (int k = 0; k < n; ++k) z[k] = v[k] - Gv[k];
   }
   or_mgs(n, t, Z);
@@ -253,6 +260,7 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
     double *sz = SZ + (size_t)i * n, *sp = SP + (size_t)i * n;
     apply_s(A, G, GT, z, sz, t1, t2);
     const double q = or_dot(n, z, sz);
+    #pragma omp parallel for schedule(static) if (n > 65536)
     for (int k = 0; k < n; ++k) p[k] = 2.0 * fma(-q, z[k], sz[k]);
     apply_s(A, G, GT, p, sp, t1, t2);
     f[i] = 1.0;
@@ -274,6 +282,7 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
        * ascending from 0 */
       for (int w = 0; w < 2; ++w) {
         double *X = w == 0 ? Z : SZ;
+        #pragma omp parallel for schedule(static) if (n > 65536)
         for (int k = 0; k < n; ++k) {
           double row[64];
           for (int j = 0; j < t; ++j) {
@@ -293,6 +302,7 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
       const double d = or_dot(n, p, p), e = or_dot(n, z, sz), fi = f[i];
       if (!(b > 0.0)) continue;
       const double alpha = or_rq_line_min(a, b, c, d, e, fi);
+      #pragma omp parallel for schedule(static) if (n > 65536)
       for (int k = 0; k < n; ++k) {
         z[k] = fma(alpha, p[k], z[k]);
         sz[k] = fma(alpha, sp[k], sz[k]);
@@ -300,9 +310,11 @@ int or_srqcg(const obsr *A, const obsr *G, const obsr *GT, int kmax,
       const double fn = or_dot(n, z, z);
       const double q = or_dot(n, z, sz) / fn;
       const double rf = 1.0 / fn;
+      #pragma omp parallel for schedule(static) if (n > 65536)
       for (int k = 0; k < n; ++k) Gv[k] = (2.0 * fma(-q, z[k], sz[k])) * rf;
       apply_s(A, G, GT, Gv, SG, t1, t2);
       const double beta = -(or_dot(n, Gv, sp) / b);
+      #pragma omp parallel for schedule(static) if (n > 65536)
       for (int k = 0; k < n; ++k) {
         p[k] = fma(beta, p[k], Gv[k]);
         sp[k] = fma(beta, sp[k], SG[k]);

@@ -2,6 +2,11 @@
  * Oracle utilities: counter-based random numbers, the fixed-order dot product,
  * block sparse matrix-vector products, transposition and small dense Cholesky.
  * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * OpenMP (when compiled in) only splits loops whose iterations write disjoint
+ * outputs (matrix rows, dot-product chunks, Cholesky entries of one column);
+ * every value is formed by the same operations in the same order as in a
+ * single thread.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -42,18 +47,32 @@ static void exchange32(double *v) {
   }
 }
 
+static double chunk_sum(int n, const double *x, const double *y, int base) {
+  double lane[32];
+  for (int l = 0; l < 32; ++l) {
+    double s = 0.0;
+    for (int i = base + l; i < base + 1024 && i < n; i += 32) s = fma(x[i], y[i], s);
+    lane[l] = s;
+  }
+  exchange32(lane);
+  return lane[0];
+}
+
+/* The chunk sums are independent of each other; with OpenMP they are formed
+ * by several threads (each one exactly as above) and then combined in chunk
+ * order, so the result does not depend on the number of threads. */
 double or_dot(int n, const double *x, const double *y) {
   double top[32];
   for (int l = 0; l < 32; ++l) top[l] = 0.0;
-  for (int c = 0, base = 0; base < n; ++c, base += 1024) {
-    double lane[32];
-    for (int l = 0; l < 32; ++l) {
-      double s = 0.0;
-      for (int i = base + l; i < base + 1024 && i < n; i += 32) s = fma(x[i], y[i], s);
-      lane[l] = s;
-    }
-    exchange32(lane);
-    top[c % 32] = top[c % 32] + lane[0];
+  const int nch = (n + 1023) / 1024;
+  if (nch <= 64) {
+    for (int c = 0; c < nch; ++c) top[c % 32] = top[c % 32] + chunk_sum(n, x, y, c * 1024);
+  } else {
+    double *cs = (double *)malloc((size_t)nch * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < nch; ++c) cs[c] = chunk_sum(n, x, y, c * 1024);
+    for (int c = 0; c < nch; ++c) top[c % 32] = top[c % 32] + cs[c];
+    free(cs);
   }
   exchange32(top);
   return top[0];
@@ -64,6 +83,7 @@ double or_dot(int n, const double *x, const double *y) {
  * from 0. */
 void or_spmv(const obsr *A, const double *x, double *y) {
   const int b = A->b;
+#pragma omp parallel for schedule(static) if (A->nr > 4096)
   for (int I = 0; I < A->nr; ++I) {
     for (int r = 0; r < b; ++r) {
       double s = 0.0;
@@ -142,6 +162,7 @@ int or_chol(int m, const double *M, double *L) {
     if (!(s > 0.0)) return OR_ERR_NOT_SPD;
     const double d = sqrt(s), rho = 1.0 / d;
     L[j * m + j] = d;
+#pragma omp parallel for schedule(static) if (m - j > 512)
     for (int i = j + 1; i < m; ++i) {
       double t = M[i * m + j];
       for (int k = 0; k < j; ++k) t = fma(-L[i * m + k], L[j * m + k], t);

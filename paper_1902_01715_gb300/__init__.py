@@ -290,8 +290,8 @@ class Solver:
         """(ms per launch, algorithmic bytes per launch) of a solve-phase
         sparse product timed with CUDA events on the handle's stream;
         which="A_cols" times the set-up's FP64 product of A with the n_tv
-        test-space columns."""
-        code = {"A": 0, "G": 1, "GT": 2, "P": 3, "R": 4, "A_cols": 5}[which]
+        test-space columns, which="fsai" the first aFSAI pass of the level."""
+        code = {"A": 0, "G": 1, "GT": 2, "P": 3, "R": 4, "A_cols": 5, "fsai": 6}[which]
         ms, by = C.c_double(), C.c_double()
         check(lib().amg_bench_spmv(self._h, level, code, int(a64), reps, C.byref(ms), C.byref(by)),
               "amg_bench_spmv")

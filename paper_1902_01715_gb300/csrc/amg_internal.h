@@ -255,6 +255,7 @@ int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters,
 int vcycle_apply(Handle *h, const double *y, double *z);
 int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes);
 int vcycle_apply_noalloc(Handle *h, const double *y, double *z);
+int bench_fsai(Handle *h, int lev, int reps, double *ms);
 // ---- batched solve (batch.cu) ----
 int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres);
 void free_batch(Handle *h);

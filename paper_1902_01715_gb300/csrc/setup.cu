@@ -692,6 +692,40 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
   return AMG_OK;
 }
 
+// Average time of one first aFSAI pass (k_g steps from the identity pattern,
+// the launch of Algorithm 3 that every set-up makes) on level `lev`, timed
+// with CUDA events on the handle's stream; the pattern is not compacted.
+int bench_fsai(Handle *h, int lev, int reps, double *ms) {
+  const Level &L = *h->lev[lev];
+  const amg_params &p = h->prm;
+  cudaStream_t s = h->stream;
+  const int n = L.A.nr, maxg = p.max_g_nodes;
+  int maxdeg = 0;
+  for (int I = 0; I < n; ++I) maxdeg = std::max(maxdeg, L.A.h_rowptr[I + 1] - L.A.h_rowptr[I]);
+  DBuf<int> np, pat, status;
+  DBuf<double> val;
+  AMG_TRY(np.alloc(n));
+  AMG_TRY(pat.alloc((size_t)n * maxg));
+  AMG_TRY(val.alloc((size_t)n * (maxg + 1) * 9));
+  AMG_TRY(status.alloc(1));
+  AMG_TRY(status.zero(s));
+  det::FsaiOut out{np.p, pat.p, val.p};
+  AMG_TRY(det::fsai(L.A, nullptr, p.k_g, p.rho_g, p.eps_g, maxg, maxdeg, out, status.p, s));
+  cudaEvent_t e0, e1;
+  AMG_CU(cudaEventCreate(&e0));
+  AMG_CU(cudaEventCreate(&e1));
+  AMG_CU(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) AMG_TRY(det::fsai(L.A, nullptr, p.k_g, p.rho_g, p.eps_g, maxg, maxdeg, out, status.p, s));
+  AMG_CU(cudaEventRecord(e1, s));
+  AMG_CU(cudaEventSynchronize(e1));
+  float t = 0.f;
+  AMG_CU(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = (double)t / reps;
+  return AMG_OK;
+}
+
 // Algorithm 3, first part: the aFSAI factor G of the level, then the
 // Lanczos estimate of lambda_max(G A G^T) queued on the second stream into
 // `out` (3 doubles); smoother_finish waits for it.  The test space of the

@@ -643,8 +643,13 @@ int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
 // Average time of one solve-phase sparse product of a level matrix, launched
 // back to back on the handle's stream between CUDA events.
 int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes) {
-  if (lev < 0 || lev >= h->nlev || which < 0 || which > 5 || reps < 1) return AMG_ERR_ARG;
+  if (lev < 0 || lev >= h->nlev || which < 0 || which > 6 || reps < 1) return AMG_ERR_ARG;
   Level &L = *h->lev[lev];
+  if (which == 6) {  // the set-up's first aFSAI pass on A_lev
+    if (lev == h->nlev - 1) return AMG_ERR_ARG;
+    *bytes = 0.0;
+    return bench_fsai(h, lev, reps, ms);
+  }
   if (which == 5) {  // the set-up's FP64 product of A_k with the n_tv test-space columns
     const int t = h->prm.n_tv;
     const size_t n = 3 * (size_t)L.A.nr;

@@ -58,3 +58,35 @@ SMALL = {
     "beam": lambda: W.beam(32, 8, 8),
     "slab": lambda: W.slab(32, 32, 4),
 }
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    den = np.abs(b).max() if b.size else 0.0
+    return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a - b).max() if a.size else 0.0)
+
+
+def compare_hierarchies(S, H):
+    """GPU hierarchy S (library handle) against the oracle's H, level by level:
+    the C/F split and the patterns of A_k, G_k, P_k, R_k bit for bit, their
+    values within 1e-13 relative, omega_k, lambda_1 and the refinement passes
+    exactly, the test spaces within 1e-12 relative."""
+    assert S.nlev == H.nlev, (S.nlev, H.nlev)
+    for k in range(H.nlev):
+        go, oo = S.level_info(k), H.info(k)
+        assert go["nr"] == oo["nr"] and go["nnzb_A"] == oo["nnzb_A"], k
+        Ao = H.matrix(k, "A")
+        rp, col, val = S.level_matrix(k, "A")
+        assert np.array_equal(rp, Ao.rowptr) and np.array_equal(col, Ao.col[:Ao.nnzb]), k
+        assert rel(val, Ao.val[:Ao.nnzb]) <= 1e-13, k
+        if k == H.nlev - 1:
+            continue
+        assert go["npasses"] == oo["npasses"], k
+        assert go["omega"] == oo["omega"] and go["lmax"] == oo["lmax"], k
+        assert np.array_equal(S.level_cf(k), H.cf(k)), k
+        for which in ("G", "P", "R"):
+            Mo = H.matrix(k, which)
+            rp, col, val = S.level_matrix(k, which)
+            assert np.array_equal(rp, Mo.rowptr) and np.array_equal(col, Mo.col[:Mo.nnzb]), (k, which)
+            assert rel(val, Mo.val[:Mo.nnzb]) <= 1e-13, (k, which)
+        assert rel(S.level_testspace(k), H.V(k)) <= 1e-12, k

@@ -137,3 +137,115 @@ def test_padding_generator_statistics(orc):
     assert u.min() >= -1.0 and u.max() < 1.0
     assert abs(u.mean()) < 0.02 and abs(u.var() - 1 / 3) < 0.01
     assert len(np.unique(u)) == len(u)
+
+
+def _mgs_plain(V):
+    """Modified Gram-Schmidt in column order, then unit columns."""
+    V = V.copy()
+    for j in range(V.shape[1]):
+        for i in range(j):
+            V[:, j] -= (V[:, i] @ V[:, j]) * V[:, i]
+        V[:, j] /= np.linalg.norm(V[:, j])
+    return V
+
+
+def _line_min_plain(a, b, c, d, e, f):
+    """The stationary points of rq(alpha) = (e + 2 alpha a + alpha^2 b) /
+    (f + 2 alpha c + alpha^2 d), i.e. the roots of (bc - ad) alpha^2 +
+    (bf - de) alpha + (af - ce) = 0, and the one with the smaller quotient."""
+    qa, qb, qc = b * c - a * d, b * f - d * e, a * f - c * e
+    if qa == 0.0:
+        return -qc / qb if qb != 0.0 else 0.0
+    disc = qb * qb - 4 * qa * qc
+    if disc < 0:
+        return 0.0
+    roots = [(-qb + s * np.sqrt(disc)) / (2 * qa) for s in (1.0, -1.0)]
+    return min(roots, key=lambda al: (e + 2 * al * a + al * al * b) / (f + 2 * al * c + al * al * d))
+
+
+def _srqcg_plain(S, Gd, V0, kmax, k_ritz):
+    """Algorithm 4 as printed, with the dense S = G A G^T applied afresh
+    wherever the algorithm names S Z_i, S P_i (no recurrences), the Rayleigh
+    quotient of a column z as z^T S z / z^T z, f_i = 1 after a Ritz step, the
+    Ritz vectors from scipy (ascending, each signed by its largest entry) and
+    a column with p^T S p <= 0 left as it is."""
+    n, t = V0.shape
+    Z = _mgs_plain(V0 - S @ V0)
+    P = np.empty_like(Z)
+    f = np.ones(t)
+    for i in range(t):
+        z = Z[:, i]
+        q = z @ S @ z
+        P[:, i] = 2 * (S @ z - q * z)
+    for k in range(1, kmax + 1):
+        if k_ritz > 0 and k % k_ritz == 0:
+            lam, U = sla.eigh(Z.T @ S @ Z, Z.T @ Z)
+            for j in range(t):
+                if U[np.argmax(np.abs(U[:, j])), j] < 0:
+                    U[:, j] = -U[:, j]
+            Z = Z @ U
+            f[:] = 1.0
+        for i in range(t):
+            z, p = Z[:, i].copy(), P[:, i].copy()
+            a, b, c, d, e = p @ S @ z, p @ S @ p, p @ z, p @ p, z @ S @ z
+            if not b > 0:
+                continue
+            alpha = _line_min_plain(a, b, c, d, e, f[i])
+            z = z + alpha * p
+            fi = z @ z
+            q = (z @ S @ z) / fi
+            g = 2 * (S @ z - q * z) / fi
+            beta = -(g @ S @ p) / b
+            P[:, i] = g + beta * p
+            Z[:, i] = z
+            f[i] = fi
+    return _mgs_plain(Gd.T @ Z)
+
+
+@pytest.mark.parametrize("b", [1, 3])
+def test_srqcg_matches_plain_algorithm4(orc, b):
+    """The oracle's SRQCG (S Z and S P carried by recurrences, fused
+    multiply-adds, fixed-order sums) against Algorithm 4 restated in numpy with
+    S applied afresh each time: the same test space up to rounding."""
+    A = small_problem(orc, n=3, b=b)
+    G = orc.afsai(A, None, 2, 2 if b == 3 else 4, 1e-3, 24 if b == 3 else 64)
+    GT = orc.transpose(G)
+    Gd, Ad = G.todense(), A.todense()
+    S = Gd @ Ad @ Gd.T
+    n, t = Ad.shape[0], 4
+    V0 = np.random.default_rng(16).normal(size=(n, t))
+    for kmax in (0, 1, 10):
+        V = orc.srqcg(A, G, GT, V0, kmax=kmax, k_ritz=1)
+        Vp = _srqcg_plain(S, Gd, V0, kmax, 1)
+        assert np.abs(V - Vp).max() <= 1e-9, (kmax, np.abs(V - Vp).max())
+    # and without Ritz steps (k_ritz = 0: pure per-column CG on the quotient)
+    V = orc.srqcg(A, G, GT, V0, kmax=10, k_ritz=0)
+    Vp = _srqcg_plain(S, Gd, V0, 10, 0)
+    assert np.abs(V - Vp).max() <= 1e-9
+
+
+def test_coarse_test_space_starts_from_injection(orc):
+    """A coarser level's test space is SRQCG on that level (its A and G)
+    started from the finer level's test space restricted to the coarse nodes,
+    in increasing fine-node order (the coarse numbering of P's columns)."""
+    import workloads as W
+    from _problems import oracle_problem
+    p = W.beam(24, 6, 6)
+    K, V0, f, nm = oracle_problem(orc, p)
+    prm = orc.default_params(3, n_coarse=300)
+    H = orc.Hierarchy(K, V0, prm)
+    assert H.nlev >= 3
+    for k in range(H.nlev - 2):
+        cf = H.cf(k)
+        C = np.flatnonzero(cf == 1)
+        # P's C rows are identity blocks onto the coarse nodes numbered by
+        # increasing fine index
+        P = H.matrix(k, "P")
+        for j, I in enumerate(C):
+            assert P.rowptr[I + 1] - P.rowptr[I] == 1 and P.col[P.rowptr[I]] == j
+            assert np.array_equal(P.val[P.rowptr[I]], np.eye(3))
+        rows = (3 * C[:, None] + np.arange(3)).reshape(-1)
+        Vin = H.V(k)[rows]
+        A1, G1, GT1 = H.matrix(k + 1, "A"), H.matrix(k + 1, "G"), H.matrix(k + 1, "GT")
+        V1 = orc.srqcg(A1, G1, GT1, Vin, kmax=prm.n_rq, k_ritz=prm.k_ritz)
+        assert np.array_equal(V1, H.V(k + 1)), k
