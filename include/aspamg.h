@@ -2,13 +2,17 @@
  * aspamg.h -- C ABI of the GB300 library for the adaptive AMG solver aSP-AMG
  * (Franceschini, Paludetto Magri, Mazzucco, Spiezia, Janna, "A robust adaptive
  * algebraic multigrid linear solver for structural mechanics", arXiv
- * 1902.01715), with 3x3 nodal blocks.
+ * 1902.01715), with 3x3 nodal blocks, or, with amg_params.block = 1, in
+ * the paper's own scalar (per-dof) form.
  *
  * Conventions shared by every entry point
- *  - Matrices are block CSR with 3x3 blocks ("BSR3"): rowptr[nnodes+1],
- *    colind[nnzb] (ascending inside a row), vals[nnzb*9] with each block
- *    row-major.  Vectors have 3*nnodes entries, dof 3*I+c = component c of
- *    node I.  Several right-hand sides are stored column-major (n x k).
+ *  - Matrices are block CSR with b x b blocks, b = amg_params.block: b = 3
+ *    ("BSR3", the default) groups the 3 dofs of a mesh node, b = 1 is plain
+ *    scalar CSR (one row per dof, the paper's algorithm as printed).
+ *    rowptr[nnodes+1], colind[nnzb] (ascending inside a row), vals[nnzb*b*b]
+ *    with each block row-major; nnodes counts block rows (nodes for b = 3,
+ *    dofs for b = 1).  Vectors have b*nnodes entries, dof b*I+c = component c
+ *    of block row I.  Several right-hand sides are stored column-major (n x k).
  *  - Pointers are device pointers unless the argument says "host" or a
  *    `mem` argument selects AMG_MEM_HOST.  Device pointers must be usable on
  *    the handle's stream; the library never frees caller memory.
@@ -63,7 +67,7 @@ typedef struct {
   double omega_bar;       /* Algorithm 3: refine while omega < omega_bar ... */
   double rho_bar;         /* ... and blocks per block row of G < rho_bar */
   int max_refine;         /* at most this many refinement calls */
-  int max_g_nodes;        /* cap on off-diagonal nodes of a G row (<= 32) */
+  int max_g_nodes;        /* cap on off-diagonal nodes of a G row (<= 64) */
   int lanczos_m;          /* Lanczos steps for lambda_1(G A G^T) (<= 64) */
   double omega_safety;    /* omega = min(1, omega_safety * 2 / lambda_1) */
   int n_tv, n_rq, k_ritz; /* test space size, SRQCG iterations, Ritz period (Alg. 4) */
@@ -76,6 +80,9 @@ typedef struct {
   int vcycle_prec;        /* AMG_FP64 | AMG_FP32 | AMG_FP32_BF16GP */
   int maxit;              /* PCG iteration limit (1000, as in Sec. 4.2) */
   unsigned long long seed;/* counter generator: test-space padding, Lanczos start */
+  int block;              /* 3: nodal 3x3 blocks (default); 1: scalar, the paper's
+                           * form (its Table "TestParam" then counts rho_g in dofs:
+                           * rho_g = rho_i = 4, rho_bar = 34, max_g_nodes = 64) */
 } amg_params;
 
 typedef struct {
@@ -230,6 +237,15 @@ int amg_fe_assemble(int nx, int ny, int nz, double hx, double hy, double hz,
 int amg_fe_load(int nx, int ny, int nz, double hx, double hy, double hz,
                 int clamp, int kind, const double *g, const double *p,
                 double *f, void *stream);
+/* Scalar CSR form (b = 1) of a 3x3-block matrix (device arrays): row 3I+r
+ * holds, for each block of block row I in order, its entries (3I+r, 3J+c),
+ * c = 0..2, stored zeros included.  srowptr[3*nr+1], scolind[9*nnzb],
+ * svals[9*nnzb] are the caller's.  Feeds amg_setup with block = 1 from the
+ * structured-hex assembly. */
+int amg_bsr_to_scalar(int nr, int nnzb, const int *rowptr, const int *colind,
+                      const double *vals, int *srowptr, int *scolind,
+                      double *svals, void *stream);
+
 /* Rigid-body modes (device, 3*nfree x 6 column-major) about the mesh centre. */
 int amg_fe_rbm(int nx, int ny, int nz, double hx, double hy, double hz,
                int clamp, double *V, void *stream);

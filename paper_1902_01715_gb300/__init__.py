@@ -27,7 +27,7 @@ EXPORTS = [
     "amg_elem_grad", "amg_get_stats", "amg_free", "amg_strerror", "amg_last_error",
     "amg_level_info", "amg_level_matrix", "amg_level_cf", "amg_level_testspace", "amg_vcycle",
     "amg_fe_size", "amg_fe_assemble", "amg_fe_load", "amg_fe_rbm", "amg_fe_conn",
-    "amg_bench_spmv", "amg_launch_count", "amg_vcycle_noalloc",
+    "amg_bench_spmv", "amg_launch_count", "amg_vcycle_noalloc", "amg_bsr_to_scalar",
 ]
 
 
@@ -39,7 +39,8 @@ class AmgParams(C.Structure):
                 ("n_tv", C.c_int), ("n_rq", C.c_int), ("k_ritz", C.c_int), ("theta", C.c_int),
                 ("n_max", C.c_int), ("d_p", C.c_int), ("kappa_p", C.c_double),
                 ("n_coarse", C.c_int), ("max_levels", C.c_int), ("max_coarse_ratio", C.c_double),
-                ("vcycle_prec", C.c_int), ("maxit", C.c_int), ("seed", C.c_ulonglong)]
+                ("vcycle_prec", C.c_int), ("maxit", C.c_int), ("seed", C.c_ulonglong),
+                ("block", C.c_int)]
 
 
 class AmgStats(C.Structure):
@@ -104,6 +105,7 @@ def lib(path: str | None = None):
         "amg_bench_spmv": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp]),
         "amg_launch_count": (C.c_longlong, []),
         "amg_vcycle_noalloc": (C.c_int, [_vp, _vp, _vp]),
+        "amg_bsr_to_scalar": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -125,8 +127,13 @@ def check(rc, where="", allow=()):
 
 
 def default_params(**over) -> AmgParams:
+    """amg_default_params with overrides; block=1 (the scalar form) first
+    takes the paper's per-dof defaults rho_g = rho_i = 4 (rho_bar =
+    2 (1 + k_g rho_g) = 34) and max_g_nodes = 64."""
     p = AmgParams()
     check(lib().amg_default_params(C.byref(p)), "amg_default_params")
+    if over.get("block", 3) == 1:
+        p.rho_g, p.rho_i, p.rho_bar, p.max_g_nodes = 4, 4, 2.0 * (1 + 4 * 4), 64
     for k, v in over.items():
         if k == "vcycle_prec" and isinstance(v, str):
             v = PREC[v]
@@ -213,6 +220,19 @@ def elem_grad(conn, Ke0, dEdp, U, Lam):
     return grad
 
 
+def bsr_to_scalar(rowptr, col, vals):
+    """Scalar CSR (rowptr, col, vals (nnz,)) of a 3x3-block matrix on the
+    device, stored zeros of the blocks included."""
+    torch = _torch()
+    nr, nnzb = rowptr.numel() - 1, col.numel()
+    srp = torch.empty(3 * nr + 1, dtype=torch.int32, device=rowptr.device)
+    scol = torch.empty(9 * nnzb, dtype=torch.int32, device=rowptr.device)
+    sval = torch.empty(9 * nnzb, dtype=torch.float64, device=rowptr.device)
+    check(lib().amg_bsr_to_scalar(nr, nnzb, _ptr(rowptr), _ptr(col), _ptr(vals.contiguous()), _ptr(srp),
+                                  _ptr(scol), _ptr(sval), _stream()), "amg_bsr_to_scalar")
+    return srp, scol, sval
+
+
 def _colmajor(t):
     """(n, k) tensor -> contiguous column-major storage (as a (k, n) tensor)."""
     if t.dim() == 1:
@@ -224,11 +244,13 @@ def _colmajor(t):
 
 class Solver:
     """Hierarchy handle: ``Solver(rowptr, col, vals, V0, params)`` with CUDA
-    tensors (vals (nnzb, 3, 3) float64, V0 (n, t0) float64)."""
+    tensors (vals (nnzb, b, b) or (nnz,) float64 for b = block, V0 (n, t0)
+    float64)."""
 
     def __init__(self, rowptr, col, vals, V0=None, params: AmgParams | None = None, **over):
         torch = _torch()
         self.params = params if params is not None else default_params(**over)
+        self.b = self.params.block
         self.n = rowptr.numel() - 1
         nnzb = col.numel()
         self._keep = (rowptr, col, vals)
@@ -333,13 +355,14 @@ class Solver:
         nr = info["nc"] if which == "R" else info["nr"]
         nnzb = {"A": info["nnzb_A"], "G": info["nnzb_G"], "GT": info["nnzb_G"],
                 "P": info["nnzb_P"], "R": info["nnzb_P"]}[which]
+        b = self.b
         rowptr = np.zeros(nr + 1, np.int32)
         col = np.zeros(max(nnzb, 1), np.int32)
-        val = np.zeros(max(nnzb, 1) * 9)
+        val = np.zeros(max(nnzb, 1) * b * b)
         check(lib().amg_level_matrix(self._h, k, code, rowptr.ctypes.data_as(C.c_void_p),
                                      col.ctypes.data_as(C.c_void_p), val.ctypes.data_as(C.c_void_p)),
               "amg_level_matrix")
-        return rowptr, col[:nnzb], val[:nnzb * 9].reshape(-1, 3, 3)
+        return rowptr, col[:nnzb], val[:nnzb * b * b].reshape(-1, b, b)
 
     def level_cf(self, k):
         import numpy as np
@@ -349,7 +372,7 @@ class Solver:
 
     def level_testspace(self, k):
         import numpy as np
-        n = 3 * self.level_info(k)["nr"]
+        n = self.b * self.level_info(k)["nr"]
         t = self.params.n_tv
         V = np.zeros(n * t)
         check(lib().amg_level_testspace(self._h, k, V.ctypes.data_as(C.c_void_p)),

@@ -94,18 +94,20 @@ struct DBuf {
   }
 };
 
-// Block CSR matrix with 3x3 blocks, values row-major per block ("AoS"); the
-// pattern is mirrored on the host for the integer graph work of the set-up.
+// Block CSR matrix with b x b blocks (b = 3: nodal blocks; b = 1: the
+// scalar matrix of the paper's per-dof method), values row-major per block
+// ("AoS"); the pattern is mirrored on the host for the integer graph work of
+// the set-up.
 struct DevBsr {
-  int nr = 0, nc = 0, nnzb = 0;
+  int nr = 0, nc = 0, nnzb = 0, b = 3;
   DBuf<int> rowptr, col;
   DBuf<double> val;
   std::vector<int> h_rowptr, h_col;
-  int alloc(int nr_, int nc_, int nnzb_) {
-    nr = nr_; nc = nc_; nnzb = nnzb_;
+  int alloc(int nr_, int nc_, int nnzb_, int b_) {
+    nr = nr_; nc = nc_; nnzb = nnzb_; b = b_;
     AMG_TRY(rowptr.alloc(nr + 1));
     AMG_TRY(col.alloc(nnzb));
-    AMG_TRY(val.alloc((size_t)nnzb * 9));
+    AMG_TRY(val.alloc((size_t)nnzb * b * b));
     return AMG_OK;
   }
   int upload_pattern(cudaStream_t s) {
@@ -128,7 +130,7 @@ struct DevBsr {
 // slp[s] + 32 j + l holds block j of row 32 s + l (column scol[slot], entry e
 // at 9 (slp[s] + 32 j) + 32 e + l of a value array).
 struct SolveMat {
-  int nr = 0, nc = 0, nnzb = 0;
+  int nr = 0, nc = 0, nnzb = 0, b = 3;
   int ns = 0;      // slices
   long nslot = 0;  // slots, including padding
   const int *rowptr = nullptr, *col = nullptr;
@@ -138,6 +140,10 @@ struct SolveMat {
   DBuf<__nv_bfloat16> v16;
   int map = 0;    // warp mapping, FP32/bf16 storage (set by the autotuner)
   int map64 = 0;  // warp mapping, FP64 storage
+  // batched product (k columns): mapping per storage (FP64, FP32, bf16) and
+  // the k it was tuned for
+  int bmap[3] = {1, 1, 1};
+  int bmap_k[3] = {0, 0, 0};
 };
 
 // Row accumulator of the solve-phase block products.  FP64: every product is one FMA into the running sum.
@@ -156,6 +162,8 @@ template <> struct RowAcc<double> {
     s[r] = fma(m1, x1, s[r]);
     s[r] = fma(m2, x2, s[r]);
   }
+  // scalar (1x1) block
+  __device__ __forceinline__ void add1(int r, double m0, double x0) { s[r] = fma(m0, x0, s[r]); }
   __device__ __forceinline__ void merge(int r, double hi, double) { s[r] += hi; }
   __device__ __forceinline__ double hi(int r) const { return s[r]; }
   __device__ __forceinline__ double lo(int) const { return 0.0; }
@@ -173,6 +181,8 @@ template <> struct RowAcc<float> {
   __device__ __forceinline__ void add(int r, float m0, float m1, float m2, float x0, float x1, float x2) {
     two_sum(r, fmaf(m2, x2, fmaf(m1, x1, __fmul_rn(m0, x0))));
   }
+  // scalar (1x1) block: the product is the block partial
+  __device__ __forceinline__ void add1(int r, float m0, float x0) { two_sum(r, __fmul_rn(m0, x0)); }
   __device__ __forceinline__ void merge(int r, float hi, float lo) {
     two_sum(r, hi);
     c[r] = __fadd_rn(c[r], lo);
@@ -213,7 +223,8 @@ struct Handle {
   amg_params prm{};
   cudaStream_t stream = nullptr;
   int dev = -1;  // device current at amg_setup
-  int n = 0;  // fine nodes
+  int b = 3;     // block size: 3 (nodal blocks) or 1 (scalar, the paper's form)
+  int n = 0;  // fine nodes (block rows)
   int nlev = 0;
   std::vector<std::unique_ptr<Level>> lev;
   // last level: explicit inverse of its matrix (dense, row-major, symmetric)

@@ -9,6 +9,9 @@
 // are deterministic (per-column partials per block, summed in block order by
 // the last block).
 #include <cmath>
+#include <cstdlib>
+#include <mutex>
+#include <type_traits>
 
 #include "amg_internal.h"
 
@@ -22,71 +25,219 @@ __device__ __forceinline__ float cvb(__nv_bfloat16 v, float) { return __bfloat16
 
 enum { BE_SET = 0, BE_SCALE = 1, BE_RESID = 2, BE_SADD = 3, BE_ACC = 4 };
 
-// Y = epilogue(A X) on interleaved n x k blocks; one warp per block row of
-// the sliced layout (every lane reads the same block: a broadcast).
-template <typename TM, typename TX, int EP>
+// Y = epilogue(A X) on interleaved n x k blocks of the sliced layout.
+// Mapping (L, NC): a warp holds 32 / L lane groups of L lanes, one block row
+// per group; lane l of a group handles columns c0 + l + i L (i < NC) of each
+// tile of L NC columns, reading the row's blocks once per tile (every lane of
+// the group reads the same block: a broadcast) and its columns of the
+// neighbours' B x k values with coalesced loads.  Every (row, column) sum
+// adds the row's blocks in the same order whatever the mapping, so the
+// mapping changes the time, not the result.
+template <typename TM, typename TX, int B, int EP, int L, int NC>
 __global__ void __launch_bounds__(256) k_bsrmm(int nr, int k, const int *__restrict__ rp, const int *__restrict__ slp,
                                                const int *__restrict__ scol, const TM *__restrict__ v,
                                                const TX *__restrict__ X, TX *__restrict__ Y,
                                                const TX *__restrict__ AUX, TX w, const int *__restrict__ done) {
   if (done && *done) return;
-  const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= nr) return;
+  constexpr int R = 32 / L, BB = B * B;
+  const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, gl = lane % L;
+  const long rowl = gw * R + lane / L;
+  if (rowl >= nr) return;
+  const int row = (int)rowl, rl = row & 31;
   const int len = rp[row + 1] - rp[row];
-  const long base = (long)slp[row >> 5] + (row & 31);
-  for (int c0 = 0; c0 < k; c0 += 64) {
-    const int ca = c0 + lane, cb = c0 + 32 + lane;
-    const bool va = ca < k, vb = cb < k;
-    RowAcc<TX> a, b;
+  const long sbase = slp[row >> 5];
+  for (int c0 = 0; c0 < k; c0 += L * NC) {
+    RowAcc<TX> acc[NC];
     for (int q = 0; q < len; ++q) {
-      const long slot = base + 32L * q;
-      const long j = scol[slot];
-      const TM *mp = v + 9 * (slot - (row & 31)) + (row & 31);
-      const TX m0 = cvb(mp[0], TX(0)), m1 = cvb(mp[32], TX(0)), m2 = cvb(mp[64], TX(0));
-      const TX m3 = cvb(mp[96], TX(0)), m4 = cvb(mp[128], TX(0)), m5 = cvb(mp[160], TX(0));
-      const TX m6 = cvb(mp[192], TX(0)), m7 = cvb(mp[224], TX(0)), m8 = cvb(mp[256], TX(0));
-      const TX *xj = X + 3 * j * k;
-      if (va) {
-        const TX x0 = xj[ca], x1 = xj[k + ca], x2 = xj[2 * k + ca];
-        a.add(0, m0, m1, m2, x0, x1, x2);
-        a.add(1, m3, m4, m5, x0, x1, x2);
-        a.add(2, m6, m7, m8, x0, x1, x2);
-      }
-      if (vb) {
-        const TX x0 = xj[cb], x1 = xj[k + cb], x2 = xj[2 * k + cb];
-        b.add(0, m0, m1, m2, x0, x1, x2);
-        b.add(1, m3, m4, m5, x0, x1, x2);
-        b.add(2, m6, m7, m8, x0, x1, x2);
+      const long slot = sbase + 32L * q;
+      const long j = scol[slot + rl];
+      const TM *mp = v + BB * slot + rl;
+      TX m[BB];
+#pragma unroll
+      for (int e = 0; e < BB; ++e) m[e] = cvb(mp[32 * e], TX(0));
+      const TX *xj = X + (long)B * j * k;
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        const int c = c0 + gl + i * L;
+        if (c < k) {
+          if constexpr (B == 3) {
+            const TX x0 = xj[c], x1 = xj[k + c], x2 = xj[2 * k + c];
+            acc[i].add(0, m[0], m[1], m[2], x0, x1, x2);
+            acc[i].add(1, m[3], m[4], m[5], x0, x1, x2);
+            acc[i].add(2, m[6], m[7], m[8], x0, x1, x2);
+          } else {
+            acc[i].add1(0, m[0], xj[c]);
+          }
+        }
       }
     }
-    const long o = 3L * row * k;
-    auto put = [&](int c, TX s0, TX s1, TX s2) {
-      TX *y = Y + o + c;
-      const TX *ax = AUX ? AUX + o + c : nullptr;
-      if (EP == BE_SET) { y[0] = s0; y[k] = s1; y[2 * k] = s2; }
-      if (EP == BE_SCALE) { y[0] = w * s0; y[k] = w * s1; y[2 * k] = w * s2; }
-      if (EP == BE_RESID) { y[0] = ax[0] - s0; y[k] = ax[k] - s1; y[2 * k] = ax[2 * k] - s2; }
-      if (EP == BE_SADD) { y[0] = ax[0] + w * s0; y[k] = ax[k] + w * s1; y[2 * k] = ax[2 * k] + w * s2; }
-      if (EP == BE_ACC) { y[0] += s0; y[k] += s1; y[2 * k] += s2; }
-    };
-    if (va) put(ca, a.get(0), a.get(1), a.get(2));
-    if (vb) put(cb, b.get(0), b.get(1), b.get(2));
+    const long o = (long)B * row * k;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int c = c0 + gl + i * L;
+      if (c >= k) continue;
+#pragma unroll
+      for (int r = 0; r < B; ++r) {
+        const long at = o + (long)r * k + c;
+        const TX a = acc[i].get(r);
+        if (EP == BE_SET) Y[at] = a;
+        if (EP == BE_SCALE) Y[at] = w * a;
+        if (EP == BE_RESID) Y[at] = AUX[at] - a;
+        if (EP == BE_SADD) Y[at] = AUX[at] + w * a;
+        if (EP == BE_ACC) Y[at] += a;
+      }
+    }
   }
+}
+
+// candidate mappings (lanes per row, columns per lane and tile)
+struct BMap {
+  int L, NC;
+};
+static const BMap kBMaps[] = {{32, 1}, {32, 2}, {16, 2}, {16, 4}, {8, 4}};
+constexpr int kNumBMaps = (int)(sizeof(kBMaps) / sizeof(kBMaps[0]));
+
+template <typename TM, typename TX, int B, int L, int NC>
+static void bmm_launch(int ep, const SolveMat &M, const TM *v, int k, const TX *X, TX *Y, const TX *AUX, TX w,
+                       const int *done, cudaStream_t s) {
+  constexpr int R = 32 / L;
+  const long warps = (M.nr + R - 1) / R;
+  const int nb = nblk(32L * warps, 256);
+  if (!nb) return;
+#define AMG_BMM_ARGS M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done
+  switch (ep) {
+    case BE_SET: AMG_KCOUNT k_bsrmm<TM, TX, B, BE_SET, L, NC><<<nb, 256, 0, s>>>(AMG_BMM_ARGS); break;
+    case BE_SCALE: AMG_KCOUNT k_bsrmm<TM, TX, B, BE_SCALE, L, NC><<<nb, 256, 0, s>>>(AMG_BMM_ARGS); break;
+    case BE_RESID: AMG_KCOUNT k_bsrmm<TM, TX, B, BE_RESID, L, NC><<<nb, 256, 0, s>>>(AMG_BMM_ARGS); break;
+    case BE_SADD: AMG_KCOUNT k_bsrmm<TM, TX, B, BE_SADD, L, NC><<<nb, 256, 0, s>>>(AMG_BMM_ARGS); break;
+    default: AMG_KCOUNT k_bsrmm<TM, TX, B, BE_ACC, L, NC><<<nb, 256, 0, s>>>(AMG_BMM_ARGS); break;
+  }
+#undef AMG_BMM_ARGS
+}
+
+template <typename TM, typename TX, int B>
+static void bmm_b(int map, int ep, const SolveMat &M, const TM *v, int k, const TX *X, TX *Y, const TX *AUX, TX w,
+                  const int *done, cudaStream_t s) {
+  switch (map) {
+    case 0: bmm_launch<TM, TX, B, 32, 1>(ep, M, v, k, X, Y, AUX, w, done, s); break;
+    case 2: bmm_launch<TM, TX, B, 16, 2>(ep, M, v, k, X, Y, AUX, w, done, s); break;
+    case 3: bmm_launch<TM, TX, B, 16, 4>(ep, M, v, k, X, Y, AUX, w, done, s); break;
+    case 4: bmm_launch<TM, TX, B, 8, 4>(ep, M, v, k, X, Y, AUX, w, done, s); break;
+    default: bmm_launch<TM, TX, B, 32, 2>(ep, M, v, k, X, Y, AUX, w, done, s); break;
+  }
+}
+
+// the mapping the batched autotuner chose for this matrix, storage and k
+// (32 x 2 until tuned)
+template <typename TM>
+static int bmap_of(const SolveMat &M, int k) {
+  const int kind = std::is_same<TM, double>::value ? 0 : (std::is_same<TM, float>::value ? 1 : 2);
+  return M.bmap_k[kind] == k ? M.bmap[kind] : 1;
 }
 
 template <typename TM, typename TX>
 static void bmm(int ep, const SolveMat &M, const TM *v, int k, const TX *X, TX *Y, const TX *AUX, TX w, const int *done,
                 cudaStream_t s) {
-  const int nb = nblk(32L * M.nr, 256);
-  if (!nb) return;
-  switch (ep) {
-    case BE_SET: AMG_KCOUNT k_bsrmm<TM, TX, BE_SET><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
-    case BE_SCALE: AMG_KCOUNT k_bsrmm<TM, TX, BE_SCALE><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
-    case BE_RESID: AMG_KCOUNT k_bsrmm<TM, TX, BE_RESID><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
-    case BE_SADD: AMG_KCOUNT k_bsrmm<TM, TX, BE_SADD><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
-    default: AMG_KCOUNT k_bsrmm<TM, TX, BE_ACC><<<nb, 256, 0, s>>>(M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done); break;
+  const int map = bmap_of<TM>(M, k);
+  if (M.b == 1) bmm_b<TM, TX, 1>(map, ep, M, v, k, X, Y, AUX, w, done, s);
+  else bmm_b<TM, TX, 3>(map, ep, M, v, k, X, Y, AUX, w, done, s);
+}
+
+// ---------------------------------------------------------------- batched autotuner
+// Each level matrix of a batched solve is timed with every mapping for the
+// solve's k (CUDA events, one warm-up and two timed launches) on scratch
+// blocks, in the storage the solve uses; the winner is kept on the matrix
+// and cached per (storage, slice count, average row length, k), so later
+// hierarchies of the same shape reuse it.  AMG_BMAP=<0..4> pins a mapping.
+static std::mutex g_btune_mu;
+static std::vector<std::pair<long long, int>> g_btune_cache;
+
+template <typename TM, typename TX>
+static int tune_bmm(SolveMat &M, const TM *v, int k, cudaStream_t s) {
+  const int kind = std::is_same<TM, double>::value ? 0 : (std::is_same<TM, float>::value ? 1 : 2);
+  if (M.nr == 0 || !v) return AMG_OK;
+  if (const char *pin = getenv("AMG_BMAP")) {
+    const int m = atoi(pin);
+    if (m >= 0 && m < kNumBMaps) {
+      M.bmap[kind] = m;
+      M.bmap_k[kind] = k;
+      return AMG_OK;
+    }
   }
+  const double avg = (double)M.nnzb / M.nr;
+  const long long key = ((long long)kind << 60) | ((long long)M.b << 56) | ((long long)k << 40) |
+                        ((long long)M.ns << 16) | (long long)(avg * 16.0 + 0.5);
+  {
+    std::lock_guard<std::mutex> lock(g_btune_mu);
+    for (auto &e : g_btune_cache)
+      if (e.first == key) {
+        M.bmap[kind] = e.second;
+        M.bmap_k[kind] = k;
+        return AMG_OK;
+      }
+  }
+  DBuf<TX> X, Y;
+  AMG_TRY(X.alloc((size_t)M.b * M.nc * k));
+  AMG_TRY(Y.alloc((size_t)M.b * M.nr * k));
+  AMG_TRY(X.zero(s));
+  cudaEvent_t e0, e1;
+  AMG_CU(cudaEventCreate(&e0));
+  AMG_CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bm = 1;
+  for (int c = 0; c < kNumBMaps; ++c) {
+    auto launch = [&]() {
+      if (M.b == 1) bmm_b<TM, TX, 1>(c, BE_SET, M, v, k, X.p, Y.p, (const TX *)nullptr, TX(0), nullptr, s);
+      else bmm_b<TM, TX, 3>(c, BE_SET, M, v, k, X.p, Y.p, (const TX *)nullptr, TX(0), nullptr, s);
+    };
+    launch();
+    AMG_CU(cudaEventRecord(e0, s));
+    launch();
+    launch();
+    AMG_CU(cudaEventRecord(e1, s));
+    AMG_CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      bm = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  AMG_LAUNCH_CHECK();
+  M.bmap[kind] = bm;
+  M.bmap_k[kind] = k;
+  if (getenv("AMG_TRACE"))
+    fprintf(stderr, "[amg] batched mapping kind %d rows %d k %d -> L %d NC %d (%.4f ms)\n", kind, M.nr, k,
+            kBMaps[bm].L, kBMaps[bm].NC, best / 2.0);
+  std::lock_guard<std::mutex> lock(g_btune_mu);
+  g_btune_cache.push_back({key, bm});
+  return AMG_OK;
+}
+
+// every matrix the batched solve of k columns applies, in its storage
+static int tune_batch(Handle *h, int k) {
+  cudaStream_t s = h->stream;
+  const int prec = h->prm.vcycle_prec;
+  const bool b16 = prec == AMG_FP32_BF16GP;
+  AMG_TRY((tune_bmm<double, double>(h->lev[0]->sA, h->lev[0]->sA.v64.p, k, s)));  // CG operator
+  for (int l = 0; l < h->nlev - 1; ++l) {
+    Level &L = *h->lev[l];
+    if (prec == AMG_FP64) {
+      for (SolveMat *M : {&L.sG, &L.sGT, &L.sP, &L.sR}) AMG_TRY((tune_bmm<double, double>(*M, M->v64.p, k, s)));
+      if (l > 0) AMG_TRY((tune_bmm<double, double>(L.sA, L.sA.v64.p, k, s)));
+    } else {
+      AMG_TRY((tune_bmm<float, float>(L.sA, L.sA.v32.p, k, s)));
+      for (SolveMat *M : {&L.sG, &L.sGT, &L.sP, &L.sR}) {
+        if (b16) AMG_TRY((tune_bmm<__nv_bfloat16, float>(*M, M->v16.p, k, s)));
+        else AMG_TRY((tune_bmm<float, float>(*M, M->v32.p, k, s)));
+      }
+    }
+  }
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
 }
 
 template <typename TX>
@@ -444,7 +595,7 @@ template <typename TX>
 static void biteration(Handle *h, Batch &B, bool mixed) {
   cudaStream_t s = h->stream;
   const int k = B.k;
-  const long n = 3L * h->n;
+  const long n = (long)h->b * h->n;
   Level &L0 = *h->lev[0];
   const int bt = block_threads(k);
   const size_t shm = bt * sizeof(double);
@@ -475,9 +626,10 @@ static int ensure_batch(Handle *h, Batch &B, int k) {
     cudaGraphExecDestroy(B.graph);
     B.graph = nullptr;
   }
+  AMG_TRY(tune_batch(h, k));
   B.k = k;
   B.prec = prec;
-  const size_t nk = 3 * (size_t)h->n * k;
+  const size_t nk = (size_t)h->b * h->n * k;
   AMG_TRY(B.x.alloc(nk));
   AMG_TRY(B.r.alloc(nk));
   AMG_TRY(B.z.alloc(nk));
@@ -496,7 +648,7 @@ static int ensure_batch(Handle *h, Batch &B, int k) {
     AMG_TRY(B.zlow.alloc(nk));
   }
   for (int l = 0; l < h->nlev; ++l) {
-    const size_t m = 3 * (size_t)h->lev[l]->n * k;
+    const size_t m = (size_t)h->b * h->lev[l]->n * k;
     BatchLevel &BL = B.lev[l];
     if (mixed) {
       if (l > 0) {
@@ -524,7 +676,7 @@ int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int
     // independent groups of at most 256 columns
     int worst = AMG_OK, nit = 0, nrs = 0;
     double rec = 0.0, tru = 0.0;
-    const size_t n = 3 * (size_t)h->n;
+    const size_t n = (size_t)h->b * h->n;
     for (int c0 = 0; c0 < k; c0 += 256) {
       const int kk = k - c0 < 256 ? k - c0 : 256;
       const int rc = solve_batched(h, kk, B + c0 * n, X + c0 * n, rtol, iters + c0, relres + c0);
@@ -545,7 +697,7 @@ int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int
   Batch &Bt = *h->batch;
   AMG_TRY(ensure_batch(h, Bt, k));
   cudaStream_t s = h->stream;
-  const long n = 3L * h->n;
+  const long n = (long)h->b * h->n;
   const bool mixed = h->prm.vcycle_prec != AMG_FP64;
   const int bt = block_threads(k);
   const size_t shm = bt * sizeof(double);

@@ -40,15 +40,17 @@ extern "C" int amg_default_params(amg_params *p) {
   p->vcycle_prec = AMG_FP64;
   p->maxit = 1000;
   p->seed = 20190205ull;
+  p->block = 3;
   return AMG_OK;
 }
 
 static int check_params(const amg_params *p) {
   if (!p) return AMG_ERR_ARG;
-  if (p->k_g < 0 || p->rho_g < 1 || p->k_i < 0 || p->rho_i < 1 || p->max_g_nodes < 1 || p->max_g_nodes > 32 ||
+  if (p->k_g < 0 || p->rho_g < 1 || p->k_i < 0 || p->rho_i < 1 || p->max_g_nodes < 1 || p->max_g_nodes > 64 ||
       p->lanczos_m < 1 || p->lanczos_m > 64 || p->n_tv < 3 || p->n_tv > 16 || p->n_rq < 0 || p->k_ritz < 0 ||
       p->theta < 1 || p->n_max < 1 || p->d_p < 1 || !(p->kappa_p >= 1.0) || p->n_coarse < 0 || p->max_levels < 1 ||
-      p->vcycle_prec < AMG_FP64 || p->vcycle_prec > AMG_FP32_BF16GP || p->maxit < 1) {
+      p->vcycle_prec < AMG_FP64 || p->vcycle_prec > AMG_FP32_BF16GP || p->maxit < 1 ||
+      (p->block != 1 && p->block != 3) || p->n_tv < p->block) {
     set_error("amg_params: a parameter is out of the supported range");
     return AMG_ERR_ARG;
   }
@@ -71,6 +73,7 @@ extern "C" int amg_setup(const amg_params *p, int nnodes, int nnzb, const int *r
   Handle *h = new (std::nothrow) Handle();
   if (!h) return AMG_ERR_MEM;
   h->prm = *p;
+  h->b = p->block;
   if (cudaGetDevice(&h->dev) != cudaSuccess) {
     delete h;
     set_error("amg_setup: cudaGetDevice failed");
@@ -114,7 +117,7 @@ static int staged_solve(Handle *h, int k, const double *B, double *X, double rto
     set_error("amg_solve: invalid argument");
     return AMG_ERR_ARG;
   }
-  const size_t nk = (size_t)3 * h->n * k;
+  const size_t nk = (size_t)h->b * h->n * k;
   StreamScope scope(h->stream);
   const auto t0 = std::chrono::steady_clock::now();
   int rc;
@@ -199,7 +202,8 @@ extern "C" int amg_level_matrix(amg_handle hh, int lev, int which, int *rowptr, 
   if (M->nr == 0 && which != 0) return AMG_ERR_ARG;
   if (rowptr) memcpy(rowptr, M->h_rowptr.data(), (M->nr + 1) * sizeof(int));
   if (col && M->nnzb) memcpy(col, M->h_col.data(), M->nnzb * sizeof(int));
-  if (val && M->nnzb) AMG_CU(cudaMemcpy(val, M->val.p, (size_t)M->nnzb * 9 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (val && M->nnzb)
+    AMG_CU(cudaMemcpy(val, M->val.p, (size_t)M->nnzb * M->b * M->b * sizeof(double), cudaMemcpyDeviceToHost));
   return AMG_OK;
 }
 
@@ -217,7 +221,7 @@ extern "C" int amg_level_testspace(amg_handle hh, int lev, double *V) {
   if (!h || lev < 0 || lev >= h->nlev || !V) return AMG_ERR_ARG;
   const Level &L = *h->lev[lev];
   if (!L.V.p) return AMG_ERR_ARG;
-  AMG_CU(cudaMemcpy(V, L.V.p, (size_t)3 * L.n * h->prm.n_tv * sizeof(double), cudaMemcpyDeviceToHost));
+  AMG_CU(cudaMemcpy(V, L.V.p, (size_t)h->b * L.n * h->prm.n_tv * sizeof(double), cudaMemcpyDeviceToHost));
   return AMG_OK;
 }
 

@@ -45,42 +45,43 @@ __device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t counter) {
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------- SpMV
-// sum_k sum_c A_k[r][c] x[3 J_k + c] over the blocks kb..ke-1 of one block
-// row, one fused multiply-add per term in block and column order.  The
-// indices and operands of B blocks are loaded ahead of their chain, so a long
-// row waits on memory once per B blocks rather than once per block.
-template <int B>
+// sum_k sum_c A_k[r][c] x[BS J_k + c] over the blocks kb..ke-1 of one block
+// row (BS x BS blocks), one fused multiply-add per term in block and column
+// order.  The indices and operands of U blocks are loaded ahead of their
+// chain, so a long row waits on memory once per U blocks rather than once per
+// block.
+template <int BS, int U>
 __device__ __forceinline__ double row_chain(int kb, int ke, int r, const int *__restrict__ col,
                                             const double *__restrict__ val, const double *__restrict__ x, double s) {
-  for (int k0 = kb; k0 < ke; k0 += B) {
-    long J[B];
-    double a[B][3], xv[B][3];
+  for (int k0 = kb; k0 < ke; k0 += U) {
+    long J[U];
+    double a[U][BS], xv[U][BS];
 #pragma unroll
-    for (int u = 0; u < B; ++u) J[u] = k0 + u < ke ? col[k0 + u] : 0;
+    for (int u = 0; u < U; ++u) J[u] = k0 + u < ke ? col[k0 + u] : 0;
 #pragma unroll
-    for (int u = 0; u < B; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        a[u][c] = k0 + u < ke ? val[(size_t)(k0 + u) * 9 + r * 3 + c] : 0.0;
-        xv[u][c] = k0 + u < ke ? x[J[u] * 3 + c] : 0.0;
+      for (int c = 0; c < BS; ++c) {
+        a[u][c] = k0 + u < ke ? val[(size_t)(k0 + u) * BS * BS + r * BS + c] : 0.0;
+        xv[u][c] = k0 + u < ke ? x[J[u] * BS + c] : 0.0;
       }
 #pragma unroll
-    for (int u = 0; u < B; ++u)
+    for (int u = 0; u < U; ++u)
       if (k0 + u < ke)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) s = fma(a[u][c], xv[u][c], s);
+        for (int c = 0; c < BS; ++c) s = fma(a[u][c], xv[u][c], s);
   }
   return s;
 }
 
-template <int B>
+template <int BS, int U>
 __global__ void k_spmv(int nr, const int *__restrict__ rowptr, const int *__restrict__ col,
                        const double *__restrict__ val, const double *__restrict__ x,
                        double *__restrict__ y) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3L * nr) return;
-  const int I = (int)(t / 3), r = (int)(t - 3L * I);
-  y[t] = row_chain<B>(rowptr[I], rowptr[I + 1], r, col, val, x, 0.0);
+  if (t >= (long)BS * nr) return;
+  const int I = (int)(t / BS), r = (int)(t - (long)BS * I);
+  y[t] = row_chain<BS, U>(rowptr[I], rowptr[I + 1], r, col, val, x, 0.0);
 }
 
 // Below this many block rows a product has too few warps to hide memory
@@ -88,12 +89,19 @@ __global__ void k_spmv(int nr, const int *__restrict__ rowptr, const int *__rest
 // plain loop keeps more warps resident.
 constexpr int SMALL_ROWS = 16384;
 
+template <int BS>
+static void spmv_b(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
+  const long n = (long)BS * A.nr;
+  if (A.nr < SMALL_ROWS)
+    AMG_KCOUNT k_spmv<BS, 8><<<nblk(n, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+  else
+    AMG_KCOUNT k_spmv<BS, 1><<<nblk(n, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+}
+
 int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
   if (A.nr == 0) return AMG_OK;
-  if (A.nr < SMALL_ROWS)
-    AMG_KCOUNT k_spmv<8><<<nblk(3L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
-  else
-    AMG_KCOUNT k_spmv<1><<<nblk(3L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+  if (A.b == 1) spmv_b<1>(A, x, y, s);
+  else spmv_b<3>(A, x, y, s);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -476,19 +484,15 @@ struct FsaiK {
   int candcap, mmax, hcap;
 };
 
+template <int B>
 __device__ __forceinline__ const double *find_blk(const int *rp, const int *col, const double *val, int i, int j) {
   int lo = rp[i], hi = rp[i + 1] - 1;
   while (lo <= hi) {
     const int mid = (lo + hi) >> 1, c = col[mid];
-    if (c == j) return val + (size_t)mid * 9;
+    if (c == j) return val + (size_t)mid * B * B;
     if (c < j) lo = mid + 1; else hi = mid - 1;
   }
   return nullptr;
-}
-
-__device__ __forceinline__ double a_entry(const FsaiK &K, int r, int c) {
-  const double *b = find_blk(K.Arp, K.Acol, K.Aval, r / 3, c / 3);
-  return b ? b[(r % 3) * 3 + (c % 3)] : 0.0;
 }
 
 // Lockstep slots.  Each warp works on FS_NG node rows at once, FS_GL lanes
@@ -515,44 +519,46 @@ __device__ __forceinline__ void tri_decode(int idx, int &rr, int &kk) {
   kk = idx - r * (r + 1) / 2;
 }
 
-// Solve the 3 dof rows of node I on pattern pat[0..np-1] (slots with act);
-// returns 0 or an error, the same in every lane of a slot.  The system of
-// dof row c is A[Q_c, Q_c] with Q_c = (pattern dofs, 3I, ..., 3I+c-1), so the
-// systems of rows 0 and 1 are leading principal blocks of the system of row
-// 2: one Cholesky factor of the largest serves all three (entry (r,k) of a
-// Cholesky factor depends only on the leading (r+1)x(r+1) block, so each
-// row's factor is exactly what factoring it alone gives).  A is read one 3x3
-// block per node pair: the lower triangle of the largest system,
-// rhs_c = -A[Q_c, 3I+c] and ent_c = A[3I+c, Q_c].  Column j of the factor is
-// scaled by rho_j = 1 / L_jj, which the diagonal then holds for the
-// substitutions (a product per unknown instead of a division).
+// Solve the B dof rows of node I on pattern pat[0..np-1] (slots with act;
+// B = 3 for nodal blocks, B = 1 for the scalar method); returns 0 or an
+// error, the same in every lane of a slot.  The system of dof row c is
+// A[Q_c, Q_c] with Q_c = (pattern dofs, BI, ..., BI+c-1), so the systems of
+// rows 0 .. B-2 are leading principal blocks of the system of row B-1: one
+// Cholesky factor of the largest serves all B (entry (r,k) of a Cholesky
+// factor depends only on the leading (r+1)x(r+1) block, so each row's factor
+// is exactly what factoring it alone gives).  A is read one BxB block per
+// node pair: the lower triangle of the largest system, rhs_c = -A[Q_c, BI+c]
+// and ent_c = A[BI+c, Q_c].  Column j of the factor is scaled by
+// rho_j = 1 / L_jj, which the diagonal then holds for the substitutions (a
+// product per unknown instead of a division).
+template <int B>
 __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, int np, double *M, double *gh,
                                double *rhs, double *ent, double *psi, int g, int gl) {
-  const int m2 = act ? 3 * np + 2 : 0, mm = K.mmax, nn = np + 1;
+  const int m2 = act ? B * np + (B - 1) : 0, mm = K.mmax, nn = np + 1;
   const int npairs = act ? nn * (nn + 1) / 2 : 0;
   for (int idx = gl; idx < npairs; idx += FS_GL) {
     int p, q;
     tri_decode(idx, p, q);
-    const double *b = find_blk(K.Arp, K.Acol, K.Aval, p < np ? pat[p] : I, q < np ? pat[q] : I);
-    for (int a = 0; a < 3; ++a) {
-      const int r = 3 * p + a;
+    const double *b = find_blk<B>(K.Arp, K.Acol, K.Aval, p < np ? pat[p] : I, q < np ? pat[q] : I);
+    for (int a = 0; a < B; ++a) {
+      const int r = B * p + a;
       if (r >= m2) break;
-      for (int e = 0; e < 3; ++e) {
-        const int cc = 3 * q + e;
-        if (cc <= r) M[r * m2 + cc] = b ? b[a * 3 + e] : 0.0;
+      for (int e = 0; e < B; ++e) {
+        const int cc = B * q + e;
+        if (cc <= r) M[r * m2 + cc] = b ? b[a * B + e] : 0.0;
       }
     }
   }
   for (int idx = gl; idx < (act ? nn : 0); idx += FS_GL) {
     const int Np = idx < np ? pat[idx] : I;
-    const double *bc = find_blk(K.Arp, K.Acol, K.Aval, Np, I);
-    const double *br = find_blk(K.Arp, K.Acol, K.Aval, I, Np);
-    for (int a = 0; a < 3; ++a) {
-      const int qa = 3 * idx + a;
-      for (int c = 0; c < 3; ++c)
-        if (qa < 3 * np + c) {
-          rhs[c * mm + qa] = -(bc ? bc[a * 3 + c] : 0.0);
-          ent[c * mm + qa] = br ? br[c * 3 + a] : 0.0;
+    const double *bc = find_blk<B>(K.Arp, K.Acol, K.Aval, Np, I);
+    const double *br = find_blk<B>(K.Arp, K.Acol, K.Aval, I, Np);
+    for (int a = 0; a < B; ++a) {
+      const int qa = B * idx + a;
+      for (int c = 0; c < B; ++c)
+        if (qa < B * np + c) {
+          rhs[c * mm + qa] = -(bc ? bc[a * B + c] : 0.0);
+          ent[c * mm + qa] = br ? br[c * B + a] : 0.0;
         }
     }
   }
@@ -604,27 +610,27 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
     __syncwarp();
   }
   const bool ok = act && !bad;
-  // forward substitution for the three right-hand sides together (row c
-  // uses the leading 3np + c rows): y_k = rhs_k (1 / L_kk), then rhs_r -= L_rk y_k
+  // forward substitution for the B right-hand sides together (row c
+  // uses the leading B np + c rows): y_k = rhs_k (1 / L_kk), then rhs_r -= L_rk y_k
   // (k ascending for every r), in blocks of FS_PB columns: inside a block
   // column by column, then the rows below it take the block's updates in
   // one pass
   for (int k0 = 0; k0 < mx; k0 += FS_PB) {
     const int k1 = min(k0 + FS_PB, mx);
     for (int k = k0; k < k1; ++k) {
-      if (ok && gl < 3 && k < 3 * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] * M[k * m2 + k];
+      if (ok && gl < B && k < B * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] * M[k * m2 + k];
       __syncwarp();
       if (ok)
-        for (int idx = gl; idx < 3 * (k1 - k - 1); idx += FS_GL) {
+        for (int idx = gl; idx < B * (k1 - k - 1); idx += FS_GL) {
           const int c = idx / (k1 - k - 1), r = k + 1 + idx % (k1 - k - 1);
-          if (r < 3 * np + c) rhs[c * mm + r] = fma(-M[r * m2 + k], rhs[c * mm + k], rhs[c * mm + r]);
+          if (r < B * np + c) rhs[c * mm + r] = fma(-M[r * m2 + k], rhs[c * mm + k], rhs[c * mm + r]);
         }
       __syncwarp();
     }
     if (ok && k1 < m2)
-      for (int idx = gl; idx < 3 * (m2 - k1); idx += FS_GL) {
+      for (int idx = gl; idx < B * (m2 - k1); idx += FS_GL) {
         const int c = idx / (m2 - k1), r = k1 + idx % (m2 - k1);
-        if (r < 3 * np + c) {
+        if (r < B * np + c) {
           double a = rhs[c * mm + r];
           for (int k = k0; k < k1; ++k) a = fma(-M[r * m2 + k], rhs[c * mm + k], a);
           rhs[c * mm + r] = a;
@@ -638,38 +644,38 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
   for (int k1 = mx; k1 > 0; k1 -= FS_PB) {
     const int k0 = max(k1 - FS_PB, 0);
     for (int k = k1 - 1; k >= k0; --k) {
-      if (ok && gl < 3 && k < 3 * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] * M[k * m2 + k];
+      if (ok && gl < B && k < B * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] * M[k * m2 + k];
       __syncwarp();
       if (ok && k < m2)
-        for (int idx = gl; idx < 3 * (k - k0); idx += FS_GL) {
+        for (int idx = gl; idx < B * (k - k0); idx += FS_GL) {
           const int c = idx / (k - k0), r = k0 + idx % (k - k0);
-          if (k < 3 * np + c) rhs[c * mm + r] = fma(-M[k * m2 + r], gh[c * mm + k], rhs[c * mm + r]);
+          if (k < B * np + c) rhs[c * mm + r] = fma(-M[k * m2 + r], gh[c * mm + k], rhs[c * mm + r]);
         }
       __syncwarp();
     }
     if (ok)
-      for (int idx = gl; idx < 3 * k0; idx += FS_GL) {
+      for (int idx = gl; idx < B * k0; idx += FS_GL) {
         const int c = idx / k0, r = idx % k0;
         double a = rhs[c * mm + r];
-        for (int k = min(k1, 3 * np + c) - 1; k >= k0; --k) a = fma(-M[k * m2 + r], gh[c * mm + k], a);
+        for (int k = min(k1, B * np + c) - 1; k >= k0; --k) a = fma(-M[k * m2 + r], gh[c * mm + k], a);
         rhs[c * mm + r] = a;
       }
     __syncwarp();
   }
-  // psi_c = a_ii + sum_a A[i, Q_a] gh_a (a ascending), i = 3I + c
+  // psi_c = a_ii + sum_a A[i, Q_a] gh_a (a ascending), i = B I + c
   double sv = 0.0;
-  if (ok && gl < 3) {
+  if (ok && gl < B) {
     const int c = gl;
-    const double *bii = find_blk(K.Arp, K.Acol, K.Aval, I, I);
-    sv = bii ? bii[c * 3 + c] : 0.0;
-    for (int a = 0; a < 3 * np + c; ++a) sv = fma(ent[c * mm + a], gh[c * mm + a], sv);
+    const double *bii = find_blk<B>(K.Arp, K.Acol, K.Aval, I, I);
+    sv = bii ? bii[c * B + c] : 0.0;
+    for (int a = 0; a < B * np + c; ++a) sv = fma(ent[c * mm + a], gh[c * mm + a], sv);
   }
-  double ps[3];
-  for (int c = 0; c < 3; ++c) ps[c] = __shfl_sync(0xffffffffu, sv, g * FS_GL + c);
+  double ps[B];
+  for (int c = 0; c < B; ++c) ps[c] = __shfl_sync(0xffffffffu, sv, g * FS_GL + c);
   __syncwarp();
   if (!act) return AMG_OK;
   if (bad) return AMG_ERR_NOT_SPD;
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < B; ++c) {
     if (!(ps[c] > 0.0)) return AMG_ERR_NOT_SPD;
     psi[c] = ps[c];
   }
@@ -705,6 +711,7 @@ __device__ __forceinline__ bool set_insert(unsigned long long *tab, int cap, uns
   return false;
 }
 
+template <int B>
 __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
   const int lane = threadIdx.x & 31, g = lane / FS_GL, gl = lane % FS_GL;
   const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -713,9 +720,9 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
   const int mm = K.mmax;
   double *M = K.dscr + slot * K.dper;
   double *gh = M + (size_t)mm * mm;
-  double *rhs = gh + 3 * mm;
-  double *ent = rhs + 3 * mm;
-  double *score = ent + 3 * mm;
+  double *rhs = gh + B * mm;
+  double *ent = rhs + B * mm;
+  double *score = ent + B * mm;
   int *pat = K.iscr + slot * K.iper;
   int *cand = pat + K.maxg + 1;
   int *ccount = cand + K.candcap;
@@ -733,7 +740,7 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
     np = __shfl_sync(0xffffffffu, np, g * FS_GL);
     __syncwarp();
     double psi[3] = {0.0, 0.0, 0.0}, psi_old[3];
-    int rc = fsai_solve_rows(K, have, I, pat, np, M, gh, rhs, ent, psi, g, gl);
+    int rc = fsai_solve_rows<B>(K, have, I, pat, np, M, gh, rhs, ent, psi, g, gl);
     bool active = have && rc == 0;
     for (int step = 0; step < K.ksteps; ++step) {
       if (active && np >= K.maxg) active = false;
@@ -755,29 +762,29 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
         }
       __syncwarp();
       const int nc = active ? *(volatile int *)ccount : 0;
-      // gradient entries g[c][d] = (A gt_c)_{3J+d}: pattern dofs in
-      // ascending order, then the dofs 3I+e < 3I+c, then the unit entry;
+      // gradient entries g[c][d] = (A gt_c)_{BJ+d}: pattern dofs in
+      // ascending order, then the dofs BI+e < BI+c, then the unit entry;
       // node score = sum over c, d of g^2
       for (int t = gl; t < nc; t += FS_GL) {
         const int J = cand[t];
-        double gg[3][3];
-        for (int c = 0; c < 3; ++c)
-          for (int d = 0; d < 3; ++d) gg[c][d] = 0.0;
+        double gg[B][B];
+        for (int c = 0; c < B; ++c)
+          for (int d = 0; d < B; ++d) gg[c][d] = 0.0;
         for (int j = 0; j < np; ++j) {
-          const double *blk = find_blk(K.Arp, K.Acol, K.Aval, J, pat[j]);
+          const double *blk = find_blk<B>(K.Arp, K.Acol, K.Aval, J, pat[j]);
           if (blk)
-            for (int c = 0; c < 3; ++c)
-              for (int d = 0; d < 3; ++d)
-                for (int e = 0; e < 3; ++e) gg[c][d] = fma(blk[d * 3 + e], gh[c * mm + 3 * j + e], gg[c][d]);
+            for (int c = 0; c < B; ++c)
+              for (int d = 0; d < B; ++d)
+                for (int e = 0; e < B; ++e) gg[c][d] = fma(blk[d * B + e], gh[c * mm + B * j + e], gg[c][d]);
         }
-        const double *bI = find_blk(K.Arp, K.Acol, K.Aval, J, I);
+        const double *bI = find_blk<B>(K.Arp, K.Acol, K.Aval, J, I);
         double sc = 0.0;
-        for (int c = 0; c < 3; ++c)
-          for (int d = 0; d < 3; ++d) {
+        for (int c = 0; c < B; ++c)
+          for (int d = 0; d < B; ++d) {
             double gv = gg[c][d];
             if (bI) {
-              for (int e = 0; e < c; ++e) gv = fma(bI[d * 3 + e], gh[c * mm + 3 * np + e], gv);
-              gv = gv + bI[d * 3 + c] * 1.0;
+              for (int e = 0; e < c; ++e) gv = fma(bI[d * B + e], gh[c * mm + B * np + e], gv);
+              gv = gv + bI[d * B + c] * 1.0;
             }
             sc = fma(gv, gv, sc);
           }
@@ -828,15 +835,15 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
       }
       if (active) np += got;
       __syncwarp();
-      for (int c = 0; c < 3; ++c) psi_old[c] = psi[c];
-      const int rc2 = fsai_solve_rows(K, active, I, pat, np, M, gh, rhs, ent, psi, g, gl);
+      for (int c = 0; c < B; ++c) psi_old[c] = psi[c];
+      const int rc2 = fsai_solve_rows<B>(K, active, I, pat, np, M, gh, rhs, ent, psi, g, gl);
       if (active) {
         if (rc2) {
           rc = rc2;
           active = false;
         } else {
           int stalled = 1;
-          for (int c = 0; c < 3; ++c)
+          for (int c = 0; c < B; ++c)
             if (psi_old[c] - psi[c] > K.eps * psi_old[c]) stalled = 0;
           if (stalled) active = false;
         }
@@ -849,14 +856,14 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
     }
     if (gl == 0) K.out_np[I] = np;
     for (int j = gl; j < np; j += FS_GL) K.out_pat[(size_t)I * K.maxg + j] = pat[j];
-    double rs[3];  // 1 / sqrt(psi_c): one division per row, products per entry
-    for (int c = 0; c < 3; ++c) rs[c] = 1.0 / sqrt(psi[c]);
-    double *ov = K.out_val + (size_t)I * (K.maxg + 1) * 9;
-    for (int idx = gl; idx < (np + 1) * 9; idx += FS_GL) {
-      const int j = idx / 9, c = (idx % 9) / 3, d = idx % 3;
+    double rs[B];  // 1 / sqrt(psi_c): one division per row, products per entry
+    for (int c = 0; c < B; ++c) rs[c] = 1.0 / sqrt(psi[c]);
+    double *ov = K.out_val + (size_t)I * (K.maxg + 1) * B * B;
+    for (int idx = gl; idx < (np + 1) * B * B; idx += FS_GL) {
+      const int j = idx / (B * B), c = (idx % (B * B)) / B, d = idx % B;
       double gv;
-      if (j < np) gv = gh[c * mm + 3 * j + d];
-      else gv = (d < c) ? gh[c * mm + 3 * np + d] : (d == c ? 1.0 : 0.0);
+      if (j < np) gv = gh[c * mm + B * j + d];
+      else gv = (d < c) ? gh[c * mm + B * np + d] : (d == c ? 1.0 : 0.0);
       ov[idx] = (j < np || d <= c) ? gv * rs[c] : 0.0;
     }
   }
@@ -893,11 +900,11 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
     npcap += np0;
   }
   if (npcap > maxg) npcap = maxg;
-  K.mmax = 3 * (int)npcap + 3;
+  K.mmax = A.b * (int)npcap + A.b;
   K.candcap = ((int)npcap + 1) * maxdeg;
   K.hcap = 64;
   while (K.hcap < 2 * K.candcap) K.hcap *= 2;
-  K.dper = (long)K.mmax * K.mmax + 9L * K.mmax + K.candcap;
+  K.dper = (long)K.mmax * K.mmax + 3L * A.b * K.mmax + K.candcap;
   K.iper = (maxg + 1) + K.candcap + 1;
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
@@ -917,7 +924,8 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   K.dscr = ds.p;
   K.iscr = is.p;
   K.htab = hs.p;
-  AMG_KCOUNT k_fsai<<<(int)nblocks, threads, 0, s>>>(K);
+  if (A.b == 1) AMG_KCOUNT k_fsai<1><<<(int)nblocks, threads, 0, s>>>(K);
+  else AMG_KCOUNT k_fsai<3><<<(int)nblocks, threads, 0, s>>>(K);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -1179,17 +1187,17 @@ __global__ void __launch_bounds__(32) k_cdots(int n, int t, int nk, CDot a, doub
 // order.  One warp per block row: lane (j, r) computes dof row r of column j,
 // so every lane walks the same blocks (the row's values are read once per
 // warp and no FP64 instruction runs on a partly idle warp for lack of work).
-template <int B>
+template <int BS, int U>
 __global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const int *__restrict__ col,
                             const double *__restrict__ val, const double *__restrict__ X, double *__restrict__ Y) {
-  const long n = 3L * nr;
+  const long n = (long)BS * nr;
   const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (I >= nr) return;
   const int kb = rowptr[I], ke = rowptr[I + 1];
-  for (int pr = lane; pr < 3 * t; pr += 32) {
-    const int j = pr / 3, r = pr - 3 * j;
-    Y[(size_t)j * n + 3L * I + r] = row_chain<B>(kb, ke, r, col, val, X + (size_t)j * n, 0.0);
+  for (int pr = lane; pr < BS * t; pr += 32) {
+    const int j = pr / BS, r = pr - BS * j;
+    Y[(size_t)j * n + (long)BS * I + r] = row_chain<BS, U>(kb, ke, r, col, val, X + (size_t)j * n, 0.0);
   }
 }
 
@@ -1354,12 +1362,18 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
   return 0;
 }
 
+template <int BS>
+static void spmv_cols_b(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
+  if (A.nr < SMALL_ROWS)
+    AMG_KCOUNT k_spmv_cols<BS, 4><<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+  else
+    AMG_KCOUNT k_spmv_cols<BS, 1><<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+}
+
 int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
   if (A.nr == 0) return AMG_OK;
-  if (A.nr < SMALL_ROWS)
-    AMG_KCOUNT k_spmv_cols<4><<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
-  else
-    AMG_KCOUNT k_spmv_cols<1><<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+  if (A.b == 1) spmv_cols_b<1>(A, t, X, Y, s);
+  else spmv_cols_b<3>(A, t, X, Y, s);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -1385,7 +1399,7 @@ static int cdots(int n, int t, int nk, const CDot &a, double *out, int fin, doub
 
 int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ritz, int t, const double *V0, double *V,
           int *status, cudaStream_t s) {
-  const int n = 3 * A.nr;
+  const int n = A.b * A.nr;
   if (t > TMAXD) {
     set_error("n_tv = %d exceeds the supported maximum %d", t, TMAXD);
     return AMG_ERR_ARG;
@@ -1547,7 +1561,7 @@ __global__ void k_lz_reorth(long n, int j, double *__restrict__ w, const double 
 // square, [160..223] re-orthogonalisation coefficients, [256..319] 1 / beta.
 int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t seed, int level,
             double safety, double *d_out, cudaStream_t s, bool sync) {
-  const int n = 3 * A.nr;
+  const int n = A.b * A.nr;
   if (m > n) m = n;
   if (m > 64) m = 64;
   DBuf<double> Vs, w, t1, t2, sc, part;
@@ -1598,28 +1612,31 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
 }
 
 // ---------------------------------------------------------------- SoC + filter
-// Node gram of the test space: M[r][c] = sum_k V[k][3I+r] V[k][3J+c], k ascending.
+// Node gram of the test space: M[r][c] = sum_k V[k][BI+r] V[k][BJ+c], k ascending.
+template <int B>
 __device__ __forceinline__ void node_gram(long n, int t, const double *__restrict__ V, int I, int J, double *M) {
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) {
+  for (int r = 0; r < B; ++r)
+    for (int c = 0; c < B; ++c) {
       double s = 0.0;
-      for (int k = 0; k < t; ++k) s = fma(V[(size_t)k * n + 3L * I + r], V[(size_t)k * n + 3L * J + c], s);
-      M[r * 3 + c] = s;
+      for (int k = 0; k < t; ++k) s = fma(V[(size_t)k * n + (long)B * I + r], V[(size_t)k * n + (long)B * J + c], s);
+      M[r * B + c] = s;
     }
 }
 
+template <int B>
 __device__ __forceinline__ double fro2(const double *M) {
   double s = 0.0;
-  for (int i = 0; i < 9; ++i) s = fma(M[i], M[i], s);
+  for (int i = 0; i < B * B; ++i) s = fma(M[i], M[i], s);
   return s;
 }
 
+template <int B>
 __global__ void k_soc_nrm(int nn, int t, const double *__restrict__ V, double *__restrict__ nrm) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nn) return;
-  double M[9];
-  node_gram(3L * nn, t, V, I, I, M);
-  nrm[I] = sqrt(fro2(M));
+  double M[B * B];
+  node_gram<B>((long)B * nn, t, V, I, I, M);
+  nrm[I] = sqrt(fro2<B>(M));
 }
 
 __device__ __forceinline__ int find_in_row(const int *rp, const int *col, int row, int v) {
@@ -1635,6 +1652,7 @@ __device__ __forceinline__ int find_in_row(const int *rp, const int *col, int ro
 // SoC of the block pair {(I,J), (J,I)} with I < J, computed once from the
 // smaller node first and written to both positions (one thread per stored
 // block of the upper triangle); diagonal blocks get 0.
+template <int B>
 __global__ void k_soc_pairs(int nn, int nnzb, int t, const int *__restrict__ rp, const int *__restrict__ col,
                             const double *__restrict__ V, const double *__restrict__ nrm, double *__restrict__ soc) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1652,9 +1670,9 @@ __global__ void k_soc_pairs(int nn, int nnzb, int t, const int *__restrict__ rp,
   const int kt = find_in_row(rp, col, J, I);
   if (J < I && kt >= 0) return;  // the mirror's thread writes both
   const int a = I < J ? I : J, b = I < J ? J : I;
-  double M[9];
-  node_gram(3L * nn, t, V, a, b, M);
-  const double num = fro2(M), den = nrm[a] * nrm[b];
+  double M[B * B];
+  node_gram<B>((long)B * nn, t, V, a, b, M);
+  const double num = fro2<B>(M), den = nrm[a] * nrm[b];
   const double v = den > 0.0 ? num / den : 0.0;
   soc[k] = v;
   if (kt >= 0) soc[kt] = v;
@@ -1700,8 +1718,13 @@ int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char
   AMG_TRY(kept.alloc(A.nnzb));
   const int nb = nblk(A.nr, 128);
   AMG_TRY(soc.zero(s));
-  AMG_KCOUNT k_soc_nrm<<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
-  AMG_KCOUNT k_soc_pairs<<<nblk(A.nnzb, 128), 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+  if (A.b == 1) {
+    AMG_KCOUNT k_soc_nrm<1><<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
+    AMG_KCOUNT k_soc_pairs<1><<<nblk(A.nnzb, 128), 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+  } else {
+    AMG_KCOUNT k_soc_nrm<3><<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
+    AMG_KCOUNT k_soc_pairs<3><<<nblk(A.nnzb, 128), 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+  }
   AMG_KCOUNT k_soc_select<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, soc.p, theta, kept.p);
   AMG_KCOUNT k_strong<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, kept.p, strong);
   AMG_LAUNCH_CHECK();
@@ -1726,42 +1749,45 @@ __device__ __forceinline__ void reflect(int t, int p, const double *v, double rv
 // same chain of fused multiply-adds with the factors swapped, hence equal
 // bit for bit: the six distinct entries are formed once and the nine squares
 // are added in row-major order.
+template <int B>
 __device__ __forceinline__ double gram_fro2(int t, int p, const double *X) {
-  double g[3][3];
+  double g[B][B];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < B; ++a)
 #pragma unroll
-    for (int c = a; c < 3; ++c) {
+    for (int c = a; c < B; ++c) {
       double s = 0.0;
-      for (int k = p; k < t; ++k) s = fma(X[k * 3 + a], X[k * 3 + c], s);
+      for (int k = p; k < t; ++k) s = fma(X[k * B + a], X[k * B + c], s);
       g[a][c] = s;
       g[c][a] = s;
     }
   double f = 0.0;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < B; ++a)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) f = fma(g[a][c], g[a][c], f);
+    for (int c = 0; c < B; ++c) f = fma(g[a][c], g[a][c], f);
   return f;
 }
 
 // affinity of residual X and candidate Y; xx = gram_fro2(X), the same for
 // every candidate of one step
+template <int B>
 __device__ __forceinline__ double affinity(int t, int p, const double *X, double xx, const double *Y) {
   double xy = 0.0;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < B; ++a)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < B; ++c) {
       double s = 0.0;
-      for (int k = p; k < t; ++k) s = fma(X[k * 3 + a], Y[k * 3 + c], s);
+      for (int k = p; k < t; ++k) s = fma(X[k * B + a], Y[k * B + c], s);
       xy = fma(s, s, xy);
     }
-  const double yy = gram_fro2(t, p, Y);
+  const double yy = gram_fro2<B>(t, p, Y);
   const double den = sqrt(xx) * sqrt(yy);
   return den > 0.0 ? xy / den : -1.0;
 }
 
+template <int B>
 __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, const double *__restrict__ V,
                        const int *__restrict__ cptr, const int *__restrict__ cand, const int *__restrict__ cidx,
                        double *__restrict__ Vt, unsigned char *__restrict__ taken, int n_max, double kappa_p,
@@ -1771,32 +1797,32 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
   if (f >= nf) return;
   const int I = fnodes[f];
   const int c0 = cptr[f], ncand = cptr[f + 1] - c0;
-  double *vt = Vt + (size_t)c0 * t * 3;
+  double *vt = Vt + (size_t)c0 * t * B;
   unsigned char *tk = taken + c0;
-  double r[TMAXD * 3], R[TMAXD * TMAXD], Y[TMAXD * 3], hv[3][TMAXD], hvv[3], w[TMAXD * 3];
+  double r[TMAXD * B], R[TMAXD * TMAXD], Y[TMAXD * B], hv[B][TMAXD], hvv[B], w[TMAXD * B];
   int sel[TMAXD];
   for (int i = 0; i < TMAXD * TMAXD; ++i) R[i] = 0.0;
   for (int k = 0; k < t; ++k)
-    for (int c = 0; c < 3; ++c) r[k * 3 + c] = V[(size_t)k * n + 3L * I + c];
+    for (int c = 0; c < B; ++c) r[k * B + c] = V[(size_t)k * n + (long)B * I + c];
   for (int j = 0; j < ncand; ++j) {
     tk[j] = 0;
     for (int k = 0; k < t; ++k)
-      for (int c = 0; c < 3; ++c) vt[((size_t)j * t + k) * 3 + c] = V[(size_t)k * n + 3L * cand[c0 + j] + c];
+      for (int c = 0; c < B; ++c) vt[((size_t)j * t + k) * B + c] = V[(size_t)k * n + (long)B * cand[c0 + j] + c];
   }
   int nsel = 0, p = 0;
   double rdmax = 0.0, rdmin = 0.0;
   for (;;) {
-    if (nsel >= n_max || p + 3 > t) break;
+    if (nsel >= n_max || p + B > t) break;
     double rr = 0.0;
     for (int k = p; k < t; ++k)
-      for (int c = 0; c < 3; ++c) rr = fma(r[k * 3 + c], r[k * 3 + c], rr);
+      for (int c = 0; c < B; ++c) rr = fma(r[k * B + c], r[k * B + c], rr);
     if (rr == 0.0) break;
-    const double xx = gram_fro2(t, p, r);
+    const double xx = gram_fro2<B>(t, p, r);
     int best = -1;
     double baff = 0.0;
     for (int j = 0; j < ncand; ++j) {
       if (tk[j]) continue;
-      const double a = affinity(t, p, r, xx, vt + (size_t)j * t * 3);
+      const double a = affinity<B>(t, p, r, xx, vt + (size_t)j * t * B);
       if (a < 0.0) continue;
       if (best < 0 || a > baff) {
         best = j;
@@ -1804,27 +1830,27 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
       }
     }
     if (best < 0) break;
-    for (int i = 0; i < t * 3; ++i) Y[i] = vt[(size_t)best * t * 3 + i];
+    for (int i = 0; i < t * B; ++i) Y[i] = vt[(size_t)best * t * B + i];
     int ok = 1;
     double dmax = rdmax, dmin = rdmin;
-    for (int c = 0; c < 3 && ok; ++c) {
+    for (int c = 0; c < B && ok; ++c) {
       const int pc = p + c;
       double sg = 0.0;
-      for (int k = pc; k < t; ++k) sg = fma(Y[k * 3 + c], Y[k * 3 + c], sg);
+      for (int k = pc; k < t; ++k) sg = fma(Y[k * B + c], Y[k * B + c], sg);
       sg = sqrt(sg);
       if (!(sg > 0.0)) {
         ok = 0;
         break;
       }
-      const double alpha = Y[pc * 3 + c] >= 0.0 ? -sg : sg;
-      for (int k = 0; k < t; ++k) hv[c][k] = (k >= pc) ? Y[k * 3 + c] : 0.0;
-      hv[c][pc] = Y[pc * 3 + c] - alpha;
+      const double alpha = Y[pc * B + c] >= 0.0 ? -sg : sg;
+      for (int k = 0; k < t; ++k) hv[c][k] = (k >= pc) ? Y[k * B + c] : 0.0;
+      hv[c][pc] = Y[pc * B + c] - alpha;
       double vv = 0.0;
       for (int k = pc; k < t; ++k) vv = fma(hv[c][k], hv[c][k], vv);
       hvv[c] = 1.0 / vv;  // reciprocal
-      for (int c2 = c + 1; c2 < 3; ++c2) reflect(t, pc, hv[c], hvv[c], Y + c2, 3);
-      Y[pc * 3 + c] = alpha;
-      for (int k = pc + 1; k < t; ++k) Y[k * 3 + c] = 0.0;
+      for (int c2 = c + 1; c2 < B; ++c2) reflect(t, pc, hv[c], hvv[c], Y + c2, B);
+      Y[pc * B + c] = alpha;
+      for (int k = pc + 1; k < t; ++k) Y[k * B + c] = 0.0;
       const double ad = fabs(alpha);
       if (pc == 0) {
         dmax = ad;
@@ -1835,26 +1861,26 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
       }
     }
     if (!ok || !(dmin > 0.0) || dmax / dmin > kappa_p) break;
-    for (int c = 0; c < 3; ++c)
-      for (int k = 0; k <= p + c; ++k) R[k * TMAXD + p + c] = Y[k * 3 + c];
-    for (int c = 0; c < 3; ++c) {
-      for (int c2 = 0; c2 < 3; ++c2) reflect(t, p + c, hv[c], hvv[c], r + c2, 3);
+    for (int c = 0; c < B; ++c)
+      for (int k = 0; k <= p + c; ++k) R[k * TMAXD + p + c] = Y[k * B + c];
+    for (int c = 0; c < B; ++c) {
+      for (int c2 = 0; c2 < B; ++c2) reflect(t, p + c, hv[c], hvv[c], r + c2, B);
       for (int j = 0; j < ncand; ++j) {
         if (tk[j] || j == best) continue;
-        for (int c2 = 0; c2 < 3; ++c2) reflect(t, p + c, hv[c], hvv[c], vt + (size_t)j * t * 3 + c2, 3);
+        for (int c2 = 0; c2 < B; ++c2) reflect(t, p + c, hv[c], hvv[c], vt + (size_t)j * t * B + c2, B);
       }
     }
     tk[best] = 1;
     sel[nsel++] = cand[c0 + best];
-    p += 3;
+    p += B;
     rdmax = dmax;
     rdmin = dmin;
   }
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < B; ++c)
     for (int i = p - 1; i >= 0; --i) {
-      double s = r[i * 3 + c];
-      for (int k = p - 1; k > i; --k) s = fma(-R[i * TMAXD + k], w[k * 3 + c], s);
-      w[i * 3 + c] = s / R[i * TMAXD + i];
+      double s = r[i * B + c];
+      for (int k = p - 1; k > i; --k) s = fma(-R[i * TMAXD + k], w[k * B + c], s);
+      w[i * B + c] = s / R[i * TMAXD + i];
     }
   // entries sorted by coarse index
   int ord[TMAXD];
@@ -1869,9 +1895,9 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
   for (int u = 0; u < nsel; ++u) {
     const int m = ord[u];
     out_col[(size_t)f * nsel_cap + u] = cidx[sel[m]];
-    double *o = out_val + ((size_t)f * nsel_cap + u) * 9;
-    for (int c = 0; c < 3; ++c)
-      for (int d = 0; d < 3; ++d) o[c * 3 + d] = w[(3 * m + d) * 3 + c];
+    double *o = out_val + ((size_t)f * nsel_cap + u) * B * B;
+    for (int c = 0; c < B; ++c)
+      for (int d = 0; d < B; ++d) o[c * B + d] = w[(B * m + d) * B + c];
   }
 }
 
@@ -1889,11 +1915,16 @@ int dpls(const DevBsr &A, const unsigned char *strong, const int *cf, const int 
   AMG_CU(cudaStreamSynchronize(s));
   DBuf<double> Vt;
   DBuf<unsigned char> taken;
-  AMG_TRY(Vt.alloc((size_t)total * t * 3));
+  const int B = A.b;
+  AMG_TRY(Vt.alloc((size_t)total * t * B));
   AMG_TRY(taken.alloc(total));
-  const int cap = n_max < t / 3 ? n_max : t / 3;
-  AMG_KCOUNT k_dpls<<<nblk(nf, 64), 64, 0, s>>>(nf, fnodes, 3L * A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p, n_max,
-                                     kappa_p, cap > 0 ? cap : 1, out_cnt, out_col, out_val);
+  const int cap = n_max < t / B ? n_max : t / B;
+  if (B == 1)
+    AMG_KCOUNT k_dpls<1><<<nblk(nf, 64), 64, 0, s>>>(nf, fnodes, (long)A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p,
+                                                    n_max, kappa_p, cap > 0 ? cap : 1, out_cnt, out_col, out_val);
+  else
+    AMG_KCOUNT k_dpls<3><<<nblk(nf, 64), 64, 0, s>>>(nf, fnodes, 3L * A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p,
+                                                    n_max, kappa_p, cap > 0 ? cap : 1, out_cnt, out_col, out_val);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -1905,15 +1936,17 @@ int dpls(const DevBsr &A, const unsigned char *strong, const int *cf, const int 
 // d ascending from 0), accumulating from 0.  Nine lanes per output block,
 // one per entry (3 blocks per warp): the nine walk the same k and take the
 // same branches, so the FP64 work runs on full lane groups.
+template <int B>
 __global__ void k_spgemm(int nr, const int *__restrict__ xr, const int *__restrict__ xc, const double *__restrict__ xv,
                          const int *__restrict__ yr, const int *__restrict__ yc, const double *__restrict__ yv,
                          const int *__restrict__ zr, const int *__restrict__ zc, double *__restrict__ zv, int nnz) {
+  constexpr int BB = B * B, PER = 32 / BB;  // output blocks per warp
   const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (lane >= 27) return;
-  const long ql = 3 * w + lane / 9;
+  if (lane >= PER * BB) return;
+  const long ql = PER * w + lane / BB;
   if (ql >= nnz) return;
-  const int q = (int)ql, e = lane % 9, r = e / 3, qq = e - 3 * r;
+  const int q = (int)ql, e = lane % BB, r = e / B, qq = e - B * r;
   int lo = 0, hi = nr - 1;
   while (lo < hi) {  // row of entry q: last row with zr[row] <= q
     const int mid = (lo + hi + 1) >> 1;
@@ -1930,18 +1963,22 @@ __global__ void k_spgemm(int nr, const int *__restrict__ xr, const int *__restri
       if (yc[mid] < c) a = mid + 1; else b = mid - 1;
     }
     if (ky < 0) continue;
-    const double *x = xv + (size_t)kx * 9, *y = yv + (size_t)ky * 9;
+    const double *x = xv + (size_t)kx * BB, *y = yv + (size_t)ky * BB;
     double sv = 0.0;
-    for (int d = 0; d < 3; ++d) sv = fma(x[r * 3 + d], y[d * 3 + qq], sv);
+    for (int d = 0; d < B; ++d) sv = fma(x[r * B + d], y[d * B + qq], sv);
     acc = acc + sv;
   }
-  zv[(size_t)q * 9 + e] = acc;
+  zv[(size_t)q * BB + e] = acc;
 }
 
 int spgemm_numeric(const DevBsr &X, const DevBsr &Y, DevBsr &Z, cudaStream_t s) {
   if (Z.nnzb == 0) return AMG_OK;
-  AMG_KCOUNT k_spgemm<<<nblk(32L * ((Z.nnzb + 2) / 3), 128), 128, 0, s>>>(Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
-                                            Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
+  if (Z.b == 1)
+    AMG_KCOUNT k_spgemm<1><<<nblk(32L * ((Z.nnzb + 31) / 32), 128), 128, 0, s>>>(
+        Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p, Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
+  else
+    AMG_KCOUNT k_spgemm<3><<<nblk(32L * ((Z.nnzb + 2) / 3), 128), 128, 0, s>>>(
+        Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p, Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }

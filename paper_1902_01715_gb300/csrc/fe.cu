@@ -357,3 +357,38 @@ extern "C" int amg_elem_grad(int ne, const int *conn, const double *Ke0, const d
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
 }
+
+// Scalar CSR copy of a 3x3-block matrix: scalar row 3I + r lists, for each
+// block k of block row I in order, the entries (3I + r, 3 col[k] + c), c = 0..2
+// (explicit zeros of a stored block included, so the pattern is the block
+// pattern expanded).  One thread per scalar row.
+__global__ void k_bsr_to_scalar(int nr, const int *__restrict__ rp, const int *__restrict__ col,
+                                const double *__restrict__ val, int *__restrict__ srp, int *__restrict__ scol,
+                                double *__restrict__ sval) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3L * nr) return;
+  const int I = (int)(i / 3), r = (int)(i - 3L * I);
+  const int kb = rp[I], len = rp[I + 1] - kb;
+  const long start = 9L * kb + 3L * r * len;
+  srp[i] = (int)start;
+  if (i == 3L * nr - 1) srp[3L * nr] = 9 * rp[nr];
+  for (int q = 0; q < len; ++q)
+    for (int c = 0; c < 3; ++c) {
+      scol[start + 3 * q + c] = 3 * col[kb + q] + c;
+      sval[start + 3 * q + c] = val[9L * (kb + q) + 3 * r + c];
+    }
+}
+
+extern "C" int amg_bsr_to_scalar(int nr, int nnzb, const int *rowptr, const int *colind, const double *vals,
+                                 int *srowptr, int *scolind, double *svals, void *stream) {
+  if (nr < 1 || nnzb < 0 || nnzb > 0x7fffffff / 9 || !rowptr || !colind || !vals || !srowptr || !scolind ||
+      !svals) {
+    set_error("amg_bsr_to_scalar: invalid argument");
+    return AMG_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  AMG_KCOUNT k_bsr_to_scalar<<<nblk(3L * nr, 128), 128, 0, s>>>(nr, rowptr, colind, vals, srowptr, scolind, svals);
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaStreamSynchronize(s));
+  return AMG_OK;
+}

@@ -84,52 +84,62 @@ static void trace(const char *what, int level, double t0) {
 }
 
 // ---------------------------------------------------------------- kernels
-// Copy rows stored with a fixed capacity into a compact BSR (values only).
+// Copy rows stored with a fixed capacity into a compact BSR (values only,
+// B x B blocks).
+template <int B>
 __global__ void k_compact_vals(int n, int cap, const int *__restrict__ rowptr, const double *__restrict__ src,
                                double *__restrict__ dst) {
+  constexpr int BB = B * B;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int I = (int)(t / (cap * 9));
+  const int I = (int)(t / (cap * BB));
   if (I >= n) return;
-  const int rem = (int)(t - (long)I * cap * 9);
-  const int j = rem / 9, e = rem % 9;
+  const int rem = (int)(t - (long)I * cap * BB);
+  const int j = rem / BB, e = rem % BB;
   const int len = rowptr[I + 1] - rowptr[I];
   if (j >= len) return;
-  dst[((size_t)rowptr[I] + j) * 9 + e] = src[((size_t)I * cap + j) * 9 + e];
+  dst[((size_t)rowptr[I] + j) * BB + e] = src[((size_t)I * cap + j) * BB + e];
 }
 
 // T.val[dst] = transpose(A.val[perm[dst]])
+template <int B>
 __global__ void k_transpose_vals(int nnzb, const int *__restrict__ perm, const double *__restrict__ src,
                                  double *__restrict__ dst) {
+  constexpr int BB = B * B;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 9L * nnzb) return;
-  const int q = (int)(t / 9), e = (int)(t % 9), r = e / 3, c = e % 3;
-  dst[(size_t)q * 9 + c * 3 + r] = src[(size_t)perm[q] * 9 + e];
+  if (t >= (long)BB * nnzb) return;
+  const int q = (int)(t / BB), e = (int)(t % BB), r = e / B, c = e % B;
+  dst[(size_t)q * BB + c * B + r] = src[(size_t)perm[q] * BB + e];
 }
 
 // P values: identity for coarse rows, DPLS blocks for fine rows.
+template <int B>
 __global__ void k_p_vals(int n, const int *__restrict__ rowptr, const int *__restrict__ fidx, int cap,
                          const double *__restrict__ fval, double *__restrict__ pv) {
+  constexpr int BB = B * B;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int I = (int)(t / (cap * 9));
+  const int I = (int)(t / (cap * BB));
   if (I >= n) return;
-  const int rem = (int)(t - (long)I * cap * 9);
-  const int j = rem / 9, e = rem % 9;
+  const int rem = (int)(t - (long)I * cap * BB);
+  const int j = rem / BB, e = rem % BB;
   const int len = rowptr[I + 1] - rowptr[I];
   if (j >= len) return;
   const int f = fidx[I];
-  const double v = (f < 0) ? ((e % 4 == 0) ? 1.0 : 0.0) : fval[((size_t)f * cap + j) * 9 + e];
-  pv[((size_t)rowptr[I] + j) * 9 + e] = v;
+  const double v = (f < 0) ? ((e % (B + 1) == 0) ? 1.0 : 0.0) : fval[((size_t)f * cap + j) * BB + e];
+  pv[((size_t)rowptr[I] + j) * BB + e] = v;
 }
 
-// dense copy of a BSR matrix (row-major m x m, m = 3 nr)
+// dense copy of a BSR matrix (row-major m x m, m = B nr); block I of the grid
+// copies block row I, BB threads per block
+template <int B>
 __global__ void k_to_dense(int nr, const int *__restrict__ rp, const int *__restrict__ col,
                            const double *__restrict__ val, double *__restrict__ D) {
+  constexpr int BB = B * B;
   const int I = blockIdx.x;
-  const int m = 3 * nr;
-  for (int k = rp[I] + threadIdx.x / 9; k < rp[I + 1]; k += blockDim.x / 9) {
-    if ((int)threadIdx.x >= (blockDim.x / 9) * 9) break;
-    const int e = threadIdx.x % 9, r = e / 3, c = e % 3;
-    D[(size_t)(3 * I + r) * m + 3 * col[k] + c] = val[(size_t)k * 9 + e];
+  const long m = (long)B * nr;
+  for (int k = rp[I] + threadIdx.x / BB; k < rp[I + 1]; k += blockDim.x / BB) {
+    if ((int)threadIdx.x >= (blockDim.x / BB) * BB) break;
+    const int e = threadIdx.x % BB, r = e / B, c = e % B;
+    D[(size_t)((long)B * I + r) * m + (long)B * col[k] + c] = val[(size_t)k * BB + e];
   }
 }
 
@@ -230,7 +240,7 @@ __global__ void __launch_bounds__(256) k_gj_update(int m, int k0, int nb, double
 // ---------------------------------------------------------------- host graph work
 int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s) {
   const int nnzb = A.nnzb;
-  AMG_TRY(T.alloc(A.nc, A.nr, nnzb));
+  AMG_TRY(T.alloc(A.nc, A.nr, nnzb, A.b));
   T.h_rowptr.assign(A.nc + 1, 0);
   T.h_col.resize(nnzb);
   std::vector<int> perm(nnzb > 0 ? nnzb : 1);
@@ -248,7 +258,10 @@ int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s) {
     DBuf<int> dperm;
     AMG_TRY(dperm.alloc(nnzb));
     AMG_CU(cudaMemcpyAsync(dperm.p, perm.data(), nnzb * sizeof(int), cudaMemcpyHostToDevice, s));
-    AMG_KCOUNT k_transpose_vals<<<nblk(9L * nnzb, 256), 256, 0, s>>>(nnzb, dperm.p, A.val.p, T.val.p);
+    if (A.b == 1)
+      AMG_KCOUNT k_transpose_vals<1><<<nblk((long)nnzb, 256), 256, 0, s>>>(nnzb, dperm.p, A.val.p, T.val.p);
+    else
+      AMG_KCOUNT k_transpose_vals<3><<<nblk(9L * nnzb, 256), 256, 0, s>>>(nnzb, dperm.p, A.val.p, T.val.p);
     AMG_LAUNCH_CHECK();
     AMG_CU(cudaStreamSynchronize(s));
   }
@@ -602,7 +615,7 @@ static int symbolic_product_gpu(const DevBsr &X, const DevBsr &Y, DevBsr &Z, boo
   int nnz = 0;
   AMG_CU(cudaMemcpyAsync(&nnz, rp.p + nr, sizeof(int), cudaMemcpyDeviceToHost, s));
   AMG_CU(cudaStreamSynchronize(s));
-  AMG_TRY(Z.alloc(nr, Y.nc, nnz));
+  AMG_TRY(Z.alloc(nr, Y.nc, nnz, X.b));
   AMG_CU(cudaMemcpyAsync(Z.rowptr.p, rp.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
   if (nr) AMG_KCOUNT k_sym_merge<<<nb, 256, 0, s>>>(nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, rp.p, Z.col.p, nullptr);
   AMG_LAUNCH_CHECK();
@@ -619,7 +632,7 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
   bool ap_host = false;
   if (rc == AMG_ERR_ARG) {
     symbolic_product(A, P, AP);
-    AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb));
+    AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb, A.b));
     AMG_TRY(AP.upload_pattern(s));
     ap_host = true;
   } else if (rc) {
@@ -635,7 +648,7 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
   if (rc == AMG_ERR_ARG) {
     if (!ap_host) AMG_TRY(AP.download_pattern(s));
     symbolic_product(R, AP, Ac);
-    AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb));
+    AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb, A.b));
     AMG_TRY(Ac.upload_pattern(s));
   } else if (rc) {
     return rc;
@@ -656,9 +669,10 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
   for (int I = 0; I < n; ++I) maxdeg = std::max(maxdeg, A.h_rowptr[I + 1] - A.h_rowptr[I]);
   DBuf<int> np, pat, status;
   DBuf<double> val;
+  const int bb = A.b * A.b;
   AMG_TRY(np.alloc(n));
   AMG_TRY(pat.alloc((size_t)n * maxg));
-  AMG_TRY(val.alloc((size_t)n * (maxg + 1) * 9));
+  AMG_TRY(val.alloc((size_t)n * (maxg + 1) * bb));
   AMG_TRY(status.alloc(1));
   AMG_TRY(status.zero(s));
   det::FsaiOut out{np.p, pat.p, val.p};
@@ -682,11 +696,15 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
       o[hnp[I]] = I;
     }
   });
-  AMG_TRY(G.alloc(n, n, (int)cl.size()));
+  AMG_TRY(G.alloc(n, n, (int)cl.size(), A.b));
   G.h_rowptr = std::move(rp);
   G.h_col = std::move(cl);
   AMG_TRY(G.upload_pattern(s));
-  AMG_KCOUNT k_compact_vals<<<nblk((long)n * (maxg + 1) * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
+  if (A.b == 1)
+    AMG_KCOUNT k_compact_vals<1><<<nblk((long)n * (maxg + 1), 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
+  else
+    AMG_KCOUNT k_compact_vals<3><<<nblk((long)n * (maxg + 1) * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p,
+                                                                                   G.val.p);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -706,7 +724,7 @@ int bench_fsai(Handle *h, int lev, int reps, double *ms) {
   DBuf<double> val;
   AMG_TRY(np.alloc(n));
   AMG_TRY(pat.alloc((size_t)n * maxg));
-  AMG_TRY(val.alloc((size_t)n * (maxg + 1) * 9));
+  AMG_TRY(val.alloc((size_t)n * (maxg + 1) * L.A.b * L.A.b));
   AMG_TRY(status.alloc(1));
   AMG_TRY(status.zero(s));
   det::FsaiOut out{np.p, pat.p, val.p};
@@ -861,7 +879,8 @@ static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong
   L.nc = nc;
   double tt = now_s();
   const int nf = (int)fnodes.size();
-  const int cap = std::max(1, std::min(p.n_max, t / 3));
+  const int B = L.A.b, BB = B * B;
+  const int cap = std::max(1, std::min(p.n_max, t / B));
   DBuf<int> d_cidx, d_f, d_cptr, d_cand, d_cnt, d_col, d_cf;
   DBuf<double> d_val;
   AMG_TRY(d_cidx.alloc(n));
@@ -869,7 +888,7 @@ static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong
   AMG_TRY(d_cptr.alloc(nf + 1));
   AMG_TRY(d_cnt.alloc(nf));
   AMG_TRY(d_col.alloc((size_t)nf * cap));
-  AMG_TRY(d_val.alloc((size_t)nf * cap * 9));
+  AMG_TRY(d_val.alloc((size_t)nf * cap * BB));
   AMG_CU(cudaMemcpyAsync(d_cidx.p, cidx.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
   if (nf) AMG_CU(cudaMemcpyAsync(d_f.p, fnodes.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s));
   int maxdeg = 0;
@@ -920,14 +939,18 @@ static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong
     }
     rp[I + 1] = (int)cl.size();
   }
-  AMG_TRY(L.P.alloc(n, nc, (int)cl.size()));
+  AMG_TRY(L.P.alloc(n, nc, (int)cl.size(), B));
   L.P.h_rowptr = std::move(rp);
   L.P.h_col = std::move(cl);
   AMG_TRY(L.P.upload_pattern(s));
   DBuf<int> d_fidx;
   AMG_TRY(d_fidx.alloc(n));
   AMG_CU(cudaMemcpyAsync(d_fidx.p, fidx.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
-  AMG_KCOUNT k_p_vals<<<nblk((long)n * cap * 9, 256), 256, 0, s>>>(n, L.P.rowptr.p, d_fidx.p, cap, d_val.p, L.P.val.p);
+  if (B == 1)
+    AMG_KCOUNT k_p_vals<1><<<nblk((long)n * cap, 256), 256, 0, s>>>(n, L.P.rowptr.p, d_fidx.p, cap, d_val.p, L.P.val.p);
+  else
+    AMG_KCOUNT k_p_vals<3><<<nblk((long)n * cap * 9, 256), 256, 0, s>>>(n, L.P.rowptr.p, d_fidx.p, cap, d_val.p,
+                                                                      L.P.val.p);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -935,7 +958,7 @@ static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong
 
 static int coarse_factor(Handle *h, Level &L) {
   cudaStream_t s = h->stream;
-  const int m = 3 * L.n;
+  const int m = L.A.b * L.n;
   if (m > 6000) {
     set_error("last level has %d dofs; the dense coarse solve supports at most 6000", m);
     return AMG_ERR_COARSENING;
@@ -952,7 +975,8 @@ static int coarse_factor(Handle *h, Level &L) {
     AMG_TRY(R.alloc((size_t)CB * m));
     AMG_TRY(C.alloc((size_t)m * CB));
     double *D = h->Cinv.p;
-    AMG_KCOUNT k_to_dense<<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
+    if (L.A.b == 1) AMG_KCOUNT k_to_dense<1><<<L.n, 128, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
+    else AMG_KCOUNT k_to_dense<3><<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
     const int nt = (m + CB - 1) / CB;
     for (int k0 = 0; k0 < m; k0 += CB) {
       const int nb = m - k0 < CB ? m - k0 : CB;
@@ -993,7 +1017,7 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     L0->A = std::move(h->lev[0]->A);
     L0->n = L0->A.nr;
     free_hierarchy(h);
-    AMG_CU(cudaMemcpyAsync(L0->A.val.p, vals, (size_t)L0->A.nnzb * 9 * sizeof(double), kind, s));
+    AMG_CU(cudaMemcpyAsync(L0->A.val.p, vals, (size_t)L0->A.nnzb * h->b * h->b * sizeof(double), kind, s));
   } else {
     free_hierarchy(h);
     if (!rowptr || !col) {
@@ -1005,7 +1029,7 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     if (mem == AMG_MEM_HOST) memcpy(hrp.data(), rowptr, (n + 1) * sizeof(int));
     else AMG_CU(cudaMemcpy(hrp.data(), rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
     const int nnzb = hrp[n];
-    AMG_TRY(L0->A.alloc(n, n, nnzb));
+    AMG_TRY(L0->A.alloc(n, n, nnzb, h->b));
     L0->A.h_rowptr = std::move(hrp);
     L0->A.h_col.resize(nnzb);
     if (mem == AMG_MEM_HOST) memcpy(L0->A.h_col.data(), col, nnzb * sizeof(int));
@@ -1020,13 +1044,13 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
       }
     }
     AMG_TRY(L0->A.upload_pattern(s));
-    AMG_CU(cudaMemcpyAsync(L0->A.val.p, vals, (size_t)nnzb * 9 * sizeof(double), kind, s));
+    AMG_CU(cudaMemcpyAsync(L0->A.val.p, vals, (size_t)nnzb * h->b * h->b * sizeof(double), kind, s));
     L0->n = n;
   }
   // starting test space: V0 padded with counter-generator columns
   DBuf<double> Vin;
   {
-    const int n3 = 3 * h->n;
+    const int n3 = h->b * h->n;
     AMG_TRY(Vin.alloc((size_t)n3 * t));
     if (ntv0 > 0)
       AMG_CU(cudaMemcpyAsync(Vin.p, V0, (size_t)n3 * ntv0 * sizeof(double),
@@ -1042,7 +1066,8 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
   DBuf<unsigned char> d_strong;
   for (int k = 0;; ++k) {
     Level &L = *h->lev[k];
-    const int n3 = 3 * L.n;
+    const int B = h->b;
+    const int n3 = B * L.n;
     if (n3 <= p.n_coarse || k == p.max_levels - 1 || k == 31) break;
     double t0 = now_s();
     DBuf<double> om;
@@ -1113,19 +1138,19 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     T_rap += t5 - t4;
     // next level's starting test space: rows of the coarse nodes
     {
-      std::vector<int> src(3 * nc);
+      std::vector<int> src((size_t)B * nc);
       int q = 0;
       for (int I = 0; I < L.n; ++I)
         if (L.cf[I] == 1) {
-          for (int c = 0; c < 3; ++c) src[3 * q + c] = 3 * I + c;
+          for (int c = 0; c < B; ++c) src[(size_t)B * q + c] = B * I + c;
           ++q;
         }
       DBuf<int> dsrc;
-      AMG_TRY(dsrc.alloc(3 * nc));
-      AMG_CU(cudaMemcpyAsync(dsrc.p, src.data(), 3 * nc * sizeof(int), cudaMemcpyHostToDevice, s));
+      AMG_TRY(dsrc.alloc((size_t)B * nc));
+      AMG_CU(cudaMemcpyAsync(dsrc.p, src.data(), (size_t)B * nc * sizeof(int), cudaMemcpyHostToDevice, s));
       DBuf<double> Vn;
-      AMG_TRY(Vn.alloc((size_t)3 * nc * t));
-      AMG_TRY(det::gather_rows(dsrc.p, 3 * nc, n3, t, L.V.p, Vn.p, s));
+      AMG_TRY(Vn.alloc((size_t)B * nc * t));
+      AMG_TRY(det::gather_rows(dsrc.p, B * nc, n3, t, L.V.p, Vn.p, s));
       AMG_CU(cudaStreamSynchronize(s));
       Vin = std::move(Vn);
     }

@@ -44,7 +44,7 @@ int prepare_solve(Handle *h) {
       AMG_TRY(tune_solvemat(L.sP, kg, s));
       AMG_TRY(tune_solvemat(L.sR, kg, s));
     }
-    const size_t n3 = 3 * (size_t)L.n;
+    const size_t n3 = (size_t)h->b * L.n;
     if (f64) {
       AMG_TRY(L.y64.alloc(n3)); AMG_TRY(L.z64.alloc(n3));
       AMG_TRY(L.s64.alloc(n3)); AMG_TRY(L.r64.alloc(n3)); AMG_TRY(L.t64.alloc(n3));
@@ -371,7 +371,7 @@ __global__ void k_set_flags(int *flags, int maxit) {
 
 static int ensure_pcg(Handle *h) {
   if (h->kcap >= 1 && h->x.p) return AMG_OK;
-  const size_t n3 = 3 * (size_t)h->n;
+  const size_t n3 = (size_t)h->b * h->n;
   AMG_TRY(h->x.alloc(n3));
   AMG_TRY(h->r.alloc(n3));
   AMG_TRY(h->z.alloc(n3));
@@ -397,7 +397,7 @@ template <typename TX>
 static void pcg_iteration(Handle *h, bool mixed) {
   cudaStream_t s = h->stream;
   Level &L0 = *h->lev[0];
-  const long n = 3L * h->n;
+  const long n = (long)h->b * h->n;
   double *part = h->red.p, *part2 = h->red.p + 2 * RED_BLOCKS;
   int *fl = h->flags.p;
   double *sc = h->scal.p;
@@ -424,7 +424,7 @@ template <typename TX>
 static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int *iters, double *relres,
                          double *rec_relres, int *nrestart, bool mixed) {
   cudaStream_t s = h->stream;
-  const long n = 3L * h->n;
+  const long n = (long)h->b * h->n;
   double *part = h->red.p;
   int *fl = h->flags.p;
   double *sc = h->scal.p;
@@ -523,7 +523,7 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
 int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres) {
   if (k > 1) return solve_batched(h, k, B, X, rtol, iters, relres);
   AMG_TRY(ensure_pcg(h));
-  const long n = 3L * h->n;
+  const long n = (long)h->b * h->n;
   const bool mixed = h->prm.vcycle_prec != AMG_FP64;
   int worst = AMG_OK, maxit = 0, nrs = 0;
   double rec_max = 0.0, true_max = 0.0;
@@ -561,7 +561,7 @@ __global__ void k_f2d(long n, const float *__restrict__ a, double *__restrict__ 
 int vcycle_apply(Handle *h, const double *y, double *z) {
   AMG_TRY(ensure_pcg(h));
   cudaStream_t s = h->stream;
-  const long n = 3L * h->n;
+  const long n = (long)h->b * h->n;
   AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(h->flags.p, 1);
   if (h->prm.vcycle_prec == AMG_FP64) {
     vcycle_level<double>(h, 0, y, z, h->flags.p + F_DONE);
@@ -622,7 +622,7 @@ int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
   AMG_TRY(vc_scratch_address(&base));
   int *flags = (int *)base;
   cudaStream_t s = h->stream;
-  const long n = 3L * h->n;
+  const long n = (long)h->b * h->n;
   // the flag block keeps the previous call's contents: reset it first
   AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(flags, 1);
   if (h->prm.vcycle_prec == AMG_FP64) {
@@ -652,7 +652,7 @@ int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, dou
   }
   if (which == 5) {  // the set-up's FP64 product of A_k with the n_tv test-space columns
     const int t = h->prm.n_tv;
-    const size_t n = 3 * (size_t)L.A.nr;
+    const size_t n = (size_t)L.A.b * L.A.nr;
     if (L.A.nr == 0) return AMG_ERR_ARG;
     cudaStream_t s = h->stream;
     DBuf<double> X, Y;
@@ -672,7 +672,7 @@ int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, dou
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *ms = (double)tm / reps;
-    *bytes = (double)L.A.nnzb * (9.0 * 8 + 4.0) + 4.0 * (L.A.nr + 1) + 8.0 * t * (2.0 * n);
+    *bytes = (double)L.A.nnzb * (L.A.b * L.A.b * 8.0 + 4.0) + 4.0 * (L.A.nr + 1) + 8.0 * t * (2.0 * n);
     return AMG_OK;
   }
   SolveMat *M = which == 0 ? &L.sA : which == 1 ? &L.sG : which == 2 ? &L.sGT : which == 3 ? &L.sP : &L.sR;
@@ -681,7 +681,7 @@ int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, dou
   const int prec = h->prm.vcycle_prec;
   const bool dbl = (prec == AMG_FP64) || (which == 0 && a64 && M->v64.p);
   const bool b16 = !dbl && prec == AMG_FP32_BF16GP && which != 0;
-  const size_t nx = 3 * (size_t)M->nc, ny = 3 * (size_t)M->nr;
+  const size_t nx = (size_t)M->b * M->nc, ny = (size_t)M->b * M->nr;
   const size_t xs = dbl ? 8 : 4, vs = dbl ? 8 : (b16 ? 2 : 4);
   DBuf<double> x64, y64;
   DBuf<float> x32, y32;
@@ -713,7 +713,7 @@ int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, dou
   cudaEventDestroy(e1);
   AMG_LAUNCH_CHECK();
   *ms = (double)t / reps;
-  *bytes = (double)M->nnzb * (9.0 * vs + 4.0) + 4.0 * (M->nr + 1) + (double)xs * (nx + ny);
+  *bytes = (double)M->nnzb * (M->b * M->b * vs + 4.0) + 4.0 * (M->nr + 1) + (double)xs * (nx + ny);
   return AMG_OK;
 }
 

@@ -52,7 +52,7 @@ template <int WPS> struct SellCta {
   static constexpr int slices = warps / WPS;
 };
 
-template <typename TM, typename TX, int EP, int WPS, int U>
+template <typename TM, typename TX, int B, int EP, int WPS, int U>
 __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int nr, const int *__restrict__ rp,
                                                                   const int *__restrict__ slp,
                                                                   const int *__restrict__ scol,
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int nr, const 
                                                                   const TX *__restrict__ aux, TX w,
                                                                   const int *__restrict__ done) {
   if (done && *done) return;
-  constexpr int SPB = SellCta<WPS>::slices;
+  constexpr int SPB = SellCta<WPS>::slices, BB = B * B;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sl = blockIdx.x * SPB + warp / WPS;
   const int part = warp % WPS;
@@ -72,55 +72,63 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int nr, const 
   RowAcc<TX> acc;
   for (int j0 = part; j0 < len; j0 += WPS * U) {
     int c[U];
-    TM m[U][9];
+    TM m[U][BB];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * WPS;
       if (j < len) {
         const long slot = base + 32L * j;
         c[u] = scol[slot + lane];
-        const TM *vp = v + 9 * slot + lane;
+        const TM *vp = v + BB * slot + lane;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) m[u][e] = vp[32 * e];
+        for (int e = 0; e < BB; ++e) m[u][e] = vp[32 * e];
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * WPS;
       if (j < len) {
-        const TX *xp = x + 3L * c[u];
-        const TX x0 = xp[0], x1 = xp[1], x2 = xp[2];
+        const TX *xp = x + (long)B * c[u];
+        if constexpr (B == 3) {
+          const TX x0 = xp[0], x1 = xp[1], x2 = xp[2];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
-          acc.add(r, cvs(m[u][3 * r], TX(0)), cvs(m[u][3 * r + 1], TX(0)), cvs(m[u][3 * r + 2], TX(0)), x0, x1, x2);
+          for (int r = 0; r < 3; ++r)
+            acc.add(r, cvs(m[u][3 * r], TX(0)), cvs(m[u][3 * r + 1], TX(0)), cvs(m[u][3 * r + 2], TX(0)), x0, x1,
+                    x2);
+        } else {
+          acc.add1(0, cvs(m[u][0], TX(0)), xp[0]);
+        }
       }
     }
   }
   if (WPS > 1) {
-    __shared__ TX red[SellCta<WPS>::warps][6][32];
+    __shared__ TX red[SellCta<WPS>::warps][2 * B][32];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < B; ++r) {
       red[warp][r][lane] = acc.hi(r);
-      red[warp][3 + r][lane] = acc.lo(r);
+      red[warp][B + r][lane] = acc.lo(r);
     }
     __syncthreads();
     if (part != 0) return;
 #pragma unroll
     for (int p = 1; p < WPS; ++p)
 #pragma unroll
-      for (int r = 0; r < 3; ++r) acc.merge(r, red[warp + p][r][lane], red[warp + p][3 + r][lane]);
+      for (int r = 0; r < B; ++r) acc.merge(r, red[warp + p][r][lane], red[warp + p][B + r][lane]);
   }
-  const TX a0 = acc.get(0), a1 = acc.get(1), a2 = acc.get(2);
   if (!valid) return;
-  const long o = 3L * row;
-  if (EP == EP_SET) { y[o] = a0; y[o + 1] = a1; y[o + 2] = a2; }
-  if (EP == EP_SCALE) { y[o] = w * a0; y[o + 1] = w * a1; y[o + 2] = w * a2; }
-  if (EP == EP_RESID) { y[o] = aux[o] - a0; y[o + 1] = aux[o + 1] - a1; y[o + 2] = aux[o + 2] - a2; }
-  if (EP == EP_SADD) { y[o] = aux[o] + w * a0; y[o + 1] = aux[o + 1] + w * a1; y[o + 2] = aux[o + 2] + w * a2; }
-  if (EP == EP_ACC) { y[o] += a0; y[o + 1] += a1; y[o + 2] += a2; }
+  const long o = (long)B * row;
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const TX a = acc.get(r);
+    if (EP == EP_SET) y[o + r] = a;
+    if (EP == EP_SCALE) y[o + r] = w * a;
+    if (EP == EP_RESID) y[o + r] = aux[o + r] - a;
+    if (EP == EP_SADD) y[o + r] = aux[o + r] + w * a;
+    if (EP == EP_ACC) y[o + r] += a;
+  }
 }
 
-template <typename TM, typename TX, int WPS, int U>
+template <typename TM, typename TX, int B, int WPS, int U>
 static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
                        const int *done, cudaStream_t s) {
   const int nb = nblk(M.ns, SellCta<WPS>::slices);
@@ -128,11 +136,11 @@ static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *
   if (nb == 0) return;
 #define AMG_SELL_ARGS M.nr, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
   switch (ep) {
-    case EP_SET: AMG_KCOUNT k_sellmv<TM, TX, EP_SET, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SCALE: AMG_KCOUNT k_sellmv<TM, TX, EP_SCALE, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_RESID: AMG_KCOUNT k_sellmv<TM, TX, EP_RESID, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SADD: AMG_KCOUNT k_sellmv<TM, TX, EP_SADD, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
-    default: AMG_KCOUNT k_sellmv<TM, TX, EP_ACC, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SET: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SET, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SCALE: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SCALE, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_RESID: AMG_KCOUNT k_sellmv<TM, TX, B, EP_RESID, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SADD: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SADD, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    default: AMG_KCOUNT k_sellmv<TM, TX, B, EP_ACC, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
   }
 #undef AMG_SELL_ARGS
 }
@@ -341,23 +349,31 @@ int bulk_copy_error() {
   return AMG_OK;
 }
 
-template <typename TM, typename TX>
-void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
-           cudaStream_t s) {
+template <typename TM, typename TX, int B>
+static void bsrmv_b(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
+                    cudaStream_t s) {
   switch (std::is_same<TM, double>::value ? M.map64 : M.map) {
-    case 0: launch_map<TM, TX, 1, 2>(ep, M, v, x, y, aux, w, done, s); break;
-    case 1: launch_map<TM, TX, 1, 4>(ep, M, v, x, y, aux, w, done, s); break;
-    case 2: launch_map<TM, TX, 2, 2>(ep, M, v, x, y, aux, w, done, s); break;
-    case 3: launch_map<TM, TX, 2, 4>(ep, M, v, x, y, aux, w, done, s); break;
-    case 4: launch_map<TM, TX, 4, 2>(ep, M, v, x, y, aux, w, done, s); break;
-    case 5: launch_map<TM, TX, 4, 4>(ep, M, v, x, y, aux, w, done, s); break;
-    case 6: launch_map<TM, TX, 8, 2>(ep, M, v, x, y, aux, w, done, s); break;
-    case 7: launch_map<TM, TX, 16, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 0: launch_map<TM, TX, B, 1, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 1: launch_map<TM, TX, B, 1, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 2: launch_map<TM, TX, B, 2, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 3: launch_map<TM, TX, B, 2, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 4: launch_map<TM, TX, B, 4, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 5: launch_map<TM, TX, B, 4, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 6: launch_map<TM, TX, B, 8, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 7: launch_map<TM, TX, B, 16, 2>(ep, M, v, x, y, aux, w, done, s); break;
     default:
-      if constexpr (std::is_same<TM, double>::value) launch_map<TM, TX, 1, 2>(ep, M, v, x, y, aux, w, done, s);
+      // the bulk-copy variant is written for 3x3 blocks in FP32/bf16
+      if constexpr (std::is_same<TM, double>::value || B != 3) launch_map<TM, TX, B, 1, 2>(ep, M, v, x, y, aux, w, done, s);
       else launch_bulk<TM, TX>(ep, M, v, x, y, aux, w, done, s);
       break;
   }
+}
+
+template <typename TM, typename TX>
+void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
+           cudaStream_t s) {
+  if (M.b == 1) bsrmv_b<TM, TX, 1>(ep, M, v, x, y, aux, w, done, s);
+  else bsrmv_b<TM, TX, 3>(ep, M, v, x, y, aux, w, done, s);
 }
 
 template void bsrmv<double, double>(int, const SolveMat &, const double *, const double *, double *, const double *,
@@ -379,10 +395,11 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(dou
   return __float2bfloat16_rn((float)a);
 }
 
-template <typename T>
+template <typename T, int B>
 __global__ void k_to_sell(int nr, const int *__restrict__ rp, const int *__restrict__ col,
                           const double *__restrict__ src, const int *__restrict__ slp, int *__restrict__ scol,
                           T *__restrict__ dst) {
+  constexpr int BB = B * B;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= nr) return;
   const int sl = row >> 5, lane = row & 31;
@@ -391,10 +408,20 @@ __global__ void k_to_sell(int nr, const int *__restrict__ rp, const int *__restr
   for (int j = 0; j < len; ++j) {
     const long slot = base + 32L * j;
     if (scol) scol[slot + lane] = col[kb + j];
-    const double *b = src + 9L * (kb + j);
+    const double *b = src + (long)BB * (kb + j);
 #pragma unroll
-    for (int e = 0; e < 9; ++e) dst[9 * slot + 32 * e + lane] = from_f64<T>(b[e]);
+    for (int e = 0; e < BB; ++e) dst[BB * slot + 32 * e + lane] = from_f64<T>(b[e]);
   }
+}
+
+template <typename T>
+static void to_sell(const DevBsr &A, const SolveMat &M, int *cols, T *dst, cudaStream_t s) {
+  const int nb = nblk(A.nr, 128);
+  if (!nb) return;
+  if (A.b == 1)
+    AMG_KCOUNT k_to_sell<T, 1><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, dst);
+  else
+    AMG_KCOUNT k_to_sell<T, 3><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, dst);
 }
 
 // Mapping rule for matrices too small to time: few slices of long rows
@@ -418,6 +445,7 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
   M.nr = A.nr;
   M.nc = A.nc;
   M.nnzb = A.nnzb;
+  M.b = A.b;
   M.rowptr = A.rowptr.p;
   M.col = A.col.p;
   M.ns = (A.nr + 31) / 32;
@@ -440,24 +468,21 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
   AMG_CU(cudaMemcpyAsync(M.slp.p, hs.data(), (M.ns + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   AMG_TRY(M.scol.alloc(tot));
   M.map = M.map64 = rule_map(M);
-  const long n9 = 9L * tot;
-  const int nb = nblk(A.nr, 128);
+  const long n9 = (long)A.b * A.b * tot;
   int *cols = M.scol.p;
   if (f64) {
     AMG_TRY(M.v64.alloc(n9));
-    if (nb) AMG_KCOUNT k_to_sell<double><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, M.v64.p);
+    to_sell<double>(A, M, cols, M.v64.p, s);
     cols = nullptr;
   }
   if (f32) {
     AMG_TRY(M.v32.alloc(n9));
-    if (nb) AMG_KCOUNT k_to_sell<float><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, M.v32.p);
+    to_sell<float>(A, M, cols, M.v32.p, s);
     cols = nullptr;
   }
   if (b16) {
     AMG_TRY(M.v16.alloc(n9));
-    if (nb)
-      AMG_KCOUNT k_to_sell<__nv_bfloat16><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols,
-                                                               M.v16.p);
+    to_sell<__nv_bfloat16>(A, M, cols, M.v16.p, s);
   }
   AMG_LAUNCH_CHECK();
   // the host slice offsets must outlive the asynchronous copy
@@ -493,8 +518,8 @@ static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
       }
   }
   DBuf<TX> x, y;
-  AMG_TRY(x.alloc(3 * (size_t)M.nc));
-  AMG_TRY(y.alloc(3 * (size_t)M.nr));
+  AMG_TRY(x.alloc((size_t)M.b * M.nc));
+  AMG_TRY(y.alloc((size_t)M.b * M.nr));
   AMG_TRY(x.zero(s));
   cudaEvent_t e0, e1;
   AMG_CU(cudaEventCreate(&e0));
@@ -505,7 +530,7 @@ static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
   for (int c = 0; c < kNumMaps; ++c) {
     const int wps = kMaps[c].wps == 0 ? 1 : kMaps[c].wps;  // bulk copy: one warp per slice
     if (wps != rule_wps) continue;
-    if (kMaps[c].wps == 0 && std::is_same<TM, double>::value) continue;  // FP64 has no bulk variant
+    if (kMaps[c].wps == 0 && (std::is_same<TM, double>::value || M.b != 3)) continue;  // no bulk variant
     map = c;
     bsrmv<TM, TX>(EP_SET, M, v, x.p, y.p, (const TX *)nullptr, TX(0), nullptr, s);
     AMG_CU(cudaEventRecord(e0, s));
