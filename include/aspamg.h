@@ -215,6 +215,36 @@ long long amg_launch_count(void);
  * (pool or otherwise) and no allocating library routine is called. */
 int amg_vcycle_noalloc(amg_handle h, const double *y, double *z);
 
+/* ---- row-partitioned solve (one process per GPU; the orchestration,
+ * halo exchange and all-reduces are in paper_1902_01715_gb300/dist.py) ----
+ * Every rank builds the same hierarchy and applies the products of its own
+ * block rows.  Vectors are device arrays of the level's full length on every
+ * rank; the calls run on the handle's stream and return without waiting. */
+/* y = epilogue(M x) on block rows [row0, row1) of matrix `which` (0 A, 1 G,
+ * 2 G^T, 3 P, 4 R) of level `lev`, FP64 storage (a handle with an FP64
+ * V-cycle, or the level-0 A of any handle): ep 0 y = Mx, 1 y = w Mx,
+ * 2 y = aux - Mx, 3 y = aux + w Mx, 4 y += Mx, on those rows only.  Entries
+ * of x outside the rank's rows must already hold the owners' values (the
+ * halo).  Errors: AMG_ERR_ARG (bad level, matrix, rows, or no FP64 copy). */
+int amg_level_apply(amg_handle h, int lev, int which, int ep, int row0,
+                    int row1, const double *x, double *y, const double *aux,
+                    double w);
+/* z = A_L^{-1} y on the last level (its explicit inverse, FP64, all rows). */
+int amg_coarse_apply(amg_handle h, const double *y, double *z);
+/* *out (device) = sum over i in [n0, n1) of x_i y_i in a fixed order (one
+ * block: thread j sums i = n0 + j, n0 + j + 256, ..., then a binary tree). */
+int amg_range_dot(long long n0, long long n1, const double *x, const double *y,
+                  double *out, void *stream);
+/* y_i = a x_i + b y_i for i in [n0, n1) (device vectors). */
+int amg_range_axpby(long long n0, long long n1, double a, const double *x,
+                    double b, double *y, void *stream);
+/* out[i] = x[idx[i]] and x[idx[i]] = in[i], i < m (device arrays; idx int64):
+ * packing and unpacking of halo exchanges. */
+int amg_gather(long long m, const long long *idx, const double *x, double *out,
+               void *stream);
+int amg_scatter(long long m, const long long *idx, const double *in, double *x,
+                void *stream);
+
 /* ---- structured Q1-hex elasticity problems (problem generation) ----
  * Mesh: nodes (ix,iy,iz) with global id ix + (nx+1)(iy + (ny+1) iz) at
  * (ix hx, iy hy, iz hz); element (ex,ey,ez) id ex + nx (ey + ny ez); clamp

@@ -28,6 +28,7 @@ EXPORTS = [
     "amg_level_info", "amg_level_matrix", "amg_level_cf", "amg_level_testspace", "amg_vcycle",
     "amg_fe_size", "amg_fe_assemble", "amg_fe_load", "amg_fe_rbm", "amg_fe_conn",
     "amg_bench_spmv", "amg_launch_count", "amg_vcycle_noalloc", "amg_bsr_to_scalar",
+    "amg_level_apply", "amg_coarse_apply", "amg_range_dot", "amg_range_axpby", "amg_gather", "amg_scatter",
 ]
 
 
@@ -106,6 +107,13 @@ def lib(path: str | None = None):
         "amg_launch_count": (C.c_longlong, []),
         "amg_vcycle_noalloc": (C.c_int, [_vp, _vp, _vp]),
         "amg_bsr_to_scalar": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "amg_level_apply": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp,
+                                      C.c_double]),
+        "amg_coarse_apply": (C.c_int, [_vp, _vp, _vp]),
+        "amg_range_dot": (C.c_int, [C.c_longlong, C.c_longlong, _vp, _vp, _vp, _vp]),
+        "amg_range_axpby": (C.c_int, [C.c_longlong, C.c_longlong, C.c_double, _vp, C.c_double, _vp, _vp]),
+        "amg_gather": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp]),
+        "amg_scatter": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

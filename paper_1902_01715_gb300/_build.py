@@ -26,6 +26,7 @@ UNITS = {
     "capi.cu": [],
     "batch.cu": [],
     "spmv.cu": [],
+    "dist.cu": [],
 }
 
 

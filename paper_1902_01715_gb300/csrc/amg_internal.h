@@ -198,6 +198,9 @@ enum { EP_SET = 0, EP_SCALE = 1, EP_RESID = 2, EP_SADD = 3, EP_ACC = 4 };
 template <typename TM, typename TX>
 void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w, const int *done,
            cudaStream_t s);
+// y = epilogue(A x) on block rows [r0, r1) only, FP64 storage
+void bsrmv_rows(int ep, const SolveMat &M, const double *x, double *y, const double *aux, double w, int r0, int r1,
+                cudaStream_t s);
 int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s);
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s);  // kind 0 FP64, 1 FP32, 2 bf16
 const char *mapping_name(const SolveMat &M, bool f64);

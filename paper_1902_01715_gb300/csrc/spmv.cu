@@ -53,7 +53,7 @@ template <int WPS> struct SellCta {
 };
 
 template <typename TM, typename TX, int B, int EP, int WPS, int U>
-__global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int nr, const int *__restrict__ rp,
+__global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int r0, int r1, const int *__restrict__ rp,
                                                                   const int *__restrict__ slp,
                                                                   const int *__restrict__ scol,
                                                                   const TM *__restrict__ v,
@@ -63,10 +63,10 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int nr, const 
   if (done && *done) return;
   constexpr int SPB = SellCta<WPS>::slices, BB = B * B;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sl = blockIdx.x * SPB + warp / WPS;
+  const int sl = (r0 >> 5) + blockIdx.x * SPB + warp / WPS;  // rows [r0, r1) only
   const int part = warp % WPS;
   const int row = sl * 32 + lane;
-  const bool valid = row < nr;
+  const bool valid = row >= r0 && row < r1;
   const int len = valid ? rp[row + 1] - rp[row] : 0;
   const long base = valid ? (long)slp[sl] : 0L;
   RowAcc<TX> acc;
@@ -130,11 +130,14 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int nr, const 
 
 template <typename TM, typename TX, int B, int WPS, int U>
 static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
-                       const int *done, cudaStream_t s) {
-  const int nb = nblk(M.ns, SellCta<WPS>::slices);
+                       const int *done, cudaStream_t s, int r0 = 0, int r1 = -1) {
+  if (r1 < 0) r1 = M.nr;
+  if (r1 <= r0) return;
+  const int nsl = ((r1 - 1) >> 5) - (r0 >> 5) + 1;  // slices holding rows [r0, r1)
+  const int nb = nblk(nsl, SellCta<WPS>::slices);
   constexpr int T = SellCta<WPS>::threads;
   if (nb == 0) return;
-#define AMG_SELL_ARGS M.nr, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
+#define AMG_SELL_ARGS r0, r1, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
   switch (ep) {
     case EP_SET: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SET, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
     case EP_SCALE: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SCALE, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
@@ -374,6 +377,30 @@ void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX 
            cudaStream_t s) {
   if (M.b == 1) bsrmv_b<TM, TX, 1>(ep, M, v, x, y, aux, w, done, s);
   else bsrmv_b<TM, TX, 3>(ep, M, v, x, y, aux, w, done, s);
+}
+
+// rows [r0, r1) only, FP64 storage (the row-partitioned solve)
+template <int B>
+static void bsrmv_rows_b(int ep, const SolveMat &M, const double *x, double *y, const double *aux, double w, int r0,
+                         int r1, cudaStream_t s) {
+  const double *v = M.v64.p;
+  switch (M.map64) {
+    case 0: launch_map<double, double, B, 1, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 1: launch_map<double, double, B, 1, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 2: launch_map<double, double, B, 2, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 3: launch_map<double, double, B, 2, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 4: launch_map<double, double, B, 4, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 5: launch_map<double, double, B, 4, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 6: launch_map<double, double, B, 8, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 7: launch_map<double, double, B, 16, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    default: launch_map<double, double, B, 1, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+  }
+}
+
+void bsrmv_rows(int ep, const SolveMat &M, const double *x, double *y, const double *aux, double w, int r0, int r1,
+                cudaStream_t s) {
+  if (M.b == 1) bsrmv_rows_b<1>(ep, M, x, y, aux, w, r0, r1, s);
+  else bsrmv_rows_b<3>(ep, M, x, y, aux, w, r0, r1, s);
 }
 
 template void bsrmv<double, double>(int, const SolveMat &, const double *, const double *, double *, const double *,

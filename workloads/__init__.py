@@ -34,12 +34,13 @@ class Problem:
     nu: float
     E: np.ndarray                  # (nx*ny*nz,) Young's modulus per element
     clamp_axis: int                # 0: x = 0 face clamped, 2: z = 0 face clamped
-    load: str                      # "body" | "top_pressure" | "end_shear" | "top_nodal"
+    load: str                      # "body" | "top_pressure" | "end_shear" | "top_nodal" | "ones"
     body: tuple = (0.0, 0.0, -1.0)
     pressure: np.ndarray | None = None   # (nx*ny,) per top-face element, pushes -z
     shear_total: float = -1.0           # resultant in z on the x = nx*hx face
     nodal: np.ndarray | None = None      # (k, (nx+1)*(ny+1), 3) forces on top-face nodes
     rho: np.ndarray | None = None        # SIMP densities (adjoint recipe)
+    nu_elem: np.ndarray | None = None    # per-element Poisson ratio (two-material beam)
     nrhs: int = 1
     extra: dict = field(default_factory=dict)
 
@@ -100,6 +101,22 @@ def cube_simp(n: int = 128) -> Problem:
     h = 1.0 / n
     rho = _rng(5).uniform(0.1, 1.0, size=n ** 3)
     return Problem("simp%d" % n, n, n, n, h, h, h, 0.3, rho * rho * rho, 2, "body", rho=rho)
+
+
+def beam6502k(nx: int = 512, ny: int = 64, nz: int = 64) -> Problem:
+    """The paper's beam6502k (App. A.6), synthetic: a 8 x 1 x 1 cantilever of
+    nx x ny x nz cubic elements (512 x 64 x 64: 2,097,152 elements,
+    2,167,425 nodes), x = 0 face clamped, two materials along the length
+    (first half E = 1e4, nu = 0.2; second half E = 1e7, nu = 0.4), and the
+    paper's right-hand side of all ones (Sec. 4).  K_e = E_e Ke0(nu_e): each
+    side assembles one matrix per Poisson ratio with the other material's
+    moduli set to 0 and adds them."""
+    h = 8.0 / nx
+    ex = np.tile(np.arange(nx), ny * nz)
+    first = ex < nx // 2
+    E = np.where(first, 1e4, 1e7)
+    nu_e = np.where(first, 0.2, 0.4)
+    return Problem("beam6502k_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, h, h, h, 0.2, E, 0, "ones", nu_elem=nu_e)
 
 
 CONFIGS = {
