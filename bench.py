@@ -25,6 +25,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -263,6 +265,67 @@ def extra_adjoint(A, W):
            "forward_adjoint_gradient_ms": ms, "setup_ms": st["T_p"] * 1e3, "n_it": st["n_it"],
            "grad_abs_sum": float(g.abs().sum())}
     S.close()
+    return out
+
+
+def extra_scalar_vs_block(A, W):
+    """The bench beam with the paper's scalar method (block size 1: every dof
+    its own node, the per-dof defaults of Table "TestParam") against the
+    3x3-block form: iterations, complexities, set-up and solve time (FP64)."""
+    import torch
+    p = W.beam()
+    d = gpu_problem(A, p)
+    out = {"workload": "cantilever beam 128x32x32 (%d dofs), FP64 V-cycle, rtol 1e-8" % (3 * d["nfree"])}
+    srp, scol, sval = A.bsr_to_scalar(d["rowptr"], d["col"], d["vals"])
+    for name, args, kw in (("block3", (d["rowptr"], d["col"], d["vals"]), {}),
+                           ("scalar", (srp, scol, sval), {"block": 1})):
+        S = A.Solver(*args, d["V0"], **kw)
+        vals = args[2]
+
+        def step():
+            S.update_values(vals)
+            return S.solve(d["f"], RTOL)
+        (x, its, rel, rc), ms = _timed(step)
+        st = S.stats()
+        out[name] = {"ms_per_solution": ms, "n_it": its[0], "setup_ms": st["T_p"] * 1e3, "solve_ms": st["T_s"] * 1e3,
+                     "levels": st["nlev"], "C_gd": st["C_gd"], "C_op": st["C_op"], "C_fs": st["C_fs"],
+                     "true_relres": rel[0]}
+        S.close()
+    return out
+
+
+def extra_beam6502k(A, W):
+    """The paper's beam6502k shape (App. A.6): 512 x 64 x 64 two-material
+    cantilever, right-hand side of ones, FP64 and FP32 V-cycles to 1e-8.  The
+    paper reports 87 iterations, T_p = 115.1 s, T_s = 53.6 s on one KNL with
+    its real matrix (Table of App. A.6, default parameters): context only."""
+    import torch
+    p = W.beam6502k()
+    vals = None
+    for nu in np.unique(p.nu_elem):
+        Em = np.where(p.nu_elem == nu, p.E, 0.0)
+        dm = A.fe_assemble(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, float(nu), Em, p.clamp_axis)
+        if vals is None:
+            d, vals = dm, dm["vals"].clone()
+        else:
+            vals += dm["vals"]
+    n = d["nfree"]
+    V0 = A.fe_rbm(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.clamp_axis, n)
+    f = torch.ones(3 * n, dtype=torch.float64, device="cuda")
+    out = {"workload": "beam6502k-like 512x64x64 (%d dofs, %d blocks), E 1e4/1e7, nu 0.2/0.4, b = ones"
+                       % (3 * n, d["col"].numel()),
+           "paper_context": {"n_it": 87, "T_p_s": 115.1, "T_s_s": 53.6, "hardware": "1x Xeon Phi 7250 (68 cores)"}}
+    for prec in ("fp64", "fp32"):
+        S = A.Solver(d["rowptr"], d["col"], vals, V0, vcycle_prec=prec)
+
+        def step():
+            S.update_values(vals)
+            return S.solve(f, RTOL)
+        (x, its, rel, rc), ms = _timed(step)
+        st = S.stats()
+        out[prec] = {"ms_per_solution": ms, "n_it": its[0], "rc": rc, "setup_ms": st["T_p"] * 1e3,
+                     "solve_ms": st["T_s"] * 1e3, "levels": st["nlev"], "C_op": st["C_op"], "true_relres": rel[0]}
+        S.close()
     return out
 
 
@@ -554,7 +617,8 @@ def run_ours(args):
     extras = None
     if not args.no_extras:
         extras = {"mixed_precision": extra_slab(A, W), "batched": extra_batched(A, W),
-                  "adjoint": extra_adjoint(A, W)}
+                  "adjoint": extra_adjoint(A, W), "scalar_vs_block": extra_scalar_vs_block(A, W),
+                  "beam6502k": extra_beam6502k(A, W)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
