@@ -296,9 +296,12 @@ def extra_scalar_vs_block(A, W):
 
 def extra_beam6502k(A, W):
     """The paper's beam6502k shape (App. A.6): 512 x 64 x 64 two-material
-    cantilever, right-hand side of ones, FP64 and FP32 V-cycles to 1e-8.  The
-    paper reports 87 iterations, T_p = 115.1 s, T_s = 53.6 s on one KNL with
-    its real matrix (Table of App. A.6, default parameters): context only."""
+    cantilever, right-hand side of ones, FP32 V-cycle inside FP64 CG to 1e-8,
+    one set-up and one solve.  The paper reports 87 iterations, T_p = 115.1 s,
+    T_s = 53.6 s on one KNL with its real matrix (App. A.6, default
+    parameters): context only.  The material jump slows this solver down (its
+    iteration count grows with the mesh on this shape), hence the higher
+    iteration limit."""
     import torch
     p = W.beam6502k()
     vals = None
@@ -315,17 +318,12 @@ def extra_beam6502k(A, W):
     out = {"workload": "beam6502k-like 512x64x64 (%d dofs, %d blocks), E 1e4/1e7, nu 0.2/0.4, b = ones"
                        % (3 * n, d["col"].numel()),
            "paper_context": {"n_it": 87, "T_p_s": 115.1, "T_s_s": 53.6, "hardware": "1x Xeon Phi 7250 (68 cores)"}}
-    for prec in ("fp64", "fp32"):
-        S = A.Solver(d["rowptr"], d["col"], vals, V0, vcycle_prec=prec)
-
-        def step():
-            S.update_values(vals)
-            return S.solve(f, RTOL)
-        (x, its, rel, rc), ms = _timed(step)
-        st = S.stats()
-        out[prec] = {"ms_per_solution": ms, "n_it": its[0], "rc": rc, "setup_ms": st["T_p"] * 1e3,
-                     "solve_ms": st["T_s"] * 1e3, "levels": st["nlev"], "C_op": st["C_op"], "true_relres": rel[0]}
-        S.close()
+    S = A.Solver(d["rowptr"], d["col"], vals, V0, vcycle_prec="fp32", maxit=4000)
+    x, its, rel, rc = S.solve(f, RTOL)
+    st = S.stats()
+    out["fp32"] = {"n_it": its[0], "rc": rc, "setup_ms": st["T_p"] * 1e3, "solve_ms": st["T_s"] * 1e3,
+                   "levels": st["nlev"], "C_op": st["C_op"], "true_relres": rel[0]}
+    S.close()
     return out
 
 
