@@ -127,14 +127,16 @@ struct DevBsr {
 
 // Solve-phase copy of a level matrix in the sliced layout of spmv.cu: block
 // rows in slices of 32, slice s owning slots [slp[s], slp[s+1]); slot
-// slp[s] + 32 j + l holds block j of row 32 s + l (column scol[slot], entry e
-// at 9 (slp[s] + 32 j) + 32 e + l of a value array).
+// slp[s] + 32 j + l holds block j of the row at position 32 s + l (row
+// prow[32 s + l], or 32 s + l when prow is empty; column scol[slot], entry e
+// at b*b (slp[s] + 32 j) + 32 e + l of a value array).
 struct SolveMat {
   int nr = 0, nc = 0, nnzb = 0, b = 3;
   int ns = 0;      // slices
   long nslot = 0;  // slots, including padding
   const int *rowptr = nullptr, *col = nullptr;
   DBuf<int> slp, scol;
+  DBuf<int> prow;  // position -> block row (rows sorted by length in windows); empty: identity
   DBuf<double> v64;
   DBuf<float> v32;
   DBuf<__nv_bfloat16> v16;

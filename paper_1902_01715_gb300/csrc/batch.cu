@@ -34,7 +34,8 @@ enum { BE_SET = 0, BE_SCALE = 1, BE_RESID = 2, BE_SADD = 3, BE_ACC = 4 };
 // adds the row's blocks in the same order whatever the mapping, so the
 // mapping changes the time, not the result.
 template <typename TM, typename TX, int B, int EP, int L, int NC>
-__global__ void __launch_bounds__(256) k_bsrmm(int nr, int k, const int *__restrict__ rp, const int *__restrict__ slp,
+__global__ void __launch_bounds__(256) k_bsrmm(int nr, int k, const int *__restrict__ prow, const int *__restrict__ rp,
+                                               const int *__restrict__ slp,
                                                const int *__restrict__ scol, const TM *__restrict__ v,
                                                const TX *__restrict__ X, TX *__restrict__ Y,
                                                const TX *__restrict__ AUX, TX w, const int *__restrict__ done) {
@@ -42,11 +43,12 @@ __global__ void __launch_bounds__(256) k_bsrmm(int nr, int k, const int *__restr
   constexpr int R = 32 / L, BB = B * B;
   const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, gl = lane % L;
-  const long rowl = gw * R + lane / L;
-  if (rowl >= nr) return;
-  const int row = (int)rowl, rl = row & 31;
+  const long posl = gw * R + lane / L;  // position in the sliced layout
+  if (posl >= nr) return;
+  const int pos = (int)posl, rl = pos & 31;
+  const int row = prow ? prow[pos] : pos;
   const int len = rp[row + 1] - rp[row];
-  const long sbase = slp[row >> 5];
+  const long sbase = slp[pos >> 5];
   for (int c0 = 0; c0 < k; c0 += L * NC) {
     RowAcc<TX> acc[NC];
     for (int q = 0; q < len; ++q) {
@@ -105,7 +107,7 @@ static void bmm_launch(int ep, const SolveMat &M, const TM *v, int k, const TX *
   const long warps = (M.nr + R - 1) / R;
   const int nb = nblk(32L * warps, 256);
   if (!nb) return;
-#define AMG_BMM_ARGS M.nr, k, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done
+#define AMG_BMM_ARGS M.nr, k, M.prow.p, M.rowptr, M.slp.p, M.scol.p, v, X, Y, AUX, w, done
   switch (ep) {
     case BE_SET: AMG_KCOUNT k_bsrmm<TM, TX, B, BE_SET, L, NC><<<nb, 256, 0, s>>>(AMG_BMM_ARGS); break;
     case BE_SCALE: AMG_KCOUNT k_bsrmm<TM, TX, B, BE_SCALE, L, NC><<<nb, 256, 0, s>>>(AMG_BMM_ARGS); break;

@@ -12,6 +12,12 @@
 // j-th blocks with one fully used 32-element load per entry, and a slice is
 // one contiguous run of memory.  Padding slots (rows shorter than the
 // slice's longest) are never read: each lane stops at its own row length.
+// Rows are placed in the slices in order of decreasing length inside windows
+// of SIGMA consecutive rows (ties keep row order; prow[position] = row), so
+// the rows of a slice have nearly equal lengths and the lanes of a warp
+// finish together (FP64 instructions cost the same with idle lanes); the
+// window keeps the rows a warp reads and writes close together.  A row is
+// still summed by the same lanes in the same order, whatever its position.
 //
 // Mapping.  WPS warps share one slice (warp p of the slice takes blocks
 // j = p, p + WPS, ...) and their partial sums are added in warp order through
@@ -42,6 +48,7 @@ struct Mapping {
   int wps, u;
 };
 // the last entry is the bulk-copy variant below (FP32 and bf16 storage)
+constexpr int SELL_SIGMA = 1024;  // rows per sorting window (a multiple of 32)
 static const Mapping kMaps[] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}, {4, 4}, {8, 2}, {16, 2}, {0, 0}};
 constexpr int kNumMaps = (int)(sizeof(kMaps) / sizeof(kMaps[0]));
 
@@ -53,7 +60,9 @@ template <int WPS> struct SellCta {
 };
 
 template <typename TM, typename TX, int B, int EP, int WPS, int U>
-__global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int r0, int r1, const int *__restrict__ rp,
+__global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int s0, int r0, int r1, int nr,
+                                                                  const int *__restrict__ prow,
+                                                                  const int *__restrict__ rp,
                                                                   const int *__restrict__ slp,
                                                                   const int *__restrict__ scol,
                                                                   const TM *__restrict__ v,
@@ -63,10 +72,11 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int r0, int r1
   if (done && *done) return;
   constexpr int SPB = SellCta<WPS>::slices, BB = B * B;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sl = (r0 >> 5) + blockIdx.x * SPB + warp / WPS;  // rows [r0, r1) only
+  const int sl = s0 + blockIdx.x * SPB + warp / WPS;
   const int part = warp % WPS;
-  const int row = sl * 32 + lane;
-  const bool valid = row >= r0 && row < r1;
+  const int pos = sl * 32 + lane;
+  const int row = pos < nr ? (prow ? prow[pos] : pos) : -1;
+  const bool valid = row >= r0 && row < r1;  // rows [r0, r1) only
   const int len = valid ? rp[row + 1] - rp[row] : 0;
   const long base = valid ? (long)slp[sl] : 0L;
   RowAcc<TX> acc;
@@ -128,16 +138,29 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int r0, int r1
   }
 }
 
+// positions holding rows [r0, r1): the same range without a permutation, else
+// the SIGMA windows that contain them
+static void row_slices(const SolveMat &M, int r0, int r1, int &s0, int &s1) {
+  int p0 = r0, p1 = r1;
+  if (M.prow.p) {
+    p0 = (r0 / SELL_SIGMA) * SELL_SIGMA;
+    p1 = std::min(M.nr, ((r1 + SELL_SIGMA - 1) / SELL_SIGMA) * SELL_SIGMA);
+  }
+  s0 = p0 >> 5;
+  s1 = ((p1 - 1) >> 5) + 1;
+}
+
 template <typename TM, typename TX, int B, int WPS, int U>
 static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
                        const int *done, cudaStream_t s, int r0 = 0, int r1 = -1) {
   if (r1 < 0) r1 = M.nr;
   if (r1 <= r0) return;
-  const int nsl = ((r1 - 1) >> 5) - (r0 >> 5) + 1;  // slices holding rows [r0, r1)
-  const int nb = nblk(nsl, SellCta<WPS>::slices);
+  int s0, s1;
+  row_slices(M, r0, r1, s0, s1);
+  const int nb = nblk(s1 - s0, SellCta<WPS>::slices);
   constexpr int T = SellCta<WPS>::threads;
   if (nb == 0) return;
-#define AMG_SELL_ARGS r0, r1, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
+#define AMG_SELL_ARGS s0, r0, r1, M.nr, M.prow.p, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
   switch (ep) {
     case EP_SET: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SET, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
     case EP_SCALE: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SCALE, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
@@ -201,7 +224,8 @@ struct BulkStage {
 };
 
 template <typename TM, typename TX, int EP>
-__global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, const int *__restrict__ rp,
+__global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, const int *__restrict__ prow,
+                                                               const int *__restrict__ rp,
                                                                const int *__restrict__ slp,
                                                                const int *__restrict__ scol,
                                                                const TM *__restrict__ v, const TX *__restrict__ x,
@@ -252,7 +276,8 @@ __global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, c
   bool failed = false;
   for (int sl = gw; sl < ns && !failed; sl += nw) {
     const int len_s = (slp[sl + 1] - slp[sl]) >> 5;
-    const int row = sl * 32 + lane;
+    const int pos = sl * 32 + lane;
+    const int row = pos < nr ? (prow ? prow[pos] : pos) : nr;
     const int len = row < nr ? rp[row + 1] - rp[row] : 0;
     RowAcc<TX> acc;
     for (int c = 0; c * BK_JC < len_s; ++c) {
@@ -329,7 +354,7 @@ static void launch_bulk(int ep, const SolveMat &M, const TM *v, const TX *x, TX 
   const int cap = nsm * 5;  // five CTAs per SM
   if (nb > cap) nb = cap;
   if (nb == 0) return;
-#define AMG_BULK_ARGS M.nr, M.ns, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
+#define AMG_BULK_ARGS M.nr, M.ns, M.prow.p, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
   switch (ep) {
     case EP_SET: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_SET><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
     case EP_SCALE: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_SCALE><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
@@ -423,13 +448,14 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(dou
 }
 
 template <typename T, int B>
-__global__ void k_to_sell(int nr, const int *__restrict__ rp, const int *__restrict__ col,
-                          const double *__restrict__ src, const int *__restrict__ slp, int *__restrict__ scol,
-                          T *__restrict__ dst) {
+__global__ void k_to_sell(int nr, const int *__restrict__ prow, const int *__restrict__ rp,
+                          const int *__restrict__ col, const double *__restrict__ src, const int *__restrict__ slp,
+                          int *__restrict__ scol, T *__restrict__ dst) {
   constexpr int BB = B * B;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nr) return;
-  const int sl = row >> 5, lane = row & 31;
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nr) return;
+  const int row = prow ? prow[pos] : pos;
+  const int sl = pos >> 5, lane = pos & 31;
   const int kb = rp[row], len = rp[row + 1] - kb;
   const long base = slp[sl];
   for (int j = 0; j < len; ++j) {
@@ -446,9 +472,9 @@ static void to_sell(const DevBsr &A, const SolveMat &M, int *cols, T *dst, cudaS
   const int nb = nblk(A.nr, 128);
   if (!nb) return;
   if (A.b == 1)
-    AMG_KCOUNT k_to_sell<T, 1><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, dst);
+    AMG_KCOUNT k_to_sell<T, 1><<<nb, 128, 0, s>>>(A.nr, M.prow.p, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, dst);
   else
-    AMG_KCOUNT k_to_sell<T, 3><<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, dst);
+    AMG_KCOUNT k_to_sell<T, 3><<<nb, 128, 0, s>>>(A.nr, M.prow.p, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, dst);
 }
 
 // Mapping rule for matrices too small to time: few slices of long rows
@@ -476,12 +502,28 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
   M.rowptr = A.rowptr.p;
   M.col = A.col.p;
   M.ns = (A.nr + 31) / 32;
+  // rows by decreasing length inside each window of SELL_SIGMA rows (stable)
+  std::vector<int> perm(A.nr);
+  bool ident = true;
+  auto rlen = [&](int r) { return A.h_rowptr[r + 1] - A.h_rowptr[r]; };
+  for (int w0 = 0; w0 < A.nr; w0 += SELL_SIGMA) {
+    const int w1 = std::min(A.nr, w0 + SELL_SIGMA);
+    for (int r = w0; r < w1; ++r) perm[r] = r;
+    std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int a, int b) { return rlen(a) > rlen(b); });
+    for (int r = w0; r < w1 && ident; ++r) ident = perm[r] == r;
+  }
+  if (!ident) {
+    AMG_TRY(M.prow.alloc(A.nr));
+    AMG_CU(cudaMemcpyAsync(M.prow.p, perm.data(), A.nr * sizeof(int), cudaMemcpyHostToDevice, s));
+  } else {
+    M.prow.release();
+  }
   std::vector<int> hs(M.ns + 1, 0);
   long tot = 0;
   for (int sl = 0; sl < M.ns; ++sl) {
     int mx = 0;
     const int r1 = std::min(A.nr, 32 * sl + 32);
-    for (int r = 32 * sl; r < r1; ++r) mx = std::max(mx, A.h_rowptr[r + 1] - A.h_rowptr[r]);
+    for (int r = 32 * sl; r < r1; ++r) mx = std::max(mx, rlen(perm[r]));
     hs[sl] = (int)tot;
     tot += 32L * mx;
   }
