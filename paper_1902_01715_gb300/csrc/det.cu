@@ -791,21 +791,25 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
         score[t] = sc;
       }
       __syncwarp();
-      // the rho best (score > 0, ties to the smaller node), by slot
+      // the rho best (score > 0, ties to the smaller node), by slot.  Scores
+      // are sums of squares (>= +0), whose IEEE bit patterns order like
+      // 64-bit integers, so the selection compares integers (the same
+      // decisions; a double compare would take an FP64 issue slot); a taken
+      // candidate gets the pattern of -1.0 (negative as an integer).
       const int want = active ? (K.rho < K.maxg - np ? K.rho : K.maxg - np) : 0;
       const int wmax = warp_max(want);
       int got = 0;
       bool more = true;
       for (int p = 0; p < wmax; ++p) {
-        double bs = -1.0;
+        long long bs = -1;
         int bj = 0x7fffffff, bt = -1;
         if (more && p < want)
           for (int t = gl; t < nc; t += FS_GL) {
-            const double sc = score[t];
-            if (sc > 0.0 && (sc > bs || (sc == bs && cand[t] < bj))) { bs = sc; bj = cand[t]; bt = t; }
+            const long long sc = __double_as_longlong(score[t]);
+            if (sc > 0 && (sc > bs || (sc == bs && cand[t] < bj))) { bs = sc; bj = cand[t]; bt = t; }
           }
         for (int off = FS_GL / 2; off >= 1; off >>= 1) {
-          const double os = __shfl_xor_sync(0xffffffffu, bs, off);
+          const long long os = __shfl_xor_sync(0xffffffffu, bs, off);
           const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
           const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
           if (os > bs || (os == bs && oj < bj)) { bs = os; bj = oj; bt = ot; }

@@ -502,15 +502,37 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
   M.rowptr = A.rowptr.p;
   M.col = A.col.p;
   M.ns = (A.nr + 31) / 32;
-  // rows by decreasing length inside each window of SELL_SIGMA rows (stable)
-  std::vector<int> perm(A.nr);
-  bool ident = true;
+  // Rows by decreasing length inside each window of SELL_SIGMA rows (stable,
+  // by counting), for FP64 storage only and only where the natural order
+  // fills the slices poorly: FP64 instructions cost the same with idle lanes,
+  // while the bandwidth-bound FP32/bf16 products lose more to the scattered
+  // row order than they gain.
   auto rlen = [&](int r) { return A.h_rowptr[r + 1] - A.h_rowptr[r]; };
-  for (int w0 = 0; w0 < A.nr; w0 += SELL_SIGMA) {
-    const int w1 = std::min(A.nr, w0 + SELL_SIGMA);
-    for (int r = w0; r < w1; ++r) perm[r] = r;
-    std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int a, int b) { return rlen(a) > rlen(b); });
-    for (int r = w0; r < w1 && ident; ++r) ident = perm[r] == r;
+  std::vector<int> perm(A.nr);
+  for (int r = 0; r < A.nr; ++r) perm[r] = r;
+  bool ident = true;
+  if (f64 && !f32 && !b16 && A.nr > 0) {
+    long used = 0, slots = 0;
+    for (int sl = 0; sl < M.ns; ++sl) {
+      int mx = 0;
+      const int r1 = std::min(A.nr, 32 * sl + 32);
+      for (int r = 32 * sl; r < r1; ++r) mx = std::max(mx, rlen(r));
+      slots += 32L * mx;
+    }
+    used = A.nnzb;
+    if (slots > 0 && (double)used < 0.9 * (double)slots) {
+      int maxlen = 0;
+      for (int r = 0; r < A.nr; ++r) maxlen = std::max(maxlen, rlen(r));
+      std::vector<int> cnt(maxlen + 2);
+      for (int w0 = 0; w0 < A.nr; w0 += SELL_SIGMA) {
+        const int w1 = std::min(A.nr, w0 + SELL_SIGMA);
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int r = w0; r < w1; ++r) ++cnt[maxlen - rlen(r) + 1];  // longest first
+        for (int q = 1; q <= maxlen + 1; ++q) cnt[q] += cnt[q - 1];
+        for (int r = w0; r < w1; ++r) perm[w0 + cnt[maxlen - rlen(r)]++] = r;
+      }
+      ident = false;
+    }
   }
   if (!ident) {
     AMG_TRY(M.prow.alloc(A.nr));
