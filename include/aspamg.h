@@ -100,6 +100,8 @@ typedef struct {
    * ||b - K x||/||b||, and the number of true-residual restarts */
   double relres_rec, relres_true;
   int restarts;
+  int vcycle_fused_level; /* levels from this one down run as one persistent
+                           * kernel (-1: every product is its own launch) */
 } amg_stats;
 
 /* Fill *p with the defaults.  Returns AMG_ERR_ARG for p == NULL. */

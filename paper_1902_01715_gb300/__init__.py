@@ -51,7 +51,7 @@ class AmgStats(C.Structure):
                 ("T_p", C.c_double), ("T_s", C.c_double), ("level_nodes", C.c_int * 32),
                 ("level_nnzb", C.c_int * 32), ("level_g_nnzb", C.c_int * 32),
                 ("level_omega", C.c_double * 32), ("relres_rec", C.c_double),
-                ("relres_true", C.c_double), ("restarts", C.c_int)]
+                ("relres_true", C.c_double), ("restarts", C.c_int), ("vcycle_fused_level", C.c_int)]
 
 
 class AmgError(RuntimeError):

@@ -27,6 +27,7 @@ UNITS = {
     "batch.cu": [],
     "spmv.cu": [],
     "dist.cu": [],
+    "vtail.cu": [],
 }
 
 

@@ -206,6 +206,7 @@ void bsrmv_rows(int ep, const SolveMat &M, const double *x, double *y, const dou
 int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s);
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s);  // kind 0 FP64, 1 FP32, 2 bf16
 const char *mapping_name(const SolveMat &M, bool f64);
+int mapping_wps(const SolveMat &M, bool f64);  // warps per slice of the chosen mapping
 int bulk_copy_error();  // AMG_ERR_CUDA (and clears it) if a bulk-copy stage timed out
 
 struct Level {
@@ -255,6 +256,13 @@ struct Handle {
   // while the test space of the same level is generated
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_main = nullptr, ev_aux = nullptr;
+  // fused coarse end of the V-cycle (vtail.cu): start level (-1: off), its
+  // program, grid barrier words, a set "done" flag for the trial capture
+  int vt_level = -1, vt_grid = 0;
+  void *vt_func = nullptr;
+  DBuf<unsigned char> vt_prog;
+  DBuf<unsigned> vt_bar;
+  DBuf<int> vt_flag;
   ~Handle();
 };
 
@@ -271,6 +279,10 @@ int solve(Handle *h, int k, const double *B, double *X, double rtol, int *iters,
 int vcycle_apply(Handle *h, const double *y, double *z);
 int bench_spmv(Handle *h, int lev, int which, int a64, int reps, double *ms, double *bytes);
 int vcycle_apply_noalloc(Handle *h, const double *y, double *z);
+// ---- fused coarse end of the V-cycle (vtail.cu) ----
+int vtail_prepare(Handle *h);
+int vtail_run(Handle *h, const int *done, cudaStream_t s);
+int vtail_error();  // AMG_ERR_CUDA (and clears it) if a grid barrier wait ran out
 int bench_fsai(Handle *h, int lev, int reps, double *ms);
 // ---- batched solve (batch.cu) ----
 int solve_batched(Handle *h, int k, const double *B, double *X, double rtol, int *iters, double *relres);

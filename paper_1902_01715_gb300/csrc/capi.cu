@@ -152,6 +152,7 @@ extern "C" int amg_adjoint(amg_handle hh, int k, const double *G, double *Lambda
 extern "C" int amg_get_stats(amg_handle hh, amg_stats *s) {
   Handle *h = (Handle *)hh;
   if (!h || !s) return AMG_ERR_ARG;
+  h->stats.vcycle_fused_level = h->vt_level;
   *s = h->stats;
   return AMG_OK;
 }

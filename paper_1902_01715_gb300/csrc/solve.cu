@@ -62,6 +62,7 @@ int prepare_solve(Handle *h) {
   h->x.release();
   free_batch(h);
   AMG_CU(cudaStreamSynchronize(s));
+  AMG_TRY(vtail_prepare(h));
   return AMG_OK;
 }
 
@@ -123,6 +124,10 @@ void mv<double>(int ep, const SolveMat &M, bool, const double *x, double *y, con
 template <typename TX>
 static void vcycle_level(Handle *h, int k, const TX *y, TX *z, const int *done) {
   cudaStream_t st = h->stream;
+  if (k > 0 && k == h->vt_level) {  // levels k.. in one persistent kernel (vtail.cu)
+    vtail_run(h, done, st);
+    return;
+  }
   Level &L = *h->lev[k];
   const bool b16 = h->prm.vcycle_prec == AMG_FP32_BF16GP;
   if (k == h->nlev - 1) {
@@ -517,6 +522,7 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
   *rec_relres = hsc[P_BN2] > 0.0 ? std::sqrt(hsc[P_RR] / hsc[P_BN2]) : 0.0;
   *nrestart = restarts;
   if (mixed) AMG_TRY(bulk_copy_error());
+  if (h->vt_level >= 0) AMG_TRY(vtail_error());
   return hflags[F_STATUS];
 }
 
@@ -572,8 +578,9 @@ int vcycle_apply(Handle *h, const double *y, double *z) {
   }
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
-  // a bulk-copy stage that timed out left rows of z unwritten
+  // a bulk-copy stage or a fused-kernel barrier that timed out left rows of z unwritten
   if (h->prm.vcycle_prec != AMG_FP64) AMG_TRY(bulk_copy_error());
+  if (h->vt_level >= 0) AMG_TRY(vtail_error());
   return AMG_OK;
 }
 
@@ -634,9 +641,11 @@ int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
   }
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
-  // a bulk-copy stage that timed out left rows of z unwritten (the error word
-  // is read and cleared with plain symbol copies: no allocation)
+  // a bulk-copy stage or a fused-kernel barrier that timed out left rows of z
+  // unwritten (the error words are read and cleared with plain symbol copies:
+  // no allocation)
   if (h->prm.vcycle_prec != AMG_FP64) AMG_TRY(bulk_copy_error());
+  if (h->vt_level >= 0) AMG_TRY(vtail_error());
   return AMG_OK;
 }
 
@@ -725,6 +734,9 @@ Handle::~Handle() {
   // buffers are returned on the stream they were taken on: before it goes
   for (DBuf<double> *b : {&Cinv, &x, &r, &z, &p, &q, &zold, &bvec, &scal, &red, &V0keep}) b->release();
   flags.release();
+  vt_prog.release();
+  vt_bar.release();
+  vt_flag.release();
   if (aux) cudaStreamDestroy(aux);
   if (ev_main) cudaEventDestroy(ev_main);
   if (ev_aux) cudaEventDestroy(ev_aux);

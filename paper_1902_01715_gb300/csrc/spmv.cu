@@ -662,6 +662,12 @@ int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
   return tune_one<__nv_bfloat16, float>(M, M.v16.p, s, 2);
 }
 
+int mapping_wps(const SolveMat &M, bool f64) {
+  const int m = f64 ? M.map64 : M.map;
+  if (m < 0 || m >= kNumMaps) return 1;
+  return kMaps[m].wps == 0 ? 1 : kMaps[m].wps;  // the bulk-copy variant sums like one warp per slice
+}
+
 const char *mapping_name(const SolveMat &M, bool f64) {
   static const char *names[kNumMaps] = {"wps1_u2", "wps1_u4", "wps2_u2", "wps2_u4", "wps4_u2",
                                         "wps4_u4", "wps8_u2", "wps16_u2", "bulk_copy"};
