@@ -78,10 +78,13 @@ __device__ __forceinline__ void vt_spmv(const VtOp &o, T (*red)[2 * B][32]) {
   constexpr int SPB = VT_WARPS / WPS, BB = B * B;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int part = warp % WPS;
+  // Vectors are written by earlier products of this kernel on other SMs:
+  // they are read through L2 (__ldcg), never through the non-coherent L1 or
+  // read-only paths; the matrices do not change while the kernel runs.
   const T *__restrict__ v = (const T *)o.v;
-  const T *__restrict__ x = (const T *)o.x;
-  const T *__restrict__ aux = (const T *)o.aux;
-  T *__restrict__ y = (T *)o.y;
+  const T *x = (const T *)o.x;
+  const T *aux = (const T *)o.aux;
+  T *y = (T *)o.y;
   const T w = (T)o.w;
   const int rounds = (o.ns + gridDim.x * SPB - 1) / (gridDim.x * SPB);
   for (int rd = 0; rd < rounds; ++rd) {
@@ -112,11 +115,11 @@ __device__ __forceinline__ void vt_spmv(const VtOp &o, T (*red)[2 * B][32]) {
         if (j < len) {
           const T *xp = x + (long)B * c[u];
           if constexpr (B == 3) {
-            const T x0 = xp[0], x1 = xp[1], x2 = xp[2];
+            const T x0 = __ldcg(xp), x1 = __ldcg(xp + 1), x2 = __ldcg(xp + 2);
 #pragma unroll
             for (int r = 0; r < 3; ++r) acc.add(r, m[u][3 * r], m[u][3 * r + 1], m[u][3 * r + 2], x0, x1, x2);
           } else {
-            acc.add1(0, m[u][0], xp[0]);
+            acc.add1(0, m[u][0], __ldcg(xp));
           }
         }
       }
@@ -143,9 +146,9 @@ __device__ __forceinline__ void vt_spmv(const VtOp &o, T (*red)[2 * B][32]) {
         const T a = acc.get(r);
         if (o.ep == EP_SET) y[ob + r] = a;
         else if (o.ep == EP_SCALE) y[ob + r] = w * a;
-        else if (o.ep == EP_RESID) y[ob + r] = aux[ob + r] - a;
-        else if (o.ep == EP_SADD) y[ob + r] = aux[ob + r] + w * a;
-        else y[ob + r] += a;
+        else if (o.ep == EP_RESID) y[ob + r] = __ldcg(aux + ob + r) - a;
+        else if (o.ep == EP_SADD) y[ob + r] = __ldcg(aux + ob + r) + w * a;
+        else y[ob + r] = __ldcg(y + ob + r) + a;
       }
     }
   }
@@ -153,15 +156,15 @@ __device__ __forceinline__ void vt_spmv(const VtOp &o, T (*red)[2 * B][32]) {
 
 template <typename T>
 __device__ __forceinline__ void vt_coarse(const VtOp &o) {
-  const T *__restrict__ yv = (const T *)o.x;
-  T *__restrict__ z = (T *)o.y;
+  const T *yv = (const T *)o.x;  // written by the restriction before: read through L2
+  T *z = (T *)o.y;
   const int lane = threadIdx.x & 31;
   const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nw = ((long)gridDim.x * blockDim.x) >> 5;
   for (long row = gw; row < o.m; row += nw) {
     double s = 0.0;
     const double *Cr = o.Ci + (size_t)row * o.m;
-    for (int k = lane; k < o.m; k += 32) s = fma(Cr[k], (double)yv[k], s);
+    for (int k = lane; k < o.m; k += 32) s = fma(Cr[k], (double)__ldcg(yv + k), s);
     for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) z[row] = (T)s;
   }
