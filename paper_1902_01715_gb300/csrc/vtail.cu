@@ -59,7 +59,8 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int *fai
     } else {
       const long long t0 = clock64();
       while (((volatile unsigned *)bar)[1] == gen) {
-        if (clock64() - t0 > (1LL << 32)) {
+        // another block gave up: leave at once instead of waiting out the limit
+        if (*(volatile int *)&g_vtail_err || clock64() - t0 > (1LL << 32)) {
           atomicExch(&g_vtail_err, 1);
           *fail = 1;
           break;
