@@ -16,6 +16,14 @@
  * re-solved, and the row stops early when psi decreased by no more than eps
  * relative to its previous value.
  *
+ * Order of the row system (the method does not fix it): the pattern nodes in
+ * the order they were added -- the starting pattern (a row of G_s) in
+ * ascending order, then each step's nodes in the order they were picked --
+ * so every step only appends to the system (the factor of the earlier nodes
+ * stays valid, and the GPU factors only the new rows); the gradient and psi
+ * sums run over the pattern in the same order; G is written with its pattern
+ * in ascending order.
+ *
  * Block form (b = 3).  The pattern is kept per node: node row I holds a set of
  * nodes J < I, and each dof row c of node I uses all dofs of those nodes plus
  * the dofs of I below c (so the diagonal block is lower triangular).  A
@@ -148,8 +156,7 @@ static int afsai_row(const obsr *A, const obsr *Gs, int I, int ksteps, int rho, 
       score[best] = -1.0;
     }
     if (got == 0) break;
-    np += got;
-    qsort(pat, np, sizeof(int), cmp_int);
+    np += got; /* the new nodes stay after the old ones (insertion order) */
     for (int c = 0; c < b; ++c) psi_old[c] = psi[c];
     rc = solve_rows(A, I, pat, np, gh, psi, w->M, w->L, w->rhs, w->Q);
     if (rc) break;
@@ -159,15 +166,28 @@ static int afsai_row(const obsr *A, const obsr *Gs, int I, int ksteps, int rho, 
     if (stalled) break;
   }
   if (rc) return rc;
-  /* row I: pattern blocks then the diagonal block */
+  /* row I: pattern blocks in ascending node order, then the diagonal block;
+   * ord[j] = position in the row system of the j-th smallest pattern node */
+  int *ord = w->cand; /* the candidate list is free once the row is done */
+  for (int j = 0; j < np; ++j) ord[j] = j;
+  for (int u = 1; u < np; ++u) {
+    const int v = ord[u];
+    int w = u - 1;
+    while (w >= 0 && pat[ord[w]] > pat[v]) {
+      ord[w + 1] = ord[w];
+      --w;
+    }
+    ord[w + 1] = v;
+  }
   for (int j = 0; j <= np; ++j) {
     double *blk = val_out + (size_t)j * b * b;
-    if (j < np) pat_out[j] = pat[j];
+    const int q = j < np ? ord[j] : np;
+    if (j < np) pat_out[j] = pat[q];
     for (int c = 0; c < b; ++c) {
       const double rs = 1.0 / sqrt(psi[c]); /* g / sqrt(psi) as g times 1 / sqrt(psi) */
       for (int d = 0; d < b; ++d) {
         double g;
-        if (j < np) g = gh[c][b * j + d];
+        if (j < np) g = gh[c][b * q + d];
         else g = (d < c) ? gh[c][b * np + d] : (d == c ? 1.0 : 0.0);
         blk[c * b + d] = (j < np || d <= c) ? g * rs : 0.0;
       }

@@ -532,11 +532,17 @@ __device__ __forceinline__ void tri_decode(int idx, int &rr, int &kk) {
 // rho_j = 1 / L_jj, which the diagonal then holds for the substitutions (a
 // product per unknown instead of a division).
 template <int B>
-__device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, int np, double *M, double *gh,
+__device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, int np, int r0, double *M, double *gh,
                                double *rhs, double *ent, double *psi, int g, int gl) {
+  // Rows [0, r0) of the factor in M (stride mmax) are kept from the previous
+  // solve of this row: the pattern only grew at its end, and entry (r, k) of
+  // a Cholesky factor depends only on the leading (r+1) x (r+1) block.  Only
+  // rows r0.. (the new pattern dofs and the row's own dofs, which follow
+  // them) are formed and factored.
   const int m2 = act ? B * np + (B - 1) : 0, mm = K.mmax, nn = np + 1;
+  const int p0 = r0 / B;  // first node whose rows are new
   const int npairs = act ? nn * (nn + 1) / 2 : 0;
-  for (int idx = gl; idx < npairs; idx += FS_GL) {
+  for (int idx = p0 * (p0 + 1) / 2 + gl; idx < npairs; idx += FS_GL) {
     int p, q;
     tri_decode(idx, p, q);
     const double *b = find_blk<B>(K.Arp, K.Acol, K.Aval, p < np ? pat[p] : I, q < np ? pat[q] : I);
@@ -545,7 +551,7 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       if (r >= m2) break;
       for (int e = 0; e < B; ++e) {
         const int cc = B * q + e;
-        if (cc <= r) M[r * m2 + cc] = b ? b[a * B + e] : 0.0;
+        if (cc <= r) M[r * mm + cc] = b ? b[a * B + e] : 0.0;
       }
     }
   }
@@ -565,9 +571,11 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
   __syncwarp();
   // right-looking Cholesky of the lower triangle in panels of FS_PB columns
   // (each entry receives its updates k = 0, 1, ... in ascending order, then
-  // the division, exactly as column by column): inside a panel column by
-  // column; the trailing entries then receive the panel's FS_PB updates in
-  // one pass, reading each of their two panel rows once
+  // the scaling by its column's reciprocal pivot, exactly as column by
+  // column): inside a panel column by column; the trailing entries then
+  // receive the panel's FS_PB updates in one pass, reading each of their two
+  // panel rows once.  Columns below r0 already hold their reciprocal pivots:
+  // only the new rows take their scalings and updates.
   constexpr int FS_PB = 8;
   const int mx = warp_max(m2);
   int bad = 0;
@@ -575,36 +583,40 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
     const int j1 = min(j0 + FS_PB, m2);  // this slot's panel end
     for (int j = j0; j < j0 + FS_PB && j < mx; ++j) {
       const bool on = j < m2 && !bad;
+      const bool kept = j < r0;  // pivot of a kept row
       double rho = 1.0;
       if (on) {
-        const double sjj = M[j * m2 + j];
-        if (!(sjj > 0.0)) bad = 1;
+        const double sjj = M[j * mm + j];
+        if (kept) rho = sjj;
+        else if (!(sjj > 0.0)) bad = 1;
         else rho = 1.0 / sqrt(sjj);
       }
       __syncwarp();
+      const int rb = max(j + 1, r0);  // first row this column updates
       if (on && !bad) {
-        for (int r = j + 1 + gl; r < m2; r += FS_GL) M[r * m2 + j] = M[r * m2 + j] * rho;
-        if (gl == 0) M[j * m2 + j] = rho;  // the diagonal holds 1 / L_jj
+        for (int r = rb + gl; r < m2; r += FS_GL) M[r * mm + j] = M[r * mm + j] * rho;
+        if (gl == 0 && !kept) M[j * mm + j] = rho;  // the diagonal holds 1 / L_jj
       }
       __syncwarp();
-      if (on && !bad) {  // the panel's later columns, rows k..m2-1
+      if (on && !bad) {  // the panel's later columns, rows max(k, r0)..m2-1
         const int pk = j1 - j - 1;
-        for (int idx = gl; idx < pk * (m2 - j - 1); idx += FS_GL) {
-          const int k = j + 1 + idx % pk, r = j + 1 + idx / pk;
-          if (r >= k) M[r * m2 + k] = fma(-M[r * m2 + j], M[k * m2 + j], M[r * m2 + k]);
+        for (int idx = gl; idx < pk * (m2 - rb); idx += FS_GL) {
+          const int k = j + 1 + idx % pk, r = rb + idx / pk;
+          if (r >= k) M[r * mm + k] = fma(-M[r * mm + j], M[k * mm + j], M[r * mm + k]);
         }
       }
       __syncwarp();
     }
-    if (!bad && j1 < m2 && j0 < m2) {  // trailing lower triangle from column j1
+    if (!bad && j1 < m2 && j0 < m2) {  // trailing rows max(j1, r0).. from column j1
       const int w = m2 - j1, nt = w * (w + 1) / 2;
-      for (int idx = gl; idx < nt; idx += FS_GL) {
+      const int rb = max(r0, j1) - j1, t0 = rb * (rb + 1) / 2;
+      for (int idx = t0 + gl; idx < nt; idx += FS_GL) {
         int rr, kk;
         tri_decode(idx, rr, kk);
         const int r = j1 + rr, k = j1 + kk;
-        double a = M[r * m2 + k];
-        for (int j = j0; j < j1; ++j) a = fma(-M[r * m2 + j], M[k * m2 + j], a);
-        M[r * m2 + k] = a;
+        double a = M[r * mm + k];
+        for (int j = j0; j < j1; ++j) a = fma(-M[r * mm + j], M[k * mm + j], a);
+        M[r * mm + k] = a;
       }
     }
     __syncwarp();
@@ -618,12 +630,12 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
   for (int k0 = 0; k0 < mx; k0 += FS_PB) {
     const int k1 = min(k0 + FS_PB, mx);
     for (int k = k0; k < k1; ++k) {
-      if (ok && gl < B && k < B * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] * M[k * m2 + k];
+      if (ok && gl < B && k < B * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] * M[k * mm + k];
       __syncwarp();
       if (ok)
         for (int idx = gl; idx < B * (k1 - k - 1); idx += FS_GL) {
           const int c = idx / (k1 - k - 1), r = k + 1 + idx % (k1 - k - 1);
-          if (r < B * np + c) rhs[c * mm + r] = fma(-M[r * m2 + k], rhs[c * mm + k], rhs[c * mm + r]);
+          if (r < B * np + c) rhs[c * mm + r] = fma(-M[r * mm + k], rhs[c * mm + k], rhs[c * mm + r]);
         }
       __syncwarp();
     }
@@ -632,7 +644,7 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
         const int c = idx / (m2 - k1), r = k1 + idx % (m2 - k1);
         if (r < B * np + c) {
           double a = rhs[c * mm + r];
-          for (int k = k0; k < k1; ++k) a = fma(-M[r * m2 + k], rhs[c * mm + k], a);
+          for (int k = k0; k < k1; ++k) a = fma(-M[r * mm + k], rhs[c * mm + k], a);
           rhs[c * mm + r] = a;
         }
       }
@@ -644,12 +656,12 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
   for (int k1 = mx; k1 > 0; k1 -= FS_PB) {
     const int k0 = max(k1 - FS_PB, 0);
     for (int k = k1 - 1; k >= k0; --k) {
-      if (ok && gl < B && k < B * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] * M[k * m2 + k];
+      if (ok && gl < B && k < B * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] * M[k * mm + k];
       __syncwarp();
       if (ok && k < m2)
         for (int idx = gl; idx < B * (k - k0); idx += FS_GL) {
           const int c = idx / (k - k0), r = k0 + idx % (k - k0);
-          if (k < B * np + c) rhs[c * mm + r] = fma(-M[k * m2 + r], gh[c * mm + k], rhs[c * mm + r]);
+          if (k < B * np + c) rhs[c * mm + r] = fma(-M[k * mm + r], gh[c * mm + k], rhs[c * mm + r]);
         }
       __syncwarp();
     }
@@ -657,7 +669,7 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       for (int idx = gl; idx < B * k0; idx += FS_GL) {
         const int c = idx / k0, r = idx % k0;
         double a = rhs[c * mm + r];
-        for (int k = min(k1, B * np + c) - 1; k >= k0; --k) a = fma(-M[k * m2 + r], gh[c * mm + k], a);
+        for (int k = min(k1, B * np + c) - 1; k >= k0; --k) a = fma(-M[k * mm + r], gh[c * mm + k], a);
         rhs[c * mm + r] = a;
       }
     __syncwarp();
@@ -723,9 +735,10 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
   double *rhs = gh + B * mm;
   double *ent = rhs + B * mm;
   double *score = ent + B * mm;
-  int *pat = K.iscr + slot * K.iper;
+  int *pat = K.iscr + slot * K.iper;  // pattern in the order the nodes were added
   int *cand = pat + K.maxg + 1;
   int *ccount = cand + K.candcap;
+  int *spat = ccount + 1;  // the same nodes in ascending order (membership tests)
   unsigned long long *tab = K.htab + slot * K.hcap;
   const long nrounds = (K.n + nslots - 1) / nslots;
   for (long rd = 0; rd < nrounds; ++rd) {
@@ -735,12 +748,16 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
     int np = 0;
     if (have && gl == 0 && K.Gsrp) {
       for (int k = K.Gsrp[I]; k < K.Gsrp[I + 1]; ++k)
-        if (K.Gscol[k] != I && np < K.maxg) pat[np++] = K.Gscol[k];
+        if (K.Gscol[k] != I && np < K.maxg) {
+          pat[np] = K.Gscol[k];  // a row of G_s: ascending
+          spat[np] = K.Gscol[k];
+          ++np;
+        }
     }
     np = __shfl_sync(0xffffffffu, np, g * FS_GL);
     __syncwarp();
     double psi[3] = {0.0, 0.0, 0.0}, psi_old[3];
-    int rc = fsai_solve_rows<B>(K, have, I, pat, np, M, gh, rhs, ent, psi, g, gl);
+    int rc = fsai_solve_rows<B>(K, have, I, pat, np, 0, M, gh, rhs, ent, psi, g, gl);
     bool active = have && rc == 0;
     for (int step = 0; step < K.ksteps; ++step) {
       if (active && np >= K.maxg) active = false;
@@ -756,7 +773,7 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
           const int b0 = K.Arp[Kn], len = K.Arp[Kn + 1] - b0;
           for (int e = gl; e < len; e += FS_GL) {
             const int J = K.Acol[b0 + e];
-            if (J < I && !in_sorted(pat, np, J) && set_insert(tab, K.hcap, stamp, J))
+            if (J < I && !in_sorted(spat, np, J) && set_insert(tab, K.hcap, stamp, J))
               cand[atomicAdd(ccount, 1)] = J;
           }
         }
@@ -828,19 +845,19 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
         __syncwarp();
       }
       if (active && got == 0) active = false;
-      if (active && gl == 0) {
-        const int tot = np + got;
-        for (int u = 1; u < tot; ++u) {
+      if (active && gl == 0) {  // the new nodes stay at the end of pat; spat takes them in order
+        for (int u = np; u < np + got; ++u) {
           const int v = pat[u];
           int w = u - 1;
-          while (w >= 0 && pat[w] > v) { pat[w + 1] = pat[w]; --w; }
-          pat[w + 1] = v;
+          while (w >= 0 && spat[w] > v) { spat[w + 1] = spat[w]; --w; }
+          spat[w + 1] = v;
         }
       }
+      const int np_old = np;
       if (active) np += got;
       __syncwarp();
       for (int c = 0; c < B; ++c) psi_old[c] = psi[c];
-      const int rc2 = fsai_solve_rows<B>(K, active, I, pat, np, M, gh, rhs, ent, psi, g, gl);
+      const int rc2 = fsai_solve_rows<B>(K, active, I, pat, np, B * np_old, M, gh, rhs, ent, psi, g, gl);
       if (active) {
         if (rc2) {
           rc = rc2;
@@ -858,15 +875,23 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
       if (gl == 0) atomicMin(K.status, rc);
       continue;
     }
+    // G row in ascending node order: ord[j] = position in pat of spat[j]
+    int *ord = cand;  // free once the steps are done
+    for (int j = gl; j < np; j += FS_GL) {
+      const int v = spat[j];
+      for (int q = 0; q < np; ++q)
+        if (pat[q] == v) ord[j] = q;
+    }
+    __syncwarp(0xffu << (g * FS_GL));  // only this slot's lanes are here
     if (gl == 0) K.out_np[I] = np;
-    for (int j = gl; j < np; j += FS_GL) K.out_pat[(size_t)I * K.maxg + j] = pat[j];
+    for (int j = gl; j < np; j += FS_GL) K.out_pat[(size_t)I * K.maxg + j] = spat[j];
     double rs[B];  // 1 / sqrt(psi_c): one division per row, products per entry
     for (int c = 0; c < B; ++c) rs[c] = 1.0 / sqrt(psi[c]);
     double *ov = K.out_val + (size_t)I * (K.maxg + 1) * B * B;
     for (int idx = gl; idx < (np + 1) * B * B; idx += FS_GL) {
       const int j = idx / (B * B), c = (idx % (B * B)) / B, d = idx % B;
       double gv;
-      if (j < np) gv = gh[c * mm + B * j + d];
+      if (j < np) gv = gh[c * mm + B * ord[j] + d];
       else gv = (d < c) ? gh[c * mm + B * np + d] : (d == c ? 1.0 : 0.0);
       ov[idx] = (j < np || d <= c) ? gv * rs[c] : 0.0;
     }
@@ -909,7 +934,7 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   K.hcap = 64;
   while (K.hcap < 2 * K.candcap) K.hcap *= 2;
   K.dper = (long)K.mmax * K.mmax + 3L * A.b * K.mmax + K.candcap;
-  K.iper = (maxg + 1) + K.candcap + 1;
+  K.iper = (maxg + 1) + K.candcap + 1 + (maxg + 1);
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
