@@ -1,6 +1,7 @@
-"""The coarse end of the V-cycle as one persistent kernel (vtail.cu) against
-the same V-cycle with one launch per product: the same bits, in FP64 and FP32
-and for both block sizes, for the V-cycle alone and for whole solves."""
+"""The coarse end of the V-cycle as one persistent kernel (vtail.cu, opt-in
+through AMG_VTAIL_LEVEL) against the same V-cycle with one launch per
+product: the same bits, in FP64 and FP32 and for both block sizes, for the
+V-cycle alone and for whole solves."""
 import os
 
 import numpy as np
@@ -24,10 +25,9 @@ def A():
 
 def _solver(A, d, block, prec, fused):
     if fused:
-        os.environ.pop("AMG_NO_VTAIL", None)
         os.environ["AMG_VTAIL_LEVEL"] = "1"
     else:
-        os.environ["AMG_NO_VTAIL"] = "1"
+        os.environ.pop("AMG_VTAIL_LEVEL", None)
     try:
         if block == 1:
             rp, col, val = A.bsr_to_scalar(d["rowptr"], d["col"], d["vals"])
@@ -35,7 +35,6 @@ def _solver(A, d, block, prec, fused):
             rp, col, val = d["rowptr"], d["col"], d["vals"]
         return A.Solver(rp, col, val, d["V0"], block=block, vcycle_prec=prec)
     finally:
-        os.environ.pop("AMG_NO_VTAIL", None)
         os.environ.pop("AMG_VTAIL_LEVEL", None)
 
 
