@@ -142,6 +142,12 @@ struct SolveMat {
   DBuf<__nv_bfloat16> v16;
   int map = 0;    // warp mapping, FP32/bf16 storage (set by the autotuner)
   int map64 = 0;  // warp mapping, FP64 storage
+  // one-warp-CTA mappings: partial row sums of the warps of a slice (ns x
+  // WPS x 2B x 32 values of the vector type) and one arrival counter per
+  // slice (zero between launches)
+  int wps_rule = 1;
+  DBuf<double> wpart;
+  DBuf<unsigned> wtick;
   // batched product (k columns): mapping per storage (FP64, FP32, bf16) and
   // the k it was tuned for
   int bmap[3] = {1, 1, 1};
@@ -167,6 +173,7 @@ template <> struct RowAcc<double> {
   // scalar (1x1) block
   __device__ __forceinline__ void add1(int r, double m0, double x0) { s[r] = fma(m0, x0, s[r]); }
   __device__ __forceinline__ void merge(int r, double hi, double) { s[r] += hi; }
+  __device__ __forceinline__ void set(int r, double hi, double) { s[r] = hi; }
   __device__ __forceinline__ double hi(int r) const { return s[r]; }
   __device__ __forceinline__ double lo(int) const { return 0.0; }
   __device__ __forceinline__ double get(int r) const { return s[r]; }
@@ -188,6 +195,10 @@ template <> struct RowAcc<float> {
   __device__ __forceinline__ void merge(int r, float hi, float lo) {
     two_sum(r, hi);
     c[r] = __fadd_rn(c[r], lo);
+  }
+  __device__ __forceinline__ void set(int r, float hi, float lo) {
+    s[r] = hi;
+    c[r] = lo;
   }
   __device__ __forceinline__ float hi(int r) const { return s[r]; }
   __device__ __forceinline__ float lo(int r) const { return c[r]; }

@@ -78,7 +78,20 @@ __global__ void k_coarse_mv(int m, const double *__restrict__ Ci, const TX *__re
   if (row >= m) return;
   double s = 0.0;
   const double *Cr = Ci + (size_t)row * m;
-  for (int k = lane; k < m; k += 32) s = fma(Cr[k], (double)y[k], s);
+  // the loads of 16 terms are issued before their FMAs (same order of terms)
+  constexpr int CU = 16;
+  for (int k0 = lane; k0 < m; k0 += 32 * CU) {
+    double a[CU], b[CU];
+#pragma unroll
+    for (int u = 0; u < CU; ++u) {
+      const int k = k0 + 32 * u;
+      a[u] = k < m ? Cr[k] : 0.0;
+      b[u] = k < m ? (double)y[k] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < CU; ++u)
+      if (k0 + 32 * u < m) s = fma(a[u], b[u], s);
+  }
   for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (lane == 0) z[row] = (TX)s;
 }

@@ -46,10 +46,14 @@ __device__ __forceinline__ float cvs(__nv_bfloat16 v, float) { return __bfloat16
 
 struct Mapping {
   int wps, u;
+  bool w1;  // one warp per CTA (k_sellmv_w)
 };
-// the last entry is the bulk-copy variant below (FP32 and bf16 storage)
+// entry 8 is the bulk-copy variant below (FP32 and bf16 storage); 9.. put
+// every warp in a CTA of its own
 constexpr int SELL_SIGMA = 1024;  // rows per sorting window (a multiple of 32)
-static const Mapping kMaps[] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}, {4, 4}, {8, 2}, {16, 2}, {0, 0}};
+static const Mapping kMaps[] = {{1, 2, false}, {1, 4, false}, {2, 2, false}, {2, 4, false}, {4, 2, false},
+                                {4, 4, false}, {8, 2, false}, {16, 2, false}, {0, 0, false}, {1, 2, true},
+                                {2, 2, true},  {4, 2, true},  {8, 2, true},  {16, 2, true}};
 constexpr int kNumMaps = (int)(sizeof(kMaps) / sizeof(kMaps[0]));
 
 // CTA size: 4 warps, or one slice of WPS warps when WPS > 4
@@ -138,6 +142,102 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int s0, int r0
   }
 }
 
+// The same product with one warp per CTA, for matrices whose slices are too
+// few to give every SM a CTA of the kernel above: the CTAs then spread over
+// all SMs (a small level's FP64 product is bounded by the FP64 pipes of the
+// SMs it reaches).  The WPS warps of a slice are CTAs of their own; each
+// stores its partial row sums, and the last to arrive (an arrival counter
+// per slice) rebuilds the partial of warp 0 and adds those of warps 1,
+// 2, ... in order -- the additions, in the order, of the shared-memory merge
+// above, so both kernels give the same bits -- then writes the rows and
+// clears the counter for the next launch.
+template <typename TM, typename TX, int B, int EP, int WPS, int U>
+__global__ void __launch_bounds__(32) k_sellmv_w(int s0, int r0, int r1, int nr, const int *__restrict__ prow,
+                                                 const int *__restrict__ rp, const int *__restrict__ slp,
+                                                 const int *__restrict__ scol, const TM *__restrict__ v,
+                                                 const TX *__restrict__ x, TX *__restrict__ y,
+                                                 const TX *__restrict__ aux, TX w, const int *__restrict__ done,
+                                                 TX *__restrict__ wpart, unsigned *__restrict__ wtick) {
+  if (done && *done) return;
+  constexpr int BB = B * B;
+  const int lane = threadIdx.x;
+  const int sl = s0 + (int)(blockIdx.x / WPS);
+  const int part = (int)(blockIdx.x % WPS);
+  const int pos = sl * 32 + lane;
+  const int row = pos < nr ? (prow ? prow[pos] : pos) : -1;
+  const bool valid = row >= r0 && row < r1;
+  const int len = valid ? rp[row + 1] - rp[row] : 0;
+  const long base = valid ? (long)slp[sl] : 0L;
+  RowAcc<TX> acc;
+  for (int j0 = part; j0 < len; j0 += WPS * U) {
+    int c[U];
+    TM m[U][BB];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u * WPS;
+      if (j < len) {
+        const long slot = base + 32L * j;
+        c[u] = scol[slot + lane];
+        const TM *vp = v + BB * slot + lane;
+#pragma unroll
+        for (int e = 0; e < BB; ++e) m[u][e] = vp[32 * e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u * WPS;
+      if (j < len) {
+        const TX *xp = x + (long)B * c[u];
+        if constexpr (B == 3) {
+          const TX x0 = xp[0], x1 = xp[1], x2 = xp[2];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+            acc.add(r, cvs(m[u][3 * r], TX(0)), cvs(m[u][3 * r + 1], TX(0)), cvs(m[u][3 * r + 2], TX(0)), x0, x1,
+                    x2);
+        } else {
+          acc.add1(0, cvs(m[u][0], TX(0)), xp[0]);
+        }
+      }
+    }
+  }
+  if (WPS > 1) {
+    TX *mine = wpart + ((size_t)sl * WPS + part) * (2 * B * 32);
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      mine[r * 32 + lane] = acc.hi(r);
+      mine[(B + r) * 32 + lane] = acc.lo(r);
+    }
+    __threadfence();
+    __syncwarp();
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(&wtick[sl], 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t != (unsigned)(WPS - 1)) return;
+    __threadfence();
+    const TX *sp = wpart + (size_t)sl * WPS * (2 * B * 32);
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc.set(r, __ldcg(sp + r * 32 + lane), __ldcg(sp + (B + r) * 32 + lane));
+#pragma unroll
+    for (int p = 1; p < WPS; ++p) {
+      const TX *pp = sp + (size_t)p * (2 * B * 32);
+#pragma unroll
+      for (int r = 0; r < B; ++r) acc.merge(r, __ldcg(pp + r * 32 + lane), __ldcg(pp + (B + r) * 32 + lane));
+    }
+    if (lane == 0) wtick[sl] = 0u;
+  }
+  if (!valid) return;
+  const long o = (long)B * row;
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const TX a = acc.get(r);
+    if (EP == EP_SET) y[o + r] = a;
+    if (EP == EP_SCALE) y[o + r] = w * a;
+    if (EP == EP_RESID) y[o + r] = aux[o + r] - a;
+    if (EP == EP_SADD) y[o + r] = aux[o + r] + w * a;
+    if (EP == EP_ACC) y[o + r] += a;
+  }
+}
+
 // positions holding rows [r0, r1): the same range without a permutation, else
 // the SIGMA windows that contain them
 static void row_slices(const SolveMat &M, int r0, int r1, int &s0, int &s1) {
@@ -167,6 +267,28 @@ static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *
     case EP_RESID: AMG_KCOUNT k_sellmv<TM, TX, B, EP_RESID, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
     case EP_SADD: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SADD, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
     default: AMG_KCOUNT k_sellmv<TM, TX, B, EP_ACC, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+  }
+#undef AMG_SELL_ARGS
+}
+
+template <typename TM, typename TX, int B, int WPS>
+static void launch_w(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
+                     const int *done, cudaStream_t s, int r0 = 0, int r1 = -1) {
+  if (r1 < 0) r1 = M.nr;
+  if (r1 <= r0) return;
+  int s0, s1;
+  row_slices(M, r0, r1, s0, s1);
+  const long nb = (long)(s1 - s0) * WPS;
+  if (nb == 0) return;
+  TX *wp = reinterpret_cast<TX *>(M.wpart.p);
+  unsigned *wt = M.wtick.p;
+#define AMG_SELL_ARGS s0, r0, r1, M.nr, M.prow.p, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done, wp, wt
+  switch (ep) {
+    case EP_SET: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SET, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SCALE: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SCALE, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_RESID: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_RESID, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SADD: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SADD, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    default: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_ACC, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
   }
 #undef AMG_SELL_ARGS
 }
@@ -389,6 +511,11 @@ static void bsrmv_b(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, 
     case 5: launch_map<TM, TX, B, 4, 4>(ep, M, v, x, y, aux, w, done, s); break;
     case 6: launch_map<TM, TX, B, 8, 2>(ep, M, v, x, y, aux, w, done, s); break;
     case 7: launch_map<TM, TX, B, 16, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 9: launch_w<TM, TX, B, 1>(ep, M, v, x, y, aux, w, done, s); break;
+    case 10: launch_w<TM, TX, B, 2>(ep, M, v, x, y, aux, w, done, s); break;
+    case 11: launch_w<TM, TX, B, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 12: launch_w<TM, TX, B, 8>(ep, M, v, x, y, aux, w, done, s); break;
+    case 13: launch_w<TM, TX, B, 16>(ep, M, v, x, y, aux, w, done, s); break;
     default:
       // the bulk-copy variant is written for 3x3 blocks in FP32/bf16
       if constexpr (std::is_same<TM, double>::value || B != 3) launch_map<TM, TX, B, 1, 2>(ep, M, v, x, y, aux, w, done, s);
@@ -418,6 +545,11 @@ static void bsrmv_rows_b(int ep, const SolveMat &M, const double *x, double *y, 
     case 5: launch_map<double, double, B, 4, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
     case 6: launch_map<double, double, B, 8, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
     case 7: launch_map<double, double, B, 16, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 9: launch_w<double, double, B, 1>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 10: launch_w<double, double, B, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 11: launch_w<double, double, B, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 12: launch_w<double, double, B, 8>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 13: launch_w<double, double, B, 16>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
     default: launch_map<double, double, B, 1, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
   }
 }
@@ -477,20 +609,29 @@ static void to_sell(const DevBsr &A, const SolveMat &M, int *cols, T *dst, cudaS
     AMG_KCOUNT k_to_sell<T, 3><<<nb, 128, 0, s>>>(A.nr, M.prow.p, A.rowptr.p, A.col.p, A.val.p, M.slp.p, cols, dst);
 }
 
-// Mapping rule for matrices too small to time: few slices of long rows
-// leave SMs idle unless several warps share a slice, so the warps per slice
-// double while the launch has fewer than 16 warps per SM and each warp keeps
-// at least two blocks of an average row per chunk.
-static int rule_map(const SolveMat &M) {
+// Warps per slice: few slices of long rows leave SMs idle unless several
+// warps share a slice, so the warps per slice double while the launch has
+// fewer than 16 warps per SM and each warp keeps at least two blocks of an
+// average row per chunk.  This fixes the order of every row sum.
+static int rule_wps(const SolveMat &M) {
   const double avg = M.nr ? (double)M.nnzb / M.nr : 1.0;
   int wps = 1;
   while (wps < 16 && (long)M.ns * wps < 16L * 152 && avg / (2.0 * wps * 2) >= 1.0) wps *= 2;
+  return wps;
+}
+
+// Mapping for matrices too small to time: CTAs of 4 warps (or of one slice),
+// unless that gives fewer than two CTAs per SM; then one warp per CTA.
+static int rule_map(const SolveMat &M) {
+  const int wps = rule_wps(M);
+  const long ctas = wps <= 4 ? ((long)M.ns * wps + 3) / 4 : (long)M.ns;
+  const bool w1 = ctas < 2L * 152;
   switch (wps) {
-    case 1: return 0;   // WPS 1, U 2
-    case 2: return 2;   // WPS 2, U 2
-    case 4: return 4;   // WPS 4, U 2
-    case 8: return 6;   // WPS 8, U 2
-    default: return 7;  // WPS 16, U 2
+    case 1: return w1 ? 9 : 0;    // WPS 1, U 2
+    case 2: return w1 ? 10 : 2;   // WPS 2, U 2
+    case 4: return w1 ? 11 : 4;   // WPS 4, U 2
+    case 8: return w1 ? 12 : 6;   // WPS 8, U 2
+    default: return w1 ? 13 : 7;  // WPS 16, U 2
   }
 }
 
@@ -559,6 +700,15 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
   AMG_CU(cudaMemcpyAsync(M.slp.p, hs.data(), (M.ns + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   AMG_TRY(M.scol.alloc(tot));
   M.map = M.map64 = rule_map(M);
+  M.wps_rule = rule_wps(M);
+  if (M.wps_rule > 1) {  // partial sums of the one-warp-CTA mappings
+    AMG_TRY(M.wpart.alloc((size_t)M.ns * M.wps_rule * 2 * A.b * 32));
+    AMG_TRY(M.wtick.alloc(M.ns));
+    AMG_TRY(M.wtick.zero(s));
+  } else {
+    M.wpart.release();
+    M.wtick.release();
+  }
   const long n9 = (long)A.b * A.b * tot;
   int *cols = M.scol.p;
   if (f64) {
@@ -648,10 +798,11 @@ static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
 }
 
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
-  // AMG_MAP=<0..8> pins the mapping of every matrix (for experiments)
+  // AMG_MAP=<0..13> pins the mapping of every matrix (for experiments);
+  // one-warp-CTA mappings only with the matrix's own warps per slice
   if (const char *pin = getenv("AMG_MAP")) {
     const int m = atoi(pin);
-    if (m >= 0 && m < kNumMaps) {
+    if (m >= 0 && m < kNumMaps && (!kMaps[m].w1 || kMaps[m].wps == M.wps_rule)) {
       (kind == 0 ? M.map64 : M.map) = m;
       return AMG_OK;
     }
@@ -669,8 +820,9 @@ int mapping_wps(const SolveMat &M, bool f64) {
 }
 
 const char *mapping_name(const SolveMat &M, bool f64) {
-  static const char *names[kNumMaps] = {"wps1_u2", "wps1_u4", "wps2_u2", "wps2_u4", "wps4_u2",
-                                        "wps4_u4", "wps8_u2", "wps16_u2", "bulk_copy"};
+  static const char *names[kNumMaps] = {"wps1_u2",  "wps1_u4",  "wps2_u2",  "wps2_u4",  "wps4_u2",
+                                        "wps4_u4",  "wps8_u2",  "wps16_u2", "bulk_copy", "w1_wps1",
+                                        "w1_wps2",  "w1_wps4",  "w1_wps8",  "w1_wps16"};
   const int m = f64 ? M.map64 : M.map;
   return (m >= 0 && m < kNumMaps) ? names[m] : "?";
 }
