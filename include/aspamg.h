@@ -101,7 +101,10 @@ typedef struct {
   double relres_rec, relres_true;
   int restarts;
   int vcycle_fused_level; /* levels from this one down run as one persistent
-                           * kernel (-1: every product is its own launch) */
+                           * kernel (-1: every product is its own launch, the
+                           * default; the environment variable
+                           * AMG_VTAIL_LEVEL=<k> asks for the fused form from
+                           * level k >= 1, FP64 and FP32 V-cycles only) */
 } amg_stats;
 
 /* Fill *p with the defaults.  Returns AMG_ERR_ARG for p == NULL. */
@@ -119,8 +122,11 @@ int amg_default_params(amg_params *p);
  *   V0: 3*nnodes x ntv0 column-major near-null space (e.g. the 6 rigid-body
  *       modes), ntv0 <= n_tv, in `mem` memory; copied.
  *   stream: cudaStream_t to run on (NULL: the legacy default stream).
- * Errors: AMG_ERR_ARG (bad sizes/params), AMG_ERR_NOT_SPD, AMG_ERR_COARSENING,
- * AMG_ERR_CUDA, AMG_ERR_MEM.  On error *out is NULL. */
+ * Errors: AMG_ERR_ARG (bad sizes/params, or a pattern whose row pointers do
+ * not start at 0, decrease or exceed rowptr[nnodes], or whose column indices
+ * leave [0, nnodes) or do not increase along a row -- checked on the GPU
+ * before anything else reads the pattern), AMG_ERR_NOT_SPD,
+ * AMG_ERR_COARSENING, AMG_ERR_CUDA, AMG_ERR_MEM.  On error *out is NULL. */
 int amg_setup(const amg_params *p, int nnodes, int nnzb, const int *rowptr,
               const int *colind, const double *vals, int ntv0,
               const double *V0, int mem, void *stream, amg_handle *out);

@@ -22,6 +22,7 @@ UNITS = {
     "det.cu": ["-fmad=false"],
     "fe.cu": ["-fmad=false"],
     "setup.cu": [],
+    "graph.cu": [],
     "solve.cu": [],
     "capi.cu": [],
     "batch.cu": [],

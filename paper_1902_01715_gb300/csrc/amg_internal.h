@@ -95,32 +95,27 @@ struct DBuf {
 };
 
 // Block CSR matrix with b x b blocks (b = 3: nodal blocks; b = 1: the
-// scalar matrix of the paper's per-dof method), values row-major per block
-// ("AoS"); the pattern is mirrored on the host for the integer graph work of
-// the set-up.
+// scalar matrix of the paper's per-dof method; b = 0: a pattern without
+// values), values row-major per block ("AoS"), all on the device.
 struct DevBsr {
   int nr = 0, nc = 0, nnzb = 0, b = 3;
   DBuf<int> rowptr, col;
   DBuf<double> val;
-  std::vector<int> h_rowptr, h_col;
+  mutable int maxlen = -1;  // longest row, once known
   int alloc(int nr_, int nc_, int nnzb_, int b_) {
     nr = nr_; nc = nc_; nnzb = nnzb_; b = b_;
+    maxlen = -1;
     AMG_TRY(rowptr.alloc(nr + 1));
     AMG_TRY(col.alloc(nnzb));
     AMG_TRY(val.alloc((size_t)nnzb * b * b));
     return AMG_OK;
   }
-  int upload_pattern(cudaStream_t s) {
-    AMG_CU(cudaMemcpyAsync(rowptr.p, h_rowptr.data(), (nr + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (nnzb) AMG_CU(cudaMemcpyAsync(col.p, h_col.data(), nnzb * sizeof(int), cudaMemcpyHostToDevice, s));
-    return AMG_OK;
-  }
-  int download_pattern(cudaStream_t s) {
-    h_rowptr.resize(nr + 1);
-    h_col.resize(nnzb);
-    AMG_CU(cudaMemcpyAsync(h_rowptr.data(), rowptr.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
-    if (nnzb) AMG_CU(cudaMemcpyAsync(h_col.data(), col.p, nnzb * sizeof(int), cudaMemcpyDeviceToHost, s));
-    AMG_CU(cudaStreamSynchronize(s));
+  // longest row (a device reduction the first time, then kept)
+  int row_max(cudaStream_t s, int *out) const;
+  // blocking copy of the pattern to host arrays (rowptr: nr + 1, col: nnzb)
+  int copy_pattern(int *h_rowptr, int *h_col) const {
+    if (h_rowptr) AMG_CU(cudaMemcpy(h_rowptr, rowptr.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    if (h_col && nnzb) AMG_CU(cudaMemcpy(h_col, col.p, (size_t)nnzb * sizeof(int), cudaMemcpyDeviceToHost));
     return AMG_OK;
   }
 };
@@ -227,7 +222,7 @@ struct Level {
   double omega = 0.0, lmax = 0.0;
   int npasses = 0;
   int nc = 0;
-  std::vector<int> cf;  // host, 1 = coarse
+  DBuf<int> cf;         // 1 = coarse, 0 = fine (levels that were coarsened)
   DBuf<double> V;       // test space, 3n x n_tv column-major
   // V-cycle work vectors (3n x kcap, node-major with the k columns interleaved)
   DBuf<double> y64, s64, r64, t64, z64;
@@ -329,7 +324,17 @@ int gather_rows(const int *src_idx, int nrows_out, int n_in, int t, const double
 int uniform_fill(double *v, int n, int col0, int ncols, uint64_t seed, cudaStream_t s);
 }  // namespace det
 
-// helpers (setup.cu)
+// ---- integer pattern work on the GPU (graph.cu) ----
+// out[i] = sum_{j<i} (in[j] + add), out[n] = total (launch only)
+int dev_scan(int n, const int *in, int add, int *out, cudaStream_t s);
+int read_int(const int *d, int *h, cudaStream_t s);  // blocking
+int dev_row_max(int n, const int *rp, int *out, cudaStream_t s);
 int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s);
+// Z = pattern of X Y (values of b x b blocks allocated, unset; b = 0: none)
+int symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z, int b, cudaStream_t s);
+// coarse nodes within d_p strong edges of each fine node, ascending:
+// cptr[0..nf] (device) and cand (allocated here)
+int dpls_candidates_gpu(const DevBsr &A, const unsigned char *strong, const int *cf, const int *fnodes, int nf,
+                        int d_p, int *cptr, DBuf<int> &cand, cudaStream_t s);
 
 }  // namespace amg

@@ -92,6 +92,20 @@ extern "C" int amg_setup(const amg_params *p, int nnodes, int nnzb, const int *r
   }
   h->n = nnodes;
   StreamScope scope(h->stream);
+  int last = 0;  // the pattern's entry count must be the nnzb given
+  if (mem == AMG_MEM_HOST) {
+    last = rowptr[nnodes];
+  } else if (cudaMemcpyAsync(&last, rowptr + nnodes, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+             cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    delete h;
+    set_error("amg_setup: reading rowptr[nnodes] failed");
+    return AMG_ERR_CUDA;
+  }
+  if (last != nnzb) {
+    delete h;
+    set_error("amg_setup: rowptr[nnodes] = %d differs from nnzb = %d", last, nnzb);
+    return AMG_ERR_ARG;
+  }
   int rc = build_hierarchy(h, rowptr, colind, vals, mem, ntv0, V0, mem);
   if (rc) {
     delete h;
@@ -201,8 +215,7 @@ extern "C" int amg_level_matrix(amg_handle hh, int lev, int which, int *rowptr, 
   const Level &L = *h->lev[lev];
   const DevBsr *M = which == 0 ? &L.A : which == 1 ? &L.G : which == 2 ? &L.GT : which == 3 ? &L.P : &L.R;
   if (M->nr == 0 && which != 0) return AMG_ERR_ARG;
-  if (rowptr) memcpy(rowptr, M->h_rowptr.data(), (M->nr + 1) * sizeof(int));
-  if (col && M->nnzb) memcpy(col, M->h_col.data(), M->nnzb * sizeof(int));
+  AMG_TRY(M->copy_pattern(rowptr, col));
   if (val && M->nnzb)
     AMG_CU(cudaMemcpy(val, M->val.p, (size_t)M->nnzb * M->b * M->b * sizeof(double), cudaMemcpyDeviceToHost));
   return AMG_OK;
@@ -212,8 +225,8 @@ extern "C" int amg_level_cf(amg_handle hh, int lev, int *cf) {
   Handle *h = (Handle *)hh;
   if (!h || lev < 0 || lev >= h->nlev || !cf) return AMG_ERR_ARG;
   const Level &L = *h->lev[lev];
-  if ((int)L.cf.size() != L.n) return AMG_ERR_ARG;
-  memcpy(cf, L.cf.data(), L.n * sizeof(int));
+  if (!L.cf.p || (int)L.cf.n < L.n) return AMG_ERR_ARG;
+  if (L.n) AMG_CU(cudaMemcpy(cf, L.cf.p, (size_t)L.n * sizeof(int), cudaMemcpyDeviceToHost));
   return AMG_OK;
 }
 

@@ -920,13 +920,10 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   // systems, candidate lists and hash sets are sized by it (the hash sets
   // are probed at random positions, so smaller ones stay in L2)
   long npcap = (long)ksteps * rho;
-  if (Gs) {
-    int np0 = 0;
-    for (int I = 0; I < Gs->nr; ++I) {
-      const int len = Gs->h_rowptr[I + 1] - Gs->h_rowptr[I] - 1;
-      if (len > np0) np0 = len;
-    }
-    npcap += np0;
+  if (Gs) {  // a row of G_s holds its pattern nodes and the diagonal
+    int len = 0;
+    AMG_TRY(Gs->row_max(s, &len));
+    npcap += len > 0 ? len - 1 : 0;
   }
   if (npcap > maxg) npcap = maxg;
   K.mmax = A.b * (int)npcap + A.b;

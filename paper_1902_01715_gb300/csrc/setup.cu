@@ -1,20 +1,17 @@
 // Hierarchy set-up (Algorithm 1 of the paper): per level the aFSAI smoother
 // (Algorithm 3), the SRQCG test space (Algorithm 4), the affinity C/F split
 // (Sec. 3.3), DPLS prolongation (Algorithm 5) and the Galerkin product.
-// Floating-point work runs in the kernels of det.cu; this file does the
-// control flow and the integer graph work (pattern compaction and
-// transposition, DPLS candidate sets and the symbolic Galerkin pattern) on
-// the host; the maximal independent set runs in rounds on the GPU.
+// Floating-point work runs in the kernels of det.cu, the integer pattern work
+// in those of graph.cu and of this file (maximal independent set, candidate
+// sets, pattern compaction); the host keeps the control flow and reads back
+// only sizes and status words.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdarg>
 #include <cstdlib>
-#include <condition_variable>
 #include <cstring>
-#include <functional>
 #include <mutex>
-#include <thread>
 
 #include "amg_internal.h"
 
@@ -98,17 +95,6 @@ __global__ void k_compact_vals(int n, int cap, const int *__restrict__ rowptr, c
   const int len = rowptr[I + 1] - rowptr[I];
   if (j >= len) return;
   dst[((size_t)rowptr[I] + j) * BB + e] = src[((size_t)I * cap + j) * BB + e];
-}
-
-// T.val[dst] = transpose(A.val[perm[dst]])
-template <int B>
-__global__ void k_transpose_vals(int nnzb, const int *__restrict__ perm, const double *__restrict__ src,
-                                 double *__restrict__ dst) {
-  constexpr int BB = B * B;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long)BB * nnzb) return;
-  const int q = (int)(t / BB), e = (int)(t % BB), r = e / B, c = e % B;
-  dst[(size_t)q * BB + c * B + r] = src[(size_t)perm[q] * BB + e];
 }
 
 // P values: identity for coarse rows, DPLS blocks for fine rows.
@@ -237,37 +223,7 @@ __global__ void __launch_bounds__(256) k_gj_update(int m, int k0, int nb, double
   }
 }
 
-// ---------------------------------------------------------------- host graph work
-int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s) {
-  const int nnzb = A.nnzb;
-  AMG_TRY(T.alloc(A.nc, A.nr, nnzb, A.b));
-  T.h_rowptr.assign(A.nc + 1, 0);
-  T.h_col.resize(nnzb);
-  std::vector<int> perm(nnzb > 0 ? nnzb : 1);
-  for (int k = 0; k < nnzb; ++k) T.h_rowptr[A.h_col[k] + 1]++;
-  for (int i = 0; i < A.nc; ++i) T.h_rowptr[i + 1] += T.h_rowptr[i];
-  std::vector<int> next(T.h_rowptr.begin(), T.h_rowptr.end() - 1);
-  for (int I = 0; I < A.nr; ++I)
-    for (int k = A.h_rowptr[I]; k < A.h_rowptr[I + 1]; ++k) {
-      const int dst = next[A.h_col[k]]++;
-      T.h_col[dst] = I;
-      perm[dst] = k;
-    }
-  AMG_TRY(T.upload_pattern(s));
-  if (nnzb) {
-    DBuf<int> dperm;
-    AMG_TRY(dperm.alloc(nnzb));
-    AMG_CU(cudaMemcpyAsync(dperm.p, perm.data(), nnzb * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (A.b == 1)
-      AMG_KCOUNT k_transpose_vals<1><<<nblk((long)nnzb, 256), 256, 0, s>>>(nnzb, dperm.p, A.val.p, T.val.p);
-    else
-      AMG_KCOUNT k_transpose_vals<3><<<nblk(9L * nnzb, 256), 256, 0, s>>>(nnzb, dperm.p, A.val.p, T.val.p);
-    AMG_LAUNCH_CHECK();
-    AMG_CU(cudaStreamSynchronize(s));
-  }
-  return AMG_OK;
-}
-
+// ---------------------------------------------------------------- graph work
 // Maximal independent set of the strong graph, the one the greedy visit by
 // (degree descending, index ascending) gives: a visited undecided node
 // becomes coarse and its strong neighbours fine.  The same set comes out of
@@ -322,337 +278,72 @@ __global__ void k_mis_apply(int n, const int *__restrict__ rp, const int *__rest
     }
 }
 
-static int mis_gpu(const DevBsr &A, const unsigned char *d_strong, std::vector<int> &cf, cudaStream_t s) {
+// The C/F split into L.cf (1 coarse, 0 fine) on the device.
+static int mis_gpu(Level &L, const unsigned char *d_strong, cudaStream_t s) {
+  const DevBsr &A = L.A;
   const int n = A.nr;
-  cf.assign(n, 0);
+  AMG_TRY(L.cf.alloc(n));
   if (n == 0) return AMG_OK;
-  DBuf<int> deg, state, left;
+  DBuf<int> deg, left;
   DBuf<unsigned char> flag;
+  int *state = L.cf.p;
   AMG_TRY(deg.alloc(n));
-  AMG_TRY(state.alloc(n));
   AMG_TRY(flag.alloc(n));
   AMG_TRY(left.alloc(1));
   const int nb = nblk(n, 256);
-  AMG_KCOUNT k_mis_deg<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state.p);
+  AMG_KCOUNT k_mis_deg<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state);
   AMG_LAUNCH_CHECK();
   for (int round = 0;; ++round) {
     AMG_TRY(left.zero(s));
-    AMG_KCOUNT k_mis_select<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state.p, flag.p, left.p);
-    AMG_KCOUNT k_mis_apply<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, flag.p, state.p);
+    AMG_KCOUNT k_mis_select<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state, flag.p, left.p);
+    AMG_KCOUNT k_mis_apply<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, flag.p, state);
     AMG_LAUNCH_CHECK();
     int hl = 0;
-    AMG_CU(cudaMemcpyAsync(&hl, left.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AMG_CU(cudaStreamSynchronize(s));
+    AMG_TRY(read_int(left.p, &hl, s));
     if (hl == 0) break;
     if (round > n) {  // every round decides at least the top-ranked undecided node
       set_error("MIS: no progress");
       return AMG_ERR_CUDA;
     }
   }
-  AMG_CU(cudaMemcpy(cf.data(), state.p, n * sizeof(int), cudaMemcpyDeviceToHost));
   return AMG_OK;
 }
 
-// Host worker pool for the row-parallel graph work: rows are cut into
-// contiguous ranges, each range produces its own output in row order, and the
-// ranges are concatenated in order, so the result does not depend on the
-// number of threads.
-static int host_threads() {
-  static const int n = [] {
-    const char *e = getenv("AMG_HOST_THREADS");
-    int v = e ? atoi(e) : (int)std::thread::hardware_concurrency();
-    return v < 1 ? 1 : (v > 64 ? 64 : v);
-  }();
-  return n;
+// flag[I] = (cf[I] == want)
+__global__ void k_cf_flag(int n, const int *__restrict__ cf, int want, int *__restrict__ flag) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < n) flag[I] = cf[I] == want;
 }
 
-// Persistent workers: parallel_ranges hands each worker one contiguous range
-// and waits for all of them (threads are created once per process).
-class HostPool {
- public:
-  static HostPool &get() {
-    static HostPool pool(host_threads());
-    return pool;
-  }
-  void run(int nt, const std::function<void(int)> &job) {
-    std::lock_guard<std::mutex> one_at_a_time(run_mu_);  // callers from several host threads
-    std::unique_lock<std::mutex> lock(mu_);
-    job_ = &job;
-    njobs_ = nt;
-    next_ = 1;
-    done_ = 0;
-    ++epoch_;
-    cv_.notify_all();
-    lock.unlock();
-    job(0);  // the caller takes range 0
-    lock.lock();
-    ++done_;
-    done_cv_.wait(lock, [&] { return done_ == njobs_; });
-    job_ = nullptr;
-  }
-  ~HostPool() {
-    {
-      std::lock_guard<std::mutex> lock(mu_);
-      stop_ = true;
-      ++epoch_;
-    }
-    cv_.notify_all();
-    for (auto &t : th_) t.join();
-  }
-
- private:
-  explicit HostPool(int n) {
-    for (int i = 1; i < n; ++i) th_.emplace_back([this] { loop(); });
-  }
-  void loop() {
-    long seen = 0;
-    std::unique_lock<std::mutex> lock(mu_);
-    for (;;) {
-      cv_.wait(lock, [&] { return stop_ || (epoch_ != seen && job_ && next_ < njobs_); });
-      if (stop_) return;
-      seen = epoch_;
-      while (job_ && next_ < njobs_) {
-        const int id = next_++;
-        const std::function<void(int)> *job = job_;
-        lock.unlock();
-        (*job)(id);
-        lock.lock();
-        if (++done_ == njobs_) done_cv_.notify_all();
-      }
-    }
-  }
-  std::vector<std::thread> th_;
-  std::mutex run_mu_, mu_;
-  std::condition_variable cv_, done_cv_;
-  const std::function<void(int)> *job_ = nullptr;
-  int njobs_ = 0, next_ = 0, done_ = 0;
-  long epoch_ = 0;
-  bool stop_ = false;
-};
-
-template <class F>
-static void parallel_ranges(int n, F f) {
-  const int nt = std::min(host_threads(), std::max(1, n / 2048));
-  if (nt <= 1) {
-    f(0, 0, n);
-    return;
-  }
-  const std::function<void(int)> job = [&](int t) {
-    const int lo = (int)((long)n * t / nt), hi = (int)((long)n * (t + 1) / nt);
-    f(t, lo, hi);
-  };
-  HostPool::get().run(nt, job);
+// From the prefix sums of the coarse and fine flags: cidx[I] = coarse index
+// of I (or -1), fidx[I] = fine index of I (or -1), fnodes[fine index] = I.
+__global__ void k_cf_split(int n, const int *__restrict__ cf, const int *__restrict__ cs, const int *__restrict__ fs,
+                           int *__restrict__ cidx, int *__restrict__ fidx, int *__restrict__ fnodes) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  const bool c = cf[I] == 1;
+  cidx[I] = c ? cs[I] : -1;
+  fidx[I] = c ? -1 : fs[I];
+  if (!c) fnodes[fs[I]] = I;
 }
 
-// Concatenates per-range outputs in range order: row lengths into a row
-// pointer starting at rp[0], entries into out (both filled in parallel).
-static void concat_ranges(const std::vector<std::vector<int>> &len, const std::vector<std::vector<int>> &ent,
-                          std::vector<int> &rp, std::vector<int> &out) {
-  const int nt = (int)len.size();
-  std::vector<long> row0(nt + 1, 0), e0(nt + 1, 0);
-  for (int t = 0; t < nt; ++t) {
-    row0[t + 1] = row0[t] + (long)len[t].size();
-    e0[t + 1] = e0[t] + (long)ent[t].size();
-  }
-  rp.assign(row0[nt] + 1, 0);
-  out.resize(e0[nt]);
-  const std::function<void(int)> job = [&](int t) {
-    std::copy(ent[t].begin(), ent[t].end(), out.begin() + e0[t]);
-    long r = row0[t], acc = e0[t];
-    for (int l : len[t]) {
-      acc += l;
-      rp[++r] = (int)acc;
-    }
-  };
-  if (nt > 1) HostPool::get().run(nt, job);
-  else if (nt == 1) job(0);
+// rows of the next level's starting test space: the B dofs of each coarse node
+__global__ void k_coarse_src(int n, int B, const int *__restrict__ cidx, int *__restrict__ src) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n || cidx[I] < 0) return;
+  for (int c = 0; c < B; ++c) src[B * cidx[I] + c] = B * I + c;
 }
 
-// Coarse nodes within d_p strong edges of every fine node, ascending.
-static void dpls_candidates(const DevBsr &A, const std::vector<unsigned char> &strong, const std::vector<int> &cf,
-                            int d_p, std::vector<int> &fnodes, std::vector<int> &cptr, std::vector<int> &cand) {
-  const int n = A.nr;
-  const int nt = std::min(host_threads(), std::max(1, n / 2048));
-  std::vector<std::vector<int>> pf(nt), pl(nt), pc(nt);
-  parallel_ranges(n, [&](int t, int lo, int hi) {
-    std::vector<int> dist(n, -1), front;
-    std::vector<int> &fn = pf[t], &len = pl[t], &cd = pc[t];
-    for (int I = lo; I < hi; ++I) {
-      if (cf[I] == 1) continue;
-      fn.push_back(I);
-      front.assign(1, I);
-      dist[I] = 0;
-      const size_t c0 = cd.size();
-      for (size_t q = 0; q < front.size(); ++q) {
-        const int K = front[q];
-        if (dist[K] >= d_p) continue;
-        for (int k = A.h_rowptr[K]; k < A.h_rowptr[K + 1]; ++k) {
-          const int J = A.h_col[k];
-          if (!strong[k] || J == K || dist[J] >= 0) continue;
-          dist[J] = dist[K] + 1;
-          front.push_back(J);
-          if (cf[J] == 1) cd.push_back(J);
-        }
-      }
-      for (int K : front) dist[K] = -1;
-      std::sort(cd.begin() + c0, cd.end());
-      len.push_back((int)(cd.size() - c0));
-    }
-  });
-  fnodes.clear();
-  for (int t = 0; t < (int)pf.size(); ++t) fnodes.insert(fnodes.end(), pf[t].begin(), pf[t].end());
-  concat_ranges(pl, pc, cptr, cand);
-}
-
-// Pattern of Z = X Y (columns ascending).
-static void symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z) {
-  const int nr = X.nr, nc = Y.nc;
-  const int nt = std::min(host_threads(), std::max(1, nr / 2048));
-  std::vector<std::vector<int>> pcols(nt), plen(nt);
-  parallel_ranges(nr, [&](int t, int lo, int hi) {
-    std::vector<int> mark(nc, -1), cols;
-    std::vector<int> &out = pcols[t], &len = plen[t];
-    for (int i = lo; i < hi; ++i) {
-      cols.clear();
-      for (int kx = X.h_rowptr[i]; kx < X.h_rowptr[i + 1]; ++kx) {
-        const int k = X.h_col[kx];
-        for (int ky = Y.h_rowptr[k]; ky < Y.h_rowptr[k + 1]; ++ky) {
-          const int c = Y.h_col[ky];
-          if (mark[c] != i) {
-            mark[c] = i;
-            cols.push_back(c);
-          }
-        }
-      }
-      std::sort(cols.begin(), cols.end());
-      out.insert(out.end(), cols.begin(), cols.end());
-      len.push_back((int)cols.size());
-    }
-  });
-  concat_ranges(plen, pcols, Z.h_rowptr, Z.h_col);
-  Z.nr = nr;
-  Z.nc = nc;
-  Z.nnzb = (int)Z.h_col.size();
-}
-
-// Pattern of Z = X Y on the GPU: row i of Z is the union of the (sorted)
-// rows of Y named by row i of X.  One warp per row merges them: lane l holds
-// the heads of lists l, l+32, ...; each step takes the warp minimum, emits it
-// once and advances every list whose head equals it, so the output is
-// ascending and duplicate-free.  Pass 0 counts, pass 1 writes.
-__global__ void k_sym_merge(int nr, const int *__restrict__ xr, const int *__restrict__ xc,
-                            const int *__restrict__ yr, const int *__restrict__ yc, const int *__restrict__ zr,
-                            int *__restrict__ zc, int *__restrict__ cnt) {
-  const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i >= nr) return;
-  const int l0 = xr[i], nl = xr[i + 1] - l0;
-  constexpr int PER = 8;  // lists per lane held in registers
-  int pos[PER], end[PER];
-  for (int u = 0; u < PER; ++u) {
-    const int q = lane + 32 * u;
-    if (q < nl) {
-      const int k = xc[l0 + q];
-      pos[u] = yr[k];
-      end[u] = yr[k + 1];
-    } else {
-      pos[u] = end[u] = 0;
-    }
-  }
-  int out = zc ? zr[i] : 0, n = 0;
-  for (;;) {
-    int h = 0x7fffffff;
-    for (int u = 0; u < PER; ++u)
-      if (pos[u] < end[u]) h = min(h, yc[pos[u]]);
-    for (int off = 16; off >= 1; off >>= 1) h = min(h, __shfl_xor_sync(0xffffffffu, h, off));
-    if (h == 0x7fffffff) break;
-    if (lane == 0 && zc) zc[out + n] = h;
-    ++n;
-    for (int u = 0; u < PER; ++u)
-      if (pos[u] < end[u] && yc[pos[u]] == h) ++pos[u];
-  }
-  if (lane == 0 && !zc) cnt[i] = n;
-}
-
-// exclusive prefix sum of n ints into out[0..n] (one block; the host checks
-// that n is small enough, else the scan runs on the host)
-__global__ void __launch_bounds__(1024) k_scan1(int n, const int *__restrict__ in, int *__restrict__ out) {
-  __shared__ int part[1024];
-  const int per = (n + 1023) / 1024;
-  const int lo = threadIdx.x * per, hi = min(n, lo + per);
-  int s = 0;
-  for (int i = lo; i < hi; ++i) s += in[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int acc = threadIdx.x ? part[threadIdx.x - 1] : 0;
-  for (int i = lo; i < hi; ++i) {
-    out[i] = acc;
-    acc += in[i];
-  }
-  if (threadIdx.x == 1023) out[n] = part[1023];
-}
-
-// Z's pattern on the device (Z.rowptr, Z.col, Z.val allocated); the host
-// mirror only when want_host.
-static int symbolic_product_gpu(const DevBsr &X, const DevBsr &Y, DevBsr &Z, bool want_host, cudaStream_t s) {
-  const int nr = X.nr;
-  int maxlen = 0;
-  for (int i = 0; i < nr; ++i) maxlen = std::max(maxlen, X.h_rowptr[i + 1] - X.h_rowptr[i]);
-  if (maxlen > 32 * 8) return AMG_ERR_ARG;  // caller falls back to the host product
-  DBuf<int> cnt, rp;
-  AMG_TRY(cnt.alloc(nr));
-  AMG_TRY(rp.alloc(nr + 1));
-  const int nb = nblk(32L * nr, 256);
-  if (nr) AMG_KCOUNT k_sym_merge<<<nb, 256, 0, s>>>(nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, nullptr, nullptr, cnt.p);
-  AMG_KCOUNT k_scan1<<<1, 1024, 0, s>>>(nr, cnt.p, rp.p);
-  AMG_LAUNCH_CHECK();
-  int nnz = 0;
-  AMG_CU(cudaMemcpyAsync(&nnz, rp.p + nr, sizeof(int), cudaMemcpyDeviceToHost, s));
-  AMG_CU(cudaStreamSynchronize(s));
-  AMG_TRY(Z.alloc(nr, Y.nc, nnz, X.b));
-  AMG_CU(cudaMemcpyAsync(Z.rowptr.p, rp.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  if (nr) AMG_KCOUNT k_sym_merge<<<nb, 256, 0, s>>>(nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, rp.p, Z.col.p, nullptr);
-  AMG_LAUNCH_CHECK();
-  if (want_host) AMG_TRY(Z.download_pattern(s));
-  return AMG_OK;
-}
-
+// Galerkin product A_c = R (A P): patterns by pattern products on the GPU,
+// values in fixed order (det::spgemm_numeric).
 static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &Ac, cudaStream_t s) {
   DevBsr AP;
   double tt = now_s();
-  // AP's pattern stays on the device (its host mirror is only needed when
-  // R's rows are too long for the GPU merge)
-  int rc = symbolic_product_gpu(A, P, AP, false, s);
-  bool ap_host = false;
-  if (rc == AMG_ERR_ARG) {
-    symbolic_product(A, P, AP);
-    AMG_TRY(AP.alloc(AP.nr, AP.nc, AP.nnzb, A.b));
-    AMG_TRY(AP.upload_pattern(s));
-    ap_host = true;
-  } else if (rc) {
-    return rc;
-  }
+  AMG_TRY(symbolic_product(A, P, AP, A.b, s));
   trace("AP symbolic", -1, tt);
   tt = now_s();
   AMG_TRY(det::spgemm_numeric(A, P, AP, s));
-  AMG_CU(cudaStreamSynchronize(s));
-  trace("AP numeric", -1, tt);
-  tt = now_s();
-  rc = symbolic_product_gpu(R, AP, Ac, true, s);
-  if (rc == AMG_ERR_ARG) {
-    if (!ap_host) AMG_TRY(AP.download_pattern(s));
-    symbolic_product(R, AP, Ac);
-    AMG_TRY(Ac.alloc(Ac.nr, Ac.nc, Ac.nnzb, A.b));
-    AMG_TRY(Ac.upload_pattern(s));
-  } else if (rc) {
-    return rc;
-  }
+  AMG_TRY(symbolic_product(R, AP, Ac, A.b, s));
   trace("RAP symbolic", -1, tt);
   tt = now_s();
   AMG_TRY(det::spgemm_numeric(R, AP, Ac, s));
@@ -661,12 +352,22 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
   return AMG_OK;
 }
 
+// G column indices from the aFSAI output: row I holds its pattern nodes
+// (ascending), then I
+__global__ void k_fsai_cols(int n, int maxg, const int *__restrict__ np, const int *__restrict__ pat,
+                            const int *__restrict__ rp, int *__restrict__ col) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = (int)(t / (maxg + 1)), j = (int)(t % (maxg + 1));
+  if (I >= n || j > np[I]) return;
+  col[rp[I] + j] = j < np[I] ? pat[(size_t)I * maxg + j] : I;
+}
+
 // aFSAI(A, G_s, k, rho, eps) into a compact G.
 static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double eps, int maxg, DevBsr &G,
                     cudaStream_t s) {
   const int n = A.nr;
   int maxdeg = 0;
-  for (int I = 0; I < n; ++I) maxdeg = std::max(maxdeg, A.h_rowptr[I + 1] - A.h_rowptr[I]);
+  AMG_TRY(A.row_max(s, &maxdeg));
   DBuf<int> np, pat, status;
   DBuf<double> val;
   const int bb = A.b * A.b;
@@ -678,33 +379,24 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
   det::FsaiOut out{np.p, pat.p, val.p};
   AMG_TRY(det::fsai(A, Gs, k, rho, eps, maxg, maxdeg, out, status.p, s));
   int st = 0;
-  AMG_CU(cudaMemcpy(&st, status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  AMG_TRY(read_int(status.p, &st, s));
   if (st) {
     set_error("aFSAI: non-positive pivot in a row system (matrix not SPD)");
     return st;
   }
-  std::vector<int> hnp(n), hpat((size_t)n * maxg);
-  AMG_CU(cudaMemcpy(hnp.data(), np.p, n * sizeof(int), cudaMemcpyDeviceToHost));
-  AMG_CU(cudaMemcpy(hpat.data(), pat.p, (size_t)n * maxg * sizeof(int), cudaMemcpyDeviceToHost));
-  std::vector<int> rp(n + 1, 0);
-  for (int I = 0; I < n; ++I) rp[I + 1] = rp[I] + hnp[I] + 1;
-  std::vector<int> cl(rp[n]);
-  parallel_ranges(n, [&](int, int lo, int hi) {
-    for (int I = lo; I < hi; ++I) {
-      int *o = cl.data() + rp[I];
-      for (int j = 0; j < hnp[I]; ++j) o[j] = hpat[(size_t)I * maxg + j];
-      o[hnp[I]] = I;
-    }
-  });
-  AMG_TRY(G.alloc(n, n, (int)cl.size(), A.b));
-  G.h_rowptr = std::move(rp);
-  G.h_col = std::move(cl);
-  AMG_TRY(G.upload_pattern(s));
+  DBuf<int> rp;
+  AMG_TRY(rp.alloc(n + 1));
+  AMG_TRY(dev_scan(n, np.p, 1, rp.p, s));
+  int nnz = 0;
+  AMG_TRY(read_int(rp.p + n, &nnz, s));
+  AMG_TRY(G.alloc(n, n, nnz, A.b));
+  AMG_CU(cudaMemcpyAsync(G.rowptr.p, rp.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  const long nt = (long)n * (maxg + 1);
+  if (n) AMG_KCOUNT k_fsai_cols<<<nblk(nt, 256), 256, 0, s>>>(n, maxg, np.p, pat.p, G.rowptr.p, G.col.p);
   if (A.b == 1)
-    AMG_KCOUNT k_compact_vals<1><<<nblk((long)n * (maxg + 1), 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
+    AMG_KCOUNT k_compact_vals<1><<<nblk(nt, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
   else
-    AMG_KCOUNT k_compact_vals<3><<<nblk((long)n * (maxg + 1) * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p,
-                                                                                   G.val.p);
+    AMG_KCOUNT k_compact_vals<3><<<nblk(nt * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -719,7 +411,7 @@ int bench_fsai(Handle *h, int lev, int reps, double *ms) {
   cudaStream_t s = h->stream;
   const int n = L.A.nr, maxg = p.max_g_nodes;
   int maxdeg = 0;
-  for (int I = 0; I < n; ++I) maxdeg = std::max(maxdeg, L.A.h_rowptr[I + 1] - L.A.h_rowptr[I]);
+  AMG_TRY(L.A.row_max(s, &maxdeg));
   DBuf<int> np, pat, status;
   DBuf<double> val;
   AMG_TRY(np.alloc(n));
@@ -866,90 +558,103 @@ __global__ void __launch_bounds__(128) k_dpls_cand(int nf, const int *__restrict
   if (lane == 0 && !cand) cnt[f] = n;
 }
 
-static int build_P(Handle *h, Level &L, const std::vector<unsigned char> &strong, const unsigned char *d_strong) {
+// P row lengths: 1 for a coarse node, its DPLS count for a fine node
+__global__ void k_p_len(int n, const int *__restrict__ fidx, const int *__restrict__ cnt, int *__restrict__ len) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < n) len[I] = fidx[I] < 0 ? 1 : cnt[fidx[I]];
+}
+
+// P columns: the coarse index of a coarse node, the DPLS columns of a fine one
+__global__ void k_p_cols(int n, int cap, const int *__restrict__ cidx, const int *__restrict__ fidx,
+                         const int *__restrict__ fcol, const int *__restrict__ rp, int *__restrict__ col) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = (int)(t / cap), j = (int)(t % cap);
+  if (I >= n || j >= rp[I + 1] - rp[I]) return;
+  col[rp[I] + j] = cidx[I] >= 0 ? cidx[I] : fcol[(size_t)fidx[I] * cap + j];
+}
+
+// Node numbering of the C/F split of a level (device arrays).
+struct CfSplit {
+  DBuf<int> cidx, fidx, fnodes;
+  int nc = 0, nf = 0;
+};
+
+static int split_nodes(const Level &L, CfSplit &c, cudaStream_t s) {
+  const int n = L.n;
+  DBuf<int> flag, cs, fs;
+  AMG_TRY(flag.alloc(n));
+  AMG_TRY(cs.alloc(n + 1));
+  AMG_TRY(fs.alloc(n + 1));
+  const int nb = nblk(n, 256);
+  if (n) AMG_KCOUNT k_cf_flag<<<nb, 256, 0, s>>>(n, L.cf.p, 1, flag.p);
+  AMG_TRY(dev_scan(n, flag.p, 0, cs.p, s));
+  if (n) AMG_KCOUNT k_cf_flag<<<nb, 256, 0, s>>>(n, L.cf.p, 0, flag.p);
+  AMG_TRY(dev_scan(n, flag.p, 0, fs.p, s));
+  AMG_TRY(read_int(cs.p + n, &c.nc, s));
+  c.nf = n - c.nc;
+  AMG_TRY(c.cidx.alloc(n));
+  AMG_TRY(c.fidx.alloc(n));
+  AMG_TRY(c.fnodes.alloc(c.nf));
+  if (n) AMG_KCOUNT k_cf_split<<<nb, 256, 0, s>>>(n, L.cf.p, cs.p, fs.p, c.cidx.p, c.fidx.p, c.fnodes.p);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+static int build_P(Handle *h, Level &L, const unsigned char *d_strong, const CfSplit &c) {
   const amg_params &p = h->prm;
   cudaStream_t s = h->stream;
-  const int n = L.n, t = p.n_tv;
-  std::vector<int> cidx(n, -1), fnodes;
-  int nc = 0;
-  for (int I = 0; I < n; ++I) {
-    if (L.cf[I] == 1) cidx[I] = nc++;
-    else fnodes.push_back(I);
-  }
-  L.nc = nc;
+  const int n = L.n, t = p.n_tv, nf = c.nf;
+  L.nc = c.nc;
   double tt = now_s();
-  const int nf = (int)fnodes.size();
   const int B = L.A.b, BB = B * B;
   const int cap = std::max(1, std::min(p.n_max, t / B));
-  DBuf<int> d_cidx, d_f, d_cptr, d_cand, d_cnt, d_col, d_cf;
+  DBuf<int> d_cptr, d_cand, d_cnt, d_col;
   DBuf<double> d_val;
-  AMG_TRY(d_cidx.alloc(n));
-  AMG_TRY(d_f.alloc(nf));
   AMG_TRY(d_cptr.alloc(nf + 1));
   AMG_TRY(d_cnt.alloc(nf));
   AMG_TRY(d_col.alloc((size_t)nf * cap));
   AMG_TRY(d_val.alloc((size_t)nf * cap * BB));
-  AMG_CU(cudaMemcpyAsync(d_cidx.p, cidx.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
-  if (nf) AMG_CU(cudaMemcpyAsync(d_f.p, fnodes.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s));
   int maxdeg = 0;
-  for (int I = 0; I < n; ++I) maxdeg = std::max(maxdeg, L.A.h_rowptr[I + 1] - L.A.h_rowptr[I]);
+  AMG_TRY(L.A.row_max(s, &maxdeg));
   if (nf && p.d_p <= 2 && maxdeg < 256) {
-    AMG_TRY(d_cf.alloc(n));
-    AMG_CU(cudaMemcpyAsync(d_cf.p, L.cf.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
     const int nb = nblk(32L * nf, 128);
-    AMG_KCOUNT k_dpls_cand<<<nb, 128, 0, s>>>(nf, d_f.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, d_cf.p,
+    AMG_KCOUNT k_dpls_cand<<<nb, 128, 0, s>>>(nf, c.fnodes.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, L.cf.p,
                                               nullptr, nullptr, d_cnt.p);
-    AMG_KCOUNT k_scan1<<<1, 1024, 0, s>>>(nf, d_cnt.p, d_cptr.p);
     AMG_LAUNCH_CHECK();
+    AMG_TRY(dev_scan(nf, d_cnt.p, 0, d_cptr.p, s));
     int ncand = 0;
-    AMG_CU(cudaMemcpyAsync(&ncand, d_cptr.p + nf, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AMG_CU(cudaStreamSynchronize(s));
+    AMG_TRY(read_int(d_cptr.p + nf, &ncand, s));
     AMG_TRY(d_cand.alloc(ncand));
-    AMG_KCOUNT k_dpls_cand<<<nb, 128, 0, s>>>(nf, d_f.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, d_cf.p,
+    AMG_KCOUNT k_dpls_cand<<<nb, 128, 0, s>>>(nf, c.fnodes.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, L.cf.p,
                                               d_cptr.p, d_cand.p, nullptr);
     AMG_LAUNCH_CHECK();
-  } else if (nf) {
-    std::vector<int> fn2, cptr, cand;
-    dpls_candidates(L.A, strong, L.cf, p.d_p, fn2, cptr, cand);
-    AMG_TRY(d_cand.alloc(cand.size()));
-    AMG_CU(cudaMemcpyAsync(d_cptr.p, cptr.data(), (nf + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (!cand.empty())
-      AMG_CU(cudaMemcpyAsync(d_cand.p, cand.data(), cand.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    AMG_CU(cudaStreamSynchronize(s));
+  } else if (nf) {  // longer rows or a larger distance: products of patterns
+    AMG_TRY(dpls_candidates_gpu(L.A, d_strong, L.cf.p, c.fnodes.p, nf, p.d_p, d_cptr.p, d_cand, s));
   }
   trace("DPLS candidates", -1, tt);
   tt = now_s();
   if (nf) {
-    AMG_TRY(det::dpls(L.A, nullptr, nullptr, d_cidx.p, d_f.p, nf, d_cptr.p, d_cand.p, t, L.V.p, p.n_max,
+    AMG_TRY(det::dpls(L.A, nullptr, nullptr, c.cidx.p, c.fnodes.p, nf, d_cptr.p, d_cand.p, t, L.V.p, p.n_max,
                       p.kappa_p, d_cnt.p, d_col.p, d_val.p, nullptr, s));
   }
   trace("DPLS kernel", -1, tt);
-  std::vector<int> hcnt(nf), hcol((size_t)nf * cap), fidx(n, -1);
-  if (nf) {
-    AMG_CU(cudaMemcpy(hcnt.data(), d_cnt.p, nf * sizeof(int), cudaMemcpyDeviceToHost));
-    AMG_CU(cudaMemcpy(hcol.data(), d_col.p, (size_t)nf * cap * sizeof(int), cudaMemcpyDeviceToHost));
-  }
-  for (int f = 0; f < nf; ++f) fidx[fnodes[f]] = f;
-  std::vector<int> rp(n + 1, 0), cl;
-  for (int I = 0; I < n; ++I) {
-    if (L.cf[I] == 1) cl.push_back(cidx[I]);
-    else {
-      const int f = fidx[I];
-      for (int u = 0; u < hcnt[f]; ++u) cl.push_back(hcol[(size_t)f * cap + u]);
-    }
-    rp[I + 1] = (int)cl.size();
-  }
-  AMG_TRY(L.P.alloc(n, nc, (int)cl.size(), B));
-  L.P.h_rowptr = std::move(rp);
-  L.P.h_col = std::move(cl);
-  AMG_TRY(L.P.upload_pattern(s));
-  DBuf<int> d_fidx;
-  AMG_TRY(d_fidx.alloc(n));
-  AMG_CU(cudaMemcpyAsync(d_fidx.p, fidx.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  DBuf<int> len, rp;
+  AMG_TRY(len.alloc(n));
+  AMG_TRY(rp.alloc(n + 1));
+  if (n) AMG_KCOUNT k_p_len<<<nblk(n, 256), 256, 0, s>>>(n, c.fidx.p, d_cnt.p, len.p);
+  AMG_TRY(dev_scan(n, len.p, 0, rp.p, s));
+  int nnz = 0;
+  AMG_TRY(read_int(rp.p + n, &nnz, s));
+  AMG_TRY(L.P.alloc(n, c.nc, nnz, B));
+  AMG_CU(cudaMemcpyAsync(L.P.rowptr.p, rp.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (n)
+    AMG_KCOUNT k_p_cols<<<nblk((long)n * cap, 256), 256, 0, s>>>(n, cap, c.cidx.p, c.fidx.p, d_col.p, L.P.rowptr.p,
+                                                                  L.P.col.p);
   if (B == 1)
-    AMG_KCOUNT k_p_vals<1><<<nblk((long)n * cap, 256), 256, 0, s>>>(n, L.P.rowptr.p, d_fidx.p, cap, d_val.p, L.P.val.p);
+    AMG_KCOUNT k_p_vals<1><<<nblk((long)n * cap, 256), 256, 0, s>>>(n, L.P.rowptr.p, c.fidx.p, cap, d_val.p,
+                                                                     L.P.val.p);
   else
-    AMG_KCOUNT k_p_vals<3><<<nblk((long)n * cap * 9, 256), 256, 0, s>>>(n, L.P.rowptr.p, d_fidx.p, cap, d_val.p,
+    AMG_KCOUNT k_p_vals<3><<<nblk((long)n * cap * 9, 256), 256, 0, s>>>(n, L.P.rowptr.p, c.fidx.p, cap, d_val.p,
                                                                       L.P.val.p);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
@@ -996,6 +701,32 @@ static int coarse_factor(Handle *h, Level &L) {
   return AMG_OK;
 }
 
+// First invalid row of a level-0 pattern (else *bad stays n): row pointers
+// start at 0, do not decrease and stay within [0, nnzb]; columns lie in
+// [0, n) and increase strictly along a row.  Columns are read only between
+// valid row pointers.
+__global__ void k_check_pattern(int n, int nnzb, const int *__restrict__ rp, const int *__restrict__ col,
+                                int *__restrict__ bad) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I > n) return;
+  if (I == n) {
+    if (rp[n] != nnzb) atomicMin(bad, n > 0 ? n - 1 : 0);
+    return;
+  }
+  const int b = rp[I], e = rp[I + 1];
+  if ((I == 0 && b != 0) || b < 0 || e < b || e > nnzb) {
+    atomicMin(bad, I);
+    return;
+  }
+  for (int k = b; k < e; ++k) {
+    const int J = col[k];
+    if (J < 0 || J >= n || (k > b && col[k - 1] >= J)) {
+      atomicMin(bad, I);
+      return;
+    }
+  }
+}
+
 void free_hierarchy(Handle *h) {
   h->lev.clear();
   h->nlev = 0;
@@ -1025,25 +756,27 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
       return AMG_ERR_ARG;
     }
     const int n = h->n;
-    std::vector<int> hrp(n + 1);
-    if (mem == AMG_MEM_HOST) memcpy(hrp.data(), rowptr, (n + 1) * sizeof(int));
-    else AMG_CU(cudaMemcpy(hrp.data(), rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
-    const int nnzb = hrp[n];
-    AMG_TRY(L0->A.alloc(n, n, nnzb, h->b));
-    L0->A.h_rowptr = std::move(hrp);
-    L0->A.h_col.resize(nnzb);
-    if (mem == AMG_MEM_HOST) memcpy(L0->A.h_col.data(), col, nnzb * sizeof(int));
-    else AMG_CU(cudaMemcpy(L0->A.h_col.data(), col, nnzb * sizeof(int), cudaMemcpyDeviceToHost));
-    for (int I = 0; I < n; ++I) {
-      for (int k = L0->A.h_rowptr[I]; k < L0->A.h_rowptr[I + 1]; ++k) {
-        const int J = L0->A.h_col[k];
-        if (J < 0 || J >= n || (k > L0->A.h_rowptr[I] && L0->A.h_col[k - 1] >= J)) {
-          set_error("K pattern: row %d has an invalid or unsorted column index %d", I, J);
-          return AMG_ERR_ARG;
-        }
-      }
+    int nnzb = 0;
+    if (mem == AMG_MEM_HOST) nnzb = rowptr[n];
+    else AMG_TRY(read_int(rowptr + n, &nnzb, s));
+    if (nnzb < 0) {
+      set_error("K pattern: negative entry count %d", nnzb);
+      return AMG_ERR_ARG;
     }
-    AMG_TRY(L0->A.upload_pattern(s));
+    AMG_TRY(L0->A.alloc(n, n, nnzb, h->b));
+    AMG_CU(cudaMemcpyAsync(L0->A.rowptr.p, rowptr, (n + 1) * sizeof(int), kind, s));
+    if (nnzb) AMG_CU(cudaMemcpyAsync(L0->A.col.p, col, (size_t)nnzb * sizeof(int), kind, s));
+    DBuf<int> bad;
+    AMG_TRY(bad.alloc(1));
+    AMG_CU(cudaMemcpyAsync(bad.p, &n, sizeof(int), cudaMemcpyHostToDevice, s));
+    AMG_KCOUNT k_check_pattern<<<nblk(n + 1, 256), 256, 0, s>>>(n, nnzb, L0->A.rowptr.p, L0->A.col.p, bad.p);
+    AMG_LAUNCH_CHECK();
+    int hb = n;
+    AMG_TRY(read_int(bad.p, &hb, s));
+    if (hb < n) {
+      set_error("K pattern: row %d has an invalid row pointer or an invalid or unsorted column index", hb);
+      return AMG_ERR_ARG;
+    }
     AMG_CU(cudaMemcpyAsync(L0->A.val.p, vals, (size_t)nnzb * h->b * h->b * sizeof(double), kind, s));
     L0->n = n;
   }
@@ -1109,25 +842,23 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     T_ts += t2 - t1 - tw;
     AMG_TRY(d_strong.alloc(L.A.nnzb));
     AMG_TRY(det::soc_filter(L.A, t, L.V.p, p.theta, d_strong.p, s));
-    std::vector<unsigned char> strong(L.A.nnzb);
-    if (L.A.nnzb)
-      AMG_CU(cudaMemcpy(strong.data(), d_strong.p, L.A.nnzb, cudaMemcpyDeviceToHost));
     trace("SoC filter", k, t2);
     double tm = now_s();
-    AMG_TRY(mis_gpu(L.A, d_strong.p, L.cf, s));
+    AMG_TRY(mis_gpu(L, d_strong.p, s));
+    CfSplit split;
+    AMG_TRY(split_nodes(L, split, s));
     trace("MIS", k, tm);
-    int nc = 0;
-    for (int I = 0; I < L.n; ++I) nc += (L.cf[I] == 1);
+    const int nc = split.nc;
     double t3 = now_s();
     T_cs += t3 - t2;
     if (nc == 0 || (double)nc > p.max_coarse_ratio * (double)L.n) {
       L.G = DevBsr();
       L.GT = DevBsr();
       L.V.release();
-      L.cf.clear();
+      L.cf.release();
       break;
     }
-    AMG_TRY(build_P(h, L, strong, d_strong.p));
+    AMG_TRY(build_P(h, L, d_strong.p, split));
     AMG_TRY(transpose_bsr(L.P, L.R, s));
     double t4 = now_s();
     T_pl += t4 - t3;
@@ -1138,16 +869,10 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     T_rap += t5 - t4;
     // next level's starting test space: rows of the coarse nodes
     {
-      std::vector<int> src((size_t)B * nc);
-      int q = 0;
-      for (int I = 0; I < L.n; ++I)
-        if (L.cf[I] == 1) {
-          for (int c = 0; c < B; ++c) src[(size_t)B * q + c] = B * I + c;
-          ++q;
-        }
       DBuf<int> dsrc;
       AMG_TRY(dsrc.alloc((size_t)B * nc));
-      AMG_CU(cudaMemcpyAsync(dsrc.p, src.data(), (size_t)B * nc * sizeof(int), cudaMemcpyHostToDevice, s));
+      AMG_KCOUNT k_coarse_src<<<nblk(L.n, 256), 256, 0, s>>>(L.n, B, split.cidx.p, dsrc.p);
+      AMG_LAUNCH_CHECK();
       DBuf<double> Vn;
       AMG_TRY(Vn.alloc((size_t)B * nc * t));
       AMG_TRY(det::gather_rows(dsrc.p, B * nc, n3, t, L.V.p, Vn.p, s));

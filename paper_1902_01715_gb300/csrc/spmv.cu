@@ -635,6 +635,43 @@ static int rule_map(const SolveMat &M) {
   }
 }
 
+// Slice heights of the layout: h[s] = 32 x the longest row at positions
+// [32 s, 32 s + 32) (row prow[pos], or pos); their sum into *tot.  One warp
+// per slice.
+__global__ void k_slice_h(int nr, int ns, const int *__restrict__ rp, const int *__restrict__ prow,
+                          int *__restrict__ h, unsigned long long *__restrict__ tot) {
+  const int sl = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (sl >= ns) return;
+  const int pos = 32 * sl + lane;
+  int len = 0;
+  if (pos < nr) {
+    const int r = prow ? prow[pos] : pos;
+    len = rp[r + 1] - rp[r];
+  }
+  for (int off = 16; off; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
+  if (lane == 0) {
+    h[sl] = 32 * len;
+    atomicAdd(tot, 32ULL * (unsigned long long)len);
+  }
+}
+
+// Rows by decreasing length inside windows of SELL_SIGMA rows, ties in row
+// order: the position of row r in its window is the number of rows of the
+// window that are longer, plus those before r that are as long.  One CTA of
+// SELL_SIGMA threads per window.
+__global__ void __launch_bounds__(SELL_SIGMA) k_sell_perm(int nr, const int *__restrict__ rp, int *__restrict__ prow) {
+  __shared__ int len[SELL_SIGMA];
+  const int w0 = blockIdx.x * SELL_SIGMA, q = threadIdx.x;
+  const int wn = min(SELL_SIGMA, nr - w0);
+  if (q < wn) len[q] = rp[w0 + q + 1] - rp[w0 + q];
+  __syncthreads();
+  if (q >= wn) return;
+  const int L = len[q];
+  int at = 0;
+  for (int u = 0; u < wn; ++u) at += (len[u] > L) || (len[u] == L && u < q);
+  prow[w0 + at] = w0 + q;
+}
+
 int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s) {
   M.nr = A.nr;
   M.nc = A.nc;
@@ -643,62 +680,40 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
   M.rowptr = A.rowptr.p;
   M.col = A.col.p;
   M.ns = (A.nr + 31) / 32;
-  // Rows by decreasing length inside each window of SELL_SIGMA rows (stable,
-  // by counting), for FP64 storage only and only where the natural order
-  // fills the slices poorly: FP64 instructions cost the same with idle lanes,
-  // while the bandwidth-bound FP32/bf16 products lose more to the scattered
-  // row order than they gain.
-  auto rlen = [&](int r) { return A.h_rowptr[r + 1] - A.h_rowptr[r]; };
-  std::vector<int> perm(A.nr);
-  for (int r = 0; r < A.nr; ++r) perm[r] = r;
-  bool ident = true;
-  if (f64 && !f32 && !b16 && A.nr > 0) {
-    long used = 0, slots = 0;
-    for (int sl = 0; sl < M.ns; ++sl) {
-      int mx = 0;
-      const int r1 = std::min(A.nr, 32 * sl + 32);
-      for (int r = 32 * sl; r < r1; ++r) mx = std::max(mx, rlen(r));
-      slots += 32L * mx;
-    }
-    used = A.nnzb;
-    if (slots > 0 && (double)used < 0.9 * (double)slots) {
-      int maxlen = 0;
-      for (int r = 0; r < A.nr; ++r) maxlen = std::max(maxlen, rlen(r));
-      std::vector<int> cnt(maxlen + 2);
-      for (int w0 = 0; w0 < A.nr; w0 += SELL_SIGMA) {
-        const int w1 = std::min(A.nr, w0 + SELL_SIGMA);
-        std::fill(cnt.begin(), cnt.end(), 0);
-        for (int r = w0; r < w1; ++r) ++cnt[maxlen - rlen(r) + 1];  // longest first
-        for (int q = 1; q <= maxlen + 1; ++q) cnt[q] += cnt[q - 1];
-        for (int r = w0; r < w1; ++r) perm[w0 + cnt[maxlen - rlen(r)]++] = r;
-      }
-      ident = false;
-    }
-  }
-  if (!ident) {
+  // Rows by decreasing length inside each window of SELL_SIGMA rows (ties in
+  // row order), for FP64 storage only and only where the natural order fills
+  // the slices poorly: FP64 instructions cost the same with idle lanes, while
+  // the bandwidth-bound FP32/bf16 products lose more to the scattered row
+  // order than they gain.
+  DBuf<int> hsl;
+  DBuf<unsigned long long> tot;
+  AMG_TRY(hsl.alloc(M.ns));
+  AMG_TRY(tot.alloc(1));
+  unsigned long long slots = 0;
+  auto heights = [&](const int *prow) -> int {
+    AMG_CU(cudaMemsetAsync(tot.p, 0, sizeof(unsigned long long), s));
+    if (M.ns) AMG_KCOUNT k_slice_h<<<nblk(32L * M.ns, 256), 256, 0, s>>>(A.nr, M.ns, A.rowptr.p, prow, hsl.p, tot.p);
+    AMG_LAUNCH_CHECK();
+    AMG_CU(cudaMemcpyAsync(&slots, tot.p, sizeof slots, cudaMemcpyDeviceToHost, s));
+    AMG_CU(cudaStreamSynchronize(s));
+    return AMG_OK;
+  };
+  AMG_TRY(heights(nullptr));
+  M.prow.release();
+  if (f64 && !f32 && !b16 && A.nr > 0 && slots > 0 && (double)A.nnzb < 0.9 * (double)slots) {
     AMG_TRY(M.prow.alloc(A.nr));
-    AMG_CU(cudaMemcpyAsync(M.prow.p, perm.data(), A.nr * sizeof(int), cudaMemcpyHostToDevice, s));
-  } else {
-    M.prow.release();
+    AMG_KCOUNT k_sell_perm<<<nblk(A.nr, SELL_SIGMA), SELL_SIGMA, 0, s>>>(A.nr, A.rowptr.p, M.prow.p);
+    AMG_TRY(heights(M.prow.p));
   }
-  std::vector<int> hs(M.ns + 1, 0);
-  long tot = 0;
-  for (int sl = 0; sl < M.ns; ++sl) {
-    int mx = 0;
-    const int r1 = std::min(A.nr, 32 * sl + 32);
-    for (int r = 32 * sl; r < r1; ++r) mx = std::max(mx, rlen(perm[r]));
-    hs[sl] = (int)tot;
-    tot += 32L * mx;
-  }
-  if (tot > 0x7fffffffL) {
-    set_error("matrix too large for 32-bit slot offsets (%ld slots)", tot);
+  if (slots > 0x7fffffffULL) {
+    set_error("matrix too large for 32-bit slot offsets (%llu slots)", slots);
     return AMG_ERR_ARG;
   }
-  hs[M.ns] = (int)tot;
-  M.nslot = tot;
+  M.nslot = (long)slots;
   AMG_TRY(M.slp.alloc(M.ns + 1));
-  AMG_CU(cudaMemcpyAsync(M.slp.p, hs.data(), (M.ns + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-  AMG_TRY(M.scol.alloc(tot));
+  AMG_TRY(dev_scan(M.ns, hsl.p, 0, M.slp.p, s));
+  const long tot_slots = M.nslot;
+  AMG_TRY(M.scol.alloc(tot_slots));
   M.map = M.map64 = rule_map(M);
   M.wps_rule = rule_wps(M);
   if (M.wps_rule > 1) {  // partial sums of the one-warp-CTA mappings
@@ -709,7 +724,7 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
     M.wpart.release();
     M.wtick.release();
   }
-  const long n9 = (long)A.b * A.b * tot;
+  const long n9 = (long)A.b * A.b * tot_slots;
   int *cols = M.scol.p;
   if (f64) {
     AMG_TRY(M.v64.alloc(n9));
