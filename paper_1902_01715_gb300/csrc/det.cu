@@ -18,6 +18,7 @@
 //    by xor-exchange steps 16, 8, 4, 2, 1; one level up, lane l sums chunk
 //    sums l, l+32, ... ascending and the same exchange steps give the total.
 #include <cfloat>
+#include <cstdlib>
 
 #include "amg_internal.h"
 
@@ -457,7 +458,7 @@ int mgs(int n, int t, double *V, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- FSAI
-// Warp-cooperative aFSAI rows (FS_NG node rows per warp, below).  The
+// Warp-cooperative aFSAI rows (NG node rows per warp, below).  The
 // arithmetic of each scalar follows the plain sequential definition:
 //  * Cholesky of A[Q,Q] entry (i,j): A_ij - sum_{k<j} L_ik L_jk (k ascending),
 //    then sqrt / division (the right-looking update subtracts the same
@@ -495,15 +496,16 @@ __device__ __forceinline__ const double *find_blk(const int *rp, const int *col,
   return nullptr;
 }
 
-// Lockstep slots.  Each warp works on FS_NG node rows at once, FS_GL lanes
+// Lockstep slots.  Each warp works on NG node rows at once, 32 / NG lanes
 // per row ("slot"); every loop that contains a warp-wide step runs to the
 // warp's largest bound with the per-slot work predicated, so the FP64
 // instructions of the sequential parts (square roots and divisions of the
-// Cholesky factor and of the substitutions) serve FS_NG rows each.  FP64 issue
+// Cholesky factor and of the substitutions) serve NG rows each.  FP64 issue
 // slots are the scarce resource of this GPU: a warp instruction costs the
-// same with one lane active as with 32.
-constexpr int FS_NG = 4;
-constexpr int FS_GL = 32 / FS_NG;
+// same with one lane active as with 32.  Large levels take NG = 4; small
+// ones fewer rows per warp (more lanes per row), so that their few rows
+// still reach every SM's FP64 pipes.  Every scalar gets the same operations
+// in the same order whatever NG: lanes only share out independent entries.
 
 __device__ __forceinline__ int warp_max(int v) {
   for (int off = 16; off >= 1; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
@@ -531,9 +533,10 @@ __device__ __forceinline__ void tri_decode(int idx, int &rr, int &kk) {
 // and ent_c = A[BI+c, Q_c].  Column j of the factor is scaled by
 // rho_j = 1 / L_jj, which the diagonal then holds for the substitutions (a
 // product per unknown instead of a division).
-template <int B>
+template <int B, int NG>
 __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, int np, int r0, double *M, double *gh,
                                double *rhs, double *ent, double *psi, int g, int gl) {
+  constexpr int GL = 32 / NG;
   // Rows [0, r0) of the factor in M (stride mmax) are kept from the previous
   // solve of this row: the pattern only grew at its end, and entry (r, k) of
   // a Cholesky factor depends only on the leading (r+1) x (r+1) block.  Only
@@ -542,7 +545,7 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
   const int m2 = act ? B * np + (B - 1) : 0, mm = K.mmax, nn = np + 1;
   const int p0 = r0 / B;  // first node whose rows are new
   const int npairs = act ? nn * (nn + 1) / 2 : 0;
-  for (int idx = p0 * (p0 + 1) / 2 + gl; idx < npairs; idx += FS_GL) {
+  for (int idx = p0 * (p0 + 1) / 2 + gl; idx < npairs; idx += GL) {
     int p, q;
     tri_decode(idx, p, q);
     const double *b = find_blk<B>(K.Arp, K.Acol, K.Aval, p < np ? pat[p] : I, q < np ? pat[q] : I);
@@ -555,7 +558,7 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       }
     }
   }
-  for (int idx = gl; idx < (act ? nn : 0); idx += FS_GL) {
+  for (int idx = gl; idx < (act ? nn : 0); idx += GL) {
     const int Np = idx < np ? pat[idx] : I;
     const double *bc = find_blk<B>(K.Arp, K.Acol, K.Aval, Np, I);
     const double *br = find_blk<B>(K.Arp, K.Acol, K.Aval, I, Np);
@@ -594,13 +597,13 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       __syncwarp();
       const int rb = max(j + 1, r0);  // first row this column updates
       if (on && !bad) {
-        for (int r = rb + gl; r < m2; r += FS_GL) M[r * mm + j] = M[r * mm + j] * rho;
+        for (int r = rb + gl; r < m2; r += GL) M[r * mm + j] = M[r * mm + j] * rho;
         if (gl == 0 && !kept) M[j * mm + j] = rho;  // the diagonal holds 1 / L_jj
       }
       __syncwarp();
       if (on && !bad) {  // the panel's later columns, rows max(k, r0)..m2-1
         const int pk = j1 - j - 1;
-        for (int idx = gl; idx < pk * (m2 - rb); idx += FS_GL) {
+        for (int idx = gl; idx < pk * (m2 - rb); idx += GL) {
           const int k = j + 1 + idx % pk, r = rb + idx / pk;
           if (r >= k) M[r * mm + k] = fma(-M[r * mm + j], M[k * mm + j], M[r * mm + k]);
         }
@@ -610,7 +613,7 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
     if (!bad && j1 < m2 && j0 < m2) {  // trailing rows max(j1, r0).. from column j1
       const int w = m2 - j1, nt = w * (w + 1) / 2;
       const int rb = max(r0, j1) - j1, t0 = rb * (rb + 1) / 2;
-      for (int idx = t0 + gl; idx < nt; idx += FS_GL) {
+      for (int idx = t0 + gl; idx < nt; idx += GL) {
         int rr, kk;
         tri_decode(idx, rr, kk);
         const int r = j1 + rr, k = j1 + kk;
@@ -633,14 +636,14 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       if (ok && gl < B && k < B * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] * M[k * mm + k];
       __syncwarp();
       if (ok)
-        for (int idx = gl; idx < B * (k1 - k - 1); idx += FS_GL) {
+        for (int idx = gl; idx < B * (k1 - k - 1); idx += GL) {
           const int c = idx / (k1 - k - 1), r = k + 1 + idx % (k1 - k - 1);
           if (r < B * np + c) rhs[c * mm + r] = fma(-M[r * mm + k], rhs[c * mm + k], rhs[c * mm + r]);
         }
       __syncwarp();
     }
     if (ok && k1 < m2)
-      for (int idx = gl; idx < B * (m2 - k1); idx += FS_GL) {
+      for (int idx = gl; idx < B * (m2 - k1); idx += GL) {
         const int c = idx / (m2 - k1), r = k1 + idx % (m2 - k1);
         if (r < B * np + c) {
           double a = rhs[c * mm + r];
@@ -659,14 +662,14 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       if (ok && gl < B && k < B * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] * M[k * mm + k];
       __syncwarp();
       if (ok && k < m2)
-        for (int idx = gl; idx < B * (k - k0); idx += FS_GL) {
+        for (int idx = gl; idx < B * (k - k0); idx += GL) {
           const int c = idx / (k - k0), r = k0 + idx % (k - k0);
           if (k < B * np + c) rhs[c * mm + r] = fma(-M[k * mm + r], gh[c * mm + k], rhs[c * mm + r]);
         }
       __syncwarp();
     }
     if (ok)
-      for (int idx = gl; idx < B * k0; idx += FS_GL) {
+      for (int idx = gl; idx < B * k0; idx += GL) {
         const int c = idx / k0, r = idx % k0;
         double a = rhs[c * mm + r];
         for (int k = min(k1, B * np + c) - 1; k >= k0; --k) a = fma(-M[k * mm + r], gh[c * mm + k], a);
@@ -683,7 +686,7 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
     for (int a = 0; a < B * np + c; ++a) sv = fma(ent[c * mm + a], gh[c * mm + a], sv);
   }
   double ps[B];
-  for (int c = 0; c < B; ++c) ps[c] = __shfl_sync(0xffffffffu, sv, g * FS_GL + c);
+  for (int c = 0; c < B; ++c) ps[c] = __shfl_sync(0xffffffffu, sv, g * GL + c);
   __syncwarp();
   if (!act) return AMG_OK;
   if (bad) return AMG_ERR_NOT_SPD;
@@ -723,12 +726,14 @@ __device__ __forceinline__ bool set_insert(unsigned long long *tab, int cap, uns
   return false;
 }
 
-template <int B>
+template <int B, int NG>
 __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
-  const int lane = threadIdx.x & 31, g = lane / FS_GL, gl = lane % FS_GL;
+  constexpr int GL = 32 / NG;
+  const unsigned smask = GL == 32 ? 0xffffffffu : (((1u << (GL & 31)) - 1u) << ((threadIdx.x & 31) / GL * GL));
+  const int lane = threadIdx.x & 31, g = lane / GL, gl = lane % GL;
   const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-  const long slot = gw * FS_NG + g, nslots = nw * FS_NG;
+  const long slot = gw * NG + g, nslots = nw * NG;
   const int mm = K.mmax;
   double *M = K.dscr + slot * K.dper;
   double *gh = M + (size_t)mm * mm;
@@ -754,10 +759,10 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
           ++np;
         }
     }
-    np = __shfl_sync(0xffffffffu, np, g * FS_GL);
+    np = __shfl_sync(0xffffffffu, np, g * GL);
     __syncwarp();
     double psi[3] = {0.0, 0.0, 0.0}, psi_old[3];
-    int rc = fsai_solve_rows<B>(K, have, I, pat, np, 0, M, gh, rhs, ent, psi, g, gl);
+    int rc = fsai_solve_rows<B, NG>(K, have, I, pat, np, 0, M, gh, rhs, ent, psi, g, gl);
     bool active = have && rc == 0;
     for (int step = 0; step < K.ksteps; ++step) {
       if (active && np >= K.maxg) active = false;
@@ -771,7 +776,7 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
         for (int run = 0; run <= np; ++run) {
           const int Kn = run < np ? pat[run] : I;
           const int b0 = K.Arp[Kn], len = K.Arp[Kn + 1] - b0;
-          for (int e = gl; e < len; e += FS_GL) {
+          for (int e = gl; e < len; e += GL) {
             const int J = K.Acol[b0 + e];
             if (J < I && !in_sorted(spat, np, J) && set_insert(tab, K.hcap, stamp, J))
               cand[atomicAdd(ccount, 1)] = J;
@@ -782,7 +787,7 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
       // gradient entries g[c][d] = (A gt_c)_{BJ+d}: pattern dofs in
       // ascending order, then the dofs BI+e < BI+c, then the unit entry;
       // node score = sum over c, d of g^2
-      for (int t = gl; t < nc; t += FS_GL) {
+      for (int t = gl; t < nc; t += GL) {
         const int J = cand[t];
         double gg[B][B];
         for (int c = 0; c < B; ++c)
@@ -821,11 +826,11 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
         long long bs = -1;
         int bj = 0x7fffffff, bt = -1;
         if (more && p < want)
-          for (int t = gl; t < nc; t += FS_GL) {
+          for (int t = gl; t < nc; t += GL) {
             const long long sc = __double_as_longlong(score[t]);
             if (sc > 0 && (sc > bs || (sc == bs && cand[t] < bj))) { bs = sc; bj = cand[t]; bt = t; }
           }
-        for (int off = FS_GL / 2; off >= 1; off >>= 1) {
+        for (int off = GL / 2; off >= 1; off >>= 1) {
           const long long os = __shfl_xor_sync(0xffffffffu, bs, off);
           const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
           const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
@@ -857,7 +862,7 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
       if (active) np += got;
       __syncwarp();
       for (int c = 0; c < B; ++c) psi_old[c] = psi[c];
-      const int rc2 = fsai_solve_rows<B>(K, active, I, pat, np, B * np_old, M, gh, rhs, ent, psi, g, gl);
+      const int rc2 = fsai_solve_rows<B, NG>(K, active, I, pat, np, B * np_old, M, gh, rhs, ent, psi, g, gl);
       if (active) {
         if (rc2) {
           rc = rc2;
@@ -877,18 +882,18 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
     }
     // G row in ascending node order: ord[j] = position in pat of spat[j]
     int *ord = cand;  // free once the steps are done
-    for (int j = gl; j < np; j += FS_GL) {
+    for (int j = gl; j < np; j += GL) {
       const int v = spat[j];
       for (int q = 0; q < np; ++q)
         if (pat[q] == v) ord[j] = q;
     }
-    __syncwarp(0xffu << (g * FS_GL));  // only this slot's lanes are here
+    __syncwarp(smask);  // only this slot's lanes are here
     if (gl == 0) K.out_np[I] = np;
-    for (int j = gl; j < np; j += FS_GL) K.out_pat[(size_t)I * K.maxg + j] = spat[j];
+    for (int j = gl; j < np; j += GL) K.out_pat[(size_t)I * K.maxg + j] = spat[j];
     double rs[B];  // 1 / sqrt(psi_c): one division per row, products per entry
     for (int c = 0; c < B; ++c) rs[c] = 1.0 / sqrt(psi[c]);
     double *ov = K.out_val + (size_t)I * (K.maxg + 1) * B * B;
-    for (int idx = gl; idx < (np + 1) * B * B; idx += FS_GL) {
+    for (int idx = gl; idx < (np + 1) * B * B; idx += GL) {
       const int j = idx / (B * B), c = (idx % (B * B)) / B, d = idx % B;
       double gv;
       if (j < np) gv = gh[c * mm + B * ord[j] + d];
@@ -935,11 +940,25 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // rows per warp: 4 while that still gives 32 warps per SM, else 2, else 1
+  // (measured on the beam's levels: 139k and 30k rows fastest with 4, 6.2k
+  // and 1.3k rows with 1)
+  int ng = 4;
+  while (ng > 1 && (long)A.nr / ng < 32L * nsm) ng /= 2;
+  if (const char *e = getenv("AMG_FSAI_NG")) {
+    const int v = atoi(e);
+    if (v == 1 || v == 2 || v == 4) ng = v;
+  }
+  const void *fn = nullptr;
+  if (A.b == 1) fn = ng == 4 ? (const void *)k_fsai<1, 4> : ng == 2 ? (const void *)k_fsai<1, 2> : (const void *)k_fsai<1, 1>;
+  else fn = ng == 4 ? (const void *)k_fsai<3, 4> : ng == 2 ? (const void *)k_fsai<3, 2> : (const void *)k_fsai<3, 1>;
   const int threads = 128;
-  long nblocks = (long)nsm * 5;  // 20 warps, 80 slots per SM (96 registers a thread allow 5 blocks)
-  const long need = ((long)A.nr + 4 * FS_NG - 1) / (4 * FS_NG);
+  int per_sm = 0;
+  AMG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0));
+  long nblocks = (long)nsm * (per_sm > 0 ? per_sm : 1);
+  const long need = ((long)A.nr + 4 * ng - 1) / (4 * ng);
   if (nblocks > need) nblocks = need > 0 ? need : 1;
-  const long nslots = nblocks * (threads / 32) * FS_NG;
+  const long nslots = nblocks * (threads / 32) * ng;
   DBuf<double> ds;
   DBuf<int> is;
   DBuf<unsigned long long> hs;
@@ -950,8 +969,9 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   K.dscr = ds.p;
   K.iscr = is.p;
   K.htab = hs.p;
-  if (A.b == 1) AMG_KCOUNT k_fsai<1><<<(int)nblocks, threads, 0, s>>>(K);
-  else AMG_KCOUNT k_fsai<3><<<(int)nblocks, threads, 0, s>>>(K);
+  void *args[] = {&K};
+  count_launches(1);
+  AMG_CU(cudaLaunchKernel(fn, dim3((unsigned)nblocks), dim3(threads), args, 0, s));
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
