@@ -130,7 +130,7 @@ struct Fin {
 };
 
 __device__ double line_min(double a, double b, double c, double d, double e, double f);
-__device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, double *lam, double *w, int lane);
+__device__ int gen_eig_cta(int t, const double *H, const double *M, double *U, double *lam, double *w, int tid);
 
 __device__ __forceinline__ double exchange32(double s) {
   for (int off = 16; off >= 1; off >>= 1) s = s + __shfl_xor_sync(0xffffffffu, s, off);
@@ -289,8 +289,8 @@ static int dot1(int n, const double *x, const double *y, double *out, DotCtx ctx
 }
 
 // Gram sums of the Ritz step, H[i][j] = Z_i . SZ_j and M[i][j] = Z_i . Z_j for
-// i <= j (each in the fixed dot order, mirrored to j < i); the last warp then
-// solves the pencil (H, M) for U and resets the quotient scalars f_i to 1.
+// i <= j (each in the fixed dot order, mirrored to j < i); k_ritz_eig then
+// solves the pencil (H, M) for U.
 __device__ __forceinline__ void pair_of(int d, int t, int &which, int &i, int &j) {
   const int npair = t * (t + 1) / 2;
   which = d / npair;
@@ -302,17 +302,13 @@ __device__ __forceinline__ void pair_of(int d, int t, int &which, int &i, int &j
 
 __global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restrict__ Z, const double *__restrict__ SZ,
                                              double *__restrict__ part, unsigned *ticket, int nchunks,
-                                             double *__restrict__ H, double *__restrict__ M, double *__restrict__ U,
-                                             double *__restrict__ lam, double *__restrict__ f,
-                                             int *__restrict__ status) {
-  // the last warp's working arrays (6 t^2 + t doubles, dynamic shared memory)
-  extern __shared__ double wk[];
+                                             double *__restrict__ H, double *__restrict__ M) {
   const int nd = t * (t + 1);
   const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
   const long total = nchunks > 0 ? (long)nchunks * nd : 1;
   if (w >= total) return;
-  const bool last = dot_warp(
+  dot_warp(
       w, n, nd, nchunks, part, ticket, lane,
       [&](int d, const double *&x, const double *&y) {
         int which, i, j;
@@ -327,16 +323,24 @@ __global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restr
         O[i * t + j] = v;
         O[j * t + i] = v;
       });
-  if (!last) return;
-  // the pencil was written by other warps: read it through L2 into shared memory
+}
+
+// The pencil (H, M) of the Gram kernel solved for U (and lam); the quotient
+// scalars f_i reset to 1.  One CTA of 64 threads.
+__global__ void __launch_bounds__(64) k_ritz_eig(int t, const double *__restrict__ H, const double *__restrict__ M,
+                                                 double *__restrict__ U, double *__restrict__ lam,
+                                                 double *__restrict__ f, int *__restrict__ status) {
+  extern __shared__ double wk[];  // 6 t^2 + t doubles
+  const int tid = threadIdx.x;
+  // the pencil was written by other CTAs: read it through L2 into shared memory
   double *Hs = wk + 4 * t * t + t, *Ms = Hs + t * t;
-  for (int q = lane; q < t * t; q += 32) {
+  for (int q = tid; q < t * t; q += 64) {
     Hs[q] = __ldcg(H + q);
     Ms[q] = __ldcg(M + q);
   }
-  __syncwarp();
-  const int bad = gen_eig_warp(t, Hs, Ms, U, lam, wk, lane);
-  if (lane == 0) {
+  __syncthreads();
+  const int bad = gen_eig_cta(t, Hs, Ms, U, lam, wk, tid);
+  if (tid == 0) {
     if (bad) atomicMin(status, AMG_ERR_NOT_SPD);
     for (int i = 0; i < t; ++i) f[i] = 1.0;
   }
@@ -418,23 +422,45 @@ __global__ void __launch_bounds__(32) k_mgs_step(int n, int t, int nchunks, doub
   const double r = i > 0 ? sc[i - 1] : 0.0;
   const double *vu = V + (size_t)(i > 0 ? i - 1 : 0) * n;  // v_{i-1}
   const double *vi = V + (size_t)i * n;
+  // the lane's entries in groups of MB: every load of a group is issued
+  // before any of its entries is formed (a lane reads and writes only its own
+  // entries, and the columns read are other than the ones written, except
+  // v_i = v_j and v_i = v_{j-1}, which take the values just formed)
+  const bool load_i = i != j && !(norm_prev && i == j - 1);
+  constexpr int MB = 8;
   double s = 0.0;
-  for (int k = base + lane; k < end; k += 32) {
-    double xp = 0.0;
-    if (norm_prev) {
-      xp = vp[k];
-      if (nr > 0.0) {
-        xp = xp * rn;
-        vp[k] = xp;
+  for (int k0 = base + lane; k0 < end; k0 += 32 * MB) {
+    double pv[MB], jv[MB], uv[MB], iv[MB];
+#pragma unroll
+    for (int u = 0; u < MB; ++u) {
+      const int k = k0 + 32 * u;
+      const bool in = k < end;
+      pv[u] = (in && norm_prev) ? vp[k] : 0.0;
+      jv[u] = in ? vj[k] : 0.0;
+      uv[u] = (in && i > 0) ? vu[k] : 0.0;
+      iv[u] = (in && load_i) ? vi[k] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < MB; ++u) {
+      const int k = k0 + 32 * u;
+      if (k < end) {
+        double xp = 0.0;
+        if (norm_prev) {
+          xp = pv[u];
+          if (nr > 0.0) {
+            xp = xp * rn;
+            vp[k] = xp;
+          }
+        }
+        double y = jv[u];
+        if (i > 0) {
+          y = fma(-r, uv[u], y);
+          vj[k] = y;
+        }
+        const double x = i == j ? y : (norm_prev && i == j - 1) ? xp : iv[u];
+        s = fma(x, y, s);
       }
     }
-    double y = vj[k];
-    if (i > 0) {
-      y = fma(-r, vu[k], y);
-      vj[k] = y;
-    }
-    const double x = i == j ? y : (norm_prev && i == j - 1) ? xp : vi[k];
-    s = fma(x, y, s);
   }
   s = exchange32(s);
   dot_finish(w, 1, nchunks, part, ticket, lane, s, [&](int, double v) { sc[i < j ? i : t] = v; });
@@ -729,6 +755,7 @@ __device__ __forceinline__ bool set_insert(unsigned long long *tab, int cap, uns
 template <int B, int NG>
 __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
   constexpr int GL = 32 / NG;
+  static_assert(GL >= B, "a slot needs a lane per dof row of a node");
   const unsigned smask = GL == 32 ? 0xffffffffu : (((1u << (GL & 31)) - 1u) << ((threadIdx.x & 31) / GL * GL));
   const int lane = threadIdx.x & 31, g = lane / GL, gl = lane % GL;
   const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -940,18 +967,23 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // rows per warp: 4 while that still gives 32 warps per SM, else 2, else 1
-  // (measured on the beam's levels: 139k and 30k rows fastest with 4, 6.2k
-  // and 1.3k rows with 1)
-  int ng = 4;
+  // rows per warp: 8 while that still gives 32 warps per SM, else 4, 2, 1
+  // (measured first aFSAI pass on the beam's levels: 139k rows 16.6 ms with
+  // 8, 18.2 with 4; 30k rows 7.9 with 8 or 4; 6.2k rows 2.6 with 1, 3.4 with
+  // 4; 1.3k rows 1.0 with 1, 3.2 with 4)
+  int ng = 8;
   while (ng > 1 && (long)A.nr / ng < 32L * nsm) ng /= 2;
   if (const char *e = getenv("AMG_FSAI_NG")) {
     const int v = atoi(e);
-    if (v == 1 || v == 2 || v == 4) ng = v;
+    if (v == 1 || v == 2 || v == 4 || v == 8) ng = v;
   }
   const void *fn = nullptr;
-  if (A.b == 1) fn = ng == 4 ? (const void *)k_fsai<1, 4> : ng == 2 ? (const void *)k_fsai<1, 2> : (const void *)k_fsai<1, 1>;
-  else fn = ng == 4 ? (const void *)k_fsai<3, 4> : ng == 2 ? (const void *)k_fsai<3, 2> : (const void *)k_fsai<3, 1>;
+  if (A.b == 1)
+    fn = ng == 8 ? (const void *)k_fsai<1, 8> : ng == 4 ? (const void *)k_fsai<1, 4>
+       : ng == 2 ? (const void *)k_fsai<1, 2> : (const void *)k_fsai<1, 1>;
+  else
+    fn = ng == 8 ? (const void *)k_fsai<3, 8> : ng == 4 ? (const void *)k_fsai<3, 4>
+       : ng == 2 ? (const void *)k_fsai<3, 2> : (const void *)k_fsai<3, 1>;
   const int threads = 128;
   int per_sm = 0;
   AMG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0));
@@ -1262,7 +1294,8 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z0, double *__restr
   for (int j = 0; j < t; ++j) Z[(size_t)j * n + k] = row[j];
 }
 
-// Generalised eigenproblem H U = M U diag(lam) of the Ritz step, by one warp:
+// Generalised eigenproblem H U = M U diag(lam) of the Ritz step, by one CTA of
+// two warps (the factorisation and the back-transform on warp 0):
 // M = L L^T (sub-diagonal entries scaled by 1 / L_jj, the triangular solves
 // multiply by the reciprocals Ri); C = L^{-1} (L^{-1} H)^T symmetrised as (C + C^T) * 0.5; Jacobi
 // sweeps in round-robin order (per round T/2 disjoint pairs from the circle
@@ -1274,14 +1307,24 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z0, double *__restr
 // entries (rows of a rotation, columns of a triangular solve); every entry is
 // computed by the same sequence of rounded operations as the sequential
 // definition.  Scratch w holds 4 t*t + t doubles; returns 1 if M is not SPD.
-__device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, double *lam, double *w, int lane) {
+__device__ int gen_eig_cta(int t, const double *H, const double *M, double *U, double *lam, double *w, int tid) {
+  const int lane = tid & 31, warp = tid >> 5;
+  __shared__ int sp[TMAXD / 2], sq[TMAXD / 2], sact[TMAXD / 2];
+  __shared__ double scs[TMAXD / 2], ssn[TMAXD / 2];
+  __shared__ int sbad;
   double *L = w, *W1 = w + t * t, *C = w + 2 * t * t, *Wv = w + 3 * t * t, *Ri = w + 4 * t * t;
+  if (tid == 0) sbad = 0;
+  __syncthreads();
+  if (warp == 0) {
   for (int i = lane; i < t * t; i += 32) L[i] = 0.0;
   __syncwarp();
   for (int j = 0; j < t; ++j) {
     double sj = M[j * t + j];
     for (int k = 0; k < j; ++k) sj = fma(-L[j * t + k], L[j * t + k], sj);
-    if (!(sj > 0.0)) return 1;
+    if (!(sj > 0.0)) {
+      if (lane == 0) sbad = 1;
+      break;
+    }
     const double d = sqrt(sj), rho = 1.0 / d;
     for (int i = j + 1 + lane; i < t; i += 32) {
       double u = M[i * t + j];
@@ -1294,6 +1337,8 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
     }
     __syncwarp();
   }
+  __syncwarp();
+  if (!sbad) {
   for (int j = lane; j < t; j += 32)
     for (int i = 0; i < t; ++i) {
       double sv = H[i * t + j];
@@ -1317,7 +1362,10 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
     }
   }
   for (int q = lane; q < t * t; q += 32) Wv[q] = (q / t == q % t) ? 1.0 : 0.0;
-  __syncwarp();
+  }  // not bad
+  }  // warp 0
+  __syncthreads();
+  if (sbad) return 1;
   for (int sweep = 0; sweep < 100; ++sweep) {
     double off = 0.0, dg = 0.0;
     for (int p = 0; p < t; ++p) {
@@ -1325,16 +1373,19 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
       for (int q = p + 1; q < t; ++q) off = fma(C[p * t + q], C[p * t + q], off);
     }
     if (!(off > 1e-32 * dg)) break;
-    // one sweep in round-robin order: lane i < T/2 owns pair i of the round
-    // (its rotation computed from the current C), then the column, row and
-    // W rotations of all pairs, then the pivots are zeroed
+    // one sweep in round-robin order: thread i < T/2 computes the rotation
+    // of pair i of the round from the current C; then warp 0 applies, per
+    // 2 x 2 block of C (rows of pair I, columns of pair J), the column
+    // rotation of pair J and then the row rotation of pair I (the operations
+    // of rotating all columns and then all rows), while warp 1 rotates the
+    // columns of W; then the pivots are zeroed
     const int T = t + (t & 1), hp = T / 2;
     for (int r = 0; r < T - 1; ++r) {
-      int p = 0, q = 0, act = 0;
-      double c = 1.0, sn = 0.0;
-      if (lane < hp) {
-        const int a = (lane == 0) ? 0 : 1 + (lane - 1 + r) % (T - 1);
-        const int j2 = T - 1 - lane;
+      if (tid < hp) {
+        int p = 0, q = 0, act = 0;
+        double c = 1.0, sn = 0.0;
+        const int a = (tid == 0) ? 0 : 1 + (tid - 1 + r) % (T - 1);
+        const int j2 = T - 1 - tid;
         const int b2 = (j2 == 0) ? 0 : 1 + (j2 - 1 + r) % (T - 1);
         p = a < b2 ? a : b2;
         q = a < b2 ? b2 : a;
@@ -1351,34 +1402,67 @@ __device__ int gen_eig_warp(int t, const double *H, const double *M, double *U, 
             act = 1;
           }
         }
+        sp[tid] = p;
+        sq[tid] = q;
+        sact[tid] = act;
+        scs[tid] = c;
+        ssn[tid] = sn;
       }
-      __syncwarp();
-      for (int phase = 0; phase < 3; ++phase) {
-        double *X = phase == 2 ? Wv : C;
-        for (int base = 0; base < hp * t; base += 32) {
-          const int idx = base + lane;
-          const int i = idx < hp * t ? idx / t : 0, k = idx - i * t;
-          const int pi = __shfl_sync(0xffffffffu, p, i), qi = __shfl_sync(0xffffffffu, q, i);
-          const int ai = __shfl_sync(0xffffffffu, act, i);
-          const double ci = __shfl_sync(0xffffffffu, c, i), si = __shfl_sync(0xffffffffu, sn, i);
-          if (idx < hp * t && ai) {
-            // columns p, q (phases 0 and 2) or rows p, q (phase 1), entry k
-            const int ip = phase == 1 ? pi * t + k : k * t + pi;
-            const int iq = phase == 1 ? qi * t + k : k * t + qi;
-            const double xp = X[ip], xq = X[iq];
-            X[ip] = fma(ci, xp, -(si * xq));
-            X[iq] = fma(si, xp, ci * xq);
+      __syncthreads();
+      if (warp == 0) {
+        for (int b = lane; b < hp * hp; b += 32) {
+          const int I = b / hp, J = b % hp;
+          const int pI = sp[I], qI = sq[I], pJ = sp[J], qJ = sq[J];
+          const bool rI = sact[I] != 0, cJ = sact[J] != 0;
+          if (!rI && !cJ) continue;
+          // entries (row, col) of the block that exist (q < t for active pairs;
+          // an inactive pair may name the index t when t is odd)
+          const bool hasq_r = qI < t, hasq_c = qJ < t;
+          double x00 = C[pI * t + pJ], x01 = hasq_c ? C[pI * t + qJ] : 0.0;
+          double x10 = hasq_r ? C[qI * t + pJ] : 0.0, x11 = (hasq_r && hasq_c) ? C[qI * t + qJ] : 0.0;
+          if (cJ) {  // columns pJ, qJ
+            const double c = scs[J], sn = ssn[J];
+            const double y00 = fma(c, x00, -(sn * x01)), y01 = fma(sn, x00, c * x01);
+            const double y10 = fma(c, x10, -(sn * x11)), y11 = fma(sn, x10, c * x11);
+            x00 = y00;
+            x01 = y01;
+            x10 = y10;
+            x11 = y11;
           }
+          if (rI) {  // rows pI, qI
+            const double c = scs[I], sn = ssn[I];
+            const double y00 = fma(c, x00, -(sn * x10)), y10 = fma(sn, x00, c * x10);
+            const double y01 = fma(c, x01, -(sn * x11)), y11 = fma(sn, x01, c * x11);
+            x00 = y00;
+            x10 = y10;
+            x01 = y01;
+            x11 = y11;
+          }
+          C[pI * t + pJ] = x00;
+          if (hasq_c) C[pI * t + qJ] = x01;
+          if (hasq_r) C[qI * t + pJ] = x10;
+          if (hasq_r && hasq_c) C[qI * t + qJ] = x11;
         }
-        __syncwarp();
+      } else {
+        for (int idx = lane; idx < hp * t; idx += 32) {  // W: columns p_i, q_i, row k
+          const int i = idx / t, k = idx - i * t;
+          if (!sact[i]) continue;
+          const double c = scs[i], sn = ssn[i];
+          const int ip = k * t + sp[i], iq = k * t + sq[i];
+          const double xp = Wv[ip], xq = Wv[iq];
+          Wv[ip] = fma(c, xp, -(sn * xq));
+          Wv[iq] = fma(sn, xp, c * xq);
+        }
       }
-      if (act) {
-        C[p * t + q] = 0.0;
-        C[q * t + p] = 0.0;
+      __syncthreads();
+      if (tid < hp && sact[tid]) {
+        C[sp[tid] * t + sq[tid]] = 0.0;
+        C[sq[tid] * t + sp[tid]] = 0.0;
       }
-      __syncwarp();
+      __syncthreads();
     }
   }
+  if (warp != 0) return 0;
   int order[TMAXD];
   for (int i = 0; i < t; ++i) order[i] = i;
   for (int i = 0; i < t; ++i) {
@@ -1505,8 +1589,9 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   auto iteration = [&](bool ritz) -> int {
     if (ritz) {
       const long warps = nchunks > 0 ? (long)nchunks * t * (t + 1) : 1;
-      AMG_KCOUNT k_gram<<<(int)warps, 32, (6 * t * t + t) * sizeof(double), s>>>(
-          n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p, U.p, lam.p, cs.p + C_F * t, status);
+      AMG_KCOUNT k_gram<<<(int)warps, 32, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p);
+      AMG_KCOUNT k_ritz_eig<<<1, 64, (6 * t * t + t) * sizeof(double), s>>>(t, H.p, Mg.p, U.p, lam.p, cs.p + C_F * t,
+                                                                           status);
       AMG_KCOUNT k_rotate<<<dim3(nblk(n, 256), 2), 256, 0, s>>>(n, t, Z.p, SZ.p, U.p);  // Z U, (S Z) U
       AMG_LAUNCH_CHECK();
     }

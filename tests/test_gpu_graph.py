@@ -85,3 +85,17 @@ def test_candidate_distance_bit_exact(A, orc, name, d_p):
     d = gpu_problem(A, p)
     S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], d_p=d_p)
     compare_hierarchies(S, H)
+
+
+@pytest.mark.parametrize("ng", ["1", "2", "4", "8"])
+def test_fsai_rows_per_warp_same_bits(A, orc, ng, monkeypatch):
+    """The aFSAI kernel shares a warp among 1, 2, 4 or 8 node rows (chosen by
+    level size; AMG_FSAI_NG pins it): the lanes only share out independent
+    entries, so every choice gives the oracle's hierarchy bit for bit."""
+    monkeypatch.setenv("AMG_FSAI_NG", ng)
+    p = SMALL["beam"]()
+    K, V0, f, nm = oracle_problem(orc, p)
+    H = orc.Hierarchy(K, V0, orc.default_params(3))
+    d = gpu_problem(A, p)
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
+    compare_hierarchies(S, H)
