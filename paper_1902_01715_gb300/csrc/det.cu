@@ -326,15 +326,15 @@ __global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restr
 }
 
 // The pencil (H, M) of the Gram kernel solved for U (and lam); the quotient
-// scalars f_i reset to 1.  One CTA of 64 threads.
-__global__ void __launch_bounds__(64) k_ritz_eig(int t, const double *__restrict__ H, const double *__restrict__ M,
+// scalars f_i reset to 1.  One CTA of 4 warps.
+__global__ void __launch_bounds__(128) k_ritz_eig(int t, const double *__restrict__ H, const double *__restrict__ M,
                                                  double *__restrict__ U, double *__restrict__ lam,
                                                  double *__restrict__ f, int *__restrict__ status) {
   extern __shared__ double wk[];  // 6 t^2 + t doubles
   const int tid = threadIdx.x;
   // the pencil was written by other CTAs: read it through L2 into shared memory
   double *Hs = wk + 4 * t * t + t, *Ms = Hs + t * t;
-  for (int q = tid; q < t * t; q += 64) {
+  for (int q = tid; q < t * t; q += 128) {
     Hs[q] = __ldcg(H + q);
     Ms[q] = __ldcg(M + q);
   }
@@ -498,6 +498,7 @@ struct FsaiK {
   int n;
   const int *Arp, *Acol;
   const double *Aval;
+  const int *Atr;  // per stored block (i, j): the index of block (j, i)
   const int *Gsrp, *Gscol;
   int ksteps, rho, maxg;
   double eps;
@@ -733,23 +734,51 @@ __device__ __forceinline__ int in_sorted(const int *a, int n, int v) {
   return 0;
 }
 
-// Insert J into a slot's open-addressing set for one (node, step); entries of
-// earlier uses (another stamp) count as free.  Returns true when J is new.
-// The table holds at least twice as many entries as the step can insert.
-__device__ __forceinline__ bool set_insert(unsigned long long *tab, int cap, unsigned stamp, int J) {
+// Find or insert J in a slot's open-addressing set for one (node, step);
+// entries of earlier uses (another stamp) count as free.  Returns J's table
+// position (and whether it was new), -1 if the table had no room (it holds
+// at least twice as many entries as the step can insert).
+__device__ __forceinline__ int set_find_insert(unsigned long long *tab, int cap, unsigned stamp, int J, bool &isnew) {
   const unsigned long long key = ((unsigned long long)stamp << 32) | (unsigned)J;
   unsigned h = ((unsigned)J * 2654435761u) & (unsigned)(cap - 1);
+  isnew = false;
   for (int probe = 0; probe < cap; ++probe) {
     unsigned long long cur = ((volatile unsigned long long *)tab)[h];
     for (int tries = 0; (unsigned)(cur >> 32) != stamp && tries < 64; ++tries) {
       const unsigned long long prev = atomicCAS(&tab[h], cur, key);
-      if (prev == cur) return true;
+      if (prev == cur) {
+        isnew = true;
+        return (int)h;
+      }
       cur = prev;
     }
-    if ((unsigned)(cur >> 32) == stamp && (unsigned)cur == (unsigned)J) return false;
+    if ((unsigned)(cur >> 32) == stamp && (unsigned)cur == (unsigned)J) return (int)h;
     h = (h + 1) & (unsigned)(cap - 1);
   }
-  return false;
+  return -1;
+}
+
+// Index of the transposed block of every stored block (one warp per row):
+// tr[k] = position of block (j, i) for block k = (i, j); a block without a
+// transposed partner sets *asym.
+__global__ void k_block_transpose_index(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                        int *__restrict__ tr, int *__restrict__ asym) {
+  const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= n) return;
+  for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+    const int j = col[k];
+    int lo = rp[j], hi = rp[j + 1] - 1, at = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1, c = col[mid];
+      if (c == i) {
+        at = mid;
+        break;
+      }
+      if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    tr[k] = at;
+    if (at < 0) atomicExch(asym, 1);
+  }
 }
 
 template <int B, int NG>
@@ -767,10 +796,13 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
   double *rhs = gh + B * mm;
   double *ent = rhs + B * mm;
   double *score = ent + B * mm;
+  double *acc = score + K.candcap;  // per candidate: its B x B gradient sums
   int *pat = K.iscr + slot * K.iper;  // pattern in the order the nodes were added
   int *cand = pat + K.maxg + 1;
   int *ccount = cand + K.candcap;
   int *spat = ccount + 1;  // the same nodes in ascending order (membership tests)
+  int *bidx = spat + K.maxg + 1;  // per candidate: its block (J, I), or -1
+  int *hidx = bidx + K.candcap;   // per table position: the candidate index
   unsigned long long *tab = K.htab + slot * K.hcap;
   const long nrounds = (K.n + nslots - 1) / nslots;
   for (long rd = 0; rd < nrounds; ++rd) {
@@ -799,40 +831,60 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
       const unsigned stamp = (unsigned)(rd * (K.ksteps + 1) + step + 1);
       if (gl == 0) *ccount = 0;
       __syncwarp();
+      // gradient entries g[c][d] = (A gt_c)_{BJ+d}: the pattern dofs in the
+      // pattern's order, then the dofs BI+e < BI+c, then the unit entry; node
+      // score = sum over c, d of g^2.  The rows of the pattern nodes are
+      // walked in the pattern's order (lanes over a row's entries, which name
+      // distinct nodes), so every candidate's sums take their terms in that
+      // order; the row of I then records each candidate's block (J, I).  The
+      // block (J, K) of entry (K, J) comes from the transposed-block index.
       if (active)
         for (int run = 0; run <= np; ++run) {
           const int Kn = run < np ? pat[run] : I;
           const int b0 = K.Arp[Kn], len = K.Arp[Kn + 1] - b0;
           for (int e = gl; e < len; e += GL) {
             const int J = K.Acol[b0 + e];
-            if (J < I && !in_sorted(spat, np, J) && set_insert(tab, K.hcap, stamp, J))
-              cand[atomicAdd(ccount, 1)] = J;
+            if (J >= I || in_sorted(spat, np, J)) continue;
+            bool isnew;
+            const int h = set_find_insert(tab, K.hcap, stamp, J, isnew);
+            if (h < 0) continue;
+            int idx;
+            if (isnew) {
+              idx = atomicAdd(ccount, 1);
+              cand[idx] = J;
+              hidx[h] = idx;
+              bidx[idx] = -1;
+              for (int q = 0; q < B * B; ++q) acc[(size_t)idx * B * B + q] = 0.0;
+            } else {
+              idx = hidx[h];
+            }
+            const int kt = K.Atr[b0 + e];
+            if (run == np) {
+              bidx[idx] = kt;
+            } else if (kt >= 0) {
+              const double *blk = K.Aval + (size_t)kt * B * B;
+              double *a = acc + (size_t)idx * B * B;
+              for (int c = 0; c < B; ++c)
+                for (int d = 0; d < B; ++d) {
+                  double g = a[c * B + d];
+                  for (int q = 0; q < B; ++q) g = fma(blk[d * B + q], gh[c * mm + B * run + q], g);
+                  a[c * B + d] = g;
+                }
+            }
           }
+          __syncwarp(smask);  // a later row may name the same candidates
         }
       __syncwarp();
       const int nc = active ? *(volatile int *)ccount : 0;
-      // gradient entries g[c][d] = (A gt_c)_{BJ+d}: pattern dofs in
-      // ascending order, then the dofs BI+e < BI+c, then the unit entry;
-      // node score = sum over c, d of g^2
       for (int t = gl; t < nc; t += GL) {
-        const int J = cand[t];
-        double gg[B][B];
-        for (int c = 0; c < B; ++c)
-          for (int d = 0; d < B; ++d) gg[c][d] = 0.0;
-        for (int j = 0; j < np; ++j) {
-          const double *blk = find_blk<B>(K.Arp, K.Acol, K.Aval, J, pat[j]);
-          if (blk)
-            for (int c = 0; c < B; ++c)
-              for (int d = 0; d < B; ++d)
-                for (int e = 0; e < B; ++e) gg[c][d] = fma(blk[d * B + e], gh[c * mm + B * j + e], gg[c][d]);
-        }
-        const double *bI = find_blk<B>(K.Arp, K.Acol, K.Aval, J, I);
+        const double *a = acc + (size_t)t * B * B;
+        const double *bI = bidx[t] >= 0 ? K.Aval + (size_t)bidx[t] * B * B : nullptr;
         double sc = 0.0;
         for (int c = 0; c < B; ++c)
           for (int d = 0; d < B; ++d) {
-            double gv = gg[c][d];
+            double gv = a[c * B + d];
             if (bI) {
-              for (int e = 0; e < c; ++e) gv = fma(bI[d * B + e], gh[c * mm + B * np + e], gv);
+              for (int q = 0; q < c; ++q) gv = fma(bI[d * B + q], gh[c * mm + B * np + q], gv);
               gv = gv + bI[d * B + c] * 1.0;
             }
             sc = fma(gv, gv, sc);
@@ -962,16 +1014,35 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   K.candcap = ((int)npcap + 1) * maxdeg;
   K.hcap = 64;
   while (K.hcap < 2 * K.candcap) K.hcap *= 2;
-  K.dper = (long)K.mmax * K.mmax + 3L * A.b * K.mmax + K.candcap;
-  K.iper = (maxg + 1) + K.candcap + 1 + (maxg + 1);
+  K.dper = (long)K.mmax * K.mmax + 3L * A.b * K.mmax + K.candcap + (long)K.candcap * A.b * A.b;
+  K.iper = (maxg + 1) + K.candcap + 1 + (maxg + 1) + K.candcap + K.hcap;
+  // transposed-block index of A (the level matrices have symmetric patterns;
+  // a pattern that is not is refused)
+  DBuf<int> atr, asym;
+  AMG_TRY(atr.alloc(A.nnzb));
+  AMG_TRY(asym.alloc(1));
+  AMG_TRY(asym.zero(s));
+  if (A.nr) AMG_KCOUNT k_block_transpose_index<<<(int)((32L * A.nr + 255) / 256), 256, 0, s>>>(A.nr, A.rowptr.p,
+                                                                                          A.col.p, atr.p, asym.p);
+  AMG_LAUNCH_CHECK();
+  {
+    int ha = 0;
+    AMG_CU(cudaMemcpyAsync(&ha, asym.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CU(cudaStreamSynchronize(s));
+    if (ha) {
+      set_error("aFSAI: the matrix pattern is not symmetric");
+      return AMG_ERR_ARG;
+    }
+  }
+  K.Atr = atr.p;
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // rows per warp: 8 while that still gives 32 warps per SM, else 4, 2, 1
-  // (measured first aFSAI pass on the beam's levels: 139k rows 16.6 ms with
-  // 8, 18.2 with 4; 30k rows 7.9 with 8 or 4; 6.2k rows 2.6 with 1, 3.4 with
-  // 4; 1.3k rows 1.0 with 1, 3.2 with 4)
-  int ng = 8;
+  // rows per warp: 4 while that still gives 32 warps per SM, else 2, else 1
+  // (measured first aFSAI pass on the beam's levels: 139k rows 15.5 ms with
+  // 4, 16.2 with 8; 30k rows 5.3 with 4, 6.1 with 8; 6.2k rows 1.3 with 1,
+  // 2.7 with 4; 1.3k rows 0.6 with 1, 2.4 with 4)
+  int ng = 4;
   while (ng > 1 && (long)A.nr / ng < 32L * nsm) ng /= 2;
   if (const char *e = getenv("AMG_FSAI_NG")) {
     const int v = atoi(e);
@@ -1295,7 +1366,7 @@ __global__ void k_rotate(long n, int t, double *__restrict__ Z0, double *__restr
 }
 
 // Generalised eigenproblem H U = M U diag(lam) of the Ritz step, by one CTA of
-// two warps (the factorisation and the back-transform on warp 0):
+// four warps (the factorisation and the back-transform on warp 0):
 // M = L L^T (sub-diagonal entries scaled by 1 / L_jj, the triangular solves
 // multiply by the reciprocals Ri); C = L^{-1} (L^{-1} H)^T symmetrised as (C + C^T) * 0.5; Jacobi
 // sweeps in round-robin order (per round T/2 disjoint pairs from the circle
@@ -1366,20 +1437,20 @@ __device__ int gen_eig_cta(int t, const double *H, const double *M, double *U, d
   }  // warp 0
   __syncthreads();
   if (sbad) return 1;
+  // Sweeps in round-robin order (T/2 disjoint pairs per round from the circle
+  // method).  Per round: threads i < T/2 of warp 0 compute the rotation of
+  // pair i from the current C (at the start of a sweep warp 2 forms the
+  // off-diagonal and diagonal masses of the same C meanwhile, and the sweep
+  // ends there if the off-diagonal mass is negligible); then warps 0-1
+  // update C by 2 x 2 blocks (rows of pair I, columns of pair J), one lane
+  // per block column: its two entries take the column rotation of pair J and
+  // then the row rotation of pair I -- the operations of rotating all
+  // columns and then all rows -- and the pivot entries of an active pair
+  // become zero; warps 2-3 rotate the columns of W.
+  const int T = t + (t & 1), hp = T / 2;
+  __shared__ double s_off, s_dg;
   for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, dg = 0.0;
-    for (int p = 0; p < t; ++p) {
-      dg = fma(C[p * t + p], C[p * t + p], dg);
-      for (int q = p + 1; q < t; ++q) off = fma(C[p * t + q], C[p * t + q], off);
-    }
-    if (!(off > 1e-32 * dg)) break;
-    // one sweep in round-robin order: thread i < T/2 computes the rotation
-    // of pair i of the round from the current C; then warp 0 applies, per
-    // 2 x 2 block of C (rows of pair I, columns of pair J), the column
-    // rotation of pair J and then the row rotation of pair I (the operations
-    // of rotating all columns and then all rows), while warp 1 rotates the
-    // columns of W; then the pivots are zeroed
-    const int T = t + (t & 1), hp = T / 2;
+    bool done_sw = false;
     for (int r = 0; r < T - 1; ++r) {
       if (tid < hp) {
         int p = 0, q = 0, act = 0;
@@ -1408,43 +1479,72 @@ __device__ int gen_eig_cta(int t, const double *H, const double *M, double *U, d
         scs[tid] = c;
         ssn[tid] = sn;
       }
+      if (r == 0 && tid == 64) {
+        double off = 0.0, dg = 0.0;
+        for (int p = 0; p < t; ++p) {
+          dg = fma(C[p * t + p], C[p * t + p], dg);
+          for (int q = p + 1; q < t; ++q) off = fma(C[p * t + q], C[p * t + q], off);
+        }
+        s_off = off;
+        s_dg = dg;
+      }
       __syncthreads();
-      if (warp == 0) {
-        for (int b = lane; b < hp * hp; b += 32) {
+      if (r == 0 && !(s_off > 1e-32 * s_dg)) {
+        done_sw = true;
+        break;
+      }
+      if (warp < 2) {
+        // every lane of warps 0-1 takes the same number of passes (the
+        // __syncwarp below is reached by all 32 lanes)
+        for (int e0 = 0; e0 < 2 * hp * hp; e0 += 64) {
+          const int e = e0 + tid;
+          const bool task = e < 2 * hp * hp;
+          const int b = task ? e >> 1 : 0, h = e & 1;
           const int I = b / hp, J = b % hp;
           const int pI = sp[I], qI = sq[I], pJ = sp[J], qJ = sq[J];
           const bool rI = sact[I] != 0, cJ = sact[J] != 0;
-          if (!rI && !cJ) continue;
-          // entries (row, col) of the block that exist (q < t for active pairs;
-          // an inactive pair may name the index t when t is odd)
-          const bool hasq_r = qI < t, hasq_c = qJ < t;
-          double x00 = C[pI * t + pJ], x01 = hasq_c ? C[pI * t + qJ] : 0.0;
-          double x10 = hasq_r ? C[qI * t + pJ] : 0.0, x11 = (hasq_r && hasq_c) ? C[qI * t + qJ] : 0.0;
-          if (cJ) {  // columns pJ, qJ
+          const int col = h ? qJ : pJ;
+          const bool hq = qI < t;  // row qI exists (q >= t only for an inactive pair, t odd)
+          const bool live = task && col < t && (rI || cJ);
+          double x_pp = 0.0, x_pq = 0.0, x_qp = 0.0, x_qq = 0.0;
+          if (live) {
+            x_pp = C[pI * t + pJ];
+            x_qp = hq ? C[qI * t + pJ] : 0.0;
+            if (qJ < t) {
+              x_pq = C[pI * t + qJ];
+              x_qq = hq ? C[qI * t + qJ] : 0.0;
+            }
+          }
+          __syncwarp();  // the other lane of the block has read its inputs
+          if (!live) continue;
+          // column rotation of pair J, this lane's column, rows pI and qI
+          double yp = h ? x_pq : x_pp, yq = h ? x_qq : x_qp;
+          if (cJ) {
             const double c = scs[J], sn = ssn[J];
-            const double y00 = fma(c, x00, -(sn * x01)), y01 = fma(sn, x00, c * x01);
-            const double y10 = fma(c, x10, -(sn * x11)), y11 = fma(sn, x10, c * x11);
-            x00 = y00;
-            x01 = y01;
-            x10 = y10;
-            x11 = y11;
+            if (h == 0) {
+              yp = fma(c, x_pp, -(sn * x_pq));
+              yq = fma(c, x_qp, -(sn * x_qq));
+            } else {
+              yp = fma(sn, x_pp, c * x_pq);
+              yq = fma(sn, x_qp, c * x_qq);
+            }
           }
-          if (rI) {  // rows pI, qI
+          // row rotation of pair I
+          double zp = yp, zq = yq;
+          if (rI) {
             const double c = scs[I], sn = ssn[I];
-            const double y00 = fma(c, x00, -(sn * x10)), y10 = fma(sn, x00, c * x10);
-            const double y01 = fma(c, x01, -(sn * x11)), y11 = fma(sn, x01, c * x11);
-            x00 = y00;
-            x10 = y10;
-            x01 = y01;
-            x11 = y11;
+            zp = fma(c, yp, -(sn * yq));
+            zq = fma(sn, yp, c * yq);
           }
-          C[pI * t + pJ] = x00;
-          if (hasq_c) C[pI * t + qJ] = x01;
-          if (hasq_r) C[qI * t + pJ] = x10;
-          if (hasq_r && hasq_c) C[qI * t + qJ] = x11;
+          if (I == J && rI) {  // pivot entries (pI, qI) and (qI, pI)
+            if (h == 1) zp = 0.0;
+            else zq = 0.0;
+          }
+          C[pI * t + col] = zp;
+          if (hq) C[qI * t + col] = zq;
         }
       } else {
-        for (int idx = lane; idx < hp * t; idx += 32) {  // W: columns p_i, q_i, row k
+        for (int idx = tid - 64; idx < hp * t; idx += 64) {  // W: columns p_i, q_i, row k
           const int i = idx / t, k = idx - i * t;
           if (!sact[i]) continue;
           const double c = scs[i], sn = ssn[i];
@@ -1455,12 +1555,8 @@ __device__ int gen_eig_cta(int t, const double *H, const double *M, double *U, d
         }
       }
       __syncthreads();
-      if (tid < hp && sact[tid]) {
-        C[sp[tid] * t + sq[tid]] = 0.0;
-        C[sq[tid] * t + sp[tid]] = 0.0;
-      }
-      __syncthreads();
     }
+    if (done_sw) break;
   }
   if (warp != 0) return 0;
   int order[TMAXD];
@@ -1590,7 +1686,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     if (ritz) {
       const long warps = nchunks > 0 ? (long)nchunks * t * (t + 1) : 1;
       AMG_KCOUNT k_gram<<<(int)warps, 32, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p);
-      AMG_KCOUNT k_ritz_eig<<<1, 64, (6 * t * t + t) * sizeof(double), s>>>(t, H.p, Mg.p, U.p, lam.p, cs.p + C_F * t,
+      AMG_KCOUNT k_ritz_eig<<<1, 128, (6 * t * t + t) * sizeof(double), s>>>(t, H.p, Mg.p, U.p, lam.p, cs.p + C_F * t,
                                                                            status);
       AMG_KCOUNT k_rotate<<<dim3(nblk(n, 256), 2), 256, 0, s>>>(n, t, Z.p, SZ.p, U.p);  // Z U, (S Z) U
       AMG_LAUNCH_CHECK();

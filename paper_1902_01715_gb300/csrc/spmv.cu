@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int s0, int r0
                                                                   const TX *__restrict__ x, TX *__restrict__ y,
                                                                   const TX *__restrict__ aux, TX w,
                                                                   const int *__restrict__ done) {
-  if (done && *done) return;
+  // the "done" flag is loaded with the row data and tested before any
+  // write: its latency overlaps theirs instead of preceding them
+  const int dflag = done ? *done : 0;
   constexpr int SPB = SellCta<WPS>::slices, BB = B * B;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sl = s0 + blockIdx.x * SPB + warp / WPS;
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int s0, int r0
   const bool valid = row >= r0 && row < r1;  // rows [r0, r1) only
   const int len = valid ? rp[row + 1] - rp[row] : 0;
   const long base = valid ? (long)slp[sl] : 0L;
+  if (dflag) return;  // the same for the whole grid
   RowAcc<TX> acc;
   for (int j0 = part; j0 < len; j0 += WPS * U) {
     int c[U];
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(32) k_sellmv_w(int s0, int r0, int r1, int nr,
                                                  const TX *__restrict__ x, TX *__restrict__ y,
                                                  const TX *__restrict__ aux, TX w, const int *__restrict__ done,
                                                  TX *__restrict__ wpart, unsigned *__restrict__ wtick) {
-  if (done && *done) return;
+  const int dflag = done ? *done : 0;  // tested before any write, as above
   constexpr int BB = B * B;
   const int lane = threadIdx.x;
   const int sl = s0 + (int)(blockIdx.x / WPS);
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(32) k_sellmv_w(int s0, int r0, int r1, int nr,
   const bool valid = row >= r0 && row < r1;
   const int len = valid ? rp[row + 1] - rp[row] : 0;
   const long base = valid ? (long)slp[sl] : 0L;
+  if (dflag) return;
   RowAcc<TX> acc;
   for (int j0 = part; j0 < len; j0 += WPS * U) {
     int c[U];
