@@ -353,13 +353,23 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
 }
 
 // G column indices from the aFSAI output: row I holds its pattern nodes
-// (ascending), then I
+// (ascending, below I), then I.  A row that breaks this sets *bad (the
+// set-up then stops with an error instead of handing on the pattern).
 __global__ void k_fsai_cols(int n, int maxg, const int *__restrict__ np, const int *__restrict__ pat,
-                            const int *__restrict__ rp, int *__restrict__ col) {
+                            const int *__restrict__ rp, int *__restrict__ col, int *__restrict__ bad) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int I = (int)(t / (maxg + 1)), j = (int)(t % (maxg + 1));
   if (I >= n || j > np[I]) return;
-  col[rp[I] + j] = j < np[I] ? pat[(size_t)I * maxg + j] : I;
+  int c = I;
+  if (j < np[I]) {
+    c = pat[(size_t)I * maxg + j];
+    const int nx = j + 1 < np[I] ? pat[(size_t)I * maxg + j + 1] : I;
+    if (c < 0 || c >= nx) {
+      atomicExch(bad, 1);
+      c = I;
+    }
+  }
+  col[rp[I] + j] = c;
 }
 
 // aFSAI(A, G_s, k, rho, eps) into a compact G.
@@ -392,13 +402,18 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
   AMG_TRY(G.alloc(n, n, nnz, A.b));
   AMG_CU(cudaMemcpyAsync(G.rowptr.p, rp.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
   const long nt = (long)n * (maxg + 1);
-  if (n) AMG_KCOUNT k_fsai_cols<<<nblk(nt, 256), 256, 0, s>>>(n, maxg, np.p, pat.p, G.rowptr.p, G.col.p);
+  AMG_TRY(status.zero(s));
+  if (n) AMG_KCOUNT k_fsai_cols<<<nblk(nt, 256), 256, 0, s>>>(n, maxg, np.p, pat.p, G.rowptr.p, G.col.p, status.p);
   if (A.b == 1)
     AMG_KCOUNT k_compact_vals<1><<<nblk(nt, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
   else
     AMG_KCOUNT k_compact_vals<3><<<nblk(nt * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
   AMG_LAUNCH_CHECK();
-  AMG_CU(cudaStreamSynchronize(s));
+  AMG_TRY(read_int(status.p, &st, s));
+  if (st) {
+    set_error("aFSAI: a row pattern is not ascending below its diagonal");
+    return AMG_ERR_CUDA;
+  }
   return AMG_OK;
 }
 

@@ -49,11 +49,12 @@ struct Mapping {
   bool w1;  // one warp per CTA (k_sellmv_w)
 };
 // entry 8 is the bulk-copy variant below (FP32 and bf16 storage); 9.. put
-// every warp in a CTA of its own
+// every warp in a CTA of its own (14.. with four blocks in flight per lane)
 constexpr int SELL_SIGMA = 1024;  // rows per sorting window (a multiple of 32)
 static const Mapping kMaps[] = {{1, 2, false}, {1, 4, false}, {2, 2, false}, {2, 4, false}, {4, 2, false},
                                 {4, 4, false}, {8, 2, false}, {16, 2, false}, {0, 0, false}, {1, 2, true},
-                                {2, 2, true},  {4, 2, true},  {8, 2, true},  {16, 2, true}};
+                                {2, 2, true},  {4, 2, true},  {8, 2, true},  {16, 2, true}, {1, 4, true},
+                                {2, 4, true},  {4, 4, true}};
 constexpr int kNumMaps = (int)(sizeof(kMaps) / sizeof(kMaps[0]));
 
 // CTA size: 4 warps, or one slice of WPS warps when WPS > 4
@@ -275,7 +276,7 @@ static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *
 #undef AMG_SELL_ARGS
 }
 
-template <typename TM, typename TX, int B, int WPS>
+template <typename TM, typename TX, int B, int WPS, int U = 2>
 static void launch_w(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX *aux, TX w,
                      const int *done, cudaStream_t s, int r0 = 0, int r1 = -1) {
   if (r1 < 0) r1 = M.nr;
@@ -288,11 +289,11 @@ static void launch_w(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y,
   unsigned *wt = M.wtick.p;
 #define AMG_SELL_ARGS s0, r0, r1, M.nr, M.prow.p, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done, wp, wt
   switch (ep) {
-    case EP_SET: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SET, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SCALE: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SCALE, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_RESID: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_RESID, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SADD: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SADD, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
-    default: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_ACC, WPS, 2><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SET: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SET, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SCALE: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SCALE, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_RESID: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_RESID, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SADD: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SADD, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    default: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_ACC, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
   }
 #undef AMG_SELL_ARGS
 }
@@ -520,6 +521,9 @@ static void bsrmv_b(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, 
     case 11: launch_w<TM, TX, B, 4>(ep, M, v, x, y, aux, w, done, s); break;
     case 12: launch_w<TM, TX, B, 8>(ep, M, v, x, y, aux, w, done, s); break;
     case 13: launch_w<TM, TX, B, 16>(ep, M, v, x, y, aux, w, done, s); break;
+    case 14: launch_w<TM, TX, B, 1, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 15: launch_w<TM, TX, B, 2, 4>(ep, M, v, x, y, aux, w, done, s); break;
+    case 16: launch_w<TM, TX, B, 4, 4>(ep, M, v, x, y, aux, w, done, s); break;
     default:
       // the bulk-copy variant is written for 3x3 blocks in FP32/bf16
       if constexpr (std::is_same<TM, double>::value || B != 3) launch_map<TM, TX, B, 1, 2>(ep, M, v, x, y, aux, w, done, s);
@@ -554,6 +558,9 @@ static void bsrmv_rows_b(int ep, const SolveMat &M, const double *x, double *y, 
     case 11: launch_w<double, double, B, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
     case 12: launch_w<double, double, B, 8>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
     case 13: launch_w<double, double, B, 16>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 14: launch_w<double, double, B, 1, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 15: launch_w<double, double, B, 2, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
+    case 16: launch_w<double, double, B, 4, 4>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
     default: launch_map<double, double, B, 1, 2>(ep, M, v, x, y, aux, w, nullptr, s, r0, r1); break;
   }
 }
@@ -817,7 +824,7 @@ static int tune_one(SolveMat &M, const TM *v, cudaStream_t s, int kind) {
 }
 
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s) {
-  // AMG_MAP=<0..13> pins the mapping of every matrix (for experiments);
+  // AMG_MAP=<0..16> pins the mapping of every matrix (for experiments);
   // one-warp-CTA mappings only with the matrix's own warps per slice
   if (const char *pin = getenv("AMG_MAP")) {
     const int m = atoi(pin);
@@ -839,9 +846,10 @@ int mapping_wps(const SolveMat &M, bool f64) {
 }
 
 const char *mapping_name(const SolveMat &M, bool f64) {
-  static const char *names[kNumMaps] = {"wps1_u2",  "wps1_u4",  "wps2_u2",  "wps2_u4",  "wps4_u2",
-                                        "wps4_u4",  "wps8_u2",  "wps16_u2", "bulk_copy", "w1_wps1",
-                                        "w1_wps2",  "w1_wps4",  "w1_wps8",  "w1_wps16"};
+  static const char *names[kNumMaps] = {"wps1_u2",    "wps1_u4",    "wps2_u2",    "wps2_u4",   "wps4_u2",
+                                        "wps4_u4",    "wps8_u2",    "wps16_u2",   "bulk_copy", "w1_wps1",
+                                        "w1_wps2",    "w1_wps4",    "w1_wps8",    "w1_wps16",  "w1_wps1_u4",
+                                        "w1_wps2_u4", "w1_wps4_u4"};
   const int m = f64 ? M.map64 : M.map;
   return (m >= 0 && m < kNumMaps) ? names[m] : "?";
 }

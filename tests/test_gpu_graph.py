@@ -5,6 +5,7 @@ the oracle's bit for bit."""
 import numpy as np
 import pytest
 
+import workloads as W
 from _problems import SMALL, compare_hierarchies, gpu_problem, oracle_problem
 
 pytestmark = pytest.mark.gpu
@@ -101,21 +102,18 @@ def test_fsai_rows_per_warp_same_bits(A, orc, ng, monkeypatch):
     compare_hierarchies(S, H)
 
 
-def test_asymmetric_pattern_refused(A, orc):
-    """K is symmetric: a pattern holding block (i, j) without (j, i) is
-    refused with AMG_ERR_ARG before any set-up arithmetic."""
-    import torch
-    p = SMALL["beam"]()
+
+@pytest.mark.parametrize("ng", ["4", "8"])
+def test_fsai_refinement_many_rounds_bit_exact(A, orc, ng, monkeypatch):
+    """Algorithm 3's refinement passes (the layered slab refines twice) on a
+    level with more rows than the aFSAI kernel has slots, so every slot takes
+    several rows in turn and starts each from a row of the previous G: the
+    hierarchy equals the oracle's bit for bit with 4 and 8 rows per warp."""
+    monkeypatch.setenv("AMG_FSAI_NG", ng)
+    p = W.slab(96, 96, 4)
     K, V0, f, nm = oracle_problem(orc, p)
-    rp, col, val = np.asarray(K.rowptr), np.asarray(K.col[:K.nnzb]), np.asarray(K.val[:K.nnzb])
-    i = 5
-    k = next(q for q in range(rp[i], rp[i + 1]) if col[q] != i)  # an off-diagonal block of row i
-    keep = np.ones(len(col), bool)
-    keep[k] = False
-    rp2 = rp.copy()
-    rp2[i + 1:] -= 1
-    dev = torch.device("cuda")
-    with pytest.raises(A.AmgError) as e:
-        A.Solver(torch.tensor(rp2, device=dev), torch.tensor(col[keep], device=dev),
-                 torch.tensor(val[keep].reshape(-1), device=dev), torch.tensor(V0, device=dev))
-    assert e.value.code == A.AMG_ERR_ARG
+    H = orc.Hierarchy(K, V0, orc.default_params(3))
+    assert H.info(0)["npasses"] > 0
+    d = gpu_problem(A, p)
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
+    compare_hierarchies(S, H)
