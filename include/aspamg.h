@@ -125,7 +125,9 @@ int amg_default_params(amg_params *p);
  * Errors: AMG_ERR_ARG (bad sizes/params, or a pattern whose row pointers do
  * not start at 0, decrease or exceed rowptr[nnodes], or whose column indices
  * leave [0, nnodes) or do not increase along a row -- checked on the GPU
- * before anything else reads the pattern), AMG_ERR_NOT_SPD,
+ * before anything else reads the pattern -- or a pattern that is not
+ * symmetric: K is symmetric, and a block (i, j) stored without (j, i) is
+ * refused), AMG_ERR_NOT_SPD,
  * AMG_ERR_COARSENING, AMG_ERR_CUDA, AMG_ERR_MEM.  On error *out is NULL. */
 int amg_setup(const amg_params *p, int nnodes, int nnzb, const int *rowptr,
               const int *colind, const double *vals, int ntv0,

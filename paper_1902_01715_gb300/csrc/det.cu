@@ -498,6 +498,7 @@ struct FsaiK {
   int n;
   const int *Arp, *Acol;
   const double *Aval;
+  const int *Atr;  // per stored block (i, j): the index of block (j, i)
   const int *Gsrp, *Gscol;
   int ksteps, rho, maxg;
   double eps;
@@ -733,23 +734,51 @@ __device__ __forceinline__ int in_sorted(const int *a, int n, int v) {
   return 0;
 }
 
-// Insert J into a slot's open-addressing set for one (node, step); entries of
-// earlier uses (another stamp) count as free.  Returns true when J is new.
-// The table holds at least twice as many entries as the step can insert.
-__device__ __forceinline__ bool set_insert(unsigned long long *tab, int cap, unsigned stamp, int J) {
+// Find or insert J in a slot's open-addressing set for one (node, step);
+// entries of earlier uses (another stamp) count as free.  Returns J's table
+// position (and whether it was new), -1 if the table had no room (it holds
+// at least twice as many entries as the step can insert).
+__device__ __forceinline__ int set_find_insert(unsigned long long *tab, int cap, unsigned stamp, int J, bool &isnew) {
   const unsigned long long key = ((unsigned long long)stamp << 32) | (unsigned)J;
   unsigned h = ((unsigned)J * 2654435761u) & (unsigned)(cap - 1);
+  isnew = false;
   for (int probe = 0; probe < cap; ++probe) {
     unsigned long long cur = ((volatile unsigned long long *)tab)[h];
     for (int tries = 0; (unsigned)(cur >> 32) != stamp && tries < 64; ++tries) {
       const unsigned long long prev = atomicCAS(&tab[h], cur, key);
-      if (prev == cur) return true;
+      if (prev == cur) {
+        isnew = true;
+        return (int)h;
+      }
       cur = prev;
     }
-    if ((unsigned)(cur >> 32) == stamp && (unsigned)cur == (unsigned)J) return false;
+    if ((unsigned)(cur >> 32) == stamp && (unsigned)cur == (unsigned)J) return (int)h;
     h = (h + 1) & (unsigned)(cap - 1);
   }
-  return false;
+  return -1;
+}
+
+// Index of the transposed block of every stored block (one warp per row):
+// tr[k] = position of block (j, i) for block k = (i, j); a block without a
+// transposed partner sets *asym.
+__global__ void k_block_transpose_index(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                        int *__restrict__ tr, int *__restrict__ asym) {
+  const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= n) return;
+  for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+    const int j = col[k];
+    int lo = rp[j], hi = rp[j + 1] - 1, at = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1, c = col[mid];
+      if (c == i) {
+        at = mid;
+        break;
+      }
+      if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    tr[k] = at;
+    if (at < 0) atomicExch(asym, 1);
+  }
 }
 
 template <int B, int NG>
@@ -767,10 +796,13 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
   double *rhs = gh + B * mm;
   double *ent = rhs + B * mm;
   double *score = ent + B * mm;
+  double *acc = score + K.candcap;  // per candidate: its B x B gradient sums
   int *pat = K.iscr + slot * K.iper;  // pattern in the order the nodes were added
   int *cand = pat + K.maxg + 1;
   int *ccount = cand + K.candcap;
   int *spat = ccount + 1;  // the same nodes in ascending order (membership tests)
+  int *bidx = spat + K.maxg + 1;  // per candidate: its block (J, I), or -1
+  int *hidx = bidx + K.candcap;   // per table position: the candidate index
   unsigned long long *tab = K.htab + slot * K.hcap;
   const long nrounds = (K.n + nslots - 1) / nslots;
   for (long rd = 0; rd < nrounds; ++rd) {
@@ -802,40 +834,60 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
       const unsigned stamp = (unsigned)(rd * (K.ksteps + 1) + step + 1);
       if (gl == 0) *ccount = 0;
       __syncwarp();
+      // gradient entries g[c][d] = (A gt_c)_{BJ+d}: the pattern dofs in the
+      // pattern's order, then the dofs BI+e < BI+c, then the unit entry; node
+      // score = sum over c, d of g^2.  The rows of the pattern nodes are
+      // walked in the pattern's order (lanes over a row's entries, which name
+      // distinct nodes), so every candidate's sums take their terms in that
+      // order; the row of I then records each candidate's block (J, I).  The
+      // block (J, K) of entry (K, J) comes from the transposed-block index.
       if (active)
         for (int run = 0; run <= np; ++run) {
           const int Kn = run < np ? pat[run] : I;
           const int b0 = K.Arp[Kn], len = K.Arp[Kn + 1] - b0;
           for (int e = gl; e < len; e += GL) {
             const int J = K.Acol[b0 + e];
-            if (J < I && !in_sorted(spat, np, J) && set_insert(tab, K.hcap, stamp, J))
-              cand[atomicAdd(ccount, 1)] = J;
+            if (J >= I || in_sorted(spat, np, J)) continue;
+            bool isnew;
+            const int h = set_find_insert(tab, K.hcap, stamp, J, isnew);
+            if (h < 0) continue;
+            int idx;
+            if (isnew) {
+              idx = atomicAdd(ccount, 1);
+              cand[idx] = J;
+              hidx[h] = idx;
+              bidx[idx] = -1;
+              for (int q = 0; q < B * B; ++q) acc[(size_t)idx * B * B + q] = 0.0;
+            } else {
+              idx = hidx[h];
+            }
+            const int kt = K.Atr[b0 + e];
+            if (run == np) {
+              bidx[idx] = kt;
+            } else if (kt >= 0) {
+              const double *blk = K.Aval + (size_t)kt * B * B;
+              double *a = acc + (size_t)idx * B * B;
+              for (int c = 0; c < B; ++c)
+                for (int d = 0; d < B; ++d) {
+                  double g = a[c * B + d];
+                  for (int q = 0; q < B; ++q) g = fma(blk[d * B + q], gh[c * mm + B * run + q], g);
+                  a[c * B + d] = g;
+                }
+            }
           }
+          __syncwarp(smask);  // a later row may name the same candidates
         }
       __syncwarp();
       const int nc = active ? *(volatile int *)ccount : 0;
-      // gradient entries g[c][d] = (A gt_c)_{BJ+d}: pattern dofs in
-      // ascending order, then the dofs BI+e < BI+c, then the unit entry;
-      // node score = sum over c, d of g^2
       for (int t = gl; t < nc; t += GL) {
-        const int J = cand[t];
-        double gg[B][B];
-        for (int c = 0; c < B; ++c)
-          for (int d = 0; d < B; ++d) gg[c][d] = 0.0;
-        for (int j = 0; j < np; ++j) {
-          const double *blk = find_blk<B>(K.Arp, K.Acol, K.Aval, J, pat[j]);
-          if (blk)
-            for (int c = 0; c < B; ++c)
-              for (int d = 0; d < B; ++d)
-                for (int e = 0; e < B; ++e) gg[c][d] = fma(blk[d * B + e], gh[c * mm + B * j + e], gg[c][d]);
-        }
-        const double *bI = find_blk<B>(K.Arp, K.Acol, K.Aval, J, I);
+        const double *a = acc + (size_t)t * B * B;
+        const double *bI = bidx[t] >= 0 ? K.Aval + (size_t)bidx[t] * B * B : nullptr;
         double sc = 0.0;
         for (int c = 0; c < B; ++c)
           for (int d = 0; d < B; ++d) {
-            double gv = gg[c][d];
+            double gv = a[c * B + d];
             if (bI) {
-              for (int e = 0; e < c; ++e) gv = fma(bI[d * B + e], gh[c * mm + B * np + e], gv);
+              for (int q = 0; q < c; ++q) gv = fma(bI[d * B + q], gh[c * mm + B * np + q], gv);
               gv = gv + bI[d * B + c] * 1.0;
             }
             sc = fma(gv, gv, sc);
@@ -965,8 +1017,27 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   K.candcap = ((int)npcap + 1) * maxdeg;
   K.hcap = 64;
   while (K.hcap < 2 * K.candcap) K.hcap *= 2;
-  K.dper = (long)K.mmax * K.mmax + 3L * A.b * K.mmax + K.candcap;
-  K.iper = (maxg + 1) + K.candcap + 1 + (maxg + 1);
+  K.dper = (long)K.mmax * K.mmax + 3L * A.b * K.mmax + K.candcap + (long)K.candcap * A.b * A.b;
+  K.iper = (maxg + 1) + K.candcap + 1 + (maxg + 1) + K.candcap + K.hcap;
+  // transposed-block index of A (the level matrices have symmetric patterns;
+  // a pattern that is not is refused)
+  DBuf<int> atr, asym;
+  AMG_TRY(atr.alloc(A.nnzb));
+  AMG_TRY(asym.alloc(1));
+  AMG_TRY(asym.zero(s));
+  if (A.nr) AMG_KCOUNT k_block_transpose_index<<<(int)((32L * A.nr + 255) / 256), 256, 0, s>>>(A.nr, A.rowptr.p,
+                                                                                          A.col.p, atr.p, asym.p);
+  AMG_LAUNCH_CHECK();
+  {
+    int ha = 0;
+    AMG_CU(cudaMemcpyAsync(&ha, asym.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CU(cudaStreamSynchronize(s));
+    if (ha) {
+      set_error("aFSAI: the matrix pattern is not symmetric");
+      return AMG_ERR_ARG;
+    }
+  }
+  K.Atr = atr.p;
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

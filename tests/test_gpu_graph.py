@@ -117,3 +117,23 @@ def test_fsai_refinement_many_rounds_bit_exact(A, orc, ng, monkeypatch):
     d = gpu_problem(A, p)
     S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
     compare_hierarchies(S, H)
+
+
+def test_asymmetric_pattern_refused(A, orc):
+    """K is symmetric: a pattern holding block (i, j) without (j, i) is
+    refused with AMG_ERR_ARG before any set-up arithmetic."""
+    import torch
+    p = SMALL["beam"]()
+    K, V0, f, nm = oracle_problem(orc, p)
+    rp, col, val = np.asarray(K.rowptr), np.asarray(K.col[:K.nnzb]), np.asarray(K.val[:K.nnzb])
+    i = 5
+    k = next(q for q in range(rp[i], rp[i + 1]) if col[q] != i)  # an off-diagonal block of row i
+    keep = np.ones(len(col), bool)
+    keep[k] = False
+    rp2 = rp.copy()
+    rp2[i + 1:] -= 1
+    dev = torch.device("cuda")
+    with pytest.raises(A.AmgError) as e:
+        A.Solver(torch.tensor(rp2, device=dev), torch.tensor(col[keep], device=dev),
+                 torch.tensor(val[keep].reshape(-1), device=dev), torch.tensor(V0, device=dev))
+    assert e.value.code == A.AMG_ERR_ARG
