@@ -3,8 +3,8 @@
 
 One step = the whole path for one synthetic problem already resident in HBM:
 rebuild the hierarchy from K (aFSAI smoother with Lanczos omega, SRQCG test
-space, affinity coarsening, DPLS prolongation, Galerkin products, coarse
-Cholesky) and solve K u = f by PCG with one V(1,1)-cycle per iteration to
+space, affinity coarsening, DPLS prolongation, Galerkin products, the coarse
+level's explicit inverse) and solve K u = f by PCG with one V(1,1)-cycle per iteration to
 ||r|| <= 1e-8 ||f||.  The default workload is the 128 x 32 x 32 cantilever
 beam with lognormal Young's moduli and an FP64 V-cycle; the FP32 V-cycle of the
 same configuration is measured next to it.
@@ -51,7 +51,7 @@ TRAFFIC: dict = {
 }
 # aFSAI kernel: fraction of the FP64 FMA lane peak in its ncu capture
 # (profiles/k_fsai_beam96x24x24.md); None once the kernel changed
-FSAI_LANE_FRAC = None
+FSAI_LANE_FRAC = 0.251
 
 
 def workload_config(n3=None):
