@@ -1883,16 +1883,10 @@ __device__ __forceinline__ int find_in_row(const int *rp, const int *col, int ro
 // smaller node first and written to both positions (one thread per stored
 // block of the upper triangle); diagonal blocks get 0.
 template <int B>
-__global__ void k_soc_pairs(int nn, int nnzb, int t, const int *__restrict__ rp, const int *__restrict__ col,
-                            const double *__restrict__ V, const double *__restrict__ nrm, double *__restrict__ soc) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nnzb) return;
-  int lo = 0, hi = nn - 1;
-  while (lo < hi) {  // row of block k: last row with rp[row] <= k
-    const int mid = (lo + hi + 1) >> 1;
-    if (rp[mid] <= k) lo = mid; else hi = mid - 1;
-  }
-  const int I = lo, J = col[k];
+__device__ __forceinline__ void soc_entry(int nn, int t, int I, int k, const int *__restrict__ rp,
+                                          const int *__restrict__ col, const double *__restrict__ V,
+                                          const double *__restrict__ nrm, double *__restrict__ soc) {
+  const int J = col[k];
   if (J == I) {
     soc[k] = 0.0;
     return;
@@ -1908,19 +1902,60 @@ __global__ void k_soc_pairs(int nn, int nnzb, int t, const int *__restrict__ rp,
   if (kt >= 0) soc[kt] = v;
 }
 
+// one thread per block (large levels: full lanes)
+template <int B>
+__global__ void k_soc_pairs(int nn, int nnzb, int t, const int *__restrict__ rp, const int *__restrict__ col,
+                            const double *__restrict__ V, const double *__restrict__ nrm, double *__restrict__ soc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnzb) return;
+  int lo = 0, hi = nn - 1;
+  while (lo < hi) {  // row of block k: last row with rp[row] <= k
+    const int mid = (lo + hi + 1) >> 1;
+    if (rp[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  soc_entry<B>(nn, t, lo, k, rp, col, V, nrm, soc);
+}
+
+// one warp per block row, lanes over its blocks (small levels: no row search)
+template <int B>
+__global__ void k_soc_pairs_rows(int nn, int t, const int *__restrict__ rp, const int *__restrict__ col,
+                                 const double *__restrict__ V, const double *__restrict__ nrm,
+                                 double *__restrict__ soc) {
+  const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (I >= nn) return;
+  for (int k = rp[I] + lane; k < rp[I + 1]; k += 32) soc_entry<B>(nn, t, I, k, rp, col, V, nrm, soc);
+}
+
 // The theta largest positive SoC of row I are kept (ties to the smaller
-// column).
+// column).  One warp per row: each pick is a warp arg-max over the row's
+// entries not yet kept (larger SoC first, then the smaller position, which
+// is the smaller column).
 __global__ void k_soc_select(int nn, const int *__restrict__ rp, const int *__restrict__ col,
                              const double *__restrict__ soc, int theta, unsigned char *__restrict__ kept) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (I >= nn) return;
-  for (int k = rp[I]; k < rp[I + 1]; ++k) kept[k] = 0;
+  const int k0 = rp[I], k1 = rp[I + 1];
+  for (int k = k0 + lane; k < k1; k += 32) kept[k] = 0;
+  __syncwarp();
   for (int p = 0; p < theta; ++p) {
-    int best = -1;
-    for (int k = rp[I]; k < rp[I + 1]; ++k)
-      if (!kept[k] && col[k] != I && soc[k] > 0.0 && (best < 0 || soc[k] > soc[best])) best = k;
-    if (best < 0) break;
-    kept[best] = 1;
+    double bv = 0.0;
+    int bk = -1;
+    for (int k = k0 + lane; k < k1; k += 32)
+      if (!kept[k] && col[k] != I && soc[k] > 0.0 && (bk < 0 || soc[k] > bv)) {
+        bv = soc[k];
+        bk = k;
+      }
+    for (int off = 16; off >= 1; off >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
+      if (ok >= 0 && (bk < 0 || ov > bv || (ov == bv && ok < bk))) {
+        bv = ov;
+        bk = ok;
+      }
+    }
+    if (bk < 0) break;
+    if (lane == 0) kept[bk] = 1;
+    __syncwarp();
   }
 }
 
@@ -1948,14 +1983,18 @@ int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char
   AMG_TRY(kept.alloc(A.nnzb));
   const int nb = nblk(A.nr, 128);
   AMG_TRY(soc.zero(s));
+  const bool rows = A.nr < 32768;
+  const int nbr = nblk(32L * A.nr, 128), nbe = nblk(A.nnzb, 128);
   if (A.b == 1) {
     AMG_KCOUNT k_soc_nrm<1><<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
-    AMG_KCOUNT k_soc_pairs<1><<<nblk(A.nnzb, 128), 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+    if (rows) AMG_KCOUNT k_soc_pairs_rows<1><<<nbr, 128, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+    else AMG_KCOUNT k_soc_pairs<1><<<nbe, 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
   } else {
     AMG_KCOUNT k_soc_nrm<3><<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
-    AMG_KCOUNT k_soc_pairs<3><<<nblk(A.nnzb, 128), 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+    if (rows) AMG_KCOUNT k_soc_pairs_rows<3><<<nbr, 128, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+    else AMG_KCOUNT k_soc_pairs<3><<<nbe, 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
   }
-  AMG_KCOUNT k_soc_select<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, soc.p, theta, kept.p);
+  AMG_KCOUNT k_soc_select<<<nblk(32L * A.nr, 128), 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, soc.p, theta, kept.p);
   AMG_KCOUNT k_strong<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, kept.p, strong);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));

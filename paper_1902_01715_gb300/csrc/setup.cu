@@ -293,10 +293,15 @@ static int mis_gpu(Level &L, const unsigned char *d_strong, cudaStream_t s) {
   const int nb = nblk(n, 256);
   AMG_KCOUNT k_mis_deg<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state);
   AMG_LAUNCH_CHECK();
-  for (int round = 0;; ++round) {
-    AMG_TRY(left.zero(s));
-    AMG_KCOUNT k_mis_select<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state, flag.p, left.p);
-    AMG_KCOUNT k_mis_apply<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, flag.p, state);
+  // rounds are queued four at a time between read-backs of the undecided
+  // count of the last one (rounds after the last decision change nothing)
+  constexpr int kBatch = 4;
+  for (int round = 0;; round += kBatch) {
+    for (int q = 0; q < kBatch; ++q) {
+      AMG_TRY(left.zero(s));
+      AMG_KCOUNT k_mis_select<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state, flag.p, left.p);
+      AMG_KCOUNT k_mis_apply<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, flag.p, state);
+    }
     AMG_LAUNCH_CHECK();
     int hl = 0;
     AMG_TRY(read_int(left.p, &hl, s));
