@@ -499,6 +499,7 @@ struct FsaiK {
   const int *Arp, *Acol;
   const double *Aval;
   const int *Atr;  // per stored block (i, j): the index of block (j, i)
+  int compact;     // compact a row's candidate entries before taking them
   const int *Gsrp, *Gscol;
   int ksteps, rho, maxg;
   double eps;
@@ -585,7 +586,10 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       }
     }
   }
-  for (int idx = gl; idx < (act ? nn : 0); idx += GL) {
+  // right-hand sides and entries of the new nodes and of I (those of the
+  // kept nodes are unchanged, and rhs holds their forward-substitution
+  // values y from the previous solve)
+  for (int idx = p0 + gl; idx < (act ? nn : 0); idx += GL) {
     const int Np = idx < np ? pat[idx] : I;
     const double *bc = find_blk<B>(K.Arp, K.Acol, K.Aval, Np, I);
     const double *br = find_blk<B>(K.Arp, K.Acol, K.Aval, I, Np);
@@ -656,22 +660,26 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
   // uses the leading B np + c rows): y_k = rhs_k (1 / L_kk), then rhs_r -= L_rk y_k
   // (k ascending for every r), in blocks of FS_PB columns: inside a block
   // column by column, then the rows below it take the block's updates in
-  // one pass
+  // one pass.  Rows below r0 already hold their y (a leading block of a
+  // triangular solve does not depend on the rows after it); the new rows
+  // take every update, from the kept columns too, in the same order.
   for (int k0 = 0; k0 < mx; k0 += FS_PB) {
     const int k1 = min(k0 + FS_PB, mx);
     for (int k = k0; k < k1; ++k) {
-      if (ok && gl < B && k < B * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] * M[k * mm + k];
+      if (ok && gl < B && k >= r0 && k < B * np + gl) rhs[gl * mm + k] = rhs[gl * mm + k] * M[k * mm + k];
       __syncwarp();
-      if (ok)
-        for (int idx = gl; idx < B * (k1 - k - 1); idx += GL) {
-          const int c = idx / (k1 - k - 1), r = k + 1 + idx % (k1 - k - 1);
+      const int rs = max(k + 1, r0), nr = k1 - rs;
+      if (ok && nr > 0)
+        for (int idx = gl; idx < B * nr; idx += GL) {
+          const int c = idx / nr, r = rs + idx % nr;
           if (r < B * np + c) rhs[c * mm + r] = fma(-M[r * mm + k], rhs[c * mm + k], rhs[c * mm + r]);
         }
       __syncwarp();
     }
-    if (ok && k1 < m2)
-      for (int idx = gl; idx < B * (m2 - k1); idx += GL) {
-        const int c = idx / (m2 - k1), r = k1 + idx % (m2 - k1);
+    const int rs2 = max(k1, r0), nr2 = m2 - rs2;
+    if (ok && nr2 > 0)
+      for (int idx = gl; idx < B * nr2; idx += GL) {
+        const int c = idx / nr2, r = rs2 + idx % nr2;
         if (r < B * np + c) {
           double a = rhs[c * mm + r];
           for (int k = k0; k < k1; ++k) a = fma(-M[r * mm + k], rhs[c * mm + k], a);
@@ -680,27 +688,34 @@ __device__ int fsai_solve_rows(const FsaiK &K, bool act, int I, const int *pat, 
       }
     __syncwarp();
   }
-  // backward substitution: x_k = rhs_k (1 / L_kk) for k descending, then
-  // rhs_r -= L_kr x_k for r < k (k descending for every r), in blocks of
-  // FS_PB columns from the top
+  // backward substitution on a copy of y (rhs keeps y for the next solve of
+  // this row): x_k = w_k (1 / L_kk) for k descending, then w_r -= L_kr x_k
+  // for r < k (k descending for every r), in blocks of FS_PB columns from
+  // the top; w and then x live in gh
+  if (ok)
+    for (int idx = gl; idx < B * m2; idx += GL) {
+      const int c = idx / m2, k = idx % m2;
+      if (k < B * np + c) gh[c * mm + k] = rhs[c * mm + k];
+    }
+  __syncwarp();
   for (int k1 = mx; k1 > 0; k1 -= FS_PB) {
     const int k0 = max(k1 - FS_PB, 0);
     for (int k = k1 - 1; k >= k0; --k) {
-      if (ok && gl < B && k < B * np + gl) gh[gl * mm + k] = rhs[gl * mm + k] * M[k * mm + k];
+      if (ok && gl < B && k < B * np + gl) gh[gl * mm + k] = gh[gl * mm + k] * M[k * mm + k];
       __syncwarp();
       if (ok && k < m2)
         for (int idx = gl; idx < B * (k - k0); idx += GL) {
           const int c = idx / (k - k0), r = k0 + idx % (k - k0);
-          if (k < B * np + c) rhs[c * mm + r] = fma(-M[k * mm + r], gh[c * mm + k], rhs[c * mm + r]);
+          if (k < B * np + c) gh[c * mm + r] = fma(-M[k * mm + r], gh[c * mm + k], gh[c * mm + r]);
         }
       __syncwarp();
     }
     if (ok)
       for (int idx = gl; idx < B * k0; idx += GL) {
         const int c = idx / k0, r = idx % k0;
-        double a = rhs[c * mm + r];
+        double a = gh[c * mm + r];
         for (int k = min(k1, B * np + c) - 1; k >= k0; --k) a = fma(-M[k * mm + r], gh[c * mm + k], a);
-        rhs[c * mm + r] = a;
+        gh[c * mm + r] = a;
       }
     __syncwarp();
   }
@@ -785,7 +800,8 @@ template <int B, int NG>
 __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
   constexpr int GL = 32 / NG;
   static_assert(GL >= B, "a slot needs a lane per dof row of a node");
-  const unsigned smask = GL == 32 ? 0xffffffffu : (((1u << (GL & 31)) - 1u) << ((threadIdx.x & 31) / GL * GL));
+  constexpr unsigned lowmask = GL == 32 ? 0xffffffffu : ((1u << (GL & 31)) - 1u);
+  const unsigned smask = lowmask << ((threadIdx.x & 31) / GL * GL);
   const int lane = threadIdx.x & 31, g = lane / GL, gl = lane % GL;
   const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nw = ((long)gridDim.x * blockDim.x) >> 5;
@@ -845,34 +861,64 @@ __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
         for (int run = 0; run <= np; ++run) {
           const int Kn = run < np ? pat[run] : I;
           const int b0 = K.Arp[Kn], len = K.Arp[Kn + 1] - b0;
-          for (int e = gl; e < len; e += GL) {
-            const int J = K.Acol[b0 + e];
-            if (J >= I || in_sorted(spat, np, J)) continue;
-            bool isnew;
-            const int h = set_find_insert(tab, K.hcap, stamp, J, isnew);
-            if (h < 0) continue;
-            int idx;
-            if (isnew) {
-              idx = atomicAdd(ccount, 1);
-              cand[idx] = J;
-              hidx[h] = idx;
-              bidx[idx] = -1;
-              for (int q = 0; q < B * B; ++q) acc[(size_t)idx * B * B + q] = 0.0;
-            } else {
-              idx = hidx[h];
+          // one candidate entry e of the row (J = its column): its slot and
+          // its gradient term
+          auto take = [&](int e, int J) {
+              bool isnew;
+              const int h = set_find_insert(tab, K.hcap, stamp, J, isnew);
+              if (h < 0) return;
+              int idx;
+              if (isnew) {
+                idx = atomicAdd(ccount, 1);
+                cand[idx] = J;
+                hidx[h] = idx;
+                bidx[idx] = -1;
+                for (int q = 0; q < B * B; ++q) acc[(size_t)idx * B * B + q] = 0.0;
+              } else {
+                idx = hidx[h];
+              }
+              const int kt = K.Atr[b0 + e];
+              if (run == np) {
+                bidx[idx] = kt;
+              } else if (kt >= 0) {
+                const double *blk = K.Aval + (size_t)kt * B * B;
+                double *a = acc + (size_t)idx * B * B;
+                for (int c = 0; c < B; ++c)
+                  for (int d = 0; d < B; ++d) {
+                    double gs = a[c * B + d];
+                    for (int q = 0; q < B; ++q) gs = fma(blk[d * B + q], gh[c * mm + B * run + q], gs);
+                    a[c * B + d] = gs;
+                  }
+              }
+          };
+          if (K.compact) {
+            // the row's entries that name candidates (J < I, outside the
+            // pattern), compacted in the (still unused) score array so that
+            // the lanes then take one candidate entry each
+            int *elist = reinterpret_cast<int *>(score);
+            int nq = 0;
+            for (int e0 = 0; e0 < len; e0 += GL) {
+              const int e = e0 + gl;
+              bool c = false;
+              if (e < len) {
+                const int J = K.Acol[b0 + e];
+                c = J < I && !in_sorted(spat, np, J);
+              }
+              const unsigned m = (__ballot_sync(smask, c) >> (g * GL)) & lowmask;
+              if (c) elist[nq + __popc(m & ((1u << gl) - 1u))] = e;
+              nq += __popc(m);
             }
-            const int kt = K.Atr[b0 + e];
-            if (run == np) {
-              bidx[idx] = kt;
-            } else if (kt >= 0) {
-              const double *blk = K.Aval + (size_t)kt * B * B;
-              double *a = acc + (size_t)idx * B * B;
-              for (int c = 0; c < B; ++c)
-                for (int d = 0; d < B; ++d) {
-                  double g = a[c * B + d];
-                  for (int q = 0; q < B; ++q) g = fma(blk[d * B + q], gh[c * mm + B * run + q], g);
-                  a[c * B + d] = g;
-                }
+            __syncwarp(smask);
+            for (int u = gl; u < nq; u += GL) {
+              const int e = elist[u];
+              const int J = K.Acol[b0 + e];
+              take(e, J);
+            }
+          } else {
+            for (int e = gl; e < len; e += GL) {
+              const int J = K.Acol[b0 + e];
+              if (J >= I || in_sorted(spat, np, J)) continue;
+              take(e, J);
             }
           }
           __syncwarp(smask);  // a later row may name the same candidates
@@ -1038,6 +1084,10 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
     }
   }
   K.Atr = atr.p;
+  // long rows (coarse levels): most entries of a row are skipped by some
+  // lane, so the candidate entries are compacted first (measured: faster on
+  // the beam's levels 1-3, slower on its level 0 with rows of 27 blocks)
+  K.compact = maxdeg >= 40;
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
