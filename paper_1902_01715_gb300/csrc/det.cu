@@ -405,17 +405,13 @@ int gather_rows(const int *src_idx, int nout, int nin, int t, const double *Vin,
 // sc[i]) or v_j . v_j (i = j, into sc[t]), from the values this lane has
 // just formed, in the two-level dot order.  Each entry receives the same
 // rounded operations, in the same order, as the column-by-column definition.
-__global__ void __launch_bounds__(32) k_mgs_step(int n, int t, int nchunks, double *__restrict__ V, int j, int i,
-                                                 double *__restrict__ sc, double *__restrict__ part,
-                                                 unsigned *ticket) {
-  const long w = blockIdx.x;
-  const int lane = threadIdx.x & 31;
+// Chunk c of step (j, i): the fused vector work and this chunk's part of the
+// step's dot product (exchanged over the warp); sc holds the totals of the
+// earlier steps (sc[i'] for i' < j, sc[t] the norm square of column j - 1).
+__device__ __forceinline__ double mgs_chunk(int n, int t, double *__restrict__ V, int j, int i, int c,
+                                           const double *sc, int lane) {
   double *vj = V + (size_t)j * n;
-  if (nchunks == 0) {
-    if (lane == 0) sc[i < j ? i : t] = 0.0;
-    return;
-  }
-  const int base = (int)w * CHUNK, end = min(base + CHUNK, n);
+  const int base = c * CHUNK, end = min(base + CHUNK, n);
   const bool norm_prev = i == 0 && j > 0;
   double *vp = V + (size_t)(j > 0 ? j - 1 : 0) * n;
   const double nr = norm_prev ? sqrt(sc[t]) : 1.0, rn = 1.0 / nr;
@@ -462,15 +458,135 @@ __global__ void __launch_bounds__(32) k_mgs_step(int n, int t, int nchunks, doub
       }
     }
   }
-  s = exchange32(s);
+  return exchange32(s);
+}
+
+__global__ void __launch_bounds__(32) k_mgs_step(int n, int t, int nchunks, double *__restrict__ V, int j, int i,
+                                                 double *__restrict__ sc, double *__restrict__ part,
+                                                 unsigned *ticket) {
+  const long w = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  if (nchunks == 0) {
+    if (lane == 0) sc[i < j ? i : t] = 0.0;
+    return;
+  }
+  const double s = mgs_chunk(n, t, V, j, i, (int)w, sc, lane);
   dot_finish(w, 1, nchunks, part, ticket, lane, s, [&](int, double v) { sc[i < j ? i : t] = v; });
 }
 
+// The whole Gram-Schmidt pass in one cooperative launch: warps own chunks
+// (chunk c belongs to warp c mod warps for every step), each step ends with a
+// grid barrier after which every CTA adds the chunks' parts in order -- the
+// additions of the last-warp sum above, so every CTA holds the same total,
+// which is the value the launch-per-step form computes.  Barrier waits are
+// bounded: one that runs out sets g_mgs_err and every CTA leaves.
+__device__ int g_mgs_err;
+
+__device__ __forceinline__ bool mgs_grid_sync(unsigned *bar, unsigned &gen, int *fail) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], gen + 1u);
+    } else {
+      const long long t0 = clock64();
+      while (((volatile unsigned *)bar)[1] == gen) {
+        if (*(volatile int *)&g_mgs_err || clock64() - t0 > (1LL << 32)) {
+          atomicExch(&g_mgs_err, 1);
+          *fail = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  ++gen;
+  return *(volatile int *)fail == 0;
+}
+
+constexpr int MGS_WARPS = 2;  // small CTAs: the chunks spread over all SMs
+
+__global__ void __launch_bounds__(32 * MGS_WARPS) k_mgs_coop(int n, int t, int nchunks, double *__restrict__ V,
+                                                             double *__restrict__ part, unsigned *bar) {
+  __shared__ double ssc[TMAXD + 1];
+  __shared__ int fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) fail = 0;
+  for (int q = threadIdx.x; q <= TMAXD; q += blockDim.x) ssc[q] = 0.0;
+  __syncthreads();
+  const int wg = blockIdx.x * MGS_WARPS + warp, nw = gridDim.x * MGS_WARPS;
+  unsigned gen = 0;
+  for (int j = 0; j < t; ++j)
+    for (int i = 0; i <= j; ++i) {
+      // the steps alternate between two halves of part: a CTA writes step
+      // s + 1's parts only after the barrier of step s, and the next write
+      // to the same half waits for the barrier of step s + 1, which every CTA
+      // reaches only after reading step s's total
+      double *ps = part + (size_t)(gen & 1u) * nchunks;
+      for (int c = wg; c < nchunks; c += nw) {
+        const double s = mgs_chunk(n, t, V, j, i, c, ssc, lane);
+        if (lane == 0) ps[c] = s;
+      }
+      if (!mgs_grid_sync(bar, gen, &fail)) return;
+      if (warp == 0) {
+        const double tot = sum_chunks(ps, nchunks, lane);
+        if (lane == 0) ssc[i < j ? i : t] = tot;
+      }
+      __syncthreads();
+    }
+  // the last column divided by its norm (as k_div_sqrt), each warp on the
+  // chunks it owns (it alone wrote them)
+  if (t > 0) {
+    const double nr = sqrt(ssc[t]);
+    if (nr > 0.0) {
+      const double rn = 1.0 / nr;
+      double *v = V + (size_t)(t - 1) * n;
+      for (int c = wg; c < nchunks; c += nw)
+        for (int k = c * CHUNK + lane; k < min(c * CHUNK + CHUNK, n); k += 32) v[k] = v[k] * rn;
+    }
+  }
+}
+
 int mgs(int n, int t, double *V, cudaStream_t s) {
+  const int nchunks = (n + CHUNK - 1) / CHUNK;
+  if (t > 0 && nchunks > 0 && !getenv("AMG_MGS_STEPS")) {
+    // one cooperative launch for the whole pass (at most one CTA per two
+    // chunks, every CTA resident at once)
+    int dev = 0, nsm = 0, per = 0, coop = 0;
+    AMG_CU(cudaGetDevice(&dev));
+    AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    AMG_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    AMG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgs_coop, 32 * MGS_WARPS, 0));
+    if (coop && per > 0) {
+      int grid = (nchunks + MGS_WARPS - 1) / MGS_WARPS;
+      if (grid > nsm * per) grid = nsm * per;
+      DBuf<double> part;
+      DBuf<unsigned> bar;
+      AMG_TRY(part.alloc(2 * (size_t)nchunks));
+      AMG_TRY(bar.alloc(2));
+      AMG_TRY(bar.zero(s));
+      void *args[] = {&n, &t, (void *)&nchunks, &V, &part.p, &bar.p};
+      count_launches(1);
+      AMG_CU(cudaLaunchCooperativeKernel((const void *)k_mgs_coop, dim3(grid), dim3(32 * MGS_WARPS), args, 0, s));
+      AMG_CU(cudaStreamSynchronize(s));
+      int err = 0;
+      AMG_CU(cudaMemcpyFromSymbol(&err, g_mgs_err, sizeof(int)));
+      if (err) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_mgs_err, &z, sizeof(int));
+        set_error("Gram-Schmidt: a grid barrier wait ran out");
+        return AMG_ERR_CUDA;
+      }
+      return AMG_OK;
+    }
+  }
   DBuf<double> sc, part;
   DBuf<unsigned> tk;
   AMG_TRY(sc.alloc(t + 1));
-  const int nchunks = (n + CHUNK - 1) / CHUNK;
   AMG_TRY(part.alloc((size_t)nchunks + 1));
   AMG_TRY(tk.alloc(MAXTICKETS));
   AMG_TRY(tk.zero(s));
