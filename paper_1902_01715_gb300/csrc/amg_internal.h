@@ -53,6 +53,51 @@ struct StreamScope {
 };
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
 
+// Programmatic dependent launch of the solve-phase kernels.  While a
+// PdlScope lives on the calling thread, launch_k issues kernels with
+// programmatic stream serialisation: a kernel may be scheduled while the
+// kernel before it in the stream is still running, once every CTA of that
+// kernel has issued pdl_trigger() (or exited).  The kernels issue it after
+// their main loop, before their epilogue: issued at the start, it let the
+// next kernel's CTAs crowd onto the SMs that freed first, and the solve
+// became slower than without programmatic launch.  A kernel reads, before
+// its pdl_wait(), only the solve layout of the level matrices (written by
+// the set-up, which ends with a stream synchronisation before any solve)
+// and writes nothing; pdl_wait() returns when the preceding grid has
+// completed and its memory operations are visible.  So the launch, the
+// index arithmetic and the first matrix loads of a kernel overlap the
+// epilogue of the one before it.  Outside a PdlScope (set-up, autotuning,
+// timing) launch_k is a plain launch and pdl_wait() returns at once;
+// AMG_NO_PDL in the environment makes every launch plain.
+bool pdl_enabled();
+struct PdlScope {
+  bool prev;
+  PdlScope();
+  ~PdlScope();
+};
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline void launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t shm, cudaStream_t s, A... args) {
+  count_launches(1);
+  if (!pdl_enabled()) {
+    k<<<grid, block, shm, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);  // a failure is left for the caller's launch check
+}
+
 // Owning device buffer (pool allocation on the current stream; freed on the
 // same stream).
 template <class T>

@@ -35,6 +35,10 @@ static thread_local cudaStream_t t_stream = nullptr;
 cudaStream_t current_stream() { return t_stream; }
 StreamScope::StreamScope(cudaStream_t s) : prev(t_stream) { t_stream = s; }
 StreamScope::~StreamScope() { t_stream = prev; }
+static thread_local bool t_pdl = false;
+bool pdl_enabled() { return t_pdl; }
+PdlScope::PdlScope() : prev(t_pdl) { t_pdl = getenv("AMG_NO_PDL") == nullptr; }
+PdlScope::~PdlScope() { t_pdl = prev; }
 
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
   // once per device: keep freed pool memory (the default threshold returns

@@ -72,26 +72,33 @@ int prepare_solve(Handle *h) {
 template <typename TX>
 __global__ void k_coarse_mv(int m, const double *__restrict__ Ci, const TX *__restrict__ y, TX *__restrict__ z,
                             const int *__restrict__ done) {
-  if (done && *done) return;
   const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
   double s = 0.0;
   const double *Cr = Ci + (size_t)row * m;
-  // the loads of 16 terms are issued before their FMAs (same order of terms)
+  // the loads of 16 terms are issued before their FMAs (same order of terms);
+  // the first 16 entries of the row (set-up data) before the wait for the
+  // preceding kernel
   constexpr int CU = 16;
+  double a[CU];
+#pragma unroll
+  for (int u = 0; u < CU; ++u) a[u] = lane + 32 * u < m ? Cr[lane + 32 * u] : 0.0;
+  pdl_wait();
+  if (done && *done) return;
   for (int k0 = lane; k0 < m; k0 += 32 * CU) {
-    double a[CU], b[CU];
+    double b[CU];
 #pragma unroll
     for (int u = 0; u < CU; ++u) {
       const int k = k0 + 32 * u;
-      a[u] = k < m ? Cr[k] : 0.0;
+      if (k0 != lane) a[u] = k < m ? Cr[k] : 0.0;
       b[u] = k < m ? (double)y[k] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < CU; ++u)
       if (k0 + 32 * u < m) s = fma(a[u], b[u], s);
   }
+  pdl_trigger();
   for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (lane == 0) z[row] = (TX)s;
 }
@@ -146,7 +153,7 @@ static void vcycle_level(Handle *h, int k, const TX *y, TX *z, const int *done) 
   if (k == h->nlev - 1) {
     const int m = h->nL;
     if (m == 0) return;
-    AMG_KCOUNT k_coarse_mv<TX><<<nblk(32L * m, 256), 256, 0, st>>>(m, h->Cinv.p, y, z, done);
+    launch_k(k_coarse_mv<TX>, nblk(32L * m, 256), 256, 0, st, m, (const double *)h->Cinv.p, y, z, done);
     return;
   }
   Level &C = *h->lev[k + 1];
@@ -213,10 +220,12 @@ __device__ __forceinline__ void finish_reduce(double v, double *part, int *flags
 // pq = p.q ; alpha = rz / pq
 __global__ void __launch_bounds__(RED_THREADS) k_pcg_pq(long n, const double *__restrict__ p, const double *__restrict__ q,
                                                         double *sc, int *flags, double *part) {
+  pdl_wait();
   if (flags[F_DONE]) return;
   __shared__ double sh[32];
   double v = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) v += p[i] * q[i];
+  pdl_trigger();
   finish_reduce(v, part, flags, sh, [&](double tot) {
     sc[P_PQ] = tot;
     if (!(tot > 0.0) || !isfinite(tot)) {
@@ -233,6 +242,7 @@ template <typename TX>
 __global__ void __launch_bounds__(RED_THREADS) k_pcg_xr(long n, double *__restrict__ x, double *__restrict__ r,
                                                         const double *__restrict__ p, const double *__restrict__ q,
                                                         TX *__restrict__ rlow, double *sc, int *flags, double *part) {
+  pdl_wait();
   if (flags[F_DONE]) return;
   __shared__ double sh[32];
   const double a = sc[P_ALPHA];
@@ -244,6 +254,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_xr(long n, double *__restri
     if (rlow) rlow[i] = (TX)ri;
     v += ri * ri;
   }
+  pdl_trigger();
   finish_reduce(v, part, flags, sh, [&](double tot) {
     sc[P_RR] = tot;
     const int it = flags[F_ITERS] + 1;
@@ -267,6 +278,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_rz(long n, const double *__
                                                         const TX *__restrict__ zlow, const double *__restrict__ zold,
                                                         int flexible, double *sc, int *flags, double *part,
                                                         double *part2) {
+  pdl_wait();
   if (flags[F_DONE]) return;
   __shared__ double sh[32];
   double v = 0.0, v2 = 0.0;
@@ -284,6 +296,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_rz(long n, const double *__
   const double b2 = flexible ? block_sum(v2, sh) : 0.0;
   if (flexible && threadIdx.x == 0) part2[blockIdx.x] = b2;
   __syncthreads();
+  pdl_trigger();
   finish_reduce(v, part, flags, sh, [&](double tot) {
     double rzo = 0.0;
     if (flexible)
@@ -300,6 +313,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_rz(long n, const double *__
 
 __global__ void k_pcg_p(long n, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold,
                         int flexible, const double *sc, const int *flags) {
+  pdl_wait();
   if (flags[F_DONE]) return;
   const double b = sc[P_BETA];
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -313,6 +327,7 @@ template <typename TX>
 __global__ void __launch_bounds__(RED_THREADS) k_pcg_start(long n, const double *__restrict__ b, double *__restrict__ x,
                                                            double *__restrict__ r, TX *__restrict__ rlow, double rtol,
                                                            double *sc, int *flags, double *part) {
+  pdl_wait();
   __shared__ double sh[32];
   double v = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -321,6 +336,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_start(long n, const double 
     if (rlow) rlow[i] = (TX)b[i];
     v += b[i] * b[i];
   }
+  pdl_trigger();
   finish_reduce(v, part, flags, sh, [&](double tot) {
     sc[P_BN2] = tot;
     sc[P_TOL2] = (rtol * rtol) * tot;
@@ -338,6 +354,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_start(long n, const double 
 // first direction: p = z, z_old = z, rz = r.z
 __global__ void k_pcg_first_p(long n, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold,
                               const int *flags) {
+  pdl_wait();
   if (flags[F_DONE]) return;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     p[i] = z[i];
@@ -358,6 +375,7 @@ template <typename TX>
 __global__ void __launch_bounds__(RED_THREADS) k_pcg_true(long n, const double *__restrict__ r, TX *__restrict__ rlow,
                                                           int phase, int max_phase, double *sc, int *flags,
                                                           double *part) {
+  pdl_wait();
   __shared__ double sh[32];
   double v = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -365,6 +383,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_true(long n, const double *
     if (rlow) rlow[i] = (TX)ri;
     v += ri * ri;
   }
+  pdl_trigger();
   finish_reduce(v, part, flags, sh, [&](double tot) {
     const double prev = sc[P_TRRP];
     sc[P_TRR] = tot;
@@ -421,33 +440,34 @@ static void pcg_iteration(Handle *h, bool mixed) {
   double *sc = h->scal.p;
   const int *done = fl + F_DONE;
   bsrmv<double, double>(EP_SET, L0.sA, L0.sA.v64.p, h->p.p, h->q.p, nullptr, 0.0, done, s);
-  AMG_KCOUNT k_pcg_pq<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->q.p, sc, fl, part);
+  launch_k(k_pcg_pq, RED_BLOCKS, RED_THREADS, 0, s, n, h->p.p, h->q.p, sc, fl, part);
   if (mixed) {
-    AMG_KCOUNT k_pcg_xr<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, low_r<TX>(h), sc, fl, part);
+    launch_k(k_pcg_xr<TX>, RED_BLOCKS, RED_THREADS, 0, s, n, h->x.p, h->r.p, h->p.p, h->q.p, low_r<TX>(h), sc, fl, part);
     vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), done);
-    AMG_KCOUNT k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, low_z<TX>(h), h->zold.p, 1, sc, fl, part,
+    launch_k(k_pcg_rz<TX>, RED_BLOCKS, RED_THREADS, 0, s, n, h->r.p, h->z.p, low_z<TX>(h), h->zold.p, 1, sc, fl, part,
                                                      part2);
-    AMG_KCOUNT k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 1, sc, fl);
+    launch_k(k_pcg_p, RED_BLOCKS, RED_THREADS, 0, s, n, h->p.p, h->z.p, h->zold.p, 1, sc, fl);
   } else {
-    AMG_KCOUNT k_pcg_xr<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->x.p, h->r.p, h->p.p, h->q.p, (double *)nullptr, sc, fl,
+    launch_k(k_pcg_xr<double>, RED_BLOCKS, RED_THREADS, 0, s, n, h->x.p, h->r.p, h->p.p, h->q.p, (double *)nullptr, sc, fl,
                                                          part);
     vcycle_level<double>(h, 0, h->r.p, h->z.p, done);
-    AMG_KCOUNT k_pcg_rz<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, (const double *)nullptr, h->zold.p, 0, sc,
+    launch_k(k_pcg_rz<double>, RED_BLOCKS, RED_THREADS, 0, s, n, h->r.p, h->z.p, (const double *)nullptr, h->zold.p, 0, sc,
                                                          fl, part, part2);
-    AMG_KCOUNT k_pcg_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, 0, sc, fl);
+    launch_k(k_pcg_p, RED_BLOCKS, RED_THREADS, 0, s, n, h->p.p, h->z.p, h->zold.p, 0, sc, fl);
   }
 }
 
 template <typename TX>
 static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int *iters, double *relres,
                          double *rec_relres, int *nrestart, bool mixed) {
+  PdlScope pdl;
   cudaStream_t s = h->stream;
   const long n = (long)h->b * h->n;
   double *part = h->red.p;
   int *fl = h->flags.p;
   double *sc = h->scal.p;
   AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(fl, h->prm.maxit);
-  AMG_KCOUNT k_pcg_start<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, b, h->x.p, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr, rtol,
+  launch_k(k_pcg_start<TX>, RED_BLOCKS, RED_THREADS, 0, s, n, b, h->x.p, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr, rtol,
                                                       sc, fl, part);
   if (mixed) {
     vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), fl + F_DONE);
@@ -455,9 +475,9 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
     vcycle_level<double>(h, 0, h->r.p, h->z.p, fl + F_DONE);
   }
   // rz = r.z (beta unused)
-  AMG_KCOUNT k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
+  launch_k(k_pcg_rz<TX>, RED_BLOCKS, RED_THREADS, 0, s, n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
                                                    h->zold.p, 0, sc, fl, part, part + 2 * RED_BLOCKS);
-  AMG_KCOUNT k_pcg_first_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, fl);
+  launch_k(k_pcg_first_p, RED_BLOCKS, RED_THREADS, 0, s, n, h->p.p, h->z.p, h->zold.p, fl);
   AMG_LAUNCH_CHECK();
   const int key = mixed ? 1 : 0;
   if (!h->graph_exec || h->graph_k != 1 || h->graph_prec != key) {
@@ -511,14 +531,14 @@ static int pcg_solve_one(Handle *h, const double *b, double *x, double rtol, int
     }
     // r = b - K x with the FP64 level-0 K, its norm, and the restart decision
     bsrmv<double, double>(EP_RESID, L0.sA, L0.sA.v64.p, h->x.p, h->r.p, b, 0.0, nullptr, s);
-    AMG_KCOUNT k_pcg_true<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr,
+    launch_k(k_pcg_true<TX>, RED_BLOCKS, RED_THREADS, 0, s, n, h->r.p, mixed ? low_r<TX>(h) : (TX *)nullptr,
                                                                 restarts, kMaxRestarts, sc, fl, part);
     // restart (all done-gated: nothing runs unless k_pcg_true cleared done)
     if (mixed) vcycle_level<TX>(h, 0, low_r<TX>(h), low_z<TX>(h), fl + F_DONE);
     else vcycle_level<double>(h, 0, h->r.p, h->z.p, fl + F_DONE);
-    AMG_KCOUNT k_pcg_rz<TX><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
+    launch_k(k_pcg_rz<TX>, RED_BLOCKS, RED_THREADS, 0, s, n, h->r.p, h->z.p, mixed ? low_z<TX>(h) : (const TX *)nullptr,
                                                      h->zold.p, 0, sc, fl, part, part + 2 * RED_BLOCKS);
-    AMG_KCOUNT k_pcg_first_p<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->p.p, h->z.p, h->zold.p, fl);
+    launch_k(k_pcg_first_p, RED_BLOCKS, RED_THREADS, 0, s, n, h->p.p, h->z.p, h->zold.p, fl);
     AMG_LAUNCH_CHECK();
     AMG_CU(cudaMemcpyAsync(pinned, fl, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CU(cudaStreamSynchronize(s));
@@ -579,6 +599,7 @@ __global__ void k_f2d(long n, const float *__restrict__ a, double *__restrict__ 
 
 int vcycle_apply(Handle *h, const double *y, double *z) {
   AMG_TRY(ensure_pcg(h));
+  PdlScope pdl;
   cudaStream_t s = h->stream;
   const long n = (long)h->b * h->n;
   AMG_KCOUNT k_set_flags<<<1, 1, 0, s>>>(h->flags.p, 1);
@@ -640,6 +661,7 @@ int vcycle_apply_noalloc(Handle *h, const double *y, double *z) {
   }
   void *base = nullptr;
   AMG_TRY(vc_scratch_address(&base));
+  PdlScope pdl;
   int *flags = (int *)base;
   cudaStream_t s = h->stream;
   const long n = (long)h->b * h->n;

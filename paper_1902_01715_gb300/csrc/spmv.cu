@@ -64,6 +64,24 @@ template <int WPS> struct SellCta {
   static constexpr int slices = warps / WPS;
 };
 
+// the column indices and entries of blocks j0, j0 + WPS, ..., j0 + (U-1) WPS
+// of a lane's row (those below the row length len)
+template <typename TM, int BB, int WPS, int U>
+__device__ __forceinline__ void sell_load(int j0, int len, long base, int lane, const int *__restrict__ scol,
+                                          const TM *__restrict__ v, int (&c)[U], TM (&m)[U][BB]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int j = j0 + u * WPS;
+    if (j < len) {
+      const long slot = base + 32L * j;
+      c[u] = scol[slot + lane];
+      const TM *vp = v + BB * slot + lane;
+#pragma unroll
+      for (int e = 0; e < BB; ++e) m[u][e] = vp[32 * e];
+    }
+  }
+}
+
 template <typename TM, typename TX, int B, int EP, int WPS, int U>
 __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int s0, int r0, int r1, int nr,
                                                                   const int *__restrict__ prow,
@@ -74,9 +92,6 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int s0, int r0
                                                                   const TX *__restrict__ x, TX *__restrict__ y,
                                                                   const TX *__restrict__ aux, TX w,
                                                                   const int *__restrict__ done) {
-  // the "done" flag is loaded with the row data and tested before any
-  // write: its latency overlaps theirs instead of preceding them
-  const int dflag = done ? *done : 0;
   constexpr int SPB = SellCta<WPS>::slices, BB = B * B;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sl = s0 + blockIdx.x * SPB + warp / WPS;
@@ -86,22 +101,16 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int s0, int r0
   const bool valid = row >= r0 && row < r1;  // rows [r0, r1) only
   const int len = valid ? rp[row + 1] - rp[row] : 0;
   const long base = valid ? (long)slp[sl] : 0L;
-  if (dflag) return;  // the same for the whole grid
+  // the row data and the first U blocks (solve layout) are loaded before
+  // the wait for the preceding kernel; x, the flag and y after it
+  int c[U];
+  TM m[U][BB];
+  sell_load<TM, BB, WPS, U>(part, len, base, lane, scol, v, c, m);
+  pdl_wait();
+  if (done && *done) return;  // the same for the whole grid
   RowAcc<TX> acc;
   for (int j0 = part; j0 < len; j0 += WPS * U) {
-    int c[U];
-    TM m[U][BB];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = j0 + u * WPS;
-      if (j < len) {
-        const long slot = base + 32L * j;
-        c[u] = scol[slot + lane];
-        const TM *vp = v + BB * slot + lane;
-#pragma unroll
-        for (int e = 0; e < BB; ++e) m[u][e] = vp[32 * e];
-      }
-    }
+    if (j0 != part) sell_load<TM, BB, WPS, U>(j0, len, base, lane, scol, v, c, m);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * WPS;
@@ -119,6 +128,7 @@ __global__ void __launch_bounds__(SellCta<WPS>::threads) k_sellmv(int s0, int r0
       }
     }
   }
+  pdl_trigger();
   if (WPS > 1) {
     __shared__ TX red[SellCta<WPS>::warps][2 * B][32];
 #pragma unroll
@@ -162,7 +172,6 @@ __global__ void __launch_bounds__(32) k_sellmv_w(int s0, int r0, int r1, int nr,
                                                  const TX *__restrict__ x, TX *__restrict__ y,
                                                  const TX *__restrict__ aux, TX w, const int *__restrict__ done,
                                                  TX *__restrict__ wpart, unsigned *__restrict__ wtick) {
-  const int dflag = done ? *done : 0;  // tested before any write, as above
   constexpr int BB = B * B;
   const int lane = threadIdx.x;
   const int sl = s0 + (int)(blockIdx.x / WPS);
@@ -172,22 +181,14 @@ __global__ void __launch_bounds__(32) k_sellmv_w(int s0, int r0, int r1, int nr,
   const bool valid = row >= r0 && row < r1;
   const int len = valid ? rp[row + 1] - rp[row] : 0;
   const long base = valid ? (long)slp[sl] : 0L;
-  if (dflag) return;
+  int c[U];
+  TM m[U][BB];
+  sell_load<TM, BB, WPS, U>(part, len, base, lane, scol, v, c, m);  // before the wait, as above
+  pdl_wait();
+  if (done && *done) return;
   RowAcc<TX> acc;
   for (int j0 = part; j0 < len; j0 += WPS * U) {
-    int c[U];
-    TM m[U][BB];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = j0 + u * WPS;
-      if (j < len) {
-        const long slot = base + 32L * j;
-        c[u] = scol[slot + lane];
-        const TM *vp = v + BB * slot + lane;
-#pragma unroll
-        for (int e = 0; e < BB; ++e) m[u][e] = vp[32 * e];
-      }
-    }
+    if (j0 != part) sell_load<TM, BB, WPS, U>(j0, len, base, lane, scol, v, c, m);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * WPS;
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(32) k_sellmv_w(int s0, int r0, int r1, int nr,
       }
     }
   }
+  pdl_trigger();
   if (WPS > 1) {
     TX *mine = wpart + ((size_t)sl * WPS + part) * (2 * B * 32);
 #pragma unroll
@@ -267,11 +269,11 @@ static void launch_map(int ep, const SolveMat &M, const TM *v, const TX *x, TX *
   if (nb == 0) return;
 #define AMG_SELL_ARGS s0, r0, r1, M.nr, M.prow.p, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
   switch (ep) {
-    case EP_SET: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SET, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SCALE: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SCALE, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_RESID: AMG_KCOUNT k_sellmv<TM, TX, B, EP_RESID, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SADD: AMG_KCOUNT k_sellmv<TM, TX, B, EP_SADD, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
-    default: AMG_KCOUNT k_sellmv<TM, TX, B, EP_ACC, WPS, U><<<nb, T, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SET: launch_k(k_sellmv<TM, TX, B, EP_SET, WPS, U>, nb, T, 0, s, AMG_SELL_ARGS); break;
+    case EP_SCALE: launch_k(k_sellmv<TM, TX, B, EP_SCALE, WPS, U>, nb, T, 0, s, AMG_SELL_ARGS); break;
+    case EP_RESID: launch_k(k_sellmv<TM, TX, B, EP_RESID, WPS, U>, nb, T, 0, s, AMG_SELL_ARGS); break;
+    case EP_SADD: launch_k(k_sellmv<TM, TX, B, EP_SADD, WPS, U>, nb, T, 0, s, AMG_SELL_ARGS); break;
+    default: launch_k(k_sellmv<TM, TX, B, EP_ACC, WPS, U>, nb, T, 0, s, AMG_SELL_ARGS); break;
   }
 #undef AMG_SELL_ARGS
 }
@@ -289,11 +291,11 @@ static void launch_w(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y,
   unsigned *wt = M.wtick.p;
 #define AMG_SELL_ARGS s0, r0, r1, M.nr, M.prow.p, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done, wp, wt
   switch (ep) {
-    case EP_SET: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SET, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SCALE: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SCALE, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_RESID: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_RESID, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
-    case EP_SADD: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_SADD, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
-    default: AMG_KCOUNT k_sellmv_w<TM, TX, B, EP_ACC, WPS, U><<<nb, 32, 0, s>>>(AMG_SELL_ARGS); break;
+    case EP_SET: launch_k(k_sellmv_w<TM, TX, B, EP_SET, WPS, U>, (unsigned)nb, 32, 0, s, AMG_SELL_ARGS); break;
+    case EP_SCALE: launch_k(k_sellmv_w<TM, TX, B, EP_SCALE, WPS, U>, (unsigned)nb, 32, 0, s, AMG_SELL_ARGS); break;
+    case EP_RESID: launch_k(k_sellmv_w<TM, TX, B, EP_RESID, WPS, U>, (unsigned)nb, 32, 0, s, AMG_SELL_ARGS); break;
+    case EP_SADD: launch_k(k_sellmv_w<TM, TX, B, EP_SADD, WPS, U>, (unsigned)nb, 32, 0, s, AMG_SELL_ARGS); break;
+    default: launch_k(k_sellmv_w<TM, TX, B, EP_ACC, WPS, U>, (unsigned)nb, 32, 0, s, AMG_SELL_ARGS); break;
   }
 #undef AMG_SELL_ARGS
 }
@@ -358,6 +360,7 @@ __global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, c
                                                                const TM *__restrict__ v, const TX *__restrict__ x,
                                                                TX *__restrict__ y, const TX *__restrict__ aux, TX w,
                                                                const int *__restrict__ done) {
+  pdl_wait();
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char bk_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -449,6 +452,7 @@ __global__ void __launch_bounds__(32 * BK_WARPS) k_sellmv_bulk(int nr, int ns, c
     if (EP == EP_SADD) { y[o] = aux[o] + w * a0; y[o + 1] = aux[o + 1] + w * a1; y[o + 2] = aux[o + 2] + w * a2; }
     if (EP == EP_ACC) { y[o] += a0; y[o + 1] += a1; y[o + 2] += a2; }
   }
+  pdl_trigger();
   if (failed && lane == 0)  // let the copies still in flight land (bounded) before the warp leaves
     for (int k = 0; k < BK_ST; ++k)
       if (pending & (1u << k)) mbar_wait(smem_u32(&bars[warp][k]), phase[k]);
@@ -483,11 +487,11 @@ static void launch_bulk(int ep, const SolveMat &M, const TM *v, const TX *x, TX 
   if (nb == 0) return;
 #define AMG_BULK_ARGS M.nr, M.ns, M.prow.p, M.rowptr, M.slp.p, M.scol.p, v, x, y, aux, w, done
   switch (ep) {
-    case EP_SET: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_SET><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
-    case EP_SCALE: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_SCALE><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
-    case EP_RESID: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_RESID><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
-    case EP_SADD: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_SADD><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
-    default: AMG_KCOUNT k_sellmv_bulk<TM, TX, EP_ACC><<<nb, 32 * BK_WARPS, shm, s>>>(AMG_BULK_ARGS); break;
+    case EP_SET: launch_k(k_sellmv_bulk<TM, TX, EP_SET>, nb, 32 * BK_WARPS, shm, s, AMG_BULK_ARGS); break;
+    case EP_SCALE: launch_k(k_sellmv_bulk<TM, TX, EP_SCALE>, nb, 32 * BK_WARPS, shm, s, AMG_BULK_ARGS); break;
+    case EP_RESID: launch_k(k_sellmv_bulk<TM, TX, EP_RESID>, nb, 32 * BK_WARPS, shm, s, AMG_BULK_ARGS); break;
+    case EP_SADD: launch_k(k_sellmv_bulk<TM, TX, EP_SADD>, nb, 32 * BK_WARPS, shm, s, AMG_BULK_ARGS); break;
+    default: launch_k(k_sellmv_bulk<TM, TX, EP_ACC>, nb, 32 * BK_WARPS, shm, s, AMG_BULK_ARGS); break;
   }
 #undef AMG_BULK_ARGS
 }
@@ -752,8 +756,6 @@ int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cu
     to_sell<__nv_bfloat16>(A, M, cols, M.v16.p, s);
   }
   AMG_LAUNCH_CHECK();
-  // the host slice offsets must outlive the asynchronous copy
-  AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
 }
 
