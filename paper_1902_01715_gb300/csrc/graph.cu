@@ -274,9 +274,19 @@ int symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z, int b, cudaStr
     AMG_KCOUNT k_sym_long<false><<<nlong, 256, 0, s>>>(nr, Y.nc, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, nullptr,
                                                        nullptr, cnt.p, bm.p);
   AMG_TRY(dev_scan(nr, cnt.p, 0, rp.p, s));
-  int nnz = 0;
-  AMG_TRY(read_int(rp.p + nr, &nnz, s));
+  // entry count and longest row of Z in one read-back
+  DBuf<int> tail;
+  AMG_TRY(tail.alloc(2));
+  AMG_TRY(tail.zero(s));
+  AMG_CU(cudaMemcpyAsync(tail.p, rp.p + nr, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (nr) AMG_KCOUNT k_row_max<<<nblk(nr, 256), 256, 0, s>>>(nr, rp.p, tail.p + 1);
+  AMG_LAUNCH_CHECK();
+  int ht[2] = {0, 0};
+  AMG_CU(cudaMemcpyAsync(ht, tail.p, sizeof ht, cudaMemcpyDeviceToHost, s));
+  AMG_CU(cudaStreamSynchronize(s));
+  const int nnz = ht[0];
   AMG_TRY(Z.alloc(nr, Y.nc, nnz, b));
+  Z.maxlen = ht[1];
   AMG_CU(cudaMemcpyAsync(Z.rowptr.p, rp.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
   if (nr) AMG_KCOUNT k_sym_merge<<<nb, 256, 0, s>>>(nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, rp.p, Z.col.p,
                                                     nullptr);
