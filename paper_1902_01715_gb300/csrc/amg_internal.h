@@ -53,26 +53,30 @@ struct StreamScope {
 };
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
 
-// Programmatic dependent launch of the solve-phase kernels.  While a
-// PdlScope lives on the calling thread, launch_k issues kernels with
-// programmatic stream serialisation: a kernel may be scheduled while the
-// kernel before it in the stream is still running, once every CTA of that
-// kernel has issued pdl_trigger() (or exited).  The kernels issue it after
-// their main loop, before their epilogue: issued at the start, it let the
-// next kernel's CTAs crowd onto the SMs that freed first, and the solve
-// became slower than without programmatic launch.  A kernel reads, before
-// its pdl_wait(), only the solve layout of the level matrices (written by
-// the set-up, which ends with a stream synchronisation before any solve)
-// and writes nothing; pdl_wait() returns when the preceding grid has
-// completed and its memory operations are visible.  So the launch, the
-// index arithmetic and the first matrix loads of a kernel overlap the
-// epilogue of the one before it.  Outside a PdlScope (set-up, autotuning,
-// timing) launch_k is a plain launch and pdl_wait() returns at once;
-// AMG_NO_PDL in the environment makes every launch plain.
+// Programmatic dependent launch.  While a PdlScope(true) lives on the
+// calling thread (the hierarchy set-up, a solve, a V-cycle), launch_k issues
+// kernels with programmatic stream serialisation: a kernel may be scheduled
+// while the kernel before it in the stream is still running, once every CTA
+// of that kernel has issued pdl_trigger() (or exited), so its launch and
+// prologue overlap the end of the one before it.  pdl_wait() returns when
+// the preceding grid has completed and its memory operations are visible.
+// Every kernel launched through launch_k calls it before touching memory
+// that kernels write -- the set-up kernels as their first statement; the
+// solve-phase kernels first load their row data and first matrix blocks
+// (the solve layout, written by the set-up, which ends with a stream
+// synchronisation before any solve) and write nothing before it.  The
+// solve-phase kernels issue pdl_trigger() after their main loop: issued at
+// the start, it let the next kernel's CTAs crowd onto the SMs that freed
+// first, and the solve became slower than without programmatic launch.
+// A PdlScope(false) (building the solve layout and timing its mappings,
+// whose kernels read a layout that the kernel just before may be writing)
+// and no scope at all (the timing entry points) give plain launches, where
+// pdl_wait() returns at once; AMG_NO_PDL in the environment makes every
+// launch plain.
 bool pdl_enabled();
 struct PdlScope {
   bool prev;
-  PdlScope();
+  explicit PdlScope(bool on = true);
   ~PdlScope();
 };
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

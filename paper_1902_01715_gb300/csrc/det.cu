@@ -79,6 +79,7 @@ template <int BS, int U>
 __global__ void k_spmv(int nr, const int *__restrict__ rowptr, const int *__restrict__ col,
                        const double *__restrict__ val, const double *__restrict__ x,
                        double *__restrict__ y) {
+  pdl_wait();
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long)BS * nr) return;
   const int I = (int)(t / BS), r = (int)(t - (long)BS * I);
@@ -94,9 +95,9 @@ template <int BS>
 static void spmv_b(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
   const long n = (long)BS * A.nr;
   if (A.nr < SMALL_ROWS)
-    AMG_KCOUNT k_spmv<BS, 8><<<nblk(n, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+    launch_k(k_spmv<BS, 8>, nblk(n, 256), 256, 0, s, A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
   else
-    AMG_KCOUNT k_spmv<BS, 1><<<nblk(n, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
+    launch_k(k_spmv<BS, 1>, nblk(n, 256), 256, 0, s, A.nr, A.rowptr.p, A.col.p, A.val.p, x, y);
 }
 
 int spmv(const DevBsr &A, const double *x, double *y, cudaStream_t s) {
@@ -250,6 +251,7 @@ __device__ void run_fin(const Fin &f, const double *v) {
 
 __global__ void __launch_bounds__(32) k_dots(int n, int nd, DotArgs a, double *__restrict__ part, unsigned *ticket,
                                              int nchunks, double *__restrict__ out, Fin fin) {
+  pdl_wait();
   const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
   const long total = nchunks > 0 ? (long)nchunks * nd : 1;
@@ -275,7 +277,7 @@ struct DotCtx {
 static int dots(int n, int nd, const DotArgs &a, double *out, DotCtx ctx, cudaStream_t s, Fin fin = Fin()) {
   const int nchunks = (n + CHUNK - 1) / CHUNK;
   const long warps = nchunks > 0 ? (long)nchunks * nd : 1;
-  AMG_KCOUNT k_dots<<<(int)warps, 32, 0, s>>>(n, nd, a, ctx.part, ctx.ticket, nchunks, out, fin);
+  launch_k(k_dots, (int)warps, 32, 0, s, n, nd, a, ctx.part, ctx.ticket, nchunks, out, fin);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -303,6 +305,7 @@ __device__ __forceinline__ void pair_of(int d, int t, int &which, int &i, int &j
 __global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restrict__ Z, const double *__restrict__ SZ,
                                              double *__restrict__ part, unsigned *ticket, int nchunks,
                                              double *__restrict__ H, double *__restrict__ M) {
+  pdl_wait();
   const int nd = t * (t + 1);
   const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
@@ -330,6 +333,7 @@ __global__ void __launch_bounds__(32) k_gram(int n, int t, const double *__restr
 __global__ void __launch_bounds__(128) k_ritz_eig(int t, const double *__restrict__ H, const double *__restrict__ M,
                                                  double *__restrict__ U, double *__restrict__ lam,
                                                  double *__restrict__ f, int *__restrict__ status) {
+  pdl_wait();
   extern __shared__ double wk[];  // 6 t^2 + t doubles
   const int tid = threadIdx.x;
   // the pencil was written by other CTAs: read it through L2 into shared memory
@@ -350,6 +354,7 @@ __global__ void __launch_bounds__(128) k_ritz_eig(int t, const double *__restric
 
 // v = v (1 / sqrt(*nn)) when *nn > 0 (normalisation by a squared norm)
 __global__ void k_div_sqrt(long n, double *__restrict__ v, const double *__restrict__ nn) {
+  pdl_wait();
   const double nr = sqrt(*nn);
   if (!(nr > 0.0)) return;
   const double rn = 1.0 / nr;
@@ -360,11 +365,13 @@ __global__ void k_div_sqrt(long n, double *__restrict__ v, const double *__restr
 // out = in * (*rd), rd a reciprocal formed once
 __global__ void k_mul_by(long n, double *__restrict__ out, const double *__restrict__ in,
                          const double *__restrict__ rd) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = in[i] * (*rd);
 }
 
 __global__ void k_uniform(long n, int col0, int ncols, uint64_t seed, double *__restrict__ V, int ld) {
+  pdl_wait();
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * ncols) return;
   const int j = col0 + (int)(t / n);
@@ -374,13 +381,14 @@ __global__ void k_uniform(long n, int col0, int ncols, uint64_t seed, double *__
 
 int uniform_fill(double *v, int n, int col0, int ncols, uint64_t seed, cudaStream_t s) {
   if (ncols <= 0 || n <= 0) return AMG_OK;
-  AMG_KCOUNT k_uniform<<<nblk((long)n * ncols, 256), 256, 0, s>>>(n, col0, ncols, seed, v, n);
+  launch_k(k_uniform, nblk((long)n * ncols, 256), 256, 0, s, n, col0, ncols, seed, v, n);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
 
 __global__ void k_gather_rows(const int *__restrict__ src, int nout, int nin, int t, const double *__restrict__ Vin,
                               double *__restrict__ Vout) {
+  pdl_wait();
   const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long)nout * t) return;
   const int j = (int)(q / nout);
@@ -390,7 +398,7 @@ __global__ void k_gather_rows(const int *__restrict__ src, int nout, int nin, in
 
 int gather_rows(const int *src_idx, int nout, int nin, int t, const double *Vin, double *Vout, cudaStream_t s) {
   if (nout <= 0) return AMG_OK;
-  AMG_KCOUNT k_gather_rows<<<nblk((long)nout * t, 256), 256, 0, s>>>(src_idx, nout, nin, t, Vin, Vout);
+  launch_k(k_gather_rows, nblk((long)nout * t, 256), 256, 0, s, src_idx, nout, nin, t, Vin, Vout);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -464,6 +472,7 @@ __device__ __forceinline__ double mgs_chunk(int n, int t, double *__restrict__ V
 __global__ void __launch_bounds__(32) k_mgs_step(int n, int t, int nchunks, double *__restrict__ V, int j, int i,
                                                  double *__restrict__ sc, double *__restrict__ part,
                                                  unsigned *ticket) {
+  pdl_wait();
   const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
   if (nchunks == 0) {
@@ -512,6 +521,7 @@ constexpr int MGS_WARPS = 2;  // small CTAs: the chunks spread over all SMs
 
 __global__ void __launch_bounds__(32 * MGS_WARPS) k_mgs_coop(int n, int t, int nchunks, double *__restrict__ V,
                                                              double *__restrict__ part, unsigned *bar) {
+  pdl_wait();
   __shared__ double ssc[TMAXD + 1];
   __shared__ int fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -592,8 +602,8 @@ int mgs(int n, int t, double *V, cudaStream_t s) {
   AMG_TRY(tk.zero(s));
   for (int j = 0; j < t; ++j)
     for (int i = 0; i <= j; ++i)
-      AMG_KCOUNT k_mgs_step<<<nchunks > 0 ? nchunks : 1, 32, 0, s>>>(n, t, nchunks, V, j, i, sc.p, part.p, tk.p);
-  if (t > 0 && n > 0) AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, V + (size_t)(t - 1) * n, sc.p + t);
+      launch_k(k_mgs_step, nchunks > 0 ? nchunks : 1, 32, 0, s, n, t, nchunks, V, j, i, sc.p, part.p, tk.p);
+  if (t > 0 && n > 0) launch_k(k_div_sqrt, nblk(n, 256), 256, 0, s, n, V + (size_t)(t - 1) * n, sc.p + t);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -894,6 +904,7 @@ __device__ __forceinline__ int set_find_insert(unsigned long long *tab, int cap,
 // transposed partner sets *asym.
 __global__ void k_block_transpose_index(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                         int *__restrict__ tr, int *__restrict__ asym) {
+  pdl_wait();
   const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= n) return;
   for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) {
@@ -914,6 +925,7 @@ __global__ void k_block_transpose_index(int n, const int *__restrict__ rp, const
 
 template <int B, int NG>
 __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
+  pdl_wait();
   constexpr int GL = 32 / NG;
   static_assert(GL >= B, "a slot needs a lane per dof row of a node");
   constexpr unsigned lowmask = GL == 32 ? 0xffffffffu : ((1u << (GL & 31)) - 1u);
@@ -1187,7 +1199,7 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   AMG_TRY(atr.alloc(A.nnzb));
   AMG_TRY(asym.alloc(1));
   AMG_TRY(asym.zero(s));
-  if (A.nr) AMG_KCOUNT k_block_transpose_index<<<(int)((32L * A.nr + 255) / 256), 256, 0, s>>>(A.nr, A.rowptr.p,
+  if (A.nr) launch_k(k_block_transpose_index, (int)((32L * A.nr + 255) / 256), 256, 0, s, A.nr, A.rowptr.p,
                                                                                           A.col.p, atr.p, asym.p);
   AMG_LAUNCH_CHECK();
   {
@@ -1291,6 +1303,7 @@ __device__ __forceinline__ int sturm_count(int mm, const double *al, const doubl
 
 __global__ void __launch_bounds__(32) k_lanczos_bisect(int m, const double *__restrict__ sc, double safety,
                                                        double *__restrict__ out) {
+  pdl_wait();
   __shared__ double al[64], be[64], bb[64];
   const int lane = threadIdx.x;
   for (int i = lane; i < 64; i += 32) {
@@ -1361,9 +1374,11 @@ __global__ void __launch_bounds__(32) k_lanczos_bisect(int m, const double *__re
   }
 }
 
-__global__ void k_set_neg(double *p) { *p = -1.0; }
+__global__ void k_set_neg(double *p) {
+  pdl_wait(); *p = -1.0; }
 
 __global__ void k_lanczos_start(long n, uint64_t seed, uint64_t base, double *__restrict__ v) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = uniform_pm1(seed, base | (uint64_t)i);
 }
@@ -1398,6 +1413,7 @@ __device__ double line_min(double a, double b, double c, double d, double e, dou
 enum { C_ALPHA = 0, C_Q = 1, C_FN = 2, C_BETA = 3, C_B = 4, C_F = 5, C_RF = 6, C_NUM = 7 };
 
 __global__ void k_b_z0(long nt, double *__restrict__ z, const double *__restrict__ v, const double *__restrict__ sv) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nt) z[i] = v[i] - sv[i];
 }
@@ -1405,6 +1421,7 @@ __global__ void k_b_z0(long nt, double *__restrict__ z, const double *__restrict
 // p = 2 (S z - q z) with q = out[j] (the first quotients, f = 1)
 __global__ void k_b_p0(long n, int t, double *__restrict__ p, const double *__restrict__ z,
                        const double *__restrict__ sz, const double *__restrict__ q) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * t) return;
   const int j = (int)(i / n);
@@ -1415,6 +1432,7 @@ __global__ void k_b_p0(long n, int t, double *__restrict__ p, const double *__re
 __global__ void k_b_zupd(long n, int t, double *__restrict__ z, const double *__restrict__ p,
                          double *__restrict__ sz, const double *__restrict__ sp, const double *__restrict__ cs,
                          const int *__restrict__ skip) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * t) return;
   const int j = (int)(i / n);
@@ -1426,6 +1444,7 @@ __global__ void k_b_zupd(long n, int t, double *__restrict__ z, const double *__
 
 __global__ void k_b_grad(long n, int t, double *__restrict__ g, const double *__restrict__ sz,
                          const double *__restrict__ z, const double *__restrict__ cs, const int *__restrict__ skip) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * t) return;
   const int j = (int)(i / n);
@@ -1437,6 +1456,7 @@ __global__ void k_b_grad(long n, int t, double *__restrict__ g, const double *__
 __global__ void k_b_pupd(long n, int t, double *__restrict__ p, const double *__restrict__ g,
                          double *__restrict__ sp, const double *__restrict__ sg, double *__restrict__ cs,
                          const int *__restrict__ skip) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * t) return;
   const int j = (int)(i / n);
@@ -1448,6 +1468,7 @@ __global__ void k_b_pupd(long n, int t, double *__restrict__ p, const double *__
 }
 
 __global__ void k_fill(double *__restrict__ p, int n, double v) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
 }
@@ -1465,6 +1486,7 @@ struct CDot {
 __global__ void __launch_bounds__(32) k_cdots(int n, int t, int nk, CDot a, double *__restrict__ part, unsigned *ticket,
                                               int nchunks, double *__restrict__ out, int fin, double *__restrict__ cs,
                                               int *__restrict__ skip) {
+  pdl_wait();
   const int nd = nk * t;
   const long w = blockIdx.x;
   const int lane = threadIdx.x & 31;
@@ -1508,6 +1530,7 @@ __global__ void __launch_bounds__(32) k_cdots(int n, int t, int nk, CDot a, doub
 template <int BS, int U>
 __global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const int *__restrict__ col,
                             const double *__restrict__ val, const double *__restrict__ X, double *__restrict__ Y) {
+  pdl_wait();
   const long n = (long)BS * nr;
   const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -1522,6 +1545,7 @@ __global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const
 // X = X U for X = Z (blockIdx.y 0) and X = S Z (blockIdx.y 1)
 __global__ void k_rotate(long n, int t, double *__restrict__ Z0, double *__restrict__ Z1,
                          const double *__restrict__ U) {
+  pdl_wait();
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   double *__restrict__ Z = blockIdx.y ? Z1 : Z0;
@@ -1760,9 +1784,9 @@ __device__ int gen_eig_cta(int t, const double *H, const double *M, double *U, d
 template <int BS>
 static void spmv_cols_b(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
   if (A.nr < SMALL_ROWS)
-    AMG_KCOUNT k_spmv_cols<BS, 4><<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+    launch_k(k_spmv_cols<BS, 4>, nblk(32L * A.nr, 256), 256, 0, s, A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
   else
-    AMG_KCOUNT k_spmv_cols<BS, 1><<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+    launch_k(k_spmv_cols<BS, 1>, nblk(32L * A.nr, 256), 256, 0, s, A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
 }
 
 int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
@@ -1786,7 +1810,7 @@ static int cdots(int n, int t, int nk, const CDot &a, double *out, int fin, doub
                  cudaStream_t s) {
   const int nchunks = (n + CHUNK - 1) / CHUNK;
   const long warps = nchunks > 0 ? (long)nchunks * nk * t : 1;
-  AMG_KCOUNT k_cdots<<<(int)warps, 32, 0, s>>>(n, t, nk, a, ctx.part, ctx.ticket, nchunks, out, fin, cs,
+  launch_k(k_cdots, (int)warps, 32, 0, s, n, t, nk, a, ctx.part, ctx.ticket, nchunks, out, fin, cs,
                                                            skip);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -1834,7 +1858,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   const int nb = nblk((long)nt, 256);
   // Z0 = (I - S) V0, orthonormalised
   AMG_TRY(apply_s_cols(A, G, GT, t, V0, SZ.p, T1.p, T2.p, s));
-  AMG_KCOUNT k_b_z0<<<nb, 256, 0, s>>>((long)nt, Z.p, V0, SZ.p);
+  launch_k(k_b_z0, nb, 256, 0, s, (long)nt, Z.p, V0, SZ.p);
   AMG_LAUNCH_CHECK();
   AMG_TRY(mgs(n, t, Z.p, s));
   // first quotients (unit columns), directions P = 2 (S Z - q Z), then S P
@@ -1845,8 +1869,8 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     a.y[0] = SZ.p;
     a.xs[0] = a.ys[0] = n;
     AMG_TRY(cdots(n, t, 1, a, out.p, CF_NONE, cs.p, skip.p, ctx, s));
-    AMG_KCOUNT k_b_p0<<<nb, 256, 0, s>>>(n, t, P.p, Z.p, SZ.p, out.p);
-    AMG_KCOUNT k_fill<<<1, 64, 0, s>>>(cs.p + C_F * t, t, 1.0);
+    launch_k(k_b_p0, nb, 256, 0, s, n, t, P.p, Z.p, SZ.p, out.p);
+    launch_k(k_fill, 1, 64, 0, s, cs.p + C_F * t, t, 1.0);
     AMG_LAUNCH_CHECK();
   }
   AMG_TRY(apply_s_cols(A, G, GT, t, P.p, SP.p, T1.p, T2.p, s));
@@ -1854,10 +1878,10 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
   auto iteration = [&](bool ritz) -> int {
     if (ritz) {
       const long warps = nchunks > 0 ? (long)nchunks * t * (t + 1) : 1;
-      AMG_KCOUNT k_gram<<<(int)warps, 32, 0, s>>>(n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p);
-      AMG_KCOUNT k_ritz_eig<<<1, 128, (6 * t * t + t) * sizeof(double), s>>>(t, H.p, Mg.p, U.p, lam.p, cs.p + C_F * t,
+      launch_k(k_gram, (int)warps, 32, 0, s, n, t, Z.p, SZ.p, part.p, tk.p, nchunks, H.p, Mg.p);
+      launch_k(k_ritz_eig, 1, 128, (6 * t * t + t) * sizeof(double), s, t, H.p, Mg.p, U.p, lam.p, cs.p + C_F * t,
                                                                            status);
-      AMG_KCOUNT k_rotate<<<dim3(nblk(n, 256), 2), 256, 0, s>>>(n, t, Z.p, SZ.p, U.p);  // Z U, (S Z) U
+      launch_k(k_rotate, dim3(nblk(n, 256), 2), 256, 0, s, n, t, Z.p, SZ.p, U.p);  // Z U, (S Z) U
       AMG_LAUNCH_CHECK();
     }
     CDot a5{};
@@ -1868,14 +1892,14 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     a5.x[4] = Z.p; a5.y[4] = SZ.p;
     for (int q = 0; q < 5; ++q) a5.xs[q] = a5.ys[q] = n;
     AMG_TRY(cdots(n, t, 5, a5, out.p, CF_ALPHA, cs.p, skip.p, ctx, s));
-    AMG_KCOUNT k_b_zupd<<<nb, 256, 0, s>>>(n, t, Z.p, P.p, SZ.p, SP.p, cs.p, skip.p);
+    launch_k(k_b_zupd, nb, 256, 0, s, n, t, Z.p, P.p, SZ.p, SP.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
     CDot a2{};
     a2.x[0] = Z.p; a2.y[0] = Z.p;
     a2.x[1] = Z.p; a2.y[1] = SZ.p;
     a2.xs[0] = a2.ys[0] = a2.xs[1] = a2.ys[1] = n;
     AMG_TRY(cdots(n, t, 2, a2, out.p, CF_Q, cs.p, skip.p, ctx, s));
-    AMG_KCOUNT k_b_grad<<<nb, 256, 0, s>>>(n, t, Gv.p, SZ.p, Z.p, cs.p, skip.p);
+    launch_k(k_b_grad, nb, 256, 0, s, n, t, Gv.p, SZ.p, Z.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
     AMG_TRY(apply_s_cols(A, G, GT, t, Gv.p, SG.p, T1.p, T2.p, s));  // the one product with S
     CDot a1{};
@@ -1883,7 +1907,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
     a1.y[0] = SP.p;
     a1.xs[0] = a1.ys[0] = n;
     AMG_TRY(cdots(n, t, 1, a1, out.p, CF_BETA, cs.p, skip.p, ctx, s));
-    AMG_KCOUNT k_b_pupd<<<nb, 256, 0, s>>>(n, t, P.p, Gv.p, SP.p, SG.p, cs.p, skip.p);
+    launch_k(k_b_pupd, nb, 256, 0, s, n, t, P.p, Gv.p, SP.p, SG.p, cs.p, skip.p);
     AMG_LAUNCH_CHECK();
     return AMG_OK;
   };
@@ -1933,6 +1957,7 @@ int srqcg(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int kmax, int k_ri
 // w = (w - alpha_j v_j) - beta_{j-1} v_{j-1}
 __global__ void k_lz_ab(long n, double *__restrict__ w, const double *__restrict__ v, const double *__restrict__ vp,
                         const double *__restrict__ sc, int j) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = fma(-sc[j], v[i], w[i]);
@@ -1943,6 +1968,7 @@ __global__ void k_lz_ab(long n, double *__restrict__ w, const double *__restrict
 // w_i - sum_{k <= j} h_k v_k,i, k ascending (one classical Gram-Schmidt pass)
 __global__ void k_lz_reorth(long n, int j, double *__restrict__ w, const double *__restrict__ Vs,
                             const double *__restrict__ h) {
+  pdl_wait();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = w[i];
@@ -1971,36 +1997,36 @@ int lanczos(const DevBsr &A, const DevBsr &G, const DevBsr &GT, int m, uint64_t 
   AMG_TRY(sc.alloc(320));
   AMG_TRY(part.alloc((size_t)((n + CHUNK - 1) / CHUNK + 1) * 66));
   AMG_TRY(sc.zero(s));
-  AMG_KCOUNT k_set_neg<<<1, 1, 0, s>>>(sc.p + 128);
-  AMG_KCOUNT k_lanczos_start<<<nblk(n, 256), 256, 0, s>>>(n, seed, (1ull << 62) | ((uint64_t)level << 40), Vs.p);
+  launch_k(k_set_neg, 1, 1, 0, s, sc.p + 128);
+  launch_k(k_lanczos_start, nblk(n, 256), 256, 0, s, n, seed, (1ull << 62) | ((uint64_t)level << 40), Vs.p);
   AMG_LAUNCH_CHECK();
   const DotCtx ctx{part.p, tk.p};
   AMG_TRY(dot1(n, Vs.p, Vs.p, sc.p + 129, ctx, s));
-  AMG_KCOUNT k_div_sqrt<<<nblk(n, 256), 256, 0, s>>>(n, Vs.p, sc.p + 129);
+  launch_k(k_div_sqrt, nblk(n, 256), 256, 0, s, n, Vs.p, sc.p + 129);
   for (int j = 0; j < m; ++j) {
     double *v = Vs.p + (size_t)j * n;
     AMG_TRY(spmv(GT, v, t1.p, s));
     AMG_TRY(spmv(A, t1.p, t2.p, s));
     AMG_TRY(spmv(G, t2.p, w.p, s));
     AMG_TRY(dot1(n, w.p, v, sc.p + j, ctx, s));
-    AMG_KCOUNT k_lz_ab<<<nblk(n, 256), 256, 0, s>>>(n, w.p, v, j > 0 ? v - n : nullptr, sc.p, j);
+    launch_k(k_lz_ab, nblk(n, 256), 256, 0, s, n, w.p, v, j > 0 ? v - n : nullptr, sc.p, j);
     CDot a{};
     a.x[0] = w.p;
     a.xs[0] = 0;
     a.y[0] = Vs.p;
     a.ys[0] = n;
     AMG_TRY(cdots(n, j + 1, 1, a, sc.p + 160, CF_NONE, nullptr, nullptr, ctx, s));
-    AMG_KCOUNT k_lz_reorth<<<nblk(n, 256), 256, 0, s>>>(n, j, w.p, Vs.p, sc.p + 160);
+    launch_k(k_lz_reorth, nblk(n, 256), 256, 0, s, n, j, w.p, Vs.p, sc.p + 160);
     Fin fb;
     fb.op = FIN_LZ_BETA;
     fb.sc = sc.p;
     fb.j = j;
     fb.m = m;
     AMG_TRY(dot1(n, w.p, w.p, sc.p + 129, ctx, s, fb));
-    if (j < m - 1) AMG_KCOUNT k_mul_by<<<nblk(n, 256), 256, 0, s>>>(n, v + n, w.p, sc.p + 256 + j);
+    if (j < m - 1) launch_k(k_mul_by, nblk(n, 256), 256, 0, s, n, v + n, w.p, sc.p + 256 + j);
     AMG_LAUNCH_CHECK();
   }
-  AMG_KCOUNT k_lanczos_bisect<<<1, 32, 0, s>>>(m, sc.p, safety, d_out);
+  launch_k(k_lanczos_bisect, 1, 32, 0, s, m, sc.p, safety, d_out);
   AMG_LAUNCH_CHECK();
   // the temporaries above are returned to the pool in the order of s
   if (sync) AMG_CU(cudaStreamSynchronize(s));
@@ -2028,6 +2054,7 @@ __device__ __forceinline__ double fro2(const double *M) {
 
 template <int B>
 __global__ void k_soc_nrm(int nn, int t, const double *__restrict__ V, double *__restrict__ nrm) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nn) return;
   double M[B * B];
@@ -2072,6 +2099,7 @@ __device__ __forceinline__ void soc_entry(int nn, int t, int I, int k, const int
 template <int B>
 __global__ void k_soc_pairs(int nn, int nnzb, int t, const int *__restrict__ rp, const int *__restrict__ col,
                             const double *__restrict__ V, const double *__restrict__ nrm, double *__restrict__ soc) {
+  pdl_wait();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnzb) return;
   int lo = 0, hi = nn - 1;
@@ -2087,6 +2115,7 @@ template <int B>
 __global__ void k_soc_pairs_rows(int nn, int t, const int *__restrict__ rp, const int *__restrict__ col,
                                  const double *__restrict__ V, const double *__restrict__ nrm,
                                  double *__restrict__ soc) {
+  pdl_wait();
   const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (I >= nn) return;
   for (int k = rp[I] + lane; k < rp[I + 1]; k += 32) soc_entry<B>(nn, t, I, k, rp, col, V, nrm, soc);
@@ -2098,6 +2127,7 @@ __global__ void k_soc_pairs_rows(int nn, int t, const int *__restrict__ rp, cons
 // is the smaller column).
 __global__ void k_soc_select(int nn, const int *__restrict__ rp, const int *__restrict__ col,
                              const double *__restrict__ soc, int theta, unsigned char *__restrict__ kept) {
+  pdl_wait();
   const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (I >= nn) return;
   const int k0 = rp[I], k1 = rp[I + 1];
@@ -2127,6 +2157,7 @@ __global__ void k_soc_select(int nn, const int *__restrict__ rp, const int *__re
 
 __global__ void k_strong(int nn, const int *__restrict__ rp, const int *__restrict__ col,
                          const unsigned char *__restrict__ kept, unsigned char *__restrict__ strong) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nn) return;
   for (int k = rp[I]; k < rp[I + 1]; ++k) {
@@ -2152,16 +2183,16 @@ int soc_filter(const DevBsr &A, int t, const double *V, int theta, unsigned char
   const bool rows = A.nr < 32768;
   const int nbr = nblk(32L * A.nr, 128), nbe = nblk(A.nnzb, 128);
   if (A.b == 1) {
-    AMG_KCOUNT k_soc_nrm<1><<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
-    if (rows) AMG_KCOUNT k_soc_pairs_rows<1><<<nbr, 128, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
-    else AMG_KCOUNT k_soc_pairs<1><<<nbe, 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+    launch_k(k_soc_nrm<1>, nb, 128, 0, s, A.nr, t, V, nrm.p);
+    if (rows) launch_k(k_soc_pairs_rows<1>, nbr, 128, 0, s, A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+    else launch_k(k_soc_pairs<1>, nbe, 128, 0, s, A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
   } else {
-    AMG_KCOUNT k_soc_nrm<3><<<nb, 128, 0, s>>>(A.nr, t, V, nrm.p);
-    if (rows) AMG_KCOUNT k_soc_pairs_rows<3><<<nbr, 128, 0, s>>>(A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
-    else AMG_KCOUNT k_soc_pairs<3><<<nbe, 128, 0, s>>>(A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+    launch_k(k_soc_nrm<3>, nb, 128, 0, s, A.nr, t, V, nrm.p);
+    if (rows) launch_k(k_soc_pairs_rows<3>, nbr, 128, 0, s, A.nr, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
+    else launch_k(k_soc_pairs<3>, nbe, 128, 0, s, A.nr, A.nnzb, t, A.rowptr.p, A.col.p, V, nrm.p, soc.p);
   }
-  AMG_KCOUNT k_soc_select<<<nblk(32L * A.nr, 128), 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, soc.p, theta, kept.p);
-  AMG_KCOUNT k_strong<<<nb, 128, 0, s>>>(A.nr, A.rowptr.p, A.col.p, kept.p, strong);
+  launch_k(k_soc_select, nblk(32L * A.nr, 128), 128, 0, s, A.nr, A.rowptr.p, A.col.p, soc.p, theta, kept.p);
+  launch_k(k_strong, nb, 128, 0, s, A.nr, A.rowptr.p, A.col.p, kept.p, strong);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -2228,6 +2259,7 @@ __global__ void k_dpls(int nf, const int *__restrict__ fnodes, long n, int t, co
                        double *__restrict__ Vt, unsigned char *__restrict__ taken, int n_max, double kappa_p,
                        int nsel_cap, int *__restrict__ out_cnt, int *__restrict__ out_col,
                        double *__restrict__ out_val) {
+  pdl_wait();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
   const int I = fnodes[f];
@@ -2355,10 +2387,10 @@ int dpls(const DevBsr &A, const unsigned char *strong, const int *cf, const int 
   AMG_TRY(taken.alloc(total));
   const int cap = n_max < t / B ? n_max : t / B;
   if (B == 1)
-    AMG_KCOUNT k_dpls<1><<<nblk(nf, 64), 64, 0, s>>>(nf, fnodes, (long)A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p,
+    launch_k(k_dpls<1>, nblk(nf, 64), 64, 0, s, nf, fnodes, (long)A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p,
                                                     n_max, kappa_p, cap > 0 ? cap : 1, out_cnt, out_col, out_val);
   else
-    AMG_KCOUNT k_dpls<3><<<nblk(nf, 64), 64, 0, s>>>(nf, fnodes, 3L * A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p,
+    launch_k(k_dpls<3>, nblk(nf, 64), 64, 0, s, nf, fnodes, 3L * A.nr, t, V, cand_ptr, cand, cidx, Vt.p, taken.p,
                                                     n_max, kappa_p, cap > 0 ? cap : 1, out_cnt, out_col, out_val);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
@@ -2375,6 +2407,7 @@ template <int B>
 __global__ void k_spgemm(int nr, const int *__restrict__ xr, const int *__restrict__ xc, const double *__restrict__ xv,
                          const int *__restrict__ yr, const int *__restrict__ yc, const double *__restrict__ yv,
                          const int *__restrict__ zr, const int *__restrict__ zc, double *__restrict__ zv, int nnz) {
+  pdl_wait();
   constexpr int BB = B * B, PER = 32 / BB;  // output blocks per warp
   const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -2423,6 +2456,7 @@ __global__ void __launch_bounds__(32) k_spgemm_rows(const int *__restrict__ xr, 
                                                     const int *__restrict__ yc, const double *__restrict__ yv,
                                                     const int *__restrict__ zr, const int *__restrict__ zc,
                                                     double *__restrict__ zv) {
+  pdl_wait();
   constexpr int BB = B * B;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ double sacc[];  // len * BB accumulators, then len columns
@@ -2496,20 +2530,18 @@ int spgemm_numeric(const DevBsr &X, const DevBsr &Y, DevBsr &Z, cudaStream_t s) 
   // output block)
   if (Z.nr >= 4096 && shm <= 48 * 1024) {
     if (Z.b == 1)
-      AMG_KCOUNT k_spgemm_rows<1><<<Z.nr, 32, shm, s>>>(X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
+      launch_k(k_spgemm_rows<1>, Z.nr, 32, shm, s, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
                                                        Z.rowptr.p, Z.col.p, Z.val.p);
     else
-      AMG_KCOUNT k_spgemm_rows<3><<<Z.nr, 32, shm, s>>>(X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
+      launch_k(k_spgemm_rows<3>, Z.nr, 32, shm, s, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p,
                                                        Z.rowptr.p, Z.col.p, Z.val.p);
     AMG_LAUNCH_CHECK();
     return AMG_OK;
   }
   if (Z.b == 1)
-    AMG_KCOUNT k_spgemm<1><<<nblk(32L * ((Z.nnzb + 31) / 32), 128), 128, 0, s>>>(
-        Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p, Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
+    launch_k(k_spgemm<1>, nblk(32L * ((Z.nnzb + 31) / 32), 128), 128, 0, s, Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p, Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
   else
-    AMG_KCOUNT k_spgemm<3><<<nblk(32L * ((Z.nnzb + 2) / 3), 128), 128, 0, s>>>(
-        Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p, Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
+    launch_k(k_spgemm<3>, nblk(32L * ((Z.nnzb + 2) / 3), 128), 128, 0, s, Z.nr, X.rowptr.p, X.col.p, X.val.p, Y.rowptr.p, Y.col.p, Y.val.p, Z.rowptr.p, Z.col.p, Z.val.p, Z.nnzb);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }

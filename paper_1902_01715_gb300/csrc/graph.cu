@@ -16,6 +16,7 @@ static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 // 1024 threads: each sums a contiguous chunk, the chunk sums are scanned in
 // shared memory, then each thread writes its chunk.
 __global__ void __launch_bounds__(1024) k_scan(int n, const int *__restrict__ in, int add, int *__restrict__ out) {
+  pdl_wait();
   __shared__ int part[1024];
   const int per = (n + 1023) / 1024;
   const int lo = (int)min((long)n, (long)threadIdx.x * per), hi = min(n, lo + per);
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(1024) k_scan(int n, const int *__restrict__ in
 }
 
 int dev_scan(int n, const int *in, int add, int *out, cudaStream_t s) {
-  AMG_KCOUNT k_scan<<<1, 1024, 0, s>>>(n, in, add, out);
+  launch_k(k_scan, 1, 1024, 0, s, n, in, add, out);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -51,6 +52,7 @@ int read_int(const int *d, int *h, cudaStream_t s) {
 
 // ---------------------------------------------------------------- longest row
 __global__ void k_row_max(int n, const int *__restrict__ rp, int *__restrict__ out) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int v = i < n ? rp[i + 1] - rp[i] : 0;
   for (int off = 16; off; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
@@ -63,7 +65,7 @@ int dev_row_max(int n, const int *rp, int *out, cudaStream_t s) {
   DBuf<int> d;
   AMG_TRY(d.alloc(1));
   AMG_TRY(d.zero(s));
-  AMG_KCOUNT k_row_max<<<nblk(n, 256), 256, 0, s>>>(n, rp, d.p);
+  launch_k(k_row_max, nblk(n, 256), 256, 0, s, n, rp, d.p);
   AMG_LAUNCH_CHECK();
   return read_int(d.p, out, s);
 }
@@ -80,6 +82,7 @@ int DevBsr::row_max(cudaStream_t s, int *out) const {
 // among the rows of that column (the rows of a column are distinct), so the
 // rows of T come out ascending whatever order the claims took.
 __global__ void k_tr_count(int nnzb, const int *__restrict__ col, int *__restrict__ cnt) {
+  pdl_wait();
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < nnzb) atomicAdd(&cnt[col[k]], 1);
 }
@@ -88,6 +91,7 @@ __global__ void k_tr_count(int nnzb, const int *__restrict__ col, int *__restric
 __global__ void k_tr_place(int nr, const int *__restrict__ rp, const int *__restrict__ col,
                            const int *__restrict__ trp, int *__restrict__ fill, int *__restrict__ trow,
                            int *__restrict__ tsrc) {
+  pdl_wait();
   const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (I >= nr) return;
   for (int k = rp[I] + lane; k < rp[I + 1]; k += 32) {
@@ -101,6 +105,7 @@ __global__ void k_tr_place(int nr, const int *__restrict__ rp, const int *__rest
 // one warp per column of A (row of T)
 __global__ void k_tr_rank(int nc, const int *__restrict__ trp, const int *__restrict__ trow,
                           const int *__restrict__ tsrc, int *__restrict__ tcol, int *__restrict__ perm) {
+  pdl_wait();
   const int c = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (c >= nc) return;
   const int b = trp[c], e = trp[c + 1];
@@ -117,6 +122,7 @@ __global__ void k_tr_rank(int nc, const int *__restrict__ trp, const int *__rest
 template <int B>
 __global__ void k_transpose_vals(int nnzb, const int *__restrict__ perm, const double *__restrict__ src,
                                  double *__restrict__ dst) {
+  pdl_wait();
   constexpr int BB = B * B;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long)BB * nnzb) return;
@@ -132,20 +138,20 @@ int transpose_bsr(const DevBsr &A, DevBsr &T, cudaStream_t s) {
   AMG_TRY(fill.alloc(A.nc));
   AMG_TRY(cnt.zero(s));
   AMG_TRY(fill.zero(s));
-  if (nnzb) AMG_KCOUNT k_tr_count<<<nblk(nnzb, 256), 256, 0, s>>>(nnzb, A.col.p, cnt.p);
+  if (nnzb) launch_k(k_tr_count, nblk(nnzb, 256), 256, 0, s, nnzb, A.col.p, cnt.p);
   AMG_LAUNCH_CHECK();
   AMG_TRY(dev_scan(A.nc, cnt.p, 0, T.rowptr.p, s));
   if (!nnzb) return AMG_OK;
   AMG_TRY(trow.alloc(nnzb));
   AMG_TRY(tsrc.alloc(nnzb));
   AMG_TRY(perm.alloc(nnzb));
-  AMG_KCOUNT k_tr_place<<<nblk(32L * A.nr, 256), 256, 0, s>>>(A.nr, A.rowptr.p, A.col.p, T.rowptr.p, fill.p,
+  launch_k(k_tr_place, nblk(32L * A.nr, 256), 256, 0, s, A.nr, A.rowptr.p, A.col.p, T.rowptr.p, fill.p,
                                                               trow.p, tsrc.p);
-  AMG_KCOUNT k_tr_rank<<<nblk(32L * A.nc, 256), 256, 0, s>>>(A.nc, T.rowptr.p, trow.p, tsrc.p, T.col.p, perm.p);
+  launch_k(k_tr_rank, nblk(32L * A.nc, 256), 256, 0, s, A.nc, T.rowptr.p, trow.p, tsrc.p, T.col.p, perm.p);
   if (A.b == 1)
-    AMG_KCOUNT k_transpose_vals<1><<<nblk((long)nnzb, 256), 256, 0, s>>>(nnzb, perm.p, A.val.p, T.val.p);
+    launch_k(k_transpose_vals<1>, nblk((long)nnzb, 256), 256, 0, s, nnzb, perm.p, A.val.p, T.val.p);
   else if (A.b == 3)
-    AMG_KCOUNT k_transpose_vals<3><<<nblk(9L * nnzb, 256), 256, 0, s>>>(nnzb, perm.p, A.val.p, T.val.p);
+    launch_k(k_transpose_vals<3>, nblk(9L * nnzb, 256), 256, 0, s, nnzb, perm.p, A.val.p, T.val.p);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -162,6 +168,7 @@ constexpr int SYM_MAXL = 32 * SYM_PER;
 __global__ void k_sym_merge(int nr, const int *__restrict__ xr, const int *__restrict__ xc,
                             const int *__restrict__ yr, const int *__restrict__ yc, const int *__restrict__ zr,
                             int *__restrict__ zc, int *__restrict__ cnt) {
+  pdl_wait();
   const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= nr) return;
@@ -203,6 +210,7 @@ __global__ void __launch_bounds__(256) k_sym_long(int nr, int nc, const int *__r
                                                   const int *__restrict__ yc, const int *__restrict__ zr,
                                                   int *__restrict__ zc, int *__restrict__ cnt,
                                                   unsigned *__restrict__ bm_all) {
+  pdl_wait();
   __shared__ int part[256];
   const int words = (nc + 31) >> 5;
   unsigned *bm = bm_all + (size_t)blockIdx.x * words;
@@ -268,10 +276,10 @@ int symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z, int b, cudaStr
   AMG_TRY(cnt.alloc(nr));
   AMG_TRY(rp.alloc(nr + 1));
   const int nb = nblk(32L * nr, 256);
-  if (nr) AMG_KCOUNT k_sym_merge<<<nb, 256, 0, s>>>(nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, nullptr, nullptr,
+  if (nr) launch_k(k_sym_merge, nb, 256, 0, s, nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, nullptr, nullptr,
                                                     cnt.p);
   if (longrows)
-    AMG_KCOUNT k_sym_long<false><<<nlong, 256, 0, s>>>(nr, Y.nc, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, nullptr,
+    launch_k(k_sym_long<false>, nlong, 256, 0, s, nr, Y.nc, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, nullptr,
                                                        nullptr, cnt.p, bm.p);
   AMG_TRY(dev_scan(nr, cnt.p, 0, rp.p, s));
   // entry count and longest row of Z in one read-back
@@ -279,7 +287,7 @@ int symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z, int b, cudaStr
   AMG_TRY(tail.alloc(2));
   AMG_TRY(tail.zero(s));
   AMG_CU(cudaMemcpyAsync(tail.p, rp.p + nr, sizeof(int), cudaMemcpyDeviceToDevice, s));
-  if (nr) AMG_KCOUNT k_row_max<<<nblk(nr, 256), 256, 0, s>>>(nr, rp.p, tail.p + 1);
+  if (nr) launch_k(k_row_max, nblk(nr, 256), 256, 0, s, nr, rp.p, tail.p + 1);
   AMG_LAUNCH_CHECK();
   int ht[2] = {0, 0};
   AMG_CU(cudaMemcpyAsync(ht, tail.p, sizeof ht, cudaMemcpyDeviceToHost, s));
@@ -288,10 +296,10 @@ int symbolic_product(const DevBsr &X, const DevBsr &Y, DevBsr &Z, int b, cudaStr
   AMG_TRY(Z.alloc(nr, Y.nc, nnz, b));
   Z.maxlen = ht[1];
   AMG_CU(cudaMemcpyAsync(Z.rowptr.p, rp.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  if (nr) AMG_KCOUNT k_sym_merge<<<nb, 256, 0, s>>>(nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, rp.p, Z.col.p,
+  if (nr) launch_k(k_sym_merge, nb, 256, 0, s, nr, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, rp.p, Z.col.p,
                                                     nullptr);
   if (longrows)
-    AMG_KCOUNT k_sym_long<true><<<nlong, 256, 0, s>>>(nr, Y.nc, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, rp.p,
+    launch_k(k_sym_long<true>, nlong, 256, 0, s, nr, Y.nc, X.rowptr.p, X.col.p, Y.rowptr.p, Y.col.p, rp.p,
                                                       Z.col.p, nullptr, bm.p);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -307,6 +315,7 @@ __global__ void k_keep(int nr, const int *__restrict__ rp, const int *__restrict
                        const unsigned char *__restrict__ strong, const int *__restrict__ cf,
                        const int *__restrict__ self, const int *__restrict__ orp, int *__restrict__ ocol,
                        int *__restrict__ cnt) {
+  pdl_wait();
   const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= nr) return;
   int n = 0;
@@ -333,13 +342,13 @@ static int keep_rows(int nr, int nc, const int *rp, const int *col, const unsign
   DBuf<int> zr;
   AMG_TRY(zr.alloc(nr + 1));
   const int nb = nblk(32L * nr, 256);
-  if (nr) AMG_KCOUNT k_keep<MODE><<<nb, 256, 0, s>>>(nr, rp, col, strong, cf, self, nullptr, nullptr, cnt.p);
+  if (nr) launch_k(k_keep<MODE>, nb, 256, 0, s, nr, rp, col, strong, cf, self, nullptr, nullptr, cnt.p);
   AMG_TRY(dev_scan(nr, cnt.p, 0, zr.p, s));
   int nnz = 0;
   AMG_TRY(read_int(zr.p + nr, &nnz, s));
   AMG_TRY(Z.alloc(nr, nc, nnz, 0));
   AMG_CU(cudaMemcpyAsync(Z.rowptr.p, zr.p, (nr + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  if (nr) AMG_KCOUNT k_keep<MODE><<<nb, 256, 0, s>>>(nr, rp, col, strong, cf, self, Z.rowptr.p, Z.col.p, nullptr);
+  if (nr) launch_k(k_keep<MODE>, nb, 256, 0, s, nr, rp, col, strong, cf, self, Z.rowptr.p, Z.col.p, nullptr);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }

@@ -37,7 +37,7 @@ StreamScope::StreamScope(cudaStream_t s) : prev(t_stream) { t_stream = s; }
 StreamScope::~StreamScope() { t_stream = prev; }
 static thread_local bool t_pdl = false;
 bool pdl_enabled() { return t_pdl; }
-PdlScope::PdlScope() : prev(t_pdl) { t_pdl = getenv("AMG_NO_PDL") == nullptr; }
+PdlScope::PdlScope(bool on) : prev(t_pdl) { t_pdl = on && getenv("AMG_NO_PDL") == nullptr; }
 PdlScope::~PdlScope() { t_pdl = prev; }
 
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
@@ -90,6 +90,7 @@ static void trace(const char *what, int level, double t0) {
 template <int B>
 __global__ void k_compact_vals(int n, int cap, const int *__restrict__ rowptr, const double *__restrict__ src,
                                double *__restrict__ dst) {
+  pdl_wait();
   constexpr int BB = B * B;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int I = (int)(t / (cap * BB));
@@ -105,6 +106,7 @@ __global__ void k_compact_vals(int n, int cap, const int *__restrict__ rowptr, c
 template <int B>
 __global__ void k_p_vals(int n, const int *__restrict__ rowptr, const int *__restrict__ fidx, int cap,
                          const double *__restrict__ fval, double *__restrict__ pv) {
+  pdl_wait();
   constexpr int BB = B * B;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int I = (int)(t / (cap * BB));
@@ -123,6 +125,7 @@ __global__ void k_p_vals(int n, const int *__restrict__ rowptr, const int *__res
 template <int B>
 __global__ void k_to_dense(int nr, const int *__restrict__ rp, const int *__restrict__ col,
                            const double *__restrict__ val, double *__restrict__ D) {
+  pdl_wait();
   constexpr int BB = B * B;
   const int I = blockIdx.x;
   const long m = (long)B * nr;
@@ -149,6 +152,7 @@ constexpr int CB = 32;
 // thread per entry); a pivot that is not positive sets status
 __global__ void __launch_bounds__(CB *CB) k_gj_pivot(int m, int k0, int nb, const double *__restrict__ D,
                                                      double *__restrict__ P, int *__restrict__ status) {
+  pdl_wait();
   __shared__ double a[CB][CB + 1];
   __shared__ double rinv;
   __shared__ int bad;
@@ -186,6 +190,7 @@ __global__ void __launch_bounds__(CB *CB) k_gj_pivot(int m, int k0, int nb, cons
 // C[i][q] = A[i][k0+q] (pivot column panel), for every i, j of the matrix
 __global__ void k_gj_panels(int m, int k0, int nb, const double *__restrict__ D, const double *__restrict__ P,
                             double *__restrict__ R, double *__restrict__ C) {
+  pdl_wait();
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long)CB * m) return;
   const int q = (int)(t / m), j = (int)(t % m);
@@ -200,6 +205,7 @@ __global__ void k_gj_panels(int m, int k0, int nb, const double *__restrict__ D,
 __global__ void __launch_bounds__(256) k_gj_update(int m, int k0, int nb, double *__restrict__ D,
                                                    const double *__restrict__ P, const double *__restrict__ R,
                                                    const double *__restrict__ C) {
+  pdl_wait();
   __shared__ double ct[CB][CB + 1], rt[CB][CB + 1];
   const int i0 = blockIdx.y * CB, j0 = blockIdx.x * CB;
   const bool kr = i0 == k0, kc = j0 == k0;
@@ -239,6 +245,7 @@ __device__ __forceinline__ bool mis_beats(int di, int i, int dj, int j) { return
 
 __global__ void k_mis_deg(int n, const int *__restrict__ rp, const int *__restrict__ col,
                           const unsigned char *__restrict__ strong, int *__restrict__ deg, int *__restrict__ state) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   int d = 0;
@@ -251,6 +258,7 @@ __global__ void k_mis_deg(int n, const int *__restrict__ rp, const int *__restri
 __global__ void k_mis_select(int n, const int *__restrict__ rp, const int *__restrict__ col,
                              const unsigned char *__restrict__ strong, const int *__restrict__ deg,
                              const int *__restrict__ state, unsigned char *__restrict__ flag, int *__restrict__ left) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   unsigned char f = 0;
@@ -269,6 +277,7 @@ __global__ void k_mis_select(int n, const int *__restrict__ rp, const int *__res
 __global__ void k_mis_apply(int n, const int *__restrict__ rp, const int *__restrict__ col,
                             const unsigned char *__restrict__ strong, const unsigned char *__restrict__ flag,
                             int *__restrict__ state) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n || state[I] != -1) return;
   if (flag[I]) {
@@ -295,7 +304,7 @@ static int mis_gpu(Level &L, const unsigned char *d_strong, cudaStream_t s) {
   AMG_TRY(flag.alloc(n));
   AMG_TRY(left.alloc(1));
   const int nb = nblk(n, 256);
-  AMG_KCOUNT k_mis_deg<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state);
+  launch_k(k_mis_deg, nb, 256, 0, s, n, A.rowptr.p, A.col.p, d_strong, deg.p, state);
   AMG_LAUNCH_CHECK();
   // rounds are queued four at a time between read-backs of the undecided
   // count of the last one (rounds after the last decision change nothing)
@@ -303,8 +312,8 @@ static int mis_gpu(Level &L, const unsigned char *d_strong, cudaStream_t s) {
   for (int round = 0;; round += kBatch) {
     for (int q = 0; q < kBatch; ++q) {
       AMG_TRY(left.zero(s));
-      AMG_KCOUNT k_mis_select<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, deg.p, state, flag.p, left.p);
-      AMG_KCOUNT k_mis_apply<<<nb, 256, 0, s>>>(n, A.rowptr.p, A.col.p, d_strong, flag.p, state);
+      launch_k(k_mis_select, nb, 256, 0, s, n, A.rowptr.p, A.col.p, d_strong, deg.p, state, flag.p, left.p);
+      launch_k(k_mis_apply, nb, 256, 0, s, n, A.rowptr.p, A.col.p, d_strong, flag.p, state);
     }
     AMG_LAUNCH_CHECK();
     int hl = 0;
@@ -320,6 +329,7 @@ static int mis_gpu(Level &L, const unsigned char *d_strong, cudaStream_t s) {
 
 // flag[I] = (cf[I] == want)
 __global__ void k_cf_flag(int n, const int *__restrict__ cf, int want, int *__restrict__ flag) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I < n) flag[I] = cf[I] == want;
 }
@@ -328,6 +338,7 @@ __global__ void k_cf_flag(int n, const int *__restrict__ cf, int want, int *__re
 // of I (or -1), fidx[I] = fine index of I (or -1), fnodes[fine index] = I.
 __global__ void k_cf_split(int n, const int *__restrict__ cf, const int *__restrict__ cs, const int *__restrict__ fs,
                            int *__restrict__ cidx, int *__restrict__ fidx, int *__restrict__ fnodes) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   const bool c = cf[I] == 1;
@@ -338,6 +349,7 @@ __global__ void k_cf_split(int n, const int *__restrict__ cf, const int *__restr
 
 // rows of the next level's starting test space: the B dofs of each coarse node
 __global__ void k_coarse_src(int n, int B, const int *__restrict__ cidx, int *__restrict__ src) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n || cidx[I] < 0) return;
   for (int c = 0; c < B; ++c) src[B * cidx[I] + c] = B * I + c;
@@ -366,6 +378,7 @@ static int galerkin(const DevBsr &A, const DevBsr &P, const DevBsr &R, DevBsr &A
 // set-up then stops with an error instead of handing on the pattern).
 __global__ void k_fsai_cols(int n, int maxg, const int *__restrict__ np, const int *__restrict__ pat,
                             const int *__restrict__ rp, int *__restrict__ col, int *__restrict__ bad) {
+  pdl_wait();
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int I = (int)(t / (maxg + 1)), j = (int)(t % (maxg + 1));
   if (I >= n || j > np[I]) return;
@@ -412,11 +425,11 @@ static int run_fsai(const DevBsr &A, const DevBsr *Gs, int k, int rho, double ep
   AMG_CU(cudaMemcpyAsync(G.rowptr.p, rp.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
   const long nt = (long)n * (maxg + 1);
   AMG_TRY(status.zero(s));
-  if (n) AMG_KCOUNT k_fsai_cols<<<nblk(nt, 256), 256, 0, s>>>(n, maxg, np.p, pat.p, G.rowptr.p, G.col.p, status.p);
+  if (n) launch_k(k_fsai_cols, nblk(nt, 256), 256, 0, s, n, maxg, np.p, pat.p, G.rowptr.p, G.col.p, status.p);
   if (A.b == 1)
-    AMG_KCOUNT k_compact_vals<1><<<nblk(nt, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
+    launch_k(k_compact_vals<1>, nblk(nt, 256), 256, 0, s, n, maxg + 1, G.rowptr.p, val.p, G.val.p);
   else
-    AMG_KCOUNT k_compact_vals<3><<<nblk(nt * 9, 256), 256, 0, s>>>(n, maxg + 1, G.rowptr.p, val.p, G.val.p);
+    launch_k(k_compact_vals<3>, nblk(nt * 9, 256), 256, 0, s, n, maxg + 1, G.rowptr.p, val.p, G.val.p);
   AMG_LAUNCH_CHECK();
   AMG_TRY(read_int(status.p, &st, s));
   if (st) {
@@ -536,6 +549,7 @@ __global__ void __launch_bounds__(128) k_dpls_cand(int nf, const int *__restrict
                                                    const unsigned char *__restrict__ strong,
                                                    const int *__restrict__ cf, const int *__restrict__ cptr,
                                                    int *__restrict__ cand, int *__restrict__ cnt) {
+  pdl_wait();
   constexpr int PER = 8, MAXL = 32 * PER;
   __shared__ int nbr[4][MAXL];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -584,6 +598,7 @@ __global__ void __launch_bounds__(128) k_dpls_cand(int nf, const int *__restrict
 
 // P row lengths: 1 for a coarse node, its DPLS count for a fine node
 __global__ void k_p_len(int n, const int *__restrict__ fidx, const int *__restrict__ cnt, int *__restrict__ len) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I < n) len[I] = fidx[I] < 0 ? 1 : cnt[fidx[I]];
 }
@@ -591,6 +606,7 @@ __global__ void k_p_len(int n, const int *__restrict__ fidx, const int *__restri
 // P columns: the coarse index of a coarse node, the DPLS columns of a fine one
 __global__ void k_p_cols(int n, int cap, const int *__restrict__ cidx, const int *__restrict__ fidx,
                          const int *__restrict__ fcol, const int *__restrict__ rp, int *__restrict__ col) {
+  pdl_wait();
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int I = (int)(t / cap), j = (int)(t % cap);
   if (I >= n || j >= rp[I + 1] - rp[I]) return;
@@ -610,16 +626,16 @@ static int split_nodes(const Level &L, CfSplit &c, cudaStream_t s) {
   AMG_TRY(cs.alloc(n + 1));
   AMG_TRY(fs.alloc(n + 1));
   const int nb = nblk(n, 256);
-  if (n) AMG_KCOUNT k_cf_flag<<<nb, 256, 0, s>>>(n, L.cf.p, 1, flag.p);
+  if (n) launch_k(k_cf_flag, nb, 256, 0, s, n, L.cf.p, 1, flag.p);
   AMG_TRY(dev_scan(n, flag.p, 0, cs.p, s));
-  if (n) AMG_KCOUNT k_cf_flag<<<nb, 256, 0, s>>>(n, L.cf.p, 0, flag.p);
+  if (n) launch_k(k_cf_flag, nb, 256, 0, s, n, L.cf.p, 0, flag.p);
   AMG_TRY(dev_scan(n, flag.p, 0, fs.p, s));
   AMG_TRY(read_int(cs.p + n, &c.nc, s));
   c.nf = n - c.nc;
   AMG_TRY(c.cidx.alloc(n));
   AMG_TRY(c.fidx.alloc(n));
   AMG_TRY(c.fnodes.alloc(c.nf));
-  if (n) AMG_KCOUNT k_cf_split<<<nb, 256, 0, s>>>(n, L.cf.p, cs.p, fs.p, c.cidx.p, c.fidx.p, c.fnodes.p);
+  if (n) launch_k(k_cf_split, nb, 256, 0, s, n, L.cf.p, cs.p, fs.p, c.cidx.p, c.fidx.p, c.fnodes.p);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -642,14 +658,14 @@ static int build_P(Handle *h, Level &L, const unsigned char *d_strong, const CfS
   AMG_TRY(L.A.row_max(s, &maxdeg));
   if (nf && p.d_p <= 2 && maxdeg < 256) {
     const int nb = nblk(32L * nf, 128);
-    AMG_KCOUNT k_dpls_cand<<<nb, 128, 0, s>>>(nf, c.fnodes.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, L.cf.p,
+    launch_k(k_dpls_cand, nb, 128, 0, s, nf, c.fnodes.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, L.cf.p,
                                               nullptr, nullptr, d_cnt.p);
     AMG_LAUNCH_CHECK();
     AMG_TRY(dev_scan(nf, d_cnt.p, 0, d_cptr.p, s));
     int ncand = 0;
     AMG_TRY(read_int(d_cptr.p + nf, &ncand, s));
     AMG_TRY(d_cand.alloc(ncand));
-    AMG_KCOUNT k_dpls_cand<<<nb, 128, 0, s>>>(nf, c.fnodes.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, L.cf.p,
+    launch_k(k_dpls_cand, nb, 128, 0, s, nf, c.fnodes.p, p.d_p, L.A.rowptr.p, L.A.col.p, d_strong, L.cf.p,
                                               d_cptr.p, d_cand.p, nullptr);
     AMG_LAUNCH_CHECK();
   } else if (nf) {  // longer rows or a larger distance: products of patterns
@@ -665,20 +681,20 @@ static int build_P(Handle *h, Level &L, const unsigned char *d_strong, const CfS
   DBuf<int> len, rp;
   AMG_TRY(len.alloc(n));
   AMG_TRY(rp.alloc(n + 1));
-  if (n) AMG_KCOUNT k_p_len<<<nblk(n, 256), 256, 0, s>>>(n, c.fidx.p, d_cnt.p, len.p);
+  if (n) launch_k(k_p_len, nblk(n, 256), 256, 0, s, n, c.fidx.p, d_cnt.p, len.p);
   AMG_TRY(dev_scan(n, len.p, 0, rp.p, s));
   int nnz = 0;
   AMG_TRY(read_int(rp.p + n, &nnz, s));
   AMG_TRY(L.P.alloc(n, c.nc, nnz, B));
   AMG_CU(cudaMemcpyAsync(L.P.rowptr.p, rp.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
   if (n)
-    AMG_KCOUNT k_p_cols<<<nblk((long)n * cap, 256), 256, 0, s>>>(n, cap, c.cidx.p, c.fidx.p, d_col.p, L.P.rowptr.p,
+    launch_k(k_p_cols, nblk((long)n * cap, 256), 256, 0, s, n, cap, c.cidx.p, c.fidx.p, d_col.p, L.P.rowptr.p,
                                                                   L.P.col.p);
   if (B == 1)
-    AMG_KCOUNT k_p_vals<1><<<nblk((long)n * cap, 256), 256, 0, s>>>(n, L.P.rowptr.p, c.fidx.p, cap, d_val.p,
+    launch_k(k_p_vals<1>, nblk((long)n * cap, 256), 256, 0, s, n, L.P.rowptr.p, c.fidx.p, cap, d_val.p,
                                                                      L.P.val.p);
   else
-    AMG_KCOUNT k_p_vals<3><<<nblk((long)n * cap * 9, 256), 256, 0, s>>>(n, L.P.rowptr.p, c.fidx.p, cap, d_val.p,
+    launch_k(k_p_vals<3>, nblk((long)n * cap * 9, 256), 256, 0, s, n, L.P.rowptr.p, c.fidx.p, cap, d_val.p,
                                                                       L.P.val.p);
   AMG_LAUNCH_CHECK();
   AMG_CU(cudaStreamSynchronize(s));
@@ -704,14 +720,14 @@ static int coarse_factor(Handle *h, Level &L) {
     AMG_TRY(R.alloc((size_t)CB * m));
     AMG_TRY(C.alloc((size_t)m * CB));
     double *D = h->Cinv.p;
-    if (L.A.b == 1) AMG_KCOUNT k_to_dense<1><<<L.n, 128, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
-    else AMG_KCOUNT k_to_dense<3><<<L.n, 288, 0, s>>>(L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
+    if (L.A.b == 1) launch_k(k_to_dense<1>, L.n, 128, 0, s, L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
+    else launch_k(k_to_dense<3>, L.n, 288, 0, s, L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
     const int nt = (m + CB - 1) / CB;
     for (int k0 = 0; k0 < m; k0 += CB) {
       const int nb = m - k0 < CB ? m - k0 : CB;
-      AMG_KCOUNT k_gj_pivot<<<1, CB * CB, 0, s>>>(m, k0, nb, D, Pk.p, st.p);
-      AMG_KCOUNT k_gj_panels<<<nblk((long)CB * m, 256), 256, 0, s>>>(m, k0, nb, D, Pk.p, R.p, C.p);
-      AMG_KCOUNT k_gj_update<<<dim3(nt, nt), 256, 0, s>>>(m, k0, nb, D, Pk.p, R.p, C.p);
+      launch_k(k_gj_pivot, 1, CB * CB, 0, s, m, k0, nb, D, Pk.p, st.p);
+      launch_k(k_gj_panels, nblk((long)CB * m, 256), 256, 0, s, m, k0, nb, D, Pk.p, R.p, C.p);
+      launch_k(k_gj_update, dim3(nt, nt), 256, 0, s, m, k0, nb, D, Pk.p, R.p, C.p);
     }
     AMG_LAUNCH_CHECK();
   }
@@ -731,6 +747,7 @@ static int coarse_factor(Handle *h, Level &L) {
 // valid row pointers.
 __global__ void k_check_pattern(int n, int nnzb, const int *__restrict__ rp, const int *__restrict__ col,
                                 int *__restrict__ bad) {
+  pdl_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I > n) return;
   if (I == n) {
@@ -760,6 +777,7 @@ void free_hierarchy(Handle *h) {
 
 int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *vals, int mem, int ntv0,
                     const double *V0, int memV, bool keep_pattern) {
+  PdlScope pdl;
   const amg_params &p = h->prm;
   cudaStream_t s = h->stream;
   const int t = p.n_tv;
@@ -793,7 +811,7 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     DBuf<int> bad;
     AMG_TRY(bad.alloc(1));
     AMG_CU(cudaMemcpyAsync(bad.p, &n, sizeof(int), cudaMemcpyHostToDevice, s));
-    AMG_KCOUNT k_check_pattern<<<nblk(n + 1, 256), 256, 0, s>>>(n, nnzb, L0->A.rowptr.p, L0->A.col.p, bad.p);
+    launch_k(k_check_pattern, nblk(n + 1, 256), 256, 0, s, n, nnzb, L0->A.rowptr.p, L0->A.col.p, bad.p);
     AMG_LAUNCH_CHECK();
     int hb = n;
     AMG_TRY(read_int(bad.p, &hb, s));
@@ -895,7 +913,7 @@ int build_hierarchy(Handle *h, const int *rowptr, const int *col, const double *
     {
       DBuf<int> dsrc;
       AMG_TRY(dsrc.alloc((size_t)B * nc));
-      AMG_KCOUNT k_coarse_src<<<nblk(L.n, 256), 256, 0, s>>>(L.n, B, split.cidx.p, dsrc.p);
+      launch_k(k_coarse_src, nblk(L.n, 256), 256, 0, s, L.n, B, split.cidx.p, dsrc.p);
       AMG_LAUNCH_CHECK();
       DBuf<double> Vn;
       AMG_TRY(Vn.alloc((size_t)B * nc * t));

@@ -24,6 +24,7 @@ namespace amg {
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
 int prepare_solve(Handle *h) {
+  PdlScope plain(false);  // the timed mappings read the layout just built
   cudaStream_t s = h->stream;
   const int prec = h->prm.vcycle_prec;
   const bool f64 = prec == AMG_FP64, f32 = prec != AMG_FP64, b16 = prec == AMG_FP32_BF16GP;
