@@ -521,7 +521,6 @@ constexpr int MGS_WARPS = 2;  // small CTAs: the chunks spread over all SMs
 
 __global__ void __launch_bounds__(32 * MGS_WARPS) k_mgs_coop(int n, int t, int nchunks, double *__restrict__ V,
                                                              double *__restrict__ part, unsigned *bar) {
-  pdl_wait();
   __shared__ double ssc[TMAXD + 1];
   __shared__ int fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -925,7 +924,6 @@ __global__ void k_block_transpose_index(int n, const int *__restrict__ rp, const
 
 template <int B, int NG>
 __global__ void __launch_bounds__(128) k_fsai(FsaiK K) {
-  pdl_wait();
   constexpr int GL = 32 / NG;
   static_assert(GL >= B, "a slot needs a lane per dof row of a node");
   constexpr unsigned lowmask = GL == 32 ? 0xffffffffu : ((1u << (GL & 31)) - 1u);

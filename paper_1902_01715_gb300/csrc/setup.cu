@@ -136,101 +136,147 @@ __global__ void k_to_dense(int nr, const int *__restrict__ rp, const int *__rest
   }
 }
 
-// Explicit inverse of the last level's matrix by blocked Gauss-Jordan
-// elimination, in place in a dense row-major m x m array, pivot blocks of CB
-// columns.  No pivoting is needed: every pivot block is a Schur complement of
-// an SPD matrix, hence SPD.  Step k (block rows/columns [k0, k0+nb)):
-// P = A_kk^{-1}; R = P A_kj and C = A_ik (copies of the pivot row and column
-// panels); then A_ij -= C_i R_j for i, j outside the block, A_ik = -C_i P,
-// A_kj = R_j and A_kk = P.  The coarse solve is then one dense product with
-// the (symmetric) inverse.  Each step's update is m^2 CB independent
-// multiply-adds spread over all SMs; only the CB x CB pivot inversion is
-// serial.
+// Explicit inverse of the last level's matrix by blocked sweeps (the
+// symmetric form of Gauss-Jordan elimination), in place in a dense row-major
+// m x m array of which only the lower triangle (i >= j) is kept current.
+// Sweeping the pivot block K (indices [k0, k0+nb)) of a symmetric matrix:
+// D = A_KK^{-1}; A_IJ -= A_IK D A_KJ for I, J outside K; A_IK = A_IK D;
+// A_KJ = D A_KJ; A_KK = -D.  The matrix stays symmetric, and once every
+// block has been swept it holds -A^{-1}; each pivot block is then a Schur
+// complement of an SPD matrix, hence SPD (no pivoting).  With the pivot
+// column C_J = A_JK (read from the lower triangle) and V_J = D C_J^T, step K
+// is A_IJ -= C_I V_J on the lower tiles, A_IK = V_I^T, A_KJ = V_J and
+// A_KK = -D; a last pass negates the lower triangle and mirrors it.  Half
+// the multiply-adds of Gauss-Jordan on the full array.  The coarse solve is
+// then one dense product with the inverse.
 constexpr int CB = 32;
+constexpr int SW_THREADS = 544;  // 17 warps: one thread per lower entry of a 32 x 32 block
 
-// P = A_kk^{-1} by scalar Gauss-Jordan in shared memory (one CTA, one
-// thread per entry); a pivot that is not positive sets status
-__global__ void __launch_bounds__(CB *CB) k_gj_pivot(int m, int k0, int nb, const double *__restrict__ D,
-                                                     double *__restrict__ P, int *__restrict__ status) {
+// P = A_KK^{-1} by scalar sweeps of the diagonal tile in shared memory, one
+// thread per lower entry, two buffers (a step reads one and writes the
+// other: one barrier per step).  The thread of the next pivot forms its
+// reciprocal as soon as it has the pivot, while the others update their
+// entries; a pivot that is not positive sets status.
+__global__ void __launch_bounds__(SW_THREADS) k_sw_pivot(int m, int k0, int nb, const double *__restrict__ D,
+                                                        double *__restrict__ P, int *__restrict__ status) {
   pdl_wait();
-  __shared__ double a[CB][CB + 1];
-  __shared__ double rinv;
+  __shared__ double a[2][CB][CB + 1];
+  __shared__ double rcp[2];
   __shared__ int bad;
-  const int r = threadIdx.x / CB, c = threadIdx.x % CB;
-  if (threadIdx.x == 0) bad = 0;
-  if (r < nb && c < nb) a[r][c] = D[(size_t)(k0 + r) * m + k0 + c];
-  for (int j = 0; j < nb; ++j) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double pv = a[j][j];
-      if (!(pv > 0.0)) bad = 1;
-      rinv = 1.0 / pv;
-    }
-    __syncthreads();
-    if (bad) break;
-    if (r == j && c < nb) a[j][c] = (c == j) ? rinv : a[j][c] * rinv;
-    __syncthreads();
-    double f = 0.0, rowj = 0.0;
-    if (r < nb && c < nb && r != j) {
-      f = a[r][j];
-      rowj = a[j][c];
-    }
-    __syncthreads();
-    if (r < nb && c < nb && r != j) a[r][c] = (c == j) ? -f * rinv : fma(-f, rowj, a[r][c]);
+  const int t = threadIdx.x;
+  int r = 0;  // lower entry t in row order: (r, c), c <= r
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  const int c = t - r * (r + 1) / 2;
+  const bool own = r < nb;
+  if (t == 0) bad = 0;
+  if (own) a[0][r][c] = D[(size_t)(k0 + r) * m + k0 + c];
+  __syncthreads();
+  if (t == 0) {
+    const double pv = a[0][0][0];
+    if (!(pv > 0.0)) bad = 1;
+    rcp[0] = 1.0 / pv;
   }
   __syncthreads();
+  for (int j = 0; j < nb && !bad; ++j) {
+    const int cur = j & 1, nxt = cur ^ 1;
+    const double d = rcp[cur];
+    if (own) {
+      // column j of the current matrix: entry x is stored at (max(x, j), min(x, j))
+      const double gr = r >= j ? a[cur][r][j] : a[cur][j][r];
+      const double gc = c >= j ? a[cur][c][j] : a[cur][j][c];
+      double nv;
+      if (r == j && c == j) nv = -d;
+      else if (r == j) nv = gc * d;
+      else if (c == j) nv = gr * d;
+      else nv = fma(-(gr * d), gc, a[cur][r][c]);
+      a[nxt][r][c] = nv;
+      if (r == j + 1 && c == j + 1 && j + 1 < nb) {  // the next pivot
+        if (!(nv > 0.0)) bad = 1;
+        rcp[nxt] = 1.0 / nv;
+      }
+    }
+    __syncthreads();
+  }
   if (bad) {
-    if (threadIdx.x == 0) atomicMin(status, AMG_ERR_NOT_SPD);
+    if (t == 0) atomicMin(status, AMG_ERR_NOT_SPD);
     return;
   }
-  if (r < nb && c < nb) P[r * CB + c] = a[r][c];
+  if (own) {  // the sweeps leave -A_KK^{-1}
+    const double v = -a[nb & 1][r][c];
+    P[r * CB + c] = v;
+    P[c * CB + r] = v;
+  }
 }
 
-// R[q][j] = sum_p P[q][p] A[k0+p][j] (pivot row panel times P) and
-// C[i][q] = A[i][k0+q] (pivot column panel), for every i, j of the matrix
-__global__ void k_gj_panels(int m, int k0, int nb, const double *__restrict__ D, const double *__restrict__ P,
-                            double *__restrict__ R, double *__restrict__ C) {
+// C[x][q] = A[x][k0+q] (pivot column, from the lower triangle) and
+// V[q][x] = sum_p P[q][p] C[x][p], for every row x outside the pivot block
+__global__ void k_sw_panels(int m, int k0, int nb, const double *__restrict__ D, const double *__restrict__ P,
+                            double *__restrict__ V, double *__restrict__ C) {
   pdl_wait();
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long)CB * m) return;
-  const int q = (int)(t / m), j = (int)(t % m);
-  if (q >= nb) return;
+  const int q = (int)(t / m), x = (int)(t % m);
+  if (q >= nb || (x >= k0 && x < k0 + nb)) return;
+  const bool below = x >= k0 + nb;
   double s = 0.0;
-  for (int p = 0; p < nb; ++p) s = fma(P[q * CB + p], D[(size_t)(k0 + p) * m + j], s);
-  R[(size_t)q * m + j] = s;
-  C[(size_t)j * CB + q] = D[(size_t)j * m + k0 + q];
+  for (int p = 0; p < nb; ++p) {
+    const double cx = below ? D[(size_t)x * m + k0 + p] : D[(size_t)(k0 + p) * m + x];
+    s = fma(P[q * CB + p], cx, s);
+  }
+  V[(size_t)q * m + x] = s;
+  C[(size_t)x * CB + q] = below ? D[(size_t)x * m + k0 + q] : D[(size_t)(k0 + q) * m + x];
 }
 
-// every entry of the matrix for step k, 32 x 32 tiles, 256 threads (4 rows each)
-__global__ void __launch_bounds__(256) k_gj_update(int m, int k0, int nb, double *__restrict__ D,
-                                                   const double *__restrict__ P, const double *__restrict__ R,
+// one lower tile (I >= J) per CTA, 32 x 32, 256 threads (4 rows each):
+// A_IJ -= C_I V_J; the pivot row and column tiles take V_J and V_I^T, the
+// pivot tile -P
+__global__ void __launch_bounds__(256) k_sw_update(int m, int k0, int nb, double *__restrict__ D,
+                                                   const double *__restrict__ P, const double *__restrict__ V,
                                                    const double *__restrict__ C) {
   pdl_wait();
-  __shared__ double ct[CB][CB + 1], rt[CB][CB + 1];
-  const int i0 = blockIdx.y * CB, j0 = blockIdx.x * CB;
+  __shared__ double ct[CB][CB + 1], vt[CB][CB + 1];
+  const int b = blockIdx.x;
+  int I = 0;  // lower tile b in row order: (I, J), J <= I
+  while ((I + 1) * (I + 2) / 2 <= b) ++I;
+  const int J = b - I * (I + 1) / 2;
+  const int i0 = I * CB, j0 = J * CB;
   const bool kr = i0 == k0, kc = j0 == k0;
   const int tx = threadIdx.x % CB, ty = threadIdx.x / CB;  // column, first row
-  for (int e = threadIdx.x; e < CB * CB; e += 256) {
-    const int a = e / CB, b = e % CB;
-    // C rows of this tile; R columns of this tile (P for the pivot column)
-    ct[a][b] = (i0 + a < m && b < nb) ? C[(size_t)(i0 + a) * CB + b] : 0.0;
-    rt[a][b] = (a < nb && j0 + b < m) ? (kc ? (b < nb ? P[a * CB + b] : 0.0) : R[(size_t)a * m + j0 + b]) : 0.0;
+  if (!kr && !kc) {
+    for (int e = threadIdx.x; e < CB * CB; e += 256) {
+      const int a = e / CB, q = e % CB;
+      ct[a][q] = (i0 + a < m && q < nb) ? C[(size_t)(i0 + a) * CB + q] : 0.0;
+      vt[a][q] = (a < nb && j0 + q < m) ? V[(size_t)a * m + j0 + q] : 0.0;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int j = j0 + tx;
   if (j >= m) return;
   for (int rr = ty; rr < CB; rr += 8) {
     const int i = i0 + rr;
     if (i >= m) break;
     double *dij = D + (size_t)i * m + j;
-    if (kr) {
-      if (tx < CB) *dij = kc ? (tx < nb && rr < nb ? P[rr * CB + tx] : *dij) : R[(size_t)rr * m + j];
-      continue;
+    if (kr && kc) *dij = -P[rr * CB + tx];      // pivot tile
+    else if (kr) *dij = V[(size_t)rr * m + j];  // A_KJ = V_J
+    else if (kc) *dij = V[(size_t)tx * m + i];  // A_IK = V_I^T
+    else {
+      double s = 0.0;
+      for (int q = 0; q < nb; ++q) s = fma(ct[rr][q], vt[q][tx], s);
+      *dij -= s;
     }
-    double s = 0.0;
-    for (int q = 0; q < nb; ++q) s = fma(ct[rr][q], rt[q][tx], s);
-    *dij = kc ? -s : *dij - s;
   }
+}
+
+// A^{-1} from the swept array: the lower triangle negated and mirrored
+__global__ void k_sw_final(int m, double *__restrict__ D) {
+  pdl_wait();
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)m * m) return;
+  const int i = (int)(t / m), j = (int)(t % m);
+  if (j > i) return;
+  const double v = -D[(size_t)i * m + j];
+  D[(size_t)i * m + j] = v;
+  if (j < i) D[(size_t)j * m + i] = v;
 }
 
 // ---------------------------------------------------------------- graph work
@@ -709,7 +755,7 @@ static int coarse_factor(Handle *h, Level &L) {
     return AMG_ERR_COARSENING;
   }
   h->nL = m;
-  DBuf<double> Pk, R, C;
+  DBuf<double> Pk, V, C;
   DBuf<int> st;
   AMG_TRY(st.alloc(1));
   AMG_TRY(st.zero(s));
@@ -717,7 +763,7 @@ static int coarse_factor(Handle *h, Level &L) {
   AMG_TRY(h->Cinv.zero(s));
   if (L.n > 0) {
     AMG_TRY(Pk.alloc(CB * CB));
-    AMG_TRY(R.alloc((size_t)CB * m));
+    AMG_TRY(V.alloc((size_t)CB * m));
     AMG_TRY(C.alloc((size_t)m * CB));
     double *D = h->Cinv.p;
     if (L.A.b == 1) launch_k(k_to_dense<1>, L.n, 128, 0, s, L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
@@ -725,10 +771,13 @@ static int coarse_factor(Handle *h, Level &L) {
     const int nt = (m + CB - 1) / CB;
     for (int k0 = 0; k0 < m; k0 += CB) {
       const int nb = m - k0 < CB ? m - k0 : CB;
-      launch_k(k_gj_pivot, 1, CB * CB, 0, s, m, k0, nb, D, Pk.p, st.p);
-      launch_k(k_gj_panels, nblk((long)CB * m, 256), 256, 0, s, m, k0, nb, D, Pk.p, R.p, C.p);
-      launch_k(k_gj_update, dim3(nt, nt), 256, 0, s, m, k0, nb, D, Pk.p, R.p, C.p);
+      launch_k(k_sw_pivot, 1, SW_THREADS, 0, s, m, k0, nb, (const double *)D, Pk.p, st.p);
+      launch_k(k_sw_panels, nblk((long)CB * m, 256), 256, 0, s, m, k0, nb, (const double *)D, (const double *)Pk.p,
+               V.p, C.p);
+      launch_k(k_sw_update, nt * (nt + 1) / 2, 256, 0, s, m, k0, nb, D, (const double *)Pk.p, (const double *)V.p,
+               (const double *)C.p);
     }
+    launch_k(k_sw_final, nblk((long)m * m, 256), 256, 0, s, m, D);
     AMG_LAUNCH_CHECK();
   }
   int hs = 0;
