@@ -115,7 +115,7 @@ int amg_default_params(amg_params *p);
  * Algorithm 4 started from the near-null space V0 (padded to n_tv columns by
  * the counter generator, Sec. 3.2), the affinity C/F split of Sec. 3.3, the
  * DPLS prolongation of Algorithm 5 and A_{k+1} = P^T A P; on the last level
- * its dense explicit inverse (blocked Gauss-Jordan, pivot blocks of 32; the
+ * its dense explicit inverse (blocked symmetric sweeps, pivot blocks of 32; the
  * paper's Algorithm 1 uses a dense Cholesky factor, and both give the exact
  * coarse solve up to rounding).
  *   K: rowptr, colind, vals as described above, in `mem` memory; copied.

@@ -133,8 +133,9 @@ def test_vcycle_matches_oracle(A, orc, name):
 @pytest.mark.parametrize("name", list(SMALL))
 def test_coarse_explicit_inverse_error_bound(A, orc, name):
     """The last level is solved by one product with its explicit inverse
-    (blocked Gauss-Jordan).  For an SPD A_c of order m the computed inverse X
-    satisfies ||A_c X - I|| <= c_m u cond(A_c) (Gauss-Jordan / inversion error
+    (blocked symmetric sweeps, the symmetric form of Gauss-Jordan).  For an
+    SPD A_c of order m the computed inverse X satisfies
+    ||A_c X - I|| <= c_m u cond(A_c) (Gauss-Jordan / inversion error
     analysis, u = 2^-53), so z = X y has residual ||y - A_c z|| and forward
     error ||z - A_c^{-1} y|| / ||A_c^{-1} y|| within m u cond(A_c) (c_m = m
     taken as the constant).  Checked on the last level of each small
