@@ -258,7 +258,13 @@ void bsrmv(int ep, const SolveMat &M, const TM *v, const TX *x, TX *y, const TX 
 // y = epilogue(A x) on block rows [r0, r1) only, FP64 storage
 void bsrmv_rows(int ep, const SolveMat &M, const double *x, double *y, const double *aux, double w, int r0, int r1,
                 cudaStream_t s);
-int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s);
+// one matrix's sliced layout to build, with the storage types it needs
+struct SolveJob {
+  const DevBsr *A;
+  SolveMat *M;
+  bool f64, f32, b16;
+};
+int make_solvemats(const std::vector<SolveJob> &jobs, cudaStream_t s);
 int tune_solvemat(SolveMat &M, int kind, cudaStream_t s);  // kind 0 FP64, 1 FP32, 2 bf16
 const char *mapping_name(const SolveMat &M, bool f64);
 int mapping_wps(const SolveMat &M, bool f64);  // warps per slice of the chosen mapping

@@ -29,17 +29,24 @@ int prepare_solve(Handle *h) {
   const int prec = h->prm.vcycle_prec;
   const bool f64 = prec == AMG_FP64, f32 = prec != AMG_FP64, b16 = prec == AMG_FP32_BF16GP;
   const int kv = f64 ? 0 : 1, kg = f64 ? 0 : (b16 ? 2 : 1);
+  std::vector<SolveJob> jobs;
   for (int k = 0; k < h->nlev; ++k) {
     Level &L = *h->lev[k];
     // level 0 A is always kept in FP64 for the outer CG operator
-    AMG_TRY(make_solvemat(L.A, L.sA, f64 || k == 0, f32, false, s));
+    jobs.push_back({&L.A, &L.sA, f64 || k == 0, f32, false});
+    if (k < h->nlev - 1) {
+      jobs.push_back({&L.G, &L.sG, f64, f32 && !b16, b16});
+      jobs.push_back({&L.GT, &L.sGT, f64, f32 && !b16, b16});
+      jobs.push_back({&L.P, &L.sP, f64, f32 && !b16, b16});
+      jobs.push_back({&L.R, &L.sR, f64, f32 && !b16, b16});
+    }
+  }
+  AMG_TRY(make_solvemats(jobs, s));
+  for (int k = 0; k < h->nlev; ++k) {
+    Level &L = *h->lev[k];
     AMG_TRY(tune_solvemat(L.sA, kv, s));
     if (k == 0 && !f64) AMG_TRY(tune_solvemat(L.sA, 0, s));  // FP64 copy of the CG operator
     if (k < h->nlev - 1) {
-      AMG_TRY(make_solvemat(L.G, L.sG, f64, f32 && !b16, b16, s));
-      AMG_TRY(make_solvemat(L.GT, L.sGT, f64, f32 && !b16, b16, s));
-      AMG_TRY(make_solvemat(L.P, L.sP, f64, f32 && !b16, b16, s));
-      AMG_TRY(make_solvemat(L.R, L.sR, f64, f32 && !b16, b16, s));
       AMG_TRY(tune_solvemat(L.sG, kg, s));
       AMG_TRY(tune_solvemat(L.sGT, kg, s));
       AMG_TRY(tune_solvemat(L.sP, kg, s));

@@ -673,87 +673,134 @@ __global__ void k_slice_h(int nr, int ns, const int *__restrict__ rp, const int 
 // Rows by decreasing length inside windows of SELL_SIGMA rows, ties in row
 // order: the position of row r in its window is the number of rows of the
 // window that are longer, plus those before r that are as long.  One CTA of
-// SELL_SIGMA threads per window.
+// SELL_SIGMA threads per window sorts the keys (LMAX - length, index) -- all
+// distinct -- with a bitonic network in shared memory; the unused keys of a
+// short last window are all ones and sort behind the rows.
+static_assert(SELL_SIGMA == 1024, "the sort key holds the index in a window in 10 bits");
 __global__ void __launch_bounds__(SELL_SIGMA) k_sell_perm(int nr, const int *__restrict__ rp, int *__restrict__ prow) {
-  __shared__ int len[SELL_SIGMA];
+  constexpr unsigned LMAX = (1u << 22) - 1u;
+  __shared__ unsigned key[SELL_SIGMA];
   const int w0 = blockIdx.x * SELL_SIGMA, q = threadIdx.x;
   const int wn = min(SELL_SIGMA, nr - w0);
-  if (q < wn) len[q] = rp[w0 + q + 1] - rp[w0 + q];
+  unsigned kq = 0xffffffffu;
+  if (q < wn) {
+    const unsigned len = min((unsigned)(rp[w0 + q + 1] - rp[w0 + q]), LMAX);
+    kq = ((LMAX - len) << 10) | (unsigned)q;
+  }
+  key[q] = kq;
+  for (int k = 2; k <= SELL_SIGMA; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      __syncthreads();
+      const int p = q ^ j;
+      if (p > q) {
+        const unsigned a = key[q], b = key[p];
+        if ((a > b) == ((q & k) == 0)) {
+          key[q] = b;
+          key[p] = a;
+        }
+      }
+    }
   __syncthreads();
-  if (q >= wn) return;
-  const int L = len[q];
-  int at = 0;
-  for (int u = 0; u < wn; ++u) at += (len[u] > L) || (len[u] == L && u < q);
-  prow[w0 + at] = w0 + q;
+  if (q < wn) prow[w0 + q] = w0 + (int)(key[q] & 1023u);
 }
 
-int make_solvemat(const DevBsr &A, SolveMat &M, bool f64, bool f32, bool b16, cudaStream_t s) {
-  M.nr = A.nr;
-  M.nc = A.nc;
-  M.nnzb = A.nnzb;
-  M.b = A.b;
-  M.rowptr = A.rowptr.p;
-  M.col = A.col.p;
-  M.ns = (A.nr + 31) / 32;
+// Sliced layouts of several matrices at once.  The slot counts decide the
+// allocations, so they come back to the host: all matrices' slice heights
+// are formed first and read back together, then those of the matrices that
+// take the sorted row order, then every layout is filled -- two
+// synchronisations for the whole hierarchy instead of one or two per matrix.
+int make_solvemats(const std::vector<SolveJob> &jobs, cudaStream_t s) {
+  const int nj = (int)jobs.size();
+  if (nj == 0) return AMG_OK;
+  std::vector<DBuf<int>> hsl(nj);
+  DBuf<unsigned long long> tot;
+  AMG_TRY(tot.alloc(2 * (size_t)nj));
+  AMG_CU(cudaMemsetAsync(tot.p, 0, 2 * (size_t)nj * sizeof(unsigned long long), s));
+  std::vector<unsigned long long> slots(2 * (size_t)nj, 0ULL);
+  auto heights = [&](int i, const int *prow, unsigned long long *t) {
+    const SolveMat &M = *jobs[i].M;
+    if (M.ns)
+      AMG_KCOUNT k_slice_h<<<nblk(32L * M.ns, 256), 256, 0, s>>>(M.nr, M.ns, M.rowptr, prow, hsl[i].p, t);
+  };
+  for (int i = 0; i < nj; ++i) {
+    const DevBsr &A = *jobs[i].A;
+    SolveMat &M = *jobs[i].M;
+    M.nr = A.nr;
+    M.nc = A.nc;
+    M.nnzb = A.nnzb;
+    M.b = A.b;
+    M.rowptr = A.rowptr.p;
+    M.col = A.col.p;
+    M.ns = (A.nr + 31) / 32;
+    M.prow.release();
+    AMG_TRY(hsl[i].alloc(M.ns));
+    heights(i, nullptr, tot.p + i);
+  }
+  AMG_LAUNCH_CHECK();
+  AMG_CU(cudaMemcpyAsync(slots.data(), tot.p, (size_t)nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  AMG_CU(cudaStreamSynchronize(s));
   // Rows by decreasing length inside each window of SELL_SIGMA rows (ties in
   // row order), for FP64 storage only and only where the natural order fills
   // the slices poorly: FP64 instructions cost the same with idle lanes, while
   // the bandwidth-bound FP32/bf16 products lose more to the scattered row
   // order than they gain.
-  DBuf<int> hsl;
-  DBuf<unsigned long long> tot;
-  AMG_TRY(hsl.alloc(M.ns));
-  AMG_TRY(tot.alloc(1));
-  unsigned long long slots = 0;
-  auto heights = [&](const int *prow) -> int {
-    AMG_CU(cudaMemsetAsync(tot.p, 0, sizeof(unsigned long long), s));
-    if (M.ns) AMG_KCOUNT k_slice_h<<<nblk(32L * M.ns, 256), 256, 0, s>>>(A.nr, M.ns, A.rowptr.p, prow, hsl.p, tot.p);
-    AMG_LAUNCH_CHECK();
-    AMG_CU(cudaMemcpyAsync(&slots, tot.p, sizeof slots, cudaMemcpyDeviceToHost, s));
+  bool any = false;
+  for (int i = 0; i < nj; ++i) {
+    const SolveJob &J = jobs[i];
+    SolveMat &M = *J.M;
+    if (J.f64 && !J.f32 && !J.b16 && M.nr > 0 && slots[i] > 0 && (double)M.nnzb < 0.9 * (double)slots[i]) {
+      AMG_TRY(M.prow.alloc(M.nr));
+      AMG_KCOUNT k_sell_perm<<<nblk(M.nr, SELL_SIGMA), SELL_SIGMA, 0, s>>>(M.nr, M.rowptr, M.prow.p);
+      heights(i, M.prow.p, tot.p + nj + i);
+      any = true;
+    }
+  }
+  AMG_LAUNCH_CHECK();
+  if (any) {
+    AMG_CU(cudaMemcpyAsync(slots.data() + nj, tot.p + nj, (size_t)nj * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
     AMG_CU(cudaStreamSynchronize(s));
-    return AMG_OK;
-  };
-  AMG_TRY(heights(nullptr));
-  M.prow.release();
-  if (f64 && !f32 && !b16 && A.nr > 0 && slots > 0 && (double)A.nnzb < 0.9 * (double)slots) {
-    AMG_TRY(M.prow.alloc(A.nr));
-    AMG_KCOUNT k_sell_perm<<<nblk(A.nr, SELL_SIGMA), SELL_SIGMA, 0, s>>>(A.nr, A.rowptr.p, M.prow.p);
-    AMG_TRY(heights(M.prow.p));
   }
-  if (slots > 0x7fffffffULL) {
-    set_error("matrix too large for 32-bit slot offsets (%llu slots)", slots);
-    return AMG_ERR_ARG;
-  }
-  M.nslot = (long)slots;
-  AMG_TRY(M.slp.alloc(M.ns + 1));
-  AMG_TRY(dev_scan(M.ns, hsl.p, 0, M.slp.p, s));
-  const long tot_slots = M.nslot;
-  AMG_TRY(M.scol.alloc(tot_slots));
-  M.map = M.map64 = rule_map(M);
-  M.wps_rule = rule_wps(M);
-  if (M.wps_rule > 1) {  // partial sums of the one-warp-CTA mappings
-    AMG_TRY(M.wpart.alloc((size_t)M.ns * M.wps_rule * 2 * A.b * 32));
-    AMG_TRY(M.wtick.alloc(M.ns));
-    AMG_TRY(M.wtick.zero(s));
-  } else {
-    M.wpart.release();
-    M.wtick.release();
-  }
-  const long n9 = (long)A.b * A.b * tot_slots;
-  int *cols = M.scol.p;
-  if (f64) {
-    AMG_TRY(M.v64.alloc(n9));
-    to_sell<double>(A, M, cols, M.v64.p, s);
-    cols = nullptr;
-  }
-  if (f32) {
-    AMG_TRY(M.v32.alloc(n9));
-    to_sell<float>(A, M, cols, M.v32.p, s);
-    cols = nullptr;
-  }
-  if (b16) {
-    AMG_TRY(M.v16.alloc(n9));
-    to_sell<__nv_bfloat16>(A, M, cols, M.v16.p, s);
+  for (int i = 0; i < nj; ++i) {
+    const SolveJob &J = jobs[i];
+    const DevBsr &A = *J.A;
+    SolveMat &M = *J.M;
+    const unsigned long long sl = M.prow.p ? slots[nj + i] : slots[i];
+    if (sl > 0x7fffffffULL) {
+      set_error("matrix too large for 32-bit slot offsets (%llu slots)", sl);
+      return AMG_ERR_ARG;
+    }
+    M.nslot = (long)sl;
+    AMG_TRY(M.slp.alloc(M.ns + 1));
+    AMG_TRY(dev_scan(M.ns, hsl[i].p, 0, M.slp.p, s));
+    const long tot_slots = M.nslot;
+    AMG_TRY(M.scol.alloc(tot_slots));
+    M.map = M.map64 = rule_map(M);
+    M.wps_rule = rule_wps(M);
+    if (M.wps_rule > 1) {  // partial sums of the one-warp-CTA mappings
+      AMG_TRY(M.wpart.alloc((size_t)M.ns * M.wps_rule * 2 * A.b * 32));
+      AMG_TRY(M.wtick.alloc(M.ns));
+      AMG_TRY(M.wtick.zero(s));
+    } else {
+      M.wpart.release();
+      M.wtick.release();
+    }
+    const long n9 = (long)A.b * A.b * tot_slots;
+    int *cols = M.scol.p;
+    if (J.f64) {
+      AMG_TRY(M.v64.alloc(n9));
+      to_sell<double>(A, M, cols, M.v64.p, s);
+      cols = nullptr;
+    }
+    if (J.f32) {
+      AMG_TRY(M.v32.alloc(n9));
+      to_sell<float>(A, M, cols, M.v32.p, s);
+      cols = nullptr;
+    }
+    if (J.b16) {
+      AMG_TRY(M.v16.alloc(n9));
+      to_sell<__nv_bfloat16>(A, M, cols, M.v16.p, s);
+    }
   }
   AMG_LAUNCH_CHECK();
   return AMG_OK;
