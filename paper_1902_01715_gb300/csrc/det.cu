@@ -1217,12 +1217,16 @@ int fsai(const DevBsr &A, const DevBsr *Gs, int ksteps, int rho, double eps, int
   int dev = 0, nsm = 0;
   AMG_CU(cudaGetDevice(&dev));
   AMG_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // rows per warp: 4 while that still gives 32 warps per SM, else 2, else 1
-  // (measured first aFSAI pass on the beam's levels: 139k rows 15.5 ms with
-  // 4, 16.2 with 8; 30k rows 5.3 with 4, 6.1 with 8; 6.2k rows 1.3 with 1,
-  // 2.7 with 4; 1.3k rows 0.6 with 1, 2.4 with 4)
+  // rows per warp: 4 while that still gives 32 warps per SM, else 2, else 1;
+  // and 1 on levels with rows of 40 blocks or more, whose walks fill a whole
+  // warp (measured first aFSAI pass on the beam's levels: 139k rows of at
+  // most 27 blocks 15.1 ms with 4, 15.6 with 8, 16.6 with 2, 23.1 with 1;
+  // 30k rows of 47 blocks on average 4.2 ms with 1, 4.9 with 2, 5.1 with 4, 5.5
+  // with 8; 6.2k rows 1.2 with 1, 2.4 with 4; 1.3k rows 0.6 with 1, 2.4
+  // with 4)
   int ng = 4;
   while (ng > 1 && (long)A.nr / ng < 32L * nsm) ng /= 2;
+  if (K.compact) ng = 1;
   if (const char *e = getenv("AMG_FSAI_NG")) {
     const int v = atoi(e);
     if (v == 1 || v == 2 || v == 4 || v == 8) ng = v;

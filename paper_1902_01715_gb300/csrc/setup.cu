@@ -152,47 +152,55 @@ __global__ void k_to_dense(int nr, const int *__restrict__ rp, const int *__rest
 constexpr int CB = 32;
 constexpr int SW_THREADS = 544;  // 17 warps: one thread per lower entry of a 32 x 32 block
 
-// P = A_KK^{-1} by scalar sweeps of the diagonal tile in shared memory, one
-// thread per lower entry, two buffers (a step reads one and writes the
-// other: one barrier per step).  The thread of the next pivot forms its
+// Scalar sweeps of an nb x nb SPD block whose lower triangle is in b0, by
+// the NT threads of a CTA, thread t taking the lower entries t, t + NT, ...
+// (row order: (r, c), c <= r).  Two buffers (a step reads one and writes the
+// other: one barrier per step); the thread of the next pivot forms its
 // reciprocal as soon as it has the pivot, while the others update their
-// entries; a pivot that is not positive sets status.
-__global__ void __launch_bounds__(SW_THREADS) k_sw_pivot(int m, int k0, int nb, const double *__restrict__ D,
-                                                        double *__restrict__ P, int *__restrict__ status) {
-  pdl_wait();
-  __shared__ double a[2][CB][CB + 1];
+// entries.  Leaves P = block^{-1} (both triangles), or sets status if a
+// pivot is not positive.  Every thread of the CTA must call it.
+template <int NT>
+__device__ void sweep_block(double (*b0)[CB + 1], double (*b1)[CB + 1], int nb, double *__restrict__ P,
+                            int *__restrict__ status) {
+  constexpr int NE = (CB * (CB + 1) / 2 + NT - 1) / NT;
   __shared__ double rcp[2];
   __shared__ int bad;
   const int t = threadIdx.x;
-  int r = 0;  // lower entry t in row order: (r, c), c <= r
-  while ((r + 1) * (r + 2) / 2 <= t) ++r;
-  const int c = t - r * (r + 1) / 2;
-  const bool own = r < nb;
-  if (t == 0) bad = 0;
-  if (own) a[0][r][c] = D[(size_t)(k0 + r) * m + k0 + c];
-  __syncthreads();
+  int rr[NE], cc[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int u = t + e * NT;
+    int r = 0;
+    while ((r + 1) * (r + 2) / 2 <= u) ++r;
+    rr[e] = r;
+    cc[e] = u - r * (r + 1) / 2;
+  }
   if (t == 0) {
-    const double pv = a[0][0][0];
-    if (!(pv > 0.0)) bad = 1;
+    const double pv = b0[0][0];
+    bad = !(pv > 0.0);
     rcp[0] = 1.0 / pv;
   }
   __syncthreads();
   for (int j = 0; j < nb && !bad; ++j) {
-    const int cur = j & 1, nxt = cur ^ 1;
-    const double d = rcp[cur];
-    if (own) {
+    double (*cur)[CB + 1] = (j & 1) ? b1 : b0;
+    double (*nxt)[CB + 1] = (j & 1) ? b0 : b1;
+    const double d = rcp[j & 1];
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      const int r = rr[e], c = cc[e];
+      if (r >= nb) continue;
       // column j of the current matrix: entry x is stored at (max(x, j), min(x, j))
-      const double gr = r >= j ? a[cur][r][j] : a[cur][j][r];
-      const double gc = c >= j ? a[cur][c][j] : a[cur][j][c];
+      const double gr = r >= j ? cur[r][j] : cur[j][r];
+      const double gc = c >= j ? cur[c][j] : cur[j][c];
       double nv;
       if (r == j && c == j) nv = -d;
       else if (r == j) nv = gc * d;
       else if (c == j) nv = gr * d;
-      else nv = fma(-(gr * d), gc, a[cur][r][c]);
-      a[nxt][r][c] = nv;
+      else nv = fma(-(gr * d), gc, cur[r][c]);
+      nxt[r][c] = nv;
       if (r == j + 1 && c == j + 1 && j + 1 < nb) {  // the next pivot
         if (!(nv > 0.0)) bad = 1;
-        rcp[nxt] = 1.0 / nv;
+        rcp[(j + 1) & 1] = 1.0 / nv;
       }
     }
     __syncthreads();
@@ -201,11 +209,30 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_pivot(int m, int k0, int nb, 
     if (t == 0) atomicMin(status, AMG_ERR_NOT_SPD);
     return;
   }
-  if (own) {  // the sweeps leave -A_KK^{-1}
-    const double v = -a[nb & 1][r][c];
+  double (*fin)[CB + 1] = (nb & 1) ? b1 : b0;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {  // the sweeps leave -block^{-1}
+    const int r = rr[e], c = cc[e];
+    if (r >= nb) continue;
+    const double v = -fin[r][c];
     P[r * CB + c] = v;
     P[c * CB + r] = v;
   }
+}
+
+// P = A_KK^{-1} of the first pivot block (the later ones come from the
+// update kernel of the step before)
+__global__ void __launch_bounds__(SW_THREADS) k_sw_pivot(int m, int k0, int nb, const double *__restrict__ D,
+                                                        double *__restrict__ P, int *__restrict__ status) {
+  pdl_wait();
+  __shared__ double a[2][CB][CB + 1];
+  const int t = threadIdx.x;
+  int r = 0;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  const int c = t - r * (r + 1) / 2;
+  if (r < nb) a[0][r][c] = D[(size_t)(k0 + r) * m + k0 + c];
+  __syncthreads();
+  sweep_block<SW_THREADS>(a[0], a[1], nb, P, status);
 }
 
 // C[x][q] = A[x][k0+q] (pivot column, from the lower triangle) and
@@ -229,13 +256,19 @@ __global__ void k_sw_panels(int m, int k0, int nb, const double *__restrict__ D,
 
 // one lower tile (I >= J) per CTA, 32 x 32, 256 threads (4 rows each):
 // A_IJ -= C_I V_J; the pivot row and column tiles take V_J and V_I^T, the
-// pivot tile -P
+// pivot tile -P.  Look-ahead: when Pn is given, the CTA of the next pivot
+// tile (K+1, K+1) runs first (block 0) and, once its tile is updated, sweeps
+// it into Pn = A_{K+1,K+1}^{-1} (block size nbn), so the next step needs no
+// pivot kernel and that inversion overlaps this step's other tiles.
 __global__ void __launch_bounds__(256) k_sw_update(int m, int k0, int nb, double *__restrict__ D,
                                                    const double *__restrict__ P, const double *__restrict__ V,
-                                                   const double *__restrict__ C) {
+                                                   const double *__restrict__ C, double *__restrict__ Pn, int nbn,
+                                                   int *__restrict__ status) {
   pdl_wait();
   __shared__ double ct[CB][CB + 1], vt[CB][CB + 1];
-  const int b = blockIdx.x;
+  const int Kt = k0 / CB, lt = (Kt + 1) * (Kt + 2) / 2 + (Kt + 1);  // index of tile (K+1, K+1)
+  int b = blockIdx.x;
+  if (Pn) b = b == 0 ? lt : (b - 1 >= lt ? b : b - 1);
   int I = 0;  // lower tile b in row order: (I, J), J <= I
   while ((I + 1) * (I + 2) / 2 <= b) ++I;
   const int J = b - I * (I + 1) / 2;
@@ -251,20 +284,30 @@ __global__ void __launch_bounds__(256) k_sw_update(int m, int k0, int nb, double
     __syncthreads();
   }
   const int j = j0 + tx;
-  if (j >= m) return;
-  for (int rr = ty; rr < CB; rr += 8) {
-    const int i = i0 + rr;
-    if (i >= m) break;
-    double *dij = D + (size_t)i * m + j;
-    if (kr && kc) *dij = -P[rr * CB + tx];      // pivot tile
-    else if (kr) *dij = V[(size_t)rr * m + j];  // A_KJ = V_J
-    else if (kc) *dij = V[(size_t)tx * m + i];  // A_IK = V_I^T
-    else {
-      double s = 0.0;
-      for (int q = 0; q < nb; ++q) s = fma(ct[rr][q], vt[q][tx], s);
-      *dij -= s;
+  if (j < m)
+    for (int rr = ty; rr < CB; rr += 8) {
+      const int i = i0 + rr;
+      if (i >= m) break;
+      double *dij = D + (size_t)i * m + j;
+      if (kr && kc) *dij = -P[rr * CB + tx];      // pivot tile
+      else if (kr) *dij = V[(size_t)rr * m + j];  // A_KJ = V_J
+      else if (kc) *dij = V[(size_t)tx * m + i];  // A_IK = V_I^T
+      else {
+        double s = 0.0;
+        for (int q = 0; q < nb; ++q) s = fma(ct[rr][q], vt[q][tx], s);
+        *dij -= s;
+      }
     }
+  if (!Pn || b != lt) return;  // the same for the whole CTA
+  __syncthreads();  // the tile's new values (global, written by this CTA) and ct, vt free
+  for (int u = threadIdx.x; u < CB * (CB + 1) / 2; u += 256) {
+    int r = 0;
+    while ((r + 1) * (r + 2) / 2 <= u) ++r;
+    const int c = u - r * (r + 1) / 2;
+    if (r < nbn) ct[r][c] = D[(size_t)(i0 + r) * m + j0 + c];
   }
+  __syncthreads();
+  sweep_block<256>(ct, vt, nbn, Pn, status);
 }
 
 // A^{-1} from the swept array: the lower triangle negated and mirrored
@@ -762,20 +805,25 @@ static int coarse_factor(Handle *h, Level &L) {
   AMG_TRY(h->Cinv.alloc((size_t)m * m));
   AMG_TRY(h->Cinv.zero(s));
   if (L.n > 0) {
-    AMG_TRY(Pk.alloc(CB * CB));
+    AMG_TRY(Pk.alloc(2 * CB * CB));
     AMG_TRY(V.alloc((size_t)CB * m));
     AMG_TRY(C.alloc((size_t)m * CB));
     double *D = h->Cinv.p;
     if (L.A.b == 1) launch_k(k_to_dense<1>, L.n, 128, 0, s, L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
     else launch_k(k_to_dense<3>, L.n, 288, 0, s, L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, D);
     const int nt = (m + CB - 1) / CB;
-    for (int k0 = 0; k0 < m; k0 += CB) {
+    // the pivot inverses alternate between two buffers: step K reads its own
+    // while its update kernel writes the next one
+    double *Pb[2] = {Pk.p, Pk.p + CB * CB};
+    launch_k(k_sw_pivot, 1, SW_THREADS, 0, s, m, 0, m < CB ? m : CB, (const double *)D, Pb[0], st.p);
+    for (int k0 = 0, K = 0; k0 < m; k0 += CB, ++K) {
       const int nb = m - k0 < CB ? m - k0 : CB;
-      launch_k(k_sw_pivot, 1, SW_THREADS, 0, s, m, k0, nb, (const double *)D, Pk.p, st.p);
-      launch_k(k_sw_panels, nblk((long)CB * m, 256), 256, 0, s, m, k0, nb, (const double *)D, (const double *)Pk.p,
+      const int k1 = k0 + CB, nbn = k1 < m ? (m - k1 < CB ? m - k1 : CB) : 0;
+      double *Pc = Pb[K & 1], *Pn = nbn > 0 ? Pb[(K + 1) & 1] : nullptr;
+      launch_k(k_sw_panels, nblk((long)CB * m, 256), 256, 0, s, m, k0, nb, (const double *)D, (const double *)Pc,
                V.p, C.p);
-      launch_k(k_sw_update, nt * (nt + 1) / 2, 256, 0, s, m, k0, nb, D, (const double *)Pk.p, (const double *)V.p,
-               (const double *)C.p);
+      launch_k(k_sw_update, nt * (nt + 1) / 2, 256, 0, s, m, k0, nb, D, (const double *)Pc, (const double *)V.p,
+               (const double *)C.p, Pn, nbn, st.p);
     }
     launch_k(k_sw_final, nblk((long)m * m, 256), 256, 0, s, m, D);
     AMG_LAUNCH_CHECK();
