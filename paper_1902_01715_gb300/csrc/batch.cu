@@ -303,7 +303,12 @@ enum { BF_DONE = 0, BF_TICKET = 1, BF_STATUS = 2, BF_MAXIT = 3, BF_ITER = 4, BF_
 // true-residual restarts of one batched solve
 constexpr int kMaxBatchRestarts = 8;
 
-constexpr int BRED_BLOCKS = 148;
+// Grid of the per-iteration vector kernels: two CTAs per SM (of 152), each
+// thread streaming BUNR elements per pass with all their loads issued first
+// (enough bytes in flight to keep HBM busy), and few block partials for the
+// last block to add up.
+constexpr int BRED_BLOCKS = 304;
+constexpr int BUNR = 4;
 
 // Per-column partial sums of one block into part[blockIdx][c]; the last
 // block adds the partials in block order and runs fin(c, total) per column.
@@ -374,8 +379,18 @@ __global__ void k_bpq(long n, int k, const double *__restrict__ p, const double 
                       int *flags, double *part) {
   if (flags[BF_DONE]) return;
   double v = 0.0;
-  const long stride = (long)gridDim.x * blockDim.x;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) v += p[t] * q[t];
+  const long stride = (long)gridDim.x * blockDim.x, N = n * k;
+  for (long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x; t0 < N; t0 += BUNR * stride) {
+    double pv[BUNR], qv[BUNR];
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) {
+      const long t = t0 + u * stride;
+      pv[u] = t < N ? p[t] : 0.0;
+      qv[u] = t < N ? q[t] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) v += pv[u] * qv[u];
+  }
   bfinish(v, k, part, flags, [&](int c, double tot) {
     sc[BS_PQ * k + c] = tot;
     if (col_active(flags, c)) {
@@ -395,18 +410,36 @@ __global__ void k_bxr(long n, int k, double *__restrict__ x, double *__restrict_
                       const double *__restrict__ q, TX *__restrict__ rlow, double *sc, int *flags, double *part) {
   if (flags[BF_DONE]) return;
   double v = 0.0;
-  const long stride = (long)gridDim.x * blockDim.x;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) {
-    const int c = (int)(t % k);
-    double ri = r[t];
-    if (col_active(flags, c)) {
-      const double a = sc[BS_ALPHA * k + c];
-      x[t] += a * p[t];
-      ri = ri - a * q[t];
-      r[t] = ri;
+  const long stride = (long)gridDim.x * blockDim.x, N = n * k;
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  // the stride is a multiple of k: a thread keeps its column
+  const int c = (int)(tid % k);
+  const bool act = col_active(flags, c);
+  const double a = act ? sc[BS_ALPHA * k + c] : 0.0;
+  for (long t0 = tid; t0 < N; t0 += BUNR * stride) {
+    double rv[BUNR], xv[BUNR], pv[BUNR], qv[BUNR];
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) {
+      const long t = t0 + u * stride;
+      const bool in = t < N;
+      rv[u] = in ? r[t] : 0.0;
+      xv[u] = in && act ? x[t] : 0.0;
+      pv[u] = in && act ? p[t] : 0.0;
+      qv[u] = in && act ? q[t] : 0.0;
     }
-    if (rlow) rlow[t] = (TX)ri;
-    v += ri * ri;
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) {
+      const long t = t0 + u * stride;
+      if (t >= N) break;
+      double ri = rv[u];
+      if (act) {
+        x[t] = xv[u] + a * pv[u];
+        ri = ri - a * qv[u];
+        r[t] = ri;
+      }
+      if (rlow) rlow[t] = (TX)ri;
+      v += ri * ri;
+    }
   }
   bfinish(v, k, part, flags, [&](int c, double tot) {
     if (!col_active(flags, c)) return;
@@ -430,16 +463,24 @@ __global__ void k_brz(long n, int k, const double *__restrict__ r, double *__res
                       const double *__restrict__ zold, int flexible, double *sc, int *flags, double *part) {
   if (flags[BF_DONE]) return;
   double v = 0.0;
-  const long stride = (long)gridDim.x * blockDim.x;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) {
-    double zi;
-    if (zlow) {
-      zi = (double)zlow[t];
-      z[t] = zi;
-    } else {
-      zi = z[t];
+  const long stride = (long)gridDim.x * blockDim.x, N = n * k;
+  for (long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x; t0 < N; t0 += BUNR * stride) {
+    double zv[BUNR], rv[BUNR], ov[BUNR];
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) {
+      const long t = t0 + u * stride;
+      const bool in = t < N;
+      zv[u] = in ? (zlow ? (double)zlow[t] : z[t]) : 0.0;
+      rv[u] = in ? r[t] : 0.0;
+      ov[u] = in && flexible ? zold[t] : 0.0;
     }
-    v += r[t] * (flexible ? zi - zold[t] : zi);
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) {
+      const long t = t0 + u * stride;
+      if (t >= N) break;
+      if (zlow) z[t] = zv[u];
+      v += rv[u] * (flexible ? zv[u] - ov[u] : zv[u]);
+    }
   }
   // for the flexible variant the sum above is r.(z - z_old); r.z itself is
   // needed as the next rz: accumulate it in a second pass over the block
@@ -452,8 +493,18 @@ __global__ void k_brz2(long n, int k, const double *__restrict__ r, const double
                        double *sc, int *flags, double *part) {
   if (flags[BF_DONE]) return;
   double v = 0.0;
-  const long stride = (long)gridDim.x * blockDim.x;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) v += r[t] * z[t];
+  const long stride = (long)gridDim.x * blockDim.x, N = n * k;
+  for (long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x; t0 < N; t0 += BUNR * stride) {
+    double rv[BUNR], zv[BUNR];
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) {
+      const long t = t0 + u * stride;
+      rv[u] = t < N ? r[t] : 0.0;
+      zv[u] = t < N ? z[t] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) v += rv[u] * zv[u];
+  }
   bfinish(v, k, part, flags, [&](int c, double tot) {
     const double prev = sc[BS_RZ * k + c];
     const double num = flexible ? sc[BS_BETA * k + c] : tot;
@@ -469,12 +520,26 @@ __global__ void k_brz2(long n, int k, const double *__restrict__ r, const double
 __global__ void k_bp(long n, int k, double *__restrict__ p, const double *__restrict__ z, double *__restrict__ zold,
                      int flexible, const double *sc, int *flags) {
   if (flags[BF_DONE]) return;
-  const long stride = (long)gridDim.x * blockDim.x;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += stride) {
-    const int c = (int)(t % k);
-    if (!col_active(flags, c)) continue;
-    p[t] = z[t] + sc[BS_BETA * k + c] * p[t];
-    if (flexible) zold[t] = z[t];
+  const long stride = (long)gridDim.x * blockDim.x, N = n * k;
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = (int)(tid % k);  // the stride is a multiple of k: a thread keeps its column
+  if (!col_active(flags, c)) return;
+  const double b = sc[BS_BETA * k + c];
+  for (long t0 = tid; t0 < N; t0 += BUNR * stride) {
+    double zv[BUNR], pv[BUNR];
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) {
+      const long t = t0 + u * stride;
+      zv[u] = t < N ? z[t] : 0.0;
+      pv[u] = t < N ? p[t] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < BUNR; ++u) {
+      const long t = t0 + u * stride;
+      if (t >= N) break;
+      p[t] = zv[u] + b * pv[u];
+      if (flexible) zold[t] = zv[u];
+    }
   }
 }
 
@@ -610,13 +675,13 @@ static void biteration(Handle *h, Batch &B, bool mixed) {
     bvcycle<float>(h, B, 0, B.rlow.p, B.zlow.p, done);
     AMG_KCOUNT k_brz<float><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.r.p, B.z.p, B.zlow.p, B.zold.p, 1, B.sc.p, fl, B.part.p);
     AMG_KCOUNT k_brz2<<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.r.p, B.z.p, 1, B.sc.p, fl, B.part.p);
-    AMG_KCOUNT k_bp<<<BRED_BLOCKS, 256, 0, s>>>(n, k, B.p.p, B.z.p, B.zold.p, 1, B.sc.p, fl);
+    AMG_KCOUNT k_bp<<<BRED_BLOCKS, bt, 0, s>>>(n, k, B.p.p, B.z.p, B.zold.p, 1, B.sc.p, fl);
   } else {
     AMG_KCOUNT k_bxr<double><<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.x.p, B.r.p, B.p.p, B.q.p, (double *)nullptr, B.sc.p, fl,
                                                           B.part.p);
     bvcycle<double>(h, B, 0, B.r.p, B.z.p, done);
     AMG_KCOUNT k_brz2<<<BRED_BLOCKS, bt, shm, s>>>(n, k, B.r.p, B.z.p, 0, B.sc.p, fl, B.part.p);
-    AMG_KCOUNT k_bp<<<BRED_BLOCKS, 256, 0, s>>>(n, k, B.p.p, B.z.p, B.zold.p, 0, B.sc.p, fl);
+    AMG_KCOUNT k_bp<<<BRED_BLOCKS, bt, 0, s>>>(n, k, B.p.p, B.z.p, B.zold.p, 0, B.sc.p, fl);
   }
   AMG_KCOUNT k_bcheck<<<1, 1, 0, s>>>(k, fl);
 }
