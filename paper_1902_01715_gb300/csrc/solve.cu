@@ -187,6 +187,9 @@ constexpr int RED_BLOCKS = 296;
 // true-residual restarts of one solve (each one V-cycle and one FP64 product more)
 constexpr int kMaxRestarts = 8;
 constexpr int RED_THREADS = 256;
+// elements per thread and pass of the PCG vector kernels, their loads issued
+// first (the same elements in the same order as one at a time: same sums)
+constexpr int VUNR = 4;
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
   for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -232,7 +235,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_pq(long n, const double *__
   if (flags[F_DONE]) return;
   __shared__ double sh[32];
   double v = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) v += p[i] * q[i];
+  const long S = (long)gridDim.x * blockDim.x;
+  for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += VUNR * S) {
+    double pv[VUNR], qv[VUNR];
+#pragma unroll
+    for (int u = 0; u < VUNR; ++u) {
+      const long i = i0 + u * S;
+      pv[u] = i < n ? p[i] : 0.0;
+      qv[u] = i < n ? q[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < VUNR; ++u)
+      if (i0 + u * S < n) v += pv[u] * qv[u];
+  }
   pdl_trigger();
   finish_reduce(v, part, flags, sh, [&](double tot) {
     sc[P_PQ] = tot;
@@ -255,12 +270,28 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_xr(long n, double *__restri
   __shared__ double sh[32];
   const double a = sc[P_ALPHA];
   double v = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    x[i] += a * p[i];
-    const double ri = r[i] - a * q[i];
-    r[i] = ri;
-    if (rlow) rlow[i] = (TX)ri;
-    v += ri * ri;
+  const long S = (long)gridDim.x * blockDim.x;
+  for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += VUNR * S) {
+    double xv[VUNR], rv[VUNR], pv[VUNR], qv[VUNR];
+#pragma unroll
+    for (int u = 0; u < VUNR; ++u) {
+      const long i = i0 + u * S;
+      const bool in = i < n;
+      xv[u] = in ? x[i] : 0.0;
+      rv[u] = in ? r[i] : 0.0;
+      pv[u] = in ? p[i] : 0.0;
+      qv[u] = in ? q[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < VUNR; ++u) {
+      const long i = i0 + u * S;
+      if (i >= n) break;
+      x[i] = xv[u] + a * pv[u];
+      const double ri = rv[u] - a * qv[u];
+      r[i] = ri;
+      if (rlow) rlow[i] = (TX)ri;
+      v += ri * ri;
+    }
   }
   pdl_trigger();
   finish_reduce(v, part, flags, sh, [&](double tot) {
@@ -290,16 +321,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_rz(long n, const double *__
   if (flags[F_DONE]) return;
   __shared__ double sh[32];
   double v = 0.0, v2 = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    double zi;
-    if (zlow) {
-      zi = (double)zlow[i];
-      z[i] = zi;
-    } else {
-      zi = z[i];
+  const long S = (long)gridDim.x * blockDim.x;
+  for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += VUNR * S) {
+    double zv[VUNR], rv[VUNR], ov[VUNR];
+#pragma unroll
+    for (int u = 0; u < VUNR; ++u) {
+      const long i = i0 + u * S;
+      const bool in = i < n;
+      zv[u] = in ? (zlow ? (double)zlow[i] : z[i]) : 0.0;
+      rv[u] = in ? r[i] : 0.0;
+      ov[u] = in && flexible ? zold[i] : 0.0;
     }
-    v += r[i] * zi;
-    if (flexible) v2 += r[i] * zold[i];
+#pragma unroll
+    for (int u = 0; u < VUNR; ++u) {
+      const long i = i0 + u * S;
+      if (i >= n) break;
+      if (zlow) z[i] = zv[u];
+      v += rv[u] * zv[u];
+      if (flexible) v2 += rv[u] * ov[u];
+    }
   }
   const double b2 = flexible ? block_sum(v2, sh) : 0.0;
   if (flexible && threadIdx.x == 0) part2[blockIdx.x] = b2;
@@ -324,9 +364,22 @@ __global__ void k_pcg_p(long n, double *__restrict__ p, const double *__restrict
   pdl_wait();
   if (flags[F_DONE]) return;
   const double b = sc[P_BETA];
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    p[i] = z[i] + b * p[i];
-    if (flexible) zold[i] = z[i];
+  const long S = (long)gridDim.x * blockDim.x;
+  for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += VUNR * S) {
+    double zv[VUNR], pv[VUNR];
+#pragma unroll
+    for (int u = 0; u < VUNR; ++u) {
+      const long i = i0 + u * S;
+      zv[u] = i < n ? z[i] : 0.0;
+      pv[u] = i < n ? p[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < VUNR; ++u) {
+      const long i = i0 + u * S;
+      if (i >= n) break;
+      p[i] = zv[u] + b * pv[u];
+      if (flexible) zold[i] = zv[u];
+    }
   }
 }
 
