@@ -42,10 +42,10 @@ FP64_PEAK_SOURCE = "nominal FP64 rate (1.25 TFLOP/s); FMA-chain probe measured 1
 # ncu captures summarised under profiles/; a kernel whose code changed since its
 # capture has no entry
 TRAFFIC: dict = {
-    # level-0 K of the 128x32x32 beam, one warp per slice (here the one-warp
-    # CTA form k_sellmv_w<double, double, 3, 0, 1, 2>): 279.65 MB read +
-    # 3.88 MB written (profiles/k_sellmv_level0_beam.md)
-    "k_sellmv_fp64_level0": 283.53e6,
+    # level-0 K of the 128x32x32 beam, two warps per slice (here
+    # k_sellmv<double, double, 3, 0, 2, 2>): 278.63 MB read + 4.44 MB written
+    # (profiles/k_sellmv_level0_beam.md)
+    "k_sellmv_fp64_level0": 283.07e6,
     # det::k_spmv_cols<3, 1>, level-0 A times 10 columns: 307.19 MB read +
     # 28.09 MB written (profiles/k_spmv_cols_beam.md)
     "k_spmv_cols": 335.28e6,

@@ -626,12 +626,16 @@ static void to_sell(const DevBsr &A, const SolveMat &M, int *cols, T *dst, cudaS
 
 // Warps per slice: few slices of long rows leave SMs idle unless several
 // warps share a slice, so the warps per slice double while the launch has
-// fewer than 16 warps per SM and each warp keeps at least two blocks of an
-// average row per chunk.  This fixes the order of every row sum.
+// fewer than 32 warps per SM and each warp keeps at least two blocks of an
+// average row per chunk.  This fixes the order of every row sum.  (Measured
+// on the beam, solve to 1e-8: with a bound of 16 warps per SM FP64 64.3 ms,
+// FP32 47.1 ms; 32: 63.1 and 41.0 ms, where the FP32 sums' rounding also
+// took the FP32 count from 103 to 93 iterations; 8: 69.0, 52.3; 64: 65.5,
+// 44.5.)
 static int rule_wps(const SolveMat &M) {
   const double avg = M.nr ? (double)M.nnzb / M.nr : 1.0;
   int wps = 1;
-  while (wps < 16 && (long)M.ns * wps < 16L * 152 && avg / (2.0 * wps * 2) >= 1.0) wps *= 2;
+  while (wps < 16 && (long)M.ns * wps < 32L * 152 && avg / (2.0 * wps * 2) >= 1.0) wps *= 2;
   return wps;
 }
 
