@@ -216,17 +216,26 @@ def extra_slab(A, W):
     return out
 
 
-def extra_batched(A, W):
-    """The 96^3 cube with 64 load cases: one block solve (FP32 V-cycle, FP64
-    CG, per-column masks) against solving the cases one at a time in FP64."""
+def batched_problem(A, p):
+    """K, V0 of the cube recipe p on the device and its load cases as the
+    columns of one (3 nfree, k) FP64 right-hand side."""
     import torch
-    p = W.cube_batched()
     d = gpu_problem(A, p)
     k = p.nodal.shape[0]
     F = torch.empty((3 * d["nfree"], k), dtype=torch.float64, device="cuda")
     for c in range(k):
         F[:, c] = A.fe_load(p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, p.clamp_axis, "top_nodal",
                             p=p.nodal[c].reshape(-1), nfree=d["nfree"])
+    return d, F
+
+
+def extra_batched(A, W):
+    """The 96^3 cube with 64 load cases: one block solve (FP32 V-cycle, FP64
+    CG, per-column masks) against solving the cases one at a time in FP64."""
+    import torch
+    p = W.cube_batched()
+    d, F = batched_problem(A, p)
+    k = F.shape[1]
     S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec="fp32")
     (X, its, rel, rc), ms_b = _timed(lambda: S.solve(F, RTOL))
     S64 = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"])
@@ -290,7 +299,8 @@ def extra_scalar_vs_block(A, W):
         st = S.stats()
         out[name] = {"ms_per_solution": ms, "n_it": its[0], "setup_ms": st["T_p"] * 1e3, "solve_ms": st["T_s"] * 1e3,
                      "levels": st["nlev"], "C_gd": st["C_gd"], "C_op": st["C_op"], "C_fs": st["C_fs"],
-                     "true_relres": rel[0]}
+                     "true_relres": rel[0],
+                     "setup_phases_ms": {q: 1e3 * st[q] for q in ("T_sm", "T_ts", "T_cs", "T_pl", "T_rap")}}
         S.close()
     return out
 
@@ -322,8 +332,12 @@ def extra_beam6502k(A, W):
     S = A.Solver(d["rowptr"], d["col"], vals, V0, vcycle_prec="fp32", maxit=4000)
     x, its, rel, rc = S.solve(f, RTOL)
     st = S.stats()
+    # rc follows the recurrence rule (Sec. 4); the FP64 true residual can stay
+    # above rtol on this shape, so both residuals are reported
     out["fp32"] = {"n_it": its[0], "rc": rc, "setup_ms": st["T_p"] * 1e3, "solve_ms": st["T_s"] * 1e3,
-                   "levels": st["nlev"], "C_op": st["C_op"], "true_relres": rel[0]}
+                   "levels": st["nlev"], "C_op": st["C_op"], "true_relres": rel[0],
+                   "rec_relres": st["relres_rec"], "restarts": st["restarts"],
+                   "true_residual_met": bool(rel[0] <= RTOL)}
     S.close()
     return out
 
@@ -686,6 +700,35 @@ def run_micro(args):
     print(json.dumps({"micro": rows}), flush=True)
 
 
+def run_batched(args):
+    """One batched solve of the cube recipe at n^3 with its 64 load cases
+    (FP32 V-cycle, FP64 CG, per-column masks) after a warm-up solve, inside
+    the NVTX range "batched" (the case the batched-product profiles capture)."""
+    import torch
+
+    import paper_1902_01715_gb300 as A
+    import workloads as W
+    torch.cuda.set_device(0)
+    A.build()
+    A.lib()
+    d, F = batched_problem(A, W.cube_batched(args.batched, 64))
+    S = A.Solver(d["rowptr"], d["col"], d["vals"], d["V0"], vcycle_prec="fp32")
+    S.solve(F, RTOL)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("batched")
+    e0.record()
+    X, its, rel, rc = S.solve(F, RTOL)
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"batched": {"n": args.batched, "k": F.shape[1], "rc": rc, "n_it_max": max(its),
+                                  "ms": e0.elapsed_time(e1), "max_true_relres": max(rel)}}), flush=True)
+    S.close()
+    if rc != 0:
+        sys.exit(1)
+
+
 def run_sweep(args):
     """Parameter sensitivity on the default beam (GPU timings): one JSON line
     per setting of the coarsening threshold theta, the prolongation limits
@@ -747,6 +790,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="parameter sensitivity on the beam (one line per setting)")
     ap.add_argument("--dims", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
                     help="beam size nx,ny,nz for --single (default 128,32,32)")
+    ap.add_argument("--batched", type=int, default=0, metavar="N",
+                    help="one batched solve of the N^3 cube with 64 load cases (for profilers)")
     ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -769,6 +814,8 @@ def main():
         run_sweep(args)
     elif args.micro:
         run_micro(args)
+    elif args.batched:
+        run_batched(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -214,7 +214,8 @@ long long amg_launch_count(void);
  * whose device memory is all held by its own pool (a device allocation inside
  * the call would fail or fragment it), or one that keeps every allocation out of
  * its iteration loop.  Same arguments, result and precision as amg_vcycle;
- * y and z are device vectors of 3*nnodes entries owned by the caller.
+ * y and z are device vectors of block*nnodes entries (the handle's rows) owned
+ * by the caller.
  * Scratch: a file-scope device array of 256 bytes in the library (a flag
  * block), held by every GPU that loads the library until the process exits.
  * The first call on a device looks up the array's device address (with that
