@@ -1526,17 +1526,29 @@ __global__ void __launch_bounds__(32) k_cdots(int n, int t, int nk, CDot a, doub
 }
 
 // y_j = A x_j for the t columns of n x t blocks, row sums in the fixed
-// order.  One warp per block row: lane (j, r) computes dof row r of column j,
-// so every lane walks the same blocks (the row's values are read once per
-// warp and no FP64 instruction runs on a partly idle warp for lack of work).
+// order.  rw block rows per warp (rw = 1 unless BS t <= 16): lane (g, j, r)
+// computes dof row r of column j of the warp's block row g, so the lanes of
+// a row walk the same blocks (the row's values are read once per lane group)
+// and few lanes idle: with t = 10 columns a scalar row (BS = 1) fills 10
+// lanes, three rows 30.  Every output is the same chain of fused
+// multiply-adds whatever rw is.
 template <int BS, int U>
-__global__ void k_spmv_cols(int nr, int t, const int *__restrict__ rowptr, const int *__restrict__ col,
+__global__ void k_spmv_cols(int nr, int t, int rw, const int *__restrict__ rowptr, const int *__restrict__ col,
                             const double *__restrict__ val, const double *__restrict__ X, double *__restrict__ Y) {
   pdl_wait();
   const long n = (long)BS * nr;
-  const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (I >= nr) return;
+  if (rw > 1) {
+    const int per = BS * t, g = lane / per, pr = lane - g * per;
+    const long I = w * rw + g;
+    if (g >= rw || I >= nr) return;
+    const int j = pr / BS, r = pr - BS * j;
+    Y[(size_t)j * n + BS * I + r] = row_chain<BS, U>(rowptr[I], rowptr[I + 1], r, col, val, X + (size_t)j * n, 0.0);
+    return;
+  }
+  if (w >= nr) return;
+  const int I = (int)w;
   const int kb = rowptr[I], ke = rowptr[I + 1];
   for (int pr = lane; pr < BS * t; pr += 32) {
     const int j = pr / BS, r = pr - BS * j;
@@ -1785,10 +1797,12 @@ __device__ int gen_eig_cta(int t, const double *H, const double *M, double *U, d
 
 template <int BS>
 static void spmv_cols_b(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
+  const int rw = BS * t <= 16 ? 32 / (BS * t) : 1;  // block rows per warp
+  const long warps = ((long)A.nr + rw - 1) / rw;
   if (A.nr < SMALL_ROWS)
-    launch_k(k_spmv_cols<BS, 4>, nblk(32L * A.nr, 256), 256, 0, s, A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+    launch_k(k_spmv_cols<BS, 4>, nblk(32L * warps, 256), 256, 0, s, A.nr, t, rw, A.rowptr.p, A.col.p, A.val.p, X, Y);
   else
-    launch_k(k_spmv_cols<BS, 1>, nblk(32L * A.nr, 256), 256, 0, s, A.nr, t, A.rowptr.p, A.col.p, A.val.p, X, Y);
+    launch_k(k_spmv_cols<BS, 1>, nblk(32L * warps, 256), 256, 0, s, A.nr, t, rw, A.rowptr.p, A.col.p, A.val.p, X, Y);
 }
 
 int spmv_cols(const DevBsr &A, int t, const double *X, double *Y, cudaStream_t s) {
