@@ -216,6 +216,16 @@ def extra_slab(A, W):
     return out
 
 
+def run_extra(fn, *args):
+    """fn(*args), or {"error": ...} when it raises: the extra workloads are
+    reported beside the headline, and a failing one must not take the
+    headline line with it."""
+    try:
+        return fn(*args)
+    except Exception as e:  # noqa: BLE001 -- recorded in the JSON line
+        return {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+
+
 def batched_problem(A, p):
     """K, V0 of the cube recipe p on the device and its load cases as the
     columns of one (3 nfree, k) FP64 right-hand side."""
@@ -629,9 +639,9 @@ def run_ours(args):
 
     extras = None
     if not args.no_extras:
-        extras = {"mixed_precision": extra_slab(A, W), "batched": extra_batched(A, W),
-                  "adjoint": extra_adjoint(A, W), "scalar_vs_block": extra_scalar_vs_block(A, W),
-                  "beam6502k": extra_beam6502k(A, W)}
+        extras = {name: run_extra(fn, A, W) for name, fn in (
+            ("mixed_precision", extra_slab), ("batched", extra_batched), ("adjoint", extra_adjoint),
+            ("scalar_vs_block", extra_scalar_vs_block), ("beam6502k", extra_beam6502k))}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -52,3 +52,15 @@ def test_two_cpu_ranks_aggregate_and_gate():
         assert ms == 150.0
         assert value == pytest.approx(2 * 1e3 / 150.0)
         assert out is None
+
+
+def test_failing_extra_is_recorded_not_raised():
+    """An extra workload that raises is reported as an error entry, so the
+    bench's headline line is still printed."""
+    import bench
+
+    def bad(*_):
+        raise RuntimeError("out of memory on the extra workload")
+    assert bench.run_extra(lambda a, b: {"n_it": a + b}, 1, 2) == {"n_it": 3}
+    got = bench.run_extra(bad, None, None)
+    assert set(got) == {"error"} and got["error"].startswith("RuntimeError: out of memory")
