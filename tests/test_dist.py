@@ -58,7 +58,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, out):
+def _rank(rank, world, port, out, block=3):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -74,7 +74,9 @@ def _rank(rank, world, port, out):
     try:
         p = W.beam(20, 5, 5)
         K, V0, f, nm = oracle_problem(orc, p)
-        H = orc.Hierarchy(K, V0, orc.default_params(3, n_coarse=200))
+        if block == 1:  # the paper's scalar form: one row per dof
+            K = orc.to_scalar(K)
+        H = orc.Hierarchy(K, V0, orc.default_params(block, n_coarse=200))
         S = D.DistSolver(HostBackend(H))
         import torch
         b = torch.as_tensor(f)
@@ -88,12 +90,12 @@ def _rank(rank, world, port, out):
         td.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_distributed_pcg_matches_single_process(world):
+@pytest.mark.parametrize("world,block", [(2, 3), (3, 3), (2, 1)])
+def test_distributed_pcg_matches_single_process(world, block):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q, block)) for r in range(world)]
     for pr in procs:
         pr.start()
     x, it, rr, xo, ito, nlev, halo = q.get(timeout=300)
